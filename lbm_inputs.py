@@ -1,0 +1,97 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds no arithmetic of the simulated method.  It only draws
+numbers (with ``numpy.random.default_rng``) and lays them out:
+
+* the initial density profile of the Carleman-LBM workloads:
+  rho(x) = 1 + A sin(2 pi x / Nx) + U(-0.01, 0.01), drawn for x = 0..Nx-1,
+  at zero velocity.  The initial distribution is the zero-velocity
+  equilibrium of Eq. feq, which reduces to f_q = w_q rho with the D1Q3
+  weights (1/6, 1/6, 2/3) in the paper's velocity order (e=+1, -1, 0);
+* relaxation times drawn uniformly from a range;
+* random QSP phase lists for parity tests;
+* the random gate stream of the gate-vocabulary microbenchmark, emitted as
+  canonical gate records (op, target, cmask, cval, angle, tag).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+D1Q3_WEIGHTS = (1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0)
+
+
+def density_profile(Nx: int, rng: np.random.Generator, amplitude: float = 0.05,
+                    noise: float = 0.01) -> np.ndarray:
+    x = np.arange(Nx, dtype=np.float64)
+    return 1.0 + amplitude * np.sin(2.0 * np.pi * x / Nx) + rng.uniform(-noise, noise, Nx)
+
+
+def equilibrium_at_rest(rho: np.ndarray) -> np.ndarray:
+    """f0[alpha][q] = w_q rho(alpha), shape (Nx, 3)."""
+    return np.outer(rho, np.asarray(D1Q3_WEIGHTS))
+
+
+def lbm_instance(Nx: int, seed: int, tau=None, tau_range=None, amplitude: float = 0.05):
+    """One synthetic Carleman-LBM instance.
+
+    If ``tau`` is None it is drawn first from U(tau_range); the density noise
+    is drawn next.  Returns (f0 of shape (Nx, 3), tau).
+    """
+    rng = np.random.default_rng(seed)
+    if tau is None:
+        lo, hi = tau_range
+        tau = float(rng.uniform(lo, hi))
+    rho = density_profile(Nx, rng, amplitude)
+    return equilibrium_at_rest(rho), float(tau)
+
+
+def random_phases(d: int, seed: int) -> np.ndarray:
+    return np.random.default_rng(seed).uniform(-math.pi, math.pi, d + 1)
+
+
+def random_unit_state(n: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    return v / np.linalg.norm(v)
+
+
+def microbench_gates(n: int, count: int, seed: int):
+    """Gate stream of the vocabulary microbenchmark (canonical records, tag 0).
+
+    40% single-qubit RY or RZ (50/50, angle U[0, 2pi), uniform target);
+    30% CNOT (distinct random control and target); 20% multi-controlled X
+    with U{2..8} distinct controls; 10% controlled +1 on a random 6-qubit
+    register (LSB first) with one random control outside it, emitted as its
+    MCX cascade.  RZ(theta) = diag(e^{-i theta/2}, e^{i theta/2}) is emitted as
+    the ZPHASE record with angle -theta/2.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    X, RY, ZP = 0, 2, 3
+    for _ in range(count):
+        u = rng.uniform()
+        if u < 0.4:
+            tgt = int(rng.integers(n))
+            ang = float(rng.uniform(0.0, 2.0 * math.pi))
+            if rng.uniform() < 0.5:
+                out.append((RY, tgt, 0, 0, ang, 0))
+            else:
+                out.append((ZP, tgt, 0, 0, -ang / 2.0, 0))
+        elif u < 0.7:
+            c, t = (int(v) for v in rng.choice(n, 2, replace=False))
+            out.append((X, t, 1 << c, 1 << c, 0.0, 0))
+        elif u < 0.9:
+            nc = int(rng.integers(2, 9))
+            qs = [int(v) for v in rng.choice(n, nc + 1, replace=False)]
+            t, cs = qs[0], qs[1:]
+            m = sum(1 << c for c in cs)
+            out.append((X, t, m, m, 0.0, 0))
+        else:
+            qs = [int(v) for v in rng.choice(n, 7, replace=False)]
+            reg, c = qs[:6], qs[6]
+            for j in range(5, -1, -1):
+                m = (1 << c) | sum(1 << b for b in reg[:j])
+                out.append((X, reg[j], m, m, 0.0, 0))
+    return out

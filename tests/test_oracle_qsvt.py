@@ -1,0 +1,101 @@
+"""Pins for the classical QSVT evaluator (O5) and the QSP helpers."""
+import math
+
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+from oracle import circuit as C
+from oracle import physics as P
+from oracle import qsvt as Q
+from oracle import statevec as S
+from oracle.layout import Layout
+
+
+def _simulate_qsvt(Nx, tau, NC, K, dt, Nt, f0, phases):
+    lay = Layout(Nx, NC, K, Nt)
+    psi = np.zeros(1 << lay.n, dtype=complex)
+    init, _ = C.initial_state(lay, f0)
+    for k, v in init.items():
+        psi[k] = v
+    S.DenseSim(lay.n, check_norm=True).run(psi, C.build_qsvt(Nx, tau, NC, K, dt, Nt, phases))
+    return psi, lay
+
+
+@pytest.mark.parametrize("cfg,d", [((2, 0.8, 1, 1, 0.1, 1), 3), ((4, 0.8, 1, 2, 0.1, 2), 5),
+                                   ((8, 0.7, 1, 3, 0.2, 3), 3), ((2, 0.8, 2, 1, 0.1, 1), 3),
+                                   ((2, 1.1, 2, 3, 0.1, 2), 3)])
+def test_classical_qsvt_equals_gate_simulation(cfg, d):
+    """O5 (Re P^{SV}(L/lambda) b) equals O2 simulating the full QSVT gate list."""
+    Nx, tau, NC, K, dt, Nt = cfg
+    f0, _ = I.lbm_instance(Nx, 0, tau=tau)
+    ph = I.random_phases(d, 11)
+    y, lay, M, b = Q.qsvt_postselected(Nx, tau, NC, K, dt, Nt, f0, ph)
+    psi, lay = _simulate_qsvt(Nx, tau, NC, K, dt, Nt, f0, ph)
+    phys = lay.physical_indices()
+    assert np.max(np.abs(psi[phys] - y)) < 1e-13
+    anc = sum(1 << q for q in lay.regs["t"] + lay.regs["s"] + lay.regs["iL"])
+    idx = np.arange(1 << lay.n)
+    rest = (idx & anc) == 0
+    rest[phys] = False
+    assert np.max(np.abs(psi[rest])) < 1e-15
+
+
+def test_degree_one_is_L_b_over_lambda():
+    """Phases (0, 0): W = R(x), Re P(x) = x, so the output is (L/lambda_L) b."""
+    Nx, tau, NC, K, dt, Nt = 4, 0.8, 2, 2, 0.1, 2
+    f0, _ = I.lbm_instance(Nx, 0, tau=tau)
+    y, lay, M, b = Q.qsvt_postselected(Nx, tau, NC, K, dt, Nt, f0, [0.0, 0.0])
+    A = P.carleman_A(Nx, tau, NC)
+    L = P.l_matrix(A, dt, K, Nt)
+    lam = P.lambda_L(NC, K, P.l_max(A, dt))
+    assert np.max(np.abs(y - (L @ b) / lam)) < 1e-16
+
+
+@pytest.mark.parametrize("d", [1, 3, 5, 9])
+def test_chebyshev_phase_set(d):
+    """Phases (pi/4, -pi/2, ..., -pi/2, -pi/4) give Re P = (-1)^((d-1)/2) T_d."""
+    ph = [math.pi / 4] + [-math.pi / 2] * (d - 1) + [-math.pi / 4]
+    x = np.linspace(-1, 1, 101)
+    sign = (-1) ** ((d - 1) // 2)
+    assert np.max(np.abs(Q.qsp_poly(ph, x).real - sign * np.cos(d * np.arccos(x)))) < 1e-13
+    # and the singular-value transform on a small L equals W T_d(Sigma) V^T b
+    Nx, tau, NC, K, dt, Nt = 2, 0.8, 1, 1, 0.1, 1
+    f0, _ = I.lbm_instance(Nx, 3, tau=tau)
+    y, lay, M, b = Q.qsvt_postselected(Nx, tau, NC, K, dt, Nt, f0, ph)
+    Wm, s, Vt = np.linalg.svd(M.toarray())
+    ref = Wm @ (sign * np.cos(d * np.arccos(np.clip(s, -1, 1))) * (Vt @ b))
+    assert np.max(np.abs(y - ref)) < 1e-13
+
+
+def test_cheb_coeffs_exact_for_polynomials():
+    rng = np.random.default_rng(0)
+    c = rng.standard_normal(12)
+    x = Q.chebyshev_nodes(12)
+    vals = np.polynomial.chebyshev.chebval(x, c)
+    assert np.max(np.abs(Q.cheb_coeffs(vals) - c)) < 1e-13
+
+
+@pytest.mark.parametrize("kappa,d", [(10.0, 31), (50.0, 121), (294.3, 1957)])
+def test_inverse_target_minimal_residual(kappa, d):
+    """1 - x p(x) is the shifted Chebyshev residual: max on [1/kappa, 1] = 1/T_n(z0)."""
+    Pf, scale = Q.inverse_target(kappa, d)
+    a = 1.0 / kappa
+    n = (d + 1) // 2
+    bound = 1.0 / math.cosh(n * math.acosh((1 + a * a) / (1 - a * a)))
+    x = np.linspace(a, 1.0, 20001)
+    resid = np.abs(1.0 - x * Pf(x) / scale)
+    assert np.max(resid) <= bound * (1 + 1e-9) + 1e-14
+    assert np.max(resid) >= 0.99 * bound
+    grid = np.linspace(-1, 1, 40001)
+    assert np.max(np.abs(Pf(grid[grid != 0]))) <= 0.51
+    assert np.max(np.abs(Pf(-x) + Pf(x))) < 1e-12
+
+
+def test_degree_formula():
+    """Eq. d-star with eps = 1e-3, rounded up to odd."""
+    for kappa in (7.0, 294.31456452027527, 7100.0):
+        d = Q.degree_from_kappa(kappa, 1e-3)
+        raw = kappa * math.log(2 * kappa / 1e-3) / 2
+        assert d % 2 == 1 and raw <= d <= raw + 2
+    assert Q.degree_from_kappa(294.31456452027527, 1e-3) == 1957
