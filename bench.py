@@ -1,0 +1,310 @@
+#!/usr/bin/env python3
+"""Benchmark of the state-vector QSVT path on GB300.
+
+Default workload (the precision configuration): Nx = 64, N_C = 2, K = 4,
+Nt = 16, dt = 0.1, tau drawn from U[0.6, 1.2] with seed 1, initial density
+1 + 0.05 sin(2 pi x / Nx) + U(-0.01, 0.01), QSVT degree d = 13 (the
+truncated-degree timing run), 32 qubits, complex64 state (32 GiB, twice for
+the gather ping-pong), fused sweeps.
+
+A step is one pass of the whole hot path through the C ABI: csim_init (load
+b), csim_run (the QSVT circuit: 14 fused sweeps over 2^32 amplitudes) and
+csim_postselect (FP64 norm and success probability).  The metric is
+amplitude-gate updates per second: the sum over the circuit's elementary
+gates of the amplitudes each gate changes, divided by the step time.
+
+Output: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(naive gate-by-gate simulator) on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbm_inputs as I  # noqa: E402
+
+METRIC = "amplitude-gate updates/s"
+UNIT = "amp-updates/s"
+
+WORKLOADS = {
+    # name: (Nx, N_C, K, Nt, dt, tau or None, tau_range, seed, d, kappa_qsvt, precision)
+    "precision-nx64-k4-nt16-d13-c64": (64, 2, 4, 16, 0.1, None, (0.6, 1.2), 1, 13, 1000.0, "c64"),
+    "precision-nx64-k4-nt16-d13-c128": (64, 2, 4, 16, 0.1, None, (0.6, 1.2), 1, 13, 1000.0, "c128"),
+    "plain-nx4-k2-nt2-c128": (4, 2, 2, 2, 0.1, 0.8, None, 0, 0, 0.0, "c128"),
+}
+DEFAULT = "precision-nx64-k4-nt16-d13-c64"
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one sweep_kernel launch,
+# keyed by the sha256 of kernels.cu at capture time (profiles/ has the summary).
+# A changed kernel source reports null traffic until it is captured again.
+NCU_TRAFFIC = {}
+
+
+def kernel_hash():
+    p = os.path.join(ROOT, "paper_2606_12770_gb300", "csrc", "kernels.cu")
+    with open(p, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def oracle_sample(seconds_target=15.0):
+    """Naive FP64 simulator on a bounded prefix of the plain (20-qubit) circuit."""
+    from oracle import circuit as OC
+    from oracle import statevec as S
+    from oracle.layout import Layout
+
+    cfg = (4, 0.8, 2, 2, 0.1, 2)
+    lay = Layout(4, 2, 2, 2)
+    f0, _ = I.lbm_instance(4, 0, tau=0.8)
+    gates = OC.build_qsvt(*cfg, list(I.random_phases(13, 0)))
+    psi = np.zeros(1 << lay.n, dtype=complex)
+    init, _ = OC.initial_state(lay, f0)
+    for k, v in init.items():
+        psi[k] = v
+    sim = S.DenseSim(lay.n)
+    upd = 0.0
+    count = 0
+    t0 = time.perf_counter()
+    for g in gates:
+        sim.apply(psi, g)
+        upd += 2.0 ** (lay.n - bin(g[2]).count("1"))
+        count += 1
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {count} gates of the 20-qubit plain circuit (Nx=4, N_C=2, K=2, Nt=2, "
+                      f"d=13) through the naive FP64 gate-by-gate simulator, {dt:.1f} s; the "
+                      f"32-qubit state does not fit the oracle"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    W, K = args.warmup, args.steps
+    times = []
+    vals = []
+    for i in range(W + K):
+        r = oracle_sample(seconds_target=args.ref_seconds)
+        if i >= W:
+            vals.append(r["value"])
+            times.append(args.ref_seconds)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": 1000.0 * args.ref_seconds,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "complex128 (fp64)", "data": "synthetic",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--exec", default="fused", choices=["fused", "gate"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2606_12770_gb300 as G
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    Nx, NC, K, Nt, dt, tau, tau_range, seed, d, kappa, prec = WORKLOADS[args.workload]
+    f0, tau = I.lbm_instance(Nx, seed + rank * 0, tau=tau, tau_range=tau_range)
+    circ = G.Circuit(Nx, tau, NC, K, dt, Nt, kappa_qsvt=kappa, d=d)
+    circ.set_exec(G.CSIM_EXEC_FUSED if args.exec == "fused" else G.CSIM_EXEC_GATE)
+    precision = G.CSIM_C64 if prec == "c64" else G.CSIM_C128
+    stream = torch.cuda.current_stream()
+    info = circ.info()
+    n = info["n_qubits"]
+    esz = 8 if prec == "c64" else 16
+
+    def step(want_amps=False, out=None):
+        circ.init(f0, precision, stream)
+        circ.run()
+        return circ.postselect(want_amplitudes=want_amps)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    info = circ.info()
+    passes = info["n_sweeps_run"]
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t_host0 = time.perf_counter()
+    for s in range(args.steps):
+        e = ev[s]
+        e[0].record(stream)
+        circ.init(f0, precision, stream)
+        e[1].record(stream)
+        circ.run()
+        e[2].record(stream)
+        circ.postselect(want_amplitudes=False)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    t_host = time.perf_counter() - t_host0
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [ev[s][0].elapsed_time(ev[s][3]) for s in range(args.steps)]
+    run_ms = [ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    updates = info["amp_updates_run"]
+    value = updates * world / (ms_per_step / 1000.0)
+
+    # end-to-end through the public API with host buffers: H2D of b, D2H of the
+    # postselected block into pinned memory, every step
+    e2e_ms = []
+    h2d = 0
+    d2h = 0
+    for s in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        circ.init(f0, precision, stream)
+        circ.run()
+        amps, p, tot = circ.postselect(want_amplitudes=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+        nnz = 3 * Nx + (9 * Nx * Nx if NC == 2 else 0)
+        h2d = nnz * 16 + 2 * 64 * 8
+        d2h = amps.nbytes + 16
+    e2e_val = updates * world / (statistics.median(e2e_ms) / 1000.0)
+
+    peaks, peak_kind = measured_peaks()
+    sweep_ms = statistics.mean(run_ms) / passes
+    alg_bytes = 2.0 * (1 << n) * esz
+    achieved = alg_bytes / (sweep_ms / 1000.0) / 1e9
+    khash = kernel_hash()
+    traffic = NCU_TRAFFIC.get((khash, args.workload))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "complex64 (fp32)" if prec == "c64" else "complex128 (fp64)",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "Nx": Nx, "N_C": NC, "K": K, "Nt": Nt, "dt": dt,
+                   "tau": tau, "d": info["d"], "qubits": n, "exec": args.exec,
+                   "state_bytes": (1 << n) * esz, "l2": "inputs larger than L2 (state >> 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                     "kernel": "sweep_kernel", "peak_kind": f"{peak_kind} (STREAM-style copy)",
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms,
+                     "launches_per_step": passes},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * (passes + 1 + 2),
+        "clocks": clk,
+        "host_wall_s": t_host,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(seconds_target=12.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * csim.h -- C ABI of the GB300 state-vector simulator for the Carleman-linearised
+ * D1Q3 lattice-Boltzmann QSVT circuit (Kanno et al., "Explicit Quantum Circuit
+ * Simulation of Nonlinear 1-Dimensional Fluid with Carleman-linearized Boltzmann
+ * Method").
+ *
+ * The calls follow the paper's statement of the problem:
+ *   csim_build      -- register layout, gate list and QSP phases (Sec. II.D; Fig. L;
+ *                      Fig. circuit-qsvt; Eq. d-star), host only, FP64.
+ *   csim_init       -- load f(0) as the right-hand side b (Sec. II.D.5).
+ *   csim_run        -- apply the QSVT circuit on the GPU.
+ *   csim_postselect -- final-time block (ancillas 0, signal 0, m >= Nt) and its
+ *                      success probability (Sec. II.D.4-5).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a csim_status; nothing throws across the ABI.
+ *     csim_last_error() returns a thread-local message for the last failure.
+ *   - The library owns the handle and all device memory it allocates.  The
+ *     caller owns every host buffer it passes and keeps it valid for the call.
+ *   - Device work is asynchronous on the CUDA stream given to csim_init
+ *     (NULL = the legacy default stream).  csim_sync waits for it.
+ *   - One handle must not be used by two threads at the same time.  Handles
+ *     may share a stream.
+ *   - Complex amplitudes cross the ABI as interleaved (re, im) doubles.
+ *   - Qubit indices are bit positions in the state index (bit 0 least
+ *     significant), in the register layout documented in oracle/LAYOUT.md.
+ */
+#ifndef CSIM_H
+#define CSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct csim_circuit csim_circuit; /* opaque, library-owned */
+typedef struct csim_sv csim_sv;           /* opaque raw state vector, library-owned */
+
+typedef enum {
+  CSIM_OK = 0,
+  CSIM_ERR_ARG = -1,       /* invalid argument or buffer too small */
+  CSIM_ERR_TOO_LARGE = -2, /* qubit count above the limit */
+  CSIM_ERR_OOM = -3,       /* device or host allocation failed; nothing kept */
+  CSIM_ERR_CUDA = -4,      /* a CUDA call failed (message in csim_last_error) */
+  CSIM_ERR_STATE = -5,     /* call out of order (e.g. run before init) */
+  CSIM_ERR_TIMEOUT = -6,   /* a bounded device wait expired */
+  CSIM_ERR_NUMERIC = -7    /* phase solver or norm check failed */
+} csim_status;
+
+typedef enum { CSIM_C64 = 0, CSIM_C128 = 1 } csim_precision;
+typedef enum { CSIM_BC_PERIODIC = 0, CSIM_BC_BOUNCEBACK = 1 } csim_bc;
+
+/* How csim_run applies the gate list.
+ *   CSIM_EXEC_FUSED: the fuser groups gates into sweeps (one HBM pass each).
+ *   CSIM_EXEC_GATE:  one kernel launch per elementary gate (the plain path). */
+typedef enum { CSIM_EXEC_FUSED = 0, CSIM_EXEC_GATE = 1 } csim_exec;
+
+/* Gate record: 32 bytes.  op 0 = X, 1 = H, 2 = RY(angle), 3 = ZPHASE(angle) =
+ * e^{i angle Z}.  The gate acts on `target` for every basis index with
+ * (index & cmask) == cval.  tag: 1/4 label H layers, 2 permutation, 3 value
+ * encoding, 5 target X, 6 projector phase, 7 signal H (0 for user gates). */
+typedef struct {
+  uint8_t op;
+  uint8_t target;
+  uint16_t tag;
+  uint32_t reserved; /* 0 */
+  uint64_t cmask;
+  uint64_t cval;
+  double angle;
+} csim_gate;
+
+/* Build options.  Zero or negative numeric fields select the defaults. */
+typedef struct {
+  int32_t Nx;          /* grid size, power of two >= 2 */
+  double tau;          /* BGK relaxation time > 0 */
+  int32_t N_C;         /* Carleman order, 1 or 2 */
+  int32_t K;           /* Taylor order >= 1 */
+  double dt;           /* time step > 0 */
+  int32_t Nt;          /* number of time steps >= 1 */
+  int32_t bc;          /* csim_bc; only CSIM_BC_PERIODIC is implemented */
+  double kappa_qsvt;   /* <= 0: kappa(L) = lambda_L / sigma_min(L), computed */
+  int32_t d;           /* <= 0: Eq. d-star, odd ceil(kappa ln(2 kappa/eps)/2) */
+  double eps;          /* <= 0: 1e-3 */
+  int32_t max_qubits;  /* <= 0: 34 */
+  const double* phases; /* NULL: computed; else n_phases = d+1 phases (copied) */
+  int32_t n_phases;
+} csim_build_opts;
+
+typedef struct {
+  int32_t n_qubits;
+  int32_t d;              /* QSVT degree (odd) = number of U_L / U_L^dag calls */
+  int32_t n_a, n_k, n_m, n_iL;
+  double lambda_L;        /* 2^{n_iL} L_max (Sec. II.D.4) */
+  double L_max;
+  double kappa_qsvt;      /* design parameter of the 1/x polynomial */
+  double poly_scale;      /* target polynomial = poly_scale * p(x), p ~ 1/x */
+  int64_t n_gates_UL;     /* gates of one U_L */
+  int64_t n_gates_total;  /* gates of the whole QSVT circuit */
+  int64_t n_sweeps_run;   /* fused sweeps (HBM passes) per csim_run */
+  double amp_updates_run; /* sum over gates of amplitudes the gate changes */
+  uint64_t state_bytes;   /* bytes of the current state (0 before csim_init) */
+} csim_info_t;
+
+/* --- building (host only; no GPU needed) -------------------------------- */
+
+/* Compile the circuit for the periodic D1Q3 Carleman system of order N_C with
+ * Taylor order K, step dt and Nt steps (Sec. II.B-D).  Defaults: periodic, eps
+ * 1e-3, kappa_qsvt = kappa(L), d from Eq. d-star, phases by Newton iteration.
+ * Errors: CSIM_ERR_ARG for invalid parameters (Nx not a power of two >= 2,
+ * tau/dt <= 0, N_C not 1/2, K < 1, Nt < 1), CSIM_ERR_TOO_LARGE above
+ * max_qubits, CSIM_ERR_NUMERIC if the phase solver does not converge.
+ * On success *out receives a new handle (free with csim_free). */
+csim_status csim_build(int32_t Nx, double tau, int32_t N_C, int32_t K, double dt,
+                       int32_t Nt, csim_circuit** out);
+csim_status csim_build_ex(const csim_build_opts* opts, csim_circuit** out);
+
+csim_status csim_info(const csim_circuit* c, csim_info_t* out);
+
+/* Canonical gate list.  which = 0: one U_L; which = 1: the whole QSVT circuit
+ * (H_s, PHI(phi_0), d alternating U_L / U_L^dag each followed by PHI, H_s).
+ * Writes min(cap, total) records to buf (may be NULL when cap = 0) and the
+ * total count to *len.  Returns CSIM_ERR_ARG if cap < total and buf != NULL. */
+csim_status csim_export_gates(const csim_circuit* c, int32_t which, csim_gate* buf,
+                              size_t cap, size_t* len);
+
+/* QSP phases phi_0..phi_d (reflection convention of Fig. circuit-qsvt). */
+csim_status csim_export_phases(const csim_circuit* c, double* buf, size_t cap, size_t* len);
+
+/* Postselection mask as a union of (mask, value) patterns over the state index:
+ * s = 0, t = 0, label = 0, m >= Nt. */
+csim_status csim_export_mask(const csim_circuit* c, uint64_t* masks, uint64_t* vals,
+                             size_t cap, size_t* len);
+
+/* --- device path ---------------------------------------------------------- */
+
+/* Allocate the 2^n-amplitude state (complex64 or complex128) on the current
+ * CUDA device and load b: f0 is [Nx][3] doubles in the paper's velocity order
+ * (e = +1, -1, 0); the Carleman vector (f0, f0 (x) f0) is normalised and
+ * placed in slot (m, k) = (0, 0) with all ancillas 0 (Sec. II.D.5).  A second
+ * call reuses the allocation when the precision is unchanged.  Errors:
+ * CSIM_ERR_OOM (nothing kept), CSIM_ERR_CUDA. */
+csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec,
+                      void* cuda_stream);
+
+csim_status csim_set_exec(csim_circuit* c, csim_exec mode);
+
+/* Enqueue the whole QSVT circuit on the stream.  CSIM_ERR_STATE unless a
+ * csim_init has loaded the state since the last run. */
+csim_status csim_run(csim_circuit* c);
+csim_status csim_sync(csim_circuit* c);
+
+/* Synchronises, then reduces in FP64 on the device: *norm_total = sum |a|^2
+ * over the whole state and *p_success = sum |a|^2 over the postselection mask.
+ * out_amps (caller-owned, may be NULL) receives the masked amplitudes with
+ * s = t = label = 0 and m >= Nt, ordered by state index, as interleaved
+ * doubles; cap counts complex amplitudes, *len receives the total. */
+csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_t* len,
+                            double* p_success, double* norm_total);
+
+/* Copy the whole state to the host as interleaved doubles (2 * 2^n values). */
+csim_status csim_read_state(csim_circuit* c, double* out, size_t cap_amps);
+
+csim_status csim_free(csim_circuit* c);
+
+/* --- raw state vectors (microbenchmark and parity tests) ---------------- */
+
+/* A 2^n-amplitude state on the current device (n <= 34), zero-initialised. */
+csim_status csim_sv_create(int32_t n, csim_precision prec, void* cuda_stream, csim_sv** out);
+/* Host -> device copy of 2^n interleaved complex values. */
+csim_status csim_sv_load(csim_sv* sv, const double* amps, size_t n_amps);
+/* Compile (fuse) a gate list for this state; the program is kept in the handle. */
+csim_status csim_sv_compile(csim_sv* sv, const csim_gate* gates, size_t n_gates, csim_exec mode);
+/* Enqueue the compiled program `reps` times. */
+csim_status csim_sv_run(csim_sv* sv, int32_t reps);
+csim_status csim_sv_read(csim_sv* sv, double* out, size_t n_amps);
+csim_status csim_sv_info(const csim_sv* sv, int64_t* n_sweeps, double* amp_updates,
+                         uint64_t* state_bytes);
+csim_status csim_sv_free(csim_sv* sv);
+
+const char* csim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSIM_H */

@@ -1,0 +1,13 @@
+"""GB300-native state-vector simulator for the Carleman-linearised D1Q3
+lattice-Boltzmann QSVT circuit (Kanno et al.).
+
+The compute path is the C-ABI library ``_lib/libcsim.so`` (C++ host compiler
+plus hand-written CUDA kernels for sm_103a); ``_native`` is its ctypes
+binding.  Importing this package does not load the library; the first call
+that needs it does, and raises if it cannot.
+"""
+from ._native import (CSIM_C64, CSIM_C128, CSIM_EXEC_FUSED, CSIM_EXEC_GATE, Circuit,  # noqa: F401
+                      CsimError, StateVector, gates_to_records, load)
+
+__all__ = ["Circuit", "StateVector", "CsimError", "load", "gates_to_records", "CSIM_C64",
+           "CSIM_C128", "CSIM_EXEC_FUSED", "CSIM_EXEC_GATE"]

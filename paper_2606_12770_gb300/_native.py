@@ -1,0 +1,278 @@
+"""ctypes binding of include/csim.h (argument marshalling only).
+
+Every function here forwards to the C ABI of ``_lib/libcsim.so``; all
+computation happens in the library (host compiler in C++, state-vector work
+in the CUDA kernels).  There is no Python fallback: if the library or a GPU
+is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcsim.so")
+
+CSIM_OK, CSIM_ERR_ARG, CSIM_ERR_TOO_LARGE, CSIM_ERR_OOM = 0, -1, -2, -3
+CSIM_ERR_CUDA, CSIM_ERR_STATE, CSIM_ERR_TIMEOUT, CSIM_ERR_NUMERIC = -4, -5, -6, -7
+CSIM_C64, CSIM_C128 = 0, 1
+CSIM_EXEC_FUSED, CSIM_EXEC_GATE = 0, 1
+_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_TOO_LARGE", -3: "ERR_OOM", -4: "ERR_CUDA",
+          -5: "ERR_STATE", -6: "ERR_TIMEOUT", -7: "ERR_NUMERIC"}
+
+# Every symbol declared in include/csim.h.
+EXPORTED = [
+    "csim_build", "csim_build_ex", "csim_info", "csim_export_gates", "csim_export_phases",
+    "csim_export_mask", "csim_init", "csim_set_exec", "csim_run", "csim_sync",
+    "csim_postselect", "csim_read_state", "csim_free", "csim_sv_create", "csim_sv_load",
+    "csim_sv_compile", "csim_sv_run", "csim_sv_read", "csim_sv_info", "csim_sv_free",
+    "csim_last_error",
+]
+
+
+class CsimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"csim {_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Gate(C.Structure):
+    _fields_ = [("op", C.c_uint8), ("target", C.c_uint8), ("tag", C.c_uint16),
+                ("reserved", C.c_uint32), ("cmask", C.c_uint64), ("cval", C.c_uint64),
+                ("angle", C.c_double)]
+
+
+GATE_DTYPE = np.dtype([("op", "u1"), ("target", "u1"), ("tag", "<u2"), ("reserved", "<u4"),
+                       ("cmask", "<u8"), ("cval", "<u8"), ("angle", "<f8")])
+assert GATE_DTYPE.itemsize == C.sizeof(Gate) == 32
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("Nx", C.c_int32), ("tau", C.c_double), ("N_C", C.c_int32), ("K", C.c_int32),
+                ("dt", C.c_double), ("Nt", C.c_int32), ("bc", C.c_int32),
+                ("kappa_qsvt", C.c_double), ("d", C.c_int32), ("eps", C.c_double),
+                ("max_qubits", C.c_int32), ("phases", C.POINTER(C.c_double)),
+                ("n_phases", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("d", C.c_int32), ("n_a", C.c_int32),
+                ("n_k", C.c_int32), ("n_m", C.c_int32), ("n_iL", C.c_int32),
+                ("lambda_L", C.c_double), ("L_max", C.c_double), ("kappa_qsvt", C.c_double),
+                ("poly_scale", C.c_double), ("n_gates_UL", C.c_int64),
+                ("n_gates_total", C.c_int64), ("n_sweeps_run", C.c_int64),
+                ("amp_updates_run", C.c_double), ("state_bytes", C.c_uint64)]
+
+
+_lib = None
+
+
+def load():
+    """Load the library (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    _build.build()
+    lib = C.CDLL(LIB_PATH)
+    P, VP, SZ, SZP = C.POINTER, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)
+    D, DP = C.c_double, C.POINTER(C.c_double)
+    sig = {
+        "csim_build": ([C.c_int32, D, C.c_int32, C.c_int32, D, C.c_int32, P(VP)], C.c_int),
+        "csim_build_ex": ([P(BuildOpts), P(VP)], C.c_int),
+        "csim_info": ([VP, P(Info)], C.c_int),
+        "csim_export_gates": ([VP, C.c_int32, VP, SZ, SZP], C.c_int),
+        "csim_export_phases": ([VP, DP, SZ, SZP], C.c_int),
+        "csim_export_mask": ([VP, P(C.c_uint64), P(C.c_uint64), SZ, SZP], C.c_int),
+        "csim_init": ([VP, DP, C.c_int, VP], C.c_int),
+        "csim_set_exec": ([VP, C.c_int], C.c_int),
+        "csim_run": ([VP], C.c_int),
+        "csim_sync": ([VP], C.c_int),
+        "csim_postselect": ([VP, DP, SZ, SZP, DP, DP], C.c_int),
+        "csim_read_state": ([VP, DP, SZ], C.c_int),
+        "csim_free": ([VP], C.c_int),
+        "csim_sv_create": ([C.c_int32, C.c_int, VP, P(VP)], C.c_int),
+        "csim_sv_load": ([VP, DP, SZ], C.c_int),
+        "csim_sv_compile": ([VP, VP, SZ, C.c_int], C.c_int),
+        "csim_sv_run": ([VP, C.c_int32], C.c_int),
+        "csim_sv_read": ([VP, DP, SZ], C.c_int),
+        "csim_sv_info": ([VP, P(C.c_int64), DP, P(C.c_uint64)], C.c_int),
+        "csim_sv_free": ([VP], C.c_int),
+        "csim_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != CSIM_OK:
+        raise CsimError(status, _lib.csim_last_error().decode(errors="replace"))
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_handle(stream):
+    """Accept None, an int handle, or a torch.cuda.Stream-like object."""
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+class Circuit:
+    """Handle of ``csim_circuit`` (csim_build / csim_init / csim_run / csim_postselect)."""
+
+    def __init__(self, Nx, tau, N_C, K, dt, Nt, kappa_qsvt=0.0, d=0, eps=0.0,
+                 max_qubits=0, phases=None):
+        lib = load()
+        o = BuildOpts()
+        o.Nx, o.tau, o.N_C, o.K, o.dt, o.Nt = int(Nx), float(tau), int(N_C), int(K), float(dt), int(Nt)
+        o.bc = 0
+        o.kappa_qsvt, o.d, o.eps, o.max_qubits = float(kappa_qsvt), int(d), float(eps), int(max_qubits)
+        self._phases_keep = None
+        if phases is not None:
+            ph = np.ascontiguousarray(phases, dtype=np.float64)
+            self._phases_keep = ph
+            o.phases = _dp(ph)
+            o.n_phases = int(ph.shape[0])
+        h = C.c_void_p()
+        _check(lib.csim_build_ex(C.byref(o), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.csim_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(_lib.csim_info(self._h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def export_gates(self, which: int = 0) -> np.ndarray:
+        n = C.c_size_t()
+        _check(_lib.csim_export_gates(self._h, which, None, 0, C.byref(n)))
+        out = np.zeros(n.value, dtype=GATE_DTYPE)
+        _check(_lib.csim_export_gates(self._h, which, out.ctypes.data_as(C.c_void_p), n.value,
+                                      C.byref(n)))
+        return out
+
+    def export_phases(self) -> np.ndarray:
+        n = C.c_size_t()
+        _check(_lib.csim_export_phases(self._h, None, 0, C.byref(n)))
+        out = np.zeros(n.value)
+        _check(_lib.csim_export_phases(self._h, _dp(out), n.value, C.byref(n)))
+        return out
+
+    def export_mask(self):
+        n = C.c_size_t()
+        _check(_lib.csim_export_mask(self._h, None, None, 0, C.byref(n)))
+        m = np.zeros(n.value, dtype=np.uint64)
+        v = np.zeros(n.value, dtype=np.uint64)
+        P = C.POINTER(C.c_uint64)
+        _check(_lib.csim_export_mask(self._h, m.ctypes.data_as(P), v.ctypes.data_as(P), n.value,
+                                     C.byref(n)))
+        return m, v
+
+    def init(self, f0, precision=CSIM_C128, stream=None):
+        f = np.ascontiguousarray(f0, dtype=np.float64)
+        _check(_lib.csim_init(self._h, _dp(f), int(precision), _stream_handle(stream)))
+
+    def set_exec(self, mode):
+        _check(_lib.csim_set_exec(self._h, int(mode)))
+
+    def run(self):
+        _check(_lib.csim_run(self._h))
+
+    def sync(self):
+        _check(_lib.csim_sync(self._h))
+
+    def postselect(self, want_amplitudes=True):
+        """Return (amplitudes or None, p_success, norm_total)."""
+        n = C.c_size_t()
+        p = C.c_double()
+        t = C.c_double()
+        if not want_amplitudes:
+            _check(_lib.csim_postselect(self._h, None, 0, C.byref(n), C.byref(p), C.byref(t)))
+            return None, p.value, t.value
+        _check(_lib.csim_postselect(self._h, None, 0, C.byref(n), C.byref(p), C.byref(t)))
+        out = np.zeros(2 * n.value)
+        _check(_lib.csim_postselect(self._h, _dp(out), n.value, C.byref(n), C.byref(p), C.byref(t)))
+        return out.view(np.complex128), p.value, t.value
+
+    def read_state(self) -> np.ndarray:
+        N = 1 << self.info()["n_qubits"]
+        out = np.zeros(2 * N)
+        _check(_lib.csim_read_state(self._h, _dp(out), N))
+        return out.view(np.complex128)
+
+
+class StateVector:
+    """Handle of ``csim_sv``: a raw 2^n state plus a compiled gate program."""
+
+    def __init__(self, n, precision=CSIM_C64, stream=None):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.csim_sv_create(int(n), int(precision), _stream_handle(stream), C.byref(h)))
+        self._h = h
+        self.n = int(n)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.csim_sv_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, amps):
+        a = np.ascontiguousarray(amps, dtype=np.complex128)
+        _check(_lib.csim_sv_load(self._h, _dp(a.view(np.float64)), a.shape[0]))
+
+    def compile(self, gates, mode=CSIM_EXEC_FUSED):
+        g = gates_to_records(gates)
+        _check(_lib.csim_sv_compile(self._h, g.ctypes.data_as(C.c_void_p), g.shape[0], int(mode)))
+
+    def run(self, reps=1):
+        _check(_lib.csim_sv_run(self._h, int(reps)))
+
+    def read(self) -> np.ndarray:
+        N = 1 << self.n
+        out = np.zeros(2 * N)
+        _check(_lib.csim_sv_read(self._h, _dp(out), N))
+        return out.view(np.complex128)
+
+    def info(self):
+        ns = C.c_int64()
+        au = C.c_double()
+        sb = C.c_uint64()
+        _check(_lib.csim_sv_info(self._h, C.byref(ns), C.byref(au), C.byref(sb)))
+        return {"n_sweeps": ns.value, "amp_updates": au.value, "state_bytes": sb.value}
+
+
+def gates_to_records(gates) -> np.ndarray:
+    """Gate tuples (op, target, cmask, cval, angle, tag) or a record array -> records."""
+    if isinstance(gates, np.ndarray) and gates.dtype == GATE_DTYPE:
+        return np.ascontiguousarray(gates)
+    out = np.zeros(len(gates), dtype=GATE_DTYPE)
+    for i, g in enumerate(gates):
+        out[i] = (g[0], g[1], g[5] if len(g) > 5 else 0, 0, g[2], g[3], g[4])
+    return out

@@ -1,0 +1,583 @@
+// C ABI of include/csim.h: handle management, argument checking, device
+// allocation and the run/postselect sequence.  No exception crosses the ABI.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fuse.h"
+#include "internal.h"
+#include "kernels.h"
+
+using csim::Gate;
+using csim::Layout;
+using csim::Program;
+
+namespace {
+thread_local std::string g_err;
+
+csim_status fail(csim_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+csim_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(CSIM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+}  // namespace
+
+struct csim_circuit {
+  Layout L;
+  double tau = 0, dt = 0, eps = 1e-3, kappa = 0, scale = 0, Lmax = 0, lambda = 0;
+  int d = 0, max_qubits = 34;
+  std::vector<Gate> UL;
+  std::vector<double> phases;
+  std::vector<uint64_t> pm, pv;
+  // device side
+  int prec = -1;
+  cudaStream_t stream = nullptr;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  size_t bytes = 0;
+  csim_exec exec = CSIM_EXEC_FUSED;
+  bool loaded = false, ran = false;
+  Program prog;
+  bool prog_built = false;
+  uint64_t* d_pat = nullptr;  // masks then values
+  double* d_partial = nullptr;
+  double* d_out = nullptr;
+  double* d_compact = nullptr;
+  size_t compact_cap = 0;
+};
+
+struct csim_sv {
+  int n = 0, prec = 0;
+  cudaStream_t stream = nullptr;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  size_t bytes = 0;
+  Program prog;
+  bool compiled = false;
+};
+
+namespace {
+
+void free_device(csim_circuit* c) {
+  for (void*& b : c->buf) {
+    if (b) cudaFree(b);
+    b = nullptr;
+  }
+  if (c->d_pat) cudaFree(c->d_pat);
+  if (c->d_partial) cudaFree(c->d_partial);
+  if (c->d_out) cudaFree(c->d_out);
+  if (c->d_compact) cudaFree(c->d_compact);
+  c->d_pat = nullptr;
+  c->d_partial = nullptr;
+  c->d_out = nullptr;
+  c->d_compact = nullptr;
+  c->compact_cap = 0;
+  c->bytes = 0;
+  c->prec = -1;
+  csim::free_program(&c->prog);
+  c->prog_built = false;
+}
+
+uint64_t place_bits(const std::vector<int>& bits, uint64_t v) {
+  uint64_t idx = 0;
+  for (size_t j = 0; j < bits.size(); ++j) idx |= ((v >> j) & 1ull) << bits[j];
+  return idx;
+}
+
+bool ensure_program(csim_circuit* c, std::string* err) {
+  if (c->prog_built && c->prog.mode == c->exec) return true;
+  csim::free_program(&c->prog);
+  std::vector<Gate> all = csim::build_qsvt(c->L, c->UL, c->phases);
+  csim::build_program(all, c->L.n, c->exec, &c->prog);
+  cudaError_t e = csim::upload_program(&c->prog, c->stream);
+  if (e != cudaSuccess) {
+    *err = std::string("program upload: ") + cudaGetErrorString(e);
+    csim::free_program(&c->prog);
+    return false;
+  }
+  c->prog_built = true;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* csim_last_error(void) { return g_err.c_str(); }
+
+csim_status csim_build_ex(const csim_build_opts* o, csim_circuit** out) {
+  if (!o || !out) return fail(CSIM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (!(o->tau > 0) || !(o->dt > 0) || !std::isfinite(o->tau) || !std::isfinite(o->dt))
+    return fail(CSIM_ERR_ARG, "tau and dt must be positive and finite");
+  if (o->bc != CSIM_BC_PERIODIC)
+    return fail(CSIM_ERR_ARG, "only periodic boundaries are implemented in the circuit");
+  Layout L;
+  std::string err;
+  if (!csim::make_layout(o->Nx, o->N_C, o->K, o->Nt, &L, &err)) return fail(CSIM_ERR_ARG, err);
+  const int maxq = o->max_qubits > 0 ? o->max_qubits : 34;
+  if (L.n > maxq || L.n > 62)
+    return fail(CSIM_ERR_TOO_LARGE, "circuit needs " + std::to_string(L.n) + " qubits > limit " +
+                                        std::to_string(maxq));
+  csim_circuit* c = new (std::nothrow) csim_circuit();
+  if (!c) return fail(CSIM_ERR_OOM, "host allocation");
+  c->L = L;
+  c->tau = o->tau;
+  c->dt = o->dt;
+  c->max_qubits = maxq;
+  c->eps = o->eps > 0 ? o->eps : 1e-3;
+  c->Lmax = csim::lmax_value(o->tau, o->N_C, o->dt);
+  c->lambda = std::ldexp(1.0, L.niL) * c->Lmax;
+  try {
+    c->UL = csim::build_UL(L, o->tau, o->dt);
+  } catch (const std::exception& ex) {
+    delete c;
+    return fail(CSIM_ERR_ARG, ex.what());
+  }
+  csim::postselect_patterns(L, &c->pm, &c->pv);
+  if (o->phases) {
+    if (o->n_phases < 2 || o->n_phases % 2 != 0) {
+      delete c;
+      return fail(CSIM_ERR_ARG, "n_phases must be d+1 with d odd");
+    }
+    c->phases.assign(o->phases, o->phases + o->n_phases);
+    c->d = o->n_phases - 1;
+    c->kappa = o->kappa_qsvt;
+    c->scale = 0.0;
+  } else {
+    c->kappa = o->kappa_qsvt;
+    if (!(c->kappa > 0)) {
+      c->kappa = csim::kappa_of_L(L, o->tau, o->dt, &err);
+      if (!(c->kappa > 0)) {
+        delete c;
+        return fail(CSIM_ERR_NUMERIC, err);
+      }
+    }
+    if (!(c->kappa > 1.0)) {
+      delete c;
+      return fail(CSIM_ERR_ARG, "kappa_qsvt must exceed 1");
+    }
+    c->d = o->d > 0 ? o->d : csim::degree_from_kappa(c->kappa, c->eps);
+    if (c->d % 2 == 0) {
+      delete c;
+      return fail(CSIM_ERR_ARG, "d must be odd");
+    }
+    if (!csim::solve_phases(c->kappa, c->d, &c->phases, &c->scale, &err)) {
+      delete c;
+      return fail(CSIM_ERR_NUMERIC, err);
+    }
+  }
+  *out = c;
+  return CSIM_OK;
+}
+
+csim_status csim_build(int32_t Nx, double tau, int32_t N_C, int32_t K, double dt, int32_t Nt,
+                       csim_circuit** out) {
+  csim_build_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.Nx = Nx;
+  o.tau = tau;
+  o.N_C = N_C;
+  o.K = K;
+  o.dt = dt;
+  o.Nt = Nt;
+  o.bc = CSIM_BC_PERIODIC;
+  return csim_build_ex(&o, out);
+}
+
+csim_status csim_info(const csim_circuit* c, csim_info_t* out) {
+  if (!c || !out) return fail(CSIM_ERR_ARG, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  out->n_qubits = c->L.n;
+  out->d = c->d;
+  out->n_a = c->L.na;
+  out->n_k = c->L.nk;
+  out->n_m = c->L.nm;
+  out->n_iL = c->L.niL;
+  out->lambda_L = c->lambda;
+  out->L_max = c->Lmax;
+  out->kappa_qsvt = c->kappa;
+  out->poly_scale = c->scale;
+  out->n_gates_UL = (int64_t)c->UL.size();
+  out->n_gates_total = (int64_t)c->d * ((int64_t)c->UL.size() + 3) + 5;
+  out->amp_updates_run = 0.0;
+  for (const Gate& g : c->UL) out->amp_updates_run += c->d * csim::gate_amp_updates(g, c->L.n);
+  for (const Gate& g : csim::phase_gates(c->L, 0.0))
+    out->amp_updates_run += (c->d + 1) * csim::gate_amp_updates(g, c->L.n);
+  out->amp_updates_run += 2.0 * std::ldexp(1.0, c->L.n);
+  out->n_sweeps_run = c->prog_built ? c->prog.passes : 0;
+  out->state_bytes = c->bytes;
+  return CSIM_OK;
+}
+
+csim_status csim_export_gates(const csim_circuit* c, int32_t which, csim_gate* buf, size_t cap,
+                              size_t* len) {
+  if (!c || !len) return fail(CSIM_ERR_ARG, "null argument");
+  std::vector<Gate> all;
+  const std::vector<Gate>* src = &c->UL;
+  if (which == 1) {
+    all = csim::build_qsvt(c->L, c->UL, c->phases);
+    src = &all;
+  } else if (which != 0) {
+    return fail(CSIM_ERR_ARG, "which must be 0 (U_L) or 1 (QSVT)");
+  }
+  *len = src->size();
+  if (buf) {
+    if (cap < src->size()) return fail(CSIM_ERR_ARG, "buffer too small");
+    std::memcpy(buf, src->data(), src->size() * sizeof(Gate));
+  }
+  return CSIM_OK;
+}
+
+csim_status csim_export_phases(const csim_circuit* c, double* buf, size_t cap, size_t* len) {
+  if (!c || !len) return fail(CSIM_ERR_ARG, "null argument");
+  *len = c->phases.size();
+  if (buf) {
+    if (cap < c->phases.size()) return fail(CSIM_ERR_ARG, "buffer too small");
+    std::memcpy(buf, c->phases.data(), c->phases.size() * sizeof(double));
+  }
+  return CSIM_OK;
+}
+
+csim_status csim_export_mask(const csim_circuit* c, uint64_t* masks, uint64_t* vals, size_t cap,
+                             size_t* len) {
+  if (!c || !len) return fail(CSIM_ERR_ARG, "null argument");
+  *len = c->pm.size();
+  if (masks || vals) {
+    if (!masks || !vals || cap < c->pm.size()) return fail(CSIM_ERR_ARG, "buffer too small");
+    std::memcpy(masks, c->pm.data(), c->pm.size() * sizeof(uint64_t));
+    std::memcpy(vals, c->pv.data(), c->pv.size() * sizeof(uint64_t));
+  }
+  return CSIM_OK;
+}
+
+csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec, void* stream) {
+  if (!c || !f0) return fail(CSIM_ERR_ARG, "null argument");
+  if (prec != CSIM_C64 && prec != CSIM_C128) return fail(CSIM_ERR_ARG, "bad precision");
+  const Layout& L = c->L;
+  const size_t nf = (size_t)L.Nx * 3;
+  for (size_t i = 0; i < nf; ++i)
+    if (!std::isfinite(f0[i])) return fail(CSIM_ERR_ARG, "f0 has a non-finite entry");
+  // host: b = (f, f (x) f) normalised, in register coordinates
+  std::vector<uint64_t> idx;
+  std::vector<double> val;
+  double nrm2 = 0.0;
+  for (int a = 0; a < L.Nx; ++a)
+    for (int q = 0; q < 3; ++q) {
+      const double v = f0[a * 3 + q];
+      nrm2 += v * v;
+      if (v != 0.0) {
+        idx.push_back(place_bits(L.a1, a) | place_bits(L.q1, q));
+        val.push_back(v);
+      }
+    }
+  if (L.NC == 2) {
+    for (int a1 = 0; a1 < L.Nx; ++a1)
+      for (int q1 = 0; q1 < 3; ++q1)
+        for (int a2 = 0; a2 < L.Nx; ++a2)
+          for (int q2 = 0; q2 < 3; ++q2) {
+            const double v = f0[a1 * 3 + q1] * f0[a2 * 3 + q2];
+            nrm2 += v * v;
+            if (v != 0.0) {
+              idx.push_back(place_bits(L.a1, a1) | place_bits(L.q1, q1) | place_bits(L.a2, a2) |
+                            place_bits(L.q2, q2) | place_bits(L.ord, 1));
+              val.push_back(v);
+            }
+          }
+  }
+  if (!(nrm2 > 0)) return fail(CSIM_ERR_ARG, "f0 is zero");
+  const double inv = 1.0 / std::sqrt(nrm2);
+  for (double& v : val) v *= inv;
+
+  c->stream = (cudaStream_t)stream;
+  const size_t esz = prec == CSIM_C64 ? 8 : 16;
+  const size_t bytes = ((size_t)1 << L.n) * esz;
+  const int nbuf = c->exec == CSIM_EXEC_FUSED ? 2 : 1;
+  if (c->prec != (int)prec || c->bytes != bytes || (nbuf == 2 && !c->buf[1])) {
+    for (void*& b : c->buf) {
+      if (b) cudaFree(b);
+      b = nullptr;
+    }
+    c->bytes = 0;
+    c->prec = -1;
+    for (int k = 0; k < nbuf; ++k) {
+      cudaError_t e = cudaMalloc(&c->buf[k], bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (void*& b : c->buf) {
+          if (b) cudaFree(b);
+          b = nullptr;
+        }
+        return fail(CSIM_ERR_OOM, "state allocation of " + std::to_string(bytes) + " bytes: " +
+                                      cudaGetErrorString(e));
+      }
+    }
+    c->bytes = bytes;
+    c->prec = prec;
+  }
+  if (!c->d_pat) {
+    cudaError_t e = cudaMalloc(&c->d_pat, 2 * 64 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_partial, 2 * csim::norm_partials_needed() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_out, 2 * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_device(c);
+      return fail(CSIM_ERR_OOM, "work buffers");
+    }
+  }
+  uint64_t* d_idx = nullptr;
+  double* d_val = nullptr;
+  cudaError_t e = cudaMallocAsync(&d_idx, idx.size() * sizeof(uint64_t), c->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_val, val.size() * sizeof(double), c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_idx, idx.data(), idx.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_val, val.data(), val.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream);
+  c->cur = 0;
+  if (e == cudaSuccess)
+    e = csim::launch_init(c->buf[0], prec, (uint64_t)1 << L.n, d_idx, d_val, (int64_t)idx.size(),
+                          c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (d_idx) cudaFreeAsync(d_idx, c->stream);
+  if (d_val) cudaFreeAsync(d_val, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_init");
+  c->loaded = true;
+  c->ran = false;
+  return CSIM_OK;
+}
+
+csim_status csim_set_exec(csim_circuit* c, csim_exec mode) {
+  if (!c) return fail(CSIM_ERR_ARG, "null argument");
+  if (mode != CSIM_EXEC_FUSED && mode != CSIM_EXEC_GATE) return fail(CSIM_ERR_ARG, "bad mode");
+  c->exec = mode;
+  return CSIM_OK;
+}
+
+csim_status csim_run(csim_circuit* c) {
+  if (!c) return fail(CSIM_ERR_ARG, "null argument");
+  if (!c->loaded) return fail(CSIM_ERR_STATE, "csim_run needs a fresh csim_init");
+  std::string err;
+  if (!ensure_program(c, &err)) return fail(CSIM_ERR_CUDA, err);
+  if (c->prog.pingpong && !c->buf[1]) {
+    cudaError_t e = cudaMalloc(&c->buf[1], c->bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->buf[1] = nullptr;
+      return fail(CSIM_ERR_OOM, "second state buffer");
+    }
+  }
+  cudaError_t e = csim::run_program(c->prog, c->buf, &c->cur, c->prec, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_run");
+  c->loaded = false;
+  c->ran = true;
+  return CSIM_OK;
+}
+
+csim_status csim_sync(csim_circuit* c) {
+  if (!c) return fail(CSIM_ERR_ARG, "null argument");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_sync");
+  return CSIM_OK;
+}
+
+csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_t* len,
+                            double* p_success, double* norm_total) {
+  if (!c) return fail(CSIM_ERR_ARG, "null argument");
+  if (!c->buf[c->cur] || c->prec < 0) return fail(CSIM_ERR_STATE, "no state");
+  const Layout& L = c->L;
+  const int npat = (int)c->pm.size();
+  std::vector<uint64_t> pat(c->pm);
+  pat.insert(pat.end(), c->pv.begin(), c->pv.end());
+  cudaError_t e = cudaMemcpyAsync(c->d_pat, pat.data(), pat.size() * sizeof(uint64_t),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = csim::launch_norms(c->buf[c->cur], c->prec, L.n, c->d_pat, c->d_pat + npat, npat,
+                           c->d_partial, c->d_out, c->stream);
+  double h[2] = {0, 0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h, c->d_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  const int free_shift = 2 + L.niL;
+  const int m_shift = L.m[0];
+  const int free_bits = m_shift - free_shift;
+  const uint64_t count = (((uint64_t)1 << L.nm) - (uint64_t)L.Nt) << free_bits;
+  if (len) *len = count;
+  if (e == cudaSuccess && out_amps) {
+    if (cap < count) return fail(CSIM_ERR_ARG, "out_amps too small");
+    if (c->compact_cap < count) {
+      if (c->d_compact) cudaFree(c->d_compact);
+      c->d_compact = nullptr;
+      c->compact_cap = 0;
+      e = cudaMalloc(&c->d_compact, count * 2 * sizeof(double));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CSIM_ERR_OOM, "postselect buffer");
+      }
+      c->compact_cap = count;
+    }
+    e = csim::launch_compact(c->buf[c->cur], c->prec, c->d_compact, count, free_shift, free_bits,
+                             (uint64_t)L.Nt, m_shift, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out_amps, c->d_compact, count * 2 * sizeof(double),
+                          cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_postselect");
+  if (norm_total) *norm_total = h[0];
+  if (p_success) *p_success = h[1];
+  return CSIM_OK;
+}
+
+csim_status csim_read_state(csim_circuit* c, double* out, size_t cap_amps) {
+  if (!c || !out) return fail(CSIM_ERR_ARG, "null argument");
+  if (!c->buf[c->cur] || c->prec < 0) return fail(CSIM_ERR_STATE, "no state");
+  const size_t N = (size_t)1 << c->L.n;
+  if (cap_amps < N) return fail(CSIM_ERR_ARG, "buffer too small");
+  cudaError_t e;
+  if (c->prec == CSIM_C128) {
+    e = cudaMemcpyAsync(out, c->buf[c->cur], N * 16, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  } else {
+    std::vector<float> tmp(2 * N);
+    e = cudaMemcpyAsync(tmp.data(), c->buf[c->cur], N * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    for (size_t i = 0; i < 2 * N; ++i) out[i] = tmp[i];
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "csim_read_state");
+  return CSIM_OK;
+}
+
+csim_status csim_free(csim_circuit* c) {
+  if (!c) return CSIM_OK;
+  if (c->stream || c->buf[0]) cudaStreamSynchronize(c->stream);
+  free_device(c);
+  delete c;
+  return CSIM_OK;
+}
+
+// ------------------------------------------------------------ raw states
+csim_status csim_sv_create(int32_t n, csim_precision prec, void* stream, csim_sv** out) {
+  if (!out) return fail(CSIM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (n < 1 || n > 34) return fail(CSIM_ERR_TOO_LARGE, "n must be in [1, 34]");
+  if (prec != CSIM_C64 && prec != CSIM_C128) return fail(CSIM_ERR_ARG, "bad precision");
+  csim_sv* s = new (std::nothrow) csim_sv();
+  if (!s) return fail(CSIM_ERR_OOM, "host allocation");
+  s->n = n;
+  s->prec = prec;
+  s->stream = (cudaStream_t)stream;
+  s->bytes = ((size_t)1 << n) * (prec == CSIM_C64 ? 8 : 16);
+  cudaError_t e = cudaMalloc(&s->buf[0], s->bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->buf[0], 0, s->bytes, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (s->buf[0]) cudaFree(s->buf[0]);
+    delete s;
+    return fail(CSIM_ERR_OOM, std::string("state allocation: ") + cudaGetErrorString(e));
+  }
+  *out = s;
+  return CSIM_OK;
+}
+
+csim_status csim_sv_load(csim_sv* s, const double* amps, size_t n_amps) {
+  if (!s || !amps) return fail(CSIM_ERR_ARG, "null argument");
+  const size_t N = (size_t)1 << s->n;
+  if (n_amps != N) return fail(CSIM_ERR_ARG, "n_amps must be 2^n");
+  cudaError_t e;
+  s->cur = 0;
+  if (s->prec == CSIM_C128) {
+    e = cudaMemcpyAsync(s->buf[0], amps, N * 16, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  } else {
+    std::vector<float> tmp(2 * N);
+    for (size_t i = 0; i < 2 * N; ++i) tmp[i] = (float)amps[i];
+    e = cudaMemcpyAsync(s->buf[0], tmp.data(), N * 8, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "csim_sv_load");
+  return CSIM_OK;
+}
+
+csim_status csim_sv_compile(csim_sv* s, const csim_gate* gates, size_t n_gates, csim_exec mode) {
+  if (!s || (!gates && n_gates)) return fail(CSIM_ERR_ARG, "null argument");
+  for (size_t i = 0; i < n_gates; ++i) {
+    const csim_gate& g = gates[i];
+    if (g.op > 3 || g.target >= s->n || ((g.cmask >> g.target) & 1ull) || (g.cval & ~g.cmask) ||
+        (s->n < 64 && (g.cmask >> s->n)))
+      return fail(CSIM_ERR_ARG, "invalid gate record " + std::to_string(i));
+  }
+  csim::free_program(&s->prog);
+  std::vector<Gate> gl(gates, gates + n_gates);
+  csim::build_program(gl, s->n, mode, &s->prog);
+  cudaError_t e = csim::upload_program(&s->prog, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_sv_compile");
+  if (s->prog.pingpong && !s->buf[1]) {
+    e = cudaMalloc(&s->buf[1], s->bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      s->buf[1] = nullptr;
+      return fail(CSIM_ERR_OOM, "second state buffer");
+    }
+  }
+  s->compiled = true;
+  return CSIM_OK;
+}
+
+csim_status csim_sv_run(csim_sv* s, int32_t reps) {
+  if (!s) return fail(CSIM_ERR_ARG, "null argument");
+  if (!s->compiled) return fail(CSIM_ERR_STATE, "compile a gate list first");
+  for (int r = 0; r < reps; ++r) {
+    cudaError_t e = csim::run_program(s->prog, s->buf, &s->cur, s->prec, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "csim_sv_run");
+  }
+  return CSIM_OK;
+}
+
+csim_status csim_sv_read(csim_sv* s, double* out, size_t n_amps) {
+  if (!s || !out) return fail(CSIM_ERR_ARG, "null argument");
+  const size_t N = (size_t)1 << s->n;
+  if (n_amps < N) return fail(CSIM_ERR_ARG, "buffer too small");
+  cudaError_t e;
+  if (s->prec == CSIM_C128) {
+    e = cudaMemcpyAsync(out, s->buf[s->cur], N * 16, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  } else {
+    std::vector<float> tmp(2 * N);
+    e = cudaMemcpyAsync(tmp.data(), s->buf[s->cur], N * 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    for (size_t i = 0; i < 2 * N; ++i) out[i] = tmp[i];
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "csim_sv_read");
+  return CSIM_OK;
+}
+
+csim_status csim_sv_info(const csim_sv* s, int64_t* n_sweeps, double* amp_updates,
+                         uint64_t* state_bytes) {
+  if (!s) return fail(CSIM_ERR_ARG, "null argument");
+  if (n_sweeps) *n_sweeps = s->compiled ? s->prog.passes : 0;
+  if (amp_updates) *amp_updates = s->compiled ? s->prog.amp_updates : 0.0;
+  if (state_bytes) *state_bytes = s->bytes;
+  return CSIM_OK;
+}
+
+csim_status csim_sv_free(csim_sv* s) {
+  if (!s) return CSIM_OK;
+  cudaStreamSynchronize(s->stream);
+  for (void*& b : s->buf) {
+    if (b) cudaFree(b);
+    b = nullptr;
+  }
+  csim::free_program(&s->prog);
+  delete s;
+  return CSIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,382 @@
+// CUDA kernels (sm_103a) of the state-vector path.
+//
+// State layout: 2^n complex amplitudes (float2 for complex64, double2 for
+// complex128), index bit b = qubit b.  A "warp tile" is 128 consecutive
+// amplitudes: bits 0-1 live in one thread (4 amplitudes, 32 B or 64 B),
+// bits 2-6 select the lane.  In the register layout of the circuit these
+// seven bits are the value-encoding target t, the QSVT signal s and the five
+// U_L label qubits, i.e. every qubit that is touched by a non-permutation gate.
+//
+//   init_scatter_kernel  -- zero state + scatter the normalised right-hand side b
+//   gate_kernel          -- one elementary gate over the 2^{n-1-c} matching pairs
+//   sweep_kernel         -- one fused HBM pass: gather through an index
+//                           permutation (a run of multi-controlled X gates),
+//                           then a list of gates acting inside the warp tile
+//                           (in-register for bits 0-1, warp shuffles for 2-6)
+//   norm_kernel          -- FP64 sum |a|^2 (total and under a pattern mask)
+//   compact_kernel       -- gather the postselected block
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace csim {
+namespace {
+
+template <typename R>
+struct V2;
+template <>
+struct V2<float> {
+  using T = float2;
+};
+template <>
+struct V2<double> {
+  using T = double2;
+};
+
+template <typename T>
+__device__ __forceinline__ T mk(decltype(T::x) a, decltype(T::x) b) {
+  T r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+
+// ------------------------------------------------------------------ init
+template <typename R>
+__global__ void init_scatter_kernel(typename V2<R>::T* state, const uint64_t* idx,
+                                    const double* val, int64_t count) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) state[idx[i]] = mk<typename V2<R>::T>((R)val[i], (R)0);
+}
+
+// ------------------------------------------------------- gate-by-gate path
+struct GateParams {
+  uint64_t cmask, cval, tbit;
+  uint64_t npairs;
+  int nfixed;
+  uint8_t fixed[64];  // sorted bit positions of controls + target
+  int op;
+  double c, s;        // RY: cos(th/2), sin(th/2); ZPHASE: cos(phi), sin(phi)
+};
+
+template <typename R>
+__global__ void gate_kernel(typename V2<R>::T* __restrict__ st, GateParams p) {
+  using T = typename V2<R>::T;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const R c = (R)p.c, s = (R)p.s;
+  const R h = (R)0.70710678118654752440;
+  for (uint64_t f = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; f < p.npairs; f += stride) {
+    uint64_t idx = f;
+    for (int k = 0; k < p.nfixed; ++k) {
+      const int b = p.fixed[k];
+      idx = ((idx >> b) << (b + 1)) | (idx & ((1ull << b) - 1));
+    }
+    const uint64_t i0 = idx | p.cval, i1 = i0 | p.tbit;
+    const T a = st[i0], bb = st[i1];
+    T na, nb;
+    switch (p.op) {
+      case 0:  // X
+        na = bb;
+        nb = a;
+        break;
+      case 1:  // H
+        na = mk<T>((a.x + bb.x) * h, (a.y + bb.y) * h);
+        nb = mk<T>((a.x - bb.x) * h, (a.y - bb.y) * h);
+        break;
+      case 2:  // RY
+        na = mk<T>(c * a.x - s * bb.x, c * a.y - s * bb.y);
+        nb = mk<T>(s * a.x + c * bb.x, s * a.y + c * bb.y);
+        break;
+      default:  // ZPHASE: diag(e^{i phi}, e^{-i phi})
+        na = mk<T>(a.x * c - a.y * s, a.x * s + a.y * c);
+        nb = mk<T>(bb.x * c + bb.y * s, -bb.x * s + bb.y * c);
+        break;
+    }
+    st[i0] = na;
+    st[i1] = nb;
+  }
+}
+
+// ------------------------------------------------------------ fused sweep
+template <typename T>
+__device__ __forceinline__ T shfl_xor_c(T v, int lanemask);
+template <>
+__device__ __forceinline__ float2 shfl_xor_c(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+template <>
+__device__ __forceinline__ double2 shfl_xor_c(double2 v, int m) {
+  return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_pair(typename V2<R>::T& a, typename V2<R>::T& b, int op,
+                                           R c, R s) {
+  using T = typename V2<R>::T;
+  const R h = (R)0.70710678118654752440;
+  T na, nb;
+  switch (op) {
+    case 0:
+      na = b;
+      nb = a;
+      break;
+    case 1:
+      na = mk<T>((a.x + b.x) * h, (a.y + b.y) * h);
+      nb = mk<T>((a.x - b.x) * h, (a.y - b.y) * h);
+      break;
+    case 2:
+      na = mk<T>(c * a.x - s * b.x, c * a.y - s * b.y);
+      nb = mk<T>(s * a.x + c * b.x, s * a.y + c * b.y);
+      break;
+    default:
+      na = mk<T>(a.x * c - a.y * s, a.x * s + a.y * c);
+      nb = mk<T>(b.x * c + b.y * s, -b.x * s + b.y * c);
+      break;
+  }
+  a = na;
+  b = nb;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) sweep_kernel(const typename V2<R>::T* in,
+                                                    typename V2<R>::T* out,
+                                                    uint64_t ntiles, const PermOp* __restrict__ perm,
+                                                    int nperm, const LocalOp* __restrict__ ops,
+                                                    int nops) {
+  using T = typename V2<R>::T;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t tile = warp; tile < ntiles; tile += nwarps) {
+    const uint64_t ci = (tile << 5) | (uint64_t)lane;  // chunk index = index >> 2
+    uint64_t src = ci;
+    for (int k = nperm - 1; k >= 0; --k) {
+      const PermOp p = perm[k];
+      if ((src & p.mask) == p.val) src ^= p.tbit;
+    }
+    T v[4];
+    const T* sp = in + (src << 2);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = sp[j];
+    const uint64_t idx0 = ci << 2;
+    for (int k = 0; k < nops; ++k) {
+      const LocalOp o = ops[k];
+      const R c = (R)o.c, s = (R)o.s;
+      if (o.target < 2) {
+        const int tb = 1 << o.target;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (j & tb) continue;
+          if (((idx0 | (uint64_t)j) & o.cmask) == o.cval) apply_pair<R>(v[j], v[j | tb], o.op, c, s);
+        }
+      } else {
+        const int lm = 1 << (o.target - 2);
+        const bool hi = (lane & lm) != 0;
+        const R h = (R)0.70710678118654752440;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool on = (((idx0 | (uint64_t)j) & o.cmask) == o.cval);
+          if (o.op == 3) {  // diagonal: no partner needed
+            if (on) {
+              const R sg = hi ? -s : s;
+              v[j] = mk<T>(v[j].x * c - v[j].y * sg, v[j].x * sg + v[j].y * c);
+            }
+            continue;
+          }
+          const T w = shfl_xor_c(v[j], lm);
+          if (!on) continue;
+          if (o.op == 0) {
+            v[j] = w;
+          } else if (o.op == 1) {
+            v[j] = hi ? mk<T>((w.x - v[j].x) * h, (w.y - v[j].y) * h)
+                      : mk<T>((v[j].x + w.x) * h, (v[j].y + w.y) * h);
+          } else {
+            v[j] = hi ? mk<T>(s * w.x + c * v[j].x, s * w.y + c * v[j].y)
+                      : mk<T>(c * v[j].x - s * w.x, c * v[j].y - s * w.y);
+          }
+        }
+      }
+    }
+    T* dp = out + idx0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dp[j] = v[j];
+  }
+}
+
+// --------------------------------------------------------------- reductions
+template <typename R>
+__global__ void norm_kernel(const typename V2<R>::T* __restrict__ st, uint64_t N,
+                            const uint64_t* __restrict__ pm, const uint64_t* __restrict__ pv,
+                            int npat, double* __restrict__ partial) {
+  double tot = 0.0, sel = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const auto a = st[i];
+    const double p = (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+    tot += p;
+    bool hit = false;
+    for (int k = 0; k < npat; ++k) hit |= ((i & pm[k]) == pv[k]);
+    if (hit) sel += p;
+  }
+  __shared__ double sh[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    sel += __shfl_xor_sync(0xffffffffu, sel, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sh[0][w] = tot;
+    sh[1][w] = sel;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += sh[0][k];
+      b += sh[1][k];
+    }
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblocks,
+                                       double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nblocks; ++k) {
+      a += partial[2 * k];
+      b += partial[2 * k + 1];
+    }
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+template <typename R>
+__global__ void compact_kernel(const typename V2<R>::T* __restrict__ st, double2* __restrict__ out,
+                               uint64_t count, int free_shift, int free_bits, uint64_t m_first,
+                               int m_shift) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t o = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; o < count; o += stride) {
+    const uint64_t f = o & ((1ull << free_bits) - 1);
+    const uint64_t m = m_first + (o >> free_bits);
+    const uint64_t idx = (m << m_shift) | (f << free_shift);
+    const auto a = st[idx];
+    out[o] = make_double2((double)a.x, (double)a.y);
+  }
+}
+
+int grid_for(uint64_t work, int block) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 132;
+  }
+  uint64_t g = (work + block - 1) / block;
+  const uint64_t cap = (uint64_t)sms * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,
+                        const double* d_val, int64_t count, cudaStream_t st) {
+  const size_t bytes = n_amps * (prec == CSIM_C64 ? sizeof(float2) : sizeof(double2));
+  cudaError_t e = cudaMemsetAsync(state, 0, bytes, st);
+  if (e != cudaSuccess) return e;
+  if (count <= 0) return cudaSuccess;
+  const int blk = 256;
+  const int grd = (int)((count + blk - 1) / blk);
+  if (prec == CSIM_C64)
+    init_scatter_kernel<float><<<grd, blk, 0, st>>>((float2*)state, d_idx, d_val, count);
+  else
+    init_scatter_kernel<double><<<grd, blk, 0, st>>>((double2*)state, d_idx, d_val, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaStream_t st) {
+  GateParams p;
+  p.cmask = g.cmask;
+  p.cval = g.cval;
+  p.tbit = 1ull << g.target;
+  const uint64_t fixedmask = g.cmask | p.tbit;
+  p.nfixed = 0;
+  for (int b = 0; b < 64; ++b)
+    if ((fixedmask >> b) & 1ull) p.fixed[p.nfixed++] = (uint8_t)b;
+  p.npairs = 1ull << (n - p.nfixed);
+  p.op = g.op;
+  if (g.op == 2) {
+    p.c = cos(g.angle / 2.0);
+    p.s = sin(g.angle / 2.0);
+  } else if (g.op == 3) {
+    p.c = cos(g.angle);
+    p.s = sin(g.angle);
+  } else {
+    p.c = p.s = 0.0;
+  }
+  const int blk = 256;
+  const int grd = grid_for(p.npairs, blk);
+  if (prec == CSIM_C64)
+    gate_kernel<float><<<grd, blk, 0, st>>>((float2*)state, p);
+  else
+    gate_kernel<double><<<grd, blk, 0, st>>>((double2*)state, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const PermOp* d_perm,
+                         int nperm, const LocalOp* d_ops, int nops, cudaStream_t st) {
+  const uint64_t ntiles = 1ull << (n - 7);
+  const int blk = 256;
+  const int grd = grid_for(ntiles * 32, blk);
+  if (prec == CSIM_C64)
+    sweep_kernel<float><<<grd, blk, 0, st>>>((const float2*)in, (float2*)out, ntiles, d_perm,
+                                             nperm, d_ops, nops);
+  else
+    sweep_kernel<double><<<grd, blk, 0, st>>>((const double2*)in, (double2*)out, ntiles, d_perm,
+                                              nperm, d_ops, nops);
+  return cudaGetLastError();
+}
+
+int norm_partials_needed() { return 2048; }
+
+cudaError_t launch_norms(const void* state, int prec, int n, const uint64_t* d_pm,
+                         const uint64_t* d_pv, int npat, double* d_partial, double* d_out,
+                         cudaStream_t st) {
+  const uint64_t N = 1ull << n;
+  const int blk = 256;
+  int grd = grid_for(N, blk);
+  if (grd > norm_partials_needed()) grd = norm_partials_needed();
+  if (prec == CSIM_C64)
+    norm_kernel<float><<<grd, blk, 0, st>>>((const float2*)state, N, d_pm, d_pv, npat, d_partial);
+  else
+    norm_kernel<double><<<grd, blk, 0, st>>>((const double2*)state, N, d_pm, d_pv, npat,
+                                             d_partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reduce_partials_kernel<<<1, 32, 0, st>>>(d_partial, grd, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const void* state, int prec, double* d_out, uint64_t count,
+                           int free_shift, int free_bits, uint64_t m_first, int m_shift,
+                           cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const int blk = 256;
+  const int grd = grid_for(count, blk);
+  if (prec == CSIM_C64)
+    compact_kernel<float><<<grd, blk, 0, st>>>((const float2*)state, (double2*)d_out, count,
+                                               free_shift, free_bits, m_first, m_shift);
+  else
+    compact_kernel<double><<<grd, blk, 0, st>>>((const double2*)state, (double2*)d_out, count,
+                                                free_shift, free_bits, m_first, m_shift);
+  return cudaGetLastError();
+}
+
+}  // namespace csim

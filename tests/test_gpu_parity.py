@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (derived in DESIGN.md, "Parity tolerances"):
+  * complex128, truncated d, full state vs the naive simulator: 1e-12 relative L2;
+  * complex64, full state: 1e-4 relative L2 (spec bound), expected ~1e-6;
+  * complex128 at the full QSVT degree, postselected block vs the classical
+    evaluator: rounding grows with the number of gate applications G as about
+    G * 2^-53 on a unit-norm state, relative to the block norm sqrt(p).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+import paper_2606_12770_gb300 as G
+from oracle import circuit as OC
+from oracle import qsvt as Q
+from oracle import statevec as S
+from oracle.layout import Layout
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def oracle_full_state(cfg, f0, phases):
+    Nx, tau, NC, K, dt, Nt = cfg
+    lay = Layout(Nx, NC, K, Nt)
+    psi = np.zeros(1 << lay.n, dtype=complex)
+    init, _ = OC.initial_state(lay, f0)
+    for k, v in init.items():
+        psi[k] = v
+    S.DenseSim(lay.n).run(psi, OC.build_qsvt(*cfg, list(phases)))
+    return psi, lay
+
+
+def gpu_full_state(cfg, f0, phases, prec, mode):
+    c = G.Circuit(*cfg, phases=phases)
+    c.set_exec(mode)
+    c.init(f0, prec)
+    c.run()
+    return c.read_state(), c
+
+
+C1 = (4, 0.8, 2, 2, 0.1, 2)
+SMALL = [((2, 0.8, 1, 1, 0.1, 1), 3), ((4, 0.8, 1, 2, 0.1, 2), 5), ((8, 0.7, 1, 3, 0.2, 3), 3),
+         ((2, 1.1, 2, 3, 0.1, 2), 3), ((4, 0.6, 2, 1, 0.15, 3), 1)]
+
+
+@pytest.mark.parametrize("d", [1, 3])
+@pytest.mark.parametrize("mode", [G.CSIM_EXEC_FUSED, G.CSIM_EXEC_GATE])
+def test_c1_full_state_c128(d, mode):
+    f0, _ = I.lbm_instance(4, 0, tau=0.8)
+    ph = I.random_phases(d, 100 + d)
+    ref, lay = oracle_full_state(C1, f0, ph)
+    got, c = gpu_full_state(C1, f0, ph, G.CSIM_C128, mode)
+    assert rel_l2(got, ref) < 1e-12
+    amps, p, tot = c.postselect()
+    assert abs(tot - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("cfg,d", SMALL)
+def test_small_configs_full_state_c128_and_c64(cfg, d):
+    f0, _ = I.lbm_instance(cfg[0], 5, tau=cfg[1])
+    ph = I.random_phases(d, 7)
+    ref, lay = oracle_full_state(cfg, f0, ph)
+    got, _ = gpu_full_state(cfg, f0, ph, G.CSIM_C128, G.CSIM_EXEC_FUSED)
+    assert rel_l2(got, ref) < 1e-12
+    got64, _ = gpu_full_state(cfg, f0, ph, G.CSIM_C64, G.CSIM_EXEC_FUSED)
+    assert rel_l2(got64, ref) < 1e-4
+
+
+def _postselected_reference(cfg, f0, phases):
+    y, lay, M, b = Q.qsvt_postselected(*cfg, f0, phases)
+    final = Q.final_slot_mask(lay)
+    phys = lay.physical_indices()
+    return y, lay, phys, final
+
+
+def _gpu_postselected_by_index(c, lay):
+    amps, p, tot = c.postselect()
+    free_shift = 2 + lay.niL
+    m_shift = lay.regs["m"][0]
+    free_bits = m_shift - free_shift
+    return amps, p, tot, free_shift, free_bits, m_shift
+
+
+def _compare_postselect(c, cfg, f0, phases):
+    y, lay, phys, final = _postselected_reference(cfg, f0, phases)
+    amps, p, tot, free_shift, free_bits, m_shift = _gpu_postselected_by_index(c, lay)
+    # output position of each physical final-time index
+    sel = phys[final]
+    m = sel >> m_shift
+    f = (sel >> free_shift) & ((1 << free_bits) - 1)
+    pos = ((m - lay.Nt) << free_bits) + f
+    got = amps[pos]
+    ref = y[final]
+    p_ref = float(np.sum(ref * ref))
+    # everything else in the postselected block is non-physical and must be ~0
+    mask = np.ones(amps.shape[0], dtype=bool)
+    mask[pos] = False
+    return rel_l2(got, ref), abs(p - p_ref) / p_ref, float(np.max(np.abs(amps[mask]), initial=0.0)), tot, p_ref
+
+
+@pytest.mark.parametrize("prec,tol", [(G.CSIM_C128, 1e-12), (G.CSIM_C64, 1e-4)])
+def test_c1_postselect_truncated(prec, tol):
+    f0, _ = I.lbm_instance(4, 0, tau=0.8)
+    ph = I.random_phases(13, 3)
+    c = G.Circuit(*C1, phases=ph)
+    c.init(f0, prec)
+    c.run()
+    e_amp, e_p, leak, tot, p_ref = _compare_postselect(c, C1, f0, ph)
+    assert e_amp < tol and e_p < tol and leak < tol * math.sqrt(p_ref)
+    assert abs(tot - 1.0) < (1e-12 if prec == G.CSIM_C128 else 1e-5)
+
+
+def test_c1_full_degree_postselect_c128():
+    """Full Eq. d-star degree (d = 1957) with the build's own kappa and phases."""
+    f0, _ = I.lbm_instance(4, 0, tau=0.8)
+    c = G.Circuit(*C1)
+    inf = c.info()
+    assert inf["d"] == 1957
+    ph = c.export_phases()
+    c.init(f0, G.CSIM_C128)
+    c.run()
+    e_amp, e_p, leak, tot, p_ref = _compare_postselect(c, C1, f0, ph)
+    G_gates = inf["n_gates_total"]
+    bound = 50 * G_gates * 2.0 ** -53 / math.sqrt(p_ref)
+    print(f"full-degree c128: rel L2 {e_amp:.3e}, p rel {e_p:.3e}, bound {bound:.3e}, p {p_ref:.3e}")
+    assert e_amp < bound and abs(tot - 1.0) < 1e-9
+
+
+def _random_gates(n, count, seed, high_h=True):
+    rng = np.random.default_rng(seed)
+    g = []
+    for _ in range(count):
+        op = int(rng.integers(0, 4))
+        t = int(rng.integers(n)) if (high_h or op == 0) else int(rng.integers(min(n, 7)))
+        others = [b for b in range(n) if b != t]
+        nc = int(rng.integers(0, 5))
+        cs = rng.choice(others, nc, replace=False) if nc else []
+        cm = sum(1 << int(c) for c in cs)
+        cv = sum(int(rng.integers(2)) << int(c) for c in cs)
+        ang = float(rng.uniform(-math.pi, math.pi)) if op in (2, 3) else 0.0
+        g.append((op, t, cm, cv, ang, 0))
+    return g
+
+
+@pytest.mark.parametrize("n,seed", [(5, 1), (7, 2), (12, 3), (16, 4)])
+@pytest.mark.parametrize("mode", [G.CSIM_EXEC_FUSED, G.CSIM_EXEC_GATE])
+def test_random_gate_lists(n, seed, mode):
+    gates = _random_gates(n, 120, seed)
+    psi0 = I.random_unit_state(n, seed)
+    ref = S.DenseSim(n).run(psi0.copy(), gates)
+    for prec, tol in ((G.CSIM_C128, 1e-12), (G.CSIM_C64, 1e-5)):
+        sv = G.StateVector(n, prec)
+        sv.load(psi0)
+        sv.compile(gates, mode)
+        sv.run(1)
+        assert rel_l2(sv.read(), ref) < tol
+
+
+def test_microbench_vocabulary_parity():
+    """The gate-vocabulary microbenchmark stream at n = 20, checked against O2."""
+    n = 20
+    gates = I.microbench_gates(n, 300, 0)
+    psi0 = I.random_unit_state(n, 0)
+    ref = S.DenseSim(n).run(psi0.copy(), gates)
+    for prec, tol in ((G.CSIM_C128, 1e-12), (G.CSIM_C64, 1e-5)):
+        sv = G.StateVector(n, prec)
+        sv.load(psi0)
+        sv.compile(gates, G.CSIM_EXEC_FUSED)
+        sv.run(1)
+        assert rel_l2(sv.read(), ref) < tol
+
+
+def test_empty_program_and_reuse():
+    n = 9
+    psi0 = I.random_unit_state(n, 9)
+    sv = G.StateVector(n, G.CSIM_C128)
+    sv.load(psi0)
+    sv.compile([], G.CSIM_EXEC_FUSED)
+    sv.run(3)
+    assert np.array_equal(sv.read(), psi0)
+    gates = _random_gates(n, 40, 9)
+    sv.compile(gates, G.CSIM_EXEC_FUSED)
+    sv.run(2)
+    ref = S.DenseSim(n).run(S.DenseSim(n).run(psi0.copy(), gates), gates)
+    assert rel_l2(sv.read(), ref) < 1e-12
+
+
+def test_state_machine_errors():
+    f0, _ = I.lbm_instance(4, 0, tau=0.8)
+    c = G.Circuit(*C1, phases=I.random_phases(1, 0))
+    c.init(f0, G.CSIM_C64)
+    c.run()
+    with pytest.raises(G.CsimError) as e:
+        c.run()
+    assert e.value.status == -5
+    c.init(f0, G.CSIM_C64)  # re-init reuses the allocation
+    c.run()
+    _, p, tot = c.postselect(False)
+    assert 0.0 < p < 1.0 and abs(tot - 1.0) < 1e-5
+    with pytest.raises(G.CsimError):
+        c.init(np.full((4, 3), np.nan), G.CSIM_C64)
