@@ -44,6 +44,8 @@ WORKLOADS = {
     "precision-nx64-k4-nt16-d13-c64": (64, 2, 4, 16, 0.1, None, (0.6, 1.2), 1, 13, 1000.0, "c64"),
     "precision-nx64-k4-nt16-d13-c128": (64, 2, 4, 16, 0.1, None, (0.6, 1.2), 1, 13, 1000.0, "c128"),
     "plain-nx4-k2-nt2-c128": (4, 2, 2, 2, 0.1, 0.8, None, 0, 0, 0.0, "c128"),
+    # 28-qubit member of the precision family (2 GiB in complex64) for ncu captures
+    "profile-nx16-k4-nt16-d13-c64": (16, 2, 4, 16, 0.1, None, (0.6, 1.2), 1, 13, 1000.0, "c64"),
 }
 DEFAULT = "precision-nx64-k4-nt16-d13-c64"
 

@@ -119,7 +119,8 @@ csim_status csim_build_ex(const csim_build_opts* opts, csim_circuit** out);
 csim_status csim_info(const csim_circuit* c, csim_info_t* out);
 
 /* Canonical gate list.  which = 0: one U_L; which = 1: the whole QSVT circuit
- * (H_s, PHI(phi_0), d alternating U_L / U_L^dag each followed by PHI, H_s).
+ * (H_s, PHI(phi_0), d alternating calls U_L^dag, U_L, U_L^dag, ... each followed by
+ * PHI, H_s; starting with U_L^dag makes the 1/x polynomial act as lambda_L L^{-1}).
  * Writes min(cap, total) records to buf (may be NULL when cap = 0) and the
  * total count to *len.  Returns CSIM_ERR_ARG if cap < total and buf != NULL. */
 csim_status csim_export_gates(const csim_circuit* c, int32_t which, csim_gate* buf,

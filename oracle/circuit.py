@@ -262,7 +262,13 @@ def phase_gates(lay: Layout, phi):
 
 
 def build_qsvt(Nx, tau, NC, K, dt, Nt, phases):
-    """Fig. circuit-qsvt with signal Hadamards: H, PHI(phi_0), [U_L or U_L^dag, PHI]*d, H."""
+    """Fig. circuit-qsvt with signal Hadamards: H, PHI(phi_0), [U_L^dag or U_L, PHI]*d, H.
+
+    The first oracle call on b is U_L^dag (the block encoding of L^T): an odd
+    polynomial P ~ 1/x applied this way gives P^{SV}(L^T/lambda) ~ lambda L^{-1},
+    the inverse that Sec. II.D.5 states the circuit implements.  Starting
+    with U_L, as the figure is drawn, would give (L^T)^{-1} instead.
+    """
     d = len(phases) - 1
     if d < 1 or d % 2 == 0:
         raise ValueError("need an odd degree d >= 1 (d+1 phases)")
@@ -273,7 +279,7 @@ def build_qsvt(Nx, tau, NC, K, dt, Nt, phases):
     g = [_gate(OP_H, s, tag=TAG_SIGNAL)]
     g += phase_gates(lay, float(phases[0]))
     for j in range(1, d + 1):
-        g += UL if j % 2 == 1 else ULd
+        g += ULd if j % 2 == 1 else UL
         g += phase_gates(lay, float(phases[j]))
     g.append(_gate(OP_H, s, tag=TAG_SIGNAL))
     return g

@@ -7,9 +7,11 @@ realises on each singular-value plane, a phase list (phi_0..phi_d) defines
     W(x) = e^{i phi_0 Z} R(x) e^{i phi_1 Z} R(x) ... R(x) e^{i phi_d Z},
     P(x) = <0| W(x) |0>.
 
-The signal-qubit Hadamards average the +phi and -phi branches, so the block
-(s=0, ancillas=0) of the circuit is Re(P)^{SV}(L/lambda_L) applied to b
-(reading R13), where Re(P) is the real odd polynomial x -> Re P(x).  This
+The signal-qubit Hadamards average the +phi and -phi branches, and the first
+oracle call on b is U_L^dag, so the block (s=0, ancillas=0) of the circuit is
+Re(P)^{SV}(L^T/lambda_L) applied to b (reading R13 for the real part), where
+Re(P) is the real odd polynomial x -> Re P(x); for P ~ 1/x this is
+~ lambda_L L^{-1} b, the solution of L x = b (Sec. II.D.5).  This
 module computes that vector directly from L (``physics.l_matrix``) using
 Chebyshev coefficients of Re(P) and the singular-value Chebyshev recurrence
 
@@ -88,7 +90,8 @@ def apply_odd_sv_poly(c: np.ndarray, M: sp.spmatrix, b: np.ndarray) -> np.ndarra
 def qsvt_postselected(Nx, tau, NC, K, dt, Nt, f0, phases):
     """Postselected (s=0, ancillas=0) amplitudes on every physical (slot, j).
 
-    Returns (y, lay, L_over_lambda, b) with y ordered like L's rows.
+    y = Re(P)^{SV}((L/lambda_L)^T) b.  Returns (y, lay, L/lambda_L, b), y ordered
+    like L's rows.
     """
     lay = Layout(Nx, NC, K, Nt)
     A = P.carleman_A(Nx, tau, NC, "periodic")
@@ -101,7 +104,7 @@ def qsvt_postselected(Nx, tau, NC, K, dt, Nt, f0, phases):
     if np.max(np.abs(c[0::2])) > 1e-10:
         raise ValueError("Re P is not odd")
     M = L / lam
-    y = apply_odd_sv_poly(c, M, b)
+    y = apply_odd_sv_poly(c, M.T.tocsr(), b)
     return y, lay, M, b
 
 

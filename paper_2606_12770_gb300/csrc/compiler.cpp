@@ -372,7 +372,8 @@ std::vector<Gate> build_qsvt(const Layout& L, const std::vector<Gate>& UL,
   g.push_back(gate(OP_H, s, Ctrl{}, 0.0, TAG_SIGNAL));
   for (const Gate& x : phase_gates(L, phases[0])) g.push_back(x);
   for (int j = 1; j <= d; ++j) {
-    const std::vector<Gate>& U = (j % 2 == 1) ? UL : ULd;
+    // the first call on b is U_L^dag: P^{SV}(L^T/lambda) ~ lambda L^{-1} (Sec. II.D.5)
+    const std::vector<Gate>& U = (j % 2 == 1) ? ULd : UL;
     g.insert(g.end(), U.begin(), U.end());
     for (const Gate& x : phase_gates(L, phases[j])) g.push_back(x);
   }

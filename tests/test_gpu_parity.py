@@ -131,6 +131,24 @@ def test_c1_full_degree_postselect_c128():
     bound = 50 * G_gates * 2.0 ** -53 / math.sqrt(p_ref)
     print(f"full-degree c128: rel L2 {e_amp:.3e}, p rel {e_p:.3e}, bound {bound:.3e}, p {p_ref:.3e}")
     assert e_amp < bound and abs(tot - 1.0) < 1e-9
+    # physics: the final-time block is scale * lambda_L * L^{-1} b up to the
+    # polynomial's residual 1/T_n(z0) (Sec. II.D.5; classical forward substitution)
+    from oracle import physics as P
+    A = P.carleman_A(4, 0.8, 2)
+    L = P.l_matrix(A, 0.1, 2, 2)
+    vec = P.carleman_vector(np.asarray(f0).reshape(-1), 2)
+    b = P.rhs_vector(vec / np.linalg.norm(vec), 2, 2)
+    x = inf["poly_scale"] * inf["lambda_L"] * P.solve_l(L, b)
+    y, lay, phys, final = _postselected_reference(C1, f0, ph)
+    a = 1.0 / inf["kappa_qsvt"]
+    delta = 1.0 / math.cosh(((inf["d"] + 1) // 2) * math.acosh((1 + a * a) / (1 - a * a)))
+    amps, p, tot = c.postselect()
+    sel = phys[final]
+    fs, ms = 2 + lay.niL, lay.regs["m"][0]
+    pos = ((sel >> ms) - lay.Nt) * (1 << (ms - fs)) + ((sel >> fs) & ((1 << (ms - fs)) - 1))
+    phys_err = rel_l2(amps[pos].real, x[final])
+    print(f"QSVT vs classical Taylor solve at T: rel L2 {phys_err:.3e} (polynomial residual {delta:.3e})")
+    assert phys_err < 1.01 * delta
 
 
 def _random_gates(n, count, seed, high_h=True):
@@ -194,7 +212,7 @@ def test_empty_program_and_reuse():
 
 def test_state_machine_errors():
     f0, _ = I.lbm_instance(4, 0, tau=0.8)
-    c = G.Circuit(*C1, phases=I.random_phases(1, 0))
+    c = G.Circuit(*C1, phases=I.random_phases(5, 0))
     c.init(f0, G.CSIM_C64)
     c.run()
     with pytest.raises(G.CsimError) as e:
