@@ -155,3 +155,29 @@ def degree_from_kappa(kappa: float, eps: float) -> int:
     """Eq. d-star: d = kappa * log(2 kappa / eps) / 2, rounded up to the next odd integer."""
     d = int(math.ceil(kappa * math.log(2.0 * kappa / eps) / 2.0))
     return d if d % 2 == 1 else d + 1
+
+
+def fit_phases(target, d: int, seed: int = 0, tol: float = 1e-12):
+    """Phases (reflection convention) with Re P = target on [-1, 1], by least squares.
+
+    Plain Levenberg-Marquardt (scipy) over all d+1 phases, matching Re P at
+    the d+1 Chebyshev-Gauss nodes (a degree-d odd polynomial is fixed by its
+    values there).  Slow and only meant for small d; raises if the fit does
+    not reach ``tol``.  Restarts from seeded random points.
+    """
+    from scipy.optimize import least_squares
+
+    x = chebyshev_nodes(d + 1)
+    f = target(x)
+    rng = np.random.default_rng(seed)
+    best = None
+    for _ in range(20):
+        p0 = rng.uniform(-math.pi, math.pi, d + 1)
+        r = least_squares(lambda ph: qsp_poly(ph, x).real - f, p0, method="lm",
+                          xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=200 * (d + 1))
+        err = float(np.max(np.abs(r.fun)))
+        if best is None or err < best[1]:
+            best = (r.x, err)
+        if err < tol:
+            return r.x
+    raise RuntimeError(f"phase fit did not converge (best max error {best[1]:.2e})")

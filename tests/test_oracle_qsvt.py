@@ -126,3 +126,16 @@ def test_qsvt_solves_L_within_polynomial_error(cfg):
     err = np.linalg.norm(y - xsol) / np.linalg.norm(xsol)
     assert err <= delta * 1.0001 + 1e-12
     assert err >= 0.01 * delta  # the bound is not vacuous at this degree
+
+
+@pytest.mark.parametrize("kappa,d", [(10.0, 31), (4.0, 9)])
+def test_golden_phases_reproduce_target(kappa, d):
+    """tests/golden/phases_*.txt (fitted by the oracle) realise the 1/x target."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", f"phases_k{int(kappa)}_d{d}.txt")
+    ph = np.loadtxt(path)
+    Pf, _ = Q.inverse_target(kappa, d)
+    x = np.linspace(-1, 1, 2001)
+    x = x[x != 0]
+    assert ph.shape == (d + 1,)
+    assert np.max(np.abs(Q.qsp_poly(ph, x).real - Pf(x))) < 1e-12
