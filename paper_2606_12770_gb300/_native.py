@@ -28,7 +28,7 @@ EXPORTED = [
     "csim_export_mask", "csim_init", "csim_set_exec", "csim_run", "csim_sync",
     "csim_postselect", "csim_read_state", "csim_free", "csim_sv_create", "csim_sv_load",
     "csim_sv_compile", "csim_sv_run", "csim_sv_read", "csim_sv_info", "csim_sv_free",
-    "csim_last_error",
+    "csim_emulate_fused", "csim_last_error",
 ]
 
 
@@ -100,6 +100,7 @@ def load():
         "csim_sv_read": ([VP, DP, SZ], C.c_int),
         "csim_sv_info": ([VP, P(C.c_int64), DP, P(C.c_uint64)], C.c_int),
         "csim_sv_free": ([VP], C.c_int),
+        "csim_emulate_fused": ([VP, SZ, C.c_int32, DP, P(C.c_int64)], C.c_int),
         "csim_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -266,6 +267,21 @@ class StateVector:
         sb = C.c_uint64()
         _check(_lib.csim_sv_info(self._h, C.byref(ns), C.byref(au), C.byref(sb)))
         return {"n_sweeps": ns.value, "amp_updates": au.value, "state_bytes": sb.value}
+
+
+FUSE_STAT_NAMES = ["sweeps", "single", "perm_gates", "segments", "local_gates", "mux",
+                   "mux_gates", "mux_entries", "max_bucket", "lut_entries", "max_support", "passes"]
+
+
+def emulate_fused(gates, n, amps):
+    """Host executor of the fused program (testing aid); returns (state, stats dict)."""
+    lib = load()
+    g = gates_to_records(gates)
+    a = np.ascontiguousarray(amps, dtype=np.complex128).copy()
+    st = np.zeros(12, dtype=np.int64)
+    _check(lib.csim_emulate_fused(g.ctypes.data_as(C.c_void_p), g.shape[0], int(n),
+                                  _dp(a.view(np.float64)), st.ctypes.data_as(C.POINTER(C.c_int64))))
+    return a, dict(zip(FUSE_STAT_NAMES, (int(x) for x in st)))
 
 
 def gates_to_records(gates) -> np.ndarray:

@@ -580,4 +580,31 @@ csim_status csim_sv_free(csim_sv* s) {
   return CSIM_OK;
 }
 
+csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n, double* amps,
+                               int64_t* stats) {
+  if ((!gates && n_gates) || !amps) return fail(CSIM_ERR_ARG, "null argument");
+  if (n < 7 || n > 24) return fail(CSIM_ERR_ARG, "n must be in [7, 24]");
+  for (size_t i = 0; i < n_gates; ++i) {
+    const csim_gate& g = gates[i];
+    if (g.op > 3 || g.target >= n || ((g.cmask >> g.target) & 1ull) || (g.cval & ~g.cmask) ||
+        (g.cmask >> n))
+      return fail(CSIM_ERR_ARG, "invalid gate record " + std::to_string(i));
+  }
+  Program p;
+  std::vector<Gate> gl(gates, gates + n_gates);
+  csim::build_program(gl, n, CSIM_EXEC_FUSED, &p);
+  const size_t N = (size_t)1 << n;
+  std::vector<double> st(amps, amps + 2 * N);
+  csim::emulate_program(p, &st);
+  std::memcpy(amps, st.data(), 2 * N * sizeof(double));
+  if (stats) {
+    const csim::FuseStats& f = p.stats;
+    const int64_t v[12] = {f.sweeps,     f.single,      f.perm_gates, f.segments,
+                           f.local_gates, f.mux,        f.mux_gates,  f.mux_entries,
+                           f.max_bucket, f.lut_entries, f.max_support, p.passes};
+    std::memcpy(stats, v, sizeof(v));
+  }
+  return CSIM_OK;
+}
+
 }  // extern "C"

@@ -13,31 +13,49 @@ namespace csim {
 
 struct Step {
   int kind = 0;  // 0 = fused sweep, 1 = single gate
-  int perm_off = 0, perm_cnt = 0, op_off = 0, op_cnt = 0;
+  int seg_off = 0, nseg = 0, op_off = 0, nops = 0;
   csim_gate g{};
+};
+
+struct FuseStats {
+  int64_t sweeps = 0, single = 0, perm_gates = 0, segments = 0, local_gates = 0, mux = 0;
+  int64_t mux_gates = 0, mux_entries = 0, max_bucket = 0, lut_entries = 0, max_support = 0;
 };
 
 struct Program {
   int n = 0;
   csim_exec mode = CSIM_EXEC_FUSED;
   std::vector<Step> steps;
-  std::vector<PermOp> perm;
+  std::vector<PermSeg> segs;
+  std::vector<uint16_t> lut;
   std::vector<LocalOp> ops;
-  PermOp* d_perm = nullptr;
+  std::vector<MuxDesc> mux;
+  std::vector<uint2> mtab;
+  std::vector<MuxEntry> ment;
+  // device copies
+  PermSeg* d_segs = nullptr;
+  uint16_t* d_lut = nullptr;
   LocalOp* d_ops = nullptr;
-  int64_t passes = 0;         // HBM passes per execution
-  double amp_updates = 0.0;   // sum over elementary gates of amplitudes changed
-  bool pingpong = false;      // some step gathers out of place
+  MuxDesc* d_mux = nullptr;
+  uint2* d_mtab = nullptr;
+  MuxEntry* d_ment = nullptr;
+  int64_t passes = 0;        // HBM passes per execution
+  double amp_updates = 0.0;  // sum over elementary gates of amplitudes changed
+  bool pingpong = false;     // some step gathers out of place
   bool uploaded = false;
+  FuseStats stats;
 };
 
-// Build the program for `gates` on an n-qubit state.  FUSED mode needs n >= 7
-// (the warp tile); smaller states fall back to one launch per gate.
+// Build the program for `gates` on an n-qubit state.  FUSED mode needs
+// 7 <= n <= 34 (the warp tile and 32-bit chunk indices); other sizes fall
+// back to one launch per gate.
 void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p);
 cudaError_t upload_program(Program* p, cudaStream_t st);
 void free_program(Program* p);
 // Run the program on buf[*cur] (and buf[1 - *cur] when it gathers); *cur tracks
 // which buffer holds the state afterwards.
 cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st);
+// Host executor of a fused program (FP64, kernel semantics) for testing.
+void emulate_program(const Program& p, std::vector<double>* amps);
 
 }  // namespace csim

@@ -140,53 +140,129 @@ __device__ __forceinline__ void apply_pair(typename V2<R>::T& a, typename V2<R>:
 }
 
 template <typename R>
+struct Coef;
+template <>
+struct Coef<float> {
+  template <typename O>
+  static __device__ __forceinline__ float c(const O& o) { return o.cf; }
+  template <typename O>
+  static __device__ __forceinline__ float s(const O& o) { return o.sf; }
+};
+template <>
+struct Coef<double> {
+  template <typename O>
+  static __device__ __forceinline__ double c(const O& o) { return o.cd; }
+  template <typename O>
+  static __device__ __forceinline__ double s(const O& o) { return o.sd; }
+};
+
+__device__ __forceinline__ uint32_t gather_key(uint32_t x, const BitRun* runs, uint32_t nruns) {
+  uint32_t key = 0;
+#pragma unroll
+  for (int r = 0; r < kMaxRuns; ++r) {
+    if (r < (int)nruns) {
+      const BitRun b = runs[r];
+      key |= ((x >> b.lo) & ((1u << b.len) - 1u)) << b.off;
+    }
+  }
+  return key;
+}
+
+__device__ __forceinline__ uint32_t scatter_key(uint32_t x, uint32_t v, uint32_t supmask,
+                                                const BitRun* runs, uint32_t nruns) {
+  x &= ~supmask;
+#pragma unroll
+  for (int r = 0; r < kMaxRuns; ++r) {
+    if (r < (int)nruns) {
+      const BitRun b = runs[r];
+      x |= ((v >> b.off) & ((1u << b.len) - 1u)) << b.lo;
+    }
+  }
+  return x;
+}
+
+// RY(c, s) on the in-thread pair (a, b) = (bit 0, bit 1) of the target qubit.
+template <typename T, typename R>
+__device__ __forceinline__ void rot(T& a, T& b, R c, R s) {
+  const T na = mk<T>(c * a.x - s * b.x, c * a.y - s * b.y);
+  b = mk<T>(s * a.x + c * b.x, s * a.y + c * b.y);
+  a = na;
+}
+
+// One fused sweep.  Each lane owns one 4-amplitude chunk of the destination
+// tile: it computes the source chunk by running the permutation segments
+// (the inverse permutation, i.e. the gates in reverse order), loads it, then
+// applies the tile-local gates in order.
+template <typename R>
 __global__ void __launch_bounds__(256) sweep_kernel(const typename V2<R>::T* in,
-                                                    typename V2<R>::T* out,
-                                                    uint64_t ntiles, const PermOp* __restrict__ perm,
-                                                    int nperm, const LocalOp* __restrict__ ops,
-                                                    int nops) {
+                                                    typename V2<R>::T* out, uint32_t ntiles,
+                                                    SweepArgs a) {
   using T = typename V2<R>::T;
-  const int lane = threadIdx.x & 31;
-  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t tile = warp; tile < ntiles; tile += nwarps) {
-    const uint64_t ci = (tile << 5) | (uint64_t)lane;  // chunk index = index >> 2
-    uint64_t src = ci;
-    for (int k = nperm - 1; k >= 0; --k) {
-      const PermOp p = perm[k];
-      if ((src & p.mask) == p.val) src ^= p.tbit;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t tile = warp; tile < ntiles; tile += nwarps) {
+    const uint32_t ci = (tile << 5) | lane;  // chunk index = state index >> 2
+    uint32_t src = ci;
+    for (int k = 0; k < a.nseg; ++k) {
+      const PermSeg& g = a.segs[k];
+      const uint32_t key = gather_key(src, g.runs, g.nruns);
+      const uint32_t v = __ldg(a.lut + g.lut_off + key);
+      src = scatter_key(src, v, g.supmask, g.runs, g.nruns);
     }
     T v[4];
-    const T* sp = in + (src << 2);
+    const T* sp = in + ((size_t)src << 2);
 #pragma unroll
     for (int j = 0; j < 4; ++j) v[j] = sp[j];
-    const uint64_t idx0 = ci << 2;
-    for (int k = 0; k < nops; ++k) {
-      const LocalOp o = ops[k];
-      const R c = (R)o.c, s = (R)o.s;
+    for (int k = 0; k < a.nops; ++k) {
+      const LocalOp& o = a.ops[k];
+      const bool cok = (ci & o.cm) == o.cv;
+      const uint32_t lm = o.lm, lv = o.lv;
+      if (o.op == 4) {  // multiplexed RY on bit o.target
+        const MuxDesc& md = a.mux[o.cm];
+        const uint32_t key = gather_key(ci, md.runs, md.nruns);
+        const uint2 bk = __ldg(a.mtab + md.tab_off + key);
+        for (uint32_t e = bk.x; e < bk.x + bk.y; ++e) {
+          const MuxEntry& E = a.ment[e];
+          if ((ci & E.cm) != E.cv) continue;
+          const R c = Coef<R>::c(E), s = Coef<R>::s(E);
+          if (md.target == 0) {
+            if ((0u & E.lm) == E.lv) rot<T, R>(v[0], v[1], c, s);
+            if ((2u & E.lm) == E.lv) rot<T, R>(v[2], v[3], c, s);
+          } else {
+            if ((0u & E.lm) == E.lv) rot<T, R>(v[0], v[2], c, s);
+            if ((1u & E.lm) == E.lv) rot<T, R>(v[1], v[3], c, s);
+          }
+        }
+        continue;
+      }
+      const R c = Coef<R>::c(o), s = Coef<R>::s(o);
       if (o.target < 2) {
-        const int tb = 1 << o.target;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (j & tb) continue;
-          if (((idx0 | (uint64_t)j) & o.cmask) == o.cval) apply_pair<R>(v[j], v[j | tb], o.op, c, s);
+        if (!cok) continue;
+        if (o.target == 0) {
+          if ((0u & lm) == lv) apply_pair<R>(v[0], v[1], o.op, c, s);
+          if ((2u & lm) == lv) apply_pair<R>(v[2], v[3], o.op, c, s);
+        } else {
+          if ((0u & lm) == lv) apply_pair<R>(v[0], v[2], o.op, c, s);
+          if ((1u & lm) == lv) apply_pair<R>(v[1], v[3], o.op, c, s);
         }
       } else {
-        const int lm = 1 << (o.target - 2);
-        const bool hi = (lane & lm) != 0;
+        const int lmask = 1 << (o.target - 2);
+        const bool hi = (lane & (uint32_t)lmask) != 0;
         const R h = (R)0.70710678118654752440;
+        if (o.op == 3) {  // diagonal: no partner needed
+          if (!cok) continue;
+          const R sg = hi ? -s : s;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (((uint32_t)j & lm) == lv)
+              v[j] = mk<T>(v[j].x * c - v[j].y * sg, v[j].x * sg + v[j].y * c);
+          continue;
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const bool on = (((idx0 | (uint64_t)j) & o.cmask) == o.cval);
-          if (o.op == 3) {  // diagonal: no partner needed
-            if (on) {
-              const R sg = hi ? -s : s;
-              v[j] = mk<T>(v[j].x * c - v[j].y * sg, v[j].x * sg + v[j].y * c);
-            }
-            continue;
-          }
-          const T w = shfl_xor_c(v[j], lm);
-          if (!on) continue;
+          const T w = shfl_xor_c(v[j], lmask);
+          if (!cok || (((uint32_t)j & lm) != lv)) continue;
           if (o.op == 0) {
             v[j] = w;
           } else if (o.op == 1) {
@@ -199,7 +275,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const typename V2<R>::T* in,
         }
       }
     }
-    T* dp = out + idx0;
+    T* dp = out + ((size_t)ci << 2);
 #pragma unroll
     for (int j = 0; j < 4; ++j) dp[j] = v[j];
   }
@@ -330,17 +406,15 @@ cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const PermOp* d_perm,
-                         int nperm, const LocalOp* d_ops, int nops, cudaStream_t st) {
-  const uint64_t ntiles = 1ull << (n - 7);
+cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepArgs& a,
+                         cudaStream_t st) {
+  const uint32_t ntiles = 1u << (n - 7);
   const int blk = 256;
-  const int grd = grid_for(ntiles * 32, blk);
+  const int grd = grid_for((uint64_t)ntiles * 32, blk);
   if (prec == CSIM_C64)
-    sweep_kernel<float><<<grd, blk, 0, st>>>((const float2*)in, (float2*)out, ntiles, d_perm,
-                                             nperm, d_ops, nops);
+    sweep_kernel<float><<<grd, blk, 0, st>>>((const float2*)in, (float2*)out, ntiles, a);
   else
-    sweep_kernel<double><<<grd, blk, 0, st>>>((const double2*)in, (double2*)out, ntiles, d_perm,
-                                              nperm, d_ops, nops);
+    sweep_kernel<double><<<grd, blk, 0, st>>>((const double2*)in, (double2*)out, ntiles, a);
   return cudaGetLastError();
 }
 

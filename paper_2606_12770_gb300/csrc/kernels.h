@@ -9,25 +9,65 @@
 
 namespace csim {
 
-// One multi-controlled X of a fused permutation, in chunk-index space
-// (state index >> 2; the two lowest qubits never take part).
-struct PermOp {
-  uint64_t mask, val, tbit;
+// Bits [lo, lo+len) of a 32-bit chunk index (state index >> 2) are bits
+// [off, off+len) of a table key.
+struct BitRun {
+  uint8_t lo, len, off, pad;
 };
 
-// One gate acting inside the 128-amplitude warp tile (target qubit 0..6);
-// controls may sit on any qubit.  c, s: RY cos/sin(theta/2), ZPHASE cos/sin(phi).
+constexpr int kMaxRuns = 8;
+
+// A run of multi-controlled X gates compiled to a lookup table over the
+// chunk-index bits they read or write (their support): the table maps the
+// support bits of an index to the support bits of its image.
+struct PermSeg {
+  uint32_t supmask;
+  uint32_t lut_off;  // into the uint16 table array
+  uint32_t nruns;
+  BitRun runs[kMaxRuns];
+};
+
+// One gate inside the 128-amplitude warp tile.  Controls are split into the
+// chunk-index part (state bits >= 2) and state bits 0-1.
+// op: 0 X, 1 H, 2 RY, 3 ZPHASE, 4 multiplexed RY (cm = index of its MuxDesc).
 struct LocalOp {
-  uint64_t cmask, cval;
-  int32_t op, target;
-  double c, s;
+  uint32_t cm, cv;
+  uint8_t lm, lv, op, target;
+  float cf, sf;   // RY cos/sin(theta/2); ZPHASE cos/sin(phi)
+  double cd, sd;  // the same in FP64
+};
+
+// Multiplexed RY on an in-thread qubit: key bits of the chunk index select a
+// bucket of candidate gates; each candidate is checked in full.
+struct MuxDesc {
+  uint32_t nruns;
+  BitRun runs[kMaxRuns];
+  uint32_t tab_off;    // into the (start, count) bucket table
+  uint32_t target;
+};
+struct MuxEntry {
+  uint32_t cm, cv;
+  uint8_t lm, lv, pad0, pad1;
+  float cf, sf;
+  double cd, sd;
+};
+
+struct SweepArgs {
+  const PermSeg* segs;
+  int nseg;
+  const LocalOp* ops;
+  int nops;
+  const uint16_t* lut;
+  const MuxDesc* mux;
+  const uint2* mtab;
+  const MuxEntry* ment;
 };
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,
                         const double* d_val, int64_t count, cudaStream_t st);
 cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaStream_t st);
-cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const PermOp* d_perm,
-                         int nperm, const LocalOp* d_ops, int nops, cudaStream_t st);
+cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepArgs& a,
+                         cudaStream_t st);
 int norm_partials_needed();
 cudaError_t launch_norms(const void* state, int prec, int n, const uint64_t* d_pm,
                          const uint64_t* d_pv, int npat, double* d_partial, double* d_out,

@@ -1,0 +1,86 @@
+"""The fused-program format executed on the host (csim_emulate_fused) against the oracle.
+
+The same fuser output runs on the GPU; these CPU tests check the fuser's
+lookup-table permutations, multiplexed rotations and warp-tile gates."""
+import math
+
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+from oracle import circuit as OC
+from oracle import statevec as S
+from oracle.layout import Layout
+from paper_2606_12770_gb300 import _native as N
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def random_gates(n, count, seed, ops=(0, 1, 2, 3), maxc=4, targets=None):
+    rng = np.random.default_rng(seed)
+    g = []
+    for _ in range(count):
+        op = int(rng.choice(ops))
+        t = int(rng.choice(targets)) if targets is not None else int(rng.integers(n))
+        others = [b for b in range(n) if b != t]
+        nc = int(rng.integers(0, maxc + 1))
+        cs = rng.choice(others, nc, replace=False) if nc else []
+        cm = sum(1 << int(c) for c in cs)
+        cv = sum(int(rng.integers(2)) << int(c) for c in cs)
+        ang = float(rng.uniform(-math.pi, math.pi)) if op in (2, 3) else 0.0
+        g.append((op, t, cm, cv, ang, 0))
+    return g
+
+
+@pytest.mark.parametrize("n,seed", [(7, 1), (9, 2), (12, 3), (15, 4)])
+def test_random_lists(n, seed):
+    g = random_gates(n, 250, seed)
+    psi = I.random_unit_state(n, seed)
+    got, st = N.emulate_fused(g, n, psi)
+    assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-13
+
+
+def test_long_permutation_runs_split_into_tables():
+    """Only multi-controlled X on qubits >= 2: one gather, several lookup tables."""
+    n = 16
+    g = random_gates(n, 300, 7, ops=(0,), maxc=6, targets=list(range(2, 16)))
+    g = [x for x in g if x[2] & 3 == 0]
+    psi = I.random_unit_state(n, 7)
+    got, st = N.emulate_fused(g, n, psi)
+    assert st["passes"] == 1 and st["segments"] > 1 and st["max_support"] <= 13
+    assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-14
+
+
+@pytest.mark.parametrize("target", [0, 1])
+def test_multiplexed_rotations(target):
+    """Runs of RY on an in-thread qubit, controls anywhere (incl. the other low qubit)."""
+    n = 14
+    g = random_gates(n, 200, 11 + target, ops=(2,), maxc=7, targets=[target])
+    psi = I.random_unit_state(n, 3)
+    got, st = N.emulate_fused(g, n, psi)
+    assert st["mux"] == 1 and st["mux_gates"] == 200
+    assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-13
+
+
+def test_microbench_stream():
+    n = 16
+    g = I.microbench_gates(n, 400, 1)
+    psi = I.random_unit_state(n, 1)
+    got, _ = N.emulate_fused(g, n, psi)
+    assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-13
+
+
+@pytest.mark.parametrize("cfg,d", [((4, 0.8, 2, 2, 0.1, 2), 3), ((8, 0.7, 1, 3, 0.2, 3), 5)])
+def test_qsvt_circuit_one_sweep_per_call(cfg, d):
+    lay = Layout(cfg[0], cfg[2], cfg[3], cfg[5])
+    f0, _ = I.lbm_instance(cfg[0], 0, tau=cfg[1])
+    gates = OC.build_qsvt(*cfg, list(I.random_phases(d, 5)))
+    psi = np.zeros(1 << lay.n, dtype=complex)
+    init, _ = OC.initial_state(lay, f0)
+    for k, v in init.items():
+        psi[k] = v
+    got, st = N.emulate_fused(gates, lay.n, psi)
+    assert st["passes"] == d + 1 and st["single"] == 0
+    assert rel(got, S.DenseSim(lay.n).run(psi.copy(), gates)) < 1e-13
