@@ -185,10 +185,10 @@ csim_status csim_sv_free(csim_sv* sv);
  * sweeps (lookup-table permutations, multiplexed rotations, warp-tile gates)
  * on the host in FP64 with the kernel's semantics.  amps: 2^n interleaved
  * complex values, updated in place.  For testing the fuser without a GPU;
- * n must be in [7, 24].  If stats is non-NULL it receives 12 counters: sweeps,
+ * n must be in [7, 24].  If stats is non-NULL it receives 13 counters: sweeps,
  * single-gate steps, permutation gates, lookup tables, local gates,
  * multiplexers, multiplexed gates, multiplexer entries, largest bucket,
- * table entries, largest table support, HBM passes. */
+ * table entries, largest table support, HBM passes, averaging blocks. */
 csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n, double* amps,
                                int64_t* stats);
 

@@ -270,7 +270,8 @@ class StateVector:
 
 
 FUSE_STAT_NAMES = ["sweeps", "single", "perm_gates", "segments", "local_gates", "mux",
-                   "mux_gates", "mux_entries", "max_bucket", "lut_entries", "max_support", "passes"]
+                   "mux_gates", "mux_entries", "max_bucket", "lut_entries", "max_support", "passes",
+                   "reflect"]
 
 
 def emulate_fused(gates, n, amps):
@@ -278,7 +279,7 @@ def emulate_fused(gates, n, amps):
     lib = load()
     g = gates_to_records(gates)
     a = np.ascontiguousarray(amps, dtype=np.complex128).copy()
-    st = np.zeros(12, dtype=np.int64)
+    st = np.zeros(13, dtype=np.int64)
     _check(lib.csim_emulate_fused(g.ctypes.data_as(C.c_void_p), g.shape[0], int(n),
                                   _dp(a.view(np.float64)), st.ctypes.data_as(C.POINTER(C.c_int64))))
     return a, dict(zip(FUSE_STAT_NAMES, (int(x) for x in st)))

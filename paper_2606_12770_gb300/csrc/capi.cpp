@@ -599,9 +599,9 @@ csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n
   std::memcpy(amps, st.data(), 2 * N * sizeof(double));
   if (stats) {
     const csim::FuseStats& f = p.stats;
-    const int64_t v[12] = {f.sweeps,     f.single,      f.perm_gates, f.segments,
-                           f.local_gates, f.mux,        f.mux_gates,  f.mux_entries,
-                           f.max_bucket, f.lut_entries, f.max_support, p.passes};
+    const int64_t v[13] = {f.sweeps,      f.single,      f.perm_gates,  f.segments, f.local_gates,
+                           f.mux,         f.mux_gates,   f.mux_entries, f.max_bucket,
+                           f.lut_entries, f.max_support, p.passes,      f.reflect};
     std::memcpy(stats, v, sizeof(v));
   }
   return CSIM_OK;

@@ -17,8 +17,11 @@
 // single-gate step.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstdlib>
+
+#include <cstring>
 
 #include "fuse.h"
 
@@ -26,7 +29,7 @@ namespace csim {
 
 namespace {
 
-constexpr int kMaxSupport = 13;   // bits per permutation lookup table
+constexpr int kMaxSupport = 14;   // bits per permutation lookup table
 constexpr int kMuxKeyBits = 11;   // bits of the multiplexer bucket key
 constexpr int kMuxMinGates = 4;   // shorter RY runs stay individual gates
 
@@ -200,11 +203,111 @@ void compile_mux(const std::vector<csim_gate>& grp, Program* p) {
   p->stats.mux_entries = (int64_t)p->ment.size();
 }
 
+using cplx = std::complex<double>;
+
+bool in_tile(const csim_gate& g) { return g.target <= 6 && (g.cmask >> 7) == 0; }
+
+// Dense 128 x 128 matrix (column-major per input basis state) of a window of
+// tile-only gates.
+std::vector<cplx> tile_matrix(const std::vector<csim_gate>& run, size_t i, size_t j) {
+  std::vector<cplx> U(128 * 128, 0.0);
+  const double h = 0.70710678118654752440;
+  for (int col = 0; col < 128; ++col) {
+    cplx* v = &U[(size_t)col * 128];
+    v[col] = 1.0;
+    for (size_t k = i; k < j; ++k) {
+      const csim_gate& g = run[k];
+      const int tb = 1 << g.target;
+      const double c2 = std::cos(g.angle / 2), s2 = std::sin(g.angle / 2);
+      const cplx ph(std::cos(g.angle), std::sin(g.angle));
+      for (int x = 0; x < 128; ++x) {
+        if ((x & tb) || ((uint64_t)x & g.cmask) != g.cval) continue;
+        cplx a0 = v[x], a1 = v[x | tb];
+        switch (g.op) {
+          case OP_X: v[x] = a1; v[x | tb] = a0; break;
+          case OP_H: v[x] = (a0 + a1) * h; v[x | tb] = (a0 - a1) * h; break;
+          case OP_RY: v[x] = c2 * a0 - s2 * a1; v[x | tb] = s2 * a0 + c2 * a1; break;
+          default: v[x] = a0 * ph; v[x | tb] = a1 * std::conj(ph); break;
+        }
+      }
+    }
+  }
+  return U;
+}
+
+// If the window's matrix is I (x) A + J (x) B over the lane bits in lanes
+// (a 5-bit mask of lane-index bits), fill the descriptor and return true.
+bool reflect_form(const std::vector<cplx>& U, uint32_t lanes, ReflectDesc* d) {
+  auto at = [&](int row, int col) { return U[(size_t)col * 128 + row]; };
+  const int cls = 1 << __builtin_popcount(lanes);
+  int l1 = 0;
+  for (int b = 0; b < 5; ++b)
+    if ((lanes >> b) & 1u) { l1 = 1 << b; break; }
+  cplx A[4][4], B[4][4];
+  for (int y = 0; y < 4; ++y)
+    for (int yp = 0; yp < 4; ++yp) {
+      B[y][yp] = at((0 << 2) | y, (l1 << 2) | yp) * (double)cls;
+      A[y][yp] = at(y, yp) - B[y][yp] / (double)cls;
+    }
+  for (int l = 0; l < 32; ++l)
+    for (int lp = 0; lp < 32; ++lp) {
+      const bool same_class = ((l ^ lp) & ~lanes & 31) == 0;
+      for (int y = 0; y < 4; ++y)
+        for (int yp = 0; yp < 4; ++yp) {
+          cplx model = (l == lp ? A[y][yp] : 0.0) + (same_class ? B[y][yp] / (double)cls : 0.0);
+          if (std::abs(at((l << 2) | y, (lp << 2) | yp) - model) > 1e-12) return false;
+        }
+    }
+  std::memset(d, 0, sizeof(*d));
+  d->lanemask = lanes;
+  for (int y = 0; y < 4; ++y)
+    for (int yp = 0; yp < 4; ++yp) {
+      const int q = y * 4 + yp;
+      const cplx av = A[y][yp], bv = B[y][yp] / (double)cls;
+      d->ad[q] = make_double2(av.real(), av.imag());
+      d->af[q] = make_float2((float)av.real(), (float)av.imag());
+      d->bd[q] = make_double2(bv.real(), bv.imag());
+      d->bf[q] = make_float2((float)bv.real(), (float)bv.imag());
+      if (std::abs(av) > 1e-15) d->nzA |= 1u << q;
+      if (std::abs(bv) > 1e-15) d->nzB |= 1u << q;
+    }
+  return true;
+}
+
+// Longest window starting at i (an H on a lane bit) with the averaging form.
+size_t try_reflect(const std::vector<csim_gate>& run, size_t i, Program* p) {
+  const csim_gate& g0 = run[i];
+  if (!(g0.op == OP_H && g0.target >= 2 && g0.cmask == 0)) return 0;
+  size_t end = i;
+  while (end < run.size() && in_tile(run[end])) ++end;
+  for (size_t j = end; j > i + 1; --j) {
+    const csim_gate& gl = run[j - 1];
+    if (!(gl.op == OP_H && gl.target >= 2 && gl.cmask == 0)) continue;
+    uint32_t lanes = 0;
+    for (size_t k = i; k < j; ++k)
+      if (run[k].op == OP_H && run[k].target >= 2) lanes |= 1u << (run[k].target - 2);
+    ReflectDesc d;
+    if (!reflect_form(tile_matrix(run, i, j), lanes, &d)) continue;
+    LocalOp mo{};
+    mo.op = 5;
+    mo.cm = (uint32_t)p->refl.size();
+    p->refl.push_back(d);
+    p->ops.push_back(mo);
+    p->stats.reflect++;
+    return j - i;
+  }
+  return 0;
+}
+
 void compile_local(const std::vector<csim_gate>& run, Program* p, Step* st) {
   st->op_off = (int)p->ops.size();
   size_t i = 0;
   while (i < run.size()) {
     const csim_gate& g = run[i];
+    if (const size_t w = try_reflect(run, i, p)) {
+      i += w;
+      continue;
+    }
     if (g.op == OP_RY && g.target < 2) {
       size_t j = i;
       while (j < run.size() && run[j].op == OP_RY && run[j].target == g.target) ++j;
@@ -285,11 +388,11 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
     std::fprintf(stderr,
                  "[csim fuse] n=%d sweeps=%lld single=%lld perm_gates=%lld segments=%lld "
                  "max_support=%lld lut=%lld local=%lld mux=%lld mux_gates=%lld entries=%lld "
-                 "max_bucket=%lld\n",
+                 "max_bucket=%lld reflect=%lld\n",
                  n, (long long)f.sweeps, (long long)f.single, (long long)f.perm_gates,
                  (long long)f.segments, (long long)f.max_support, (long long)f.lut_entries,
                  (long long)f.local_gates, (long long)f.mux, (long long)f.mux_gates,
-                 (long long)f.mux_entries, (long long)f.max_bucket);
+                 (long long)f.mux_entries, (long long)f.max_bucket, (long long)f.reflect);
   }
 }
 
@@ -311,6 +414,7 @@ cudaError_t upload_program(Program* p, cudaStream_t st) {
   if (e == cudaSuccess) e = up(&p->d_mux, p->mux, st);
   if (e == cudaSuccess) e = up(&p->d_mtab, p->mtab, st);
   if (e == cudaSuccess) e = up(&p->d_ment, p->ment, st);
+  if (e == cudaSuccess) e = up(&p->d_refl, p->refl, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     free_program(p);
@@ -321,7 +425,7 @@ cudaError_t upload_program(Program* p, cudaStream_t st) {
 }
 
 void free_program(Program* p) {
-  void* ptrs[] = {p->d_segs, p->d_lut, p->d_ops, p->d_mux, p->d_mtab, p->d_ment};
+  void* ptrs[] = {p->d_segs, p->d_lut, p->d_ops, p->d_mux, p->d_mtab, p->d_ment, p->d_refl};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->d_segs = nullptr;
@@ -330,6 +434,7 @@ void free_program(Program* p) {
   p->d_mux = nullptr;
   p->d_mtab = nullptr;
   p->d_ment = nullptr;
+  p->d_refl = nullptr;
   p->uploaded = false;
 }
 
@@ -348,6 +453,7 @@ cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cuda
       a.mux = p.d_mux;
       a.mtab = p.d_mtab;
       a.ment = p.d_ment;
+      a.refl = p.d_refl;
       if (s.nseg == 0) {
         e = launch_sweep(buf[*cur], buf[*cur], prec, p.n, a, st);
       } else {
@@ -433,6 +539,39 @@ void emulate_program(const Program& p, std::vector<double>* amps) {
                 if (((uint32_t)j0 & E.lm) != E.lv) continue;
                 pair(v[lane][j0], v[lane][j0 | (1 << md.target)], 2, E.cd, E.sd);
               }
+            }
+          }
+          continue;
+        }
+        if (o.op == 5) {
+          const ReflectDesc& rd = p.refl[o.cm];
+          double S[32][4][2];
+          for (uint32_t lane = 0; lane < 32; ++lane)
+            for (int y = 0; y < 4; ++y) {
+              S[lane][y][0] = S[lane][y][1] = 0.0;
+              for (uint32_t l2 = 0; l2 < 32; ++l2)
+                if (((lane ^ l2) & ~rd.lanemask & 31u) == 0) {
+                  S[lane][y][0] += v[l2][y][0];
+                  S[lane][y][1] += v[l2][y][1];
+                }
+            }
+          for (uint32_t lane = 0; lane < 32; ++lane) {
+            double o4[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+            for (int y = 0; y < 4; ++y)
+              for (int yp = 0; yp < 4; ++yp) {
+                const int q = y * 4 + yp;
+                if ((rd.nzA >> q) & 1u) {
+                  o4[y][0] += rd.ad[q].x * v[lane][yp][0] - rd.ad[q].y * v[lane][yp][1];
+                  o4[y][1] += rd.ad[q].x * v[lane][yp][1] + rd.ad[q].y * v[lane][yp][0];
+                }
+                if ((rd.nzB >> q) & 1u) {
+                  o4[y][0] += rd.bd[q].x * S[lane][yp][0] - rd.bd[q].y * S[lane][yp][1];
+                  o4[y][1] += rd.bd[q].x * S[lane][yp][1] + rd.bd[q].y * S[lane][yp][0];
+                }
+              }
+            for (int y = 0; y < 4; ++y) {
+              v[lane][y][0] = o4[y][0];
+              v[lane][y][1] = o4[y][1];
             }
           }
           continue;

@@ -20,6 +20,7 @@ struct Step {
 struct FuseStats {
   int64_t sweeps = 0, single = 0, perm_gates = 0, segments = 0, local_gates = 0, mux = 0;
   int64_t mux_gates = 0, mux_entries = 0, max_bucket = 0, lut_entries = 0, max_support = 0;
+  int64_t reflect = 0;
 };
 
 struct Program {
@@ -32,6 +33,7 @@ struct Program {
   std::vector<MuxDesc> mux;
   std::vector<uint2> mtab;
   std::vector<MuxEntry> ment;
+  std::vector<ReflectDesc> refl;
   // device copies
   PermSeg* d_segs = nullptr;
   uint16_t* d_lut = nullptr;
@@ -39,6 +41,7 @@ struct Program {
   MuxDesc* d_mux = nullptr;
   uint2* d_mtab = nullptr;
   MuxEntry* d_ment = nullptr;
+  ReflectDesc* d_refl = nullptr;
   int64_t passes = 0;        // HBM passes per execution
   double amp_updates = 0.0;  // sum over elementary gates of amplitudes changed
   bool pingpong = false;     // some step gathers out of place

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 
 #include "kernels.h"
 
@@ -189,95 +191,181 @@ __device__ __forceinline__ void rot(T& a, T& b, R c, R s) {
   a = na;
 }
 
-// One fused sweep.  Each lane owns one 4-amplitude chunk of the destination
-// tile: it computes the source chunk by running the permutation segments
-// (the inverse permutation, i.e. the gates in reverse order), loads it, then
-// applies the tile-local gates in order.
 template <typename R>
-__global__ void __launch_bounds__(256) sweep_kernel(const typename V2<R>::T* in,
+struct CplxOf;
+template <>
+struct CplxOf<float> {
+  static __device__ __forceinline__ float2 a(const ReflectDesc& d, int k) { return d.af[k]; }
+  static __device__ __forceinline__ float2 b(const ReflectDesc& d, int k) { return d.bf[k]; }
+};
+template <>
+struct CplxOf<double> {
+  static __device__ __forceinline__ double2 a(const ReflectDesc& d, int k) { return d.ad[k]; }
+  static __device__ __forceinline__ double2 b(const ReflectDesc& d, int k) { return d.bd[k]; }
+};
+
+// One fused sweep.  Each lane owns one 4-amplitude chunk of U destination
+// tiles: it computes the source chunk by running the permutation segments
+// (the inverse permutation, i.e. the gates in reverse order), loads it, then
+// applies the tile-local gates in order.  Descriptors are read once per
+// group of U tiles.
+template <typename R, int U, int MINB>
+__global__ void __launch_bounds__(256, MINB) sweep_kernel(const typename V2<R>::T* in,
                                                     typename V2<R>::T* out, uint32_t ntiles,
                                                     SweepArgs a) {
   using T = typename V2<R>::T;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t tile = warp; tile < ntiles; tile += nwarps) {
-    const uint32_t ci = (tile << 5) | lane;  // chunk index = state index >> 2
-    uint32_t src = ci;
+  for (uint32_t t0 = warp * U; t0 < ntiles; t0 += nwarps * U) {
+    uint32_t ci[U], src[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) src[u] = ci[u] = ((t0 + u) << 5) | lane;
     for (int k = 0; k < a.nseg; ++k) {
       const PermSeg& g = a.segs[k];
-      const uint32_t key = gather_key(src, g.runs, g.nruns);
-      const uint32_t v = __ldg(a.lut + g.lut_off + key);
-      src = scatter_key(src, v, g.supmask, g.runs, g.nruns);
-    }
-    T v[4];
-    const T* sp = in + ((size_t)src << 2);
+      const uint32_t nr = g.nruns, sup = g.supmask, off = g.lut_off;
+      BitRun rr[kMaxRuns];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = sp[j];
+      for (int r = 0; r < kMaxRuns; ++r)
+        if (r < (int)nr) rr[r] = g.runs[r];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t key = gather_key(src[u], rr, nr);
+        const uint32_t v = __ldg(a.lut + off + key);
+        src[u] = scatter_key(src[u], v, sup, rr, nr);
+      }
+    }
+    T v[U][4];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const T* sp = in + ((size_t)src[u] << 2);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[u][j] = sp[j];
+    }
     for (int k = 0; k < a.nops; ++k) {
       const LocalOp& o = a.ops[k];
-      const bool cok = (ci & o.cm) == o.cv;
-      const uint32_t lm = o.lm, lv = o.lv;
-      if (o.op == 4) {  // multiplexed RY on bit o.target
-        const MuxDesc& md = a.mux[o.cm];
-        const uint32_t key = gather_key(ci, md.runs, md.nruns);
-        const uint2 bk = __ldg(a.mtab + md.tab_off + key);
-        for (uint32_t e = bk.x; e < bk.x + bk.y; ++e) {
-          const MuxEntry& E = a.ment[e];
-          if ((ci & E.cm) != E.cv) continue;
-          const R c = Coef<R>::c(E), s = Coef<R>::s(E);
-          if (md.target == 0) {
-            if ((0u & E.lm) == E.lv) rot<T, R>(v[0], v[1], c, s);
-            if ((2u & E.lm) == E.lv) rot<T, R>(v[2], v[3], c, s);
-          } else {
-            if ((0u & E.lm) == E.lv) rot<T, R>(v[0], v[2], c, s);
-            if ((1u & E.lm) == E.lv) rot<T, R>(v[1], v[3], c, s);
+      const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv, op = o.op, tg = o.target;
+      if (op == 4) {  // multiplexed RY on bit tg
+        const MuxDesc& md = a.mux[ocm];
+        const uint32_t nr = md.nruns, toff = md.tab_off;
+        BitRun rr[kMaxRuns];
+#pragma unroll
+        for (int r = 0; r < kMaxRuns; ++r)
+          if (r < (int)nr) rr[r] = md.runs[r];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t key = gather_key(ci[u], rr, nr);
+          const uint2 bk = __ldg(a.mtab + toff + key);
+          for (uint32_t e = bk.x; e < bk.x + bk.y; ++e) {
+            const MuxEntry& E = a.ment[e];
+            if ((ci[u] & E.cm) != E.cv) continue;
+            const R c = Coef<R>::c(E), s = Coef<R>::s(E);
+            const uint32_t elm = E.lm, elv = E.lv;
+            if (tg == 0) {
+              if ((0u & elm) == elv) rot<T, R>(v[u][0], v[u][1], c, s);
+              if ((2u & elm) == elv) rot<T, R>(v[u][2], v[u][3], c, s);
+            } else {
+              if ((0u & elm) == elv) rot<T, R>(v[u][0], v[u][2], c, s);
+              if ((1u & elm) == elv) rot<T, R>(v[u][1], v[u][3], c, s);
+            }
           }
         }
         continue;
       }
-      const R c = Coef<R>::c(o), s = Coef<R>::s(o);
-      if (o.target < 2) {
-        if (!cok) continue;
-        if (o.target == 0) {
-          if ((0u & lm) == lv) apply_pair<R>(v[0], v[1], o.op, c, s);
-          if ((2u & lm) == lv) apply_pair<R>(v[2], v[3], o.op, c, s);
-        } else {
-          if ((0u & lm) == lv) apply_pair<R>(v[0], v[2], o.op, c, s);
-          if ((1u & lm) == lv) apply_pair<R>(v[1], v[3], o.op, c, s);
+      if (op == 5) {  // I (x) A + J (x) B over the lane bits of lanemask
+        const ReflectDesc& rd = a.refl[ocm];
+        const uint32_t lmask = rd.lanemask, nzA = rd.nzA, nzB = rd.nzB;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          T S[4];
+#pragma unroll
+          for (int y = 0; y < 4; ++y) S[y] = v[u][y];
+#pragma unroll
+          for (int b = 0; b < 5; ++b) {
+            if (!((lmask >> b) & 1u)) continue;
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+              const T w = shfl_xor_c(S[y], 1 << b);
+              S[y].x += w.x;
+              S[y].y += w.y;
+            }
+          }
+          T o4[4];
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            o4[y] = mk<T>((R)0, (R)0);
+#pragma unroll
+            for (int yp = 0; yp < 4; ++yp) {
+              const int q = y * 4 + yp;
+              if ((nzA >> q) & 1u) {
+                const T c = CplxOf<R>::a(rd, q);
+                o4[y].x += c.x * v[u][yp].x - c.y * v[u][yp].y;
+                o4[y].y += c.x * v[u][yp].y + c.y * v[u][yp].x;
+              }
+              if ((nzB >> q) & 1u) {
+                const T c = CplxOf<R>::b(rd, q);
+                o4[y].x += c.x * S[yp].x - c.y * S[yp].y;
+                o4[y].y += c.x * S[yp].y + c.y * S[yp].x;
+              }
+            }
+          }
+#pragma unroll
+          for (int y = 0; y < 4; ++y) v[u][y] = o4[y];
         }
-      } else {
-        const int lmask = 1 << (o.target - 2);
-        const bool hi = (lane & (uint32_t)lmask) != 0;
-        const R h = (R)0.70710678118654752440;
-        if (o.op == 3) {  // diagonal: no partner needed
+        continue;
+      }
+      const R c = Coef<R>::c(o), s = Coef<R>::s(o);
+      if (tg < 2) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if ((ci[u] & ocm) != ocv) continue;
+          if (tg == 0) {
+            if ((0u & lm) == lv) apply_pair<R>(v[u][0], v[u][1], op, c, s);
+            if ((2u & lm) == lv) apply_pair<R>(v[u][2], v[u][3], op, c, s);
+          } else {
+            if ((0u & lm) == lv) apply_pair<R>(v[u][0], v[u][2], op, c, s);
+            if ((1u & lm) == lv) apply_pair<R>(v[u][1], v[u][3], op, c, s);
+          }
+        }
+        continue;
+      }
+      const int lmask = 1 << (tg - 2);
+      const bool hi = (lane & (uint32_t)lmask) != 0;
+      const R h = (R)0.70710678118654752440;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool cok = (ci[u] & ocm) == ocv;
+        if (op == 3) {  // diagonal: no partner needed
           if (!cok) continue;
           const R sg = hi ? -s : s;
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             if (((uint32_t)j & lm) == lv)
-              v[j] = mk<T>(v[j].x * c - v[j].y * sg, v[j].x * sg + v[j].y * c);
+              v[u][j] = mk<T>(v[u][j].x * c - v[u][j].y * sg, v[u][j].x * sg + v[u][j].y * c);
           continue;
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const T w = shfl_xor_c(v[j], lmask);
+          const T w = shfl_xor_c(v[u][j], lmask);
           if (!cok || (((uint32_t)j & lm) != lv)) continue;
-          if (o.op == 0) {
-            v[j] = w;
-          } else if (o.op == 1) {
-            v[j] = hi ? mk<T>((w.x - v[j].x) * h, (w.y - v[j].y) * h)
-                      : mk<T>((v[j].x + w.x) * h, (v[j].y + w.y) * h);
+          if (op == 0) {
+            v[u][j] = w;
+          } else if (op == 1) {
+            v[u][j] = hi ? mk<T>((w.x - v[u][j].x) * h, (w.y - v[u][j].y) * h)
+                         : mk<T>((v[u][j].x + w.x) * h, (v[u][j].y + w.y) * h);
           } else {
-            v[j] = hi ? mk<T>(s * w.x + c * v[j].x, s * w.y + c * v[j].y)
-                      : mk<T>(c * v[j].x - s * w.x, c * v[j].y - s * w.y);
+            v[u][j] = hi ? mk<T>(s * w.x + c * v[u][j].x, s * w.y + c * v[u][j].y)
+                         : mk<T>(c * v[u][j].x - s * w.x, c * v[u][j].y - s * w.y);
           }
         }
       }
     }
-    T* dp = out + ((size_t)ci << 2);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) dp[j] = v[j];
+    for (int u = 0; u < U; ++u) {
+      T* dp = out + ((size_t)ci[u] << 2);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) dp[j] = v[u][j];
+    }
   }
 }
 
@@ -406,15 +494,62 @@ cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaSt
   return cudaGetLastError();
 }
 
+namespace {
+
+// Tiles per warp iteration (U) and minimum resident blocks per SM (MINB) of
+// the sweep kernel; CSIM_SWEEP_CFG="U,MINB" overrides the defaults.
+struct SweepCfg {
+  int u64, u128, minb;
+};
+
+SweepCfg sweep_cfg() {
+  static SweepCfg cfg = [] {
+    SweepCfg c{4, 2, 1};
+    if (const char* e = std::getenv("CSIM_SWEEP_CFG")) {
+      int u = 0, m = 0;
+      if (std::sscanf(e, "%d,%d", &u, &m) == 2 && (u == 1 || u == 2 || u == 4) && (m == 1 || m == 2)) {
+        c.u64 = u;
+        c.u128 = u;
+        c.minb = m;
+      }
+    }
+    return c;
+  }();
+  return cfg;
+}
+
+template <typename R, int U, int MINB>
+void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepArgs& a, cudaStream_t st) {
+  using T = typename V2<R>::T;
+  const int blk = 256;
+  const int grd = grid_for((uint64_t)ntiles / U * 32, blk);
+  sweep_kernel<R, U, MINB><<<grd, blk, 0, st>>>((const T*)in, (T*)out, ntiles, a);
+}
+
+template <typename R>
+void launch_sweep_r(const void* in, void* out, uint32_t ntiles, int u, int minb, const SweepArgs& a,
+                    cudaStream_t st) {
+  while ((uint32_t)u > ntiles) u >>= 1;
+  if (minb == 2) {
+    if (u == 4) return launch_sweep_t<R, 4, 2>(in, out, ntiles, a, st);
+    if (u == 2) return launch_sweep_t<R, 2, 2>(in, out, ntiles, a, st);
+    return launch_sweep_t<R, 1, 2>(in, out, ntiles, a, st);
+  }
+  if (u == 4) return launch_sweep_t<R, 4, 1>(in, out, ntiles, a, st);
+  if (u == 2) return launch_sweep_t<R, 2, 1>(in, out, ntiles, a, st);
+  return launch_sweep_t<R, 1, 1>(in, out, ntiles, a, st);
+}
+
+}  // namespace
+
 cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepArgs& a,
                          cudaStream_t st) {
   const uint32_t ntiles = 1u << (n - 7);
-  const int blk = 256;
-  const int grd = grid_for((uint64_t)ntiles * 32, blk);
+  const SweepCfg c = sweep_cfg();
   if (prec == CSIM_C64)
-    sweep_kernel<float><<<grd, blk, 0, st>>>((const float2*)in, (float2*)out, ntiles, a);
+    launch_sweep_r<float>(in, out, ntiles, c.u64, c.minb, a, st);
   else
-    sweep_kernel<double><<<grd, blk, 0, st>>>((const double2*)in, (double2*)out, ntiles, a);
+    launch_sweep_r<double>(in, out, ntiles, c.u128, c.minb, a, st);
   return cudaGetLastError();
 }
 

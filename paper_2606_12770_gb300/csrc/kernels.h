@@ -29,7 +29,8 @@ struct PermSeg {
 
 // One gate inside the 128-amplitude warp tile.  Controls are split into the
 // chunk-index part (state bits >= 2) and state bits 0-1.
-// op: 0 X, 1 H, 2 RY, 3 ZPHASE, 4 multiplexed RY (cm = index of its MuxDesc).
+// op: 0 X, 1 H, 2 RY, 3 ZPHASE, 4 multiplexed RY (cm = index of its MuxDesc),
+// 5 averaging block (cm = index of its ReflectDesc).
 struct LocalOp {
   uint32_t cm, cv;
   uint8_t lm, lv, op, target;
@@ -52,6 +53,19 @@ struct MuxEntry {
   double cd, sd;
 };
 
+// A window of tile-local gates whose 128 x 128 matrix is I (x) A + J (x) B on
+// (lane bits) x (bits 0-1), J the summing matrix over the lane bits in
+// `lanemask`: out[l][y] = sum_y' A[y][y'] v[l][y'] + B[y][y'] sum_l'(v[l'][y']),
+// the sum running over the lanes that differ from l only in `lanemask` bits.
+// A and B are dense 4 x 4 (index y*4+y'); nzA / nzB flag the non-zero entries.
+struct ReflectDesc {
+  uint32_t lanemask;
+  uint32_t nzA, nzB;
+  uint32_t pad;
+  float2 af[16], bf[16];
+  double2 ad[16], bd[16];
+};
+
 struct SweepArgs {
   const PermSeg* segs;
   int nseg;
@@ -61,6 +75,7 @@ struct SweepArgs {
   const MuxDesc* mux;
   const uint2* mtab;
   const MuxEntry* ment;
+  const ReflectDesc* refl;
 };
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,

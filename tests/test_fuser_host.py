@@ -44,12 +44,12 @@ def test_random_lists(n, seed):
 
 def test_long_permutation_runs_split_into_tables():
     """Only multi-controlled X on qubits >= 2: one gather, several lookup tables."""
-    n = 16
-    g = random_gates(n, 300, 7, ops=(0,), maxc=6, targets=list(range(2, 16)))
+    n = 20
+    g = random_gates(n, 300, 7, ops=(0,), maxc=6, targets=list(range(2, 20)))
     g = [x for x in g if x[2] & 3 == 0]
     psi = I.random_unit_state(n, 7)
     got, st = N.emulate_fused(g, n, psi)
-    assert st["passes"] == 1 and st["segments"] > 1 and st["max_support"] <= 13
+    assert st["passes"] == 1 and st["segments"] > 1 and st["max_support"] <= 14
     assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-14
 
 
@@ -83,4 +83,21 @@ def test_qsvt_circuit_one_sweep_per_call(cfg, d):
         psi[k] = v
     got, st = N.emulate_fused(gates, lay.n, psi)
     assert st["passes"] == d + 1 and st["single"] == 0
+    if cfg[2] == 2:  # five label qubits = all lane bits: projector phases become averaging blocks
+        assert st["reflect"] == d - 1  # every phase between two oracle calls
     assert rel(got, S.DenseSim(lay.n).run(psi.copy(), gates)) < 1e-13
+
+
+def test_averaging_block_detection_general():
+    """H layer on lane bits, tile-internal diagonal/controlled gates, H layer: one block."""
+    n = 12
+    lanes = [2, 3, 4, 5, 6]
+    g = [(1, b, 0, 0, 0.0, 0) for b in lanes]
+    anc = sum(1 << b for b in lanes) | 1
+    g += [(0, 0, 0, 0, 0.0, 0), (0, 1, anc, 0, 0.0, 0), (3, 1, 0, 0, 0.37, 0), (0, 1, anc, 0, 0.0, 0),
+          (0, 0, 0, 0, 0.0, 0)]
+    g += [(1, b, 0, 0, 0.0, 0) for b in lanes]
+    psi = I.random_unit_state(n, 4)
+    got, st = N.emulate_fused(g, n, psi)
+    assert st["reflect"] == 1
+    assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-13

@@ -243,3 +243,43 @@ def test_state_machine_errors():
     assert 0.0 < p < 1.0 and abs(tot - 1.0) < 1e-5
     with pytest.raises(G.CsimError):
         c.init(np.full((4, 3), np.nan), G.CSIM_C64)
+
+
+VARIANT_SCRIPT = r'''
+import sys, numpy as np
+sys.path.insert(0, sys.argv[1])
+import lbm_inputs as I, paper_2606_12770_gb300 as G
+from oracle import statevec as S, circuit as OC
+from oracle.layout import Layout
+cfg = (4, 0.8, 2, 2, 0.1, 2)
+lay = Layout(4, 2, 2, 2)
+f0, _ = I.lbm_instance(4, 0, tau=0.8)
+ph = I.random_phases(5, 2)
+gates = OC.build_qsvt(*cfg, list(ph))
+psi = np.zeros(1 << lay.n, dtype=complex)
+init, _ = OC.initial_state(lay, f0)
+for k, v in init.items():
+    psi[k] = v
+ref = S.DenseSim(lay.n).run(psi.copy(), gates)
+for prec, tol in ((G.CSIM_C128, 1e-12), (G.CSIM_C64, 1e-5)):
+    sv = G.StateVector(lay.n, prec)
+    sv.load(psi)
+    sv.compile(gates, G.CSIM_EXEC_FUSED)
+    sv.run(1)
+    err = np.linalg.norm(sv.read() - ref) / np.linalg.norm(ref)
+    assert err < tol, (prec, err)
+print("ok")
+'''
+
+
+@pytest.mark.parametrize("cfg", ["1,1", "2,1", "4,1", "1,2", "2,2", "4,2"])
+def test_sweep_kernel_variants(cfg):
+    """Every compiled sweep-kernel variant (tiles per iteration, blocks per SM)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CSIM_SWEEP_CFG=cfg)
+    r = subprocess.run([sys.executable, "-c", VARIANT_SCRIPT, root], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
