@@ -1,26 +1,27 @@
 // The fuser: groups consecutive elementary gates into sweeps, each one HBM pass.
 //
-// A sweep is  [permutation]  then  [tile-local gates]:
+// A sweep combines a permutation and tile-local gates:
 //  * permutation: a maximal run of multi-controlled X gates whose target is a
 //    qubit >= 2 and whose controls avoid qubits 0-1.  Such a run maps every
-//    4-amplitude chunk (qubits 0-1) to another chunk, so the kernel gathers
-//    each destination chunk from the chunk obtained by applying the run's
-//    gates in reverse order to the destination.  The reversed run is cut into
-//    segments whose support (bits read or written) has at most kMaxSupport
-//    bits; each segment becomes a lookup table over its support.
+//    4-amplitude chunk (qubits 0-1) to another chunk.  The run is cut into
+//    segments whose support (chunk-index bits read or written) has at most
+//    kMaxSupport bits; each segment becomes a lookup table over its support.
 //  * tile-local gates: any gate whose target is one of the 7 lowest qubits
 //    (the 128-amplitude warp tile); controls may sit anywhere.  Runs of RY
-//    gates on the same in-thread qubit (0 or 1) commute and become one
-//    multiplexed rotation: a few chunk-index bits select a bucket of
-//    candidate gates, each checked in full.
-// A gate fitting neither class (e.g. H on a high qubit) becomes its own
-// single-gate step.
+//    gates on the same in-thread qubit (0 or 1) commute and become
+//    multiplexed rotations (a few chunk-index bits select a bucket of
+//    candidate gates, each checked in full).  A window of gates acting only
+//    inside the tile whose 128 x 128 matrix is I (x) A + J (x) B over lane
+//    bits becomes one averaging block (a warp reduction).
+// Gather form: [permutation as a gather][tile gates].  Scatter form: [tile
+// gates][permutation as a scatter].  A gate fitting neither class (e.g. H on
+// a high qubit) becomes its own single-gate step.  Sweeps whose descriptors
+// exceed the kernel parameter block are split.
 #include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
 #include <cstdlib>
-
 #include <cstring>
 
 #include "fuse.h"
@@ -30,7 +31,7 @@ namespace csim {
 namespace {
 
 constexpr int kMaxSupport = 14;   // bits per permutation lookup table
-constexpr int kMuxKeyBits = 11;   // bits of the multiplexer bucket key
+constexpr int kMuxKeyBits = 12;   // bits of the multiplexer bucket key
 constexpr int kMuxMinGates = 4;   // shorter RY runs stay individual gates
 
 bool perm_eligible(const csim_gate& g) {
@@ -60,14 +61,16 @@ std::vector<BitRun> runs_of(uint32_t mask) {
   return runs;
 }
 
-uint32_t deposit(uint32_t key, const std::vector<BitRun>& runs) {
+uint32_t deposit(uint32_t key, const BitRun* runs, uint32_t nruns) {
   uint32_t x = 0;
-  for (const BitRun& r : runs) x |= ((key >> r.off) & ((1u << r.len) - 1u)) << r.lo;
+  for (uint32_t i = 0; i < nruns; ++i)
+    x |= ((key >> runs[i].off) & ((1u << runs[i].len) - 1u)) << runs[i].lo;
   return x;
 }
-uint32_t extract(uint32_t x, const std::vector<BitRun>& runs) {
+uint32_t extract(uint32_t x, const BitRun* runs, uint32_t nruns) {
   uint32_t k = 0;
-  for (const BitRun& r : runs) k |= ((x >> r.lo) & ((1u << r.len) - 1u)) << r.off;
+  for (uint32_t i = 0; i < nruns; ++i)
+    k |= ((x >> runs[i].lo) & ((1u << runs[i].len) - 1u)) << runs[i].off;
   return k;
 }
 
@@ -79,23 +82,26 @@ ChunkGate chunk_gate(const csim_gate& g) {
   return {(uint32_t)(g.cmask >> 2), (uint32_t)(g.cval >> 2), 1u << (g.target - 2)};
 }
 
-// Compile a run of X gates (time order) into lookup-table segments in
-// evaluation order (the inverse permutation: gates taken from the last).
-void compile_perm(const std::vector<csim_gate>& run, Program* p, Step* st) {
-  st->seg_off = (int)p->segs.size();
-  st->nseg = 0;
-  size_t i = run.size();
-  while (i > 0) {
+// Segments of a run of X gates.  forward: segments in time order, each
+// mapping an index to its image (scatter).  Otherwise in reverse order, each
+// mapping an index to its preimage (gather).
+std::vector<PermSeg> compile_perm(const std::vector<csim_gate>& run, bool forward, Program* p) {
+  std::vector<PermSeg> out;
+  std::vector<ChunkGate> gs;
+  for (const csim_gate& g : run) gs.push_back(chunk_gate(g));
+  if (!forward) std::reverse(gs.begin(), gs.end());
+  size_t i = 0;
+  while (i < gs.size()) {
     std::vector<ChunkGate> seg;
     uint32_t sup = 0;
-    while (i > 0) {
-      const ChunkGate cg = chunk_gate(run[i - 1]);
-      const uint32_t ns = sup | cg.m | cg.t;
-      if (!seg.empty() && (__builtin_popcount(ns) > kMaxSupport || (int)runs_of(ns).size() > kMaxRuns))
+    while (i < gs.size()) {
+      const uint32_t ns = sup | gs[i].m | gs[i].t;
+      if (!seg.empty() &&
+          (__builtin_popcount(ns) > kMaxSupport || (int)runs_of(ns).size() > kMaxRuns))
         break;
       sup = ns;
-      seg.push_back(cg);
-      --i;
+      seg.push_back(gs[i]);
+      ++i;
     }
     const std::vector<BitRun> runs = runs_of(sup);
     const int w = __builtin_popcount(sup);
@@ -105,17 +111,17 @@ void compile_perm(const std::vector<csim_gate>& run, Program* p, Step* st) {
     ps.nruns = (uint32_t)runs.size();
     for (size_t r = 0; r < runs.size(); ++r) ps.runs[r] = runs[r];
     for (uint32_t key = 0; key < (1u << w); ++key) {
-      uint32_t x = deposit(key, runs);
+      uint32_t x = deposit(key, ps.runs, ps.nruns);
       for (const ChunkGate& cg : seg)
         if ((x & cg.m) == cg.v) x ^= cg.t;
-      p->lut.push_back((uint16_t)extract(x, runs));
+      p->lut.push_back((uint16_t)extract(x, ps.runs, ps.nruns));
     }
-    p->segs.push_back(ps);
-    ++st->nseg;
+    out.push_back(ps);
     p->stats.segments++;
     p->stats.max_support = std::max<int64_t>(p->stats.max_support, w);
   }
   p->stats.perm_gates += (int64_t)run.size();
+  return out;
 }
 
 LocalOp local_op(const csim_gate& g) {
@@ -141,8 +147,14 @@ LocalOp local_op(const csim_gate& g) {
   return o;
 }
 
-void compile_mux(const std::vector<csim_gate>& grp, Program* p) {
-  // key bits: the chunk bits constrained by the most gates
+// A tile-local op before it is placed into a sweep's parameter block.
+struct OpItem {
+  LocalOp op;
+  MuxDesc mux;
+  ReflectDesc refl;
+};
+
+void compile_mux_group(const std::vector<csim_gate>& grp, Program* p, std::vector<OpItem>* out) {
   int freq[32] = {0};
   for (const csim_gate& g : grp) {
     const uint32_t m = (uint32_t)(g.cmask >> 2);
@@ -163,52 +175,64 @@ void compile_mux(const std::vector<csim_gate>& grp, Program* p) {
   std::vector<std::vector<int>> bucket((size_t)1 << w);
   for (size_t gi = 0; gi < grp.size(); ++gi) {
     const uint32_t m = (uint32_t)(grp[gi].cmask >> 2), v = (uint32_t)(grp[gi].cval >> 2);
-    const uint32_t fixed_m = extract(m & keymask, runs), fixed_v = extract(v & keymask, runs);
+    const uint32_t fm = extract(m & keymask, runs.data(), (uint32_t)runs.size());
+    const uint32_t fv = extract(v & keymask, runs.data(), (uint32_t)runs.size());
     for (uint32_t key = 0; key < (1u << w); ++key)
-      if ((key & fixed_m) == fixed_v) bucket[key].push_back((int)gi);
+      if ((key & fm) == fv) bucket[key].push_back((int)gi);
   }
-  MuxDesc md{};
-  md.nruns = (uint32_t)runs.size();
-  for (size_t r = 0; r < runs.size(); ++r) md.runs[r] = runs[r];
-  md.tab_off = (uint32_t)p->mtab.size();
-  md.target = grp[0].target;
+  OpItem it{};
+  it.mux.nruns = (uint32_t)runs.size();
+  for (size_t r = 0; r < runs.size(); ++r) it.mux.runs[r] = runs[r];
+  it.mux.tab_off = (uint32_t)p->mtab.size();
+  it.mux.target = grp[0].target;
+  it.mux.lm = (uint8_t)(grp[0].cmask & 3ull);
+  it.mux.lv = (uint8_t)(grp[0].cval & 3ull);
   for (uint32_t key = 0; key < (1u << w); ++key) {
-    uint2 be;
-    be.x = (uint32_t)p->ment.size();
-    be.y = (uint32_t)bucket[key].size();
-    p->mtab.push_back(be);
-    p->stats.max_bucket = std::max<int64_t>(p->stats.max_bucket, be.y);
+    if (bucket[key].size() > 255) {
+      std::fprintf(stderr, "csim fuser: multiplexer bucket overflow\n");
+      std::abort();
+    }
+    p->mtab.push_back(((uint32_t)p->mentf.size() << 8) | (uint32_t)bucket[key].size());
+    p->stats.max_bucket = std::max<int64_t>(p->stats.max_bucket, (int64_t)bucket[key].size());
     for (int gi : bucket[key]) {
       const LocalOp o = local_op(grp[gi]);
-      MuxEntry e{};
-      e.cm = o.cm;
-      e.cv = o.cv;
-      e.lm = o.lm;
-      e.lv = o.lv;
-      e.cf = o.cf;
-      e.sf = o.sf;
-      e.cd = o.cd;
-      e.sd = o.sd;
-      p->ment.push_back(e);
+      MuxEntryF ef{o.cm, o.cv, o.cf, o.sf};
+      MuxEntryD ed{o.cm, o.cv, 0u, 0u, o.cd, o.sd};
+      p->mentf.push_back(ef);
+      p->mentd.push_back(ed);
     }
   }
-  LocalOp mo{};
-  mo.op = 4;
-  mo.target = grp[0].target;
-  mo.cm = (uint32_t)p->mux.size();
-  p->mux.push_back(md);
-  p->ops.push_back(mo);
+  it.op.op = 4;
+  it.op.target = grp[0].target;
+  out->push_back(it);
   p->stats.mux++;
   p->stats.mux_gates += (int64_t)grp.size();
-  p->stats.mux_entries = (int64_t)p->ment.size();
+  p->stats.mux_entries = (int64_t)p->mentf.size();
+}
+
+// RY gates on one in-thread qubit commute: split the run by its controls on
+// state bits 0-1 and multiplex each part.
+void compile_mux(const std::vector<csim_gate>& grp, Program* p, std::vector<OpItem>* out) {
+  std::vector<std::vector<csim_gate>> parts;
+  std::vector<uint32_t> keys;
+  for (const csim_gate& g : grp) {
+    const uint32_t k = (uint32_t)((g.cmask & 3ull) | ((g.cval & 3ull) << 2));
+    size_t j = 0;
+    while (j < keys.size() && keys[j] != k) ++j;
+    if (j == keys.size()) {
+      keys.push_back(k);
+      parts.emplace_back();
+    }
+    parts[j].push_back(g);
+  }
+  for (const auto& part : parts) compile_mux_group(part, p, out);
 }
 
 using cplx = std::complex<double>;
 
 bool in_tile(const csim_gate& g) { return g.target <= 6 && (g.cmask >> 7) == 0; }
 
-// Dense 128 x 128 matrix (column-major per input basis state) of a window of
-// tile-only gates.
+// Dense 128 x 128 matrix (column by column) of a window of tile-only gates.
 std::vector<cplx> tile_matrix(const std::vector<csim_gate>& run, size_t i, size_t j) {
   std::vector<cplx> U(128 * 128, 0.0);
   const double h = 0.70710678118654752440;
@@ -222,7 +246,7 @@ std::vector<cplx> tile_matrix(const std::vector<csim_gate>& run, size_t i, size_
       const cplx ph(std::cos(g.angle), std::sin(g.angle));
       for (int x = 0; x < 128; ++x) {
         if ((x & tb) || ((uint64_t)x & g.cmask) != g.cval) continue;
-        cplx a0 = v[x], a1 = v[x | tb];
+        const cplx a0 = v[x], a1 = v[x | tb];
         switch (g.op) {
           case OP_X: v[x] = a1; v[x | tb] = a0; break;
           case OP_H: v[x] = (a0 + a1) * h; v[x | tb] = (a0 - a1) * h; break;
@@ -235,18 +259,21 @@ std::vector<cplx> tile_matrix(const std::vector<csim_gate>& run, size_t i, size_
   return U;
 }
 
-// If the window's matrix is I (x) A + J (x) B over the lane bits in lanes
-// (a 5-bit mask of lane-index bits), fill the descriptor and return true.
+// If the window's matrix is I (x) A + J (x) B over the lane bits in `lanes`,
+// fill the descriptor and return true.
 bool reflect_form(const std::vector<cplx>& U, uint32_t lanes, ReflectDesc* d) {
   auto at = [&](int row, int col) { return U[(size_t)col * 128 + row]; };
   const int cls = 1 << __builtin_popcount(lanes);
   int l1 = 0;
   for (int b = 0; b < 5; ++b)
-    if ((lanes >> b) & 1u) { l1 = 1 << b; break; }
+    if ((lanes >> b) & 1u) {
+      l1 = 1 << b;
+      break;
+    }
   cplx A[4][4], B[4][4];
   for (int y = 0; y < 4; ++y)
     for (int yp = 0; yp < 4; ++yp) {
-      B[y][yp] = at((0 << 2) | y, (l1 << 2) | yp) * (double)cls;
+      B[y][yp] = at(y, (l1 << 2) | yp) * (double)cls;
       A[y][yp] = at(y, yp) - B[y][yp] / (double)cls;
     }
   for (int l = 0; l < 32; ++l)
@@ -254,7 +281,8 @@ bool reflect_form(const std::vector<cplx>& U, uint32_t lanes, ReflectDesc* d) {
       const bool same_class = ((l ^ lp) & ~lanes & 31) == 0;
       for (int y = 0; y < 4; ++y)
         for (int yp = 0; yp < 4; ++yp) {
-          cplx model = (l == lp ? A[y][yp] : 0.0) + (same_class ? B[y][yp] / (double)cls : 0.0);
+          const cplx model =
+              (l == lp ? A[y][yp] : 0.0) + (same_class ? B[y][yp] / (double)cls : 0.0);
           if (std::abs(at((l << 2) | y, (lp << 2) | yp) - model) > 1e-12) return false;
         }
     }
@@ -274,54 +302,124 @@ bool reflect_form(const std::vector<cplx>& U, uint32_t lanes, ReflectDesc* d) {
   return true;
 }
 
+bool is_lane_h(const csim_gate& g) { return g.op == OP_H && g.target >= 2 && g.cmask == 0; }
+
 // Longest window starting at i (an H on a lane bit) with the averaging form.
-size_t try_reflect(const std::vector<csim_gate>& run, size_t i, Program* p) {
-  const csim_gate& g0 = run[i];
-  if (!(g0.op == OP_H && g0.target >= 2 && g0.cmask == 0)) return 0;
+size_t try_reflect(const std::vector<csim_gate>& run, size_t i, Program* p,
+                   std::vector<OpItem>* out) {
+  if (!is_lane_h(run[i])) return 0;
   size_t end = i;
   while (end < run.size() && in_tile(run[end])) ++end;
   for (size_t j = end; j > i + 1; --j) {
-    const csim_gate& gl = run[j - 1];
-    if (!(gl.op == OP_H && gl.target >= 2 && gl.cmask == 0)) continue;
+    if (!is_lane_h(run[j - 1])) continue;
     uint32_t lanes = 0;
     for (size_t k = i; k < j; ++k)
       if (run[k].op == OP_H && run[k].target >= 2) lanes |= 1u << (run[k].target - 2);
-    ReflectDesc d;
-    if (!reflect_form(tile_matrix(run, i, j), lanes, &d)) continue;
-    LocalOp mo{};
-    mo.op = 5;
-    mo.cm = (uint32_t)p->refl.size();
-    p->refl.push_back(d);
-    p->ops.push_back(mo);
+    OpItem it{};
+    if (!reflect_form(tile_matrix(run, i, j), lanes, &it.refl)) continue;
+    it.op.op = 5;
+    out->push_back(it);
     p->stats.reflect++;
     return j - i;
   }
   return 0;
 }
 
-void compile_local(const std::vector<csim_gate>& run, Program* p, Step* st) {
-  st->op_off = (int)p->ops.size();
+std::vector<OpItem> compile_local(const std::vector<csim_gate>& run, Program* p) {
+  std::vector<OpItem> out;
   size_t i = 0;
   while (i < run.size()) {
-    const csim_gate& g = run[i];
-    if (const size_t w = try_reflect(run, i, p)) {
+    if (const size_t w = try_reflect(run, i, p, &out)) {
       i += w;
       continue;
     }
+    const csim_gate& g = run[i];
     if (g.op == OP_RY && g.target < 2) {
       size_t j = i;
       while (j < run.size() && run[j].op == OP_RY && run[j].target == g.target) ++j;
       if ((int)(j - i) >= kMuxMinGates) {
-        compile_mux(std::vector<csim_gate>(run.begin() + i, run.begin() + j), p);
+        compile_mux(std::vector<csim_gate>(run.begin() + i, run.begin() + j), p, &out);
         i = j;
         continue;
       }
     }
-    p->ops.push_back(local_op(g));
+    OpItem it{};
+    it.op = local_op(g);
+    out.push_back(it);
     ++i;
   }
-  st->nops = (int)p->ops.size() - st->op_off;
   p->stats.local_gates += (int64_t)run.size();
+  return out;
+}
+
+// Split an op list into chunks that fit one parameter block.
+std::vector<std::vector<OpItem>> chunk_ops(const std::vector<OpItem>& ops) {
+  std::vector<std::vector<OpItem>> out;
+  std::vector<OpItem> cur;
+  int nmux = 0, nrefl = 0;
+  for (const OpItem& it : ops) {
+    const bool m = it.op.op == 4, r = it.op.op == 5;
+    if ((int)cur.size() + 1 > kMaxOps || (m && nmux + 1 > kMaxMux) || (r && nrefl + 1 > kMaxRefl)) {
+      out.push_back(cur);
+      cur.clear();
+      nmux = nrefl = 0;
+    }
+    cur.push_back(it);
+    nmux += m;
+    nrefl += r;
+  }
+  if (!cur.empty()) out.push_back(cur);
+  return out;
+}
+
+void emit_sweep(Program* p, const std::vector<PermSeg>& segs, const std::vector<OpItem>& ops) {
+  SweepParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.scatter = p->scatter ? 1 : 0;
+  sp.nseg = (int)segs.size();
+  for (size_t k = 0; k < segs.size(); ++k) sp.segs[k] = segs[k];
+  int nmux = 0, nrefl = 0;
+  for (const OpItem& it : ops) {
+    LocalOp o = it.op;
+    if (o.op == 4) {
+      sp.mux[nmux] = it.mux;
+      o.cm = (uint32_t)nmux++;
+    } else if (o.op == 5) {
+      sp.refl[nrefl] = it.refl;
+      o.cm = (uint32_t)nrefl++;
+    }
+    sp.ops[sp.nops++] = o;
+  }
+  Step st;
+  st.kind = 0;
+  st.param = (int)p->params.size();
+  st.gather = !segs.empty();
+  p->params.push_back(sp);
+  p->steps.push_back(st);
+  p->stats.sweeps++;
+}
+
+// Place one [permutation run, tile-local run] group into sweeps.
+void emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vector<csim_gate>& local) {
+  const std::vector<PermSeg> segs = compile_perm(perm, p->scatter, p);
+  std::vector<std::vector<PermSeg>> sc;
+  for (size_t k = 0; k < segs.size(); k += kMaxSeg)
+    sc.emplace_back(segs.begin() + k, segs.begin() + std::min(segs.size(), k + kMaxSeg));
+  std::vector<std::vector<OpItem>> oc = chunk_ops(compile_local(local, p));
+  if (!p->scatter) {
+    // gather: segment chunks are in evaluation (reverse time) order, so the
+    // last chunk holds the earliest gates and runs first
+    for (size_t k = sc.size(); k > 1; --k) emit_sweep(p, sc[k - 1], {});
+    emit_sweep(p, sc.empty() ? std::vector<PermSeg>() : sc[0],
+               oc.empty() ? std::vector<OpItem>() : oc[0]);
+    for (size_t k = 1; k < oc.size(); ++k) emit_sweep(p, {}, oc[k]);
+  } else {
+    // scatter: ops first (in place), the last op chunk with the first segments
+    for (size_t k = 0; k + 1 < oc.size(); ++k) emit_sweep(p, {}, oc[k]);
+    emit_sweep(p, sc.empty() ? std::vector<PermSeg>() : sc[0],
+               oc.empty() ? std::vector<OpItem>() : oc.back());
+    for (size_t k = 1; k < sc.size(); ++k) emit_sweep(p, sc[k], {});
+  }
 }
 
 }  // namespace
@@ -330,6 +428,8 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
   *p = Program();
   p->n = n;
   p->mode = mode;
+  const char* form = std::getenv("CSIM_SWEEP_FORM");
+  p->scatter = form && std::strcmp(form, "scatter") == 0;
   for (const csim_gate& g : gates) p->amp_updates += gate_amp_updates(g, n);
   if (mode == CSIM_EXEC_GATE || n < 7 || n > 34) {
     for (const csim_gate& g : gates) {
@@ -346,30 +446,39 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
   bool open = false;
   auto close = [&]() {
     if (!open) return;
-    Step st;
-    st.kind = 0;
-    compile_perm(perm, p, &st);
-    compile_local(local, p, &st);
-    p->steps.push_back(st);
-    p->stats.sweeps++;
+    emit_group(p, perm, local);
     perm.clear();
     local.clear();
     open = false;
   };
   for (const csim_gate& g : gates) {
     const bool pe = perm_eligible(g), le = local_eligible(g);
-    if (open && local.empty() && pe) {
-      perm.push_back(g);
-      continue;
-    }
-    if (open && le) {
-      local.push_back(g);
-      continue;
+    if (!p->scatter) {  // gather form: [perm][local]
+      if (open && local.empty() && pe) {
+        perm.push_back(g);
+        continue;
+      }
+      if (open && le) {
+        local.push_back(g);
+        continue;
+      }
+    } else {  // scatter form: [local][perm]
+      if (open && perm.empty() && le) {
+        local.push_back(g);
+        continue;
+      }
+      if (open && pe) {
+        perm.push_back(g);
+        continue;
+      }
     }
     close();
     if (pe || le) {
       open = true;
-      (pe ? perm : local).push_back(g);
+      if (!p->scatter)
+        (pe ? perm : local).push_back(g);
+      else
+        (le ? local : perm).push_back(g);
     } else {
       Step s;
       s.kind = 1;
@@ -381,18 +490,19 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
   close();
   p->passes = (int64_t)p->steps.size();
   for (const Step& s : p->steps)
-    if (s.kind == 0 && s.nseg > 0) p->pingpong = true;
+    if (s.kind == 0 && s.gather) p->pingpong = true;
   p->stats.lut_entries = (int64_t)p->lut.size();
   if (std::getenv("CSIM_FUSE_STATS")) {
     const FuseStats& f = p->stats;
     std::fprintf(stderr,
-                 "[csim fuse] n=%d sweeps=%lld single=%lld perm_gates=%lld segments=%lld "
+                 "[csim fuse] n=%d form=%s sweeps=%lld single=%lld perm_gates=%lld segments=%lld "
                  "max_support=%lld lut=%lld local=%lld mux=%lld mux_gates=%lld entries=%lld "
                  "max_bucket=%lld reflect=%lld\n",
-                 n, (long long)f.sweeps, (long long)f.single, (long long)f.perm_gates,
-                 (long long)f.segments, (long long)f.max_support, (long long)f.lut_entries,
-                 (long long)f.local_gates, (long long)f.mux, (long long)f.mux_gates,
-                 (long long)f.mux_entries, (long long)f.max_bucket, (long long)f.reflect);
+                 n, p->scatter ? "scatter" : "gather", (long long)f.sweeps, (long long)f.single,
+                 (long long)f.perm_gates, (long long)f.segments, (long long)f.max_support,
+                 (long long)f.lut_entries, (long long)f.local_gates, (long long)f.mux,
+                 (long long)f.mux_gates, (long long)f.mux_entries, (long long)f.max_bucket,
+                 (long long)f.reflect);
   }
 }
 
@@ -408,33 +518,33 @@ cudaError_t up(T** d, const std::vector<T>& h, cudaStream_t st) {
 
 cudaError_t upload_program(Program* p, cudaStream_t st) {
   if (p->uploaded) return cudaSuccess;
-  cudaError_t e = up(&p->d_segs, p->segs, st);
-  if (e == cudaSuccess) e = up(&p->d_lut, p->lut, st);
-  if (e == cudaSuccess) e = up(&p->d_ops, p->ops, st);
-  if (e == cudaSuccess) e = up(&p->d_mux, p->mux, st);
+  cudaError_t e = up(&p->d_lut, p->lut, st);
   if (e == cudaSuccess) e = up(&p->d_mtab, p->mtab, st);
-  if (e == cudaSuccess) e = up(&p->d_ment, p->ment, st);
-  if (e == cudaSuccess) e = up(&p->d_refl, p->refl, st);
+  if (e == cudaSuccess) e = up(&p->d_mentf, p->mentf, st);
+  if (e == cudaSuccess) e = up(&p->d_mentd, p->mentd, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     free_program(p);
     return e;
+  }
+  for (SweepParams& sp : p->params) {
+    sp.lut = p->d_lut;
+    sp.mtab = p->d_mtab;
+    sp.mentf = p->d_mentf;
+    sp.mentd = p->d_mentd;
   }
   p->uploaded = true;
   return cudaSuccess;
 }
 
 void free_program(Program* p) {
-  void* ptrs[] = {p->d_segs, p->d_lut, p->d_ops, p->d_mux, p->d_mtab, p->d_ment, p->d_refl};
+  void* ptrs[] = {p->d_lut, p->d_mtab, p->d_mentf, p->d_mentd};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  p->d_segs = nullptr;
   p->d_lut = nullptr;
-  p->d_ops = nullptr;
-  p->d_mux = nullptr;
   p->d_mtab = nullptr;
-  p->d_ment = nullptr;
-  p->d_refl = nullptr;
+  p->d_mentf = nullptr;
+  p->d_mentd = nullptr;
   p->uploaded = false;
 }
 
@@ -443,169 +553,164 @@ cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cuda
     cudaError_t e;
     if (s.kind == 1) {
       e = launch_gate(buf[*cur], prec, p.n, s.g, st);
+    } else if (!s.gather) {
+      e = launch_sweep(buf[*cur], buf[*cur], prec, p.n, p.params[s.param], st);
     } else {
-      SweepArgs a;
-      a.segs = p.d_segs + s.seg_off;
-      a.nseg = s.nseg;
-      a.ops = p.d_ops + s.op_off;
-      a.nops = s.nops;
-      a.lut = p.d_lut;
-      a.mux = p.d_mux;
-      a.mtab = p.d_mtab;
-      a.ment = p.d_ment;
-      a.refl = p.d_refl;
-      if (s.nseg == 0) {
-        e = launch_sweep(buf[*cur], buf[*cur], prec, p.n, a, st);
-      } else {
-        e = launch_sweep(buf[*cur], buf[1 - *cur], prec, p.n, a, st);
-        *cur = 1 - *cur;
-      }
+      e = launch_sweep(buf[*cur], buf[1 - *cur], prec, p.n, p.params[s.param], st);
+      *cur = 1 - *cur;
     }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// Host executor of a fused program with the kernel's semantics (FP64), used to
-// test the fuser without a GPU.  amps: 2^n interleaved complex values.
+// ------------------------------------------------------------ host executor
+namespace {
+
+void pair_op(double* a, double* b, int op, double c, double s) {
+  const double h = 0.70710678118654752440;
+  const double ar = a[0], ai = a[1], br = b[0], bi = b[1];
+  switch (op) {
+    case 0: a[0] = br; a[1] = bi; b[0] = ar; b[1] = ai; break;
+    case 1: a[0] = (ar + br) * h; a[1] = (ai + bi) * h; b[0] = (ar - br) * h; b[1] = (ai - bi) * h; break;
+    case 2: a[0] = c * ar - s * br; a[1] = c * ai - s * bi; b[0] = s * ar + c * br; b[1] = s * ai + c * bi; break;
+    default: a[0] = ar * c - ai * s; a[1] = ar * s + ai * c; b[0] = br * c + bi * s; b[1] = -br * s + bi * c; break;
+  }
+}
+
+uint32_t emu_permute(const Program& p, const SweepParams& sp, uint32_t x) {
+  for (int k = 0; k < sp.nseg; ++k) {
+    const PermSeg& g = sp.segs[k];
+    const uint32_t key = extract(x, g.runs, g.nruns);
+    x = (x & ~g.supmask) | deposit(p.lut[g.lut_off + key], g.runs, g.nruns);
+  }
+  return x;
+}
+
+void emu_ops(const Program& p, const SweepParams& sp, uint32_t tile, double (&v)[32][4][2]) {
+  for (int k = 0; k < sp.nops; ++k) {
+    const LocalOp& o = sp.ops[k];
+    if (o.op == 4) {
+      const MuxDesc& md = sp.mux[o.cm];
+      for (uint32_t lane = 0; lane < 32; ++lane) {
+        const uint32_t ci = (tile << 5) | lane;
+        const uint32_t bk = p.mtab[md.tab_off + extract(ci, md.runs, md.nruns)];
+        for (uint32_t e = bk >> 8; e < (bk >> 8) + (bk & 255u); ++e) {
+          const MuxEntryD& E = p.mentd[e];
+          if ((ci & E.cm) != E.cv) continue;
+          for (int j0 = 0; j0 < 4; ++j0) {
+            if (j0 & (1 << md.target)) continue;
+            if (((uint32_t)j0 & md.lm) != md.lv) continue;
+            pair_op(v[lane][j0], v[lane][j0 | (1 << md.target)], 2, E.c, E.s);
+          }
+        }
+      }
+      continue;
+    }
+    if (o.op == 5) {
+      const ReflectDesc& rd = sp.refl[o.cm];
+      double S[32][4][2];
+      for (uint32_t lane = 0; lane < 32; ++lane)
+        for (int y = 0; y < 4; ++y) {
+          S[lane][y][0] = S[lane][y][1] = 0.0;
+          for (uint32_t l2 = 0; l2 < 32; ++l2)
+            if (((lane ^ l2) & ~rd.lanemask & 31u) == 0) {
+              S[lane][y][0] += v[l2][y][0];
+              S[lane][y][1] += v[l2][y][1];
+            }
+        }
+      for (uint32_t lane = 0; lane < 32; ++lane) {
+        double o4[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        for (int y = 0; y < 4; ++y)
+          for (int yp = 0; yp < 4; ++yp) {
+            const int q = y * 4 + yp;
+            if ((rd.nzA >> q) & 1u) {
+              o4[y][0] += rd.ad[q].x * v[lane][yp][0] - rd.ad[q].y * v[lane][yp][1];
+              o4[y][1] += rd.ad[q].x * v[lane][yp][1] + rd.ad[q].y * v[lane][yp][0];
+            }
+            if ((rd.nzB >> q) & 1u) {
+              o4[y][0] += rd.bd[q].x * S[lane][yp][0] - rd.bd[q].y * S[lane][yp][1];
+              o4[y][1] += rd.bd[q].x * S[lane][yp][1] + rd.bd[q].y * S[lane][yp][0];
+            }
+          }
+        for (int y = 0; y < 4; ++y) {
+          v[lane][y][0] = o4[y][0];
+          v[lane][y][1] = o4[y][1];
+        }
+      }
+      continue;
+    }
+    if (o.target < 2) {
+      for (uint32_t lane = 0; lane < 32; ++lane) {
+        const uint32_t ci = (tile << 5) | lane;
+        if ((ci & o.cm) != o.cv) continue;
+        for (int j0 = 0; j0 < 4; ++j0) {
+          if (j0 & (1 << o.target)) continue;
+          if (((uint32_t)j0 & o.lm) != o.lv) continue;
+          pair_op(v[lane][j0], v[lane][j0 | (1 << o.target)], o.op, o.cd, o.sd);
+        }
+      }
+    } else {
+      const uint32_t lm = 1u << (o.target - 2);
+      for (uint32_t lane = 0; lane < 32; ++lane) {
+        if (lane & lm) continue;
+        const uint32_t ci = (tile << 5) | lane;
+        if ((ci & o.cm) != o.cv) continue;
+        for (int j = 0; j < 4; ++j)
+          if (((uint32_t)j & o.lm) == o.lv) pair_op(v[lane][j], v[lane | lm][j], o.op, o.cd, o.sd);
+      }
+    }
+  }
+}
+
+}  // namespace
+
 void emulate_program(const Program& p, std::vector<double>* amps) {
-  const int n = p.n;
-  const size_t N = (size_t)1 << n;
+  const size_t N = (size_t)1 << p.n;
   std::vector<double> other(2 * N);
   std::vector<double>* cur = amps;
   std::vector<double>* nxt = &other;
-  const double h = 0.70710678118654752440;
-  auto pair = [&](double* a, double* b, int op, double c, double s) {
-    double ar = a[0], ai = a[1], br = b[0], bi = b[1];
-    switch (op) {
-      case 0:
-        a[0] = br; a[1] = bi; b[0] = ar; b[1] = ai;
-        break;
-      case 1:
-        a[0] = (ar + br) * h; a[1] = (ai + bi) * h; b[0] = (ar - br) * h; b[1] = (ai - bi) * h;
-        break;
-      case 2:
-        a[0] = c * ar - s * br; a[1] = c * ai - s * bi; b[0] = s * ar + c * br; b[1] = s * ai + c * bi;
-        break;
-      default:
-        a[0] = ar * c - ai * s; a[1] = ar * s + ai * c; b[0] = br * c + bi * s; b[1] = -br * s + bi * c;
-        break;
-    }
-  };
   for (const Step& st : p.steps) {
     if (st.kind == 1) {
       const csim_gate& g = st.g;
       double c = 0, s = 0;
-      if (g.op == OP_RY) { c = std::cos(g.angle / 2); s = std::sin(g.angle / 2); }
-      if (g.op == OP_ZPHASE) { c = std::cos(g.angle); s = std::sin(g.angle); }
+      if (g.op == OP_RY) {
+        c = std::cos(g.angle / 2);
+        s = std::sin(g.angle / 2);
+      }
+      if (g.op == OP_ZPHASE) {
+        c = std::cos(g.angle);
+        s = std::sin(g.angle);
+      }
       const uint64_t tb = 1ull << g.target;
       for (uint64_t i = 0; i < N; ++i)
-        if (!(i & tb) && (i & g.cmask) == g.cval) pair(&(*cur)[2 * i], &(*cur)[2 * (i | tb)], g.op, c, s);
+        if (!(i & tb) && (i & g.cmask) == g.cval)
+          pair_op(&(*cur)[2 * i], &(*cur)[2 * (i | tb)], g.op, c, s);
       continue;
     }
-    const bool gather = st.nseg > 0;
-    std::vector<double>& dst = gather ? *nxt : *cur;
-    const uint32_t nchunks = (uint32_t)(N >> 2);
-    for (uint32_t tile = 0; tile < (nchunks >> 5); ++tile) {
+    const SweepParams& sp = p.params[st.param];
+    std::vector<double>& dst = st.gather ? *nxt : *cur;
+    const uint32_t ntiles = (uint32_t)(N >> 7);
+    for (uint32_t tile = 0; tile < ntiles; ++tile) {
       double v[32][4][2];
+      uint32_t where[32];
       for (uint32_t lane = 0; lane < 32; ++lane) {
         const uint32_t ci = (tile << 5) | lane;
-        uint32_t src = ci;
-        for (int k = 0; k < st.nseg; ++k) {
-          const PermSeg& g = p.segs[st.seg_off + k];
-          std::vector<BitRun> runs(g.runs, g.runs + g.nruns);
-          const uint32_t key = extract(src, runs);
-          const uint32_t val = p.lut[g.lut_off + key];
-          src = (src & ~g.supmask) | deposit(val, runs);
-        }
+        const uint32_t src = sp.scatter ? ci : emu_permute(p, sp, ci);
+        where[lane] = sp.scatter ? emu_permute(p, sp, ci) : ci;
         for (int j = 0; j < 4; ++j) {
           v[lane][j][0] = (*cur)[2 * (((size_t)src << 2) + j)];
           v[lane][j][1] = (*cur)[2 * (((size_t)src << 2) + j) + 1];
         }
       }
-      for (int k = 0; k < st.nops; ++k) {
-        const LocalOp& o = p.ops[st.op_off + k];
-        if (o.op == 4) {
-          const MuxDesc& md = p.mux[o.cm];
-          std::vector<BitRun> runs(md.runs, md.runs + md.nruns);
-          for (uint32_t lane = 0; lane < 32; ++lane) {
-            const uint32_t ci = (tile << 5) | lane;
-            const uint2 bk = p.mtab[md.tab_off + extract(ci, runs)];
-            for (uint32_t e = bk.x; e < bk.x + bk.y; ++e) {
-              const MuxEntry& E = p.ment[e];
-              if ((ci & E.cm) != E.cv) continue;
-              for (int j0 = 0; j0 < 4; ++j0) {
-                if (j0 & (1 << md.target)) continue;
-                if (((uint32_t)j0 & E.lm) != E.lv) continue;
-                pair(v[lane][j0], v[lane][j0 | (1 << md.target)], 2, E.cd, E.sd);
-              }
-            }
-          }
-          continue;
-        }
-        if (o.op == 5) {
-          const ReflectDesc& rd = p.refl[o.cm];
-          double S[32][4][2];
-          for (uint32_t lane = 0; lane < 32; ++lane)
-            for (int y = 0; y < 4; ++y) {
-              S[lane][y][0] = S[lane][y][1] = 0.0;
-              for (uint32_t l2 = 0; l2 < 32; ++l2)
-                if (((lane ^ l2) & ~rd.lanemask & 31u) == 0) {
-                  S[lane][y][0] += v[l2][y][0];
-                  S[lane][y][1] += v[l2][y][1];
-                }
-            }
-          for (uint32_t lane = 0; lane < 32; ++lane) {
-            double o4[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-            for (int y = 0; y < 4; ++y)
-              for (int yp = 0; yp < 4; ++yp) {
-                const int q = y * 4 + yp;
-                if ((rd.nzA >> q) & 1u) {
-                  o4[y][0] += rd.ad[q].x * v[lane][yp][0] - rd.ad[q].y * v[lane][yp][1];
-                  o4[y][1] += rd.ad[q].x * v[lane][yp][1] + rd.ad[q].y * v[lane][yp][0];
-                }
-                if ((rd.nzB >> q) & 1u) {
-                  o4[y][0] += rd.bd[q].x * S[lane][yp][0] - rd.bd[q].y * S[lane][yp][1];
-                  o4[y][1] += rd.bd[q].x * S[lane][yp][1] + rd.bd[q].y * S[lane][yp][0];
-                }
-              }
-            for (int y = 0; y < 4; ++y) {
-              v[lane][y][0] = o4[y][0];
-              v[lane][y][1] = o4[y][1];
-            }
-          }
-          continue;
-        }
-        if (o.target < 2) {
-          for (uint32_t lane = 0; lane < 32; ++lane) {
-            const uint32_t ci = (tile << 5) | lane;
-            if ((ci & o.cm) != o.cv) continue;
-            for (int j0 = 0; j0 < 4; ++j0) {
-              if (j0 & (1 << o.target)) continue;
-              if (((uint32_t)j0 & o.lm) != o.lv) continue;
-              pair(v[lane][j0], v[lane][j0 | (1 << o.target)], o.op, o.cd, o.sd);
-            }
-          }
-        } else {
-          const uint32_t lm = 1u << (o.target - 2);
-          for (uint32_t lane = 0; lane < 32; ++lane) {
-            if (lane & lm) continue;
-            const uint32_t ci = (tile << 5) | lane;
-            if ((ci & o.cm) != o.cv) continue;
-            for (int j = 0; j < 4; ++j)
-              if (((uint32_t)j & o.lm) == o.lv) pair(v[lane][j], v[lane | lm][j], o.op, o.cd, o.sd);
-          }
-        }
-      }
-      for (uint32_t lane = 0; lane < 32; ++lane) {
-        const uint32_t ci = (tile << 5) | lane;
+      emu_ops(p, sp, tile, v);
+      for (uint32_t lane = 0; lane < 32; ++lane)
         for (int j = 0; j < 4; ++j) {
-          dst[2 * (((size_t)ci << 2) + j)] = v[lane][j][0];
-          dst[2 * (((size_t)ci << 2) + j) + 1] = v[lane][j][1];
+          dst[2 * (((size_t)where[lane] << 2) + j)] = v[lane][j][0];
+          dst[2 * (((size_t)where[lane] << 2) + j) + 1] = v[lane][j][1];
         }
-      }
     }
-    if (gather) std::swap(cur, nxt);
+    if (st.gather) std::swap(cur, nxt);
   }
   if (cur != amps) *amps = *cur;
 }

@@ -12,8 +12,9 @@
 namespace csim {
 
 struct Step {
-  int kind = 0;  // 0 = fused sweep, 1 = single gate
-  int seg_off = 0, nseg = 0, op_off = 0, nops = 0;
+  int kind = 0;    // 0 = fused sweep, 1 = single gate
+  int param = -1;  // index into Program::params (sweeps)
+  bool gather = false;  // the sweep moves data (out of place)
   csim_gate g{};
 };
 
@@ -26,37 +27,34 @@ struct FuseStats {
 struct Program {
   int n = 0;
   csim_exec mode = CSIM_EXEC_FUSED;
+  bool scatter = false;  // sweep form: [ops][scatter] instead of [gather][ops]
   std::vector<Step> steps;
-  std::vector<PermSeg> segs;
+  std::vector<SweepParams> params;
   std::vector<uint16_t> lut;
-  std::vector<LocalOp> ops;
-  std::vector<MuxDesc> mux;
-  std::vector<uint2> mtab;
-  std::vector<MuxEntry> ment;
-  std::vector<ReflectDesc> refl;
-  // device copies
-  PermSeg* d_segs = nullptr;
+  std::vector<uint32_t> mtab;
+  std::vector<MuxEntryF> mentf;
+  std::vector<MuxEntryD> mentd;
+  // device copies of the tables
   uint16_t* d_lut = nullptr;
-  LocalOp* d_ops = nullptr;
-  MuxDesc* d_mux = nullptr;
-  uint2* d_mtab = nullptr;
-  MuxEntry* d_ment = nullptr;
-  ReflectDesc* d_refl = nullptr;
+  uint32_t* d_mtab = nullptr;
+  MuxEntryF* d_mentf = nullptr;
+  MuxEntryD* d_mentd = nullptr;
   int64_t passes = 0;        // HBM passes per execution
   double amp_updates = 0.0;  // sum over elementary gates of amplitudes changed
-  bool pingpong = false;     // some step gathers out of place
+  bool pingpong = false;     // some step moves data out of place
   bool uploaded = false;
   FuseStats stats;
 };
 
 // Build the program for `gates` on an n-qubit state.  FUSED mode needs
 // 7 <= n <= 34 (the warp tile and 32-bit chunk indices); other sizes fall
-// back to one launch per gate.
+// back to one launch per gate.  The sweep form is gather unless
+// CSIM_SWEEP_FORM=scatter.
 void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p);
 cudaError_t upload_program(Program* p, cudaStream_t st);
 void free_program(Program* p);
-// Run the program on buf[*cur] (and buf[1 - *cur] when it gathers); *cur tracks
-// which buffer holds the state afterwards.
+// Run the program on buf[*cur] (and buf[1 - *cur] when it moves data); *cur
+// tracks which buffer holds the state afterwards.
 cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st);
 // Host executor of a fused program (FP64, kernel semantics) for testing.
 void emulate_program(const Program& p, std::vector<double>* amps);

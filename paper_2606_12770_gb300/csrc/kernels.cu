@@ -197,174 +197,214 @@ template <>
 struct CplxOf<float> {
   static __device__ __forceinline__ float2 a(const ReflectDesc& d, int k) { return d.af[k]; }
   static __device__ __forceinline__ float2 b(const ReflectDesc& d, int k) { return d.bf[k]; }
+  static __device__ __forceinline__ void entry(const SweepParams& p, uint32_t e, uint32_t* cm,
+                                               uint32_t* cv, float* c, float* s) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(p.mentf) + e);
+    *cm = w.x;
+    *cv = w.y;
+    *c = __uint_as_float(w.z);
+    *s = __uint_as_float(w.w);
+  }
 };
 template <>
 struct CplxOf<double> {
   static __device__ __forceinline__ double2 a(const ReflectDesc& d, int k) { return d.ad[k]; }
   static __device__ __forceinline__ double2 b(const ReflectDesc& d, int k) { return d.bd[k]; }
+  static __device__ __forceinline__ void entry(const SweepParams& p, uint32_t e, uint32_t* cm,
+                                               uint32_t* cv, double* c, double* s) {
+    const MuxEntryD& E = p.mentd[e];
+    *cm = E.cm;
+    *cv = E.cv;
+    *c = E.c;
+    *s = E.s;
+  }
 };
 
-// One fused sweep.  Each lane owns one 4-amplitude chunk of U destination
-// tiles: it computes the source chunk by running the permutation segments
-// (the inverse permutation, i.e. the gates in reverse order), loads it, then
-// applies the tile-local gates in order.  Descriptors are read once per
-// group of U tiles.
+// Apply the tile-local ops of one sweep to U tiles held by the warp.
+template <typename R, int U>
+__device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::T (&v)[U][4],
+                                          const uint32_t (&ci)[U], uint32_t lane) {
+  using T = typename V2<R>::T;
+  for (int k = 0; k < a.nops; ++k) {
+    const LocalOp& o = a.ops[k];
+    const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv, op = o.op, tg = o.target;
+    if (op == 4) {  // multiplexed RY on bit tg (0 or 1)
+      const MuxDesc& md = a.mux[ocm];
+      const uint32_t nr = md.nruns, toff = md.tab_off, mt = md.target, mlm = md.lm, mlv = md.lv;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t key = gather_key(ci[u], md.runs, nr);
+        const uint32_t bk = __ldg(a.mtab + toff + key);
+        const uint32_t e0 = bk >> 8, e1 = e0 + (bk & 255u);
+        for (uint32_t e = e0; e < e1; ++e) {
+          uint32_t cm, cv;
+          R c, s;
+          CplxOf<R>::entry(a, e, &cm, &cv, &c, &s);
+          if ((ci[u] & cm) != cv) continue;
+          if (mt == 0) {
+            if ((0u & mlm) == mlv) rot<T, R>(v[u][0], v[u][1], c, s);
+            if ((2u & mlm) == mlv) rot<T, R>(v[u][2], v[u][3], c, s);
+          } else {
+            if ((0u & mlm) == mlv) rot<T, R>(v[u][0], v[u][2], c, s);
+            if ((1u & mlm) == mlv) rot<T, R>(v[u][1], v[u][3], c, s);
+          }
+        }
+      }
+      continue;
+    }
+    if (op == 5) {  // I (x) A + J (x) B over the lane bits of lanemask
+      const ReflectDesc& rd = a.refl[ocm];
+      const uint32_t lmask = rd.lanemask, nzA = rd.nzA, nzB = rd.nzB;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        T S[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) S[y] = v[u][y];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          if (!((lmask >> b) & 1u)) continue;
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const T w = shfl_xor_c(S[y], 1 << b);
+            S[y].x += w.x;
+            S[y].y += w.y;
+          }
+        }
+        T o4[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          o4[y] = mk<T>((R)0, (R)0);
+#pragma unroll
+          for (int yp = 0; yp < 4; ++yp) {
+            const int q = y * 4 + yp;
+            if ((nzA >> q) & 1u) {
+              const T c = CplxOf<R>::a(rd, q);
+              o4[y].x += c.x * v[u][yp].x - c.y * v[u][yp].y;
+              o4[y].y += c.x * v[u][yp].y + c.y * v[u][yp].x;
+            }
+            if ((nzB >> q) & 1u) {
+              const T c = CplxOf<R>::b(rd, q);
+              o4[y].x += c.x * S[yp].x - c.y * S[yp].y;
+              o4[y].y += c.x * S[yp].y + c.y * S[yp].x;
+            }
+          }
+        }
+#pragma unroll
+        for (int y = 0; y < 4; ++y) v[u][y] = o4[y];
+      }
+      continue;
+    }
+    const R c = Coef<R>::c(o), s = Coef<R>::s(o);
+    if (tg < 2) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if ((ci[u] & ocm) != ocv) continue;
+        if (tg == 0) {
+          if ((0u & lm) == lv) apply_pair<R>(v[u][0], v[u][1], op, c, s);
+          if ((2u & lm) == lv) apply_pair<R>(v[u][2], v[u][3], op, c, s);
+        } else {
+          if ((0u & lm) == lv) apply_pair<R>(v[u][0], v[u][2], op, c, s);
+          if ((1u & lm) == lv) apply_pair<R>(v[u][1], v[u][3], op, c, s);
+        }
+      }
+      continue;
+    }
+    const int lmask = 1 << (tg - 2);
+    const bool hi = (lane & (uint32_t)lmask) != 0;
+    const R h = (R)0.70710678118654752440;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool cok = (ci[u] & ocm) == ocv;
+      if (op == 3) {  // diagonal: no partner needed
+        if (!cok) continue;
+        const R sg = hi ? -s : s;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (((uint32_t)j & lm) == lv)
+            v[u][j] = mk<T>(v[u][j].x * c - v[u][j].y * sg, v[u][j].x * sg + v[u][j].y * c);
+        continue;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const T w = shfl_xor_c(v[u][j], lmask);
+        if (!cok || (((uint32_t)j & lm) != lv)) continue;
+        if (op == 0) {
+          v[u][j] = w;
+        } else if (op == 1) {
+          v[u][j] = hi ? mk<T>((w.x - v[u][j].x) * h, (w.y - v[u][j].y) * h)
+                       : mk<T>((v[u][j].x + w.x) * h, (v[u][j].y + w.y) * h);
+        } else {
+          v[u][j] = hi ? mk<T>(s * w.x + c * v[u][j].x, s * w.y + c * v[u][j].y)
+                       : mk<T>(c * v[u][j].x - s * w.x, c * v[u][j].y - s * w.y);
+        }
+      }
+    }
+  }
+}
+
+// Map chunk indices through the permutation segments of a sweep.
+template <int U>
+__device__ __forceinline__ void permute(const SweepParams& a, uint32_t (&x)[U]) {
+  for (int k = 0; k < a.nseg; ++k) {
+    const PermSeg& g = a.segs[k];
+    const uint32_t nr = g.nruns, sup = g.supmask, off = g.lut_off;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t key = gather_key(x[u], g.runs, nr);
+      const uint32_t val = __ldg(a.lut + off + key);
+      x[u] = scatter_key(x[u], val, sup, g.runs, nr);
+    }
+  }
+}
+
+// One fused sweep over U tiles per warp iteration (one 4-amplitude chunk per
+// lane and tile).  Gather form: the lane computes its source chunk through the
+// segments (the inverse permutation), loads it, applies the tile-local ops,
+// and stores contiguously.  Scatter form: the lane loads its own chunk, applies
+// the tile-local ops, and stores to the chunk's image under the permutation.
 template <typename R, int U, int MINB>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(const typename V2<R>::T* in,
-                                                    typename V2<R>::T* out, uint32_t ntiles,
-                                                    SweepArgs a) {
+                                                          typename V2<R>::T* out, uint32_t ntiles,
+                                                          const __grid_constant__ SweepParams a) {
   using T = typename V2<R>::T;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t t0 = warp * U; t0 < ntiles; t0 += nwarps * U) {
-    uint32_t ci[U], src[U];
+    uint32_t ci[U], mv[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) src[u] = ci[u] = ((t0 + u) << 5) | lane;
-    for (int k = 0; k < a.nseg; ++k) {
-      const PermSeg& g = a.segs[k];
-      const uint32_t nr = g.nruns, sup = g.supmask, off = g.lut_off;
-      BitRun rr[kMaxRuns];
-#pragma unroll
-      for (int r = 0; r < kMaxRuns; ++r)
-        if (r < (int)nr) rr[r] = g.runs[r];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint32_t key = gather_key(src[u], rr, nr);
-        const uint32_t v = __ldg(a.lut + off + key);
-        src[u] = scatter_key(src[u], v, sup, rr, nr);
-      }
-    }
+    for (int u = 0; u < U; ++u) mv[u] = ci[u] = ((t0 + u) << 5) | lane;
     T v[U][4];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const T* sp = in + ((size_t)src[u] << 2);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) v[u][j] = sp[j];
-    }
-    for (int k = 0; k < a.nops; ++k) {
-      const LocalOp& o = a.ops[k];
-      const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv, op = o.op, tg = o.target;
-      if (op == 4) {  // multiplexed RY on bit tg
-        const MuxDesc& md = a.mux[ocm];
-        const uint32_t nr = md.nruns, toff = md.tab_off;
-        BitRun rr[kMaxRuns];
-#pragma unroll
-        for (int r = 0; r < kMaxRuns; ++r)
-          if (r < (int)nr) rr[r] = md.runs[r];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const uint32_t key = gather_key(ci[u], rr, nr);
-          const uint2 bk = __ldg(a.mtab + toff + key);
-          for (uint32_t e = bk.x; e < bk.x + bk.y; ++e) {
-            const MuxEntry& E = a.ment[e];
-            if ((ci[u] & E.cm) != E.cv) continue;
-            const R c = Coef<R>::c(E), s = Coef<R>::s(E);
-            const uint32_t elm = E.lm, elv = E.lv;
-            if (tg == 0) {
-              if ((0u & elm) == elv) rot<T, R>(v[u][0], v[u][1], c, s);
-              if ((2u & elm) == elv) rot<T, R>(v[u][2], v[u][3], c, s);
-            } else {
-              if ((0u & elm) == elv) rot<T, R>(v[u][0], v[u][2], c, s);
-              if ((1u & elm) == elv) rot<T, R>(v[u][1], v[u][3], c, s);
-            }
-          }
-        }
-        continue;
-      }
-      if (op == 5) {  // I (x) A + J (x) B over the lane bits of lanemask
-        const ReflectDesc& rd = a.refl[ocm];
-        const uint32_t lmask = rd.lanemask, nzA = rd.nzA, nzB = rd.nzB;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          T S[4];
-#pragma unroll
-          for (int y = 0; y < 4; ++y) S[y] = v[u][y];
-#pragma unroll
-          for (int b = 0; b < 5; ++b) {
-            if (!((lmask >> b) & 1u)) continue;
-#pragma unroll
-            for (int y = 0; y < 4; ++y) {
-              const T w = shfl_xor_c(S[y], 1 << b);
-              S[y].x += w.x;
-              S[y].y += w.y;
-            }
-          }
-          T o4[4];
-#pragma unroll
-          for (int y = 0; y < 4; ++y) {
-            o4[y] = mk<T>((R)0, (R)0);
-#pragma unroll
-            for (int yp = 0; yp < 4; ++yp) {
-              const int q = y * 4 + yp;
-              if ((nzA >> q) & 1u) {
-                const T c = CplxOf<R>::a(rd, q);
-                o4[y].x += c.x * v[u][yp].x - c.y * v[u][yp].y;
-                o4[y].y += c.x * v[u][yp].y + c.y * v[u][yp].x;
-              }
-              if ((nzB >> q) & 1u) {
-                const T c = CplxOf<R>::b(rd, q);
-                o4[y].x += c.x * S[yp].x - c.y * S[yp].y;
-                o4[y].y += c.x * S[yp].y + c.y * S[yp].x;
-              }
-            }
-          }
-#pragma unroll
-          for (int y = 0; y < 4; ++y) v[u][y] = o4[y];
-        }
-        continue;
-      }
-      const R c = Coef<R>::c(o), s = Coef<R>::s(o);
-      if (tg < 2) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if ((ci[u] & ocm) != ocv) continue;
-          if (tg == 0) {
-            if ((0u & lm) == lv) apply_pair<R>(v[u][0], v[u][1], op, c, s);
-            if ((2u & lm) == lv) apply_pair<R>(v[u][2], v[u][3], op, c, s);
-          } else {
-            if ((0u & lm) == lv) apply_pair<R>(v[u][0], v[u][2], op, c, s);
-            if ((1u & lm) == lv) apply_pair<R>(v[u][1], v[u][3], op, c, s);
-          }
-        }
-        continue;
-      }
-      const int lmask = 1 << (tg - 2);
-      const bool hi = (lane & (uint32_t)lmask) != 0;
-      const R h = (R)0.70710678118654752440;
+    if (!a.scatter) {
+      permute<U>(a, mv);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const bool cok = (ci[u] & ocm) == ocv;
-        if (op == 3) {  // diagonal: no partner needed
-          if (!cok) continue;
-          const R sg = hi ? -s : s;
+        const T* sp = in + ((size_t)mv[u] << 2);
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (((uint32_t)j & lm) == lv)
-              v[u][j] = mk<T>(v[u][j].x * c - v[u][j].y * sg, v[u][j].x * sg + v[u][j].y * c);
-          continue;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const T w = shfl_xor_c(v[u][j], lmask);
-          if (!cok || (((uint32_t)j & lm) != lv)) continue;
-          if (op == 0) {
-            v[u][j] = w;
-          } else if (op == 1) {
-            v[u][j] = hi ? mk<T>((w.x - v[u][j].x) * h, (w.y - v[u][j].y) * h)
-                         : mk<T>((v[u][j].x + w.x) * h, (v[u][j].y + w.y) * h);
-          } else {
-            v[u][j] = hi ? mk<T>(s * w.x + c * v[u][j].x, s * w.y + c * v[u][j].y)
-                         : mk<T>(c * v[u][j].x - s * w.x, c * v[u][j].y - s * w.y);
-          }
-        }
+        for (int j = 0; j < 4; ++j) v[u][j] = sp[j];
       }
-    }
+      apply_ops<R, U>(a, v, ci, lane);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      T* dp = out + ((size_t)ci[u] << 2);
+      for (int u = 0; u < U; ++u) {
+        T* dp = out + ((size_t)ci[u] << 2);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) dp[j] = v[u][j];
+        for (int j = 0; j < 4; ++j) dp[j] = v[u][j];
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const T* sp = in + ((size_t)ci[u] << 2);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[u][j] = sp[j];
+      }
+      apply_ops<R, U>(a, v, ci, lane);
+      permute<U>(a, mv);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        T* dp = out + ((size_t)mv[u] << 2);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dp[j] = v[u][j];
+      }
     }
   }
 }
@@ -519,7 +559,7 @@ SweepCfg sweep_cfg() {
 }
 
 template <typename R, int U, int MINB>
-void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepArgs& a, cudaStream_t st) {
+void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepParams& a, cudaStream_t st) {
   using T = typename V2<R>::T;
   const int blk = 256;
   const int grd = grid_for((uint64_t)ntiles / U * 32, blk);
@@ -527,7 +567,7 @@ void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepArgs&
 }
 
 template <typename R>
-void launch_sweep_r(const void* in, void* out, uint32_t ntiles, int u, int minb, const SweepArgs& a,
+void launch_sweep_r(const void* in, void* out, uint32_t ntiles, int u, int minb, const SweepParams& a,
                     cudaStream_t st) {
   while ((uint32_t)u > ntiles) u >>= 1;
   if (minb == 2) {
@@ -542,7 +582,7 @@ void launch_sweep_r(const void* in, void* out, uint32_t ntiles, int u, int minb,
 
 }  // namespace
 
-cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepArgs& a,
+cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
                          cudaStream_t st) {
   const uint32_t ntiles = 1u << (n - 7);
   const SweepCfg c = sweep_cfg();

@@ -39,18 +39,22 @@ struct LocalOp {
 };
 
 // Multiplexed RY on an in-thread qubit: key bits of the chunk index select a
-// bucket of candidate gates; each candidate is checked in full.
+// bucket of candidate gates; each candidate's chunk controls are checked in
+// full.  All candidates share the controls (lm, lv) on state bits 0-1.
 struct MuxDesc {
   uint32_t nruns;
   BitRun runs[kMaxRuns];
-  uint32_t tab_off;    // into the (start, count) bucket table
-  uint32_t target;
+  uint32_t tab_off;  // into the bucket table: entry start << 8 | count
+  uint8_t target, lm, lv, pad;
 };
-struct MuxEntry {
+struct MuxEntryF {
   uint32_t cm, cv;
-  uint8_t lm, lv, pad0, pad1;
-  float cf, sf;
-  double cd, sd;
+  float c, s;
+};
+struct MuxEntryD {
+  uint32_t cm, cv;
+  uint32_t pad0, pad1;
+  double c, s;
 };
 
 // A window of tile-local gates whose 128 x 128 matrix is I (x) A + J (x) B on
@@ -66,22 +70,26 @@ struct ReflectDesc {
   double2 ad[16], bd[16];
 };
 
-struct SweepArgs {
-  const PermSeg* segs;
-  int nseg;
-  const LocalOp* ops;
-  int nops;
+// Everything one sweep launch needs, passed by value in the kernel parameter
+// block (constant bank): the permutation segments, the tile-local ops and
+// their descriptors.  Large tables stay in global memory.
+constexpr int kMaxSeg = 12, kMaxOps = 40, kMaxRefl = 4, kMaxMux = 8;
+struct SweepParams {
+  int nseg, nops, scatter, pad;
+  PermSeg segs[kMaxSeg];
+  LocalOp ops[kMaxOps];
+  ReflectDesc refl[kMaxRefl];
+  MuxDesc mux[kMaxMux];
   const uint16_t* lut;
-  const MuxDesc* mux;
-  const uint2* mtab;
-  const MuxEntry* ment;
-  const ReflectDesc* refl;
+  const uint32_t* mtab;
+  const MuxEntryF* mentf;
+  const MuxEntryD* mentd;
 };
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,
                         const double* d_val, int64_t count, cudaStream_t st);
 cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaStream_t st);
-cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepArgs& a,
+cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
                          cudaStream_t st);
 int norm_partials_needed();
 cudaError_t launch_norms(const void* state, int prec, int n, const uint64_t* d_pm,

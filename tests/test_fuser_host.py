@@ -49,7 +49,9 @@ def test_long_permutation_runs_split_into_tables():
     g = [x for x in g if x[2] & 3 == 0]
     psi = I.random_unit_state(n, 7)
     got, st = N.emulate_fused(g, n, psi)
-    assert st["passes"] == 1 and st["segments"] > 1 and st["max_support"] <= 14
+    # at most 12 tables fit one kernel parameter block; longer runs take more passes
+    assert st["segments"] > 1 and st["max_support"] <= 14
+    assert st["passes"] == -(-st["segments"] // 12)
     assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-14
 
 
@@ -60,7 +62,8 @@ def test_multiplexed_rotations(target):
     g = random_gates(n, 200, 11 + target, ops=(2,), maxc=7, targets=[target])
     psi = I.random_unit_state(n, 3)
     got, st = N.emulate_fused(g, n, psi)
-    assert st["mux"] == 1 and st["mux_gates"] == 200
+    # one multiplexer per distinct control pattern on the other in-thread qubit
+    assert 1 <= st["mux"] <= 3 and st["mux_gates"] == 200
     assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-13
 
 

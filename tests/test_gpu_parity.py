@@ -272,14 +272,15 @@ print("ok")
 '''
 
 
+@pytest.mark.parametrize("form", ["gather", "scatter"])
 @pytest.mark.parametrize("cfg", ["1,1", "2,1", "4,1", "1,2", "2,2", "4,2"])
-def test_sweep_kernel_variants(cfg):
-    """Every compiled sweep-kernel variant (tiles per iteration, blocks per SM)."""
+def test_sweep_kernel_variants(cfg, form):
+    """Every compiled sweep-kernel variant (tiles per iteration, blocks per SM, form)."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, CSIM_SWEEP_CFG=cfg)
+    env = dict(os.environ, CSIM_SWEEP_CFG=cfg, CSIM_SWEEP_FORM=form)
     r = subprocess.run([sys.executable, "-c", VARIANT_SCRIPT, root], env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
