@@ -30,8 +30,7 @@ namespace csim {
 
 namespace {
 
-constexpr int kMaxSupport = 14;   // bits per permutation lookup table
-constexpr int kMuxKeyBits = 12;   // bits of the multiplexer bucket key
+constexpr int kMaxKeyBits = 14;   // key bits of a permutation or multiplexer table
 constexpr int kMuxMinGates = 4;   // shorter RY runs stay individual gates
 
 bool perm_eligible(const csim_gate& g) {
@@ -39,39 +38,45 @@ bool perm_eligible(const csim_gate& g) {
 }
 bool local_eligible(const csim_gate& g) { return g.target <= 6; }
 
-std::vector<BitRun> runs_of(uint32_t mask) {
-  std::vector<BitRun> runs;
-  int off = 0;
-  for (int b = 0; b < 32;) {
-    if (!((mask >> b) & 1u)) {
-      ++b;
-      continue;
-    }
-    int e = b;
-    while (e < 32 && ((mask >> e) & 1u)) ++e;
-    BitRun r;
-    r.lo = (uint8_t)b;
-    r.len = (uint8_t)(e - b);
-    r.off = (uint8_t)off;
-    r.pad = 0;
-    runs.push_back(r);
-    off += e - b;
-    b = e;
+// Cover the set bits of `mask` with at most two windows of total width <=
+// limit (one window when it fits).  Returns false if impossible.
+bool cover2(uint32_t mask, int limit, KeyWin* w) {
+  *w = KeyWin{0, 0, 0, 0};
+  if (!mask) return true;
+  const int lo = __builtin_ctz(mask), hi = 31 - __builtin_clz(mask);
+  if (hi - lo + 1 <= limit) {
+    *w = KeyWin{(uint8_t)lo, (uint8_t)(hi - lo + 1), 0, 0};
+    return true;
   }
-  return runs;
+  // split at the largest gap between consecutive set bits
+  int best_gap = 0, cut = -1, prev = lo;
+  for (int b = lo + 1; b <= hi; ++b) {
+    if (!((mask >> b) & 1u)) continue;
+    if (b - prev - 1 > best_gap) {
+      best_gap = b - prev - 1;
+      cut = prev;
+    }
+    prev = b;
+  }
+  if (cut < 0) return false;
+  int next = cut + 1;
+  while (!((mask >> next) & 1u)) ++next;
+  const int w0 = cut - lo + 1, w1 = hi - next + 1;
+  if (w0 + w1 > limit) return false;
+  *w = KeyWin{(uint8_t)lo, (uint8_t)w0, (uint8_t)next, (uint8_t)w1};
+  return true;
 }
 
-uint32_t deposit(uint32_t key, const BitRun* runs, uint32_t nruns) {
-  uint32_t x = 0;
-  for (uint32_t i = 0; i < nruns; ++i)
-    x |= ((key >> runs[i].off) & ((1u << runs[i].len) - 1u)) << runs[i].lo;
-  return x;
+uint32_t win_mask(const KeyWin& w) {
+  return (((1u << w.w0) - 1u) << w.lo0) | (((1u << w.w1) - 1u) << w.lo1);
 }
-uint32_t extract(uint32_t x, const BitRun* runs, uint32_t nruns) {
-  uint32_t k = 0;
-  for (uint32_t i = 0; i < nruns; ++i)
-    k |= ((x >> runs[i].lo) & ((1u << runs[i].len) - 1u)) << runs[i].off;
-  return k;
+uint32_t win_key(uint32_t x, const KeyWin& w) {
+  return ((x >> w.lo0) & ((1u << w.w0) - 1u)) | (((x >> w.lo1) & ((1u << w.w1) - 1u)) << w.w0);
+}
+uint32_t win_put(uint32_t x, uint32_t v, const KeyWin& w) {
+  const uint32_t m0 = (1u << w.w0) - 1u, m1 = (1u << w.w1) - 1u;
+  x &= ~((m0 << w.lo0) | (m1 << w.lo1));
+  return x | ((v & m0) << w.lo0) | (((v >> w.w0) & m1) << w.lo1);
 }
 
 struct ChunkGate {
@@ -94,27 +99,31 @@ std::vector<PermSeg> compile_perm(const std::vector<csim_gate>& run, bool forwar
   while (i < gs.size()) {
     std::vector<ChunkGate> seg;
     uint32_t sup = 0;
+    KeyWin win{};
     while (i < gs.size()) {
       const uint32_t ns = sup | gs[i].m | gs[i].t;
-      if (!seg.empty() &&
-          (__builtin_popcount(ns) > kMaxSupport || (int)runs_of(ns).size() > kMaxRuns))
+      KeyWin nw;
+      if (!cover2(ns, kMaxKeyBits, &nw)) {
+        if (seg.empty()) {
+          std::fprintf(stderr, "csim fuser: gate support does not fit a table key\n");
+          std::abort();
+        }
         break;
+      }
       sup = ns;
+      win = nw;
       seg.push_back(gs[i]);
       ++i;
     }
-    const std::vector<BitRun> runs = runs_of(sup);
-    const int w = __builtin_popcount(sup);
+    const int w = win.w0 + win.w1;
     PermSeg ps{};
-    ps.supmask = sup;
+    ps.win = win;
     ps.lut_off = (uint32_t)p->lut.size();
-    ps.nruns = (uint32_t)runs.size();
-    for (size_t r = 0; r < runs.size(); ++r) ps.runs[r] = runs[r];
     for (uint32_t key = 0; key < (1u << w); ++key) {
-      uint32_t x = deposit(key, ps.runs, ps.nruns);
+      uint32_t x = win_put(0u, key, win);
       for (const ChunkGate& cg : seg)
         if ((x & cg.m) == cg.v) x ^= cg.t;
-      p->lut.push_back((uint16_t)extract(x, ps.runs, ps.nruns));
+      p->lut.push_back((uint16_t)win_key(x, win));
     }
     out.push_back(ps);
     p->stats.segments++;
@@ -155,6 +164,7 @@ struct OpItem {
 };
 
 void compile_mux_group(const std::vector<csim_gate>& grp, Program* p, std::vector<OpItem>* out) {
+  // key windows: grow by the chunk bits constrained by the most gates
   int freq[32] = {0};
   for (const csim_gate& g : grp) {
     const uint32_t m = (uint32_t)(g.cmask >> 2);
@@ -164,42 +174,58 @@ void compile_mux_group(const std::vector<csim_gate>& grp, Program* p, std::vecto
   for (int b = 0; b < 32; ++b)
     if (freq[b] > 0) order.push_back(b);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return freq[a] > freq[b]; });
-  uint32_t keymask = 0;
+  uint32_t keybits = 0;
+  KeyWin win{};
   for (int b : order) {
-    const uint32_t nk = keymask | (1u << b);
-    if (__builtin_popcount(nk) > kMuxKeyBits || (int)runs_of(nk).size() > kMaxRuns) continue;
-    keymask = nk;
+    KeyWin nw;
+    if (cover2(keybits | (1u << b), kMaxKeyBits, &nw)) {
+      keybits |= 1u << b;
+      win = nw;
+    }
   }
-  const std::vector<BitRun> runs = runs_of(keymask);
-  const int w = __builtin_popcount(keymask);
+  const uint32_t wmask = win_mask(win);
+  const int w = win.w0 + win.w1;
   std::vector<std::vector<int>> bucket((size_t)1 << w);
   for (size_t gi = 0; gi < grp.size(); ++gi) {
-    const uint32_t m = (uint32_t)(grp[gi].cmask >> 2), v = (uint32_t)(grp[gi].cval >> 2);
-    const uint32_t fm = extract(m & keymask, runs.data(), (uint32_t)runs.size());
-    const uint32_t fv = extract(v & keymask, runs.data(), (uint32_t)runs.size());
+    const uint32_t m = (uint32_t)(grp[gi].cmask >> 2) & wmask;
+    const uint32_t v = (uint32_t)(grp[gi].cval >> 2) & wmask;
+    const uint32_t fm = win_key(m, win), fv = win_key(v, win);
     for (uint32_t key = 0; key < (1u << w); ++key)
       if ((key & fm) == fv) bucket[key].push_back((int)gi);
   }
   OpItem it{};
-  it.mux.nruns = (uint32_t)runs.size();
-  for (size_t r = 0; r < runs.size(); ++r) it.mux.runs[r] = runs[r];
+  it.mux.win = win;
   it.mux.tab_off = (uint32_t)p->mtab.size();
   it.mux.target = grp[0].target;
   it.mux.lm = (uint8_t)(grp[0].cmask & 3ull);
   it.mux.lv = (uint8_t)(grp[0].cval & 3ull);
   for (uint32_t key = 0; key < (1u << w); ++key) {
-    if (bucket[key].size() > 255) {
+    const std::vector<int>& bk = bucket[key];
+    if (bk.empty()) {
+      p->mtab.push_back(0u);
+      continue;
+    }
+    bool pure = true;
+    for (int gi : bk) pure = pure && (((uint32_t)(grp[gi].cmask >> 2) & ~wmask) == 0);
+    if (pure) {
+      double th = 0.0;
+      for (int gi : bk) th += grp[gi].angle;
+      p->angd.push_back(make_double2(std::cos(th / 2.0), std::sin(th / 2.0)));
+      p->angf.push_back(make_float2((float)std::cos(th / 2.0), (float)std::sin(th / 2.0)));
+      p->mtab.push_back(0x80000000u | (uint32_t)(p->angd.size() - 1));
+      p->stats.max_bucket = std::max<int64_t>(p->stats.max_bucket, 1);
+      continue;
+    }
+    if (bk.size() > 255 || p->mentf.size() >= (1u << 23)) {
       std::fprintf(stderr, "csim fuser: multiplexer bucket overflow\n");
       std::abort();
     }
-    p->mtab.push_back(((uint32_t)p->mentf.size() << 8) | (uint32_t)bucket[key].size());
-    p->stats.max_bucket = std::max<int64_t>(p->stats.max_bucket, (int64_t)bucket[key].size());
-    for (int gi : bucket[key]) {
+    p->mtab.push_back(((uint32_t)p->mentf.size() << 8) | (uint32_t)bk.size());
+    p->stats.max_bucket = std::max<int64_t>(p->stats.max_bucket, (int64_t)bk.size());
+    for (int gi : bk) {
       const LocalOp o = local_op(grp[gi]);
-      MuxEntryF ef{o.cm, o.cv, o.cf, o.sf};
-      MuxEntryD ed{o.cm, o.cv, 0u, 0u, o.cd, o.sd};
-      p->mentf.push_back(ef);
-      p->mentd.push_back(ed);
+      p->mentf.push_back(MuxEntryF{o.cm, o.cv, o.cf, o.sf});
+      p->mentd.push_back(MuxEntryD{o.cm, o.cv, 0u, 0u, o.cd, o.sd});
     }
   }
   it.op.op = 4;
@@ -522,6 +548,8 @@ cudaError_t upload_program(Program* p, cudaStream_t st) {
   if (e == cudaSuccess) e = up(&p->d_mtab, p->mtab, st);
   if (e == cudaSuccess) e = up(&p->d_mentf, p->mentf, st);
   if (e == cudaSuccess) e = up(&p->d_mentd, p->mentd, st);
+  if (e == cudaSuccess) e = up(&p->d_angf, p->angf, st);
+  if (e == cudaSuccess) e = up(&p->d_angd, p->angd, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     free_program(p);
@@ -532,19 +560,23 @@ cudaError_t upload_program(Program* p, cudaStream_t st) {
     sp.mtab = p->d_mtab;
     sp.mentf = p->d_mentf;
     sp.mentd = p->d_mentd;
+    sp.angf = p->d_angf;
+    sp.angd = p->d_angd;
   }
   p->uploaded = true;
   return cudaSuccess;
 }
 
 void free_program(Program* p) {
-  void* ptrs[] = {p->d_lut, p->d_mtab, p->d_mentf, p->d_mentd};
+  void* ptrs[] = {p->d_lut, p->d_mtab, p->d_mentf, p->d_mentd, p->d_angf, p->d_angd};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->d_lut = nullptr;
   p->d_mtab = nullptr;
   p->d_mentf = nullptr;
   p->d_mentd = nullptr;
+  p->d_angf = nullptr;
+  p->d_angd = nullptr;
   p->uploaded = false;
 }
 
@@ -581,8 +613,7 @@ void pair_op(double* a, double* b, int op, double c, double s) {
 uint32_t emu_permute(const Program& p, const SweepParams& sp, uint32_t x) {
   for (int k = 0; k < sp.nseg; ++k) {
     const PermSeg& g = sp.segs[k];
-    const uint32_t key = extract(x, g.runs, g.nruns);
-    x = (x & ~g.supmask) | deposit(p.lut[g.lut_off + key], g.runs, g.nruns);
+    x = win_put(x, p.lut[g.lut_off + win_key(x, g.win)], g.win);
   }
   return x;
 }
@@ -594,15 +625,23 @@ void emu_ops(const Program& p, const SweepParams& sp, uint32_t tile, double (&v)
       const MuxDesc& md = sp.mux[o.cm];
       for (uint32_t lane = 0; lane < 32; ++lane) {
         const uint32_t ci = (tile << 5) | lane;
-        const uint32_t bk = p.mtab[md.tab_off + extract(ci, md.runs, md.nruns)];
-        for (uint32_t e = bk >> 8; e < (bk >> 8) + (bk & 255u); ++e) {
-          const MuxEntryD& E = p.mentd[e];
-          if ((ci & E.cm) != E.cv) continue;
+        const uint32_t word = p.mtab[md.tab_off + win_key(ci, md.win)];
+        if (word == 0u) continue;
+        auto rot_all = [&](double c, double s) {
           for (int j0 = 0; j0 < 4; ++j0) {
             if (j0 & (1 << md.target)) continue;
             if (((uint32_t)j0 & md.lm) != md.lv) continue;
-            pair_op(v[lane][j0], v[lane][j0 | (1 << md.target)], 2, E.c, E.s);
+            pair_op(v[lane][j0], v[lane][j0 | (1 << md.target)], 2, c, s);
           }
+        };
+        if (word & 0x80000000u) {
+          const double2 cs = p.angd[word & 0x7fffffffu];
+          rot_all(cs.x, cs.y);
+          continue;
+        }
+        for (uint32_t e = word >> 8; e < (word >> 8) + (word & 255u); ++e) {
+          const MuxEntryD& E = p.mentd[e];
+          if ((ci & E.cm) == E.cv) rot_all(E.c, E.s);
         }
       }
       continue;

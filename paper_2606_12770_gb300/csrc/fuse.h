@@ -34,11 +34,15 @@ struct Program {
   std::vector<uint32_t> mtab;
   std::vector<MuxEntryF> mentf;
   std::vector<MuxEntryD> mentd;
+  std::vector<float2> angf;
+  std::vector<double2> angd;
   // device copies of the tables
   uint16_t* d_lut = nullptr;
   uint32_t* d_mtab = nullptr;
   MuxEntryF* d_mentf = nullptr;
   MuxEntryD* d_mentd = nullptr;
+  float2* d_angf = nullptr;
+  double2* d_angd = nullptr;
   int64_t passes = 0;        // HBM passes per execution
   double amp_updates = 0.0;  // sum over elementary gates of amplitudes changed
   bool pingpong = false;     // some step moves data out of place

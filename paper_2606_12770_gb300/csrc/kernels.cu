@@ -158,29 +158,16 @@ struct Coef<double> {
   static __device__ __forceinline__ double s(const O& o) { return o.sd; }
 };
 
-__device__ __forceinline__ uint32_t gather_key(uint32_t x, const BitRun* runs, uint32_t nruns) {
-  uint32_t key = 0;
-#pragma unroll
-  for (int r = 0; r < kMaxRuns; ++r) {
-    if (r < (int)nruns) {
-      const BitRun b = runs[r];
-      key |= ((x >> b.lo) & ((1u << b.len) - 1u)) << b.off;
-    }
-  }
-  return key;
+__device__ __forceinline__ uint32_t win_key(uint32_t x, KeyWin w) {
+  const uint32_t k0 = (x >> w.lo0) & ((1u << w.w0) - 1u);
+  const uint32_t k1 = (x >> w.lo1) & ((1u << w.w1) - 1u);
+  return k0 | (k1 << w.w0);
 }
 
-__device__ __forceinline__ uint32_t scatter_key(uint32_t x, uint32_t v, uint32_t supmask,
-                                                const BitRun* runs, uint32_t nruns) {
-  x &= ~supmask;
-#pragma unroll
-  for (int r = 0; r < kMaxRuns; ++r) {
-    if (r < (int)nruns) {
-      const BitRun b = runs[r];
-      x |= ((v >> b.off) & ((1u << b.len) - 1u)) << b.lo;
-    }
-  }
-  return x;
+__device__ __forceinline__ uint32_t win_put(uint32_t x, uint32_t v, KeyWin w) {
+  const uint32_t m0 = (1u << w.w0) - 1u, m1 = (1u << w.w1) - 1u;
+  x &= ~((m0 << w.lo0) | (m1 << w.lo1));
+  return x | ((v & m0) << w.lo0) | (((v >> w.w0) & m1) << w.lo1);
 }
 
 // RY(c, s) on the in-thread pair (a, b) = (bit 0, bit 1) of the target qubit.
@@ -191,12 +178,29 @@ __device__ __forceinline__ void rot(T& a, T& b, R c, R s) {
   a = na;
 }
 
+// RY(c, s) on both in-thread pairs of target bit mt whose other low bit
+// satisfies the controls (mlm, mlv).
+template <typename T, typename R>
+__device__ __forceinline__ void rot_pairs(T (&w)[4], uint32_t mt, uint32_t mlm, uint32_t mlv, R c,
+                                          R s) {
+  if (mt == 0) {
+    if ((0u & mlm) == mlv) rot<T, R>(w[0], w[1], c, s);
+    if ((2u & mlm) == mlv) rot<T, R>(w[2], w[3], c, s);
+  } else {
+    if ((0u & mlm) == mlv) rot<T, R>(w[0], w[2], c, s);
+    if ((1u & mlm) == mlv) rot<T, R>(w[1], w[3], c, s);
+  }
+}
+
 template <typename R>
 struct CplxOf;
 template <>
 struct CplxOf<float> {
   static __device__ __forceinline__ float2 a(const ReflectDesc& d, int k) { return d.af[k]; }
   static __device__ __forceinline__ float2 b(const ReflectDesc& d, int k) { return d.bf[k]; }
+  static __device__ __forceinline__ float2 angle(const SweepParams& p, uint32_t i) {
+    return __ldg(p.angf + i);
+  }
   static __device__ __forceinline__ void entry(const SweepParams& p, uint32_t e, uint32_t* cm,
                                                uint32_t* cv, float* c, float* s) {
     const uint4 w = __ldg(reinterpret_cast<const uint4*>(p.mentf) + e);
@@ -210,6 +214,9 @@ template <>
 struct CplxOf<double> {
   static __device__ __forceinline__ double2 a(const ReflectDesc& d, int k) { return d.ad[k]; }
   static __device__ __forceinline__ double2 b(const ReflectDesc& d, int k) { return d.bd[k]; }
+  static __device__ __forceinline__ double2 angle(const SweepParams& p, uint32_t i) {
+    return __ldg(p.angd + i);
+  }
   static __device__ __forceinline__ void entry(const SweepParams& p, uint32_t e, uint32_t* cm,
                                                uint32_t* cv, double* c, double* s) {
     const MuxEntryD& E = p.mentd[e];
@@ -230,24 +237,23 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
     const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv, op = o.op, tg = o.target;
     if (op == 4) {  // multiplexed RY on bit tg (0 or 1)
       const MuxDesc& md = a.mux[ocm];
-      const uint32_t nr = md.nruns, toff = md.tab_off, mt = md.target, mlm = md.lm, mlv = md.lv;
+      const KeyWin w = md.win;
+      const uint32_t toff = md.tab_off, mt = md.target, mlm = md.lm, mlv = md.lv;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const uint32_t key = gather_key(ci[u], md.runs, nr);
-        const uint32_t bk = __ldg(a.mtab + toff + key);
-        const uint32_t e0 = bk >> 8, e1 = e0 + (bk & 255u);
+        const uint32_t word = __ldg(a.mtab + toff + win_key(ci[u], w));
+        if (word == 0u) continue;
+        if (word & 0x80000000u) {
+          const T cs = CplxOf<R>::angle(a, word & 0x7fffffffu);
+          rot_pairs<T, R>(v[u], mt, mlm, mlv, cs.x, cs.y);
+          continue;
+        }
+        const uint32_t e0 = word >> 8, e1 = e0 + (word & 255u);
         for (uint32_t e = e0; e < e1; ++e) {
           uint32_t cm, cv;
           R c, s;
           CplxOf<R>::entry(a, e, &cm, &cv, &c, &s);
-          if ((ci[u] & cm) != cv) continue;
-          if (mt == 0) {
-            if ((0u & mlm) == mlv) rot<T, R>(v[u][0], v[u][1], c, s);
-            if ((2u & mlm) == mlv) rot<T, R>(v[u][2], v[u][3], c, s);
-          } else {
-            if ((0u & mlm) == mlv) rot<T, R>(v[u][0], v[u][2], c, s);
-            if ((1u & mlm) == mlv) rot<T, R>(v[u][1], v[u][3], c, s);
-          }
+          if ((ci[u] & cm) == cv) rot_pairs<T, R>(v[u], mt, mlm, mlv, c, s);
         }
       }
       continue;
@@ -347,13 +353,10 @@ template <int U>
 __device__ __forceinline__ void permute(const SweepParams& a, uint32_t (&x)[U]) {
   for (int k = 0; k < a.nseg; ++k) {
     const PermSeg& g = a.segs[k];
-    const uint32_t nr = g.nruns, sup = g.supmask, off = g.lut_off;
+    const KeyWin w = g.win;
+    const uint16_t* lut = a.lut + g.lut_off;
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint32_t key = gather_key(x[u], g.runs, nr);
-      const uint32_t val = __ldg(a.lut + off + key);
-      x[u] = scatter_key(x[u], val, sup, g.runs, nr);
-    }
+    for (int u = 0; u < U; ++u) x[u] = win_put(x[u], __ldg(lut + win_key(x[u], w)), w);
   }
 }
 
@@ -544,7 +547,7 @@ struct SweepCfg {
 
 SweepCfg sweep_cfg() {
   static SweepCfg cfg = [] {
-    SweepCfg c{4, 2, 1};
+    SweepCfg c{1, 1, 1};
     if (const char* e = std::getenv("CSIM_SWEEP_CFG")) {
       int u = 0, m = 0;
       if (std::sscanf(e, "%d,%d", &u, &m) == 2 && (u == 1 || u == 2 || u == 4) && (m == 1 || m == 2)) {

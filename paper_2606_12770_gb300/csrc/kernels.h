@@ -9,22 +9,18 @@
 
 namespace csim {
 
-// Bits [lo, lo+len) of a 32-bit chunk index (state index >> 2) are bits
-// [off, off+len) of a table key.
-struct BitRun {
-  uint8_t lo, len, off, pad;
+// A table key made of at most two bit windows of a 32-bit chunk index
+// (state index >> 2): key = bits [lo0, lo0+w0) | bits [lo1, lo1+w1) << w0.
+struct KeyWin {
+  uint8_t lo0, w0, lo1, w1;
 };
 
-constexpr int kMaxRuns = 8;
-
 // A run of multi-controlled X gates compiled to a lookup table over the
-// chunk-index bits they read or write (their support): the table maps the
-// support bits of an index to the support bits of its image.
+// key windows that hold every chunk-index bit the gates read or write: the
+// table maps the window bits of an index to the window bits of its image.
 struct PermSeg {
-  uint32_t supmask;
+  KeyWin win;
   uint32_t lut_off;  // into the uint16 table array
-  uint32_t nruns;
-  BitRun runs[kMaxRuns];
 };
 
 // One gate inside the 128-amplitude warp tile.  Controls are split into the
@@ -38,13 +34,15 @@ struct LocalOp {
   double cd, sd;  // the same in FP64
 };
 
-// Multiplexed RY on an in-thread qubit: key bits of the chunk index select a
-// bucket of candidate gates; each candidate's chunk controls are checked in
-// full.  All candidates share the controls (lm, lv) on state bits 0-1.
+// Multiplexed RY on an in-thread qubit: key windows of the chunk index select
+// a bucket-table word: 0 = no rotation; bit 31 set = the bucket's gates all
+// match, rotate by the precomputed angle with index (word & 0x7fffffff);
+// otherwise (start << 8 | count) candidates whose chunk controls are checked
+// in full.  All gates of one multiplexer share the controls (lm, lv) on state
+// bits 0-1.
 struct MuxDesc {
-  uint32_t nruns;
-  BitRun runs[kMaxRuns];
-  uint32_t tab_off;  // into the bucket table: entry start << 8 | count
+  KeyWin win;
+  uint32_t tab_off;
   uint8_t target, lm, lv, pad;
 };
 struct MuxEntryF {
@@ -73,7 +71,7 @@ struct ReflectDesc {
 // Everything one sweep launch needs, passed by value in the kernel parameter
 // block (constant bank): the permutation segments, the tile-local ops and
 // their descriptors.  Large tables stay in global memory.
-constexpr int kMaxSeg = 12, kMaxOps = 40, kMaxRefl = 4, kMaxMux = 8;
+constexpr int kMaxSeg = 16, kMaxOps = 40, kMaxRefl = 4, kMaxMux = 8;
 struct SweepParams {
   int nseg, nops, scatter, pad;
   PermSeg segs[kMaxSeg];
@@ -84,6 +82,8 @@ struct SweepParams {
   const uint32_t* mtab;
   const MuxEntryF* mentf;
   const MuxEntryD* mentd;
+  const float2* angf;   // cos, sin of the summed angle of pure buckets
+  const double2* angd;
 };
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,
