@@ -184,8 +184,8 @@ csim_status csim_sv_free(csim_sv* sv);
  * list with the same fuser as CSIM_EXEC_FUSED and executes the resulting
  * sweeps (lookup-table permutations, multiplexed rotations, warp-tile gates)
  * on the host in FP64 with the kernel's semantics.  amps: 2^n interleaved
- * complex values, updated in place.  For testing the fuser without a GPU;
- * n must be in [7, 24].  If stats is non-NULL it receives 13 counters: sweeps,
+ * complex values, updated in place (n in [7, 24]), or NULL to compile only and
+ * report the statistics (n in [7, 34]).  For testing the fuser without a GPU.  If stats is non-NULL it receives 13 counters: sweeps,
  * single-gate steps, permutation gates, lookup tables, local gates,
  * multiplexers, multiplexed gates, multiplexer entries, largest bucket,
  * table entries, largest table support, HBM passes, averaging blocks. */

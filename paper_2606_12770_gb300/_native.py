@@ -275,13 +275,16 @@ FUSE_STAT_NAMES = ["sweeps", "single", "perm_gates", "segments", "local_gates", 
 
 
 def emulate_fused(gates, n, amps):
-    """Host executor of the fused program (testing aid); returns (state, stats dict)."""
+    """Host executor of the fused program (testing aid); returns (state, stats dict).
+
+    amps=None compiles only and returns (None, stats)."""
     lib = load()
     g = gates_to_records(gates)
-    a = np.ascontiguousarray(amps, dtype=np.complex128).copy()
     st = np.zeros(13, dtype=np.int64)
+    a = None if amps is None else np.ascontiguousarray(amps, dtype=np.complex128).copy()
     _check(lib.csim_emulate_fused(g.ctypes.data_as(C.c_void_p), g.shape[0], int(n),
-                                  _dp(a.view(np.float64)), st.ctypes.data_as(C.POINTER(C.c_int64))))
+                                  None if a is None else _dp(a.view(np.float64)),
+                                  st.ctypes.data_as(C.POINTER(C.c_int64))))
     return a, dict(zip(FUSE_STAT_NAMES, (int(x) for x in st)))
 
 

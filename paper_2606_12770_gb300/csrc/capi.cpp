@@ -582,8 +582,8 @@ csim_status csim_sv_free(csim_sv* s) {
 
 csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n, double* amps,
                                int64_t* stats) {
-  if ((!gates && n_gates) || !amps) return fail(CSIM_ERR_ARG, "null argument");
-  if (n < 7 || n > 24) return fail(CSIM_ERR_ARG, "n must be in [7, 24]");
+  if (!gates && n_gates) return fail(CSIM_ERR_ARG, "null argument");
+  if (n < 7 || n > (amps ? 24 : 34)) return fail(CSIM_ERR_ARG, "n out of range");
   for (size_t i = 0; i < n_gates; ++i) {
     const csim_gate& g = gates[i];
     if (g.op > 3 || g.target >= n || ((g.cmask >> g.target) & 1ull) || (g.cval & ~g.cmask) ||
@@ -593,10 +593,12 @@ csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n
   Program p;
   std::vector<Gate> gl(gates, gates + n_gates);
   csim::build_program(gl, n, CSIM_EXEC_FUSED, &p);
-  const size_t N = (size_t)1 << n;
-  std::vector<double> st(amps, amps + 2 * N);
-  csim::emulate_program(p, &st);
-  std::memcpy(amps, st.data(), 2 * N * sizeof(double));
+  if (amps) {
+    const size_t N = (size_t)1 << n;
+    std::vector<double> st(amps, amps + 2 * N);
+    csim::emulate_program(p, &st);
+    std::memcpy(amps, st.data(), 2 * N * sizeof(double));
+  }
   if (stats) {
     const csim::FuseStats& f = p.stats;
     const int64_t v[13] = {f.sweeps,      f.single,      f.perm_gates,  f.segments, f.local_gates,

@@ -30,7 +30,16 @@ namespace csim {
 
 namespace {
 
-constexpr int kMaxKeyBits = 14;   // key bits of a permutation or multiplexer table
+// Key bits of a permutation or multiplexer table (CSIM_KEY_BITS overrides):
+// wider keys mean fewer chained lookups but tables that spill out of L1.
+int max_key_bits() {
+  static const int v = [] {
+    const char* e = std::getenv("CSIM_KEY_BITS");
+    const int k = e ? std::atoi(e) : 0;
+    return (k >= 8 && k <= 16) ? k : 14;
+  }();
+  return v;
+}
 constexpr int kMuxMinGates = 4;   // shorter RY runs stay individual gates
 
 bool perm_eligible(const csim_gate& g) {
@@ -87,38 +96,144 @@ ChunkGate chunk_gate(const csim_gate& g) {
   return {(uint32_t)(g.cmask >> 2), (uint32_t)(g.cval >> 2), 1u << (g.target - 2)};
 }
 
-// Segments of a run of X gates.  forward: segments in time order, each
-// mapping an index to its image (scatter).  Otherwise in reverse order, each
-// mapping an index to its preimage (gather).
+// One permutation step before table compilation.
+struct PermItem {
+  bool add = false;       // controlled +-1 on a contiguous register
+  uint32_t m = 0, v = 0;  // controls
+  uint32_t t = 0;         // gate: target bit mask
+  int base = 0, width = 0, neg = 0;
+};
+
+// Recognise controlled increment / decrement cascades of a contiguous
+// register: gates X(r[j] | C, r[0..j-1] all 1 (or all 0)) for j = w-1..0.
+bool recognise_adds() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_PERM_ADD");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+
+std::vector<PermItem> perm_items(const std::vector<csim_gate>& run) {
+  std::vector<PermItem> out;
+  size_t i = 0;
+  while (i < run.size()) {
+    if (!recognise_adds()) {
+      const ChunkGate g = chunk_gate(run[i++]);
+      PermItem it;
+      it.m = g.m;
+      it.v = g.v;
+      it.t = g.t;
+      out.push_back(it);
+      continue;
+    }
+    const ChunkGate g0 = chunk_gate(run[i]);
+    uint32_t ctl = g0.m, val = g0.v;
+    std::vector<int> tgts = {__builtin_ctz(g0.t)};
+    int sense = -1;  // 1: INC (controls 1), 0: DEC (controls 0)
+    size_t j = i + 1;
+    while (j < run.size()) {
+      const ChunkGate g = chunk_gate(run[j]);
+      const uint32_t tb = g.t;
+      if (!(ctl & tb)) break;
+      const int bv = (val & tb) ? 1 : 0;
+      if (sense >= 0 && bv != sense) break;
+      if (g.m != (ctl & ~tb) || g.v != (val & ~tb)) break;
+      sense = bv;
+      ctl = g.m;
+      val = g.v;
+      tgts.push_back(__builtin_ctz(tb));
+      ++j;
+    }
+    // register bits r[0..w-1] are the targets in reverse order; need contiguous
+    const int w = (int)tgts.size();
+    bool ok = w >= 2;
+    for (int k = 0; ok && k < w; ++k) ok = tgts[w - 1 - k] == tgts[w - 1] + k;
+    if (ok) {
+      PermItem it;
+      it.add = true;
+      it.m = ctl;
+      it.v = val;
+      it.base = tgts[w - 1];
+      it.width = w;
+      it.neg = sense == 0 ? 1 : 0;
+      out.push_back(it);
+      i = j;
+      continue;
+    }
+    PermItem it;
+    it.m = g0.m;
+    it.v = g0.v;
+    it.t = g0.t;
+    out.push_back(it);
+    ++i;
+  }
+  return out;
+}
+
+// Compiled steps of a run of X gates.  forward: time order, each step mapping
+// an index to its image (scatter).  Otherwise reverse order with inverted
+// steps, each mapping an index to its preimage (gather).
 std::vector<PermSeg> compile_perm(const std::vector<csim_gate>& run, bool forward, Program* p) {
   std::vector<PermSeg> out;
-  std::vector<ChunkGate> gs;
-  for (const csim_gate& g : run) gs.push_back(chunk_gate(g));
-  if (!forward) std::reverse(gs.begin(), gs.end());
+  std::vector<PermItem> items = perm_items(run);
+  if (!forward) {
+    std::reverse(items.begin(), items.end());
+    for (PermItem& it : items) it.neg ^= (int)it.add;
+  }
   size_t i = 0;
-  while (i < gs.size()) {
+  while (i < items.size()) {
+    if (items[i].add) {
+      PermSeg ps{};
+      ps.kind = 2;
+      ps.base = (uint8_t)items[i].base;
+      ps.width = (uint8_t)items[i].width;
+      ps.neg = (uint8_t)items[i].neg;
+      ps.m = items[i].m;
+      ps.v = items[i].v;
+      out.push_back(ps);
+      p->stats.segments++;
+      ++i;
+      continue;
+    }
     std::vector<ChunkGate> seg;
     uint32_t sup = 0;
     KeyWin win{};
-    while (i < gs.size()) {
-      const uint32_t ns = sup | gs[i].m | gs[i].t;
+    while (i < items.size() && !items[i].add) {
+      const uint32_t ns = sup | items[i].m | items[i].t;
       KeyWin nw;
-      if (!cover2(ns, kMaxKeyBits, &nw)) {
-        if (seg.empty()) {
-          std::fprintf(stderr, "csim fuser: gate support does not fit a table key\n");
-          std::abort();
-        }
-        break;
-      }
+      if (!cover2(ns, max_key_bits(), &nw)) break;
       sup = ns;
       win = nw;
-      seg.push_back(gs[i]);
+      seg.push_back(ChunkGate{items[i].m, items[i].v, items[i].t});
       ++i;
+    }
+    if (seg.empty()) {  // this gate alone exceeds a table key: apply it directly
+      PermSeg ps{};
+      ps.kind = 1;
+      ps.m = items[i].m;
+      ps.v = items[i].v;
+      ps.t = items[i].t;
+      out.push_back(ps);
+      p->stats.segments++;
+      ++i;
+      continue;
+    }
+    if (seg.size() == 1) {  // a single gate is cheaper applied directly
+      PermSeg ps{};
+      ps.kind = 1;
+      ps.m = seg[0].m;
+      ps.v = seg[0].v;
+      ps.t = seg[0].t;
+      out.push_back(ps);
+      p->stats.segments++;
+      continue;
     }
     const int w = win.w0 + win.w1;
     PermSeg ps{};
+    ps.kind = 0;
     ps.win = win;
-    ps.lut_off = (uint32_t)p->lut.size();
+    ps.t = (uint32_t)p->lut.size();
     for (uint32_t key = 0; key < (1u << w); ++key) {
       uint32_t x = win_put(0u, key, win);
       for (const ChunkGate& cg : seg)
@@ -178,7 +293,7 @@ void compile_mux_group(const std::vector<csim_gate>& grp, Program* p, std::vecto
   KeyWin win{};
   for (int b : order) {
     KeyWin nw;
-    if (cover2(keybits | (1u << b), kMaxKeyBits, &nw)) {
+    if (cover2(keybits | (1u << b), max_key_bits(), &nw)) {
       keybits |= 1u << b;
       win = nw;
     }
@@ -416,6 +531,7 @@ void emit_sweep(Program* p, const std::vector<PermSeg>& segs, const std::vector<
     }
     sp.ops[sp.nops++] = o;
   }
+  sp.nmux = nmux;
   Step st;
   st.kind = 0;
   st.param = (int)p->params.size();
@@ -613,7 +729,17 @@ void pair_op(double* a, double* b, int op, double c, double s) {
 uint32_t emu_permute(const Program& p, const SweepParams& sp, uint32_t x) {
   for (int k = 0; k < sp.nseg; ++k) {
     const PermSeg& g = sp.segs[k];
-    x = win_put(x, p.lut[g.lut_off + win_key(x, g.win)], g.win);
+    if (g.kind == 1) {
+      if ((x & g.m) == g.v) x ^= g.t;
+    } else if (g.kind == 2) {
+      if ((x & g.m) == g.v) {
+        const uint32_t rm = (1u << g.width) - 1u;
+        const uint32_t r = (((x >> g.base) & rm) + (g.neg ? rm : 1u)) & rm;
+        x = (x & ~(rm << g.base)) | (r << g.base);
+      }
+    } else {
+      x = win_put(x, p.lut[g.t + win_key(x, g.win)], g.win);
+    }
   }
   return x;
 }

@@ -228,9 +228,26 @@ struct CplxOf<double> {
 };
 
 // Apply the tile-local ops of one sweep to U tiles held by the warp.
+constexpr int kPrefetchMux = 2;
+
+// Bucket words of the first multiplexers of the sweep: they depend only on
+// the destination index, so they are loaded before the permutation chain.
+template <int U>
+__device__ __forceinline__ void prefetch_mux(const SweepParams& a, const uint32_t (&ci)[U],
+                                             uint32_t (&wd)[kPrefetchMux][U]) {
+#pragma unroll
+  for (int m = 0; m < kPrefetchMux; ++m) {
+    if (m >= a.nmux) break;
+    const MuxDesc& md = a.mux[m];
+#pragma unroll
+    for (int u = 0; u < U; ++u) wd[m][u] = __ldg(a.mtab + md.tab_off + win_key(ci[u], md.win));
+  }
+}
+
 template <typename R, int U>
 __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::T (&v)[U][4],
-                                          const uint32_t (&ci)[U], uint32_t lane) {
+                                          const uint32_t (&ci)[U], uint32_t lane,
+                                          const uint32_t (&wd)[kPrefetchMux][U]) {
   using T = typename V2<R>::T;
   for (int k = 0; k < a.nops; ++k) {
     const LocalOp& o = a.ops[k];
@@ -241,7 +258,10 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
       const uint32_t toff = md.tab_off, mt = md.target, mlm = md.lm, mlv = md.lv;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const uint32_t word = __ldg(a.mtab + toff + win_key(ci[u], w));
+        uint32_t word;
+        if (ocm == 0) word = wd[0][u];
+        else if (ocm == 1 && kPrefetchMux > 1) word = wd[1][u];
+        else word = __ldg(a.mtab + toff + win_key(ci[u], w));
         if (word == 0u) continue;
         if (word & 0x80000000u) {
           const T cs = CplxOf<R>::angle(a, word & 0x7fffffffu);
@@ -353,10 +373,25 @@ template <int U>
 __device__ __forceinline__ void permute(const SweepParams& a, uint32_t (&x)[U]) {
   for (int k = 0; k < a.nseg; ++k) {
     const PermSeg& g = a.segs[k];
-    const KeyWin w = g.win;
-    const uint16_t* lut = a.lut + g.lut_off;
+    const uint32_t kind = g.kind, m = g.m, v = g.v, t = g.t;
+    if (kind == 0) {
+      const KeyWin w = g.win;
+      const uint16_t* lut = a.lut + t;
 #pragma unroll
-    for (int u = 0; u < U; ++u) x[u] = win_put(x[u], __ldg(lut + win_key(x[u], w)), w);
+      for (int u = 0; u < U; ++u) x[u] = win_put(x[u], __ldg(lut + win_key(x[u], w)), w);
+    } else if (kind == 1) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if ((x[u] & m) == v) x[u] ^= t;
+    } else {
+      const uint32_t base = g.base, rm = (1u << g.width) - 1u, step = g.neg ? rm : 1u;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if ((x[u] & m) != v) continue;
+        const uint32_t r = (((x[u] >> base) & rm) + step) & rm;
+        x[u] = (x[u] & ~(rm << base)) | (r << base);
+      }
+    }
   }
 }
 
@@ -378,6 +413,8 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const typename V2<R>::
 #pragma unroll
     for (int u = 0; u < U; ++u) mv[u] = ci[u] = ((t0 + u) << 5) | lane;
     T v[U][4];
+    uint32_t wd[kPrefetchMux][U];
+    prefetch_mux<U>(a, ci, wd);
     if (!a.scatter) {
       permute<U>(a, mv);
 #pragma unroll
@@ -386,7 +423,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const typename V2<R>::
 #pragma unroll
         for (int j = 0; j < 4; ++j) v[u][j] = sp[j];
       }
-      apply_ops<R, U>(a, v, ci, lane);
+      apply_ops<R, U>(a, v, ci, lane, wd);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         T* dp = out + ((size_t)ci[u] << 2);
@@ -400,7 +437,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const typename V2<R>::
 #pragma unroll
         for (int j = 0; j < 4; ++j) v[u][j] = sp[j];
       }
-      apply_ops<R, U>(a, v, ci, lane);
+      apply_ops<R, U>(a, v, ci, lane, wd);
       permute<U>(a, mv);
 #pragma unroll
       for (int u = 0; u < U; ++u) {

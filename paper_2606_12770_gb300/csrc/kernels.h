@@ -15,12 +15,17 @@ struct KeyWin {
   uint8_t lo0, w0, lo1, w1;
 };
 
-// A run of multi-controlled X gates compiled to a lookup table over the
-// key windows that hold every chunk-index bit the gates read or write: the
-// table maps the window bits of an index to the window bits of its image.
+// One step of a compiled permutation (chunk-index space):
+//  kind 0: a run of multi-controlled X gates as a lookup table over the key
+//          windows holding every bit the gates read or write; the table maps
+//          the window bits of an index to those of its image (offset t);
+//  kind 1: one gate applied directly: if ((x & m) == v) x ^= t;
+//  kind 2: a controlled increment (neg = 0) or decrement (neg = 1) of the
+//          register of `width` bits at `base`: if ((x & m) == v) r = r +- 1.
 struct PermSeg {
   KeyWin win;
-  uint32_t lut_off;  // into the uint16 table array
+  uint8_t kind, base, width, neg;
+  uint32_t m, v, t;
 };
 
 // One gate inside the 128-amplitude warp tile.  Controls are split into the
@@ -71,9 +76,9 @@ struct ReflectDesc {
 // Everything one sweep launch needs, passed by value in the kernel parameter
 // block (constant bank): the permutation segments, the tile-local ops and
 // their descriptors.  Large tables stay in global memory.
-constexpr int kMaxSeg = 16, kMaxOps = 40, kMaxRefl = 4, kMaxMux = 8;
+constexpr int kMaxSeg = 32, kMaxOps = 40, kMaxRefl = 4, kMaxMux = 8;
 struct SweepParams {
-  int nseg, nops, scatter, pad;
+  int nseg, nops, scatter, nmux;
   PermSeg segs[kMaxSeg];
   LocalOp ops[kMaxOps];
   ReflectDesc refl[kMaxRefl];
