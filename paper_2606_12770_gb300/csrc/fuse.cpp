@@ -106,10 +106,13 @@ struct PermItem {
 
 // Recognise controlled increment / decrement cascades of a contiguous
 // register: gates X(r[j] | C, r[0..j-1] all 1 (or all 0)) for j = w-1..0.
+// Off by default (CSIM_PERM_ADD=1 enables): measured slower than tables on
+// the QSVT circuit because the arithmetic steps cost more issue slots than the
+// table lookups they replace.
 bool recognise_adds() {
   static const bool v = [] {
     const char* e = std::getenv("CSIM_PERM_ADD");
-    return !(e && e[0] == '0');
+    return e && e[0] == '1';
   }();
   return v;
 }

@@ -178,6 +178,42 @@ __device__ __forceinline__ void rot(T& a, T& b, R c, R s) {
   a = na;
 }
 
+// Load / store the 4-amplitude chunk of one lane with 16-byte vector accesses.
+// Loads skip L1 (the state streams; L1 is left to the lookup tables).
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  float4 r;
+  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(p));
+  return r;
+}
+__device__ __forceinline__ double2 ld_stream(const double2* p) {
+  double2 r;
+  asm volatile("ld.global.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ void load_chunk(const float2* base, float2 (&v)[4]) {
+  const float4* p = reinterpret_cast<const float4*>(base);
+  const float4 a = ld_stream(p), b = ld_stream(p + 1);
+  v[0] = make_float2(a.x, a.y);
+  v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y);
+  v[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load_chunk(const double2* base, double2 (&v)[4]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = ld_stream(base + j);
+}
+__device__ __forceinline__ void store_chunk(float2* base, const float2 (&v)[4]) {
+  float4* p = reinterpret_cast<float4*>(base);
+  p[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+  p[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+}
+__device__ __forceinline__ void store_chunk(double2* base, const double2 (&v)[4]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) base[j] = v[j];
+}
+
 // RY(c, s) on both in-thread pairs of target bit mt whose other low bit
 // satisfies the controls (mlm, mlv).
 template <typename T, typename R>
@@ -418,33 +454,17 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const typename V2<R>::
     if (!a.scatter) {
       permute<U>(a, mv);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const T* sp = in + ((size_t)mv[u] << 2);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[u][j] = sp[j];
-      }
+      for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)mv[u] << 2), v[u]);
       apply_ops<R, U>(a, v, ci, lane, wd);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        T* dp = out + ((size_t)ci[u] << 2);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) dp[j] = v[u][j];
-      }
+      for (int u = 0; u < U; ++u) store_chunk(out + ((size_t)ci[u] << 2), v[u]);
     } else {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const T* sp = in + ((size_t)ci[u] << 2);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[u][j] = sp[j];
-      }
+      for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)ci[u] << 2), v[u]);
       apply_ops<R, U>(a, v, ci, lane, wd);
       permute<U>(a, mv);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        T* dp = out + ((size_t)mv[u] << 2);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) dp[j] = v[u][j];
-      }
+      for (int u = 0; u < U; ++u) store_chunk(out + ((size_t)mv[u] << 2), v[u]);
     }
   }
 }
@@ -587,7 +607,8 @@ SweepCfg sweep_cfg() {
     SweepCfg c{1, 1, 1};
     if (const char* e = std::getenv("CSIM_SWEEP_CFG")) {
       int u = 0, m = 0;
-      if (std::sscanf(e, "%d,%d", &u, &m) == 2 && (u == 1 || u == 2 || u == 4) && (m == 1 || m == 2)) {
+      if (std::sscanf(e, "%d,%d", &u, &m) == 2 && (u == 1 || u == 2 || u == 4) &&
+          (m == 1 || m == 2 || m == 4)) {
         c.u64 = u;
         c.u128 = u;
         c.minb = m;
@@ -610,6 +631,10 @@ template <typename R>
 void launch_sweep_r(const void* in, void* out, uint32_t ntiles, int u, int minb, const SweepParams& a,
                     cudaStream_t st) {
   while ((uint32_t)u > ntiles) u >>= 1;
+  if (minb == 4) {
+    if (u == 2) return launch_sweep_t<R, 2, 4>(in, out, ntiles, a, st);
+    return launch_sweep_t<R, 1, 4>(in, out, ntiles, a, st);
+  }
   if (minb == 2) {
     if (u == 4) return launch_sweep_t<R, 4, 2>(in, out, ntiles, a, st);
     if (u == 2) return launch_sweep_t<R, 2, 2>(in, out, ntiles, a, st);

@@ -273,7 +273,7 @@ print("ok")
 
 
 @pytest.mark.parametrize("form", ["gather", "scatter"])
-@pytest.mark.parametrize("cfg", ["1,1", "2,1", "4,1", "1,2", "2,2", "4,2"])
+@pytest.mark.parametrize("cfg", ["1,1", "2,1", "4,1", "1,2", "2,2", "4,2", "1,4", "2,4"])
 def test_sweep_kernel_variants(cfg, form):
     """Every compiled sweep-kernel variant (tiles per iteration, blocks per SM, form)."""
     import os
