@@ -317,6 +317,34 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
     if (op == 5) {  // I (x) A + J (x) B over the lane bits of lanemask
       const ReflectDesc& rd = a.refl[ocm];
       const uint32_t lmask = rd.lanemask, nzA = rd.nzA, nzB = rd.nzB;
+      if (((nzA | nzB) & ~0x8421u) == 0) {  // A and B diagonal
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const int q = y * 5;
+            T S = v[u][y];
+            if ((nzB >> q) & 1u) {
+#pragma unroll
+              for (int b = 0; b < 5; ++b) {
+                if (!((lmask >> b) & 1u)) continue;
+                const T w = shfl_xor_c(S, 1 << b);
+                S.x += w.x;
+                S.y += w.y;
+              }
+            }
+            const T ca = CplxOf<R>::a(rd, q), cb = CplxOf<R>::b(rd, q);
+            const T x = v[u][y];
+            T o = mk<T>(ca.x * x.x - ca.y * x.y, ca.x * x.y + ca.y * x.x);
+            if ((nzB >> q) & 1u) {
+              o.x += cb.x * S.x - cb.y * S.y;
+              o.y += cb.x * S.y + cb.y * S.x;
+            }
+            v[u][y] = o;
+          }
+        }
+        continue;
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         T S[4];
