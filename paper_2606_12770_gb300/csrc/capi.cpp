@@ -398,9 +398,21 @@ csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_
   pat.insert(pat.end(), c->pv.begin(), c->pv.end());
   cudaError_t e = cudaMemcpyAsync(c->d_pat, pat.data(), pat.size() * sizeof(uint64_t),
                                   cudaMemcpyHostToDevice, c->stream);
+  // low index bits fixed (to the same value) by every pattern
+  int lowk = 0;
+  uint64_t lowv = 0;
+  while (lowk < L.n) {
+    const uint64_t b = 1ull << lowk;
+    bool all = true;
+    for (int k = 0; k < npat; ++k)
+      all = all && (c->pm[k] & b) && ((c->pv[k] & b) == (c->pv[0] & b));
+    if (!all) break;
+    lowv |= c->pv[0] & b;
+    ++lowk;
+  }
   if (e == cudaSuccess)
-    e = csim::launch_norms(c->buf[c->cur], c->prec, L.n, c->d_pat, c->d_pat + npat, npat,
-                           c->d_partial, c->d_out, c->stream);
+    e = csim::launch_norms(c->buf[c->cur], c->prec, L.n, c->d_pat, c->d_pat + npat, npat, lowk,
+                           lowv, c->d_partial, c->d_out, c->stream);
   double h[2] = {0, 0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h, c->d_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream);

@@ -498,19 +498,47 @@ __global__ void __launch_bounds__(256, MINB) sweep_kernel(const typename V2<R>::
 }
 
 // --------------------------------------------------------------- reductions
+// |a|^2 of one 16-byte vector of the state: two complex64 amplitudes (each
+// product in FP32, matching the data's precision) or one complex128.
+__device__ __forceinline__ double vec_norm2(const float4 v) {
+  return (double)(v.x * v.x + v.y * v.y) + (double)(v.z * v.z + v.w * v.w);
+}
+__device__ __forceinline__ double vec_norm2(const double2 v) { return v.x * v.x + v.y * v.y; }
+
+template <typename R>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+};
+
+// FP64 sums: the total over the state (streamed as 16-byte vectors) and the
+// sum over the pattern mask.  When every pattern fixes the `lowk` lowest index
+// bits to `lowv`, only the indices lowv + j 2^lowk are candidates.
 template <typename R>
 __global__ void norm_kernel(const typename V2<R>::T* __restrict__ st, uint64_t N,
                             const uint64_t* __restrict__ pm, const uint64_t* __restrict__ pv,
-                            int npat, double* __restrict__ partial) {
+                            int npat, int lowk, uint64_t lowv, double* __restrict__ partial) {
+  using VT = typename Vec16<R>::T;
   double tot = 0.0, sel = 0.0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-    const auto a = st[i];
-    const double p = (double)a.x * (double)a.x + (double)a.y * (double)a.y;
-    tot += p;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const VT* vp = reinterpret_cast<const VT*>(st);
+  const uint64_t nv = N * sizeof(typename V2<R>::T) / sizeof(VT);
+  for (uint64_t i = tid; i < nv; i += stride) tot += vec_norm2(__ldcs(vp + i));
+  const uint64_t ncand = N >> lowk;
+  for (uint64_t j = tid; j < ncand; j += stride) {
+    const uint64_t i = lowv | (j << lowk);
     bool hit = false;
     for (int k = 0; k < npat; ++k) hit |= ((i & pm[k]) == pv[k]);
-    if (hit) sel += p;
+    if (hit) {
+      const auto a = st[i];
+      sel += (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+    }
   }
   __shared__ double sh[2][32];
   for (int o = 16; o > 0; o >>= 1) {
@@ -632,7 +660,7 @@ struct SweepCfg {
 
 SweepCfg sweep_cfg() {
   static SweepCfg cfg = [] {
-    SweepCfg c{1, 1, 1};
+    SweepCfg c{2, 2, 4};
     if (const char* e = std::getenv("CSIM_SWEEP_CFG")) {
       int u = 0, m = 0;
       if (std::sscanf(e, "%d,%d", &u, &m) == 2 && (u == 1 || u == 2 || u == 4) &&
@@ -689,17 +717,18 @@ cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const Sweep
 int norm_partials_needed() { return 2048; }
 
 cudaError_t launch_norms(const void* state, int prec, int n, const uint64_t* d_pm,
-                         const uint64_t* d_pv, int npat, double* d_partial, double* d_out,
-                         cudaStream_t st) {
+                         const uint64_t* d_pv, int npat, int lowk, uint64_t lowv, double* d_partial,
+                         double* d_out, cudaStream_t st) {
   const uint64_t N = 1ull << n;
   const int blk = 256;
-  int grd = grid_for(N, blk);
+  int grd = grid_for(N / 2, blk);
   if (grd > norm_partials_needed()) grd = norm_partials_needed();
   if (prec == CSIM_C64)
-    norm_kernel<float><<<grd, blk, 0, st>>>((const float2*)state, N, d_pm, d_pv, npat, d_partial);
+    norm_kernel<float><<<grd, blk, 0, st>>>((const float2*)state, N, d_pm, d_pv, npat, lowk, lowv,
+                                            d_partial);
   else
-    norm_kernel<double><<<grd, blk, 0, st>>>((const double2*)state, N, d_pm, d_pv, npat,
-                                             d_partial);
+    norm_kernel<double><<<grd, blk, 0, st>>>((const double2*)state, N, d_pm, d_pv, npat, lowk,
+                                             lowv, d_partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   reduce_partials_kernel<<<1, 32, 0, st>>>(d_partial, grd, d_out);

@@ -97,9 +97,11 @@ cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaSt
 cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
                          cudaStream_t st);
 int norm_partials_needed();
+// FP64 total norm and masked norm.  Every pattern must fix the lowk lowest
+// index bits to the value lowv (lowk = 0 checks every index).
 cudaError_t launch_norms(const void* state, int prec, int n, const uint64_t* d_pm,
-                         const uint64_t* d_pv, int npat, double* d_partial, double* d_out,
-                         cudaStream_t st);
+                         const uint64_t* d_pv, int npat, int lowk, uint64_t lowv, double* d_partial,
+                         double* d_out, cudaStream_t st);
 cudaError_t launch_compact(const void* state, int prec, double* d_out, uint64_t count,
                            int free_shift, int free_bits, uint64_t m_first, int m_shift,
                            cudaStream_t st);
