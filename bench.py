@@ -54,6 +54,8 @@ DEFAULT = "precision-nx64-k4-nt16-d13-c64"
 # A changed kernel source reports null traffic until it is captured again.
 NCU_TRAFFIC = {}
 
+L2_BYTES = 129 * 1000 * 1000
+
 
 def kernel_hash():
     p = os.path.join(ROOT, "paper_2606_12770_gb300", "csrc", "kernels.cu")
@@ -288,7 +290,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "Nx": Nx, "N_C": NC, "K": K, "Nt": Nt, "dt": dt,
                    "tau": tau, "d": info["d"], "qubits": n, "exec": args.exec,
-                   "state_bytes": (1 << n) * esz, "l2": "inputs larger than L2 (state >> 129 MB)",
+                   "state_bytes": (1 << n) * esz,
+                   "l2": ("inputs larger than L2 (state >> 129 MB)" if ((1 << n) * esz) > L2_BYTES
+                          else "state resident in L2 (smaller than 129 MB); no flush"),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
