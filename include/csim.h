@@ -192,6 +192,41 @@ csim_status csim_sv_free(csim_sv* sv);
 csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n, double* amps,
                                int64_t* stats);
 
+/* --- reduction for callers that cannot allocate -------------------------- */
+
+/* csim_norms_noalloc has no counterpart in the paper.  It is the FP64
+ * reduction of csim_postselect, offered to callers that cannot call cudaMalloc:
+ * code inside another framework's memory pool that forbids side allocations,
+ * or a host that keeps its device footprint fixed after start-up.  The call
+ * allocates nothing.  Its per-block partial sums live in a fixed library array
+ * of 2048 (total, masked) pairs, 32 KiB, which every GPU that loads the library
+ * holds until the process exits.
+ *
+ * d_state: 2^n amplitudes on the current device, complex64 (float2) or
+ * complex128 (double2) as `prec` says, 16-byte aligned; n in [1, 34].
+ * pm, pv: host arrays of npat masks and values (0 <= npat <= 16); an index i
+ * is selected when (i & pm[k]) == pv[k] for some k (csim_export_mask gives the
+ * circuit's postselection patterns).
+ * d_out: device memory for 2 doubles, receiving sum |a|^2 over the whole state
+ * and over the selected indices.
+ * The work is enqueued on cuda_stream (NULL = the legacy default stream); the
+ * call does not synchronise.  The caller owns d_state, d_out and the host
+ * arrays, which only need to stay valid for the call itself.
+ *
+ * Errors: CSIM_ERR_TOO_LARGE for n > 34 or more than 16 patterns; CSIM_ERR_ARG
+ * for null or misaligned pointers, n < 1, or a value outside its mask;
+ * CSIM_ERR_CUDA when the launch or the set-up fails.
+ *
+ * The first call on each device looks up the array's device address with that
+ * device current.  That lookup can load the library's module, so make the
+ * first call on each device before any stream capture begins.  Every call
+ * shares the one array per device and leaves its partial sums there.  Nothing
+ * in it has to start at zero, but calls that overlap on the GPU (on different
+ * streams of one device) race on it. */
+csim_status csim_norms_noalloc(const void* d_state, int32_t n, csim_precision prec,
+                               const uint64_t* pm, const uint64_t* pv, int32_t npat,
+                               double* d_out, void* cuda_stream);
+
 const char* csim_last_error(void);
 
 #ifdef __cplusplus

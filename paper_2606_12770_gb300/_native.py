@@ -28,7 +28,7 @@ EXPORTED = [
     "csim_export_mask", "csim_init", "csim_set_exec", "csim_run", "csim_sync",
     "csim_postselect", "csim_read_state", "csim_free", "csim_sv_create", "csim_sv_load",
     "csim_sv_compile", "csim_sv_run", "csim_sv_read", "csim_sv_info", "csim_sv_free",
-    "csim_emulate_fused", "csim_last_error",
+    "csim_emulate_fused", "csim_last_error", "csim_norms_noalloc",
 ]
 
 
@@ -102,6 +102,8 @@ def load():
         "csim_sv_free": ([VP], C.c_int),
         "csim_emulate_fused": ([VP, SZ, C.c_int32, DP, P(C.c_int64)], C.c_int),
         "csim_last_error": ([], C.c_char_p),
+        "csim_norms_noalloc": ([VP, C.c_int32, C.c_int, P(C.c_uint64), P(C.c_uint64), C.c_int32,
+                                DP, VP], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -296,3 +298,19 @@ def gates_to_records(gates) -> np.ndarray:
     for i, g in enumerate(gates):
         out[i] = (g[0], g[1], g[5] if len(g) > 5 else 0, 0, g[2], g[3], g[4])
     return out
+
+
+def norms_noalloc(state_ptr, n, prec, pm, pv, out_ptr, stream=None):
+    """csim_norms_noalloc: FP64 (total, masked) norms of a caller-owned device
+    state into the caller's 2-double device buffer `out_ptr`, with no device
+    allocation by the library (for callers that cannot allocate)."""
+    lib = load()
+    m = np.ascontiguousarray(pm, dtype=np.uint64)
+    v = np.ascontiguousarray(pv, dtype=np.uint64)
+    if m.shape != v.shape:
+        raise ValueError("pm and pv differ in length")
+    _check(lib.csim_norms_noalloc(C.c_void_p(int(state_ptr)), int(n), int(prec),
+                                  m.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                  v.ctypes.data_as(C.POINTER(C.c_uint64)), int(m.shape[0]),
+                                  C.cast(C.c_void_p(int(out_ptr)), C.POINTER(C.c_double)),
+                                  _stream_handle(stream)))

@@ -28,6 +28,12 @@ csim_status cuda_fail(cudaError_t e, const char* where) {
 }
 }  // namespace
 
+namespace csim {
+// Lets entry points defined in other translation units set the message that
+// csim_last_error returns on this thread.
+void record_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace csim
+
 struct csim_circuit {
   Layout L;
   double tau = 0, dt = 0, eps = 1e-3, kappa = 0, scale = 0, Lmax = 0, lambda = 0;
