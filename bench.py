@@ -49,6 +49,19 @@ WORKLOADS = {
 }
 DEFAULT = "precision-nx64-k4-nt16-d13-c64"
 
+# Batching: count seeded instances (lbm_inputs.batch_instance), complex64,
+# run through the request pool; serving: a bounded prefix of the seeded
+# request stream (lbm_inputs.serving_requests) with Poisson arrivals.
+BATCH = {"batch-256-c64": 256}
+SERVING = {"serving-poisson-200": 200}
+
+# Gate-vocabulary microbenchmark: (qubits, gates, seed); complex64, seeded
+# random normalised initial state generated on the device.
+MICRO = {
+    "microbench-n30-c64": (30, 1000, 0),
+    "microbench-n33-c64": (33, 1000, 0),
+}
+
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one sweep_kernel launch,
 # keyed by the sha256 of kernels.cu at capture time (profiles/ has the summary).
 # A changed kernel source reports null traffic until it is captured again.
@@ -157,6 +170,349 @@ def oracle_sample(seconds_target=15.0):
                       f"32-qubit state does not fit the oracle"}
 
 
+def oracle_micro_sample(n, seconds_target=12.0):
+    """Naive FP64 simulator on a bounded prefix of the vocabulary stream at n qubits."""
+    from oracle import statevec as S
+
+    gates = I.microbench_gates(n, 1000, 0)
+    psi = I.random_unit_state(n, 0)
+    sim = S.DenseSim(n)
+    upd = 0.0
+    count = 0
+    t0 = time.perf_counter()
+    for g in gates:
+        sim.apply(psi, g)
+        upd += 2.0 ** (n - bin(g[2]).count("1"))
+        count += 1
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {count} gates of the vocabulary stream at {n} qubits through the "
+                      f"naive FP64 gate-by-gate simulator, {dt:.1f} s (the benchmark's 2^30/2^33 "
+                      f"states do not fit the oracle's FP64 copies in host memory in that time)"}
+
+
+def run_micro(args, rank, world, local, torch, G, dist):
+    """One step = the whole 1000-gate vocabulary stream over the resident state."""
+    n, count, seed = MICRO[args.workload]
+    gates = I.microbench_gates(n, count, seed)
+    records = G.gates_to_records(gates)
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed + rank)
+    x = torch.randn((1 << n, 2), generator=gen, device="cuda", dtype=torch.float32)
+    x /= torch.linalg.vector_norm(x)
+    sv = G.StateVector(n, G.CSIM_C64, stream)
+    sv.load_device(x.data_ptr())
+    del x
+    torch.cuda.empty_cache()
+    mode = G.CSIM_EXEC_FUSED if args.exec == "fused" else G.CSIM_EXEC_GATE
+    sv.compile(records, mode)
+    st = sv.stats()
+    for _ in range(max(args.warmup, 0)):
+        sv.run()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for a, b in ev:
+        a.record(stream)
+        sv.run()
+        b.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    value = st["amp_updates"] * world / (ms / 1000.0)
+    # end to end through the public API: compile the host gate list (fusing and
+    # table upload), run, and read back the FP64 norm of the result
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sv.compile(records, mode)
+        sv.run()
+        G._native.norms_noalloc(sv.device_state().ptr, n, G.CSIM_C64, [], [], out.data_ptr(), stream)
+        float(out[0].item())
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    peaks, peak_kind = measured_peaks()
+    alg_bytes = 2.0 * st["pass_amps"] * 8
+    achieved = alg_bytes / (ms / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "complex64 (fp32)",
+        "data": "synthetic (seeded gate stream; seeded random normalised state)",
+        "config": {"workload": args.workload, "qubits": n, "gates": len(gates), "exec": args.exec,
+                   "passes": st["passes"], "fused_sweeps": st["sweeps"],
+                   "single_gate_passes": st["single"], "state_bytes": st["state_bytes"],
+                   "l2": "inputs larger than L2 (state >> 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "all passes of the run (sweep_kernel and gate_kernel)",
+                     "peak_kind": f"{peak_kind} (STREAM-style copy)",
+                     "alg_bytes_per_run": alg_bytes, "launches_per_step": st["passes"]},
+        "e2e": {"value": st["amp_updates"] * world / (statistics.median(e2e_ms) / 1000.0),
+                "unit": UNIT, "h2d_bytes_per_step": int(records.nbytes), "d2h_bytes_per_step": 8},
+        "gpu_launches": args.steps * st["passes"],
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_micro_sample(22)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _build_parallel(G, specs, workers=8):
+    """Build and host-compile circuits in parallel threads (the C calls release
+    the GIL).  specs: list of (cfg, d)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(spec):
+        cfg, d = spec
+        c = G.Circuit(*cfg, kappa_qsvt=10.0, d=d)
+        c.compile()
+        return c
+
+    with ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(one, specs))
+
+
+def _pool_budget(torch, cap_bytes):
+    free, _ = torch.cuda.mem_get_info()
+    return int(min(cap_bytes, 0.85 * free))
+
+
+def _finish_line(args, line, world, dist):
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_batch(args, rank, world, local, torch, G, dist):
+    """One step = all instances submitted at once to the request pool, polled
+    until every result (norms and compacted block, copied to pinned host
+    memory) is back.  Host wall clock around the step (the pool spreads the
+    work over its own streams)."""
+    count = BATCH[args.workload]
+    insts = [I.batch_instance(i + rank * count) for i in range(count)]
+    circs = _build_parallel(G, [(cfg, d) for cfg, d, _ in insts])
+    amp_updates = 0.0
+    alg_bytes = 0.0
+    launches = 0
+    for c in circs:
+        inf = c.info()
+        amp_updates += inf["amp_updates_run"]
+        alg_bytes += 2.0 * inf["n_sweeps_run"] * (1 << inf["n_qubits"]) * 8
+        launches += inf["n_sweeps_run"] + 4  # init, sweeps, norms + reduce, compaction
+    budget = _pool_budget(torch, 200 << 30)
+
+    def pool_step(pool):
+        t0 = time.perf_counter()
+        ids = [pool.submit(c, f0, G.CSIM_C64) for c, (_, _, f0) in zip(circs, insts)]
+        left = set(ids)
+        while left:
+            for rid in pool.poll(wait_ms=5):
+                pool.result(rid, want_amplitudes=False)
+                left.discard(rid)
+        return time.perf_counter() - t0
+
+    results = {}
+    clk = None
+    graph_error = None
+    for graphs in (False, True):
+        pool = G.Pool(n_streams=8, hbm_budget=budget, max_qubits=32, use_graphs=graphs)
+        try:
+            for _ in range(max(args.warmup, 1)):
+                pool_step(pool)
+        except G.CsimError as e:
+            if not graphs:
+                raise
+            graph_error = str(e)
+            pool.close()
+            break
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        if dist is not None:
+            dist.barrier()
+        ts = [pool_step(pool) for _ in range(args.steps)]
+        c2 = clocks.stop()
+        clk = clk or c2
+        st = pool.stats()
+        pool.close()
+        results["graphs" if graphs else "streams"] = (statistics.median(ts), st)
+    # the per-instance loop: one instance at a time through csim_init/run/postselect
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, (_, _, f0) in zip(circs, insts):
+        c.init(f0, G.CSIM_C64)
+        c.run()
+        c.postselect(want_amplitudes=False)
+        c.close()  # frees the instance's state buffers before the next one
+    loop_s = time.perf_counter() - t0
+    best = min(results, key=lambda k: results[k][0])
+    step_s, st = results[best]
+    if dist is not None:
+        t = torch.tensor([step_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_s = float(t.item())
+    peaks, peak_kind = measured_peaks()
+    achieved = alg_bytes / step_s / 1e9
+    line = {
+        "metric": METRIC, "value": amp_updates * world / step_s, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * step_s,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "complex64 (fp32)", "data": "synthetic (seeded instances 0..255)",
+        "config": {"workload": args.workload, "instances": count, "qubits": "23-29",
+                   "mode": f"request pool, 8 streams, {best}",
+                   "runs_per_s": count * world / step_s,
+                   "streams_step_s": results["streams"][0],
+                   "graphs_step_s": results["graphs"][0] if "graphs" in results else graph_error,
+                   "per_instance_loop_s": loop_s,
+                   "pool_budget_bytes": st["budget"], "pool_peak_bytes": st["peak_bytes"],
+                   "timing": "host wall clock per step (work spread over the pool's streams)",
+                   "l2": "inputs larger than L2 (states 64 MB-4 GB each, 0.5 TB in total)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "sweep_kernel (all instances, aggregate)",
+                     "peak_kind": f"{peak_kind} (STREAM-style copy)",
+                     "alg_bytes_per_step": alg_bytes},
+        "e2e": {"value": amp_updates * world / step_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(16 * (3 * cfg[0] + 9 * cfg[0] ** 2) for cfg, _, _ in insts)),
+                "d2h_bytes_per_step": 16 * count,
+                "note": "the pool step is already end to end: host f0 in, H2D of b, run, D2H of results"},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+    _finish_line(args, line, world, dist)
+
+
+def run_serving(args, rank, world, local, torch, G, dist):
+    """Poisson arrivals at 0.8 of the measured capacity.  Each request is
+    built and compiled on the host after it arrives (8 builder threads), then
+    submitted to the pool; latency = arrival to result.  Requests above 32
+    qubits (Nx = 256 and 1024, and the largest Nx = 64 ones) are rejected."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    count = SERVING[args.workload]
+    reqs = I.serving_requests(count, 0)
+    budget = _pool_budget(torch, 220 << 30)
+    pool = G.Pool(n_streams=4, hbm_budget=budget, max_qubits=32, use_graphs=False)
+    precs = {"c64": G.CSIM_C64, "c128": G.CSIM_C128}
+
+    def build(r):
+        """The request's circuit, or None when it cannot be built at all (more
+        qubits than the library's 34-qubit limit)."""
+        try:
+            c = G.Circuit(r["Nx"], r["tau"], 2, r["K"], 0.1, r["Nt"], kappa_qsvt=10.0, d=r["d"])
+        except G.CsimError:
+            return None
+        if c.info()["n_qubits"] <= 32:
+            c.compile()
+        return c
+
+    def closed_loop(sub):
+        """All requests at once: requests per second (capacity)."""
+        circs = [build(r) for r in sub]
+        t0 = time.perf_counter()
+        live = set()
+        for r, c in zip(sub, circs):
+            if c is None:
+                continue
+            try:
+                live.add(pool.submit(c, I.serving_f0(r), precs[r["prec"]]))
+            except G.CsimError:
+                pass
+        while live:
+            for rid in pool.poll(wait_ms=5):
+                pool.result(rid, want_amplitudes=False)
+                live.discard(rid)
+        return len(sub) / (time.perf_counter() - t0)
+
+    closed_loop(reqs[:8])  # warm-up: kernels, pinned staging
+    capacity = closed_loop(reqs[:32])
+    rate = 0.8 * capacity
+    arrivals = np.cumsum([r["gap"] for r in reqs]) / rate
+    lat = []
+    rejected = 0
+    amp_upd = 0.0
+    ex = ThreadPoolExecutor(8)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    nxt = 0
+    building = {}
+    live = {}
+    while nxt < count or building or live:
+        now = time.perf_counter() - t0
+        while nxt < count and arrivals[nxt] <= now:
+            building[ex.submit(build, reqs[nxt])] = nxt
+            nxt += 1
+        for fut in [f for f in building if f.done()]:
+            i = building.pop(fut)
+            c = fut.result()
+            if c is None:
+                rejected += 1
+                continue
+            try:
+                rid = pool.submit(c, I.serving_f0(reqs[i]), precs[reqs[i]["prec"]])
+                live[rid] = (i, c)
+            except G.CsimError:
+                rejected += 1
+        for rid in pool.poll(wait_ms=1 if live else 0):
+            i, c = live.pop(rid)
+            pool.result(rid, want_amplitudes=True)
+            lat.append(time.perf_counter() - t0 - arrivals[i])
+            amp_upd += c.info()["amp_updates_run"]
+        if not live and not building and nxt < count:
+            time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ex.shutdown()
+    st = pool.stats()
+    pool.close()
+    lat_ms = sorted(1000.0 * x for x in lat)
+    pct = (lambda q: lat_ms[min(len(lat_ms) - 1, int(q * len(lat_ms)))]) if lat_ms else (lambda q: None)
+    peaks, peak_kind = measured_peaks()
+    line = {
+        "metric": METRIC, "value": amp_upd * world / wall, "unit": UNIT, "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": 1000.0 * wall, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "complex64 and complex128 (50/50)",
+        "data": "synthetic (seeded request stream, seed 0)",
+        "config": {"workload": args.workload, "requests": count, "completed": len(lat),
+                   "rejected_above_32_qubits": rejected, "capacity_req_per_s": capacity,
+                   "arrival_rate_req_per_s": rate, "runs_per_s": len(lat) / wall,
+                   "latency_ms_p50": pct(0.5), "latency_ms_p99": pct(0.99),
+                   "pool_budget_bytes": st["budget"], "pool_peak_bytes": st["peak_bytes"],
+                   "timing": "host wall clock over the serving session",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": None,
+        "e2e": {"value": amp_upd * world / wall, "unit": UNIT, "h2d_bytes_per_step": None,
+                "d2h_bytes_per_step": None, "note": "the session is end to end by construction"},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    _finish_line(args, line, world, dist)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -164,7 +520,10 @@ def run_reference(args, rank, world):
     times = []
     vals = []
     for i in range(W + K):
-        r = oracle_sample(seconds_target=args.ref_seconds)
+        if args.workload in MICRO:
+            r = oracle_micro_sample(22, seconds_target=args.ref_seconds)
+        else:
+            r = oracle_sample(seconds_target=args.ref_seconds)
         if i >= W:
             vals.append(r["value"])
             times.append(args.ref_seconds)
@@ -186,7 +545,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(MICRO) + sorted(BATCH) + sorted(SERVING))
     ap.add_argument("--exec", default="fused", choices=["fused", "gate"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
@@ -207,6 +566,13 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    if args.workload in MICRO:
+        return run_micro(args, rank, world, local, torch, G, dist)
+    if args.workload in BATCH:
+        return run_batch(args, rank, world, local, torch, G, dist)
+    if args.workload in SERVING:
+        return run_serving(args, rank, world, local, torch, G, dist)
 
     Nx, NC, K, Nt, dt, tau, tau_range, seed, d, kappa, prec = WORKLOADS[args.workload]
     f0, tau = I.lbm_instance(Nx, seed + rank * 0, tau=tau, tau_range=tau_range)

@@ -147,6 +147,11 @@ csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec,
 
 csim_status csim_set_exec(csim_circuit* c, csim_exec mode);
 
+/* Compile the circuit's program for the current exec mode on the host (the
+ * fusing that the first csim_run or pool submission would otherwise do); no
+ * GPU work.  Calls on different handles may run in parallel threads. */
+csim_status csim_compile(csim_circuit* c);
+
 /* Enqueue the whole QSVT circuit on the stream.  CSIM_ERR_STATE unless a
  * csim_init has loaded the state since the last run. */
 csim_status csim_run(csim_circuit* c);
@@ -163,6 +168,14 @@ csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_
 /* Copy the whole state to the host as interleaved doubles (2 * 2^n values). */
 csim_status csim_read_state(csim_circuit* c, double* out, size_t cap_amps);
 
+/* Borrowed device pointer to the circuit's current state: 2^n amplitudes,
+ * float2 (complex64) or double2 (complex128) per *prec, index bit b = qubit b.
+ * Valid until the next csim_init, csim_run or csim_free of this handle; the
+ * library keeps ownership.  For reading sampled amplitudes on the device
+ * without a 2^n host copy.  CSIM_ERR_STATE when no state is loaded. */
+csim_status csim_state_device(const csim_circuit* c, void** d_state, int32_t* n,
+                              csim_precision* prec);
+
 csim_status csim_free(csim_circuit* c);
 
 /* --- raw state vectors (microbenchmark and parity tests) ---------------- */
@@ -176,8 +189,27 @@ csim_status csim_sv_compile(csim_sv* sv, const csim_gate* gates, size_t n_gates,
 /* Enqueue the compiled program `reps` times. */
 csim_status csim_sv_run(csim_sv* sv, int32_t reps);
 csim_status csim_sv_read(csim_sv* sv, double* out, size_t n_amps);
+/* Device -> device copy of 2^n amplitudes already in the state's precision
+ * (float2 or double2), e.g. a seeded random state generated on the GPU. */
+csim_status csim_sv_load_device(csim_sv* sv, const void* d_amps, size_t n_amps);
+/* Borrowed device pointer to the current state (valid until the next
+ * csim_sv_run, csim_sv_load* or csim_sv_free). */
+csim_status csim_sv_device(const csim_sv* sv, void** d_state);
 csim_status csim_sv_info(const csim_sv* sv, int64_t* n_sweeps, double* amp_updates,
                          uint64_t* state_bytes);
+/* Program statistics of the compiled gate list (zeros before a compile).
+ * pass_amps: amplitudes the passes must read and write at minimum, 2^n per
+ * fused sweep and the changed amplitudes per single-gate pass, so that
+ * 2 * pass_amps * (8 or 16 bytes) is the algorithmic HBM traffic of one run. */
+typedef struct {
+  int64_t passes;       /* kernel launches (HBM passes) per run */
+  int64_t sweeps;       /* of which fused sweeps */
+  int64_t single;       /* of which single-gate passes */
+  double amp_updates;   /* sum over gates of the amplitudes each gate changes */
+  double pass_amps;
+  uint64_t state_bytes;
+} csim_sv_stats_t;
+csim_status csim_sv_stats(const csim_sv* sv, csim_sv_stats_t* out);
 csim_status csim_sv_free(csim_sv* sv);
 
 /* Host-only reference executor of the fused-program format: compiles the gate
@@ -191,6 +223,64 @@ csim_status csim_sv_free(csim_sv* sv);
  * table entries, largest table support, HBM passes, averaging blocks. */
 csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n, double* amps,
                                int64_t* stats);
+
+/* --- request pool: batching and serving ----------------------------------- */
+
+/* Many independent runs (instances or serving requests) on one GPU.  The pool
+ * owns an arena of hbm_budget bytes (a buddy allocator over power-of-two
+ * blocks: each request takes its two state buffers, the compacted block and
+ * the staging of b) and n_streams CUDA streams.  Queued requests are admitted
+ * in submission order whenever a stream is free and the head request's blocks
+ * fit; finished requests release their blocks at the next csim_pool_poll, so
+ * new work is admitted continuously.  With use_graphs, the requests admitted in
+ * one pass are captured into one CUDA graph (a branch per request) and
+ * launched once.  A pool is used from one thread at a time.  A circuit stays
+ * borrowed while it has requests in the pool: do not csim_free it or change
+ * its exec mode until their results are taken. */
+typedef struct csim_pool csim_pool;
+typedef struct {
+  int32_t n_streams;    /* concurrent requests; <= 0: 4 (max 64) */
+  int32_t max_qubits;   /* larger circuits are rejected; <= 0: 32 */
+  uint64_t hbm_budget;  /* arena bytes; 0: 90% of the free device memory */
+  int32_t use_graphs;   /* 1: one CUDA graph launch per admission pass */
+  uint32_t min_block;   /* smallest arena block in bytes; 0: 1 MiB */
+} csim_pool_opts;
+typedef struct {
+  int64_t submitted, admitted, completed, rejected, queued, running;
+  uint64_t bytes_in_use, peak_bytes, budget;
+  int64_t graph_launches; /* admission passes launched as one CUDA graph */
+} csim_pool_stats_t;
+
+csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out);
+/* Queue one run of circuit c (QSVT circuit on b from f0, as csim_init +
+ * csim_run + csim_postselect) and try to admit.  f0 is copied.  *id receives
+ * the request id.  CSIM_ERR_TOO_LARGE (counted as rejected) when the circuit
+ * exceeds max_qubits or its blocks cannot fit the arena. */
+csim_status csim_pool_submit(csim_pool* p, csim_circuit* c, const double* f0,
+                             csim_precision prec, int64_t* id);
+/* Retire finished requests and admit queued ones.  wait_ms > 0 blocks until a
+ * request finishes or the time passes.  Writes up to cap ids of requests
+ * finished since the last poll to done (NULL: keep them for later). */
+csim_status csim_pool_poll(csim_pool* p, int32_t wait_ms, int64_t* done, size_t cap,
+                           size_t* n_done);
+/* Results of a finished request, as csim_postselect; times (may be NULL)
+ * receives 3 doubles in seconds: queueing (submit to admission), submit to
+ * retirement, device time of the request.  Releases the request record. */
+csim_status csim_pool_result(csim_pool* p, int64_t id, double* p_success, double* norm_total,
+                             double* out_amps, size_t cap, size_t* len, double* times);
+csim_status csim_pool_stats(const csim_pool* p, csim_pool_stats_t* out);
+/* Waits for running work, then frees everything (pending results are lost). */
+csim_status csim_pool_free(csim_pool* p);
+
+/* The pool's admission policy on a simulated clock (host only, no GPU):
+ * request i arrives at arrival[i] (NULL: all at 0), needs the 4 blocks
+ * alloc_bytes[4i..4i+3] (0 = none) and runs for duration[i].  Writes start[i]
+ * and finish[i] (-1 for a request that cannot fit an empty arena) and the
+ * peak arena bytes in use.  For capacity planning and for testing the policy. */
+csim_status csim_pool_plan(uint64_t budget, uint64_t min_block, int32_t n_streams, size_t count,
+                           const uint64_t* alloc_bytes, const double* arrival,
+                           const double* duration, double* start, double* finish,
+                           uint64_t* peak_bytes);
 
 /* --- reduction for callers that cannot allocate -------------------------- */
 

@@ -95,3 +95,48 @@ def microbench_gates(n: int, count: int, seed: int):
                 m = (1 << c) | sum(1 << b for b in reg[:j])
                 out.append((X, reg[j], m, m, 0.0, 0))
     return out
+
+
+def batch_instance(i: int):
+    """Instance i of the 256-instance batching workload (seed i).
+
+    Draw order: Nx from {8, 16, 32}, K from {2, 3, 4}, Nt from {4, 8},
+    tau ~ U[0.55, 1.5], the QSVT degree d from the odd numbers 3..31, then the
+    density noise of the initial condition.  N_C = 2, dt = 0.1.  Returns
+    ((Nx, tau, 2, K, 0.1, Nt), d, f0).
+    """
+    rng = np.random.default_rng(i)
+    Nx = int(rng.choice([8, 16, 32]))
+    K = int(rng.choice([2, 3, 4]))
+    Nt = int(rng.choice([4, 8]))
+    tau = float(rng.uniform(0.55, 1.5))
+    d = int(rng.choice(np.arange(3, 32, 2)))
+    rho = density_profile(Nx, rng)
+    return (Nx, tau, 2, K, 0.1, Nt), d, equilibrium_at_rest(rho)
+
+
+def serving_requests(count: int, seed: int = 0):
+    """The serving request stream (seed 0): for each request, in order, a
+    unit-rate exponential inter-arrival gap (scaled by the caller's arrival
+    rate), Nx from {16, 64, 256, 1024}, K from 2..6, Nt from 4..64, tau ~
+    U[0.55, 1.5], d from the odd numbers 3..31, complex64 or complex128 with
+    probability 1/2, and a per-request seed for the initial density.
+    Returns a list of dicts."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(count):
+        gap = float(rng.exponential(1.0))
+        Nx = int(rng.choice([16, 64, 256, 1024]))
+        K = int(rng.integers(2, 7))
+        Nt = int(rng.integers(4, 65))
+        tau = float(rng.uniform(0.55, 1.5))
+        d = int(rng.choice(np.arange(3, 32, 2)))
+        prec = "c64" if rng.uniform() < 0.5 else "c128"
+        out.append({"gap": gap, "Nx": Nx, "K": K, "Nt": Nt, "tau": tau, "d": d, "prec": prec,
+                    "seed": 1000 + r})
+    return out
+
+
+def serving_f0(req: dict) -> np.ndarray:
+    rng = np.random.default_rng(req["seed"])
+    return equilibrium_at_rest(density_profile(req["Nx"], rng))

@@ -28,7 +28,10 @@ EXPORTED = [
     "csim_export_mask", "csim_init", "csim_set_exec", "csim_run", "csim_sync",
     "csim_postselect", "csim_read_state", "csim_free", "csim_sv_create", "csim_sv_load",
     "csim_sv_compile", "csim_sv_run", "csim_sv_read", "csim_sv_info", "csim_sv_free",
-    "csim_emulate_fused", "csim_last_error", "csim_norms_noalloc",
+    "csim_emulate_fused", "csim_last_error", "csim_norms_noalloc", "csim_state_device",
+    "csim_sv_load_device", "csim_sv_device", "csim_sv_stats", "csim_pool_create",
+    "csim_pool_submit", "csim_pool_poll", "csim_pool_result", "csim_pool_stats", "csim_pool_free",
+    "csim_pool_plan", "csim_compile",
 ]
 
 
@@ -88,6 +91,7 @@ def load():
         "csim_export_mask": ([VP, P(C.c_uint64), P(C.c_uint64), SZ, SZP], C.c_int),
         "csim_init": ([VP, DP, C.c_int, VP], C.c_int),
         "csim_set_exec": ([VP, C.c_int], C.c_int),
+        "csim_compile": ([VP], C.c_int),
         "csim_run": ([VP], C.c_int),
         "csim_sync": ([VP], C.c_int),
         "csim_postselect": ([VP, DP, SZ, SZP, DP, DP], C.c_int),
@@ -102,6 +106,18 @@ def load():
         "csim_sv_free": ([VP], C.c_int),
         "csim_emulate_fused": ([VP, SZ, C.c_int32, DP, P(C.c_int64)], C.c_int),
         "csim_last_error": ([], C.c_char_p),
+        "csim_state_device": ([VP, P(VP), P(C.c_int32), P(C.c_int)], C.c_int),
+        "csim_sv_load_device": ([VP, VP, SZ], C.c_int),
+        "csim_sv_device": ([VP, P(VP)], C.c_int),
+        "csim_sv_stats": ([VP, VP], C.c_int),
+        "csim_pool_create": ([VP, P(VP)], C.c_int),
+        "csim_pool_submit": ([VP, VP, DP, C.c_int, P(C.c_int64)], C.c_int),
+        "csim_pool_poll": ([VP, C.c_int32, P(C.c_int64), SZ, SZP], C.c_int),
+        "csim_pool_result": ([VP, C.c_int64, DP, DP, DP, SZ, SZP, DP], C.c_int),
+        "csim_pool_stats": ([VP, VP], C.c_int),
+        "csim_pool_free": ([VP], C.c_int),
+        "csim_pool_plan": ([C.c_uint64, C.c_uint64, C.c_int32, SZ, P(C.c_uint64), DP, DP, DP, DP,
+                            P(C.c_uint64)], C.c_int),
         "csim_norms_noalloc": ([VP, C.c_int32, C.c_int, P(C.c_uint64), P(C.c_uint64), C.c_int32,
                                 DP, VP], C.c_int),
     }
@@ -150,6 +166,7 @@ class Circuit:
         h = C.c_void_p()
         _check(lib.csim_build_ex(C.byref(o), C.byref(h)))
         self._h = h
+        self._Nt = int(Nt)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -196,6 +213,10 @@ class Circuit:
         f = np.ascontiguousarray(f0, dtype=np.float64)
         _check(_lib.csim_init(self._h, _dp(f), int(precision), _stream_handle(stream)))
 
+    def compile(self):
+        """Fuse the circuit's program on the host now (releases the GIL)."""
+        _check(_lib.csim_compile(self._h))
+
     def set_exec(self, mode):
         _check(_lib.csim_set_exec(self._h, int(mode)))
 
@@ -218,11 +239,49 @@ class Circuit:
         _check(_lib.csim_postselect(self._h, _dp(out), n.value, C.byref(n), C.byref(p), C.byref(t)))
         return out.view(np.complex128), p.value, t.value
 
+    def device_state(self):
+        """Borrowed view of the current device state (see DeviceState)."""
+        p = C.c_void_p()
+        n = C.c_int32()
+        pr = C.c_int()
+        _check(_lib.csim_state_device(self._h, C.byref(p), C.byref(n), C.byref(pr)))
+        return DeviceState(p.value, n.value, pr.value, self)
+
+    def postselect_count(self) -> int:
+        """Number of amplitudes in the compacted postselected block."""
+        inf = self.info()
+        free_bits = (self._m_shift() - (2 + inf["n_iL"]))
+        return ((1 << inf["n_m"]) - self._Nt) << free_bits
+
+    def _m_shift(self):
+        inf = self.info()
+        return inf["n_qubits"] - inf["n_m"]
+
     def read_state(self) -> np.ndarray:
         N = 1 << self.info()["n_qubits"]
         out = np.zeros(2 * N)
         _check(_lib.csim_read_state(self._h, _dp(out), N))
         return out.view(np.complex128)
+
+
+class SvStats(C.Structure):
+    _fields_ = [("passes", C.c_int64), ("sweeps", C.c_int64), ("single", C.c_int64),
+                ("amp_updates", C.c_double), ("pass_amps", C.c_double), ("state_bytes", C.c_uint64)]
+
+
+class DeviceState:
+    """A borrowed device state exposed through ``__cuda_array_interface__`` as
+    a (2^n, 2) array of float32 (complex64 state) or float64 (complex128 state)
+    (re, im) pairs, so ``torch.as_tensor(ds, device="cuda")`` views it without
+    a copy.  Valid until the owner's next init/run/load/free."""
+
+    def __init__(self, ptr, n, precision, owner):
+        self.ptr, self.n, self.precision, self._owner = int(ptr), int(n), int(precision), owner
+
+    @property
+    def __cuda_array_interface__(self):
+        return {"shape": (1 << self.n, 2), "typestr": "<f4" if self.precision == CSIM_C64 else "<f8",
+                "data": (self.ptr, False), "version": 3, "strides": None}
 
 
 class StateVector:
@@ -234,6 +293,7 @@ class StateVector:
         _check(lib.csim_sv_create(int(n), int(precision), _stream_handle(stream), C.byref(h)))
         self._h = h
         self.n = int(n)
+        self.precision = int(precision)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -249,6 +309,15 @@ class StateVector:
     def load(self, amps):
         a = np.ascontiguousarray(amps, dtype=np.complex128)
         _check(_lib.csim_sv_load(self._h, _dp(a.view(np.float64)), a.shape[0]))
+
+    def load_device(self, ptr):
+        """Copy 2^n amplitudes in this state's precision from device memory at ptr."""
+        _check(_lib.csim_sv_load_device(self._h, C.c_void_p(int(ptr)), 1 << self.n))
+
+    def device_state(self):
+        p = C.c_void_p()
+        _check(_lib.csim_sv_device(self._h, C.byref(p)))
+        return DeviceState(p.value, self.n, self.precision, self)
 
     def compile(self, gates, mode=CSIM_EXEC_FUSED):
         g = gates_to_records(gates)
@@ -269,6 +338,11 @@ class StateVector:
         sb = C.c_uint64()
         _check(_lib.csim_sv_info(self._h, C.byref(ns), C.byref(au), C.byref(sb)))
         return {"n_sweeps": ns.value, "amp_updates": au.value, "state_bytes": sb.value}
+
+    def stats(self):
+        st = SvStats()
+        _check(_lib.csim_sv_stats(self._h, C.cast(C.byref(st), C.c_void_p)))
+        return {k: getattr(st, k) for k, _ in SvStats._fields_}
 
 
 FUSE_STAT_NAMES = ["sweeps", "single", "perm_gates", "segments", "local_gates", "mux",
@@ -314,3 +388,101 @@ def norms_noalloc(state_ptr, n, prec, pm, pv, out_ptr, stream=None):
                                   v.ctypes.data_as(C.POINTER(C.c_uint64)), int(m.shape[0]),
                                   C.cast(C.c_void_p(int(out_ptr)), C.POINTER(C.c_double)),
                                   _stream_handle(stream)))
+
+
+class PoolOpts(C.Structure):
+    _fields_ = [("n_streams", C.c_int32), ("max_qubits", C.c_int32), ("hbm_budget", C.c_uint64),
+                ("use_graphs", C.c_int32), ("min_block", C.c_uint32)]
+
+
+class PoolStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("rejected", C.c_int64), ("queued", C.c_int64), ("running", C.c_int64),
+                ("bytes_in_use", C.c_uint64), ("peak_bytes", C.c_uint64), ("budget", C.c_uint64),
+                ("graph_launches", C.c_int64)]
+
+
+class Pool:
+    """Handle of ``csim_pool``: admission under an HBM budget, concurrent streams,
+    optional CUDA-graph admission waves (batching and serving)."""
+
+    def __init__(self, n_streams=4, hbm_budget=0, max_qubits=32, use_graphs=False, min_block=0):
+        lib = load()
+        o = PoolOpts()
+        o.n_streams, o.hbm_budget, o.max_qubits = int(n_streams), int(hbm_budget), int(max_qubits)
+        o.use_graphs, o.min_block = int(bool(use_graphs)), int(min_block)
+        h = C.c_void_p()
+        _check(lib.csim_pool_create(C.cast(C.byref(o), C.c_void_p), C.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.csim_pool_free(self._h)
+            self._h = None
+            self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, circuit, f0, precision=CSIM_C64):
+        """Queue one run; returns the request id (raises CsimError when rejected)."""
+        f = np.ascontiguousarray(f0, dtype=np.float64)
+        rid = C.c_int64()
+        _check(_lib.csim_pool_submit(self._h, circuit._h, _dp(f), int(precision), C.byref(rid)))
+        self._keep[rid.value] = circuit
+        return rid.value
+
+    def poll(self, wait_ms=0, cap=4096):
+        ids = np.zeros(cap, dtype=np.int64)
+        n = C.c_size_t()
+        _check(_lib.csim_pool_poll(self._h, int(wait_ms), ids.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   cap, C.byref(n)))
+        return [int(x) for x in ids[:n.value]]
+
+    def result(self, rid, want_amplitudes=True):
+        """(amplitudes or None, p_success, norm_total, times) of a finished request."""
+        p = C.c_double()
+        t = C.c_double()
+        n = C.c_size_t()
+        times = np.zeros(3)
+        out = None
+        if want_amplitudes:
+            # the count is known from the circuit's geometry: ask with cap 0 first is not
+            # possible after release, so size from the circuit's mask geometry
+            cnt = self._keep[rid].postselect_count()
+            out = np.zeros(2 * cnt)
+            _check(_lib.csim_pool_result(self._h, int(rid), C.byref(p), C.byref(t), _dp(out), cnt,
+                                         C.byref(n), _dp(times)))
+            out = out.view(np.complex128)
+        else:
+            _check(_lib.csim_pool_result(self._h, int(rid), C.byref(p), C.byref(t), None, 0,
+                                         C.byref(n), _dp(times)))
+        self._keep.pop(rid, None)
+        return out, p.value, t.value, {"queue_s": times[0], "latency_s": times[1],
+                                       "device_s": times[2]}
+
+    def stats(self):
+        st = PoolStats()
+        _check(_lib.csim_pool_stats(self._h, C.cast(C.byref(st), C.c_void_p)))
+        return {k: getattr(st, k) for k, _ in PoolStats._fields_}
+
+
+def pool_plan(budget, n_streams, alloc_bytes, duration, arrival=None, min_block=0):
+    """csim_pool_plan: (start, finish, peak_bytes) of the admission policy."""
+    lib = load()
+    a = np.ascontiguousarray(alloc_bytes, dtype=np.uint64).reshape(-1, 4)
+    d = np.ascontiguousarray(duration, dtype=np.float64)
+    count = a.shape[0]
+    arr = None if arrival is None else np.ascontiguousarray(arrival, dtype=np.float64)
+    start = np.zeros(count)
+    finish = np.zeros(count)
+    peak = C.c_uint64()
+    _check(lib.csim_pool_plan(int(budget), int(min_block), int(n_streams), count,
+                              a.ctypes.data_as(C.POINTER(C.c_uint64)),
+                              None if arr is None else _dp(arr), _dp(d), _dp(start), _dp(finish),
+                              C.byref(peak)))
+    return start, finish, int(peak.value)

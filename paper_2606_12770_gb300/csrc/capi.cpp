@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "fuse.h"
+#include "handles.h"
 #include "internal.h"
 #include "kernels.h"
 
@@ -34,40 +35,6 @@ namespace csim {
 void record_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace csim
 
-struct csim_circuit {
-  Layout L;
-  double tau = 0, dt = 0, eps = 1e-3, kappa = 0, scale = 0, Lmax = 0, lambda = 0;
-  int d = 0, max_qubits = 34;
-  std::vector<Gate> UL;
-  std::vector<double> phases;
-  std::vector<uint64_t> pm, pv;
-  // device side
-  int prec = -1;
-  cudaStream_t stream = nullptr;
-  void* buf[2] = {nullptr, nullptr};
-  int cur = 0;
-  size_t bytes = 0;
-  csim_exec exec = CSIM_EXEC_FUSED;
-  bool loaded = false, ran = false;
-  Program prog;
-  bool prog_built = false;
-  uint64_t* d_pat = nullptr;  // masks then values
-  double* d_partial = nullptr;
-  double* d_out = nullptr;
-  double* d_compact = nullptr;
-  size_t compact_cap = 0;
-};
-
-struct csim_sv {
-  int n = 0, prec = 0;
-  cudaStream_t stream = nullptr;
-  void* buf[2] = {nullptr, nullptr};
-  int cur = 0;
-  size_t bytes = 0;
-  Program prog;
-  bool compiled = false;
-};
-
 namespace {
 
 void free_device(csim_circuit* c) {
@@ -90,28 +57,109 @@ void free_device(csim_circuit* c) {
   c->prog_built = false;
 }
 
+
+}  // namespace
+
+namespace csim {
+
 uint64_t place_bits(const std::vector<int>& bits, uint64_t v) {
   uint64_t idx = 0;
   for (size_t j = 0; j < bits.size(); ++j) idx |= ((v >> j) & 1ull) << bits[j];
   return idx;
 }
 
-bool ensure_program(csim_circuit* c, std::string* err) {
-  if (c->prog_built && c->prog.mode == c->exec) return true;
+void ensure_built(csim_circuit* c) {
+  if (c->prog_built && c->prog.mode == c->exec) return;
   csim::free_program(&c->prog);
   std::vector<Gate> all = csim::build_qsvt(c->L, c->UL, c->phases);
   csim::build_program(all, c->L.n, c->exec, &c->prog);
-  cudaError_t e = csim::upload_program(&c->prog, c->stream);
+  c->prog_built = true;
+}
+
+bool ensure_program(csim_circuit* c, cudaStream_t st, std::string* err) {
+  ensure_built(c);
+  if (c->prog.uploaded) return true;
+  cudaError_t e = csim::upload_program(&c->prog, st);
   if (e != cudaSuccess) {
     *err = std::string("program upload: ") + cudaGetErrorString(e);
     csim::free_program(&c->prog);
     return false;
   }
-  c->prog_built = true;
   return true;
 }
 
-}  // namespace
+bool circuit_rhs(const csim_circuit* c, const double* f0, std::vector<uint64_t>* idx,
+                 std::vector<double>* val, std::string* err) {
+  const Layout& L = c->L;
+  const size_t nf = (size_t)L.Nx * 3;
+  for (size_t i = 0; i < nf; ++i)
+    if (!std::isfinite(f0[i])) {
+      *err = "f0 has a non-finite entry";
+      return false;
+    }
+  idx->clear();
+  val->clear();
+  double nrm2 = 0.0;
+  for (int a = 0; a < L.Nx; ++a)
+    for (int q = 0; q < 3; ++q) {
+      const double v = f0[a * 3 + q];
+      nrm2 += v * v;
+      if (v != 0.0) {
+        idx->push_back(place_bits(L.a1, a) | place_bits(L.q1, q));
+        val->push_back(v);
+      }
+    }
+  if (L.NC == 2) {
+    for (int a1 = 0; a1 < L.Nx; ++a1)
+      for (int q1 = 0; q1 < 3; ++q1)
+        for (int a2 = 0; a2 < L.Nx; ++a2)
+          for (int q2 = 0; q2 < 3; ++q2) {
+            const double v = f0[a1 * 3 + q1] * f0[a2 * 3 + q2];
+            nrm2 += v * v;
+            if (v != 0.0) {
+              idx->push_back(place_bits(L.a1, a1) | place_bits(L.q1, q1) | place_bits(L.a2, a2) |
+                             place_bits(L.q2, q2) | place_bits(L.ord, 1));
+              val->push_back(v);
+            }
+          }
+  }
+  if (!(nrm2 > 0)) {
+    *err = "f0 is zero";
+    return false;
+  }
+  const double inv = 1.0 / std::sqrt(nrm2);
+  for (double& v : *val) v *= inv;
+  return true;
+}
+
+void mask_low_bits(const csim_circuit* c, int* lowk, uint64_t* lowv) {
+  const int npat = (int)c->pm.size();
+  int k = 0;
+  uint64_t v = 0;
+  while (npat > 0 && k < c->L.n) {
+    const uint64_t b = 1ull << k;
+    bool all = true;
+    for (int j = 0; j < npat; ++j)
+      all = all && (c->pm[j] & b) && ((c->pv[j] & b) == (c->pv[0] & b));
+    if (!all) break;
+    v |= c->pv[0] & b;
+    ++k;
+  }
+  *lowk = k;
+  *lowv = v;
+}
+
+CompactGeom compact_geom(const csim_circuit* c) {
+  const Layout& L = c->L;
+  CompactGeom g;
+  g.free_shift = 2 + L.niL;
+  g.m_shift = L.m[0];
+  g.free_bits = g.m_shift - g.free_shift;
+  g.count = (((uint64_t)1 << L.nm) - (uint64_t)L.Nt) << g.free_bits;
+  return g;
+}
+
+}  // namespace csim
 
 extern "C" {
 
@@ -267,39 +315,13 @@ csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec, vo
   if (!c || !f0) return fail(CSIM_ERR_ARG, "null argument");
   if (prec != CSIM_C64 && prec != CSIM_C128) return fail(CSIM_ERR_ARG, "bad precision");
   const Layout& L = c->L;
-  const size_t nf = (size_t)L.Nx * 3;
-  for (size_t i = 0; i < nf; ++i)
-    if (!std::isfinite(f0[i])) return fail(CSIM_ERR_ARG, "f0 has a non-finite entry");
   // host: b = (f, f (x) f) normalised, in register coordinates
   std::vector<uint64_t> idx;
   std::vector<double> val;
-  double nrm2 = 0.0;
-  for (int a = 0; a < L.Nx; ++a)
-    for (int q = 0; q < 3; ++q) {
-      const double v = f0[a * 3 + q];
-      nrm2 += v * v;
-      if (v != 0.0) {
-        idx.push_back(place_bits(L.a1, a) | place_bits(L.q1, q));
-        val.push_back(v);
-      }
-    }
-  if (L.NC == 2) {
-    for (int a1 = 0; a1 < L.Nx; ++a1)
-      for (int q1 = 0; q1 < 3; ++q1)
-        for (int a2 = 0; a2 < L.Nx; ++a2)
-          for (int q2 = 0; q2 < 3; ++q2) {
-            const double v = f0[a1 * 3 + q1] * f0[a2 * 3 + q2];
-            nrm2 += v * v;
-            if (v != 0.0) {
-              idx.push_back(place_bits(L.a1, a1) | place_bits(L.q1, q1) | place_bits(L.a2, a2) |
-                            place_bits(L.q2, q2) | place_bits(L.ord, 1));
-              val.push_back(v);
-            }
-          }
+  {
+    std::string err;
+    if (!csim::circuit_rhs(c, f0, &idx, &val, &err)) return fail(CSIM_ERR_ARG, err);
   }
-  if (!(nrm2 > 0)) return fail(CSIM_ERR_ARG, "f0 is zero");
-  const double inv = 1.0 / std::sqrt(nrm2);
-  for (double& v : val) v *= inv;
 
   c->stream = (cudaStream_t)stream;
   const size_t esz = prec == CSIM_C64 ? 8 : 16;
@@ -360,6 +382,12 @@ csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec, vo
   return CSIM_OK;
 }
 
+csim_status csim_compile(csim_circuit* c) {
+  if (!c) return fail(CSIM_ERR_ARG, "null argument");
+  csim::ensure_built(c);
+  return CSIM_OK;
+}
+
 csim_status csim_set_exec(csim_circuit* c, csim_exec mode) {
   if (!c) return fail(CSIM_ERR_ARG, "null argument");
   if (mode != CSIM_EXEC_FUSED && mode != CSIM_EXEC_GATE) return fail(CSIM_ERR_ARG, "bad mode");
@@ -371,7 +399,7 @@ csim_status csim_run(csim_circuit* c) {
   if (!c) return fail(CSIM_ERR_ARG, "null argument");
   if (!c->loaded) return fail(CSIM_ERR_STATE, "csim_run needs a fresh csim_init");
   std::string err;
-  if (!ensure_program(c, &err)) return fail(CSIM_ERR_CUDA, err);
+  if (!csim::ensure_program(c, c->stream, &err)) return fail(CSIM_ERR_CUDA, err);
   if (c->prog.pingpong && !c->buf[1]) {
     cudaError_t e = cudaMalloc(&c->buf[1], c->bytes);
     if (e != cudaSuccess) {
@@ -407,25 +435,16 @@ csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_
   // low index bits fixed (to the same value) by every pattern
   int lowk = 0;
   uint64_t lowv = 0;
-  while (lowk < L.n) {
-    const uint64_t b = 1ull << lowk;
-    bool all = true;
-    for (int k = 0; k < npat; ++k)
-      all = all && (c->pm[k] & b) && ((c->pv[k] & b) == (c->pv[0] & b));
-    if (!all) break;
-    lowv |= c->pv[0] & b;
-    ++lowk;
-  }
+  csim::mask_low_bits(c, &lowk, &lowv);
   if (e == cudaSuccess)
     e = csim::launch_norms(c->buf[c->cur], c->prec, L.n, c->d_pat, c->d_pat + npat, npat, lowk,
                            lowv, c->d_partial, c->d_out, c->stream);
   double h[2] = {0, 0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h, c->d_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
-  const int free_shift = 2 + L.niL;
-  const int m_shift = L.m[0];
-  const int free_bits = m_shift - free_shift;
-  const uint64_t count = (((uint64_t)1 << L.nm) - (uint64_t)L.Nt) << free_bits;
+  const csim::CompactGeom cg = csim::compact_geom(c);
+  const int free_shift = cg.free_shift, m_shift = cg.m_shift, free_bits = cg.free_bits;
+  const uint64_t count = cg.count;
   if (len) *len = count;
   if (e == cudaSuccess && out_amps) {
     if (cap < count) return fail(CSIM_ERR_ARG, "out_amps too small");
@@ -450,6 +469,16 @@ csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_
   if (e != cudaSuccess) return cuda_fail(e, "csim_postselect");
   if (norm_total) *norm_total = h[0];
   if (p_success) *p_success = h[1];
+  return CSIM_OK;
+}
+
+csim_status csim_state_device(const csim_circuit* c, void** d_state, int32_t* n,
+                              csim_precision* prec) {
+  if (!c || !d_state) return fail(CSIM_ERR_ARG, "null argument");
+  if (!c->buf[c->cur] || c->prec < 0) return fail(CSIM_ERR_STATE, "no state");
+  *d_state = c->buf[c->cur];
+  if (n) *n = c->L.n;
+  if (prec) *prec = (csim_precision)c->prec;
   return CSIM_OK;
 }
 
@@ -583,6 +612,35 @@ csim_status csim_sv_info(const csim_sv* s, int64_t* n_sweeps, double* amp_update
   if (n_sweeps) *n_sweeps = s->compiled ? s->prog.passes : 0;
   if (amp_updates) *amp_updates = s->compiled ? s->prog.amp_updates : 0.0;
   if (state_bytes) *state_bytes = s->bytes;
+  return CSIM_OK;
+}
+
+csim_status csim_sv_stats(const csim_sv* s, csim_sv_stats_t* out) {
+  if (!s || !out) return fail(CSIM_ERR_ARG, "null argument");
+  *out = csim_sv_stats_t{};
+  out->state_bytes = s->bytes;
+  if (!s->compiled) return CSIM_OK;
+  out->passes = s->prog.passes;
+  out->sweeps = s->prog.stats.sweeps;
+  out->single = s->prog.stats.single;
+  out->amp_updates = s->prog.amp_updates;
+  out->pass_amps = s->prog.pass_amps;
+  return CSIM_OK;
+}
+
+csim_status csim_sv_load_device(csim_sv* s, const void* d_amps, size_t n_amps) {
+  if (!s || !d_amps) return fail(CSIM_ERR_ARG, "null argument");
+  if (n_amps != ((size_t)1 << s->n)) return fail(CSIM_ERR_ARG, "n_amps must be 2^n");
+  s->cur = 0;
+  cudaError_t e = cudaMemcpyAsync(s->buf[0], d_amps, s->bytes, cudaMemcpyDeviceToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_sv_load_device");
+  return CSIM_OK;
+}
+
+csim_status csim_sv_device(const csim_sv* s, void** d_state) {
+  if (!s || !d_state) return fail(CSIM_ERR_ARG, "null argument");
+  *d_state = s->buf[s->cur];
   return CSIM_OK;
 }
 

@@ -236,12 +236,20 @@ std::vector<PermSeg> compile_perm(const std::vector<csim_gate>& run, bool forwar
     PermSeg ps{};
     ps.kind = 0;
     ps.win = win;
-    ps.t = (uint32_t)p->lut.size();
-    for (uint32_t key = 0; key < (1u << w); ++key) {
-      uint32_t x = win_put(0u, key, win);
-      for (const ChunkGate& cg : seg)
-        if ((x & cg.m) == cg.v) x ^= cg.t;
-      p->lut.push_back((uint16_t)win_key(x, win));
+    std::string key(reinterpret_cast<const char*>(&win), sizeof(win));
+    key.append(reinterpret_cast<const char*>(seg.data()), seg.size() * sizeof(ChunkGate));
+    const auto hit = p->lut_cache.find(key);
+    if (hit != p->lut_cache.end()) {
+      ps.t = hit->second;
+    } else {
+      ps.t = (uint32_t)p->lut.size();
+      p->lut_cache.emplace(std::move(key), ps.t);
+      for (uint32_t k = 0; k < (1u << w); ++k) {
+        uint32_t x = win_put(0u, k, win);
+        for (const ChunkGate& cg : seg)
+          if ((x & cg.m) == cg.v) x ^= cg.t;
+        p->lut.push_back((uint16_t)win_key(x, win));
+      }
     }
     out.push_back(ps);
     p->stats.segments++;
@@ -281,7 +289,24 @@ struct OpItem {
   ReflectDesc refl;
 };
 
+OpItem out_item_of(const Program* p, uint32_t mux_index) {
+  OpItem it{};
+  it.mux = p->mux_descs[mux_index];
+  it.op.op = 4;
+  it.op.target = it.mux.target;
+  return it;
+}
+
 void compile_mux_group(const std::vector<csim_gate>& grp, Program* p, std::vector<OpItem>* out) {
+  std::string ckey(reinterpret_cast<const char*>(grp.data()), grp.size() * sizeof(csim_gate));
+  const auto hit = p->mux_cache.find(ckey);
+  if (hit != p->mux_cache.end()) {
+    OpItem it = out_item_of(p, hit->second);
+    out->push_back(it);
+    p->stats.mux++;
+    p->stats.mux_gates += (int64_t)grp.size();
+    return;
+  }
   // key windows: grow by the chunk bits constrained by the most gates
   int freq[32] = {0};
   for (const csim_gate& g : grp) {
@@ -348,6 +373,8 @@ void compile_mux_group(const std::vector<csim_gate>& grp, Program* p, std::vecto
   }
   it.op.op = 4;
   it.op.target = grp[0].target;
+  p->mux_cache.emplace(std::move(ckey), (uint32_t)p->mux_descs.size());
+  p->mux_descs.push_back(it.mux);
   out->push_back(it);
   p->stats.mux++;
   p->stats.mux_gates += (int64_t)grp.size();
@@ -585,6 +612,7 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
     }
     p->passes = (int64_t)p->steps.size();
     p->stats.single = p->passes;
+    p->pass_amps = p->amp_updates;
     return;
   }
   std::vector<csim_gate> perm, local;
@@ -634,6 +662,8 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
   }
   close();
   p->passes = (int64_t)p->steps.size();
+  for (const Step& s : p->steps)
+    p->pass_amps += s.kind == 0 ? std::ldexp(1.0, n) : gate_amp_updates(s.g, n);
   for (const Step& s : p->steps)
     if (s.kind == 0 && s.gather) p->pingpong = true;
   p->stats.lut_entries = (int64_t)p->lut.size();

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -44,10 +45,16 @@ struct Program {
   float2* d_angf = nullptr;
   double2* d_angd = nullptr;
   int64_t passes = 0;        // HBM passes per execution
+  double pass_amps = 0.0;    // amplitudes the passes read (and write) at minimum: 2^n per
+                             // sweep, the changed amplitudes per single-gate step
   double amp_updates = 0.0;  // sum over elementary gates of amplitudes changed
   bool pingpong = false;     // some step moves data out of place
   bool uploaded = false;
   FuseStats stats;
+  // identical permutation runs and multiplexers (every U_L call of a QSVT
+  // circuit repeats them) share one table: content -> table offset
+  std::unordered_map<std::string, uint32_t> lut_cache, mux_cache;
+  std::vector<MuxDesc> mux_descs;  // compiled multiplexers, indexed by mux_cache
 };
 
 // Build the program for `gates` on an n-qubit state.  FUSED mode needs

@@ -1,0 +1,67 @@
+// Handle structures behind the opaque types of include/csim.h, and the
+// helpers that the C ABI (capi.cpp) and the request pool (pool.cpp) share.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "fuse.h"
+#include "internal.h"
+
+struct csim_circuit {
+  csim::Layout L;
+  double tau = 0, dt = 0, eps = 1e-3, kappa = 0, scale = 0, Lmax = 0, lambda = 0;
+  int d = 0, max_qubits = 34;
+  std::vector<csim::Gate> UL;
+  std::vector<double> phases;
+  std::vector<uint64_t> pm, pv;
+  // device side
+  int prec = -1;
+  cudaStream_t stream = nullptr;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  size_t bytes = 0;
+  csim_exec exec = CSIM_EXEC_FUSED;
+  bool loaded = false, ran = false;
+  csim::Program prog;
+  bool prog_built = false;
+  uint64_t* d_pat = nullptr;  // masks then values
+  double* d_partial = nullptr;
+  double* d_out = nullptr;
+  double* d_compact = nullptr;
+  size_t compact_cap = 0;
+};
+
+struct csim_sv {
+  int n = 0, prec = 0;
+  cudaStream_t stream = nullptr;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  size_t bytes = 0;
+  csim::Program prog;
+  bool compiled = false;
+};
+
+namespace csim {
+
+uint64_t place_bits(const std::vector<int>& bits, uint64_t v);
+// Build (once, host only) the fused or gate-by-gate program of the circuit.
+void ensure_built(csim_circuit* c);
+// ensure_built, then upload the program's tables to the device (once).
+bool ensure_program(csim_circuit* c, cudaStream_t st, std::string* err);
+// Normalised right-hand side b = (f, f (x) f) as (state index, value) pairs
+// (Sec. II.D.5); false with a message for a non-finite or zero f0.
+bool circuit_rhs(const csim_circuit* c, const double* f0, std::vector<uint64_t>* idx,
+                 std::vector<double>* val, std::string* err);
+// Lowest index bits that every postselection pattern fixes to the same value.
+void mask_low_bits(const csim_circuit* c, int* lowk, uint64_t* lowv);
+// Geometry of the compacted postselected block (m >= Nt, s = t = label = 0).
+struct CompactGeom {
+  int free_shift = 0, free_bits = 0, m_shift = 0;
+  uint64_t count = 0;
+};
+CompactGeom compact_geom(const csim_circuit* c);
+
+}  // namespace csim

@@ -97,6 +97,9 @@ cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaSt
 cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
                          cudaStream_t st);
 int norm_partials_needed();
+// Load every kernel of this file and compute the cached launch shapes (before
+// any stream capture).
+cudaError_t warm_kernels();
 // FP64 total norm and masked norm.  Every pattern must fix the lowk lowest
 // index bits to the value lowv (lowk = 0 checks every index).
 cudaError_t launch_norms(const void* state, int prec, int n, const uint64_t* d_pm,

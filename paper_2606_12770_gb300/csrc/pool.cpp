@@ -1,0 +1,687 @@
+// Request pool: many circuit runs on one GPU (batching and serving).
+//
+//  * Admission.  Each request needs device memory for its two state buffers
+//    (ping-pong), the compacted postselected block and the staging of b.  The
+//    pool owns one arena of `hbm_budget` bytes carved by a buddy allocator
+//    (every state is a power of two bytes), and admits queued requests in
+//    arrival order while a stream slot is free and the head request's blocks
+//    fit (first come, first served; the head is never overtaken).
+//  * Execution.  An admitted request runs on its slot's CUDA stream:
+//    H2D of b, init kernel, the fused program, FP64 norms, compaction and D2H
+//    of the results into the slot's pinned buffers.  With use_graphs, all
+//    requests admitted in one admission pass are captured into one CUDA graph
+//    (one branch per request) and launched once.
+//  * Completion.  csim_pool_poll retires finished requests (event queries),
+//    releases their blocks and admits more: continuous batching.
+//  * Planner.  csim_pool_plan runs the same arena and admission policy on a
+//    discrete-event clock with given durations (no GPU) for capacity planning
+//    and for testing the policy.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <new>
+#include <set>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "handles.h"
+#include "kernels.h"
+
+namespace csim {
+void record_last_error(const std::string& msg);
+}
+
+namespace {
+
+csim_status pfail(csim_status s, const std::string& msg) {
+  csim::record_last_error(msg);
+  return s;
+}
+csim_status pcuda(cudaError_t e, const char* where) {
+  return pfail(CSIM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// Buddy allocator over byte offsets [0, capacity).  The capacity is split
+// into power-of-two regions (largest first); blocks are min_block << order.
+class BuddyArena {
+ public:
+  void init(uint64_t bytes, uint64_t min_block) {
+    min_ = min_block;
+    regions_.clear();
+    free_.assign(64, {});
+    live_.clear();
+    in_use_ = 0;
+    uint64_t units = bytes / min_block, base = 0;
+    for (int k = 63; k >= 0; --k) {
+      if (!((units >> k) & 1ull)) continue;
+      regions_.push_back({base, k});
+      free_[k].insert(base);
+      base += min_block << k;
+    }
+    cap_ = base;
+  }
+  static int order_for(uint64_t bytes, uint64_t min_block) {
+    int k = 0;
+    while ((min_block << k) < bytes) ++k;
+    return k;
+  }
+  bool alloc(uint64_t bytes, uint64_t* off) {
+    const int j = order_for(bytes, min_);
+    int k = j;
+    while (k < 64 && free_[k].empty()) ++k;
+    if (k >= 64) return false;
+    uint64_t o = *free_[k].begin();
+    free_[k].erase(free_[k].begin());
+    while (k > j) {
+      --k;
+      free_[k].insert(o + (min_ << k));
+    }
+    live_[o] = j;
+    in_use_ += min_ << j;
+    *off = o;
+    return true;
+  }
+  void release(uint64_t off) {
+    auto it = live_.find(off);
+    if (it == live_.end()) return;
+    int j = it->second;
+    live_.erase(it);
+    in_use_ -= min_ << j;
+    const Region& r = region_of(off);
+    while (j < r.order) {
+      const uint64_t buddy = r.base + ((off - r.base) ^ (min_ << j));
+      auto f = free_[j].find(buddy);
+      if (f == free_[j].end()) break;
+      free_[j].erase(f);
+      off = std::min(off, buddy);
+      ++j;
+    }
+    free_[j].insert(off);
+  }
+  uint64_t in_use() const { return in_use_; }
+  uint64_t capacity() const { return cap_; }
+  uint64_t min_block() const { return min_; }
+
+ private:
+  struct Region {
+    uint64_t base;
+    int order;
+  };
+  const Region& region_of(uint64_t off) const {
+    for (const Region& r : regions_)
+      if (off >= r.base && off < r.base + (min_ << r.order)) return r;
+    return regions_.front();
+  }
+  uint64_t min_ = 1, cap_ = 0, in_use_ = 0;
+  std::vector<Region> regions_;
+  std::vector<std::set<uint64_t>> free_;
+  std::map<uint64_t, int> live_;
+};
+
+constexpr int kAllocs = 4;  // state 0, state 1, compacted block, staging of b
+
+// Whether every block of one request fits an empty arena of this capacity.
+bool fits_empty(uint64_t capacity, uint64_t min_block, const uint64_t* sizes) {
+  BuddyArena a;
+  a.init(capacity, min_block);
+  uint64_t off;
+  for (int k = 0; k < kAllocs; ++k)
+    if (sizes[k] && !a.alloc(sizes[k], &off)) return false;
+  return true;
+}
+
+// All-or-nothing allocation of a request's blocks.
+bool alloc_all(BuddyArena* a, const uint64_t* sizes, uint64_t* offs) {
+  for (int k = 0; k < kAllocs; ++k) {
+    offs[k] = ~0ull;
+    if (!sizes[k]) continue;
+    if (!a->alloc(sizes[k], &offs[k])) {
+      for (int j = 0; j < k; ++j)
+        if (offs[j] != ~0ull) a->release(offs[j]);
+      return false;
+    }
+  }
+  return true;
+}
+void release_all(BuddyArena* a, const uint64_t* offs) {
+  for (int k = 0; k < kAllocs; ++k)
+    if (offs[k] != ~0ull) a->release(offs[k]);
+}
+
+enum class RState { Queued, Running, Done };
+
+struct Request {
+  int64_t id = 0;
+  csim_circuit* c = nullptr;
+  int prec = 0;
+  std::vector<uint64_t> idx;
+  std::vector<double> val;
+  uint64_t sizes[kAllocs] = {0, 0, 0, 0};
+  uint64_t offs[kAllocs] = {~0ull, ~0ull, ~0ull, ~0ull};
+  RState st = RState::Queued;
+  int slot = -1;
+  uint64_t count = 0;  // compacted amplitudes
+  int wave = -1;       // index into csim_pool::waves when launched in a graph
+  double t_submit = 0, t_start = 0, t_done = 0;
+  double p = 0, tot = 0, dev_ms = 0;
+  std::vector<double> amps;
+};
+
+struct Slot {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  uint64_t* d_pat = nullptr;
+  double* d_partial = nullptr;
+  double* d_out = nullptr;
+  void* h_stage = nullptr;  // pinned: patterns, then idx, then val
+  size_t h_stage_cap = 0;
+  double* h_out = nullptr;  // pinned: 2 doubles
+  double* h_amps = nullptr;  // pinned: compacted block
+  size_t h_amps_cap = 0;
+  int64_t req = -1;
+};
+
+constexpr int kMaxPatterns = 64;
+
+}  // namespace
+
+struct csim_pool {
+  csim_pool_opts o{};
+  void* d_arena = nullptr;
+  BuddyArena arena;
+  std::vector<Slot> slots;
+  cudaStream_t origin = nullptr;  // graph capture origin
+  std::deque<int64_t> queue;
+  std::unordered_map<int64_t, Request> reqs;
+  std::vector<int64_t> done_unreported;
+  // One graph launch per admission pass.  Completion is taken from an event
+  // recorded on the origin stream after the launch: an event-record node
+  // inside the graph keeps its previous (completed) state until the node
+  // runs, so it cannot tell whether this launch has finished.
+  struct Wave {
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    int pending = 0;
+  };
+  std::vector<Wave> waves;
+  int64_t next_id = 1;
+  csim_pool_stats_t stats{};
+};
+
+namespace {
+
+void request_sizes(const csim_circuit* c, int prec, size_t nnz, uint64_t* sizes, uint64_t* count) {
+  const uint64_t S = ((uint64_t)1 << c->L.n) * (prec == CSIM_C64 ? 8 : 16);
+  const csim::CompactGeom g = csim::compact_geom(c);
+  sizes[0] = S;
+  sizes[1] = (c->prog_built && !c->prog.pingpong) ? 0 : S;
+  sizes[2] = std::max<uint64_t>(g.count * 16, 256);
+  sizes[3] = std::max<uint64_t>(nnz * 16, 256);
+  *count = g.count;
+}
+
+cudaError_t grow_pinned(Slot* s, size_t stage_bytes, size_t amp_bytes) {
+  cudaError_t e = cudaSuccess;
+  if (s->h_stage_cap < stage_bytes) {
+    if (s->h_stage) cudaFreeHost(s->h_stage);
+    s->h_stage = nullptr;
+    s->h_stage_cap = 0;
+    e = cudaMallocHost(&s->h_stage, stage_bytes);
+    if (e != cudaSuccess) return e;
+    s->h_stage_cap = stage_bytes;
+  }
+  if (s->h_amps_cap < amp_bytes) {
+    if (s->h_amps) cudaFreeHost(s->h_amps);
+    s->h_amps = nullptr;
+    s->h_amps_cap = 0;
+    e = cudaMallocHost((void**)&s->h_amps, amp_bytes);
+    if (e != cudaSuccess) return e;
+    s->h_amps_cap = amp_bytes;
+  }
+  return cudaSuccess;
+}
+
+// Enqueue one request's whole run on stream st (the slot's stream, possibly
+// under capture).
+cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s) {
+  csim_circuit* c = r.c;
+  char* base = static_cast<char*>(P->d_arena);
+  void* buf[2] = {base + r.offs[0], r.offs[1] != ~0ull ? base + r.offs[1] : nullptr};
+  double* d_compact = reinterpret_cast<double*>(base + r.offs[2]);
+  char* d_stage = base + r.offs[3];
+  const size_t nnz = r.idx.size();
+  const int npat = (int)c->pm.size();
+  // host staging (pinned): patterns (masks, values), idx, val
+  char* hs = static_cast<char*>(s.h_stage);
+  std::memcpy(hs, c->pm.data(), npat * 8);
+  std::memcpy(hs + npat * 8, c->pv.data(), npat * 8);
+  const size_t pat_bytes = 16 * (size_t)npat;
+  std::memcpy(hs + pat_bytes, r.idx.data(), nnz * 8);
+  std::memcpy(hs + pat_bytes + nnz * 8, r.val.data(), nnz * 8);
+  cudaStream_t st = s.st;
+  cudaError_t e = cudaEventRecord(s.ev0, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_pat, hs, pat_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_stage, hs + pat_bytes, nnz * 16, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n,
+                          reinterpret_cast<const uint64_t*>(d_stage),
+                          reinterpret_cast<const double*>(d_stage + nnz * 8), (int64_t)nnz, st);
+  int cur = 0;
+  if (e == cudaSuccess) e = csim::run_program(c->prog, buf, &cur, r.prec, st);
+  int lowk = 0;
+  uint64_t lowv = 0;
+  csim::mask_low_bits(c, &lowk, &lowv);
+  if (e == cudaSuccess)
+    e = csim::launch_norms(buf[cur], r.prec, c->L.n, s.d_pat, s.d_pat + npat, npat, lowk, lowv,
+                           s.d_partial, s.d_out, st);
+  const csim::CompactGeom g = csim::compact_geom(c);
+  if (e == cudaSuccess && g.count)
+    e = csim::launch_compact(buf[cur], r.prec, d_compact, g.count, g.free_shift, g.free_bits,
+                             (uint64_t)c->L.Nt, g.m_shift, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s.h_out, s.d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && g.count)
+    e = cudaMemcpyAsync(s.h_amps, d_compact, g.count * 16, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(s.ev1, st);
+  return e;
+}
+
+// Admit queued requests (FIFO) into free slots while their blocks fit.
+csim_status admit(csim_pool* P) {
+  std::vector<std::pair<int64_t, int>> started;
+  while (!P->queue.empty()) {
+    int free_slot = -1;
+    for (int k = 0; k < (int)P->slots.size(); ++k)
+      if (P->slots[k].req < 0) {
+        free_slot = k;
+        break;
+      }
+    if (free_slot < 0) break;
+    Request& r = P->reqs[P->queue.front()];
+    if (!alloc_all(&P->arena, r.sizes, r.offs)) break;
+    Slot& s = P->slots[free_slot];
+    cudaError_t e = grow_pinned(&s, 16 * kMaxPatterns + r.idx.size() * 16, r.count * 16 + 16);
+    if (e != cudaSuccess) {
+      release_all(&P->arena, r.offs);
+      return pcuda(e, "csim_pool: pinned staging");
+    }
+    s.req = r.id;
+    r.slot = free_slot;
+    r.st = RState::Running;
+    r.t_start = now_s();
+    P->queue.pop_front();
+    P->stats.admitted++;
+    P->stats.bytes_in_use = P->arena.in_use();
+    P->stats.peak_bytes = std::max(P->stats.peak_bytes, P->arena.in_use());
+    started.emplace_back(r.id, free_slot);
+  }
+  if (started.empty()) return CSIM_OK;
+  cudaError_t e = cudaSuccess;
+  if (!P->o.use_graphs) {
+    for (auto& [id, k] : started) {
+      e = enqueue_request(P, P->reqs[id], P->slots[k]);
+      if (e != cudaSuccess) return pcuda(e, "csim_pool: enqueue");
+    }
+    return CSIM_OK;
+  }
+  // one graph for the whole admission pass: fork from the origin stream into
+  // each request's slot stream, join back, launch once
+  const char* where = "event create";
+  cudaEvent_t fork = nullptr;
+  e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  std::vector<cudaEvent_t> joins(started.size(), nullptr);
+  for (size_t k = 0; k < started.size() && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&joins[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) {
+    where = "begin capture";
+    e = cudaStreamBeginCapture(P->origin, cudaStreamCaptureModeThreadLocal);
+  }
+  if (e == cudaSuccess) {
+    where = "fork record";
+    e = cudaEventRecord(fork, P->origin);
+  }
+  for (size_t k = 0; k < started.size() && e == cudaSuccess; ++k) {
+    Slot& s = P->slots[started[k].second];
+    where = "fork wait";
+    e = cudaStreamWaitEvent(s.st, fork, 0);
+    if (e == cudaSuccess) {
+      where = "request enqueue";
+      e = enqueue_request(P, P->reqs[started[k].first], s);
+    }
+    if (e == cudaSuccess) {
+      where = "join record";
+      e = cudaEventRecord(joins[k], s.st);
+    }
+    if (e == cudaSuccess) {
+      where = "join wait";
+      e = cudaStreamWaitEvent(P->origin, joins[k], 0);
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(P->origin, &graph);
+  if (e == cudaSuccess && ee != cudaSuccess) {
+    where = "end capture";
+    e = ee;
+  }
+  csim_pool::Wave w;
+  if (e == cudaSuccess) {
+    where = "instantiate";
+    e = cudaGraphInstantiate(&w.exec, graph, 0);
+  }
+  if (e == cudaSuccess) {
+    where = "wave event";
+    e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) {
+    where = "launch";
+    e = cudaGraphLaunch(w.exec, P->origin);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(w.done, P->origin);
+  if (graph) cudaGraphDestroy(graph);
+  if (fork) cudaEventDestroy(fork);
+  for (cudaEvent_t j : joins)
+    if (j) cudaEventDestroy(j);
+  w.pending = (int)started.size();
+  const int wi = (int)P->waves.size();
+  P->waves.push_back(w);
+  for (auto& [id, k] : started) P->reqs[id].wave = wi;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return pfail(CSIM_ERR_CUDA, std::string("csim_pool: graph ") + where + ": " +
+                                    cudaGetErrorString(e));
+  }
+  P->stats.graph_launches++;
+  return CSIM_OK;
+}
+
+// Retire every running request whose completion event has fired.
+csim_status retire(csim_pool* P, int* n_retired) {
+  *n_retired = 0;
+  for (Slot& s : P->slots) {
+    if (s.req < 0) continue;
+    Request& r = P->reqs[s.req];
+    const cudaError_t q = cudaEventQuery(r.wave >= 0 ? P->waves[r.wave].done : s.ev1);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) return pcuda(q, "csim_pool: request failed");
+    if (r.wave >= 0) P->waves[r.wave].pending--;
+    r.tot = s.h_out[0];
+    r.p = s.h_out[1];
+    r.amps.assign(s.h_amps, s.h_amps + 2 * r.count);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s.ev0, s.ev1) == cudaSuccess) r.dev_ms = ms;
+    r.t_done = now_s();
+    r.st = RState::Done;
+    release_all(&P->arena, r.offs);
+    s.req = -1;
+    P->done_unreported.push_back(r.id);
+    P->stats.completed++;
+    ++*n_retired;
+  }
+  P->stats.bytes_in_use = P->arena.in_use();
+  bool busy = false;
+  for (const Slot& s : P->slots) busy = busy || s.req >= 0;
+  if (!busy) {  // every admission pass has finished: drop its graph and event
+    for (csim_pool::Wave& w : P->waves) {
+      if (w.exec) cudaGraphExecDestroy(w.exec);
+      if (w.done) cudaEventDestroy(w.done);
+    }
+    P->waves.clear();
+  }
+  return CSIM_OK;
+}
+
+void destroy_pool(csim_pool* P) {
+  for (Slot& s : P->slots) {
+    if (s.st) cudaStreamSynchronize(s.st);
+  }
+  if (P->origin) cudaStreamSynchronize(P->origin);
+  for (csim_pool::Wave& w : P->waves) {
+    if (w.exec) cudaGraphExecDestroy(w.exec);
+    if (w.done) cudaEventDestroy(w.done);
+  }
+  for (Slot& s : P->slots) {
+    if (s.ev0) cudaEventDestroy(s.ev0);
+    if (s.ev1) cudaEventDestroy(s.ev1);
+    if (s.d_pat) cudaFree(s.d_pat);
+    if (s.d_partial) cudaFree(s.d_partial);
+    if (s.d_out) cudaFree(s.d_out);
+    if (s.h_stage) cudaFreeHost(s.h_stage);
+    if (s.h_out) cudaFreeHost(s.h_out);
+    if (s.h_amps) cudaFreeHost(s.h_amps);
+    if (s.st) cudaStreamDestroy(s.st);
+  }
+  if (P->origin) cudaStreamDestroy(P->origin);
+  if (P->d_arena) cudaFree(P->d_arena);
+  delete P;
+}
+
+}  // namespace
+
+extern "C" {
+
+csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out) {
+  if (!out) return pfail(CSIM_ERR_ARG, "null argument");
+  *out = nullptr;
+  csim_pool* P = new (std::nothrow) csim_pool();
+  if (!P) return pfail(CSIM_ERR_OOM, "host allocation");
+  if (opts) P->o = *opts;
+  if (P->o.n_streams <= 0) P->o.n_streams = 4;
+  if (P->o.n_streams > 64) P->o.n_streams = 64;
+  if (P->o.max_qubits <= 0) P->o.max_qubits = 32;
+  if (P->o.min_block == 0) P->o.min_block = 1u << 20;
+  cudaError_t e = cudaSuccess;
+  if (P->o.hbm_budget == 0) {
+    size_t fr = 0, tot = 0;
+    e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) {
+      delete P;
+      return pcuda(e, "csim_pool_create");
+    }
+    P->o.hbm_budget = (uint64_t)(0.9 * (double)fr);
+  }
+  const uint64_t cap = P->o.hbm_budget / P->o.min_block * P->o.min_block;
+  e = cudaMalloc(&P->d_arena, cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete P;
+    return pfail(CSIM_ERR_OOM, "csim_pool_create: arena of " + std::to_string(cap) + " bytes");
+  }
+  P->arena.init(cap, P->o.min_block);
+  P->stats.budget = P->arena.capacity();
+  P->slots.resize(P->o.n_streams);
+  for (Slot& s : P->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&s.ev1);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_pat, 2 * kMaxPatterns * sizeof(uint64_t));
+    if (e == cudaSuccess)
+      e = cudaMalloc(&s.d_partial, 2 * csim::norm_partials_needed() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_out, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_out, 2 * sizeof(double));
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->origin, cudaStreamNonBlocking);
+  // load every kernel and fill the launch-configuration caches now: a lazy
+  // module load must not happen inside a graph capture
+  if (e == cudaSuccess) e = csim::warm_kernels();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    destroy_pool(P);
+    return pcuda(e, "csim_pool_create");
+  }
+  *out = P;
+  return CSIM_OK;
+}
+
+csim_status csim_pool_submit(csim_pool* P, csim_circuit* c, const double* f0, csim_precision prec,
+                             int64_t* id) {
+  if (!P || !c || !f0 || !id) return pfail(CSIM_ERR_ARG, "null argument");
+  if (prec != CSIM_C64 && prec != CSIM_C128) return pfail(CSIM_ERR_ARG, "bad precision");
+  *id = 0;
+  P->stats.submitted++;
+  if (c->L.n > P->o.max_qubits) {
+    P->stats.rejected++;
+    return pfail(CSIM_ERR_TOO_LARGE, "csim_pool_submit: " + std::to_string(c->L.n) +
+                                         " qubits exceed the pool's cap of " +
+                                         std::to_string(P->o.max_qubits));
+  }
+  if ((int)c->pm.size() > kMaxPatterns) return pfail(CSIM_ERR_ARG, "too many mask patterns");
+  std::string err;
+  if (!csim::ensure_program(c, P->slots[0].st, &err)) return pfail(CSIM_ERR_CUDA, err);
+  Request r;
+  if (!csim::circuit_rhs(c, f0, &r.idx, &r.val, &err)) return pfail(CSIM_ERR_ARG, err);
+  r.c = c;
+  r.prec = prec;
+  request_sizes(c, prec, r.idx.size(), r.sizes, &r.count);
+  if (!fits_empty(P->arena.capacity(), P->arena.min_block(), r.sizes)) {
+    P->stats.rejected++;
+    return pfail(CSIM_ERR_TOO_LARGE, "csim_pool_submit: the request's device memory exceeds "
+                                     "the pool's budget");
+  }
+  r.id = P->next_id++;
+  r.t_submit = now_s();
+  *id = r.id;
+  P->queue.push_back(r.id);
+  P->reqs.emplace(r.id, std::move(r));
+  int n = 0;
+  csim_status s = retire(P, &n);
+  if (s == CSIM_OK) s = admit(P);
+  P->stats.queued = (int64_t)P->queue.size();
+  return s;
+}
+
+csim_status csim_pool_poll(csim_pool* P, int32_t wait_ms, int64_t* done, size_t cap,
+                           size_t* n_done) {
+  if (!P) return pfail(CSIM_ERR_ARG, "null argument");
+  const double t_end = now_s() + (wait_ms > 0 ? wait_ms * 1e-3 : 0.0);
+  for (;;) {
+    int n = 0;
+    csim_status s = retire(P, &n);
+    if (s == CSIM_OK) s = admit(P);
+    if (s != CSIM_OK) return s;
+    bool running = false;
+    for (const Slot& sl : P->slots) running = running || sl.req >= 0;
+    if (!P->done_unreported.empty() || !running || now_s() >= t_end) break;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  const size_t k = std::min(cap, P->done_unreported.size());
+  if (done && k) std::memcpy(done, P->done_unreported.data(), k * sizeof(int64_t));
+  P->done_unreported.erase(P->done_unreported.begin(), P->done_unreported.begin() + (done ? k : 0));
+  if (n_done) *n_done = done ? k : 0;
+  int64_t running = 0;
+  for (const Slot& sl : P->slots) running += sl.req >= 0;
+  P->stats.running = running;
+  P->stats.queued = (int64_t)P->queue.size();
+  return CSIM_OK;
+}
+
+csim_status csim_pool_result(csim_pool* P, int64_t id, double* p_success, double* norm_total,
+                             double* out_amps, size_t cap, size_t* len, double* times) {
+  if (!P) return pfail(CSIM_ERR_ARG, "null argument");
+  auto it = P->reqs.find(id);
+  if (it == P->reqs.end()) return pfail(CSIM_ERR_ARG, "unknown request id");
+  Request& r = it->second;
+  if (r.st != RState::Done) return pfail(CSIM_ERR_STATE, "request not finished");
+  if (len) *len = r.count;
+  if (out_amps) {
+    if (cap < r.count) return pfail(CSIM_ERR_ARG, "out_amps too small");
+    std::memcpy(out_amps, r.amps.data(), r.count * 16);
+  }
+  if (p_success) *p_success = r.p;
+  if (norm_total) *norm_total = r.tot;
+  if (times) {
+    times[0] = r.t_start - r.t_submit;  // queueing
+    times[1] = r.t_done - r.t_submit;   // submit to retirement
+    times[2] = r.dev_ms * 1e-3;         // device time of the request's stream work
+  }
+  P->reqs.erase(it);
+  return CSIM_OK;
+}
+
+csim_status csim_pool_stats(const csim_pool* P, csim_pool_stats_t* out) {
+  if (!P || !out) return pfail(CSIM_ERR_ARG, "null argument");
+  *out = P->stats;
+  return CSIM_OK;
+}
+
+csim_status csim_pool_free(csim_pool* P) {
+  if (!P) return CSIM_OK;
+  destroy_pool(P);
+  return CSIM_OK;
+}
+
+csim_status csim_pool_plan(uint64_t budget, uint64_t min_block, int32_t n_streams, size_t count,
+                           const uint64_t* alloc_bytes, const double* arrival,
+                           const double* duration, double* start, double* finish,
+                           uint64_t* peak_bytes) {
+  if (!alloc_bytes || !duration || !start || !finish || n_streams <= 0)
+    return pfail(CSIM_ERR_ARG, "bad argument");
+  if (min_block == 0) min_block = 1u << 20;
+  BuddyArena a;
+  a.init(budget / min_block * min_block, min_block);
+  struct Run {
+    double t_end;
+    size_t i;
+    uint64_t offs[kAllocs];
+  };
+  std::vector<Run> running;
+  std::deque<size_t> queue;
+  std::vector<size_t> order(count);
+  for (size_t i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+    return (arrival ? arrival[x] : 0.0) < (arrival ? arrival[y] : 0.0);
+  });
+  size_t next = 0;
+  double t = 0.0;
+  uint64_t peak = 0;
+  for (size_t i = 0; i < count; ++i) start[i] = finish[i] = -1.0;
+  for (;;) {
+    // arrivals up to t
+    while (next < count && (arrival ? arrival[order[next]] : 0.0) <= t) {
+      const size_t i = order[next++];
+      if (fits_empty(a.capacity(), min_block, alloc_bytes + kAllocs * i)) queue.push_back(i);
+    }
+    // admit FIFO
+    while (!queue.empty() && (int)running.size() < n_streams) {
+      Run r{};
+      r.i = queue.front();
+      if (!alloc_all(&a, alloc_bytes + kAllocs * r.i, r.offs)) break;
+      queue.pop_front();
+      start[r.i] = t;
+      r.t_end = t + duration[r.i];
+      running.push_back(r);
+      peak = std::max(peak, a.in_use());
+    }
+    // next event: a completion or an arrival
+    double tn = 1e300;
+    for (const Run& r : running) tn = std::min(tn, r.t_end);
+    if (next < count) tn = std::min(tn, arrival ? arrival[order[next]] : 0.0);
+    if (tn >= 1e300) break;
+    t = std::max(t, tn);
+    for (size_t k = 0; k < running.size();) {
+      if (running[k].t_end <= t) {
+        finish[running[k].i] = running[k].t_end;
+        release_all(&a, running[k].offs);
+        running[k] = running.back();
+        running.pop_back();
+      } else {
+        ++k;
+      }
+    }
+  }
+  if (peak_bytes) *peak_bytes = peak;
+  return CSIM_OK;
+}
+
+}  // extern "C"

@@ -10,7 +10,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 from oracle import qsvt as Q  # noqa: E402
 
-CASES = [(10.0, 31), (4.0, 9)]
+CASES = [(10.0, 31), (4.0, 9), (1000.0, 13)]
 
 if __name__ == "__main__":
     for kappa, d in CASES:

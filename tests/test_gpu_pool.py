@@ -1,0 +1,87 @@
+"""The request pool on the GPU: every request's results equal the same
+circuit run alone through csim_init / csim_run / csim_postselect (bit for bit:
+the kernels are deterministic and a request's work does not depend on what
+runs beside it), with and without CUDA-graph admission waves, under a budget
+small enough to force several admission waves."""
+import numpy as np
+import pytest
+
+import lbm_inputs as I
+import paper_2606_12770_gb300 as G
+
+pytestmark = pytest.mark.gpu
+
+MIX = [  # (Nx, tau, N_C, K, dt, Nt), d, precision
+    ((4, 0.8, 2, 2, 0.1, 2), 5, G.CSIM_C64),
+    ((4, 0.8, 2, 2, 0.1, 2), 5, G.CSIM_C128),
+    ((8, 0.7, 1, 3, 0.2, 3), 7, G.CSIM_C64),
+    ((2, 1.1, 2, 3, 0.1, 2), 9, G.CSIM_C128),
+    ((4, 0.6, 2, 1, 0.15, 3), 3, G.CSIM_C64),
+    ((8, 0.9, 2, 2, 0.1, 2), 11, G.CSIM_C64),
+    ((2, 0.55, 2, 4, 0.1, 5), 13, G.CSIM_C128),
+    ((16, 1.2, 1, 2, 0.1, 8), 5, G.CSIM_C64),
+]
+
+
+def _instances():
+    out = []
+    for k, (cfg, d, prec) in enumerate(MIX):
+        f0, _ = I.lbm_instance(cfg[0], 10 + k, tau=cfg[1])
+        c = G.Circuit(*cfg, kappa_qsvt=10.0, d=d)
+        out.append((c, f0, prec))
+    return out
+
+
+def _alone(inst):
+    res = []
+    for c, f0, prec in inst:
+        c.init(f0, prec)
+        c.run()
+        res.append(c.postselect())
+    return res
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_pool_mix_equals_alone(graphs):
+    inst = _instances()
+    alone = _alone(inst)
+    # budget: room for about two of the largest requests at once
+    pool = G.Pool(n_streams=3, hbm_budget=160 << 20, max_qubits=30, use_graphs=graphs)
+    ids = [pool.submit(c, f0, prec) for c, f0, prec in inst]
+    done = set()
+    for _ in range(20000):
+        done.update(pool.poll(wait_ms=20))
+        if len(done) == len(ids):
+            break
+    assert len(done) == len(ids)
+    st = pool.stats()
+    assert st["completed"] == len(ids) and st["rejected"] == 0
+    assert 0 < st["peak_bytes"] <= st["budget"]
+    assert (st["graph_launches"] > 0) == graphs
+    for rid, (amps0, p0, t0) in zip(ids, alone):
+        amps, p, t, times = pool.result(rid)
+        assert np.array_equal(amps, amps0)
+        assert p == p0 and t == t0
+        assert times["latency_s"] >= times["queue_s"] >= 0.0
+    pool.close()
+
+
+def test_pool_rejects_above_the_qubit_cap():
+    pool = G.Pool(n_streams=2, hbm_budget=64 << 20, max_qubits=18)
+    c = G.Circuit(4, 0.8, 2, 2, 0.1, 2, kappa_qsvt=10.0, d=3)  # 20 qubits
+    f0, _ = I.lbm_instance(4, 0, tau=0.8)
+    with pytest.raises(G.CsimError) as e:
+        pool.submit(c, f0, G.CSIM_C64)
+    assert e.value.status == -2
+    assert pool.stats()["rejected"] == 1
+    pool.close()
+
+
+def test_pool_rejects_requests_larger_than_the_budget():
+    pool = G.Pool(n_streams=2, hbm_budget=8 << 20, max_qubits=30)
+    c = G.Circuit(4, 0.8, 2, 2, 0.1, 2, kappa_qsvt=10.0, d=3)  # 2 x 16 MiB in complex128
+    f0, _ = I.lbm_instance(4, 0, tau=0.8)
+    with pytest.raises(G.CsimError) as e:
+        pool.submit(c, f0, G.CSIM_C128)
+    assert e.value.status == -2
+    pool.close()
