@@ -45,7 +45,20 @@ constexpr int kMuxMinGates = 4;   // shorter RY runs stay individual gates
 bool perm_eligible(const csim_gate& g) {
   return g.op == OP_X && g.target >= 2 && (g.cmask & 3ull) == 0;
 }
-bool local_eligible(const csim_gate& g) { return g.target <= 6; }
+// Tile-local: any gate on state bits 0-6, and a diagonal phase on any qubit
+// (it needs no partner amplitude, only the index bit).
+bool local_eligible(const csim_gate& g) { return g.target <= 6 || g.op == OP_ZPHASE; }
+
+// Whether the permutation gate p (an X with controls) commutes with the
+// tile-local gate l, so that p can move ahead of l inside one sweep: p must
+// not flip a qubit l reads or acts on, and l must not change a qubit p reads
+// (a diagonal l changes none).
+bool commutes(const csim_gate& p, const csim_gate& l) {
+  const uint64_t supp_l = l.cmask | (1ull << l.target);
+  if ((supp_l >> p.target) & 1ull) return false;
+  if (l.op == OP_ZPHASE) return true;
+  return ((p.cmask >> l.target) & 1ull) == 0;
+}
 
 // Cover the set bits of `mask` with at most two windows of total width <=
 // limit (one window when it fits).  Returns false if impossible.
@@ -267,6 +280,10 @@ LocalOp local_op(const csim_gate& g) {
   o.lv = (uint8_t)(g.cval & 3ull);
   o.op = g.op;
   o.target = g.target;
+  if (g.op == OP_ZPHASE && g.target >= 7) {
+    o.op = 6;
+    o.target = (uint8_t)(g.target - 2);
+  }
   double c = 0.0, s = 0.0;
   if (g.op == OP_RY) {
     c = std::cos(g.angle / 2.0);
@@ -617,17 +634,40 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
   }
   std::vector<csim_gate> perm, local;
   bool open = false;
+  const double sweep_cost = std::ldexp(1.0, n);
+  auto single = [&](const csim_gate& g) {
+    Step s;
+    s.kind = 1;
+    s.g = g;
+    p->steps.push_back(s);
+    p->stats.single++;
+  };
   auto close = [&]() {
     if (!open) return;
-    emit_group(p, perm, local);
+    // a group whose gates change fewer amplitudes in total than one sweep
+    // moves (e.g. a few multi-controlled X) runs cheaper as single gates
+    double cost = 0.0;
+    for (const csim_gate& g : perm) cost += gate_amp_updates(g, n);
+    for (const csim_gate& g : local) cost += gate_amp_updates(g, n);
+    if (cost < sweep_cost) {
+      for (const csim_gate& g : perm) single(g);
+      for (const csim_gate& g : local) single(g);
+    } else {
+      emit_group(p, perm, local);
+    }
     perm.clear();
     local.clear();
     open = false;
   };
+  auto commutes_all = [&](const csim_gate& g) {
+    for (const csim_gate& l : local)
+      if (!commutes(g, l)) return false;
+    return true;
+  };
   for (const csim_gate& g : gates) {
     const bool pe = perm_eligible(g), le = local_eligible(g);
     if (!p->scatter) {  // gather form: [perm][local]
-      if (open && local.empty() && pe) {
+      if (open && pe && (local.empty() || commutes_all(g))) {
         perm.push_back(g);
         continue;
       }
@@ -653,11 +693,7 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
       else
         (le ? local : perm).push_back(g);
     } else {
-      Step s;
-      s.kind = 1;
-      s.g = g;
-      p->steps.push_back(s);
-      p->stats.single++;
+      single(g);
     }
   }
   close();
@@ -834,6 +870,20 @@ void emu_ops(const Program& p, const SweepParams& sp, uint32_t tile, double (&v)
         for (int y = 0; y < 4; ++y) {
           v[lane][y][0] = o4[y][0];
           v[lane][y][1] = o4[y][1];
+        }
+      }
+      continue;
+    }
+    if (o.op == 6) {  // e^{i phi Z} on chunk bit o.target
+      for (uint32_t lane = 0; lane < 32; ++lane) {
+        const uint32_t ci = (tile << 5) | lane;
+        if ((ci & o.cm) != o.cv) continue;
+        const double sg = ((ci >> o.target) & 1u) ? -o.sd : o.sd;
+        for (int j = 0; j < 4; ++j) {
+          if (((uint32_t)j & o.lm) != o.lv) continue;
+          const double re = v[lane][j][0], im = v[lane][j][1];
+          v[lane][j][0] = re * o.cd - im * sg;
+          v[lane][j][1] = re * sg + im * o.cd;
         }
       }
       continue;

@@ -385,6 +385,18 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
       continue;
     }
     const R c = Coef<R>::c(o), s = Coef<R>::s(o);
+    if (op == 6) {  // e^{i phi Z} on chunk-index bit tg (a qubit above the tile)
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if ((ci[u] & ocm) != ocv) continue;
+        const R sg = ((ci[u] >> tg) & 1u) ? -s : s;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (((uint32_t)j & lm) == lv)
+            v[u][j] = mk<T>(v[u][j].x * c - v[u][j].y * sg, v[u][j].x * sg + v[u][j].y * c);
+      }
+      continue;
+    }
     if (tg < 2) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {

@@ -31,7 +31,8 @@ struct PermSeg {
 // One gate inside the 128-amplitude warp tile.  Controls are split into the
 // chunk-index part (state bits >= 2) and state bits 0-1.
 // op: 0 X, 1 H, 2 RY, 3 ZPHASE, 4 multiplexed RY (cm = index of its MuxDesc),
-// 5 averaging block (cm = index of its ReflectDesc).
+// 5 averaging block (cm = index of its ReflectDesc), 6 ZPHASE on a qubit above
+// the tile (target = its chunk-index bit, state bit - 2).
 struct LocalOp {
   uint32_t cm, cv;
   uint8_t lm, lv, op, target;

@@ -254,7 +254,7 @@ cudaError_t grow_pinned(Slot* s, size_t stage_bytes, size_t amp_bytes) {
 
 // Enqueue one request's whole run on stream st (the slot's stream, possibly
 // under capture).
-cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s) {
+cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, const char** where) {
   csim_circuit* c = r.c;
   char* base = static_cast<char*>(P->d_arena);
   void* buf[2] = {base + r.offs[0], r.offs[1] != ~0ull ? base + r.offs[1] : nullptr};
@@ -270,31 +270,47 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s) {
   std::memcpy(hs + pat_bytes, r.idx.data(), nnz * 8);
   std::memcpy(hs + pat_bytes + nnz * 8, r.val.data(), nnz * 8);
   cudaStream_t st = s.st;
+  *where = "start event";
   cudaError_t e = cudaEventRecord(s.ev0, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(s.d_pat, hs, pat_bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess) {
+    *where = "pattern copy";
+    e = cudaMemcpyAsync(s.d_pat, hs, pat_bytes, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) {
+    *where = "b copy";
     e = cudaMemcpyAsync(d_stage, hs + pat_bytes, nnz * 16, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) *where = "init";
   if (e == cudaSuccess)
     e = csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n,
                           reinterpret_cast<const uint64_t*>(d_stage),
                           reinterpret_cast<const double*>(d_stage + nnz * 8), (int64_t)nnz, st);
   int cur = 0;
-  if (e == cudaSuccess) e = csim::run_program(c->prog, buf, &cur, r.prec, st);
+  if (e == cudaSuccess) {
+    *where = "program";
+    e = csim::run_program(c->prog, buf, &cur, r.prec, st);
+  }
   int lowk = 0;
   uint64_t lowv = 0;
   csim::mask_low_bits(c, &lowk, &lowv);
+  if (e == cudaSuccess) *where = "norms";
   if (e == cudaSuccess)
     e = csim::launch_norms(buf[cur], r.prec, c->L.n, s.d_pat, s.d_pat + npat, npat, lowk, lowv,
                            s.d_partial, s.d_out, st);
   const csim::CompactGeom g = csim::compact_geom(c);
+  if (e == cudaSuccess) *where = "compaction";
   if (e == cudaSuccess && g.count)
     e = csim::launch_compact(buf[cur], r.prec, d_compact, g.count, g.free_shift, g.free_bits,
                              (uint64_t)c->L.Nt, g.m_shift, st);
+  if (e == cudaSuccess) *where = "result copy";
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(s.h_out, s.d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && g.count)
     e = cudaMemcpyAsync(s.h_amps, d_compact, g.count * 16, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaEventRecord(s.ev1, st);
+  if (e == cudaSuccess) {
+    *where = "end event";
+    e = cudaEventRecord(s.ev1, st);
+  }
   return e;
 }
 
@@ -331,8 +347,11 @@ csim_status admit(csim_pool* P) {
   cudaError_t e = cudaSuccess;
   if (!P->o.use_graphs) {
     for (auto& [id, k] : started) {
-      e = enqueue_request(P, P->reqs[id], P->slots[k]);
-      if (e != cudaSuccess) return pcuda(e, "csim_pool: enqueue");
+      const char* step = "";
+      e = enqueue_request(P, P->reqs[id], P->slots[k], &step);
+      if (e != cudaSuccess)
+        return pfail(CSIM_ERR_CUDA, std::string("csim_pool: enqueue, ") + step + ": " +
+                                        cudaGetErrorString(e));
     }
     return CSIM_OK;
   }
@@ -357,8 +376,9 @@ csim_status admit(csim_pool* P) {
     where = "fork wait";
     e = cudaStreamWaitEvent(s.st, fork, 0);
     if (e == cudaSuccess) {
-      where = "request enqueue";
-      e = enqueue_request(P, P->reqs[started[k].first], s);
+      const char* step = "";
+      e = enqueue_request(P, P->reqs[started[k].first], s, &step);
+      if (e != cudaSuccess) where = step;
     }
     if (e == cudaSuccess) {
       where = "join record";
