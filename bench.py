@@ -449,10 +449,28 @@ def run_serving(args, rank, world, local, torch, G, dist):
                 live.discard(rid)
         return n_adm / (time.perf_counter() - t0), n_adm / len(sub)
 
+    def est_bytes(r):
+        """Algorithmic HBM bytes of one request (0 if it would be rejected)."""
+        try:
+            inf = G.Circuit(r["Nx"], r["tau"], 2, r["K"], 0.1, r["Nt"], kappa_qsvt=10.0,
+                            d=r["d"]).info()
+        except G.CsimError:
+            return 0.0
+        if inf["n_qubits"] > 32:
+            return 0.0
+        esz = 8 if r["prec"] == "c64" else 16
+        return 2.0 * (r["d"] + 1) * (1 << inf["n_qubits"]) * esz
+
     closed_loop(reqs[:8])  # warm-up: kernels, pinned staging
-    capacity, admitted_frac = closed_loop(reqs[:64])
-    # offered load: admitted requests arrive at 0.8 of the measured capacity
-    rate = 0.8 * capacity / max(admitted_frac, 1e-3)
+    calib = reqs[:64]
+    t_cal = time.perf_counter()
+    capacity, admitted_frac = closed_loop(calib)
+    t_cal = time.perf_counter() - t_cal
+    # offered load: 0.8 of the measured byte throughput, spread over the mean
+    # algorithmic bytes of the whole request stream
+    bytes_per_s = sum(est_bytes(r) for r in calib) / t_cal
+    mean_bytes = sum(est_bytes(r) for r in reqs) / len(reqs)
+    rate = 0.8 * bytes_per_s / max(mean_bytes, 1.0)
     arrivals = np.cumsum([r["gap"] for r in reqs]) / rate
     lat = []
     rejected = 0
@@ -503,6 +521,7 @@ def run_serving(args, rank, world, local, torch, G, dist):
         "config": {"workload": args.workload, "requests": count, "completed": len(lat),
                    "rejected_above_32_qubits": rejected,
                    "capacity_admitted_req_per_s": capacity, "admitted_fraction": admitted_frac,
+                   "calibration_bytes_per_s": bytes_per_s,
                    "arrival_rate_req_per_s": rate, "runs_per_s": len(lat) / wall,
                    "latency_ms_p50": pct(0.5), "latency_ms_p99": pct(0.99),
                    "pool_budget_bytes": st["budget"], "pool_peak_bytes": st["peak_bytes"],

@@ -42,6 +42,15 @@ int max_key_bits() {
 }
 constexpr int kMuxMinGates = 4;   // shorter RY runs stay individual gates
 
+// Sibling-aware tile order for gather sweeps (CSIM_TILE_ORDER=0 disables).
+bool tile_order_enabled() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_TILE_ORDER");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+
 bool perm_eligible(const csim_gate& g) {
   return g.op == OP_X && g.target >= 2 && (g.cmask & 3ull) == 0;
 }
@@ -588,9 +597,75 @@ void emit_sweep(Program* p, const std::vector<PermSeg>& segs, const std::vector<
   p->stats.sweeps++;
 }
 
+// Fast tile bits for a gather sweep over the permutation run `perm` (time
+// order, chunk-index space).  A lane of destination chunk x reads source chunk
+// y = P^-1(x); the three other 32-byte chunks of y's 128-byte line are read by
+// the destinations P(y ^ j), j = 1..3.  Sample x, collect the tile-index bits in
+// which those destinations differ from x, and greedily pick bits that make the
+// most of them differ only in chosen bits (a destination differing in u new
+// bits counts 1/u for each).  At most kMaxFast bits, below the tile count.
+void choose_fast_bits(const std::vector<csim_gate>& perm, int n, uint8_t* fast, int* nfast) {
+  *nfast = 0;
+  const int tb = n - 7;  // tile-index bits
+  if (perm.empty() || tb <= 1) return;
+  std::vector<ChunkGate> cg;
+  cg.reserve(perm.size());
+  for (const csim_gate& g : perm) cg.push_back(chunk_gate(g));
+  const uint32_t nch_mask = (n - 2 >= 32) ? 0xffffffffu : ((1u << (n - 2)) - 1u);
+  auto fwd = [&](uint32_t x) {
+    for (const ChunkGate& g : cg)
+      if ((x & g.m) == g.v) x ^= g.t;
+    return x;
+  };
+  auto inv = [&](uint32_t x) {
+    for (size_t k = cg.size(); k-- > 0;)
+      if ((x & cg[k].m) == cg[k].v) x ^= cg[k].t;
+    return x;
+  };
+  std::vector<uint32_t> diffs;
+  uint64_t rs = 0x9e3779b97f4a7c15ull;  // fixed-seed xorshift: deterministic programs
+  for (int s = 0; s < 1024; ++s) {
+    rs ^= rs << 13;
+    rs ^= rs >> 7;
+    rs ^= rs << 17;
+    const uint32_t x = (uint32_t)rs & nch_mask;
+    const uint32_t y = inv(x);
+    for (uint32_t j = 1; j < 4; ++j) {
+      const uint32_t d = ((fwd(y ^ j) ^ x) >> 5);
+      if (d) diffs.push_back(d);
+    }
+  }
+  uint32_t F = 0;
+  const int limit = std::min(kMaxFast, tb - 1);
+  while (*nfast < limit) {
+    std::vector<double> w(tb, 0.0);
+    for (uint32_t d : diffs) {
+      const uint32_t u = d & ~F;
+      if (!u) continue;
+      const double inc = 1.0 / __builtin_popcount(u);
+      for (int b = 0; b < tb; ++b)
+        if ((u >> b) & 1u) w[b] += inc;
+    }
+    int best = -1;
+    double bw = 0.02 * (double)diffs.size();  // stop when a bit helps < 2% of the pairs
+    for (int b = 0; b < tb; ++b)
+      if (!((F >> b) & 1u) && w[b] > bw) {
+        bw = w[b];
+        best = b;
+      }
+    if (best < 0) break;
+    F |= 1u << best;
+    fast[(*nfast)++] = (uint8_t)best;
+  }
+}
+
 // Place one [permutation run, tile-local run] group into sweeps.
 void emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vector<csim_gate>& local) {
   const std::vector<PermSeg> segs = compile_perm(perm, p->scatter, p);
+  uint8_t fast[kMaxFast] = {0};
+  int nfast = 0;
+  if (!p->scatter && tile_order_enabled()) choose_fast_bits(perm, p->n, fast, &nfast);
+  const size_t first_param = p->params.size();
   std::vector<std::vector<PermSeg>> sc;
   for (size_t k = 0; k < segs.size(); k += kMaxSeg)
     sc.emplace_back(segs.begin() + k, segs.begin() + std::min(segs.size(), k + kMaxSeg));
@@ -608,6 +683,12 @@ void emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vecto
     emit_sweep(p, sc.empty() ? std::vector<PermSeg>() : sc[0],
                oc.empty() ? std::vector<OpItem>() : oc.back());
     for (size_t k = 1; k < sc.size(); ++k) emit_sweep(p, sc[k], {});
+  }
+  for (size_t k = first_param; k < p->params.size(); ++k) {
+    SweepParams& sp = p->params[k];
+    if (sp.nseg == 0) continue;  // in place: no gather, natural order
+    sp.nfast = nfast;
+    std::memcpy(sp.fast, fast, sizeof(fast));
   }
 }
 

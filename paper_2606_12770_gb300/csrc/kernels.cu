@@ -476,18 +476,50 @@ __device__ __forceinline__ void permute(const SweepParams& a, uint32_t (&x)[U]) 
 // segments (the inverse permutation), loads it, applies the tile-local ops,
 // and stores contiguously.  Scatter form: the lane loads its own chunk, applies
 // the tile-local ops, and stores to the chunk's image under the permutation.
+//
+// Tile order: warp w takes the tile counters c = w U + u + i (nwarps U).  With
+// nfe > 0 fast bits, counter bit j goes to tile bit fast[j] (j < nfe) and the
+// remaining counter bits fill the other tile bits in ascending order.  The
+// stride is a multiple of 2^nfe, so a warp's low counter bits never change:
+// their deposit L[u] is computed once, and the high part H advances by a
+// masked add of hstep (the deposit of stride >> nfe).  nfe = 0 is the natural
+// order.
 template <typename R, int U, int MINB>
 __global__ void __launch_bounds__(256, MINB) sweep_kernel(const typename V2<R>::T* in,
                                                           typename V2<R>::T* out, uint32_t ntiles,
+                                                          int nfe, uint32_t fmask, uint32_t hstep,
                                                           const __grid_constant__ SweepParams a) {
   using T = typename V2<R>::T;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t t0 = warp * U; t0 < ntiles; t0 += nwarps * U) {
+  const uint32_t c0 = warp * U;
+  uint32_t L[U];
+  uint32_t H = c0;
+  if (nfe > 0) {
+    const uint32_t lo = c0 & ((1u << nfe) - 1u);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      uint32_t d = 0;
+      for (int j = 0; j < nfe; ++j) d |= (((lo + (uint32_t)u) >> j) & 1u) << a.fast[j];
+      L[u] = d;
+    }
+    uint32_t hv = c0 >> nfe;
+    H = 0;
+    for (int b = 0; hv != 0u && b < 32; ++b) {
+      if ((fmask >> b) & 1u) continue;
+      H |= (hv & 1u) << b;
+      hv >>= 1;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < U; ++u) L[u] = (uint32_t)u;
+  }
+  for (uint32_t t0 = c0; t0 < ntiles; t0 += nwarps * U) {
     uint32_t ci[U], mv[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) mv[u] = ci[u] = ((t0 + u) << 5) | lane;
+    for (int u = 0; u < U; ++u) mv[u] = ci[u] = ((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane;
+    H = nfe > 0 ? (((H | fmask) + hstep) & ~fmask) : (H + nwarps * U);
     T v[U][4];
     uint32_t wd[kPrefetchMux][U];
     prefetch_mux<U>(a, ci, wd);
@@ -731,7 +763,22 @@ void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepParam
   const uint64_t need = ((uint64_t)ntiles / U * 32 + blk - 1) / blk;
   if (grd > need) grd = need;
   if (grd < 1) grd = 1;
-  sweep_kernel<R, U, MINB><<<(int)grd, blk, 0, st>>>((const T*)in, (T*)out, ntiles, a);
+  // effective fast bits: the warp stride must be a multiple of 2^nfe, and a
+  // warp's U tiles must fit in one group of 2^nfe
+  const uint32_t stride = (uint32_t)grd * (blk / 32) * U;
+  int nfe = a.nfast;
+  while (nfe > 0 && (stride & ((1u << nfe) - 1u)) != 0u) --nfe;
+  if (nfe > 0 && (1 << nfe) < U) nfe = 0;
+  uint32_t fmask = 0, hstep = 0;
+  for (int j = 0; j < nfe; ++j) fmask |= 1u << a.fast[j];
+  uint32_t hv = stride >> nfe;
+  for (int b = 0; hv != 0u && b < 32; ++b) {
+    if ((fmask >> b) & 1u) continue;
+    hstep |= (hv & 1u) << b;
+    hv >>= 1;
+  }
+  sweep_kernel<R, U, MINB><<<(int)grd, blk, 0, st>>>((const T*)in, (T*)out, ntiles, nfe, fmask,
+                                                      hstep, a);
 }
 
 template <typename R>

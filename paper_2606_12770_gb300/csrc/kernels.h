@@ -77,9 +77,14 @@ struct ReflectDesc {
 // Everything one sweep launch needs, passed by value in the kernel parameter
 // block (constant bank): the permutation segments, the tile-local ops and
 // their descriptors.  Large tables stay in global memory.
-constexpr int kMaxSeg = 32, kMaxOps = 40, kMaxRefl = 4, kMaxMux = 8;
+constexpr int kMaxSeg = 32, kMaxOps = 40, kMaxRefl = 4, kMaxMux = 8, kMaxFast = 12;
 struct SweepParams {
   int nseg, nops, scatter, nmux;
+  // Tile order (gather form): tile-index bits that vary fastest, most useful
+  // first.  Tiles whose sources share 128-byte lines differ in these bits, so
+  // they are processed together and the shared lines are read from DRAM once.
+  int nfast;
+  uint8_t fast[kMaxFast];
   PermSeg segs[kMaxSeg];
   LocalOp ops[kMaxOps];
   ReflectDesc refl[kMaxRefl];

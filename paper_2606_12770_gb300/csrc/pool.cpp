@@ -211,7 +211,7 @@ struct csim_pool {
   // runs, so it cannot tell whether this launch has finished.
   struct Wave {
     cudaGraphExec_t exec = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
     int pending = 0;
   };
   std::vector<Wave> waves;
@@ -254,7 +254,7 @@ cudaError_t grow_pinned(Slot* s, size_t stage_bytes, size_t amp_bytes) {
 
 // Enqueue one request's whole run on stream st (the slot's stream, possibly
 // under capture).
-cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, const char** where) {
+cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, bool in_graph, const char** where) {
   csim_circuit* c = r.c;
   char* base = static_cast<char*>(P->d_arena);
   void* buf[2] = {base + r.offs[0], r.offs[1] != ~0ull ? base + r.offs[1] : nullptr};
@@ -270,8 +270,10 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, const char** wher
   std::memcpy(hs + pat_bytes, r.idx.data(), nnz * 8);
   std::memcpy(hs + pat_bytes + nnz * 8, r.val.data(), nnz * 8);
   cudaStream_t st = s.st;
+  // per-request timing events on the stream path only: events recorded inside
+  // a graph do not time (the wave is timed around the launch instead)
   *where = "start event";
-  cudaError_t e = cudaEventRecord(s.ev0, st);
+  cudaError_t e = in_graph ? cudaSuccess : cudaEventRecord(s.ev0, st);
   if (e == cudaSuccess) {
     *where = "pattern copy";
     e = cudaMemcpyAsync(s.d_pat, hs, pat_bytes, cudaMemcpyHostToDevice, st);
@@ -307,7 +309,7 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, const char** wher
     e = cudaMemcpyAsync(s.h_out, s.d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && g.count)
     e = cudaMemcpyAsync(s.h_amps, d_compact, g.count * 16, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && !in_graph) {
     *where = "end event";
     e = cudaEventRecord(s.ev1, st);
   }
@@ -348,7 +350,7 @@ csim_status admit(csim_pool* P) {
   if (!P->o.use_graphs) {
     for (auto& [id, k] : started) {
       const char* step = "";
-      e = enqueue_request(P, P->reqs[id], P->slots[k], &step);
+      e = enqueue_request(P, P->reqs[id], P->slots[k], false, &step);
       if (e != cudaSuccess)
         return pfail(CSIM_ERR_CUDA, std::string("csim_pool: enqueue, ") + step + ": " +
                                         cudaGetErrorString(e));
@@ -363,6 +365,7 @@ csim_status admit(csim_pool* P) {
   std::vector<cudaEvent_t> joins(started.size(), nullptr);
   for (size_t k = 0; k < started.size() && e == cudaSuccess; ++k)
     e = cudaEventCreateWithFlags(&joins[k], cudaEventDisableTiming);
+  cudaGetLastError();  // a stale non-sticky error must not be read as a capture failure
   if (e == cudaSuccess) {
     where = "begin capture";
     e = cudaStreamBeginCapture(P->origin, cudaStreamCaptureModeThreadLocal);
@@ -371,14 +374,25 @@ csim_status admit(csim_pool* P) {
     where = "fork record";
     e = cudaEventRecord(fork, P->origin);
   }
+  std::string detail;
   for (size_t k = 0; k < started.size() && e == cudaSuccess; ++k) {
     Slot& s = P->slots[started[k].second];
+    const cudaError_t stale = cudaPeekAtLastError();
+    if (stale != cudaSuccess) {
+      detail = std::string(" (pending error before request ") + std::to_string(k) + ": " +
+               cudaGetErrorString(stale) + ")";
+      cudaGetLastError();
+    }
     where = "fork wait";
     e = cudaStreamWaitEvent(s.st, fork, 0);
     if (e == cudaSuccess) {
       const char* step = "";
-      e = enqueue_request(P, P->reqs[started[k].first], s, &step);
-      if (e != cudaSuccess) where = step;
+      e = enqueue_request(P, P->reqs[started[k].first], s, true, &step);
+      if (e != cudaSuccess) {
+        where = step;
+        detail += " (request " + std::to_string(k) + " of " + std::to_string(started.size()) +
+                  ", " + std::to_string(P->reqs[started[k].first].c->L.n) + " qubits)";
+      }
     }
     if (e == cudaSuccess) {
       where = "join record";
@@ -402,8 +416,10 @@ csim_status admit(csim_pool* P) {
   }
   if (e == cudaSuccess) {
     where = "wave event";
-    e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+    e = cudaEventCreate(&w.done);
   }
+  if (e == cudaSuccess) e = cudaEventCreate(&w.start);
+  if (e == cudaSuccess) e = cudaEventRecord(w.start, P->origin);
   if (e == cudaSuccess) {
     where = "launch";
     e = cudaGraphLaunch(w.exec, P->origin);
@@ -420,7 +436,7 @@ csim_status admit(csim_pool* P) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     return pfail(CSIM_ERR_CUDA, std::string("csim_pool: graph ") + where + ": " +
-                                    cudaGetErrorString(e));
+                                    cudaGetErrorString(e) + detail);
   }
   P->stats.graph_launches++;
   return CSIM_OK;
@@ -440,7 +456,13 @@ csim_status retire(csim_pool* P, int* n_retired) {
     r.p = s.h_out[1];
     r.amps.assign(s.h_amps, s.h_amps + 2 * r.count);
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, s.ev0, s.ev1) == cudaSuccess) r.dev_ms = ms;
+    const cudaError_t te = r.wave >= 0
+                               ? cudaEventElapsedTime(&ms, P->waves[r.wave].start, P->waves[r.wave].done)
+                               : cudaEventElapsedTime(&ms, s.ev0, s.ev1);
+    if (te == cudaSuccess)
+      r.dev_ms = ms;
+    else
+      cudaGetLastError();  // a failed timing query must not linger as the last error
     r.t_done = now_s();
     r.st = RState::Done;
     release_all(&P->arena, r.offs);
@@ -456,6 +478,7 @@ csim_status retire(csim_pool* P, int* n_retired) {
     for (csim_pool::Wave& w : P->waves) {
       if (w.exec) cudaGraphExecDestroy(w.exec);
       if (w.done) cudaEventDestroy(w.done);
+      if (w.start) cudaEventDestroy(w.start);
     }
     P->waves.clear();
   }
@@ -470,6 +493,7 @@ void destroy_pool(csim_pool* P) {
   for (csim_pool::Wave& w : P->waves) {
     if (w.exec) cudaGraphExecDestroy(w.exec);
     if (w.done) cudaEventDestroy(w.done);
+    if (w.start) cudaEventDestroy(w.start);
   }
   for (Slot& s : P->slots) {
     if (s.ev0) cudaEventDestroy(s.ev0);
