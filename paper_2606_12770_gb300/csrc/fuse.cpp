@@ -40,6 +40,18 @@ int max_key_bits() {
   }();
   return v;
 }
+// Key bits of a multiplexer bucket table (CSIM_MUX_KEY_BITS overrides).  The
+// bucket word is prefetched before the permutation chain, so a table that
+// lives in L2 rather than L1 costs little, while a wider key leaves fewer
+// lanes with candidate lists (warp-divergent loops).
+int mux_key_bits() {
+  static const int v = [] {
+    const char* e = std::getenv("CSIM_MUX_KEY_BITS");
+    const int k = e ? std::atoi(e) : 0;
+    return (k >= 8 && k <= 18) ? k : 16;
+  }();
+  return v;
+}
 constexpr int kMuxMinGates = 4;   // shorter RY runs stay individual gates
 
 // Sibling-aware tile order for gather sweeps (CSIM_TILE_ORDER=0 disables).
@@ -347,7 +359,7 @@ void compile_mux_group(const std::vector<csim_gate>& grp, Program* p, std::vecto
   KeyWin win{};
   for (int b : order) {
     KeyWin nw;
-    if (cover2(keybits | (1u << b), max_key_bits(), &nw)) {
+    if (cover2(keybits | (1u << b), mux_key_bits(), &nw)) {
       keybits |= 1u << b;
       win = nw;
     }
@@ -597,17 +609,57 @@ void emit_sweep(Program* p, const std::vector<PermSeg>& segs, const std::vector<
   p->stats.sweeps++;
 }
 
-// Fast tile bits for a gather sweep over the permutation run `perm` (time
-// order, chunk-index space).  A lane of destination chunk x reads source chunk
-// y = P^-1(x); the three other 32-byte chunks of y's 128-byte line are read by
-// the destinations P(y ^ j), j = 1..3.  Sample x, collect the tile-index bits in
-// which those destinations differ from x, and greedily pick bits that make the
-// most of them differ only in chosen bits (a destination differing in u new
-// bits counts 1/u for each).  At most kMaxFast bits, below the tile count.
-void choose_fast_bits(const std::vector<csim_gate>& perm, int n, uint8_t* fast, int* nfast) {
+uint32_t emu_permute(const Program& p, const SweepParams& sp, uint32_t x);
+
+// Fraction of DRAM lines fetched per line used by a gather sweep when the
+// tiles of `win` consecutive counters (deposited through the fast bits `fb`)
+// are in flight together: distinct 128-byte source lines x 4 chunks over the
+// chunks read.  Measured reads of the sweep kernel match a window of about 256
+// tiles (the L2 does not keep a line much longer).
+double line_fetch_ratio(const Program& p, const SweepParams& sp, const std::vector<int>& fb,
+                        int tb, uint32_t win, int nwin) {
+  uint32_t fm = 0;
+  for (int b : fb) fm |= 1u << b;
+  const uint32_t ntiles = 1u << tb;
+  std::vector<uint32_t> lines;
+  lines.reserve((size_t)win * 32);
+  double used = 0, fetched = 0;
+  for (int w = 0; w < nwin; ++w) {
+    uint32_t c0 = (uint32_t)(((uint64_t)(2 * w + 1) * 0x9E3779B1u) % ntiles);
+    c0 -= c0 % win;
+    lines.clear();
+    for (uint32_t c = c0; c < c0 + win; ++c) {
+      uint32_t t = 0;
+      for (size_t j = 0; j < fb.size(); ++j) t |= ((c >> j) & 1u) << fb[j];
+      uint32_t hv = c >> fb.size();
+      for (int b = 0; b < 32 && hv; ++b) {
+        if ((fm >> b) & 1u) continue;
+        t |= (hv & 1u) << b;
+        hv >>= 1;
+      }
+      for (uint32_t l = 0; l < 32; ++l) lines.push_back(emu_permute(p, sp, (t << 5) | l) >> 2);
+    }
+    std::sort(lines.begin(), lines.end());
+    fetched += 4.0 * (double)(std::unique(lines.begin(), lines.end()) - lines.begin());
+    used += 32.0 * win;
+  }
+  return fetched / used;
+}
+
+// Fast tile bits for one gather sweep (kernel side: the lowest tile-counter
+// bits go to these tile bits).  A lane of destination chunk x reads the
+// source chunk y = P^-1(x); the other three 32-byte chunks of y's 128-byte
+// line are read by destinations P(y ^ j), j = 1..3.  Candidates are the tile
+// bits in which those destinations differ from x (sampled from the gate run,
+// bits seen in >= 2% of the pairs); greedy selection then keeps each candidate
+// that lowers line_fetch_ratio over a 256-tile window.  States that fit in L2
+// (n < 24) keep the natural order.
+void choose_fast_bits(const std::vector<csim_gate>& perm, const Program& p, const SweepParams& sp,
+                      uint8_t* fast, int* nfast) {
   *nfast = 0;
-  const int tb = n - 7;  // tile-index bits
-  if (perm.empty() || tb <= 1) return;
+  const int n = p.n;
+  const int tb = n - 7;
+  if (perm.empty() || n < 24) return;
   std::vector<ChunkGate> cg;
   cg.reserve(perm.size());
   for (const csim_gate& g : perm) cg.push_back(chunk_gate(g));
@@ -622,7 +674,8 @@ void choose_fast_bits(const std::vector<csim_gate>& perm, int n, uint8_t* fast, 
       if ((x & cg[k].m) == cg[k].v) x ^= cg[k].t;
     return x;
   };
-  std::vector<uint32_t> diffs;
+  std::vector<double> w(tb, 0.0);
+  int npairs = 0;
   uint64_t rs = 0x9e3779b97f4a7c15ull;  // fixed-seed xorshift: deterministic programs
   for (int s = 0; s < 1024; ++s) {
     rs ^= rs << 13;
@@ -631,40 +684,43 @@ void choose_fast_bits(const std::vector<csim_gate>& perm, int n, uint8_t* fast, 
     const uint32_t x = (uint32_t)rs & nch_mask;
     const uint32_t y = inv(x);
     for (uint32_t j = 1; j < 4; ++j) {
-      const uint32_t d = ((fwd(y ^ j) ^ x) >> 5);
-      if (d) diffs.push_back(d);
+      const uint32_t d = (fwd(y ^ j) ^ x) >> 5;
+      ++npairs;
+      for (int b = 0; b < tb; ++b)
+        if ((d >> b) & 1u) w[b] += 1.0;
     }
   }
-  uint32_t F = 0;
-  const int limit = std::min(kMaxFast, tb - 1);
-  while (*nfast < limit) {
-    std::vector<double> w(tb, 0.0);
-    for (uint32_t d : diffs) {
-      const uint32_t u = d & ~F;
-      if (!u) continue;
-      const double inc = 1.0 / __builtin_popcount(u);
-      for (int b = 0; b < tb; ++b)
-        if ((u >> b) & 1u) w[b] += inc;
-    }
+  std::vector<int> cand;
+  for (int b = 0; b < tb; ++b)
+    if (w[b] >= 0.02 * npairs) cand.push_back(b);
+  std::sort(cand.begin(), cand.end(), [&](int x, int y) { return w[x] > w[y]; });
+  if (cand.size() > 12) cand.resize(12);
+  const uint32_t win = std::min<uint32_t>(256u, 1u << (tb - 1));
+  std::vector<int> fb;
+  double cur = line_fetch_ratio(p, sp, fb, tb, win, 2);
+  while ((int)fb.size() < kMaxFast) {
     int best = -1;
-    double bw = 0.02 * (double)diffs.size();  // stop when a bit helps < 2% of the pairs
-    for (int b = 0; b < tb; ++b)
-      if (!((F >> b) & 1u) && w[b] > bw) {
-        bw = w[b];
+    double bv = cur - 0.005;
+    for (int b : cand) {
+      if (std::find(fb.begin(), fb.end(), b) != fb.end()) continue;
+      std::vector<int> t = fb;
+      t.push_back(b);
+      const double v = line_fetch_ratio(p, sp, t, tb, win, 2);
+      if (v < bv) {
+        bv = v;
         best = b;
       }
+    }
     if (best < 0) break;
-    F |= 1u << best;
-    fast[(*nfast)++] = (uint8_t)best;
+    fb.push_back(best);
+    cur = bv;
   }
+  for (int b : fb) fast[(*nfast)++] = (uint8_t)b;
 }
 
 // Place one [permutation run, tile-local run] group into sweeps.
 void emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vector<csim_gate>& local) {
   const std::vector<PermSeg> segs = compile_perm(perm, p->scatter, p);
-  uint8_t fast[kMaxFast] = {0};
-  int nfast = 0;
-  if (!p->scatter && tile_order_enabled()) choose_fast_bits(perm, p->n, fast, &nfast);
   const size_t first_param = p->params.size();
   std::vector<std::vector<PermSeg>> sc;
   for (size_t k = 0; k < segs.size(); k += kMaxSeg)
@@ -684,11 +740,21 @@ void emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vecto
                oc.empty() ? std::vector<OpItem>() : oc.back());
     for (size_t k = 1; k < sc.size(); ++k) emit_sweep(p, sc[k], {});
   }
+  if (p->scatter || !tile_order_enabled()) return;
   for (size_t k = first_param; k < p->params.size(); ++k) {
     SweepParams& sp = p->params[k];
     if (sp.nseg == 0) continue;  // in place: no gather, natural order
-    sp.nfast = nfast;
-    std::memcpy(sp.fast, fast, sizeof(fast));
+    std::string key(reinterpret_cast<const char*>(sp.segs), sp.nseg * sizeof(PermSeg));
+    auto hit = p->order_cache.find(key);
+    if (hit == p->order_cache.end()) {
+      uint8_t fast[kMaxFast] = {0};
+      int nfast = 0;
+      choose_fast_bits(perm, *p, sp, fast, &nfast);
+      hit = p->order_cache.emplace(std::move(key), std::string(reinterpret_cast<char*>(fast), nfast))
+                .first;
+    }
+    sp.nfast = (int)hit->second.size();
+    std::memcpy(sp.fast, hit->second.data(), hit->second.size());
   }
 }
 

@@ -55,6 +55,7 @@ struct Program {
   // circuit repeats them) share one table: content -> table offset
   std::unordered_map<std::string, uint32_t> lut_cache, mux_cache;
   std::vector<MuxDesc> mux_descs;  // compiled multiplexers, indexed by mux_cache
+  std::unordered_map<std::string, std::string> order_cache;  // segments -> fast tile bits
 };
 
 // Build the program for `gates` on an n-qubit state.  FUSED mode needs

@@ -113,6 +113,54 @@ __device__ __forceinline__ double2 shfl_xor_c(double2 v, int m) {
   return make_double2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
+// Sums of the four complex values x[0..3] over all 32 lanes, returned in
+// every lane: a reduce-scatter (each level halves the values a lane carries)
+// followed by an all-gather, 16 shuffles instead of the 40 of four separate
+// butterflies.
+template <typename T, typename R>
+__device__ __forceinline__ void lane_sum4(const T (&x)[4], T (&S)[4], uint32_t lane) {
+  const unsigned full = 0xffffffffu;
+  R a[8] = {x[0].x, x[0].y, x[1].x, x[1].y, x[2].x, x[2].y, x[3].x, x[3].y};
+  const bool h4 = (lane & 16u) != 0, h3 = (lane & 8u) != 0, h2 = (lane & 4u) != 0;
+  R k[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {  // keep values (4 h4 + i)
+    const R send = h4 ? a[i] : a[i + 4];
+    k[i] = (h4 ? a[i + 4] : a[i]) + __shfl_xor_sync(full, send, 16);
+  }
+  R m[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {  // keep (4 h4 + 2 h3 + i)
+    const R send = h3 ? k[i] : k[i + 2];
+    m[i] = (h3 ? k[i + 2] : k[i]) + __shfl_xor_sync(full, send, 8);
+  }
+  R r = (h2 ? m[1] : m[0]) + __shfl_xor_sync(full, h2 ? m[0] : m[1], 4);
+  r += __shfl_xor_sync(full, r, 2);
+  r += __shfl_xor_sync(full, r, 1);  // total of value 4 h4 + 2 h3 + h2
+  const R p = __shfl_xor_sync(full, r, 4);
+  const R q0 = h2 ? p : r, q1 = h2 ? r : p;  // values 4 h4 + 2 h3 + {0, 1}
+  const R u0 = __shfl_xor_sync(full, q0, 8), u1 = __shfl_xor_sync(full, q1, 8);
+  R w[4];  // values 4 h4 + {0..3}
+  w[0] = h3 ? u0 : q0;
+  w[1] = h3 ? u1 : q1;
+  w[2] = h3 ? q0 : u0;
+  w[3] = h3 ? q1 : u1;
+  R z[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) z[i] = __shfl_xor_sync(full, w[i], 16);
+  R t[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    t[i] = h4 ? z[i] : w[i];
+    t[i + 4] = h4 ? w[i] : z[i];
+  }
+#pragma unroll
+  for (int y = 0; y < 4; ++y) {
+    S[y].x = t[2 * y];
+    S[y].y = t[2 * y + 1];
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void apply_pair(typename V2<R>::T& a, typename V2<R>::T& b, int op,
                                            R c, R s) {
@@ -158,12 +206,14 @@ struct Coef<double> {
   static __device__ __forceinline__ double s(const O& o) { return o.sd; }
 };
 
+// key = x[lo0, lo0+w0) | x[lo1, lo1+w1) << w0
 __device__ __forceinline__ uint32_t win_key(uint32_t x, KeyWin w) {
   const uint32_t k0 = (x >> w.lo0) & ((1u << w.w0) - 1u);
   const uint32_t k1 = (x >> w.lo1) & ((1u << w.w1) - 1u);
   return k0 | (k1 << w.w0);
 }
 
+// the inverse placement: x with its window bits replaced by the key v
 __device__ __forceinline__ uint32_t win_put(uint32_t x, uint32_t v, KeyWin w) {
   const uint32_t m0 = (1u << w.w0) - 1u, m1 = (1u << w.w1) - 1u;
   x &= ~((m0 << w.lo0) | (m1 << w.lo1));
@@ -318,6 +368,22 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
       const ReflectDesc& rd = a.refl[ocm];
       const uint32_t lmask = rd.lanemask, nzA = rd.nzA, nzB = rd.nzB;
       if (((nzA | nzB) & ~0x8421u) == 0) {  // A and B diagonal
+        if (lmask == 31u && nzB == 0x8421u) {  // every lane and every y: one joint reduction
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            T S[4];
+            lane_sum4<T, R>(v[u], S, lane);
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+              const int q = y * 5;
+              const T ca = CplxOf<R>::a(rd, q), cb = CplxOf<R>::b(rd, q);
+              const T x = v[u][y];
+              v[u][y] = mk<T>(ca.x * x.x - ca.y * x.y + cb.x * S[y].x - cb.y * S[y].y,
+                              ca.x * x.y + ca.y * x.x + cb.x * S[y].y + cb.y * S[y].x);
+            }
+          }
+          continue;
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
 #pragma unroll
@@ -485,10 +551,9 @@ __device__ __forceinline__ void permute(const SweepParams& a, uint32_t (&x)[U]) 
 // masked add of hstep (the deposit of stride >> nfe).  nfe = 0 is the natural
 // order.
 template <typename R, int U, int MINB>
-__global__ void __launch_bounds__(256, MINB) sweep_kernel(const typename V2<R>::T* in,
-                                                          typename V2<R>::T* out, uint32_t ntiles,
-                                                          int nfe, uint32_t fmask, uint32_t hstep,
-                                                          const __grid_constant__ SweepParams a) {
+__global__ void __launch_bounds__(256, MINB)
+    sweep_kernel(const typename V2<R>::T* in, typename V2<R>::T* out, uint32_t ntiles, int nfe,
+                 uint32_t fmask, uint32_t hstep, const __grid_constant__ SweepParams a) {
   using T = typename V2<R>::T;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -706,19 +771,22 @@ namespace {
 // Tiles per warp iteration (U) and minimum resident blocks per SM (MINB) of
 // the sweep kernel; CSIM_SWEEP_CFG="U,MINB" overrides the defaults.
 struct SweepCfg {
-  int u64, u128, minb;
+  int u64, minb64, u128, minb128;
 };
 
 SweepCfg sweep_cfg() {
   static SweepCfg cfg = [] {
-    SweepCfg c{2, 2, 4};
+    // measured defaults: complex64 two tiles per iteration at 4 blocks/SM;
+    // complex128 one tile at 2 blocks/SM (the wider variants spill)
+    SweepCfg c{2, 4, 1, 2};
     if (const char* e = std::getenv("CSIM_SWEEP_CFG")) {
       int u = 0, m = 0;
       if (std::sscanf(e, "%d,%d", &u, &m) == 2 && (u == 1 || u == 2 || u == 4) &&
           (m == 1 || m == 2 || m == 4)) {
         c.u64 = u;
         c.u128 = u;
-        c.minb = m;
+        c.minb64 = m;
+        c.minb128 = m;
       }
     }
     return c;
@@ -729,8 +797,7 @@ SweepCfg sweep_cfg() {
 // Grid of the sweep kernel in resident waves: blocks = SMs x co-resident
 // blocks per SM x waves (CSIM_SWEEP_WAVES overrides; default 4).  Measured on
 // the 32-qubit QSVT circuit: 4 waves is 3% faster than one persistent wave,
-// and DRAM read traffic is the same for both (the gathered 32-byte chunks of a
-// warp fall in scattered 128-byte lines either way).
+// which also reads more from DRAM.
 int sweep_waves() {
   static const int w = [] {
     const char* e = std::getenv("CSIM_SWEEP_WAVES");
@@ -758,8 +825,7 @@ template <typename R, int U, int MINB>
 void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepParams& a, cudaStream_t st) {
   using T = typename V2<R>::T;
   const int blk = 256;
-  const int resident = sweep_resident<R, U, MINB>();
-  uint64_t grd = (uint64_t)resident * sweep_waves();
+  uint64_t grd = (uint64_t)sweep_resident<R, U, MINB>() * sweep_waves();
   const uint64_t need = ((uint64_t)ntiles / U * 32 + blk - 1) / blk;
   if (grd > need) grd = need;
   if (grd < 1) grd = 1;
@@ -806,9 +872,9 @@ cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const Sweep
   const uint32_t ntiles = 1u << (n - 7);
   const SweepCfg c = sweep_cfg();
   if (prec == CSIM_C64)
-    launch_sweep_r<float>(in, out, ntiles, c.u64, c.minb, a, st);
+    launch_sweep_r<float>(in, out, ntiles, c.u64, c.minb64, a, st);
   else
-    launch_sweep_r<double>(in, out, ntiles, c.u128, c.minb, a, st);
+    launch_sweep_r<double>(in, out, ntiles, c.u128, c.minb128, a, st);
   return cudaGetLastError();
 }
 

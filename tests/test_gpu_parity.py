@@ -272,15 +272,20 @@ print("ok")
 '''
 
 
+@pytest.mark.parametrize("waves", ["4", "1"])
 @pytest.mark.parametrize("form", ["gather", "scatter"])
 @pytest.mark.parametrize("cfg", ["1,1", "2,1", "4,1", "1,2", "2,2", "4,2", "1,4", "2,4"])
-def test_sweep_kernel_variants(cfg, form):
-    """Every compiled sweep-kernel variant (tiles per iteration, blocks per SM, form)."""
+def test_sweep_kernel_variants(cfg, form, waves):
+    """Every compiled sweep-kernel variant (tiles per iteration, blocks per SM,
+    form); one resident wave makes each warp loop over several tiles at 20
+    qubits."""
     import os
     import subprocess
     import sys
+    if waves == "1" and cfg not in ("1,4", "2,4", "4,2"):
+        pytest.skip("single-wave grids are checked on three variants")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, CSIM_SWEEP_CFG=cfg, CSIM_SWEEP_FORM=form)
+    env = dict(os.environ, CSIM_SWEEP_CFG=cfg, CSIM_SWEEP_FORM=form, CSIM_SWEEP_WAVES=waves)
     r = subprocess.run([sys.executable, "-c", VARIANT_SCRIPT, root], env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
