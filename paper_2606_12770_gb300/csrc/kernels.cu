@@ -614,6 +614,24 @@ __device__ __forceinline__ double vec_norm2(const float4 v) {
 }
 __device__ __forceinline__ double vec_norm2(const double2 v) { return v.x * v.x + v.y * v.y; }
 
+// Sum of |a|^2 over four 16-byte vectors.  Complex64: the eight non-negative
+// FP32 products are added in FP32 (relative error below 8 * 2^-24, the size
+// of the products' own rounding) and converted once, so the FP64 pipe, a small
+// fraction of the FP32 rate on this GPU, handles one addition per eight
+// amplitudes.  Complex128: FP64 throughout.
+__device__ __forceinline__ double vec_norm2_4(const float4 a, const float4 b, const float4 c,
+                                              const float4 d) {
+  const float s = ((a.x * a.x + a.y * a.y) + (a.z * a.z + a.w * a.w)) +
+                  ((b.x * b.x + b.y * b.y) + (b.z * b.z + b.w * b.w)) +
+                  (((c.x * c.x + c.y * c.y) + (c.z * c.z + c.w * c.w)) +
+                   ((d.x * d.x + d.y * d.y) + (d.z * d.z + d.w * d.w)));
+  return (double)s;
+}
+__device__ __forceinline__ double vec_norm2_4(const double2 a, const double2 b, const double2 c,
+                                              const double2 d) {
+  return (vec_norm2(a) + vec_norm2(b)) + (vec_norm2(c) + vec_norm2(d));
+}
+
 template <typename R>
 struct Vec16;
 template <>
@@ -643,7 +661,7 @@ __global__ void norm_kernel(const typename V2<R>::T* __restrict__ st, uint64_t N
   for (; i + 3 * stride < nv; i += 4 * stride) {
     const VT v0 = __ldcs(vp + i), v1 = __ldcs(vp + i + stride), v2 = __ldcs(vp + i + 2 * stride),
              v3 = __ldcs(vp + i + 3 * stride);
-    tot += (vec_norm2(v0) + vec_norm2(v1)) + (vec_norm2(v2) + vec_norm2(v3));
+    tot += vec_norm2_4(v0, v1, v2, v3);
   }
   for (; i < nv; i += stride) tot += vec_norm2(__ldcs(vp + i));
   const uint64_t ncand = N >> lowk;
@@ -705,7 +723,7 @@ __global__ void compact_kernel(const typename V2<R>::T* __restrict__ st, double2
   }
 }
 
-int grid_for(uint64_t work, int block) {
+int device_sm_count() {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -713,6 +731,11 @@ int grid_for(uint64_t work, int block) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 132;
   }
+  return sms;
+}
+
+int grid_for(uint64_t work, int block) {
+  const int sms = device_sm_count();
   uint64_t g = (work + block - 1) / block;
   const uint64_t cap = (uint64_t)sms * 16;
   if (g > cap) g = cap;
@@ -881,6 +904,23 @@ cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const Sweep
 int norm_partials_needed() { return 2048; }
 
 namespace {
+// Co-resident 256-thread blocks of the norm kernel on the device (cached).
+int norm_resident(int prec) {
+  static int resident[2] = {0, 0};
+  int& res = resident[prec == CSIM_C64 ? 0 : 1];
+  if (!res) {
+    int per_sm = 0;
+    if (prec == CSIM_C64)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, norm_kernel<float>, 256, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, norm_kernel<double>, 256, 0);
+    res = device_sm_count() * (per_sm > 0 ? per_sm : 1);
+  }
+  return res;
+}
+}  // namespace
+
+namespace {
 template <typename R>
 cudaError_t warm_r() {
   cudaFuncAttributes fa;
@@ -912,6 +952,8 @@ cudaError_t warm_kernels() {
   sweep_cfg();
   sweep_waves();
   grid_for(1, 256);
+  norm_resident(CSIM_C64);
+  norm_resident(CSIM_C128);
   return e;
 }
 
@@ -920,7 +962,11 @@ cudaError_t launch_norms(const void* state, int prec, int n, const uint64_t* d_p
                          double* d_out, cudaStream_t st) {
   const uint64_t N = 1ull << n;
   const int blk = 256;
+  // one full wave of resident blocks (a partial second wave would finish
+  // alone at reduced bandwidth), at most the partial-sum capacity
+  const int res = norm_resident(prec);
   int grd = grid_for(N / 2, blk);
+  if (grd > res) grd = res;
   if (grd > norm_partials_needed()) grd = norm_partials_needed();
   if (prec == CSIM_C64)
     norm_kernel<float><<<grd, blk, 0, st>>>((const float2*)state, N, d_pm, d_pv, npat, lowk, lowv,

@@ -3,8 +3,10 @@ memory) against csim_postselect, through the C ABI, on two calls in a row.
 
 The first call reduces a 20-qubit complex128 state, the second a smaller
 complex64 state with a smaller grid, so a stale partial sum left in the shared
-scratch array by the first call would show up in the second.  Tolerance: both
-paths accumulate in FP64 and differ only in summation order, 1e-12 relative.
+scratch array by the first call would show up in the second.  Tolerances:
+complex128, both paths accumulate in FP64 and differ only in summation order,
+1e-12 relative; complex64, csim_postselect adds eight FP32 products in FP32
+before its FP64 accumulation (relative error below 8 * 2^-24 = 5e-7), 1e-6.
 """
 import numpy as np
 import pytest
@@ -16,10 +18,11 @@ from paper_2606_12770_gb300 import _native as N
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
+TOL_C64 = 1e-6
 
 
-def _close(a, b):
-    return abs(a - b) <= TOL * max(abs(b), 1e-300)
+def _close(a, b, tol=TOL):
+    return abs(a - b) <= tol * max(abs(b), 1e-300)
 
 
 def _run_circuit(cfg, d, prec, stream):
@@ -69,7 +72,7 @@ def test_noalloc_norms_match_postselect_twice():
     N.norms_noalloc(dev2.data_ptr(), n2, G.CSIM_C64, pm2, pv2, out.data_ptr(), stream)
     torch.cuda.synchronize()
     tot2, sel2 = out.cpu().tolist()
-    assert _close(tot2, t2) and _close(sel2, p2), (tot2, t2, sel2, p2)
+    assert _close(tot2, t2, TOL_C64) and _close(sel2, p2), (tot2, t2, sel2, p2)
     assert sel2 != sel1
 
 
