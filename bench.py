@@ -73,6 +73,23 @@ NCU_TRAFFIC = {
 L2_BYTES = 129 * 1000 * 1000
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest value of x over all ranks: the job takes as long as its
+    slowest replica.  dist None (one process) returns x."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each process
+    units_per_rank in the job's time."""
+    return units_per_rank * world / seconds
+
+
 def kernel_hash():
     p = os.path.join(ROOT, "paper_2606_12770_gb300", "csrc", "kernels.cu")
     with open(p, "rb") as fh:
@@ -230,12 +247,9 @@ def run_micro(args, rank, world, local, torch, G, dist):
         dist.barrier()
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
     ms = total_ms / args.steps
-    value = st["amp_updates"] * world / (ms / 1000.0)
+    value = job_rate(st["amp_updates"], world, ms / 1000.0)
     # end to end through the public API: compile the host gate list (fusing and
     # table upload), run, and read back the FP64 norm of the result
     out = torch.zeros(2, dtype=torch.float64, device="cuda")
@@ -370,10 +384,7 @@ def run_batch(args, rank, world, local, torch, G, dist):
     loop_s = time.perf_counter() - t0
     best = min(results, key=lambda k: results[k][0])
     step_s, st = results[best]
-    if dist is not None:
-        t = torch.tensor([step_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_s = float(t.item())
+    step_s = max_over_ranks(step_s, dist)
     peaks, peak_kind = measured_peaks()
     achieved = alg_bytes / step_s / 1e9
     line = {
@@ -643,13 +654,10 @@ def main():
     step_ms = [ev[s][0].elapsed_time(ev[s][3]) for s in range(args.steps)]
     run_ms = [ev[s][1].elapsed_time(ev[s][2]) for s in range(args.steps)]
     total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
     ms_per_step = total_ms / args.steps
     updates = info["amp_updates_run"]
-    value = updates * world / (ms_per_step / 1000.0)
+    value = job_rate(updates, world, ms_per_step / 1000.0)
 
     # end-to-end through the public API with host buffers: H2D of b, D2H of the
     # postselected block into pinned memory, every step
