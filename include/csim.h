@@ -79,7 +79,9 @@ typedef struct {
   int32_t K;           /* Taylor order >= 1 */
   double dt;           /* time step > 0 */
   int32_t Nt;          /* number of time steps >= 1 */
-  int32_t bc;          /* csim_bc; only CSIM_BC_PERIODIC is implemented */
+  int32_t bc;          /* csim_bc: periodic, or bounce-back walls (a population
+                          leaving the lattice returns to its site with the
+                          opposite velocity) */
   double kappa_qsvt;   /* <= 0: kappa(L) = lambda_L / sigma_min(L), computed */
   int32_t d;           /* <= 0: Eq. d-star, odd ceil(kappa ln(2 kappa/eps)/2) */
   double eps;          /* <= 0: 1e-3 */
@@ -105,8 +107,9 @@ typedef struct {
 
 /* --- building (host only; no GPU needed) -------------------------------- */
 
-/* Compile the circuit for the periodic D1Q3 Carleman system of order N_C with
- * Taylor order K, step dt and Nt steps (Sec. II.B-D).  Defaults: periodic, eps
+/* Compile the circuit for the D1Q3 Carleman system of order N_C with Taylor
+ * order K, step dt and Nt steps (Sec. II.B-D), periodic or with the bounce-back
+ * walls of Sec. II.A (csim_build_ex).  Defaults: periodic, eps
  * 1e-3, kappa_qsvt = kappa(L), d from Eq. d-star, phases by Newton iteration.
  * Errors: CSIM_ERR_ARG for invalid parameters (Nx not a power of two >= 2,
  * tau/dt <= 0, N_C not 1/2, K < 1, Nt < 1), CSIM_ERR_TOO_LARGE above

@@ -28,10 +28,10 @@ def system_inputs(lay: Layout) -> np.ndarray:
     return idx
 
 
-def extract_UL(Nx, tau, NC, K, dt, Nt):
+def extract_UL(Nx, tau, NC, K, dt, Nt, bc="periodic"):
     """Return (M_scaled, inputs, lam): M_scaled[r, c] = lambda_L <inputs[r]|U_L|inputs[c]>."""
     lay = Layout(Nx, NC, K, Nt)
-    gates = C.build_UL(Nx, tau, NC, K, dt, Nt)
+    gates = C.build_UL(Nx, tau, NC, K, dt, Nt, bc)
     inputs = system_inputs(lay)
     sim = SparseColumns(lay.n, inputs).run(gates)
     anc = 0
@@ -41,16 +41,16 @@ def extract_UL(Nx, tau, NC, K, dt, Nt):
     pos = {int(v): i for i, v in enumerate(inputs)}
     rows = np.array([pos[int(k)] for k in sim.key[keep]], dtype=np.int64)
     cols = sim.col[keep]
-    lam = float(1 << lay.niL) * C.lmax_value(tau, NC, dt)
+    lam = float(1 << lay.niL) * C.lmax_value(tau, NC, dt, bc)
     N = inputs.shape[0]
     M = sp.csr_matrix((sim.amp[keep] * lam, (rows, cols)), shape=(N, N))
     return M, inputs, lam, lay
 
 
-def compare_with_L(Nx, tau, NC, K, dt, Nt):
+def compare_with_L(Nx, tau, NC, K, dt, Nt, bc="periodic"):
     """Max |M_phys - L| and max |cross terms|, with M extracted from the circuit."""
-    M, inputs, lam, lay = extract_UL(Nx, tau, NC, K, dt, Nt)
-    A = P.carleman_A(Nx, tau, NC, "periodic")
+    M, inputs, lam, lay = extract_UL(Nx, tau, NC, K, dt, Nt, bc)
+    A = P.carleman_A(Nx, tau, NC, bc)
     L = P.l_matrix(A, dt, K, Nt).toarray()
     phys = lay.physical_indices()
     pos = {int(v): i for i, v in enumerate(inputs)}

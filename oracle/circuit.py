@@ -87,13 +87,31 @@ def _dec(bits, ctrl, tag):
     return g
 
 
-def _p11(a, q, i, X, tag):
+def _bounce(a, v, X, tag):
+    """Bounce-back fix-up after periodic streaming of the site register `a` by
+    the velocity register `v` (value 0: e=+1, 1: e=-1).  Periodic streaming
+    leaves the populations that left the lattice at (a=0, v=0) (from the right
+    wall) and (a=Nx-1, v=1) (from the left wall); exchanging these two
+    patterns returns each to its own site with the opposite velocity (the wall
+    rule of reading R2).  The exchange: flip a where v=1, flip v where a=0,
+    flip a where v=1 again (all with v's high bit 0)."""
+    v0, v1 = v
+    base = _ctrl(X, {v1: 0})
+    g = [_gate(OP_X, b, _ctrl(base, {v0: 1}), tag=tag) for b in a]
+    g.append(_gate(OP_X, v0, _ctrl(base, {b: 0 for b in a}), tag=tag))
+    g += [_gate(OP_X, b, _ctrl(base, {v0: 1}), tag=tag) for b in a]
+    return g
+
+
+def _p11(a, q, i, X, tag, bc="periodic"):
     """Collide-then-stream index map of Eq. A11-elements on (a, q) with label i."""
     q0, q1 = q
     i0, i1 = i
     g = []
     g += _inc(a, _ctrl(X, _reg_eq(i, 0)), tag)
     g += _dec(a, _ctrl(X, _reg_eq(i, 1)), tag)
+    if bc == "bounceback":
+        g += _bounce(a, i, X, tag)
     # T1: (q,i) = (0,1) <-> (1,0)
     g.append(_gate(OP_X, q0, _ctrl(X, {i0: 1}), tag=tag))
     g.append(_gate(OP_X, i0, _ctrl(X, {q0: 1, q1: 0, i1: 0}), tag=tag))
@@ -111,7 +129,7 @@ def _p11(a, q, i, X, tag):
     return g
 
 
-def _pi3(lay: Layout, X, tag):
+def _pi3(lay: Layout, X, tag, bc="periodic"):
     """A12 branch (Eq. A12-elements): a2 <- a2 - a1, label bookkeeping, stream, ord flip."""
     r = lay.regs
     a1, a2, q1, q2, i = r["a1"], r["a2"], r["q1"], r["q2"], r["i"]
@@ -127,6 +145,8 @@ def _pi3(lay: Layout, X, tag):
     g.append(_gate(OP_X, i[1], _ctrl(X, {q2[0]: 1}), tag=tag))
     g += _inc(a1, _ctrl(X, _reg_eq(q1, 0)), tag)
     g += _dec(a1, _ctrl(X, _reg_eq(q1, 1)), tag)
+    if bc == "bounceback":
+        g += _bounce(a1, q1, X, tag)
     g.append(_gate(OP_X, r["ord"][0], X, tag=tag))
     return g
 
@@ -144,8 +164,11 @@ def v11(qo, io, tau):
     return 0.0
 
 
-def max_abs_A(tau, NC):
-    """max |A_ij| of the assembled periodic Carleman matrix, from its distinct entries."""
+def max_abs_A(tau, NC, bc="periodic"):
+    """max |A_ij| of the assembled Carleman matrix, from its distinct entries.
+    Bounce-back walls add one diagonal entry per wall, c(q', qbar') - 1 (the
+    bounced coefficient lands on the same row and column as the -1 of the
+    A11 diagonal), and its sums with the second copy's diagonal in A22."""
     vals = []
     for qp in range(3):
         for q in range(3):
@@ -159,23 +182,58 @@ def max_abs_A(tau, NC):
                 for q2 in range(3):
                     vals.append(P.k12(qp, q1, q2, tau))
         vals += [-1.0 + -1.0, -1.0 + c22m1, c22m1 + c22m1]
+    if bc == "bounceback":
+        walls = [P.collision_coeff(0, 1, tau) - 1.0, P.collision_coeff(1, 0, tau) - 1.0]
+        vals += walls
+        if NC == 2:
+            for w in walls:
+                vals += [w + -1.0, w + c22m1]
+                vals += [w + w2 for w2 in walls]
     return max(abs(v) for v in vals)
 
 
-def lmax_value(tau, NC, dt):
-    return max(1.0, dt * max_abs_A(tau, NC))
+def lmax_value(tau, NC, dt, bc="periodic"):
+    return max(1.0, dt * max_abs_A(tau, NC, bc))
 
 
 def _theta(v, ko, dt, Lmax):
     return 2.0 * math.asin((((-dt) * v) / (ko + 1.0)) / Lmax)
 
 
+def _theta0(v, ko, dt, Lmax):
+    return _theta(v, ko, dt, Lmax) if v != 0.0 else 0.0
+
+
+def _wall(lay: Layout, areg, qo):
+    """Site value of the wall whose bounced population lands on output
+    velocity qo: qo = 1 at the right wall (a = Nx-1), qo = 0 at the left (a = 0)."""
+    return _reg_eq(areg, lay.Nx - 1 if qo == 1 else 0)
+
+
+def _wall_fix(lay, base, areg, qreg, vfun, ios, ko, dt, Lmax, t):
+    """Bounce-back value corrections: an output (qo, io) at its wall site
+    carries the entry of the opposite velocity, v(1-qo, io), instead of
+    v(qo, io); a second RY on t adds the angle difference there."""
+    g = []
+    for qo in (0, 1):
+        for io in ios:
+            tw = _theta0(vfun(1 - qo, io), ko, dt, Lmax)
+            tg = _theta0(vfun(qo, io), ko, dt, Lmax)
+            if tw != tg:
+                c = _ctrl(base, _reg_eq(qreg, qo), _wall(lay, areg, qo))
+                g.append(_gate(OP_RY, t, _ctrl(c, ios[io]), tw - tg, TAG_VALUE))
+    return g
+
+
 # -------------------------------------------------------------------- U_L
-def build_UL(Nx, tau, NC, K, dt, Nt):
-    """Gate list of U_L (LAYOUT.md "U_L, in time order")."""
+def build_UL(Nx, tau, NC, K, dt, Nt, bc="periodic"):
+    """Gate list of U_L (LAYOUT.md "U_L, in time order"); bc "periodic" or
+    "bounceback" (reading R2)."""
+    if bc not in ("periodic", "bounceback"):
+        raise ValueError(bc)
     lay = Layout(Nx, NC, K, Nt)
     r = lay.regs
-    Lmax = lmax_value(tau, NC, dt)
+    Lmax = lmax_value(tau, NC, dt, bc)
     t = r["t"][0]
     T = {b: 0 for b in r["e"]}
     C = {lay.top: 1, lay.sel: 0}
@@ -185,12 +243,12 @@ def build_UL(Nx, tau, NC, K, dt, Nt):
     # ---- permutation
     if NC == 2:
         cs, od = r["case"], r["ord"][0]
-        g += _p11(r["a1"], r["q1"], r["i"], _ctrl(T, _reg_eq(cs, 0), {od: 0}), TAG_PERM)
-        g += _p11(r["a1"], r["q1"], r["i"], _ctrl(T, _reg_eq(cs, 1), {od: 1}), TAG_PERM)
-        g += _p11(r["a2"], r["q2"], r["i"], _ctrl(T, _reg_eq(cs, 2), {od: 1}), TAG_PERM)
-        g += _pi3(lay, _ctrl(T, _reg_eq(cs, 3)), TAG_PERM)
+        g += _p11(r["a1"], r["q1"], r["i"], _ctrl(T, _reg_eq(cs, 0), {od: 0}), TAG_PERM, bc)
+        g += _p11(r["a1"], r["q1"], r["i"], _ctrl(T, _reg_eq(cs, 1), {od: 1}), TAG_PERM, bc)
+        g += _p11(r["a2"], r["q2"], r["i"], _ctrl(T, _reg_eq(cs, 2), {od: 1}), TAG_PERM, bc)
+        g += _pi3(lay, _ctrl(T, _reg_eq(cs, 3)), TAG_PERM, bc)
     else:
-        g += _p11(r["a1"], r["q1"], r["i"], dict(T), TAG_PERM)
+        g += _p11(r["a1"], r["q1"], r["i"], dict(T), TAG_PERM, bc)
     g += _inc(r["k"], T, TAG_PERM)
     k, l = r["k"], r["l"]
     for p in prefix_patterns(0, Nt, lay.nm):
@@ -216,6 +274,12 @@ def build_UL(Nx, tau, NC, K, dt, Nt):
                                 c = _ctrl(base, _reg_eq(cs, cval), {od: ordv},
                                           _reg_eq(r[qreg], qo), _reg_eq(r["i"], io))
                                 g.append(_gate(OP_RY, t, c, _theta(v, kn - 1, dt, Lmax), TAG_VALUE))
+                    if bc == "bounceback":
+                        areg = r["a1"] if qreg == "q1" else r["a2"]
+                        g += _wall_fix(lay, _ctrl(base, _reg_eq(cs, cval), {od: ordv}), areg,
+                                       r[qreg], lambda qo, io: v11(qo, io, tau),
+                                       {io: _reg_eq(r["i"], io) for io in range(3)},
+                                       kn - 1, dt, Lmax, t)
                 for qo in range(3):
                     for io in range(4):
                         v = P.k12(qo, io & 1, io >> 1, tau)
@@ -223,6 +287,11 @@ def build_UL(Nx, tau, NC, K, dt, Nt):
                             c = _ctrl(base, _reg_eq(cs, 3), {od: 0}, _reg_eq(r["a2"], 0),
                                       _reg_eq(r["q2"], 0), _reg_eq(r["q1"], qo), _reg_eq(r["i"], io))
                             g.append(_gate(OP_RY, t, c, _theta(v, kn - 1, dt, Lmax), TAG_VALUE))
+                if bc == "bounceback":
+                    g += _wall_fix(lay, _ctrl(base, _reg_eq(cs, 3), {od: 0}, _reg_eq(r["a2"], 0),
+                                              _reg_eq(r["q2"], 0)),
+                                   r["a1"], r["q1"], lambda qo, io: P.k12(qo, io & 1, io >> 1, tau),
+                                   {io: _reg_eq(r["i"], io) for io in range(4)}, kn - 1, dt, Lmax, t)
             else:
                 for qo in range(3):
                     for io in range(4):
@@ -230,6 +299,9 @@ def build_UL(Nx, tau, NC, K, dt, Nt):
                         if v != 0.0:
                             c = _ctrl(base, _reg_eq(r["q1"], qo), _reg_eq(r["i"], io))
                             g.append(_gate(OP_RY, t, c, _theta(v, kn - 1, dt, Lmax), TAG_VALUE))
+                if bc == "bounceback":
+                    g += _wall_fix(lay, base, r["a1"], r["q1"], lambda qo, io: v11(qo, io, tau),
+                                   {io: _reg_eq(r["i"], io) for io in range(3)}, kn - 1, dt, Lmax, t)
     unused0 = {b: 0 for b in r["unused"]}
     th_m1 = 2.0 * math.asin(-1.0 / Lmax)
     for pm in prefix_patterns(1, Nt + 1, lay.nm):
@@ -261,7 +333,7 @@ def phase_gates(lay: Layout, phi):
             _gate(OP_X, s, anc0, tag=TAG_PHASE)]
 
 
-def build_qsvt(Nx, tau, NC, K, dt, Nt, phases):
+def build_qsvt(Nx, tau, NC, K, dt, Nt, phases, bc="periodic"):
     """Fig. circuit-qsvt with signal Hadamards: H, PHI(phi_0), [U_L^dag or U_L, PHI]*d, H.
 
     The first oracle call on b is U_L^dag (the block encoding of L^T): an odd
@@ -273,7 +345,7 @@ def build_qsvt(Nx, tau, NC, K, dt, Nt, phases):
     if d < 1 or d % 2 == 0:
         raise ValueError("need an odd degree d >= 1 (d+1 phases)")
     lay = Layout(Nx, NC, K, Nt)
-    UL = build_UL(Nx, tau, NC, K, dt, Nt)
+    UL = build_UL(Nx, tau, NC, K, dt, Nt, bc)
     ULd = dagger(UL)
     s = lay.regs["s"][0]
     g = [_gate(OP_H, s, tag=TAG_SIGNAL)]

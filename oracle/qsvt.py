@@ -87,14 +87,14 @@ def apply_odd_sv_poly(c: np.ndarray, M: sp.spmatrix, b: np.ndarray) -> np.ndarra
     return y
 
 
-def qsvt_postselected(Nx, tau, NC, K, dt, Nt, f0, phases):
+def qsvt_postselected(Nx, tau, NC, K, dt, Nt, f0, phases, bc="periodic"):
     """Postselected (s=0, ancillas=0) amplitudes on every physical (slot, j).
 
     y = Re(P)^{SV}((L/lambda_L)^T) b.  Returns (y, lay, L/lambda_L, b), y ordered
     like L's rows.
     """
     lay = Layout(Nx, NC, K, Nt)
-    A = P.carleman_A(Nx, tau, NC, "periodic")
+    A = P.carleman_A(Nx, tau, NC, bc)
     L = P.l_matrix(A, dt, K, Nt)
     lam = P.lambda_L(NC, K, P.l_max(A, dt))
     f0 = np.asarray(f0, dtype=np.float64).reshape(Nx, 3)

@@ -151,11 +151,13 @@ class Circuit:
     """Handle of ``csim_circuit`` (csim_build / csim_init / csim_run / csim_postselect)."""
 
     def __init__(self, Nx, tau, N_C, K, dt, Nt, kappa_qsvt=0.0, d=0, eps=0.0,
-                 max_qubits=0, phases=None):
+                 max_qubits=0, phases=None, bc="periodic"):
         lib = load()
         o = BuildOpts()
         o.Nx, o.tau, o.N_C, o.K, o.dt, o.Nt = int(Nx), float(tau), int(N_C), int(K), float(dt), int(Nt)
-        o.bc = 0
+        if bc not in ("periodic", "bounceback"):
+            raise ValueError("bc must be 'periodic' or 'bounceback'")
+        o.bc = 0 if bc == "periodic" else 1
         o.kappa_qsvt, o.d, o.eps, o.max_qubits = float(kappa_qsvt), int(d), float(eps), int(max_qubits)
         self._phases_keep = None
         if phases is not None:

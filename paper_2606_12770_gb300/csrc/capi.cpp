@@ -170,11 +170,12 @@ csim_status csim_build_ex(const csim_build_opts* o, csim_circuit** out) {
   *out = nullptr;
   if (!(o->tau > 0) || !(o->dt > 0) || !std::isfinite(o->tau) || !std::isfinite(o->dt))
     return fail(CSIM_ERR_ARG, "tau and dt must be positive and finite");
-  if (o->bc != CSIM_BC_PERIODIC)
-    return fail(CSIM_ERR_ARG, "only periodic boundaries are implemented in the circuit");
+  if (o->bc != CSIM_BC_PERIODIC && o->bc != CSIM_BC_BOUNCEBACK)
+    return fail(CSIM_ERR_ARG, "bc must be CSIM_BC_PERIODIC or CSIM_BC_BOUNCEBACK");
   Layout L;
   std::string err;
   if (!csim::make_layout(o->Nx, o->N_C, o->K, o->Nt, &L, &err)) return fail(CSIM_ERR_ARG, err);
+  L.bc = o->bc;
   const int maxq = o->max_qubits > 0 ? o->max_qubits : 34;
   if (L.n > maxq || L.n > 62)
     return fail(CSIM_ERR_TOO_LARGE, "circuit needs " + std::to_string(L.n) + " qubits > limit " +
@@ -186,7 +187,7 @@ csim_status csim_build_ex(const csim_build_opts* o, csim_circuit** out) {
   c->dt = o->dt;
   c->max_qubits = maxq;
   c->eps = o->eps > 0 ? o->eps : 1e-3;
-  c->Lmax = csim::lmax_value(o->tau, o->N_C, o->dt);
+  c->Lmax = csim::lmax_value(o->tau, o->N_C, o->dt, o->bc);
   c->lambda = std::ldexp(1.0, L.niL) * c->Lmax;
   try {
     c->UL = csim::build_UL(L, o->tau, o->dt);

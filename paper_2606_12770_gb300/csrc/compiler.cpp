@@ -110,11 +110,26 @@ void dec(std::vector<Gate>& g, const std::vector<int>& bits, Ctrl ctrl, uint16_t
 
 // Collide-then-stream index map on (a, q) with label i: (a, q, i) with q,i <= 2
 // maps to (a + e_i, i, q); label 3 (the subtracted identity) is left in place.
+// Bounce-back fix-up after periodic streaming of the site register a by the
+// velocity register v (value 0: e = +1, 1: e = -1).  Periodic streaming leaves
+// the populations that left the lattice at (a = 0, v = 0) (right wall) and
+// (a = Nx-1, v = 1) (left wall); exchanging the two patterns returns each to
+// its own site with the opposite velocity (reading R2): flip a where v = 1,
+// flip v where a = 0, flip a where v = 1 again (v's high bit 0 throughout).
+void bounce(std::vector<Gate>& g, const std::vector<int>& a, const std::vector<int>& v, Ctrl X,
+            uint16_t tag) {
+  const Ctrl base = merge(X, bit_eq(v[1], 0));
+  for (int b : a) g.push_back(gate(OP_X, b, merge(base, bit_eq(v[0], 1)), 0.0, tag));
+  g.push_back(gate(OP_X, v[0], merge(base, all_eq(a, 0)), 0.0, tag));
+  for (int b : a) g.push_back(gate(OP_X, b, merge(base, bit_eq(v[0], 1)), 0.0, tag));
+}
+
 void p11(std::vector<Gate>& g, const std::vector<int>& a, const std::vector<int>& q,
-         const std::vector<int>& i, Ctrl X, uint16_t tag) {
+         const std::vector<int>& i, Ctrl X, uint16_t tag, bool bb) {
   const int q0 = q[0], q1 = q[1], i0 = i[0], i1 = i[1];
   inc(g, a, merge(X, reg_eq(i, 0)), tag);
   dec(g, a, merge(X, reg_eq(i, 1)), tag);
+  if (bb) bounce(g, a, i, X, tag);
   // (q,i) = (0,1) <-> (1,0)
   g.push_back(gate(OP_X, q0, merge(X, bit_eq(i0, 1)), 0.0, tag));
   g.push_back(gate(OP_X, i0, merge(X, bit_eq(q0, 1), bit_eq(q1, 0), bit_eq(i1, 0)), 0.0, tag));
@@ -131,7 +146,7 @@ void p11(std::vector<Gate>& g, const std::vector<int>& a, const std::vector<int>
 
 // A12 branch (Eq. A12-elements): a2 <- a2 - a1 (zero iff the sites match),
 // move (q1, q2) into the label, q' into q1, stream a1 by e_{q'}, ord 1 -> 0.
-void pi3(std::vector<Gate>& g, const Layout& L, Ctrl X, uint16_t tag) {
+void pi3(std::vector<Gate>& g, const Layout& L, Ctrl X, uint16_t tag, bool bb) {
   for (int j = 0; j < L.na; ++j) {
     std::vector<int> sub(L.a2.begin() + j, L.a2.end());
     dec(g, sub, merge(X, bit_eq(L.a1[j], 1)), tag);
@@ -146,6 +161,7 @@ void pi3(std::vector<Gate>& g, const Layout& L, Ctrl X, uint16_t tag) {
   g.push_back(gate(OP_X, L.i[1], merge(X, bit_eq(L.q2[0], 1)), 0.0, tag));
   inc(g, L.a1, merge(X, reg_eq(L.q1, 0)), tag);
   dec(g, L.a1, merge(X, reg_eq(L.q1, 1)), tag);
+  if (bb) bounce(g, L.a1, L.q1, X, tag);
   g.push_back(gate(OP_X, L.ord[0], X, 0.0, tag));
 }
 
@@ -236,7 +252,10 @@ double v11(int qo, int io, double tau) {
   return 0.0;
 }
 
-double max_abs_A(double tau, int NC) {
+// max |A_ij| of the assembled Carleman matrix.  Bounce-back walls add one
+// diagonal entry per wall, c(q', qbar') - 1, and its sums with the second
+// copy's diagonal in A22.
+double max_abs_A(double tau, int NC, int bc) {
   std::vector<double> vals;
   for (int qp = 0; qp < 3; ++qp)
     for (int q = 0; q < 3; ++q)
@@ -252,15 +271,55 @@ double max_abs_A(double tau, int NC) {
     vals.push_back(-1.0 + c22m1);
     vals.push_back(c22m1 + c22m1);
   }
+  if (bc == CSIM_BC_BOUNCEBACK) {
+    const double walls[2] = {collision_coeff(0, 1, tau) - 1.0, collision_coeff(1, 0, tau) - 1.0};
+    for (double w : walls) vals.push_back(w);
+    if (NC == 2)
+      for (double w : walls) {
+        vals.push_back(w + -1.0);
+        vals.push_back(w + c22m1);
+        for (double w2 : walls) vals.push_back(w + w2);
+      }
+  }
   double m = 0.0;
   for (double v : vals) m = std::max(m, std::fabs(v));
   return m;
 }
 
-double lmax_value(double tau, int NC, double dt) { return std::max(1.0, dt * max_abs_A(tau, NC)); }
+double lmax_value(double tau, int NC, double dt, int bc) {
+  return std::max(1.0, dt * max_abs_A(tau, NC, bc));
+}
+
+namespace {
+double theta0(double v, int ko, double dt, double Lmax) {
+  return v != 0.0 ? theta(v, ko, dt, Lmax) : 0.0;
+}
+
+// Bounce-back value corrections: an output (qo, io) at its wall site (a = Nx-1
+// for qo = 1, a = 0 for qo = 0) carries the entry of the opposite velocity,
+// v(1 - qo, io), instead of v(qo, io); a second RY on t adds the angle
+// difference there.  nio input labels (3 for A11, 4 for A12).
+template <typename F>
+void wall_fix(std::vector<Gate>& g, const Layout& L, const Ctrl& base, const std::vector<int>& areg,
+              const std::vector<int>& qreg, F vfun, int nio, int ko, double dt, double Lmax) {
+  const int t = L.t[0];
+  for (int qo = 0; qo < 2; ++qo)
+    for (int io = 0; io < nio; ++io) {
+      const double tw = theta0(vfun(1 - qo, io), ko, dt, Lmax);
+      const double tg = theta0(vfun(qo, io), ko, dt, Lmax);
+      if (tw != tg) {
+        Ctrl c = merge(base, reg_eq(qreg, (uint64_t)qo),
+                       reg_eq(areg, qo == 1 ? (uint64_t)(L.Nx - 1) : 0));
+        c = merge(c, reg_eq(L.i, (uint64_t)io));
+        g.push_back(gate(OP_RY, t, c, tw - tg, TAG_VALUE));
+      }
+    }
+}
+}  // namespace
 
 std::vector<Gate> build_UL(const Layout& L, double tau, double dt) {
-  const double Lmax = lmax_value(tau, L.NC, dt);
+  const double Lmax = lmax_value(tau, L.NC, dt, L.bc);
+  const bool bb = L.bc == CSIM_BC_BOUNCEBACK;
   const int t = L.t[0];
   const Ctrl T = all_eq(L.e, 0);
   const Ctrl C = merge(bit_eq(L.top, 1), bit_eq(L.sel, 0));
@@ -269,12 +328,12 @@ std::vector<Gate> build_UL(const Layout& L, double tau, double dt) {
   // permutation
   if (L.NC == 2) {
     const int od = L.ord[0];
-    p11(g, L.a1, L.q1, L.i, merge(T, reg_eq(L.cs, 0), bit_eq(od, 0)), TAG_PERM);
-    p11(g, L.a1, L.q1, L.i, merge(T, reg_eq(L.cs, 1), bit_eq(od, 1)), TAG_PERM);
-    p11(g, L.a2, L.q2, L.i, merge(T, reg_eq(L.cs, 2), bit_eq(od, 1)), TAG_PERM);
-    pi3(g, L, merge(T, reg_eq(L.cs, 3)), TAG_PERM);
+    p11(g, L.a1, L.q1, L.i, merge(T, reg_eq(L.cs, 0), bit_eq(od, 0)), TAG_PERM, bb);
+    p11(g, L.a1, L.q1, L.i, merge(T, reg_eq(L.cs, 1), bit_eq(od, 1)), TAG_PERM, bb);
+    p11(g, L.a2, L.q2, L.i, merge(T, reg_eq(L.cs, 2), bit_eq(od, 1)), TAG_PERM, bb);
+    pi3(g, L, merge(T, reg_eq(L.cs, 3)), TAG_PERM, bb);
   } else {
-    p11(g, L.a1, L.q1, L.i, T, TAG_PERM);
+    p11(g, L.a1, L.q1, L.i, T, TAG_PERM, bb);
   }
   inc(g, L.k, T, TAG_PERM);
   for (const Pattern& p : prefix_patterns(0, (uint64_t)L.Nt, L.nm)) {
@@ -297,7 +356,9 @@ std::vector<Gate> build_UL(const Layout& L, double tau, double dt) {
           const std::vector<int>* q;
         };
         const Case cases[3] = {{0, 0, &L.q1}, {1, 1, &L.q1}, {2, 1, &L.q2}};
-        for (const Case& cc : cases)
+        auto vA11 = [tau](int qo, int io) { return v11(qo, io, tau); };
+        auto vA12 = [tau](int qo, int io) { return k12(qo, io & 1, io >> 1, tau); };
+        for (const Case& cc : cases) {
           for (int qo = 0; qo < 3; ++qo)
             for (int io = 0; io < 4; ++io) {
               const double v = v11(qo, io, tau);
@@ -308,6 +369,10 @@ std::vector<Gate> build_UL(const Layout& L, double tau, double dt) {
                 g.push_back(gate(OP_RY, t, c, theta(v, kn - 1, dt, Lmax), TAG_VALUE));
               }
             }
+          if (bb)
+            wall_fix(g, L, merge(base, reg_eq(L.cs, (uint64_t)cc.cval), bit_eq(od, cc.ordv)),
+                     cc.q == &L.q1 ? L.a1 : L.a2, *cc.q, vA11, 3, kn - 1, dt, Lmax);
+        }
         for (int qo = 0; qo < 3; ++qo)
           for (int io = 0; io < 4; ++io) {
             const double v = k12(qo, io & 1, io >> 1, tau);
@@ -317,6 +382,11 @@ std::vector<Gate> build_UL(const Layout& L, double tau, double dt) {
               g.push_back(gate(OP_RY, t, c, theta(v, kn - 1, dt, Lmax), TAG_VALUE));
             }
           }
+        if (bb)
+          wall_fix(g, L,
+                   merge(merge(base, reg_eq(L.cs, 3), bit_eq(od, 0)), reg_eq(L.a2, 0),
+                         reg_eq(L.q2, 0)),
+                   L.a1, L.q1, vA12, 4, kn - 1, dt, Lmax);
       } else {
         for (int qo = 0; qo < 3; ++qo)
           for (int io = 0; io < 4; ++io) {
@@ -326,6 +396,9 @@ std::vector<Gate> build_UL(const Layout& L, double tau, double dt) {
               g.push_back(gate(OP_RY, t, c, theta(v, kn - 1, dt, Lmax), TAG_VALUE));
             }
           }
+        if (bb)
+          wall_fix(g, L, base, L.a1, L.q1, [tau](int qo, int io) { return v11(qo, io, tau); }, 3,
+                   kn - 1, dt, Lmax);
       }
     }
   }

@@ -21,6 +21,7 @@ using Gate = csim_gate;
 // Register layout of Sec. II.D (bit positions, little-endian registers).
 struct Layout {
   int Nx = 0, NC = 0, K = 0, Nt = 0;
+  int bc = CSIM_BC_PERIODIC;  // boundary condition of the streaming step (reading R2)
   int na = 0, nk = 0, nm = 0, niA = 0, niL = 0, n = 0;
   std::vector<int> t, s, iL, i, cs, e, l, unused, q1, a1, q2, a2, ord, k, m, km;
   int top = -1, sel = -1;
@@ -32,8 +33,8 @@ bool make_layout(int Nx, int NC, int K, int Nt, Layout* out, std::string* err);
 double collision_coeff(int qp, int q, double tau);
 double k12(int qp, int q1, int q2, double tau);
 double v11(int qo, int io, double tau);
-double max_abs_A(double tau, int NC);
-double lmax_value(double tau, int NC, double dt);
+double max_abs_A(double tau, int NC, int bc = CSIM_BC_PERIODIC);
+double lmax_value(double tau, int NC, double dt, int bc = CSIM_BC_PERIODIC);
 
 // Gate lists (the canonical construction of oracle/LAYOUT.md).
 std::vector<Gate> build_UL(const Layout& L, double tau, double dt);

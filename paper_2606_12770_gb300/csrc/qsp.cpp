@@ -22,9 +22,12 @@ namespace {
 using cd = std::complex<double>;
 const int E[3] = {1, -1, 0};
 
-// Matrix-free Carleman operator A (periodic) of Eq. carleman-system.
+// Matrix-free Carleman operator A of Eq. carleman-system, periodic or with
+// bounce-back walls (a population leaving the lattice returns to its own site
+// with the opposite velocity, reading R2).
 struct CarlemanOp {
   int Nx, NC;
+  bool bounce = false;
   double tau;
   int n1;      // 3 Nx
   int D;       // n1 (N_C=1) or n1 + n1^2
@@ -41,6 +44,12 @@ struct CarlemanOp {
       }
   }
   int wrap(int a) const { return ((a % Nx) + Nx) % Nx; }
+  // flat index (site * 3 + velocity) that the output population qp of site a streams to
+  int tgt(int a, int qp) const {
+    const int ap = a + E[qp];
+    if (!bounce || (ap >= 0 && ap < Nx)) return wrap(ap) * 3 + qp;
+    return a * 3 + (qp == 0 ? 1 : (qp == 1 ? 0 : qp));
+  }
 
   // y = A11 x on a 3Nx vector (Eq. A11-elements, periodic).
   void a11(const double* x, double* y) const {
@@ -49,7 +58,7 @@ struct CarlemanOp {
       for (int q = 0; q < 3; ++q) {
         const double xv = x[a * 3 + q];
         if (xv == 0.0) continue;
-        for (int qp = 0; qp < 3; ++qp) y[wrap(a + E[qp]) * 3 + qp] += c[qp][q] * xv;
+        for (int qp = 0; qp < 3; ++qp) y[tgt(a, qp)] += c[qp][q] * xv;
       }
   }
   void a11T(const double* x, double* y) const {
@@ -57,7 +66,7 @@ struct CarlemanOp {
     for (int a = 0; a < Nx; ++a)
       for (int q = 0; q < 3; ++q) {
         double acc = 0.0;
-        for (int qp = 0; qp < 3; ++qp) acc += c[qp][q] * x[wrap(a + E[qp]) * 3 + qp];
+        for (int qp = 0; qp < 3; ++qp) acc += c[qp][q] * x[tgt(a, qp)];
         y[a * 3 + q] += acc;
       }
   }
@@ -73,7 +82,7 @@ struct CarlemanOp {
         for (int q2 = 0; q2 < 3; ++q2) {
           const double xv = X2[(size_t)(a * 3 + q1) * n1 + (a * 3 + q2)];
           if (xv == 0.0) continue;
-          for (int qp = 0; qp < 3; ++qp) y[wrap(a + E[qp]) * 3 + qp] += kk[qp][q1][q2] * xv;
+          for (int qp = 0; qp < 3; ++qp) y[tgt(a, qp)] += kk[qp][q1][q2] * xv;
         }
     // A22 = A11 (x) I + I (x) A11 on the row-major matrix X2[p1][p2]
     tmp.assign(n1, 0.0);
@@ -102,7 +111,7 @@ struct CarlemanOp {
       for (int q1 = 0; q1 < 3; ++q1)
         for (int q2 = 0; q2 < 3; ++q2) {
           double acc = 0.0;
-          for (int qp = 0; qp < 3; ++qp) acc += kk[qp][q1][q2] * x[wrap(a + E[qp]) * 3 + qp];
+          for (int qp = 0; qp < 3; ++qp) acc += kk[qp][q1][q2] * x[tgt(a, qp)];
           Y2[(size_t)(a * 3 + q1) * n1 + (a * 3 + q2)] += acc;
         }
     (void)tmp;
@@ -267,6 +276,7 @@ double lanczos_top(const LInverse& Li, int m_steps, int restarts, std::string* e
 
 double kappa_of_L(const Layout& L, double tau, double dt, std::string* err) {
   CarlemanOp A(L.Nx, L.NC, tau);
+  A.bounce = L.bc == CSIM_BC_BOUNCEBACK;
   LInverse Li(A, L.K, L.Nt, L.nk, L.nm, dt);
   const size_t N = Li.size();
   if (N > (size_t)4 << 20) {
@@ -280,7 +290,7 @@ double kappa_of_L(const Layout& L, double tau, double dt, std::string* err) {
     return -1.0;
   }
   const double sigma_min = 1.0 / std::sqrt(top);
-  const double lambda = std::ldexp(1.0, L.niL) * lmax_value(tau, L.NC, dt);
+  const double lambda = std::ldexp(1.0, L.niL) * lmax_value(tau, L.NC, dt, L.bc);
   return lambda / sigma_min;
 }
 

@@ -73,8 +73,8 @@ def test_small_configs_full_state_c128_and_c64(cfg, d):
     assert rel_l2(got64, ref) < 1e-4
 
 
-def _postselected_reference(cfg, f0, phases):
-    y, lay, M, b = Q.qsvt_postselected(*cfg, f0, phases)
+def _postselected_reference(cfg, f0, phases, bc="periodic"):
+    y, lay, M, b = Q.qsvt_postselected(*cfg, f0, phases, bc)
     final = Q.final_slot_mask(lay)
     phys = lay.physical_indices()
     return y, lay, phys, final
@@ -88,13 +88,13 @@ def _gpu_postselected_by_index(c, lay):
     return amps, p, tot, free_shift, free_bits, m_shift
 
 
-def _compare_postselect(c, cfg, f0, phases):
+def _compare_postselect(c, cfg, f0, phases, bc="periodic"):
     """Errors of the GPU postselected block against the classical evaluator.
 
     Returns (max abs error of the physical entries on the unit-norm state,
     relative L2 error of the block, relative error of p, max |non-physical
     entry|, total norm, p_ref)."""
-    y, lay, phys, final = _postselected_reference(cfg, f0, phases)
+    y, lay, phys, final = _postselected_reference(cfg, f0, phases, bc)
     amps, p, tot, free_shift, free_bits, m_shift = _gpu_postselected_by_index(c, lay)
     sel = phys[final]
     m = sel >> m_shift
@@ -130,6 +130,36 @@ def test_c1_postselect_truncated(prec, abs_tol, mode):
     assert abs(tot - 1.0) < (1e-12 if prec == G.CSIM_C128 else 1e-5)
     if prec == G.CSIM_C128:
         assert e_rel < 1e-9
+
+
+@pytest.mark.parametrize("prec,abs_tol", [(G.CSIM_C128, 1e-13), (G.CSIM_C64, 1e-6)])
+def test_bounceback_postselect_truncated(prec, abs_tol):
+    """The walled circuit (reading R2) against the classical evaluator of the
+    walled L, on the 20-qubit configuration with the oracle-fitted 1/x phases;
+    and its full state against the naive simulator of the oracle's walled
+    gate list."""
+    f0, _ = I.lbm_instance(4, 0, tau=0.8)
+    c = G.Circuit(*C1, phases=GOLDEN_PHASES, bc="bounceback")
+    c.init(f0, prec)
+    c.run()
+    e_abs, e_rel, e_p, leak, tot, p_ref = _compare_postselect(c, C1, f0, GOLDEN_PHASES,
+                                                              "bounceback")
+    print(f"bounce-back prec {prec}: abs {e_abs:.2e} block-rel {e_rel:.2e} p {p_ref:.3e}")
+    assert e_abs < abs_tol and leak < abs_tol
+    assert abs(tot - 1.0) < (1e-12 if prec == G.CSIM_C128 else 1e-5)
+    if prec == G.CSIM_C128:
+        ph = I.random_phases(3, 11)
+        cfg = (2, 1.1, 2, 3, 0.1, 2)
+        lay = Layout(2, 2, 3, 2)
+        f2, _ = I.lbm_instance(2, 1, tau=1.1)
+        psi = np.zeros(1 << lay.n, dtype=complex)
+        for k, v in OC.initial_state(lay, f2)[0].items():
+            psi[k] = v
+        S.DenseSim(lay.n).run(psi, OC.build_qsvt(*cfg, list(ph), bc="bounceback"))
+        c2 = G.Circuit(*cfg, phases=ph, bc="bounceback")
+        c2.init(f2, G.CSIM_C128)
+        c2.run()
+        assert rel_l2(c2.read_state(), psi) < 1e-12
 
 
 def test_c1_full_degree_postselect_c128():
