@@ -171,6 +171,27 @@ csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_
 /* Copy the whole state to the host as interleaved doubles (2 * 2^n values). */
 csim_status csim_read_state(csim_circuit* c, double* out, size_t cap_amps);
 
+/* Checkpointed runs, for circuits of large degree (Sec. III.F: d ~ 7e4 calls).
+ * The QSVT circuit is executed as a fixed sequence of program steps (fused
+ * sweeps or single gates; csim_info().n_sweeps_run of them).
+ *   csim_run_steps: after csim_init or csim_restore, enqueue the next n_steps
+ *     steps (fewer at the end); *next_step (may be NULL) receives the index of
+ *     the next step.  When the last step has run, the run is complete, as after
+ *     csim_run.  csim_run finishes a run that csim_run_steps started.
+ *   csim_checkpoint: synchronise, copy the state to the host (2 * 2^n doubles,
+ *     as csim_read_state) and return the next step index.
+ *   csim_restore: load such a state (in either precision) and the step index
+ *     into this or another handle of the same circuit, allocating like
+ *     csim_init, so that csim_run_steps / csim_run continue from there.
+ * A run split at any step boundary, with or without a checkpoint round trip,
+ * gives the same state as csim_run (complex128 round trips are exact).
+ * Errors: CSIM_ERR_STATE without a loaded state, CSIM_ERR_ARG for a bad size
+ * or step index, CSIM_ERR_OOM, CSIM_ERR_CUDA. */
+csim_status csim_run_steps(csim_circuit* c, int64_t n_steps, int64_t* next_step);
+csim_status csim_checkpoint(csim_circuit* c, double* out, size_t cap_amps, int64_t* next_step);
+csim_status csim_restore(csim_circuit* c, const double* amps, size_t n_amps, csim_precision prec,
+                         int64_t next_step, void* cuda_stream);
+
 /* Borrowed device pointer to the circuit's current state: 2^n amplitudes,
  * float2 (complex64) or double2 (complex128) per *prec, index bit b = qubit b.
  * Valid until the next csim_init, csim_run or csim_free of this handle; the

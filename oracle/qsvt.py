@@ -87,7 +87,7 @@ def apply_odd_sv_poly(c: np.ndarray, M: sp.spmatrix, b: np.ndarray) -> np.ndarra
     return y
 
 
-def qsvt_postselected(Nx, tau, NC, K, dt, Nt, f0, phases, bc="periodic"):
+def qsvt_postselected(Nx, tau, NC, K, dt, Nt, f0, phases, bc="periodic", coeffs=None):
     """Postselected (s=0, ancillas=0) amplitudes on every physical (slot, j).
 
     y = Re(P)^{SV}((L/lambda_L)^T) b.  Returns (y, lay, L/lambda_L, b), y ordered
@@ -100,7 +100,7 @@ def qsvt_postselected(Nx, tau, NC, K, dt, Nt, f0, phases, bc="periodic"):
     f0 = np.asarray(f0, dtype=np.float64).reshape(Nx, 3)
     vec = P.carleman_vector(f0.reshape(-1), NC)
     b = P.rhs_vector(vec / np.linalg.norm(vec), K, Nt)
-    c = re_poly_coeffs(phases)
+    c = re_poly_coeffs(phases) if coeffs is None else np.asarray(coeffs)
     if np.max(np.abs(c[0::2])) > 1e-10:
         raise ValueError("Re P is not odd")
     M = L / lam

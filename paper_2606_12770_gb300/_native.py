@@ -31,7 +31,7 @@ EXPORTED = [
     "csim_emulate_fused", "csim_last_error", "csim_norms_noalloc", "csim_state_device",
     "csim_sv_load_device", "csim_sv_device", "csim_sv_stats", "csim_pool_create",
     "csim_pool_submit", "csim_pool_poll", "csim_pool_result", "csim_pool_stats", "csim_pool_free",
-    "csim_pool_plan", "csim_compile",
+    "csim_pool_plan", "csim_compile", "csim_run_steps", "csim_checkpoint", "csim_restore",
 ]
 
 
@@ -92,6 +92,9 @@ def load():
         "csim_init": ([VP, DP, C.c_int, VP], C.c_int),
         "csim_set_exec": ([VP, C.c_int], C.c_int),
         "csim_compile": ([VP], C.c_int),
+        "csim_run_steps": ([VP, C.c_int64, P(C.c_int64)], C.c_int),
+        "csim_checkpoint": ([VP, DP, SZ, P(C.c_int64)], C.c_int),
+        "csim_restore": ([VP, DP, SZ, C.c_int, C.c_int64, VP], C.c_int),
         "csim_run": ([VP], C.c_int),
         "csim_sync": ([VP], C.c_int),
         "csim_postselect": ([VP, DP, SZ, SZP, DP, DP], C.c_int),
@@ -258,6 +261,25 @@ class Circuit:
     def _m_shift(self):
         inf = self.info()
         return inf["n_qubits"] - inf["n_m"]
+
+    def run_steps(self, n_steps):
+        """Enqueue the next n_steps program steps; returns the next step index."""
+        nxt = C.c_int64()
+        _check(_lib.csim_run_steps(self._h, int(n_steps), C.byref(nxt)))
+        return nxt.value
+
+    def checkpoint(self):
+        """(state as complex128 array, next step index)."""
+        N = 1 << self.info()["n_qubits"]
+        out = np.zeros(2 * N)
+        nxt = C.c_int64()
+        _check(_lib.csim_checkpoint(self._h, _dp(out), N, C.byref(nxt)))
+        return out.view(np.complex128), nxt.value
+
+    def restore(self, amps, next_step, precision=CSIM_C128, stream=None):
+        a = np.ascontiguousarray(amps, dtype=np.complex128)
+        _check(_lib.csim_restore(self._h, _dp(a.view(np.float64)), a.shape[0], int(precision),
+                                 int(next_step), _stream_handle(stream)))
 
     def read_state(self) -> np.ndarray:
         N = 1 << self.info()["n_qubits"]

@@ -2,6 +2,7 @@
 // allocation and the run/postselect sequence.  No exception crosses the ABI.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -57,6 +58,48 @@ void free_device(csim_circuit* c) {
   c->prog_built = false;
 }
 
+
+// State buffers (two for the fused path's ping-pong) and the reduction
+// work buffers, reused when the precision and size are unchanged.
+csim_status alloc_state(csim_circuit* c, csim_precision prec) {
+  const Layout& L = c->L;
+  const size_t esz = prec == CSIM_C64 ? 8 : 16;
+  const size_t bytes = ((size_t)1 << L.n) * esz;
+  const int nbuf = c->exec == CSIM_EXEC_FUSED ? 2 : 1;
+  if (c->prec != (int)prec || c->bytes != bytes || (nbuf == 2 && !c->buf[1])) {
+    for (void*& b : c->buf) {
+      if (b) cudaFree(b);
+      b = nullptr;
+    }
+    c->bytes = 0;
+    c->prec = -1;
+    for (int k = 0; k < nbuf; ++k) {
+      cudaError_t e = cudaMalloc(&c->buf[k], bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (void*& b : c->buf) {
+          if (b) cudaFree(b);
+          b = nullptr;
+        }
+        return fail(CSIM_ERR_OOM, "state allocation of " + std::to_string(bytes) + " bytes: " +
+                                      cudaGetErrorString(e));
+      }
+    }
+    c->bytes = bytes;
+    c->prec = prec;
+  }
+  if (!c->d_pat) {
+    cudaError_t e = cudaMalloc(&c->d_pat, 2 * 64 * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_partial, 2 * csim::norm_partials_needed() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_out, 2 * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_device(c);
+      return fail(CSIM_ERR_OOM, "work buffers");
+    }
+  }
+  return CSIM_OK;
+}
 
 }  // namespace
 
@@ -325,40 +368,9 @@ csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec, vo
   }
 
   c->stream = (cudaStream_t)stream;
-  const size_t esz = prec == CSIM_C64 ? 8 : 16;
-  const size_t bytes = ((size_t)1 << L.n) * esz;
-  const int nbuf = c->exec == CSIM_EXEC_FUSED ? 2 : 1;
-  if (c->prec != (int)prec || c->bytes != bytes || (nbuf == 2 && !c->buf[1])) {
-    for (void*& b : c->buf) {
-      if (b) cudaFree(b);
-      b = nullptr;
-    }
-    c->bytes = 0;
-    c->prec = -1;
-    for (int k = 0; k < nbuf; ++k) {
-      cudaError_t e = cudaMalloc(&c->buf[k], bytes);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        for (void*& b : c->buf) {
-          if (b) cudaFree(b);
-          b = nullptr;
-        }
-        return fail(CSIM_ERR_OOM, "state allocation of " + std::to_string(bytes) + " bytes: " +
-                                      cudaGetErrorString(e));
-      }
-    }
-    c->bytes = bytes;
-    c->prec = prec;
-  }
-  if (!c->d_pat) {
-    cudaError_t e = cudaMalloc(&c->d_pat, 2 * 64 * sizeof(uint64_t));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_partial, 2 * csim::norm_partials_needed() * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_out, 2 * sizeof(double));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      free_device(c);
-      return fail(CSIM_ERR_OOM, "work buffers");
-    }
+  {
+    const csim_status st = alloc_state(c, prec);
+    if (st != CSIM_OK) return st;
   }
   uint64_t* d_idx = nullptr;
   double* d_val = nullptr;
@@ -380,6 +392,7 @@ csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec, vo
   if (e != cudaSuccess) return cuda_fail(e, "csim_init");
   c->loaded = true;
   c->ran = false;
+  c->next_step = 0;
   return CSIM_OK;
 }
 
@@ -409,10 +422,79 @@ csim_status csim_run(csim_circuit* c) {
       return fail(CSIM_ERR_OOM, "second state buffer");
     }
   }
-  cudaError_t e = csim::run_program(c->prog, c->buf, &c->cur, c->prec, c->stream);
+  cudaError_t e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream,
+                                          c->next_step, (int64_t)c->prog.steps.size());
   if (e != cudaSuccess) return cuda_fail(e, "csim_run");
+  c->next_step = (int64_t)c->prog.steps.size();
   c->loaded = false;
   c->ran = true;
+  return CSIM_OK;
+}
+
+csim_status csim_run_steps(csim_circuit* c, int64_t n_steps, int64_t* next_step) {
+  if (!c || n_steps < 0) return fail(CSIM_ERR_ARG, "bad argument");
+  if (!c->loaded) return fail(CSIM_ERR_STATE, "csim_run_steps needs csim_init or csim_restore");
+  std::string err;
+  if (!csim::ensure_program(c, c->stream, &err)) return fail(CSIM_ERR_CUDA, err);
+  if (c->prog.pingpong && !c->buf[1]) {
+    cudaError_t e = cudaMalloc(&c->buf[1], c->bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->buf[1] = nullptr;
+      return fail(CSIM_ERR_OOM, "second state buffer");
+    }
+  }
+  const int64_t total = (int64_t)c->prog.steps.size();
+  const int64_t last = std::min(total, c->next_step + n_steps);
+  cudaError_t e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream,
+                                          c->next_step, last);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps");
+  c->next_step = last;
+  if (last == total) {
+    c->loaded = false;
+    c->ran = true;
+  }
+  if (next_step) *next_step = last;
+  return CSIM_OK;
+}
+
+csim_status csim_checkpoint(csim_circuit* c, double* out, size_t cap_amps, int64_t* next_step) {
+  if (!c || !out || !next_step) return fail(CSIM_ERR_ARG, "null argument");
+  const csim_status s = csim_read_state(c, out, cap_amps);
+  if (s != CSIM_OK) return s;
+  *next_step = c->next_step;
+  return CSIM_OK;
+}
+
+csim_status csim_restore(csim_circuit* c, const double* amps, size_t n_amps, csim_precision prec,
+                         int64_t next_step, void* stream) {
+  if (!c || !amps) return fail(CSIM_ERR_ARG, "null argument");
+  if (prec != CSIM_C64 && prec != CSIM_C128) return fail(CSIM_ERR_ARG, "bad precision");
+  const size_t N = (size_t)1 << c->L.n;
+  if (n_amps != N) return fail(CSIM_ERR_ARG, "n_amps must be 2^n");
+  csim::ensure_built(c);
+  const int64_t total = (int64_t)c->prog.steps.size();
+  if (next_step < 0 || next_step > total) return fail(CSIM_ERR_ARG, "next_step out of range");
+  c->stream = (cudaStream_t)stream;
+  {
+    const csim_status st = alloc_state(c, prec);
+    if (st != CSIM_OK) return st;
+  }
+  cudaError_t e;
+  c->cur = 0;
+  if (prec == CSIM_C128) {
+    e = cudaMemcpyAsync(c->buf[0], amps, N * 16, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  } else {
+    std::vector<float> tmp(2 * N);
+    for (size_t i = 0; i < 2 * N; ++i) tmp[i] = (float)amps[i];
+    e = cudaMemcpyAsync(c->buf[0], tmp.data(), N * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "csim_restore");
+  c->next_step = next_step;
+  c->loaded = next_step < total;
+  c->ran = !c->loaded;
   return CSIM_OK;
 }
 

@@ -913,7 +913,13 @@ void free_program(Program* p) {
 }
 
 cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st) {
-  for (const Step& s : p.steps) {
+  return run_program_steps(p, buf, cur, prec, st, 0, (int64_t)p.steps.size());
+}
+
+cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
+                              int64_t first, int64_t last) {
+  for (int64_t k = first; k < last; ++k) {
+    const Step& s = p.steps[(size_t)k];
     cudaError_t e;
     if (s.kind == 1) {
       e = launch_gate(buf[*cur], prec, p.n, s.g, st);

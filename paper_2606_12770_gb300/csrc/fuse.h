@@ -68,6 +68,9 @@ void free_program(Program* p);
 // Run the program on buf[*cur] (and buf[1 - *cur] when it moves data); *cur
 // tracks which buffer holds the state afterwards.
 cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st);
+// Steps [first, last) of the program only (checkpointed runs).
+cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
+                              int64_t first, int64_t last);
 // Host executor of a fused program (FP64, kernel semantics) for testing.
 void emulate_program(const Program& p, std::vector<double>* amps);
 

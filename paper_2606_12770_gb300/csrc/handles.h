@@ -25,6 +25,7 @@ struct csim_circuit {
   size_t bytes = 0;
   csim_exec exec = CSIM_EXEC_FUSED;
   bool loaded = false, ran = false;
+  int64_t next_step = 0;  // next program step of a run in progress (csim_run_steps)
   csim::Program prog;
   bool prog_built = false;
   uint64_t* d_pat = nullptr;  // masks then values

@@ -13,6 +13,9 @@
 #include <cmath>
 #include <complex>
 #include <random>
+#include <string>
+#include <thread>
+#include <vector>
 
 #include "internal.h"
 
@@ -394,6 +397,84 @@ bool lu_solve(std::vector<double>& M, std::vector<double>& b, int n) {
   return true;
 }
 
+// Re <0| e^{i psi_0 Z} W(x) ... W(x) e^{i psi_d Z} |0> at every node, spread
+// over the host's hardware threads (O(d) per node).
+void qsp_w_values(const std::vector<double>& psi, const std::vector<double>& xs,
+                  std::vector<double>* out) {
+  const int d = (int)psi.size() - 1;
+  const size_t nn = xs.size();
+  out->assign(nn, 0.0);
+  std::vector<cd> ph(d + 1);
+  for (int j = 0; j <= d; ++j) ph[j] = std::polar(1.0, psi[j]);
+  auto work = [&](size_t lo, size_t hi) {
+    for (size_t l = lo; l < hi; ++l) {
+      const double x = xs[l], sn = std::sqrt(std::max(0.0, 1.0 - x * x));
+      cd a = ph[0], b = 0.0;
+      for (int j = 1; j <= d; ++j) {
+        const cd na = a * x + b * cd(0, sn), nb = a * cd(0, sn) + b * x;
+        a = na * ph[j];
+        b = nb * std::conj(ph[j]);
+      }
+      (*out)[l] = a.real();
+    }
+  };
+  unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+  if ((size_t)nt > nn / 64 + 1) nt = (unsigned)(nn / 64 + 1);
+  std::vector<std::thread> pool;
+  for (unsigned k = 0; k < nt; ++k)
+    pool.emplace_back(work, nn * k / nt, nn * (k + 1) / nt);
+  for (std::thread& t : pool) t.join();
+}
+
+// Coefficients c_k of sum_k c_k T_{2k+1}(x) from values at the nodes
+// x_l = cos((2l + 1) pi / (4 n)): the matrix cos((2l+1)(2k+1) pi / (4n)) is a
+// DCT-IV, orthogonal up to the factor n / 2.
+void odd_cheb_coeffs(const std::vector<double>& v, std::vector<double>* c) {
+  const size_t n = v.size();
+  c->assign(n, 0.0);
+  auto work = [&](size_t lo, size_t hi) {
+    for (size_t k = lo; k < hi; ++k) {
+      double acc = 0.0;
+      for (size_t l = 0; l < n; ++l)
+        acc += v[l] * std::cos(M_PI * (double)((2 * l + 1) * (2 * k + 1) % (8 * n)) / (4.0 * n));
+      (*c)[k] = 2.0 * acc / (double)n;
+    }
+  };
+  unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+  if ((size_t)nt > n / 64 + 1) nt = (unsigned)(n / 64 + 1);
+  std::vector<std::thread> pool;
+  for (unsigned k = 0; k < nt; ++k) pool.emplace_back(work, n * k / nt, n * (k + 1) / nt);
+  for (std::thread& t : pool) t.join();
+}
+
+// Fixed-point iteration for symmetric phases (Dong, Lin, Ni, Wang): the
+// reduced phase j moves by half the gap between the target's and the current
+// polynomial's coefficients of T_{d-2j}.  Near zero phases the map from
+// reduced phases to those coefficients is -2 times the identity, so the
+// iteration contracts when the target is small (|P| <= 1/2 here).  Each step
+// costs O(d^2), against the O(d^3) LU solve of the Newton step.
+bool fixed_point_phases(int d, const std::vector<double>& xs, const std::vector<double>& f,
+                        std::vector<double>* th, double* res_out) {
+  const int dr = (int)xs.size();
+  std::vector<double> cf, cv, v, psi(d + 1);
+  odd_cheb_coeffs(f, &cf);
+  th->assign(dr, 0.0);
+  double res = 1.0;
+  for (int it = 0; it < 200; ++it) {
+    for (int j = 0; j <= d; ++j) psi[j] = (*th)[std::min(j, d - j)];
+    psi[0] += M_PI / 4;
+    psi[d] += M_PI / 4;
+    qsp_w_values(psi, xs, &v);
+    res = 0.0;
+    for (int l = 0; l < dr; ++l) res = std::max(res, std::fabs(v[l] - f[l]));
+    if (res < 1e-12) break;
+    odd_cheb_coeffs(v, &cv);
+    for (int k = 0; k < dr; ++k) (*th)[(d - 1) / 2 - k] -= 0.5 * (cf[k] - cv[k]);
+  }
+  *res_out = res;
+  return std::isfinite(res);
+}
+
 }  // namespace
 
 bool solve_phases(double kappa, int d, std::vector<double>* phases, double* scale_out,
@@ -416,7 +497,16 @@ bool solve_phases(double kappa, int d, std::vector<double>* phases, double* scal
     psi[d] += M_PI / 4;
   };
   double res = 1.0;
-  for (int it = 0; it < 60; ++it) {
+  // Newton (dense Jacobian) up to kNewtonMax reduced phases; the fixed-point
+  // iteration beyond, where the Jacobian no longer fits
+  const int kNewtonMax = 1024;
+  if (dr > kNewtonMax) {
+    if (!fixed_point_phases(d, xs, f, &th, &res) || !(res < 1e-9)) {
+      *err = "phase solver (fixed point) did not converge, residual " + std::to_string(res);
+      return false;
+    }
+  }
+  for (int it = 0; it < 60 && dr <= kNewtonMax; ++it) {
     expand();
     std::vector<double> J((size_t)dr * dr), F(dr);
     res = 0.0;
@@ -434,7 +524,7 @@ bool solve_phases(double kappa, int d, std::vector<double>* phases, double* scal
     }
     for (int j = 0; j < dr; ++j) th[j] += F[j];
   }
-  if (!(res < 1e-11)) {
+  if (!(res < (dr > kNewtonMax ? 1e-9 : 1e-11))) {
     *err = "phase solver did not converge";
     return false;
   }
