@@ -703,7 +703,9 @@ def main():
                    "tau": tau, "d": info["d"], "qubits": n, "exec": args.exec,
                    "boundary": BOUNDARY.get(args.workload, "periodic"),
                    "state_bytes": (1 << n) * esz,
-                   "l2": ("inputs larger than L2 (state >> 129 MB)" if ((1 << n) * esz) > L2_BYTES
+                   "l2": (f"inputs larger than L2 (state {((1 << n) * esz) / 1e6:.0f} MB, two "
+                          f"ping-pong buffers {2 * ((1 << n) * esz) / 1e6:.0f} MB; L2 129 MB)"
+                          if ((1 << n) * esz) > L2_BYTES
                           else "state resident in L2 (smaller than 129 MB); no flush"),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],

@@ -100,7 +100,9 @@ typedef struct {
   double poly_scale;      /* target polynomial = poly_scale * p(x), p ~ 1/x */
   int64_t n_gates_UL;     /* gates of one U_L */
   int64_t n_gates_total;  /* gates of the whole QSVT circuit */
-  int64_t n_sweeps_run;   /* fused sweeps (HBM passes) per csim_run */
+  int64_t n_sweeps_run;   /* fused sweeps (HBM passes) per csim_run = program steps;
+                             0 until the first csim_run / csim_run_steps fuses
+                             the program (csim_run_steps(c, 0, ...) fuses only) */
   double amp_updates_run; /* sum over gates of amplitudes the gate changes */
   uint64_t state_bytes;   /* bytes of the current state (0 before csim_init) */
 } csim_info_t;
@@ -177,7 +179,9 @@ csim_status csim_read_state(csim_circuit* c, double* out, size_t cap_amps);
  *   csim_run_steps: after csim_init or csim_restore, enqueue the next n_steps
  *     steps (fewer at the end); *next_step (may be NULL) receives the index of
  *     the next step.  When the last step has run, the run is complete, as after
- *     csim_run.  csim_run finishes a run that csim_run_steps started.
+ *     csim_run.  csim_run finishes a run that csim_run_steps started.  With
+ *     n_steps = 0 it fuses the program and runs nothing, after which
+ *     csim_info().n_sweeps_run holds the step count.
  *   csim_checkpoint: synchronise, copy the state to the host (2 * 2^n doubles,
  *     as csim_read_state) and return the next step index.
  *   csim_restore: load such a state (in either precision) and the step index

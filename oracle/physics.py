@@ -5,7 +5,7 @@ assembled entry by entry from the printed formulas, in the paper's own index
 convention: f^(1) is indexed ``alpha*Q + q`` (Sec. II.B, the vector below
 Eq. ode) and f^(2) = f^(1) (x) f^(1) is indexed ``p1*(Q*Nx) + p2``.
 
-Readings of the paper used here (each also listed in the design doc):
+Readings of the paper used here:
 
 * Velocity order e_0=+1, e_1=-1, e_2=0 and weights (1/6, 1/6, 2/3): Sec. II.A.
 * Boundary: ``periodic`` wraps alpha+e mod Nx; ``bounceback`` sends the

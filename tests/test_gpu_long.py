@@ -1,4 +1,4 @@
-"""Checkpointed and long QSVT runs (NEXT-3).
+"""Checkpointed and long QSVT runs.
 
 * A run split into step ranges with a checkpoint round trip through the host
   into a second handle gives the same final state as one csim_run, bit for bit
@@ -68,7 +68,9 @@ def test_paper_long_run_nc1_checkpointed():
     ph = c.export_phases()
     f0, _ = I.lbm_instance(Nx, 0, tau=tau)
     c.init(f0, G.CSIM_C128)
+    assert c.run_steps(0) == 0  # fuses the program, runs nothing
     total = c.info()["n_sweeps_run"]
+    assert total >= d  # one fused sweep per U_L call
     chunk = total // 10 + 1
     t0 = time.perf_counter()
     nxt = c.run_steps(chunk)

@@ -1,8 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (derived in DESIGN.md, "Parity tolerances"):
+Tolerances (derived from the arithmetic of each path):
   * complex128, truncated d, full state vs the naive simulator: 1e-12 relative L2;
-  * complex64, full state: 1e-4 relative L2 (spec bound), expected ~1e-6;
+  * complex64, full state: 1e-4 relative L2 (the complex64 bound), expected ~1e-6;
   * complex128 at the full QSVT degree, postselected block vs the classical
     evaluator: rounding grows with the number of gate applications G as about
     G * 2^-53 on a unit-norm state, relative to the block norm sqrt(p).
