@@ -702,6 +702,8 @@ def main():
         "config": {"workload": args.workload, "Nx": Nx, "N_C": NC, "K": K, "Nt": Nt, "dt": dt,
                    "tau": tau, "d": info["d"], "qubits": n, "exec": args.exec,
                    "boundary": BOUNDARY.get(args.workload, "periodic"),
+                   "gather": (f"source-index tables ({info['n_src_tables']} x {(1 << n) / 1e9:.2f} GB)"
+                              if info["n_src_tables"] else "lookup-table chain"),
                    "state_bytes": (1 << n) * esz,
                    "l2": (f"inputs larger than L2 (state {((1 << n) * esz) / 1e6:.0f} MB, two "
                           f"ping-pong buffers {2 * ((1 << n) * esz) / 1e6:.0f} MB; L2 129 MB)"

@@ -105,6 +105,8 @@ typedef struct {
                              the program (csim_run_steps(c, 0, ...) fuses only) */
   double amp_updates_run; /* sum over gates of amplitudes the gate changes */
   uint64_t state_bytes;   /* bytes of the current state (0 before csim_init) */
+  int32_t n_src_tables;   /* source-index tables the gather sweeps load (2^n bytes
+                             each; 0: the sweeps walk the lookup-table chain) */
 } csim_info_t;
 
 /* --- building (host only; no GPU needed) -------------------------------- */

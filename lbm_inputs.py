@@ -8,6 +8,8 @@ numbers (with ``numpy.random.default_rng``) and lays them out:
   at zero velocity.  The initial distribution is the zero-velocity
   equilibrium of Eq. feq, which reduces to f_q = w_q rho with the D1Q3
   weights (1/6, 1/6, 2/3) in the paper's velocity order (e=+1, -1, 0);
+* the step profile of the paper's QSVT runs (left half 1 + drho/2, right
+  half 1 - drho/2), at zero velocity;
 * relaxation times drawn uniformly from a range;
 * random QSP phase lists for parity tests;
 * the random gate stream of the gate-vocabulary microbenchmark, emitted as
@@ -45,6 +47,15 @@ def lbm_instance(Nx: int, seed: int, tau=None, tau_range=None, amplitude: float 
         tau = float(rng.uniform(lo, hi))
     rho = density_profile(Nx, rng, amplitude)
     return equilibrium_at_rest(rho), float(tau)
+
+
+def step_instance(Nx: int, drho: float) -> np.ndarray:
+    """The step initial condition of the paper's QSVT runs (Sec. III.E): density
+    1 + drho/2 on the left half of the sites and 1 - drho/2 on the right half
+    (the symmetric range [1 - drho/2, 1 + drho/2]), at zero velocity.  Returns
+    f0 of shape (Nx, 3)."""
+    rho = np.where(np.arange(Nx) < Nx // 2, 1.0 + 0.5 * drho, 1.0 - 0.5 * drho)
+    return equilibrium_at_rest(rho)
 
 
 def random_phases(d: int, seed: int) -> np.ndarray:

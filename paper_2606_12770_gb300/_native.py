@@ -66,7 +66,8 @@ class Info(C.Structure):
                 ("lambda_L", C.c_double), ("L_max", C.c_double), ("kappa_qsvt", C.c_double),
                 ("poly_scale", C.c_double), ("n_gates_UL", C.c_int64),
                 ("n_gates_total", C.c_int64), ("n_sweeps_run", C.c_int64),
-                ("amp_updates_run", C.c_double), ("state_bytes", C.c_uint64)]
+                ("amp_updates_run", C.c_double), ("state_bytes", C.c_uint64),
+                ("n_src_tables", C.c_int32)]
 
 
 _lib = None

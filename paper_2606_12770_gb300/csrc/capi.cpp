@@ -21,6 +21,10 @@ using csim::Program;
 namespace {
 thread_local std::string g_err;
 
+// Distinct gather chains that get a source-index table: a QSVT circuit has
+// two (U_L and U_L^dag); a gate stream with more keeps the lookup chains.
+constexpr int kSrcIndexTables = 2;
+
 csim_status fail(csim_status s, const std::string& msg) {
   g_err = msg;
   return s;
@@ -311,6 +315,7 @@ csim_status csim_info(const csim_circuit* c, csim_info_t* out) {
   out->amp_updates_run += 2.0 * std::ldexp(1.0, c->L.n);
   out->n_sweeps_run = c->prog_built ? c->prog.passes : 0;
   out->state_bytes = c->bytes;
+  out->n_src_tables = (int32_t)c->prog.d_src.size();
   return CSIM_OK;
 }
 
@@ -422,7 +427,9 @@ csim_status csim_run(csim_circuit* c) {
       return fail(CSIM_ERR_OOM, "second state buffer");
     }
   }
-  cudaError_t e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream,
+  cudaError_t e = csim::build_src_index(&c->prog, c->stream, kSrcIndexTables);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_run: source index");
+  e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream,
                                           c->next_step, (int64_t)c->prog.steps.size());
   if (e != cudaSuccess) return cuda_fail(e, "csim_run");
   c->next_step = (int64_t)c->prog.steps.size();
@@ -446,7 +453,9 @@ csim_status csim_run_steps(csim_circuit* c, int64_t n_steps, int64_t* next_step)
   }
   const int64_t total = (int64_t)c->prog.steps.size();
   const int64_t last = std::min(total, c->next_step + n_steps);
-  cudaError_t e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream,
+  cudaError_t e = csim::build_src_index(&c->prog, c->stream, kSrcIndexTables);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps: source index");
+  e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream,
                                           c->next_step, last);
   if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps");
   c->next_step = last;
@@ -657,6 +666,8 @@ csim_status csim_sv_compile(csim_sv* s, const csim_gate* gates, size_t n_gates, 
       return fail(CSIM_ERR_OOM, "second state buffer");
     }
   }
+  e = csim::build_src_index(&s->prog, s->stream, kSrcIndexTables);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_sv_compile: source index");
   s->compiled = true;
   return CSIM_OK;
 }

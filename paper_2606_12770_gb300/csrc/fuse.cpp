@@ -899,10 +899,78 @@ cudaError_t upload_program(Program* p, cudaStream_t st) {
   return cudaSuccess;
 }
 
+namespace {
+bool src_index_enabled() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_SRC_INDEX");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+std::string chain_key(const SweepParams& sp) {
+  std::string k;
+  for (int i = 0; i < sp.nseg; ++i) {
+    const PermSeg& g = sp.segs[i];
+    const uint32_t w[8] = {g.win.lo0, g.win.w0, g.win.lo1, g.win.w1,
+                           (uint32_t)g.kind | (uint32_t)g.base << 8 | (uint32_t)g.width << 16 |
+                               (uint32_t)g.neg << 24,
+                           g.m, g.v, g.t};
+    k.append(reinterpret_cast<const char*>(w), sizeof(w));
+  }
+  return k;
+}
+}  // namespace
+
+cudaError_t build_src_index(Program* p, cudaStream_t st, int max_tables) {
+  if (p->src_tried || !p->uploaded) return cudaSuccess;
+  p->src_tried = true;
+  if (!src_index_enabled() || p->scatter || p->n < 7) return cudaSuccess;
+  std::unordered_map<std::string, int> tab_of_key;
+  std::vector<int> tab_of_param(p->params.size(), -1), first_param;
+  for (const Step& s : p->steps) {
+    if (s.kind != 0 || !s.gather) continue;
+    const SweepParams& sp = p->params[(size_t)s.param];
+    if (sp.nseg == 0) continue;
+    auto it = tab_of_key.emplace(chain_key(sp), (int)first_param.size());
+    if (it.second) first_param.push_back(s.param);
+    tab_of_param[(size_t)s.param] = it.first->second;
+  }
+  const int ntab = (int)first_param.size();
+  if (ntab == 0 || ntab > max_tables) return cudaSuccess;
+  const uint64_t bytes = 1ull << p->n;  // 2^(n-2) chunks x 4 bytes
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  if ((uint64_t)ntab * bytes > fr / 4) return cudaSuccess;
+  std::vector<uint32_t*> tabs((size_t)ntab, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (int t = 0; t < ntab && e == cudaSuccess; ++t) {
+    e = cudaMalloc((void**)&tabs[(size_t)t], bytes);
+    if (e == cudaSuccess) e = launch_perm_index(tabs[(size_t)t], p->n, p->params[(size_t)first_param[(size_t)t]], st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    for (uint32_t* q : tabs)
+      if (q) cudaFree(q);
+    return e;
+  }
+  for (size_t k = 0; k < p->params.size(); ++k)
+    if (tab_of_param[k] >= 0) p->params[k].src = tabs[(size_t)tab_of_param[k]];
+  p->d_src = tabs;
+  return cudaSuccess;
+}
+
 void free_program(Program* p) {
   void* ptrs[] = {p->d_lut, p->d_mtab, p->d_mentf, p->d_mentd, p->d_angf, p->d_angd};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (uint32_t* q : p->d_src)
+    if (q) cudaFree(q);
+  p->d_src.clear();
+  p->src_tried = false;
+  for (SweepParams& sp : p->params) sp.src = nullptr;
   p->d_lut = nullptr;
   p->d_mtab = nullptr;
   p->d_mentf = nullptr;

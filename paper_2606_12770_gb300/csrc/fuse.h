@@ -56,6 +56,10 @@ struct Program {
   std::unordered_map<std::string, uint32_t> lut_cache, mux_cache;
   std::vector<MuxDesc> mux_descs;  // compiled multiplexers, indexed by mux_cache
   std::unordered_map<std::string, std::string> order_cache;  // segments -> fast tile bits
+  // source-index tables of the gather sweeps (build_src_index), one per
+  // distinct segment chain
+  std::vector<uint32_t*> d_src;
+  bool src_tried = false;
 };
 
 // Build the program for `gates` on an n-qubit state.  FUSED mode needs
@@ -65,6 +69,13 @@ struct Program {
 void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p);
 cudaError_t upload_program(Program* p, cudaStream_t st);
 void free_program(Program* p);
+// After upload_program: precompute the source-index table of each distinct
+// gather chain (2^(n-2) uint32 entries, 2^n bytes each), so that the sweeps
+// load one index per chunk instead of walking the lookup-table chain.  Skipped
+// (the sweeps keep the chain) when CSIM_SRC_INDEX=0, when the program has more
+// than max_tables distinct chains, or when the tables would take more than a
+// quarter of the free device memory.  Runs once per program.
+cudaError_t build_src_index(Program* p, cudaStream_t st, int max_tables);
 // Run the program on buf[*cur] (and buf[1 - *cur] when it moves data); *cur
 // tracks which buffer holds the state afterwards.
 cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st);

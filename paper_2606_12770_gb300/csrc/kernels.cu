@@ -589,7 +589,12 @@ __global__ void __launch_bounds__(256, MINB)
     uint32_t wd[kPrefetchMux][U];
     prefetch_mux<U>(a, ci, wd);
     if (!a.scatter) {
-      permute<U>(a, mv);
+      if (a.src) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) mv[u] = __ldcs(a.src + ci[u]);
+      } else {
+        permute<U>(a, mv);
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)mv[u] << 2), v[u]);
       apply_ops<R, U>(a, v, ci, lane, wd);
@@ -603,6 +608,20 @@ __global__ void __launch_bounds__(256, MINB)
 #pragma unroll
       for (int u = 0; u < U; ++u) store_chunk(out + ((size_t)mv[u] << 2), v[u]);
     }
+  }
+}
+
+// Source-index table of a gather sweep: the segment chain applied to every
+// chunk index once, so that the sweeps that share the chain load one index
+// per chunk instead of walking the chain.
+__global__ void __launch_bounds__(256)
+    perm_index_kernel(uint32_t* __restrict__ src, uint64_t nchunks,
+                      const __grid_constant__ SweepParams a) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nchunks; x += stride) {
+    uint32_t m[1] = {(uint32_t)x};
+    permute<1>(a, m);
+    src[x] = m[0];
   }
 }
 
@@ -901,6 +920,14 @@ cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const Sweep
   return cudaGetLastError();
 }
 
+cudaError_t launch_perm_index(uint32_t* src, int n, const SweepParams& a, cudaStream_t st) {
+  const uint64_t nchunks = 1ull << (n - 2);
+  const int blk = 256;
+  const int grd = grid_for(nchunks, blk);
+  perm_index_kernel<<<grd, blk, 0, st>>>(src, nchunks, a);
+  return cudaGetLastError();
+}
+
 int norm_partials_needed() { return 2048; }
 
 namespace {
@@ -947,6 +974,7 @@ cudaError_t warm_r() {
 cudaError_t warm_kernels() {
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, reduce_partials_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, perm_index_kernel);
   if (e == cudaSuccess) e = warm_r<float>();
   if (e == cudaSuccess) e = warm_r<double>();
   sweep_cfg();

@@ -95,6 +95,10 @@ struct SweepParams {
   const MuxEntryD* mentd;
   const float2* angf;   // cos, sin of the summed angle of pure buckets
   const double2* angd;
+  // Gather form: when set, src[x] is the source chunk of destination chunk x
+  // (the segments applied to x, precomputed by launch_perm_index), and the
+  // kernel loads it instead of walking the segment chain.
+  const uint32_t* src;
 };
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,
@@ -102,6 +106,9 @@ cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* 
 cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaStream_t st);
 cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
                          cudaStream_t st);
+// src[x] = the segments of `a` applied to chunk index x, for every chunk of an
+// n-qubit state (2^(n-2) entries).
+cudaError_t launch_perm_index(uint32_t* src, int n, const SweepParams& a, cudaStream_t st);
 int norm_partials_needed();
 // Load every kernel of this file and compute the cached launch shapes (before
 // any stream capture).

@@ -302,20 +302,65 @@ print("ok")
 '''
 
 
+@pytest.mark.parametrize("src", ["1", "0"])
 @pytest.mark.parametrize("waves", ["4", "1"])
 @pytest.mark.parametrize("form", ["gather", "scatter"])
 @pytest.mark.parametrize("cfg", ["1,1", "2,1", "4,1", "1,2", "2,2", "4,2", "1,4", "2,4"])
-def test_sweep_kernel_variants(cfg, form, waves):
+def test_sweep_kernel_variants(cfg, form, waves, src):
     """Every compiled sweep-kernel variant (tiles per iteration, blocks per SM,
     form); one resident wave makes each warp loop over several tiles at 20
-    qubits."""
+    qubits.  Gather sweeps run with source-index tables and, on the default
+    variant, with the lookup-table chain."""
     import os
     import subprocess
     import sys
     if waves == "1" and cfg not in ("1,4", "2,4", "4,2"):
         pytest.skip("single-wave grids are checked on three variants")
+    if src == "0" and (form != "gather" or cfg != "2,4"):
+        pytest.skip("the lookup-table chain is checked on the default gather variant")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, CSIM_SWEEP_CFG=cfg, CSIM_SWEEP_FORM=form, CSIM_SWEEP_WAVES=waves)
+    env = dict(os.environ, CSIM_SWEEP_CFG=cfg, CSIM_SWEEP_FORM=form, CSIM_SWEEP_WAVES=waves,
+               CSIM_SRC_INDEX=src)
     r = subprocess.run([sys.executable, "-c", VARIANT_SCRIPT, root], env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
+
+SRC_SCRIPT = r'''
+import sys, numpy as np
+sys.path.insert(0, sys.argv[1])
+import lbm_inputs as I, paper_2606_12770_gb300 as G
+ph = np.loadtxt(sys.argv[1] + "/tests/golden/phases_k10_d31.txt")
+f0, _ = I.lbm_instance(4, 0, tau=0.8)
+out = {}
+for name, prec in (("c128", G.CSIM_C128), ("c64", G.CSIM_C64)):
+    c = G.Circuit(4, 0.8, 2, 2, 0.1, 2, phases=ph)
+    c.init(f0, prec)
+    c.run()
+    out[name] = c.read_state()
+    out[name + "_tables"] = np.array(c.info()["n_src_tables"])
+np.savez(sys.argv[2], **out)
+print("ok")
+'''
+
+
+def test_source_index_tables_equal_lookup_chain(tmp_path):
+    """The gather sweeps give the same state, bit for bit, whether they load the
+    precomputed source index of each chunk or walk the lookup-table chain (the
+    same index, the same arithmetic); the table path is the one in use by
+    default (two tables: U_L and U_L^dag)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for flag in ("0", "1"):
+        path = str(tmp_path / f"src{flag}.npz")
+        env = dict(os.environ, CSIM_SRC_INDEX=flag)
+        r = subprocess.run([sys.executable, "-c", SRC_SCRIPT, root, path], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+        res[flag] = np.load(path)
+    assert int(res["0"]["c128_tables"]) == 0 and int(res["1"]["c128_tables"]) == 2
+    for name in ("c128", "c64"):
+        assert np.array_equal(res["0"][name], res["1"][name]), name
