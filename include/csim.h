@@ -247,10 +247,11 @@ csim_status csim_sv_free(csim_sv* sv);
  * sweeps (lookup-table permutations, multiplexed rotations, warp-tile gates)
  * on the host in FP64 with the kernel's semantics.  amps: 2^n interleaved
  * complex values, updated in place (n in [7, 24]), or NULL to compile only and
- * report the statistics (n in [7, 34]).  For testing the fuser without a GPU.  If stats is non-NULL it receives 13 counters: sweeps,
+ * report the statistics (n in [7, 34]).  For testing the fuser without a GPU.  If stats is non-NULL it receives 14 counters: sweeps,
  * single-gate steps, permutation gates, lookup tables, local gates,
  * multiplexers, multiplexed gates, multiplexer entries, largest bucket,
- * table entries, largest table support, HBM passes, averaging blocks. */
+ * table entries, largest table support, HBM passes, averaging blocks, and
+ * multiplexers run as the inverse of the sweep's previous multiplexer. */
 csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n, double* amps,
                                int64_t* stats);
 
@@ -273,7 +274,7 @@ typedef struct {
   int32_t max_qubits;   /* larger circuits are rejected; <= 0: 32 */
   uint64_t hbm_budget;  /* arena bytes; 0: 90% of the free device memory */
   int32_t use_graphs;   /* 1: one CUDA graph launch per admission pass */
-  uint32_t min_block;   /* smallest arena block in bytes; 0: 1 MiB */
+  uint32_t min_block;   /* smallest arena block in bytes, a multiple of 256; 0: 1 MiB */
 } csim_pool_opts;
 typedef struct {
   int64_t submitted, admitted, completed, rejected, queued, running;

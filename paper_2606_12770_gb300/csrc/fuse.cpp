@@ -18,6 +18,7 @@
 // a high qubit) becomes its own single-gate step.  Sweeps whose descriptors
 // exceed the kernel parameter block are split.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -325,10 +326,26 @@ struct OpItem {
   LocalOp op;
   MuxDesc mux;
   ReflectDesc refl;
+  int mux_id = -1;  // index into Program::mux_descs (op 4)
 };
+
+// Order-free content of a multiplexer's gates, angles optionally negated.
+std::string mux_signature(const std::vector<csim_gate>& grp, bool negate) {
+  std::vector<std::array<uint64_t, 4>> v;
+  for (const csim_gate& g : grp) {
+    double a = negate ? -g.angle : g.angle;
+    if (a == 0.0) a = 0.0;  // one zero
+    uint64_t ab;
+    std::memcpy(&ab, &a, sizeof(ab));
+    v.push_back({(uint64_t)g.target, g.cmask, g.cval, ab});
+  }
+  std::sort(v.begin(), v.end());
+  return std::string(reinterpret_cast<const char*>(v.data()), v.size() * sizeof(v[0]));
+}
 
 OpItem out_item_of(const Program* p, uint32_t mux_index) {
   OpItem it{};
+  it.mux_id = (int)mux_index;
   it.mux = p->mux_descs[mux_index];
   it.op.op = 4;
   it.op.target = it.mux.target;
@@ -411,8 +428,20 @@ void compile_mux_group(const std::vector<csim_gate>& grp, Program* p, std::vecto
   }
   it.op.op = 4;
   it.op.target = grp[0].target;
-  p->mux_cache.emplace(std::move(ckey), (uint32_t)p->mux_descs.size());
+  const uint32_t id = (uint32_t)p->mux_descs.size();
+  it.mux_id = (int)id;
+  p->mux_cache.emplace(std::move(ckey), id);
   p->mux_descs.push_back(it.mux);
+  p->mux_inv.push_back(-1);
+  p->mux_sig.emplace(mux_signature(grp, false), id);
+  const auto inv = p->mux_sig.find(mux_signature(grp, true));
+  if (inv != p->mux_sig.end() && inv->second != id) {
+    const MuxDesc& o = p->mux_descs[inv->second];
+    if (o.target == it.mux.target && o.lm == it.mux.lm && o.lv == it.mux.lv) {
+      p->mux_inv[id] = (int)inv->second;
+      p->mux_inv[inv->second] = (int)id;
+    }
+  }
   out->push_back(it);
   p->stats.mux++;
   p->stats.mux_gates += (int64_t)grp.size();
@@ -588,11 +617,22 @@ void emit_sweep(Program* p, const std::vector<PermSeg>& segs, const std::vector<
   sp.nseg = (int)segs.size();
   for (size_t k = 0; k < segs.size(); ++k) sp.segs[k] = segs[k];
   int nmux = 0, nrefl = 0;
+  int last_mux = -1;  // the sweep's latest multiplexer (op 4), by mux_descs index
   for (const OpItem& it : ops) {
     LocalOp o = it.op;
-    if (o.op == 4) {
+    if (o.op == 4 && it.mux_id >= 0 && last_mux >= 0 && p->mux_inv[(size_t)it.mux_id] == last_mux) {
+      // the inverse of the latest multiplexer: the kernel reuses its rotation
+      o.op = 7;
+      o.target = it.mux.target;
+      o.lm = it.mux.lm;
+      o.lv = it.mux.lv;
+      o.cm = o.cv = 0;
+      last_mux = -1;
+      p->stats.mux_inverse++;
+    } else if (o.op == 4) {
       sp.mux[nmux] = it.mux;
       o.cm = (uint32_t)nmux++;
+      last_mux = it.mux_id;
     } else if (o.op == 5) {
       sp.refl[nrefl] = it.refl;
       o.cm = (uint32_t)nrefl++;
@@ -861,6 +901,23 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
                  (long long)f.lut_entries, (long long)f.local_gates, (long long)f.mux,
                  (long long)f.mux_gates, (long long)f.mux_entries, (long long)f.max_bucket,
                  (long long)f.reflect);
+    if (std::getenv("CSIM_FUSE_STATS")[0] == '2') {
+      // one line per fused sweep: segments by kind, then the local ops
+      for (size_t k = 0; k < p->steps.size(); ++k) {
+        const Step& st = p->steps[k];
+        if (st.kind != 0) {
+          std::fprintf(stderr, "[csim fuse] step %zu: single gate op %d target %d\n", k,
+                       (int)st.g.op, (int)st.g.target);
+          continue;
+        }
+        const SweepParams& sp = p->params[(size_t)st.param];
+        std::string segs, ops;
+        for (int i = 0; i < sp.nseg; ++i) segs += "TGI"[sp.segs[i].kind];
+        for (int i = 0; i < sp.nops; ++i) ops += "XHRZMAPI"[sp.ops[i].op];
+        std::fprintf(stderr, "[csim fuse] step %zu: segs %s ops %s mux %d\n", k, segs.c_str(),
+                     ops.c_str(), sp.nmux);
+      }
+    }
   }
 }
 
@@ -907,6 +964,14 @@ bool src_index_enabled() {
   }();
   return v;
 }
+// Source indices loaded one loop iteration ahead (CSIM_SRC_PREFETCH=0 disables).
+bool src_prefetch_enabled() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_SRC_PREFETCH");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
 std::string chain_key(const SweepParams& sp) {
   std::string k;
   for (int i = 0; i < sp.nseg; ++i) {
@@ -948,7 +1013,8 @@ cudaError_t build_src_index(Program* p, cudaStream_t st, int max_tables) {
   cudaError_t e = cudaSuccess;
   for (int t = 0; t < ntab && e == cudaSuccess; ++t) {
     e = cudaMalloc((void**)&tabs[(size_t)t], bytes);
-    if (e == cudaSuccess) e = launch_perm_index(tabs[(size_t)t], p->n, p->params[(size_t)first_param[(size_t)t]], st);
+    if (e == cudaSuccess)
+      e = launch_perm_index(tabs[(size_t)t], p->n, p->params[(size_t)first_param[(size_t)t]], st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -957,7 +1023,10 @@ cudaError_t build_src_index(Program* p, cudaStream_t st, int max_tables) {
     return e;
   }
   for (size_t k = 0; k < p->params.size(); ++k)
-    if (tab_of_param[k] >= 0) p->params[k].src = tabs[(size_t)tab_of_param[k]];
+    if (tab_of_param[k] >= 0) {
+      p->params[k].src = tabs[(size_t)tab_of_param[k]];
+      p->params[k].src_prefetch = src_prefetch_enabled() ? 1 : 0;
+    }
   p->d_src = tabs;
   return cudaSuccess;
 }
@@ -970,7 +1039,10 @@ void free_program(Program* p) {
     if (q) cudaFree(q);
   p->d_src.clear();
   p->src_tried = false;
-  for (SweepParams& sp : p->params) sp.src = nullptr;
+  for (SweepParams& sp : p->params) {
+    sp.src = nullptr;
+    sp.src_prefetch = 0;
+  }
   p->d_lut = nullptr;
   p->d_mtab = nullptr;
   p->d_mentf = nullptr;
@@ -1035,6 +1107,18 @@ uint32_t emu_permute(const Program& p, const SweepParams& sp, uint32_t x) {
 }
 
 void emu_ops(const Program& p, const SweepParams& sp, uint32_t tile, double (&v)[32][4][2]) {
+  double mc[32], ms[32];  // the latest multiplexer's rotation per lane (op 7 inverts it)
+  for (int l = 0; l < 32; ++l) {
+    mc[l] = 1.0;
+    ms[l] = 0.0;
+  }
+  auto rot_all = [&](uint32_t lane, int target, uint32_t lm, uint32_t lv, double c, double s) {
+    for (int j0 = 0; j0 < 4; ++j0) {
+      if (j0 & (1 << target)) continue;
+      if (((uint32_t)j0 & lm) != lv) continue;
+      pair_op(v[lane][j0], v[lane][j0 | (1 << target)], 2, c, s);
+    }
+  };
   for (int k = 0; k < sp.nops; ++k) {
     const LocalOp& o = sp.ops[k];
     if (o.op == 4) {
@@ -1042,24 +1126,30 @@ void emu_ops(const Program& p, const SweepParams& sp, uint32_t tile, double (&v)
       for (uint32_t lane = 0; lane < 32; ++lane) {
         const uint32_t ci = (tile << 5) | lane;
         const uint32_t word = p.mtab[md.tab_off + win_key(ci, md.win)];
-        if (word == 0u) continue;
-        auto rot_all = [&](double c, double s) {
-          for (int j0 = 0; j0 < 4; ++j0) {
-            if (j0 & (1 << md.target)) continue;
-            if (((uint32_t)j0 & md.lm) != md.lv) continue;
-            pair_op(v[lane][j0], v[lane][j0 | (1 << md.target)], 2, c, s);
-          }
-        };
+        double c = 1.0, s = 0.0;
         if (word & 0x80000000u) {
           const double2 cs = p.angd[word & 0x7fffffffu];
-          rot_all(cs.x, cs.y);
-          continue;
+          c = cs.x;
+          s = cs.y;
+        } else if (word != 0u) {
+          for (uint32_t e = word >> 8; e < (word >> 8) + (word & 255u); ++e) {
+            const MuxEntryD& E = p.mentd[e];
+            if ((ci & E.cm) == E.cv) {
+              const double nc = c * E.c - s * E.s;
+              s = s * E.c + c * E.s;
+              c = nc;
+            }
+          }
         }
-        for (uint32_t e = word >> 8; e < (word >> 8) + (word & 255u); ++e) {
-          const MuxEntryD& E = p.mentd[e];
-          if ((ci & E.cm) == E.cv) rot_all(E.c, E.s);
-        }
+        mc[lane] = c;
+        ms[lane] = s;
+        if (word != 0u) rot_all(lane, md.target, md.lm, md.lv, c, s);
       }
+      continue;
+    }
+    if (o.op == 7) {
+      for (uint32_t lane = 0; lane < 32; ++lane)
+        rot_all(lane, o.target, o.lm, o.lv, mc[lane], -ms[lane]);
       continue;
     }
     if (o.op == 5) {

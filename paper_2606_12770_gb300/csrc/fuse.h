@@ -23,6 +23,7 @@ struct FuseStats {
   int64_t sweeps = 0, single = 0, perm_gates = 0, segments = 0, local_gates = 0, mux = 0;
   int64_t mux_gates = 0, mux_entries = 0, max_bucket = 0, lut_entries = 0, max_support = 0;
   int64_t reflect = 0;
+  int64_t mux_inverse = 0;  // multiplexers run as the inverse of the sweep's previous one
 };
 
 struct Program {
@@ -55,6 +56,11 @@ struct Program {
   // circuit repeats them) share one table: content -> table offset
   std::unordered_map<std::string, uint32_t> lut_cache, mux_cache;
   std::vector<MuxDesc> mux_descs;  // compiled multiplexers, indexed by mux_cache
+  // mux_inv[i]: the compiled multiplexer whose gates are those of i with the
+  // angles negated (its inverse; the gates commute), or -1.  mux_sig maps the
+  // order-free gate content of each multiplexer to its index.
+  std::vector<int> mux_inv;
+  std::unordered_map<std::string, uint32_t> mux_sig;
   std::unordered_map<std::string, std::string> order_cache;  // segments -> fast tile bits
   // source-index tables of the gather sweeps (build_src_index), one per
   // distinct segment chain

@@ -228,40 +228,34 @@ __device__ __forceinline__ void rot(T& a, T& b, R c, R s) {
   a = na;
 }
 
-// Load / store the 4-amplitude chunk of one lane with 16-byte vector accesses.
-// Loads skip L1 (the state streams; L1 is left to the lookup tables).
-__device__ __forceinline__ float4 ld_stream(const float4* p) {
-  float4 r;
-  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-               : "l"(p));
-  return r;
-}
-__device__ __forceinline__ double2 ld_stream(const double2* p) {
-  double2 r;
-  asm volatile("ld.global.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
-  return r;
-}
+// A chunk is 32 bytes (complex64) or 64 bytes (complex128), 32-byte aligned
+// (launch_sweep checks the buffers), and moves with 256-bit accesses: one
+// L2 sector request per 32 bytes.
 __device__ __forceinline__ void load_chunk(const float2* base, float2 (&v)[4]) {
-  const float4* p = reinterpret_cast<const float4*>(base);
-  const float4 a = ld_stream(p), b = ld_stream(p + 1);
-  v[0] = make_float2(a.x, a.y);
-  v[1] = make_float2(a.z, a.w);
-  v[2] = make_float2(b.x, b.y);
-  v[3] = make_float2(b.z, b.w);
+  asm volatile("ld.global.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[1].x), "=f"(v[1].y), "=f"(v[2].x),
+                 "=f"(v[2].y), "=f"(v[3].x), "=f"(v[3].y)
+               : "l"(base));
 }
 __device__ __forceinline__ void load_chunk(const double2* base, double2 (&v)[4]) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) v[j] = ld_stream(base + j);
+  for (int h = 0; h < 2; ++h)
+    asm volatile("ld.global.L1::no_allocate.v4.f64 {%0,%1,%2,%3}, [%4];"
+                 : "=d"(v[2 * h].x), "=d"(v[2 * h].y), "=d"(v[2 * h + 1].x), "=d"(v[2 * h + 1].y)
+                 : "l"(base + 2 * h));
 }
 __device__ __forceinline__ void store_chunk(float2* base, const float2 (&v)[4]) {
-  float4* p = reinterpret_cast<float4*>(base);
-  p[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-  p[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(base), "f"(v[0].x),
+               "f"(v[0].y), "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y), "f"(v[3].x),
+               "f"(v[3].y)
+               : "memory");
 }
 __device__ __forceinline__ void store_chunk(double2* base, const double2 (&v)[4]) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) base[j] = v[j];
+  for (int h = 0; h < 2; ++h)
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(base + 2 * h), "d"(v[2 * h].x),
+                 "d"(v[2 * h].y), "d"(v[2 * h + 1].x), "d"(v[2 * h + 1].y)
+                 : "memory");
 }
 
 // RY(c, s) on both in-thread pairs of target bit mt whose other low bit
@@ -335,6 +329,13 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
                                           const uint32_t (&ci)[U], uint32_t lane,
                                           const uint32_t (&wd)[kPrefetchMux][U]) {
   using T = typename V2<R>::T;
+  // rotation (cos, sin of half the summed angle) of the latest multiplexer, per tile
+  R mc[U], ms[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    mc[u] = (R)1;
+    ms[u] = (R)0;
+  }
   for (int k = 0; k < a.nops; ++k) {
     const LocalOp& o = a.ops[k];
     const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv, op = o.op, tg = o.target;
@@ -348,20 +349,35 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
         if (ocm == 0) word = wd[0][u];
         else if (ocm == 1 && kPrefetchMux > 1) word = wd[1][u];
         else word = __ldg(a.mtab + toff + win_key(ci[u], w));
-        if (word == 0u) continue;
+        R c = (R)1, s = (R)0;
         if (word & 0x80000000u) {
           const T cs = CplxOf<R>::angle(a, word & 0x7fffffffu);
-          rot_pairs<T, R>(v[u], mt, mlm, mlv, cs.x, cs.y);
-          continue;
+          c = cs.x;
+          s = cs.y;
+        } else if (word != 0u) {
+          // the matching candidates' rotations commute: compose them, rotate once
+          const uint32_t e0 = word >> 8, e1 = e0 + (word & 255u);
+          for (uint32_t e = e0; e < e1; ++e) {
+            uint32_t cm, cv;
+            R ce, se;
+            CplxOf<R>::entry(a, e, &cm, &cv, &ce, &se);
+            if ((ci[u] & cm) == cv) {
+              const R nc = c * ce - s * se;
+              s = s * ce + c * se;
+              c = nc;
+            }
+          }
         }
-        const uint32_t e0 = word >> 8, e1 = e0 + (word & 255u);
-        for (uint32_t e = e0; e < e1; ++e) {
-          uint32_t cm, cv;
-          R c, s;
-          CplxOf<R>::entry(a, e, &cm, &cv, &c, &s);
-          if ((ci[u] & cm) == cv) rot_pairs<T, R>(v[u], mt, mlm, mlv, c, s);
-        }
+        mc[u] = c;
+        ms[u] = s;
+        if (word != 0u) rot_pairs<T, R>(v[u], mt, mlm, mlv, c, s);
       }
+      continue;
+    }
+    if (op == 7) {  // inverse of the latest multiplexer: RY(-theta) with the same controls
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ms[u] != (R)0 || mc[u] != (R)1) rot_pairs<T, R>(v[u], tg, lm, lv, mc[u], -ms[u]);
       continue;
     }
     if (op == 5) {  // I (x) A + J (x) B over the lane bits of lanemask
@@ -580,6 +596,14 @@ __global__ void __launch_bounds__(256, MINB)
 #pragma unroll
     for (int u = 0; u < U; ++u) L[u] = (uint32_t)u;
   }
+  // source indices of the warp's next tiles, loaded one iteration ahead
+  const bool pre = a.src != nullptr && a.src_prefetch != 0 && !a.scatter;
+  uint32_t nxt[U];
+  if (pre && c0 < ntiles) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      nxt[u] = __ldcs(a.src + (((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane));
+  }
   for (uint32_t t0 = c0; t0 < ntiles; t0 += nwarps * U) {
     uint32_t ci[U], mv[U];
 #pragma unroll
@@ -589,7 +613,15 @@ __global__ void __launch_bounds__(256, MINB)
     uint32_t wd[kPrefetchMux][U];
     prefetch_mux<U>(a, ci, wd);
     if (!a.scatter) {
-      if (a.src) {
+      if (pre) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) mv[u] = nxt[u];
+        if (t0 + nwarps * U < ntiles) {
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            nxt[u] = __ldcs(a.src + (((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane));
+        }
+      } else if (a.src) {
 #pragma unroll
         for (int u = 0; u < U; ++u) mv[u] = __ldcs(a.src + ci[u]);
       } else {
@@ -911,6 +943,9 @@ void launch_sweep_r(const void* in, void* out, uint32_t ntiles, int u, int minb,
 
 cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
                          cudaStream_t st) {
+  // the 256-bit chunk accesses need 32-byte aligned buffers
+  if (((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 31u) != 0)
+    return cudaErrorInvalidValue;
   const uint32_t ntiles = 1u << (n - 7);
   const SweepCfg c = sweep_cfg();
   if (prec == CSIM_C64)

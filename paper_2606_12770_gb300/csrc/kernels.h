@@ -32,7 +32,9 @@ struct PermSeg {
 // chunk-index part (state bits >= 2) and state bits 0-1.
 // op: 0 X, 1 H, 2 RY, 3 ZPHASE, 4 multiplexed RY (cm = index of its MuxDesc),
 // 5 averaging block (cm = index of its ReflectDesc), 6 ZPHASE on a qubit above
-// the tile (target = its chunk-index bit, state bit - 2).
+// the tile (target = its chunk-index bit, state bit - 2), 7 the inverse of the
+// sweep's latest multiplexed RY (the same rotation with the sine negated; its
+// target and bit 0-1 controls in target, lm, lv).
 struct LocalOp {
   uint32_t cm, cv;
   uint8_t lm, lv, op, target;
@@ -99,6 +101,7 @@ struct SweepParams {
   // (the segments applied to x, precomputed by launch_perm_index), and the
   // kernel loads it instead of walking the segment chain.
   const uint32_t* src;
+  int src_prefetch;  // load the next iteration's source indices one iteration ahead
 };
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,

@@ -525,6 +525,10 @@ csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out) {
   if (P->o.n_streams > 64) P->o.n_streams = 64;
   if (P->o.max_qubits <= 0) P->o.max_qubits = 32;
   if (P->o.min_block == 0) P->o.min_block = 1u << 20;
+  if (P->o.min_block % 256u != 0) {
+    delete P;
+    return pfail(CSIM_ERR_ARG, "min_block must be a multiple of 256 bytes");
+  }
   cudaError_t e = cudaSuccess;
   if (P->o.hbm_budget == 0) {
     size_t fr = 0, tot = 0;

@@ -102,3 +102,13 @@ def linf(a, b):
 def amplitude_ratio(rho_q, rho_x):
     """Ratio of the mean densities (the collapse factor of an under-inverted run)."""
     return float(np.mean(rho_q) / np.mean(rho_x))
+
+
+def compacted_rows(amps, lay):
+    """The entries of csim_postselect's compacted block (signal, label and target
+    0; slots m >= Nt), reordered like the final-slot rows of L."""
+    final = Q.final_slot_mask(lay)
+    sel = lay.physical_indices()[final]
+    fs, ms = 2 + lay.niL, lay.regs["m"][0]
+    pos = ((sel >> ms) - lay.Nt) * (1 << (ms - fs)) + ((sel >> fs) & ((1 << (ms - fs)) - 1))
+    return np.asarray(amps)[pos]

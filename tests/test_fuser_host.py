@@ -88,6 +88,9 @@ def test_qsvt_circuit_one_sweep_per_call(cfg, d):
     assert st["passes"] == d + 1 and st["single"] == 0
     if cfg[2] == 2:  # five label qubits = all lane bits: projector phases become averaging blocks
         assert st["reflect"] == d - 1  # every phase between two oracle calls
+    # the multiplexer that ends U_L and its inverse that starts the next U_L^dag
+    # share one sweep: the second reuses the first's rotation
+    assert st["mux_inverse"] == (d - 1) // 2
     assert rel(got, S.DenseSim(lay.n).run(psi.copy(), gates)) < 1e-13
 
 

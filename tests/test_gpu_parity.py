@@ -347,20 +347,23 @@ print("ok")
 def test_source_index_tables_equal_lookup_chain(tmp_path):
     """The gather sweeps give the same state, bit for bit, whether they load the
     precomputed source index of each chunk or walk the lookup-table chain (the
-    same index, the same arithmetic); the table path is the one in use by
-    default (two tables: U_L and U_L^dag)."""
+    same index, the same arithmetic), with the indices loaded one iteration
+    ahead or not; the table path is the one in use by default (two tables:
+    U_L and U_L^dag)."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     res = {}
-    for flag in ("0", "1"):
-        path = str(tmp_path / f"src{flag}.npz")
-        env = dict(os.environ, CSIM_SRC_INDEX=flag)
+    modes = {"chain": ("0", "1"), "src-nopre": ("1", "0"), "default": ("1", "1")}
+    for name, (flag, pre) in modes.items():
+        path = str(tmp_path / f"{name}.npz")
+        env = dict(os.environ, CSIM_SRC_INDEX=flag, CSIM_SRC_PREFETCH=pre)
         r = subprocess.run([sys.executable, "-c", SRC_SCRIPT, root, path], env=env,
                            capture_output=True, text=True, timeout=600)
         assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
-        res[flag] = np.load(path)
-    assert int(res["0"]["c128_tables"]) == 0 and int(res["1"]["c128_tables"]) == 2
-    for name in ("c128", "c64"):
-        assert np.array_equal(res["0"][name], res["1"][name]), name
+        res[name] = np.load(path)
+    assert int(res["chain"]["c128_tables"]) == 0 and int(res["default"]["c128_tables"]) == 2
+    for prec in ("c128", "c64"):
+        assert np.array_equal(res["chain"][prec], res["default"][prec]), prec
+        assert np.array_equal(res["src-nopre"][prec], res["default"][prec]), prec
