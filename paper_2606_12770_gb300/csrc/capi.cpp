@@ -771,9 +771,10 @@ csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n
   }
   if (stats) {
     const csim::FuseStats& f = p.stats;
-    const int64_t v[14] = {f.sweeps,      f.single,      f.perm_gates,  f.segments, f.local_gates,
+    const int64_t v[15] = {f.sweeps,      f.single,      f.perm_gates,  f.segments, f.local_gates,
                            f.mux,         f.mux_gates,   f.mux_entries, f.max_bucket,
-                           f.lut_entries, f.max_support, p.passes,      f.reflect,  f.mux_inverse};
+                           f.lut_entries, f.max_support, p.passes,      f.reflect,  f.mux_inverse,
+                           f.wht};
     std::memcpy(stats, v, sizeof(v));
   }
   return CSIM_OK;

@@ -581,6 +581,29 @@ std::vector<OpItem> compile_local(const std::vector<csim_gate>& run, Program* p)
         continue;
       }
     }
+    // uncontrolled H gates on distinct lane bits: one Walsh-Hadamard op
+    if (g.op == OP_H && g.target >= 2 && g.target < 7 && g.cmask == 0) {
+      uint32_t lanes = 0;
+      size_t j = i;
+      while (j < run.size() && run[j].op == OP_H && run[j].target >= 2 && run[j].target < 7 &&
+             run[j].cmask == 0 && !((lanes >> (run[j].target - 2)) & 1u)) {
+        lanes |= 1u << (run[j].target - 2);
+        ++j;
+      }
+      if (j - i >= 2) {
+        OpItem it{};
+        it.op.op = 8;
+        it.op.cm = lanes;
+        const double sc = std::ldexp(1.0, -(int)(j - i) / 2) *
+                          (((j - i) & 1) ? 0.70710678118654752440 : 1.0);
+        it.op.cd = sc;
+        it.op.cf = (float)sc;
+        out.push_back(it);
+        p->stats.wht++;
+        i = j;
+        continue;
+      }
+    }
     OpItem it{};
     it.op = local_op(g);
     out.push_back(it);
@@ -913,7 +936,12 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
         const SweepParams& sp = p->params[(size_t)st.param];
         std::string segs, ops;
         for (int i = 0; i < sp.nseg; ++i) segs += "TGI"[sp.segs[i].kind];
-        for (int i = 0; i < sp.nops; ++i) ops += "XHRZMAPI"[sp.ops[i].op];
+        for (int i = 0; i < sp.nops; ++i) {
+          ops += "XHRZMAPIW"[sp.ops[i].op];
+          if (sp.ops[i].op < 4 || sp.ops[i].op == 6)
+            ops += std::to_string(sp.ops[i].target) + "/" + std::to_string(sp.ops[i].cm) + ":" +
+                   std::to_string(sp.ops[i].lm) + " ";
+        }
         std::fprintf(stderr, "[csim fuse] step %zu: segs %s ops %s mux %d\n", k, segs.c_str(),
                      ops.c_str(), sp.nmux);
       }
@@ -1150,6 +1178,25 @@ void emu_ops(const Program& p, const SweepParams& sp, uint32_t tile, double (&v)
     if (o.op == 7) {
       for (uint32_t lane = 0; lane < 32; ++lane)
         rot_all(lane, o.target, o.lm, o.lv, mc[lane], -ms[lane]);
+      continue;
+    }
+    if (o.op == 8) {  // H on every lane bit of o.cm, then one scale
+      for (int b = 0; b < 5; ++b) {
+        if (!((o.cm >> b) & 1u)) continue;
+        for (uint32_t lane = 0; lane < 32; ++lane) {
+          if (lane & (1u << b)) continue;
+          const uint32_t hi = lane | (1u << b);
+          for (int y = 0; y < 4; ++y)
+            for (int r = 0; r < 2; ++r) {
+              const double x0 = v[lane][y][r], x1 = v[hi][y][r];
+              v[lane][y][r] = x0 + x1;
+              v[hi][y][r] = x0 - x1;
+            }
+        }
+      }
+      for (uint32_t lane = 0; lane < 32; ++lane)
+        for (int y = 0; y < 4; ++y)
+          for (int r = 0; r < 2; ++r) v[lane][y][r] *= o.cd;
       continue;
     }
     if (o.op == 5) {

@@ -24,6 +24,7 @@ struct FuseStats {
   int64_t mux_gates = 0, mux_entries = 0, max_bucket = 0, lut_entries = 0, max_support = 0;
   int64_t reflect = 0;
   int64_t mux_inverse = 0;  // multiplexers run as the inverse of the sweep's previous one
+  int64_t wht = 0;          // Walsh-Hadamard ops (H on several lane bits)
 };
 
 struct Program {

@@ -374,6 +374,26 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
       }
       continue;
     }
+    if (op == 8) {  // H on each lane bit of the mask: butterflies, then one scale
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        if (!((ocm >> b) & 1u)) continue;
+        const R sg = ((lane >> b) & 1u) ? (R)-1 : (R)1;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const T w = shfl_xor_c(v[u][j], 1 << b);
+            v[u][j] = mk<T>(fma(v[u][j].x, sg, w.x), fma(v[u][j].y, sg, w.y));
+          }
+      }
+      const R sc = Coef<R>::c(o);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[u][j] = mk<T>(v[u][j].x * sc, v[u][j].y * sc);
+      continue;
+    }
     if (op == 7) {  // inverse of the latest multiplexer: RY(-theta) with the same controls
 #pragma unroll
       for (int u = 0; u < U; ++u)

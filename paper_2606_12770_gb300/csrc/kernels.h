@@ -34,7 +34,8 @@ struct PermSeg {
 // 5 averaging block (cm = index of its ReflectDesc), 6 ZPHASE on a qubit above
 // the tile (target = its chunk-index bit, state bit - 2), 7 the inverse of the
 // sweep's latest multiplexed RY (the same rotation with the sine negated; its
-// target and bit 0-1 controls in target, lm, lv).
+// target and bit 0-1 controls in target, lm, lv), 8 H on every lane bit of the
+// mask cm (no controls), followed by one scale 2^(-k/2) in cf / cd.
 struct LocalOp {
   uint32_t cm, cv;
   uint8_t lm, lv, op, target;

@@ -91,7 +91,23 @@ def test_qsvt_circuit_one_sweep_per_call(cfg, d):
     # the multiplexer that ends U_L and its inverse that starts the next U_L^dag
     # share one sweep: the second reuses the first's rotation
     assert st["mux_inverse"] == (d - 1) // 2
+    # the label Hadamard layers of the first and the last call are fused
+    assert st["wht"] == 2
     assert rel(got, S.DenseSim(lay.n).run(psi.copy(), gates)) < 1e-13
+
+
+def test_lane_walsh_hadamard_fused():
+    """Uncontrolled H gates on distinct lane bits run as one Walsh-Hadamard op;
+    a repeated bit or a controlled H ends the run."""
+    n = 11
+    g = [(1, b, 0, 0, 0.0, 0) for b in (6, 4, 2, 3)]          # one op (4 bits)
+    g += [(1, 3, 0, 0, 0.0, 0), (1, 5, 0, 0, 0.0, 0)]         # bit 3 again: a second op
+    g += [(1, 2, 1 << 9, 1 << 9, 0.0, 0), (1, 4, 0, 0, 0.0, 0)]  # controlled: single gates
+    g += [(2, 0, 1 << 8, 0, 0.7, 0), (1, 5, 0, 0, 0.0, 0), (1, 6, 0, 0, 0.0, 0), (1, 2, 0, 0, 0.0, 0)]
+    psi = I.random_unit_state(n, 8)
+    got, st = N.emulate_fused(g, n, psi)
+    assert st["wht"] == 3
+    assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-14
 
 
 def test_averaging_block_detection_general():
