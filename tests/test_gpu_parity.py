@@ -348,17 +348,19 @@ def test_source_index_tables_equal_lookup_chain(tmp_path):
     """The gather sweeps give the same state, bit for bit, whether they load the
     precomputed source index of each chunk or walk the lookup-table chain (the
     same index, the same arithmetic), with the indices loaded one iteration
-    ahead or not; the table path is the one in use by default (two tables:
-    U_L and U_L^dag)."""
+    ahead or not, and in the scatter form (destination indices); the table
+    path is the one in use by default (two tables: U_L and U_L^dag)."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     res = {}
-    modes = {"chain": ("0", "1"), "src-nopre": ("1", "0"), "default": ("1", "1")}
-    for name, (flag, pre) in modes.items():
+    modes = {"chain": ("0", "1", "gather"), "src-nopre": ("1", "0", "gather"),
+             "default": ("1", "1", "gather"), "chain-scatter": ("0", "1", "scatter"),
+             "scatter": ("1", "1", "scatter")}
+    for name, (flag, pre, form) in modes.items():
         path = str(tmp_path / f"{name}.npz")
-        env = dict(os.environ, CSIM_SRC_INDEX=flag, CSIM_SRC_PREFETCH=pre)
+        env = dict(os.environ, CSIM_SRC_INDEX=flag, CSIM_SRC_PREFETCH=pre, CSIM_SWEEP_FORM=form)
         r = subprocess.run([sys.executable, "-c", SRC_SCRIPT, root, path], env=env,
                            capture_output=True, text=True, timeout=600)
         assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
@@ -367,3 +369,4 @@ def test_source_index_tables_equal_lookup_chain(tmp_path):
     for prec in ("c128", "c64"):
         assert np.array_equal(res["chain"][prec], res["default"][prec]), prec
         assert np.array_equal(res["src-nopre"][prec], res["default"][prec]), prec
+        assert np.array_equal(res["chain-scatter"][prec], res["scatter"][prec]), prec
