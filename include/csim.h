@@ -281,13 +281,19 @@ typedef struct {
   int64_t submitted, admitted, completed, rejected, queued, running;
   uint64_t bytes_in_use, peak_bytes, budget;
   int64_t graph_launches; /* admission passes launched as one CUDA graph */
+  int64_t src_tables;     /* source-index tables built in the arena for admitted requests */
 } csim_pool_stats_t;
 
 csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out);
 /* Queue one run of circuit c (QSVT circuit on b from f0, as csim_init +
  * csim_run + csim_postselect) and try to admit.  f0 is copied.  *id receives
- * the request id.  CSIM_ERR_TOO_LARGE (counted as rejected) when the circuit
- * exceeds max_qubits or its blocks cannot fit the arena. */
+ * the request id.  Besides its state buffers, a request takes the source-index
+ * tables of its sweeps from the arena (2^n bytes per distinct permutation
+ * chain, two for a QSVT circuit; built on the request's stream before its
+ * sweeps), unless the circuit already holds its own from a csim_run or the
+ * request fits the arena only without them.  CSIM_ERR_TOO_LARGE (counted as
+ * rejected) when the circuit exceeds max_qubits or its blocks cannot fit the
+ * arena. */
 csim_status csim_pool_submit(csim_pool* p, csim_circuit* c, const double* f0,
                              csim_precision prec, int64_t* id);
 /* Retire finished requests and admit queued ones.  wait_ms > 0 blocks until a

@@ -1057,22 +1057,40 @@ std::string chain_key(const SweepParams& sp) {
 }
 }  // namespace
 
+int plan_src_index(Program* p, int max_tables) {
+  if (!p->src_planned) {
+    p->src_planned = true;
+    p->src_tab.assign(p->params.size(), -1);
+    p->src_first.clear();
+    if (src_index_enabled() && p->n >= 7) {
+      std::unordered_map<std::string, int> tab_of_key;
+      for (const Step& s : p->steps) {
+        if (s.kind != 0 || !s.gather) continue;  // sweeps that move data, in either form
+        const SweepParams& sp = p->params[(size_t)s.param];
+        if (sp.nseg == 0) continue;
+        auto it = tab_of_key.emplace(chain_key(sp), (int)p->src_first.size());
+        if (it.second) p->src_first.push_back(s.param);
+        p->src_tab[(size_t)s.param] = it.first->second;
+      }
+    }
+  }
+  const int ntab = (int)p->src_first.size();
+  return ntab <= max_tables ? ntab : 0;
+}
+
+cudaError_t launch_src_tables(const Program& p, uint32_t* const* tables, cudaStream_t st) {
+  for (size_t t = 0; t < p.src_first.size(); ++t) {
+    const cudaError_t e = launch_perm_index(tables[t], p.n, p.params[(size_t)p.src_first[t]], st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t build_src_index(Program* p, cudaStream_t st, int max_tables) {
   if (p->src_tried || !p->uploaded) return cudaSuccess;
   p->src_tried = true;
-  if (!src_index_enabled() || p->n < 7) return cudaSuccess;
-  std::unordered_map<std::string, int> tab_of_key;
-  std::vector<int> tab_of_param(p->params.size(), -1), first_param;
-  for (const Step& s : p->steps) {
-    if (s.kind != 0 || !s.gather) continue;  // sweeps that move data, in either form
-    const SweepParams& sp = p->params[(size_t)s.param];
-    if (sp.nseg == 0) continue;
-    auto it = tab_of_key.emplace(chain_key(sp), (int)first_param.size());
-    if (it.second) first_param.push_back(s.param);
-    tab_of_param[(size_t)s.param] = it.first->second;
-  }
-  const int ntab = (int)first_param.size();
-  if (ntab == 0 || ntab > max_tables) return cudaSuccess;
+  const int ntab = plan_src_index(p, max_tables);
+  if (ntab == 0) return cudaSuccess;
   const uint64_t bytes = 1ull << p->n;  // 2^(n-2) chunks x 4 bytes
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
@@ -1082,11 +1100,8 @@ cudaError_t build_src_index(Program* p, cudaStream_t st, int max_tables) {
   if ((uint64_t)ntab * bytes > fr / 4) return cudaSuccess;
   std::vector<uint32_t*> tabs((size_t)ntab, nullptr);
   cudaError_t e = cudaSuccess;
-  for (int t = 0; t < ntab && e == cudaSuccess; ++t) {
-    e = cudaMalloc((void**)&tabs[(size_t)t], bytes);
-    if (e == cudaSuccess)
-      e = launch_perm_index(tabs[(size_t)t], p->n, p->params[(size_t)first_param[(size_t)t]], st);
-  }
+  for (int t = 0; t < ntab && e == cudaSuccess; ++t) e = cudaMalloc((void**)&tabs[(size_t)t], bytes);
+  if (e == cudaSuccess) e = launch_src_tables(*p, tabs.data(), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     for (uint32_t* q : tabs)
@@ -1094,8 +1109,8 @@ cudaError_t build_src_index(Program* p, cudaStream_t st, int max_tables) {
     return e;
   }
   for (size_t k = 0; k < p->params.size(); ++k)
-    if (tab_of_param[k] >= 0) {
-      p->params[k].src = tabs[(size_t)tab_of_param[k]];
+    if (p->src_tab[k] >= 0) {
+      p->params[k].src = tabs[(size_t)p->src_tab[k]];
       p->params[k].src_prefetch = src_prefetch_enabled() ? 1 : 0;
     }
   p->d_src = tabs;
@@ -1123,12 +1138,13 @@ void free_program(Program* p) {
   p->uploaded = false;
 }
 
-cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st) {
-  return run_program_steps(p, buf, cur, prec, st, 0, (int64_t)p.steps.size());
+cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
+                        const uint32_t* const* src_tables) {
+  return run_program_steps(p, buf, cur, prec, st, 0, (int64_t)p.steps.size(), src_tables);
 }
 
 cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
-                              int64_t first, int64_t last) {
+                              int64_t first, int64_t last, const uint32_t* const* src_tables) {
   for (int64_t k = first; k < last; ++k) {
     const Step& s = p.steps[(size_t)k];
     cudaError_t e;
@@ -1136,6 +1152,12 @@ cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec
       e = launch_gate(buf[*cur], prec, p.n, s.g, st);
     } else if (!s.gather) {
       e = launch_sweep(buf[*cur], buf[*cur], prec, p.n, p.params[s.param], st);
+    } else if (src_tables && (size_t)s.param < p.src_tab.size() && p.src_tab[(size_t)s.param] >= 0) {
+      SweepParams a = p.params[(size_t)s.param];
+      a.src = src_tables[p.src_tab[(size_t)s.param]];
+      a.src_prefetch = src_prefetch_enabled() ? 1 : 0;
+      e = launch_sweep(buf[*cur], buf[1 - *cur], prec, p.n, a, st);
+      *cur = 1 - *cur;
     } else {
       e = launch_sweep(buf[*cur], buf[1 - *cur], prec, p.n, p.params[s.param], st);
       *cur = 1 - *cur;

@@ -67,6 +67,10 @@ struct Program {
   // distinct segment chain
   std::vector<uint32_t*> d_src;
   bool src_tried = false;
+  // plan_src_index: the table of each sweep's chain (by params index, -1 for
+  // none) and the first sweep of each table
+  std::vector<int> src_tab, src_first;
+  bool src_planned = false;
 };
 
 // Build the program for `gates` on an n-qubit state.  FUSED mode needs
@@ -83,12 +87,22 @@ void free_program(Program* p);
 // than max_tables distinct chains, or when the tables would take more than a
 // quarter of the free device memory.  Runs once per program.
 cudaError_t build_src_index(Program* p, cudaStream_t st, int max_tables);
+// The distinct chains of the program's data-moving sweeps (cached): returns
+// how many source-index tables the program takes, 0 when it keeps the chain
+// (CSIM_SRC_INDEX=0, more than max_tables chains, n < 7).
+int plan_src_index(Program* p, int max_tables);
+// Fill caller-owned tables (2^(n-2) uint32 each, one per planned chain) on st.
+cudaError_t launch_src_tables(const Program& p, uint32_t* const* tables, cudaStream_t st);
 // Run the program on buf[*cur] (and buf[1 - *cur] when it moves data); *cur
 // tracks which buffer holds the state afterwards.
-cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st);
+// With src_tables (caller-owned, from launch_src_tables), the sweeps load
+// their source indices from those tables instead of the program's own.
+cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
+                        const uint32_t* const* src_tables = nullptr);
 // Steps [first, last) of the program only (checkpointed runs).
 cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
-                              int64_t first, int64_t last);
+                              int64_t first, int64_t last,
+                              const uint32_t* const* src_tables = nullptr);
 // Host executor of a fused program (FP64, kernel semantics) for testing.
 void emulate_program(const Program& p, std::vector<double>* amps);
 

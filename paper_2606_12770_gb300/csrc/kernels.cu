@@ -452,8 +452,13 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
               if (y == ya || y == yb) {
                 const T cb = CplxOf<R>::b(rd, q);
                 const T S = (y == ya) ? Sa : Sb;
-                o.x += cb.x * S.x - cb.y * S.y;
-                o.y += cb.x * S.y + cb.y * S.x;
+                if (cb.x == (R)0) {  // purely imaginary (the QSVT projector phase)
+                  o.x -= cb.y * S.y;
+                  o.y += cb.y * S.x;
+                } else {
+                  o.x += cb.x * S.x - cb.y * S.y;
+                  o.y += cb.x * S.y + cb.y * S.x;
+                }
               }
               v[u][y] = o;
             }
@@ -726,15 +731,24 @@ __global__ void __launch_bounds__(256, MINB)
 
 // Source-index table of a gather sweep: the segment chain applied to every
 // chunk index once, so that the sweeps that share the chain load one index
-// per chunk instead of walking the chain.
+// per chunk instead of walking the chain.  Each thread walks four chunks at a
+// time (independent lookup chains in flight) and writes them coalesced.
+constexpr int kPermIndexILP = 4;
 __global__ void __launch_bounds__(256)
     perm_index_kernel(uint32_t* __restrict__ src, uint64_t nchunks,
                       const __grid_constant__ SweepParams a) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nchunks; x += stride) {
-    uint32_t m[1] = {(uint32_t)x};
-    permute<1>(a, m);
-    src[x] = m[0];
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t stride = nthreads * kPermIndexILP;
+  for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x0 < nchunks; x0 += stride) {
+    uint32_t m[kPermIndexILP];
+#pragma unroll
+    for (int j = 0; j < kPermIndexILP; ++j) m[j] = (uint32_t)(x0 + (uint64_t)j * nthreads);
+    permute<kPermIndexILP>(a, m);
+#pragma unroll
+    for (int j = 0; j < kPermIndexILP; ++j) {
+      const uint64_t x = x0 + (uint64_t)j * nthreads;
+      if (x < nchunks) src[x] = m[j];
+    }
   }
 }
 
@@ -1039,7 +1053,7 @@ cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const Sweep
 cudaError_t launch_perm_index(uint32_t* src, int n, const SweepParams& a, cudaStream_t st) {
   const uint64_t nchunks = 1ull << (n - 2);
   const int blk = 256;
-  const int grd = grid_for(nchunks, blk);
+  const int grd = grid_for((nchunks + kPermIndexILP - 1) / kPermIndexILP, blk);
   perm_index_kernel<<<grd, blk, 0, st>>>(src, nchunks, a);
   return cudaGetLastError();
 }

@@ -129,21 +129,24 @@ class BuddyArena {
   std::map<uint64_t, int> live_;
 };
 
-constexpr int kAllocs = 4;  // state 0, state 1, compacted block, staging of b
+// Blocks of a request: state 0, state 1, compacted block, staging of b, and
+// the source-index tables of its program (two at most).  The planner's
+// requests have the first four.
+constexpr int kAllocs = 6, kPlanAllocs = 4, kTabBlock = 4, kMaxPoolTables = 2;
 
 // Whether every block of one request fits an empty arena of this capacity.
-bool fits_empty(uint64_t capacity, uint64_t min_block, const uint64_t* sizes) {
+bool fits_empty(uint64_t capacity, uint64_t min_block, const uint64_t* sizes, int n) {
   BuddyArena a;
   a.init(capacity, min_block);
   uint64_t off;
-  for (int k = 0; k < kAllocs; ++k)
+  for (int k = 0; k < n; ++k)
     if (sizes[k] && !a.alloc(sizes[k], &off)) return false;
   return true;
 }
 
 // All-or-nothing allocation of a request's blocks.
-bool alloc_all(BuddyArena* a, const uint64_t* sizes, uint64_t* offs) {
-  for (int k = 0; k < kAllocs; ++k) {
+bool alloc_all(BuddyArena* a, const uint64_t* sizes, uint64_t* offs, int n) {
+  for (int k = 0; k < n; ++k) {
     offs[k] = ~0ull;
     if (!sizes[k]) continue;
     if (!a->alloc(sizes[k], &offs[k])) {
@@ -154,8 +157,8 @@ bool alloc_all(BuddyArena* a, const uint64_t* sizes, uint64_t* offs) {
   }
   return true;
 }
-void release_all(BuddyArena* a, const uint64_t* offs) {
-  for (int k = 0; k < kAllocs; ++k)
+void release_all(BuddyArena* a, const uint64_t* offs, int n) {
+  for (int k = 0; k < n; ++k)
     if (offs[k] != ~0ull) a->release(offs[k]);
 }
 
@@ -167,8 +170,9 @@ struct Request {
   int prec = 0;
   std::vector<uint64_t> idx;
   std::vector<double> val;
-  uint64_t sizes[kAllocs] = {0, 0, 0, 0};
-  uint64_t offs[kAllocs] = {~0ull, ~0ull, ~0ull, ~0ull};
+  uint64_t sizes[kAllocs] = {0, 0, 0, 0, 0, 0};
+  uint64_t offs[kAllocs] = {~0ull, ~0ull, ~0ull, ~0ull, ~0ull, ~0ull};
+  int ntab = 0;  // source-index tables built into blocks kTabBlock.. for this run
   RState st = RState::Queued;
   int slot = -1;
   uint64_t count = 0;  // compacted amplitudes
@@ -221,13 +225,16 @@ struct csim_pool {
 
 namespace {
 
-void request_sizes(const csim_circuit* c, int prec, size_t nnz, uint64_t* sizes, uint64_t* count) {
+void request_sizes(const csim_circuit* c, int prec, size_t nnz, int ntab, uint64_t* sizes,
+                   uint64_t* count) {
   const uint64_t S = ((uint64_t)1 << c->L.n) * (prec == CSIM_C64 ? 8 : 16);
   const csim::CompactGeom g = csim::compact_geom(c);
   sizes[0] = S;
   sizes[1] = (c->prog_built && !c->prog.pingpong) ? 0 : S;
   sizes[2] = std::max<uint64_t>(g.count * 16, 256);
   sizes[3] = std::max<uint64_t>(nnz * 16, 256);
+  for (int t = 0; t < kMaxPoolTables; ++t)
+    sizes[kTabBlock + t] = t < ntab ? std::max<uint64_t>((uint64_t)1 << c->L.n, 256) : 0;
   *count = g.count;
 }
 
@@ -287,10 +294,16 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, bool in_graph, co
     e = csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n,
                           reinterpret_cast<const uint64_t*>(d_stage),
                           reinterpret_cast<const double*>(d_stage + nnz * 8), (int64_t)nnz, st);
+  uint32_t* tabs[kMaxPoolTables] = {nullptr, nullptr};
+  for (int t = 0; t < r.ntab; ++t) tabs[t] = reinterpret_cast<uint32_t*>(base + r.offs[kTabBlock + t]);
+  if (e == cudaSuccess && r.ntab > 0) {
+    *where = "source-index tables";
+    e = csim::launch_src_tables(c->prog, tabs, st);
+  }
   int cur = 0;
   if (e == cudaSuccess) {
     *where = "program";
-    e = csim::run_program(c->prog, buf, &cur, r.prec, st);
+    e = csim::run_program(c->prog, buf, &cur, r.prec, st, r.ntab > 0 ? tabs : nullptr);
   }
   int lowk = 0;
   uint64_t lowv = 0;
@@ -328,11 +341,11 @@ csim_status admit(csim_pool* P) {
       }
     if (free_slot < 0) break;
     Request& r = P->reqs[P->queue.front()];
-    if (!alloc_all(&P->arena, r.sizes, r.offs)) break;
+    if (!alloc_all(&P->arena, r.sizes, r.offs, kAllocs)) break;
     Slot& s = P->slots[free_slot];
     cudaError_t e = grow_pinned(&s, 16 * kMaxPatterns + r.idx.size() * 16, r.count * 16 + 16);
     if (e != cudaSuccess) {
-      release_all(&P->arena, r.offs);
+      release_all(&P->arena, r.offs, kAllocs);
       return pcuda(e, "csim_pool: pinned staging");
     }
     s.req = r.id;
@@ -341,6 +354,7 @@ csim_status admit(csim_pool* P) {
     r.t_start = now_s();
     P->queue.pop_front();
     P->stats.admitted++;
+    P->stats.src_tables += r.ntab;
     P->stats.bytes_in_use = P->arena.in_use();
     P->stats.peak_bytes = std::max(P->stats.peak_bytes, P->arena.in_use());
     started.emplace_back(r.id, free_slot);
@@ -465,7 +479,7 @@ csim_status retire(csim_pool* P, int* n_retired) {
       cudaGetLastError();  // a failed timing query must not linger as the last error
     r.t_done = now_s();
     r.st = RState::Done;
-    release_all(&P->arena, r.offs);
+    release_all(&P->arena, r.offs, kAllocs);
     s.req = -1;
     P->done_unreported.push_back(r.id);
     P->stats.completed++;
@@ -591,8 +605,15 @@ csim_status csim_pool_submit(csim_pool* P, csim_circuit* c, const double* f0, cs
   if (!csim::circuit_rhs(c, f0, &r.idx, &r.val, &err)) return pfail(CSIM_ERR_ARG, err);
   r.c = c;
   r.prec = prec;
-  request_sizes(c, prec, r.idx.size(), r.sizes, &r.count);
-  if (!fits_empty(P->arena.capacity(), P->arena.min_block(), r.sizes)) {
+  // source-index tables from the arena, unless the program has its own (from a
+  // csim_run) or the request only fits without them
+  r.ntab = c->prog.d_src.empty() ? csim::plan_src_index(&c->prog, kMaxPoolTables) : 0;
+  request_sizes(c, prec, r.idx.size(), r.ntab, r.sizes, &r.count);
+  if (r.ntab > 0 && !fits_empty(P->arena.capacity(), P->arena.min_block(), r.sizes, kAllocs)) {
+    r.ntab = 0;
+    request_sizes(c, prec, r.idx.size(), 0, r.sizes, &r.count);
+  }
+  if (!fits_empty(P->arena.capacity(), P->arena.min_block(), r.sizes, kAllocs)) {
     P->stats.rejected++;
     return pfail(CSIM_ERR_TOO_LARGE, "csim_pool_submit: the request's device memory exceeds "
                                      "the pool's budget");
@@ -681,7 +702,7 @@ csim_status csim_pool_plan(uint64_t budget, uint64_t min_block, int32_t n_stream
   struct Run {
     double t_end;
     size_t i;
-    uint64_t offs[kAllocs];
+    uint64_t offs[kPlanAllocs];
   };
   std::vector<Run> running;
   std::deque<size_t> queue;
@@ -698,13 +719,14 @@ csim_status csim_pool_plan(uint64_t budget, uint64_t min_block, int32_t n_stream
     // arrivals up to t
     while (next < count && (arrival ? arrival[order[next]] : 0.0) <= t) {
       const size_t i = order[next++];
-      if (fits_empty(a.capacity(), min_block, alloc_bytes + kAllocs * i)) queue.push_back(i);
+      if (fits_empty(a.capacity(), min_block, alloc_bytes + kPlanAllocs * i, kPlanAllocs))
+        queue.push_back(i);
     }
     // admit FIFO
     while (!queue.empty() && (int)running.size() < n_streams) {
       Run r{};
       r.i = queue.front();
-      if (!alloc_all(&a, alloc_bytes + kAllocs * r.i, r.offs)) break;
+      if (!alloc_all(&a, alloc_bytes + kPlanAllocs * r.i, r.offs, kPlanAllocs)) break;
       queue.pop_front();
       start[r.i] = t;
       r.t_end = t + duration[r.i];
@@ -720,7 +742,7 @@ csim_status csim_pool_plan(uint64_t budget, uint64_t min_block, int32_t n_stream
     for (size_t k = 0; k < running.size();) {
       if (running[k].t_end <= t) {
         finish[running[k].i] = running[k].t_end;
-        release_all(&a, running[k].offs);
+        release_all(&a, running[k].offs, kPlanAllocs);
         running[k] = running.back();
         running.pop_back();
       } else {

@@ -1,8 +1,9 @@
 """The request pool on the GPU: every request's results equal the same
 circuit run alone through csim_init / csim_run / csim_postselect (bit for bit:
-the kernels are deterministic and a request's work does not depend on what
-runs beside it), with and without CUDA-graph admission waves, under a budget
-small enough to force several admission waves."""
+the kernels are deterministic, a request's work does not depend on what runs
+beside it, and its source-index tables built in the arena hold the same
+indices as the circuit's own), with and without CUDA-graph admission waves,
+under a budget small enough to force several admission waves."""
 import numpy as np
 import pytest
 
@@ -43,8 +44,10 @@ def _alone(inst):
 
 @pytest.mark.parametrize("graphs", [False, True])
 def test_pool_mix_equals_alone(graphs):
+    # separate handles: the pool's circuits have not run alone, so their
+    # source-index tables come from the arena
+    alone = _alone(_instances())
     inst = _instances()
-    alone = _alone(inst)
     # budget: room for about two of the largest requests at once
     pool = G.Pool(n_streams=3, hbm_budget=160 << 20, max_qubits=30, use_graphs=graphs)
     ids = [pool.submit(c, f0, prec) for c, f0, prec in inst]
@@ -58,6 +61,7 @@ def test_pool_mix_equals_alone(graphs):
     assert st["completed"] == len(ids) and st["rejected"] == 0
     assert 0 < st["peak_bytes"] <= st["budget"]
     assert (st["graph_launches"] > 0) == graphs
+    assert st["src_tables"] == 2 * len(ids)  # U_L and U_L^dag chains of every request
     for rid, (amps0, p0, t0) in zip(ids, alone):
         amps, p, t, times = pool.result(rid)
         assert np.array_equal(amps, amps0)
