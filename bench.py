@@ -57,7 +57,12 @@ DEFAULT = "precision-nx64-k4-nt16-d13-c64"
 # minute on the host; run with --steps 1 --warmup 1.
 WORKLOADS["paper-long-nx8-nc2-k3-nt4-walls-c128"] = (8, 2, 3, 4, 0.1, 8 / 512.0 * 2.0 * 3.0, None, 0,
                                                       0, 0.0, "c128")
-BOUNDARY = {"paper-long-nx8-nc2-k3-nt4-walls-c128": "bounceback"}
+# The same run with the paper's own polynomial design: kappa_QSVT = 7100 and
+# d = 10 kappa_QSVT + 1 = 71001 (Sec. III.E.2).
+WORKLOADS["paper-long-nx8-nc2-k3-nt4-d71001-walls-c128"] = (8, 2, 3, 4, 0.1, 8 / 512.0 * 2.0 * 3.0,
+                                                             None, 0, 71001, 7100.0, "c128")
+BOUNDARY = {"paper-long-nx8-nc2-k3-nt4-walls-c128": "bounceback",
+            "paper-long-nx8-nc2-k3-nt4-d71001-walls-c128": "bounceback"}
 
 # Batching: count seeded instances (lbm_inputs.batch_instance), complex64,
 # run through the request pool; serving: a bounded prefix of the seeded
