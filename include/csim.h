@@ -247,12 +247,13 @@ csim_status csim_sv_free(csim_sv* sv);
  * sweeps (lookup-table permutations, multiplexed rotations, warp-tile gates)
  * on the host in FP64 with the kernel's semantics.  amps: 2^n interleaved
  * complex values, updated in place (n in [7, 24]), or NULL to compile only and
- * report the statistics (n in [7, 34]).  For testing the fuser without a GPU.  If stats is non-NULL it receives 15 counters: sweeps,
+ * report the statistics (n in [7, 34]).  For testing the fuser without a GPU.  If stats is non-NULL it receives 16 counters: sweeps,
  * single-gate steps, permutation gates, lookup tables, local gates,
  * multiplexers, multiplexed gates, multiplexer entries, largest bucket,
  * table entries, largest table support, HBM passes, averaging blocks,
- * multiplexers run as the inverse of the sweep's previous multiplexer, and
- * Walsh-Hadamard ops (H on several lane bits fused). */
+ * multiplexers run as the inverse of the sweep's previous multiplexer,
+ * Walsh-Hadamard ops (H on several lane bits fused), and in-place
+ * conjugated sweeps (a permutation, tile ops and the inverse permutation). */
 csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n, double* amps,
                                int64_t* stats);
 
@@ -289,7 +290,7 @@ csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out);
  * csim_run + csim_postselect) and try to admit.  f0 is copied.  *id receives
  * the request id.  Besides its state buffers, a request takes the source-index
  * tables of its sweeps from the arena (2^n bytes per distinct permutation
- * chain, two for a QSVT circuit; built on the request's stream before its
+ * chain, one for a QSVT circuit; built on the request's stream before its
  * sweeps), unless the circuit already holds its own from a csim_run or the
  * request fits the arena only without them.  CSIM_ERR_TOO_LARGE (counted as
  * rejected) when the circuit exceeds max_qubits or its blocks cannot fit the

@@ -22,7 +22,8 @@ namespace {
 thread_local std::string g_err;
 
 // Distinct gather chains that get a source-index table: a QSVT circuit has
-// two (U_L and U_L^dag); a gate stream with more keeps the lookup chains.
+// one or two (U_L^dag, and U_L when it is not fused into a conjugated sweep);
+// a gate stream with more keeps the lookup chains.
 constexpr int kSrcIndexTables = 2;
 
 csim_status fail(csim_status s, const std::string& msg) {
@@ -771,10 +772,10 @@ csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n
   }
   if (stats) {
     const csim::FuseStats& f = p.stats;
-    const int64_t v[15] = {f.sweeps,      f.single,      f.perm_gates,  f.segments, f.local_gates,
+    const int64_t v[16] = {f.sweeps,      f.single,      f.perm_gates,  f.segments, f.local_gates,
                            f.mux,         f.mux_gates,   f.mux_entries, f.max_bucket,
                            f.lut_entries, f.max_support, p.passes,      f.reflect,  f.mux_inverse,
-                           f.wht};
+                           f.wht,         f.conjugated};
     std::memcpy(stats, v, sizeof(v));
   }
   return CSIM_OK;

@@ -66,6 +66,16 @@ uint32_t order_window() {
   return v;
 }
 
+// A permutation run followed by its inverse becomes one in-place sweep
+// (CSIM_CONJUGATE=0 disables).
+bool conjugation_enabled() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_CONJUGATE");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+
 // Sibling-aware tile order for gather sweeps (CSIM_TILE_ORDER=0 disables).
 bool tile_order_enabled() {
   static const bool v = [] {
@@ -800,14 +810,26 @@ void choose_fast_bits(const std::vector<csim_gate>& perm, const Program& p, cons
 }
 
 // Place one [permutation run, tile-local run] group into sweeps.
-void emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vector<csim_gate>& local) {
+// Emit one [permutation run, tile-local run] group.  With conj (gather form),
+// the group is followed by the inverse permutation, which the caller drops:
+// when the group fits one sweep it becomes one in-place sweep that gathers
+// through P^-1, applies the ops and stores back to the gathered addresses
+// (P^-1 . ops . P); returns whether it did.
+bool emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vector<csim_gate>& local,
+                bool conj = false) {
   const std::vector<PermSeg> segs = compile_perm(perm, p->scatter, p);
   const size_t first_param = p->params.size();
   std::vector<std::vector<PermSeg>> sc;
   for (size_t k = 0; k < segs.size(); k += kMaxSeg)
     sc.emplace_back(segs.begin() + k, segs.begin() + std::min(segs.size(), k + kMaxSeg));
   std::vector<std::vector<OpItem>> oc = chunk_ops(compile_local(local, p));
-  if (!p->scatter) {
+  conj = conj && !p->scatter && sc.size() == 1 && oc.size() <= 1;
+  if (conj) {
+    emit_sweep(p, sc[0], oc.empty() ? std::vector<OpItem>() : oc[0]);
+    p->steps.back().inplace = true;
+    p->params.back().inplace = 1;
+    p->stats.conjugated++;
+  } else if (!p->scatter) {
     // gather: segment chunks are in evaluation (reverse time) order, so the
     // last chunk holds the earliest gates and runs first
     for (size_t k = sc.size(); k > 1; --k) emit_sweep(p, sc[k - 1], {});
@@ -821,7 +843,7 @@ void emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vecto
                oc.empty() ? std::vector<OpItem>() : oc.back());
     for (size_t k = 1; k < sc.size(); ++k) emit_sweep(p, sc[k], {});
   }
-  if (p->scatter || !tile_order_enabled()) return;
+  if (p->scatter || !tile_order_enabled()) return conj;
   for (size_t k = first_param; k < p->params.size(); ++k) {
     SweepParams& sp = p->params[k];
     if (sp.nseg == 0) continue;  // in place: no gather, natural order
@@ -848,6 +870,7 @@ void emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vecto
       }
     }
   }
+  return conj;
 }
 
 }  // namespace
@@ -874,26 +897,26 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
   std::vector<csim_gate> perm, local;
   bool open = false;
   const double sweep_cost = std::ldexp(1.0, n);
+  // groups and lone gates in circuit order; emitted after the scan so that a
+  // group can see whether the next one undoes its permutation
+  struct Item {
+    bool group = false;
+    std::vector<csim_gate> perm, local;
+    csim_gate g{};
+  };
+  std::vector<Item> items;
   auto single = [&](const csim_gate& g) {
-    Step s;
-    s.kind = 1;
-    s.g = g;
-    p->steps.push_back(s);
-    p->stats.single++;
+    Item it;
+    it.g = g;
+    items.push_back(std::move(it));
   };
   auto close = [&]() {
     if (!open) return;
-    // a group whose gates change fewer amplitudes in total than one sweep
-    // moves (e.g. a few multi-controlled X) runs cheaper as single gates
-    double cost = 0.0;
-    for (const csim_gate& g : perm) cost += gate_amp_updates(g, n);
-    for (const csim_gate& g : local) cost += gate_amp_updates(g, n);
-    if (cost < sweep_cost) {
-      for (const csim_gate& g : perm) single(g);
-      for (const csim_gate& g : local) single(g);
-    } else {
-      emit_group(p, perm, local);
-    }
+    Item it;
+    it.group = true;
+    it.perm = perm;
+    it.local = local;
+    items.push_back(std::move(it));
     perm.clear();
     local.clear();
     open = false;
@@ -936,11 +959,46 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
     }
   }
   close();
+  auto emit_single = [&](const csim_gate& g) {
+    Step s;
+    s.kind = 1;
+    s.g = g;
+    p->steps.push_back(s);
+    p->stats.single++;
+  };
+  auto reversed_equal = [](const std::vector<csim_gate>& a, const std::vector<csim_gate>& b) {
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i)
+      if (std::memcmp(&a[i], &b[b.size() - 1 - i], sizeof(csim_gate)) != 0) return false;
+    return true;
+  };
+  for (size_t k = 0; k < items.size(); ++k) {
+    Item& it = items[k];
+    if (!it.group) {
+      emit_single(it.g);
+      continue;
+    }
+    // a group whose gates change fewer amplitudes in total than one sweep
+    // moves (e.g. a few multi-controlled X) runs cheaper as single gates
+    double cost = 0.0;
+    for (const csim_gate& g : it.perm) cost += gate_amp_updates(g, n);
+    for (const csim_gate& g : it.local) cost += gate_amp_updates(g, n);
+    if (cost < sweep_cost) {
+      for (const csim_gate& g : it.perm) emit_single(g);
+      for (const csim_gate& g : it.local) emit_single(g);
+      continue;
+    }
+    // P^-1, ops, P (every multi-controlled X is its own inverse): one in-place sweep
+    const bool conj = conjugation_enabled() && !p->scatter && !it.perm.empty() &&
+                      k + 1 < items.size() && items[k + 1].group &&
+                      reversed_equal(it.perm, items[k + 1].perm);
+    if (emit_group(p, it.perm, it.local, conj) && conj) items[k + 1].perm.clear();
+  }
   p->passes = (int64_t)p->steps.size();
   for (const Step& s : p->steps)
     p->pass_amps += s.kind == 0 ? std::ldexp(1.0, n) : gate_amp_updates(s.g, n);
   for (const Step& s : p->steps)
-    if (s.kind == 0 && s.gather) p->pingpong = true;
+    if (s.kind == 0 && s.gather && !s.inplace) p->pingpong = true;
   p->stats.lut_entries = (int64_t)p->lut.size();
   if (std::getenv("CSIM_FUSE_STATS")) {
     const FuseStats& f = p->stats;
@@ -1152,15 +1210,17 @@ cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec
       e = launch_gate(buf[*cur], prec, p.n, s.g, st);
     } else if (!s.gather) {
       e = launch_sweep(buf[*cur], buf[*cur], prec, p.n, p.params[s.param], st);
-    } else if (src_tables && (size_t)s.param < p.src_tab.size() && p.src_tab[(size_t)s.param] >= 0) {
-      SweepParams a = p.params[(size_t)s.param];
-      a.src = src_tables[p.src_tab[(size_t)s.param]];
-      a.src_prefetch = src_prefetch_enabled() ? 1 : 0;
-      e = launch_sweep(buf[*cur], buf[1 - *cur], prec, p.n, a, st);
-      *cur = 1 - *cur;
     } else {
-      e = launch_sweep(buf[*cur], buf[1 - *cur], prec, p.n, p.params[s.param], st);
-      *cur = 1 - *cur;
+      void* out = s.inplace ? buf[*cur] : buf[1 - *cur];
+      if (src_tables && (size_t)s.param < p.src_tab.size() && p.src_tab[(size_t)s.param] >= 0) {
+        SweepParams a = p.params[(size_t)s.param];
+        a.src = src_tables[p.src_tab[(size_t)s.param]];
+        a.src_prefetch = src_prefetch_enabled() ? 1 : 0;
+        e = launch_sweep(buf[*cur], out, prec, p.n, a, st);
+      } else {
+        e = launch_sweep(buf[*cur], out, prec, p.n, p.params[s.param], st);
+      }
+      if (!s.inplace) *cur = 1 - *cur;
     }
     if (e != cudaSuccess) return e;
   }
@@ -1360,7 +1420,7 @@ void emulate_program(const Program& p, std::vector<double>* amps) {
       continue;
     }
     const SweepParams& sp = p.params[st.param];
-    std::vector<double>& dst = st.gather ? *nxt : *cur;
+    std::vector<double>& dst = (st.gather && !st.inplace) ? *nxt : *cur;
     const uint32_t ntiles = (uint32_t)(N >> 7);
     for (uint32_t tile = 0; tile < ntiles; ++tile) {
       double v[32][4][2];
@@ -1368,7 +1428,7 @@ void emulate_program(const Program& p, std::vector<double>* amps) {
       for (uint32_t lane = 0; lane < 32; ++lane) {
         const uint32_t ci = (tile << 5) | lane;
         const uint32_t src = sp.scatter ? ci : emu_permute(p, sp, ci);
-        where[lane] = sp.scatter ? emu_permute(p, sp, ci) : ci;
+        where[lane] = sp.scatter ? emu_permute(p, sp, ci) : (st.inplace ? src : ci);
         for (int j = 0; j < 4; ++j) {
           v[lane][j][0] = (*cur)[2 * (((size_t)src << 2) + j)];
           v[lane][j][1] = (*cur)[2 * (((size_t)src << 2) + j) + 1];
@@ -1381,7 +1441,7 @@ void emulate_program(const Program& p, std::vector<double>* amps) {
           dst[2 * (((size_t)where[lane] << 2) + j) + 1] = v[lane][j][1];
         }
     }
-    if (st.gather) std::swap(cur, nxt);
+    if (st.gather && !st.inplace) std::swap(cur, nxt);
   }
   if (cur != amps) *amps = *cur;
 }

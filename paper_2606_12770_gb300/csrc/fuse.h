@@ -15,7 +15,8 @@ namespace csim {
 struct Step {
   int kind = 0;    // 0 = fused sweep, 1 = single gate
   int param = -1;  // index into Program::params (sweeps)
-  bool gather = false;  // the sweep moves data (out of place)
+  bool gather = false;  // the sweep has segments (moves data)
+  bool inplace = false;  // ... and stores back to the gathered addresses (in == out)
   csim_gate g{};
 };
 
@@ -25,6 +26,7 @@ struct FuseStats {
   int64_t reflect = 0;
   int64_t mux_inverse = 0;  // multiplexers run as the inverse of the sweep's previous one
   int64_t wht = 0;          // Walsh-Hadamard ops (H on several lane bits)
+  int64_t conjugated = 0;   // in-place P^-1 . ops . P sweeps
 };
 
 struct Program {

@@ -712,7 +712,8 @@ __global__ void __launch_bounds__(256, MINB)
       for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)mv[u] << 2), v[u]);
       apply_ops<R, U>(a, v, ci, lane, wd);
 #pragma unroll
-      for (int u = 0; u < U; ++u) store_chunk(out + ((size_t)ci[u] << 2), v[u]);
+      for (int u = 0; u < U; ++u)
+        store_chunk(out + ((size_t)(a.inplace ? mv[u] : ci[u]) << 2), v[u]);
     } else {
 #pragma unroll
       for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)ci[u] << 2), v[u]);

@@ -104,6 +104,11 @@ struct SweepParams {
   // instead of walking the segment chain.
   const uint32_t* src;
   int src_prefetch;  // load the next iteration's source indices one iteration ahead
+  // Gather form: store each chunk back to the address it was loaded from
+  // (in == out), so that the sweep applies P^-1 . ops . P in place, P the
+  // segments' permutation: a permutation, tile ops, and the inverse
+  // permutation in one pass.
+  int inplace;
 };
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,

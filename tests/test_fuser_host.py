@@ -93,6 +93,9 @@ def test_qsvt_circuit_one_sweep_per_call(cfg, d):
     assert st["mux_inverse"] == (d - 1) // 2
     # the label Hadamard layers of the first and the last call are fused
     assert st["wht"] == 2
+    # each U_L^dag permutation is undone by the next U_L: one in-place sweep
+    # (P^-1, projector, P); the multiplexer sweeps between need no gather
+    assert st["conjugated"] == (d - 1) // 2
     assert rel(got, S.DenseSim(lay.n).run(psi.copy(), gates)) < 1e-13
 
 

@@ -302,15 +302,18 @@ print("ok")
 '''
 
 
+@pytest.mark.parametrize("conj", ["1", "0"])
 @pytest.mark.parametrize("src", ["1", "0"])
 @pytest.mark.parametrize("waves", ["4", "1"])
 @pytest.mark.parametrize("form", ["gather", "scatter"])
 @pytest.mark.parametrize("cfg", ["1,1", "2,1", "4,1", "1,2", "2,2", "4,2", "1,4", "2,4"])
-def test_sweep_kernel_variants(cfg, form, waves, src):
+def test_sweep_kernel_variants(cfg, form, waves, src, conj):
     """Every compiled sweep-kernel variant (tiles per iteration, blocks per SM,
     form); one resident wave makes each warp loop over several tiles at 20
     qubits.  Gather sweeps run with source-index tables and, on the default
-    variant, with the lookup-table chain."""
+    variant, with the lookup-table chain; the default variants also run with
+    the permutation pairs as separate gathers instead of in-place conjugated
+    sweeps."""
     import os
     import subprocess
     import sys
@@ -318,9 +321,11 @@ def test_sweep_kernel_variants(cfg, form, waves, src):
         pytest.skip("single-wave grids are checked on three variants")
     if src == "0" and (form != "gather" or cfg != "2,4"):
         pytest.skip("the lookup-table chain is checked on the default gather variant")
+    if conj == "0" and (form != "gather" or cfg not in ("2,4", "1,2") or waves != "4"):
+        pytest.skip("separate permutation sweeps are checked on the default variants")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, CSIM_SWEEP_CFG=cfg, CSIM_SWEEP_FORM=form, CSIM_SWEEP_WAVES=waves,
-               CSIM_SRC_INDEX=src)
+               CSIM_SRC_INDEX=src, CSIM_CONJUGATE=conj)
     r = subprocess.run([sys.executable, "-c", VARIANT_SCRIPT, root], env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
@@ -349,7 +354,8 @@ def test_source_index_tables_equal_lookup_chain(tmp_path):
     precomputed source index of each chunk or walk the lookup-table chain (the
     same index, the same arithmetic), with the indices loaded one iteration
     ahead or not, and in the scatter form (destination indices); the table
-    path is the one in use by default (two tables: U_L and U_L^dag)."""
+    path is the one in use by default (one table: the U_L^dag chain, which the
+    conjugated sweeps and the last gather share)."""
     import os
     import subprocess
     import sys
@@ -365,7 +371,7 @@ def test_source_index_tables_equal_lookup_chain(tmp_path):
                            capture_output=True, text=True, timeout=600)
         assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
         res[name] = np.load(path)
-    assert int(res["chain"]["c128_tables"]) == 0 and int(res["default"]["c128_tables"]) == 2
+    assert int(res["chain"]["c128_tables"]) == 0 and int(res["default"]["c128_tables"]) == 1
     for prec in ("c128", "c64"):
         assert np.array_equal(res["chain"][prec], res["default"][prec]), prec
         assert np.array_equal(res["src-nopre"][prec], res["default"][prec]), prec
