@@ -467,6 +467,36 @@ void compile_mux_group(const std::vector<csim_gate>& grp, Program* p, std::vecto
   p->stats.mux++;
   p->stats.mux_gates += (int64_t)grp.size();
   p->stats.mux_entries = (int64_t)p->mentf.size();
+  if (const char* dbg = std::getenv("CSIM_FUSE_STATS")) {
+    if (dbg[0] == '2' && p->n >= 12) {
+      // warp view: the candidate loop runs max-over-lanes iterations
+      uint64_t rs = 0x9e3779b97f4a7c15ull;
+      double loops = 0, warps_looping = 0, lanes_cand = 0;
+      const int samples = 4096;
+      const uint32_t tmask = (p->n - 7 >= 32) ? 0xffffffffu : ((1u << (p->n - 7)) - 1u);
+      for (int k = 0; k < samples; ++k) {
+        rs ^= rs << 13;
+        rs ^= rs >> 7;
+        rs ^= rs << 17;
+        const uint32_t tile = (uint32_t)rs & tmask;
+        uint32_t mx = 0;
+        for (uint32_t lane = 0; lane < 32; ++lane) {
+          const uint32_t w = p->mtab[it.mux.tab_off + win_key((tile << 5) | lane, win)];
+          if (w != 0u && !(w & 0x80000000u)) {
+            mx = std::max(mx, w & 255u);
+            lanes_cand += 1;
+          }
+        }
+        loops += mx;
+        warps_looping += mx > 0;
+      }
+      std::fprintf(stderr,
+                   "[csim fuse] mux %zu: key bits %d, lanes with candidates %.2f%%, warps looping "
+                   "%.1f%%, mean warp trip count %.2f\n",
+                   p->mux_descs.size() - 1, w, 100.0 * lanes_cand / (32.0 * samples),
+                   100.0 * warps_looping / samples, loops / samples);
+    }
+  }
 }
 
 // RY gates on one in-thread qubit commute: split the run by its controls on

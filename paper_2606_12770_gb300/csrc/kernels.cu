@@ -334,8 +334,184 @@ struct CplxOf<double> {
   }
 };
 
-// Apply the tile-local ops of one sweep to U tiles held by the warp.
+// Bucket words of the first kPrefetchMux multiplexers are loaded early.
 constexpr int kPrefetchMux = 2;
+
+// Averaging block: I (x) A + J (x) B over the lane bits of rd.lanemask.
+template <typename R, int U>
+__device__ __forceinline__ void op_refl(const ReflectDesc& rd, typename V2<R>::T (&v)[U][4],
+                                        uint32_t lane) {
+  using T = typename V2<R>::T;
+  const uint32_t lmask = rd.lanemask, nzA = rd.nzA, nzB = rd.nzB;
+  if (((nzA | nzB) & ~0x8421u) == 0) {  // A and B diagonal
+    if (lmask == 31u && __popc(nzB) == 2) {  // every lane, two y's: one joint reduction
+      const int ya = (__ffs(nzB) - 1) / 5, yb = (31 - __clz(nzB)) / 5;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        T xa = v[u][0], xb = v[u][0];
+#pragma unroll
+        for (int y = 1; y < 4; ++y) {
+          if (y == ya) xa = v[u][y];
+          if (y == yb) xb = v[u][y];
+        }
+        T Sa, Sb;
+        lane_sum2<T, R>(xa, xb, Sa, Sb, lane);
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int q = y * 5;
+          const T ca = CplxOf<R>::a(rd, q);
+          const T x = v[u][y];
+          T o = mk<T>(ca.x * x.x - ca.y * x.y, ca.x * x.y + ca.y * x.x);
+          if (y == ya || y == yb) {
+            const T cb = CplxOf<R>::b(rd, q);
+            const T S = (y == ya) ? Sa : Sb;
+            if (cb.x == (R)0) {  // purely imaginary (the QSVT projector phase)
+              o.x -= cb.y * S.y;
+              o.y += cb.y * S.x;
+            } else {
+              o.x += cb.x * S.x - cb.y * S.y;
+              o.y += cb.x * S.y + cb.y * S.x;
+            }
+          }
+          v[u][y] = o;
+        }
+      }
+      return;
+    }
+    if (lmask == 31u && nzB == 0x8421u) {  // every lane and every y: one joint reduction
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        T S[4];
+        lane_sum4<T, R>(v[u], S, lane);
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int q = y * 5;
+          const T ca = CplxOf<R>::a(rd, q), cb = CplxOf<R>::b(rd, q);
+          const T x = v[u][y];
+          v[u][y] = mk<T>(ca.x * x.x - ca.y * x.y + cb.x * S[y].x - cb.y * S[y].y,
+                          ca.x * x.y + ca.y * x.x + cb.x * S[y].y + cb.y * S[y].x);
+        }
+      }
+      return;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int q = y * 5;
+        T S = v[u][y];
+        if ((nzB >> q) & 1u) {
+#pragma unroll
+          for (int b = 0; b < 5; ++b) {
+            if (!((lmask >> b) & 1u)) continue;
+            const T w = shfl_xor_c(S, 1 << b);
+            S.x += w.x;
+            S.y += w.y;
+          }
+        }
+        const T ca = CplxOf<R>::a(rd, q), cb = CplxOf<R>::b(rd, q);
+        const T x = v[u][y];
+        T o = mk<T>(ca.x * x.x - ca.y * x.y, ca.x * x.y + ca.y * x.x);
+        if ((nzB >> q) & 1u) {
+          o.x += cb.x * S.x - cb.y * S.y;
+          o.y += cb.x * S.y + cb.y * S.x;
+        }
+        v[u][y] = o;
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    T S[4];
+#pragma unroll
+    for (int y = 0; y < 4; ++y) S[y] = v[u][y];
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      if (!((lmask >> b) & 1u)) continue;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const T w = shfl_xor_c(S[y], 1 << b);
+        S[y].x += w.x;
+        S[y].y += w.y;
+      }
+    }
+    T o4[4];
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      o4[y] = mk<T>((R)0, (R)0);
+#pragma unroll
+      for (int yp = 0; yp < 4; ++yp) {
+        const int q = y * 4 + yp;
+        if ((nzA >> q) & 1u) {
+          const T c = CplxOf<R>::a(rd, q);
+          o4[y].x += c.x * v[u][yp].x - c.y * v[u][yp].y;
+          o4[y].y += c.x * v[u][yp].y + c.y * v[u][yp].x;
+        }
+        if ((nzB >> q) & 1u) {
+          const T c = CplxOf<R>::b(rd, q);
+          o4[y].x += c.x * S[yp].x - c.y * S[yp].y;
+          o4[y].y += c.x * S[yp].y + c.y * S[yp].x;
+        }
+      }
+    }
+#pragma unroll
+    for (int y = 0; y < 4; ++y) v[u][y] = o4[y];
+  }
+  return;
+}
+
+// Multiplexed RY (descriptor md, prefetched bucket words in wd when slot < 2):
+// compose the rotation each chunk gets, apply it, and keep it in (mc, ms).
+template <typename R, int U>
+__device__ __forceinline__ void op_mux(const SweepParams& a, const MuxDesc& md, uint32_t slot,
+                                       typename V2<R>::T (&v)[U][4], const uint32_t (&ci)[U],
+                                       const uint32_t (&wd)[kPrefetchMux][U], R (&mc)[U],
+                                       R (&ms)[U]) {
+  using T = typename V2<R>::T;
+  const KeyWin w = md.win;
+  const uint32_t toff = md.tab_off, mt = md.target, mlm = md.lm, mlv = md.lv;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    uint32_t word;
+    if (slot == 0) word = wd[0][u];
+    else if (slot == 1 && kPrefetchMux > 1) word = wd[1][u];
+    else word = __ldg(a.mtab + toff + win_key(ci[u], w));
+    R c = (R)1, s = (R)0;
+    if (word & 0x80000000u) {
+      const T cs = CplxOf<R>::angle(a, word & 0x7fffffffu);
+      c = cs.x;
+      s = cs.y;
+    } else if (word != 0u) {
+      // the matching candidates' rotations commute: compose them, rotate once
+      const uint32_t e0 = word >> 8, e1 = e0 + (word & 255u);
+      for (uint32_t e = e0; e < e1; ++e) {
+        uint32_t cm, cv;
+        R ce, se;
+        CplxOf<R>::entry(a, e, &cm, &cv, &ce, &se);
+        if ((ci[u] & cm) == cv) {
+          const R nc = c * ce - s * se;
+          s = s * ce + c * se;
+          c = nc;
+        }
+      }
+    }
+    mc[u] = c;
+    ms[u] = s;
+    if (word != 0u) rot_pairs<T, R>(v[u], mt, mlm, mlv, c, s);
+  }
+}
+
+// The inverse of the latest multiplexer: the kept rotation with the sine negated.
+template <typename R, int U>
+__device__ __forceinline__ void op_mux_inverse(uint32_t tg, uint32_t lm, uint32_t lv,
+                                               typename V2<R>::T (&v)[U][4], const R (&mc)[U],
+                                               const R (&ms)[U]) {
+  using T = typename V2<R>::T;
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    if (ms[u] != (R)0 || mc[u] != (R)1) rot_pairs<T, R>(v[u], tg, lm, lv, mc[u], -ms[u]);
+}
 
 // Bucket words of the first multiplexers of the sweep: they depend only on
 // the destination index, so they are loaded before the permutation chain.
@@ -351,6 +527,7 @@ __device__ __forceinline__ void prefetch_mux(const SweepParams& a, const uint32_
   }
 }
 
+// Apply the tile-local ops of one sweep to U tiles held by the warp.
 template <typename R, int U>
 __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::T (&v)[U][4],
                                           const uint32_t (&ci)[U], uint32_t lane,
@@ -367,38 +544,11 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
     const LocalOp& o = a.ops[k];
     const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv, op = o.op, tg = o.target;
     if (op == 4) {  // multiplexed RY on bit tg (0 or 1)
-      const MuxDesc& md = a.mux[ocm];
-      const KeyWin w = md.win;
-      const uint32_t toff = md.tab_off, mt = md.target, mlm = md.lm, mlv = md.lv;
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        uint32_t word;
-        if (ocm == 0) word = wd[0][u];
-        else if (ocm == 1 && kPrefetchMux > 1) word = wd[1][u];
-        else word = __ldg(a.mtab + toff + win_key(ci[u], w));
-        R c = (R)1, s = (R)0;
-        if (word & 0x80000000u) {
-          const T cs = CplxOf<R>::angle(a, word & 0x7fffffffu);
-          c = cs.x;
-          s = cs.y;
-        } else if (word != 0u) {
-          // the matching candidates' rotations commute: compose them, rotate once
-          const uint32_t e0 = word >> 8, e1 = e0 + (word & 255u);
-          for (uint32_t e = e0; e < e1; ++e) {
-            uint32_t cm, cv;
-            R ce, se;
-            CplxOf<R>::entry(a, e, &cm, &cv, &ce, &se);
-            if ((ci[u] & cm) == cv) {
-              const R nc = c * ce - s * se;
-              s = s * ce + c * se;
-              c = nc;
-            }
-          }
-        }
-        mc[u] = c;
-        ms[u] = s;
-        if (word != 0u) rot_pairs<T, R>(v[u], mt, mlm, mlv, c, s);
-      }
+      op_mux<R, U>(a, a.mux[ocm], ocm, v, ci, wd, mc, ms);
+      continue;
+    }
+    if (op == 7) {  // inverse of the latest multiplexer: RY(-theta) with the same controls
+      op_mux_inverse<R, U>(tg, lm, lv, v, mc, ms);
       continue;
     }
     if (op == 8) {  // H on each lane bit of the mask: butterflies, then one scale
@@ -421,130 +571,8 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
         for (int j = 0; j < 4; ++j) v[u][j] = mk<T>(v[u][j].x * sc, v[u][j].y * sc);
       continue;
     }
-    if (op == 7) {  // inverse of the latest multiplexer: RY(-theta) with the same controls
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (ms[u] != (R)0 || mc[u] != (R)1) rot_pairs<T, R>(v[u], tg, lm, lv, mc[u], -ms[u]);
-      continue;
-    }
     if (op == 5) {  // I (x) A + J (x) B over the lane bits of lanemask
-      const ReflectDesc& rd = a.refl[ocm];
-      const uint32_t lmask = rd.lanemask, nzA = rd.nzA, nzB = rd.nzB;
-      if (((nzA | nzB) & ~0x8421u) == 0) {  // A and B diagonal
-        if (lmask == 31u && __popc(nzB) == 2) {  // every lane, two y's: one joint reduction
-          const int ya = (__ffs(nzB) - 1) / 5, yb = (31 - __clz(nzB)) / 5;
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            T xa = v[u][0], xb = v[u][0];
-#pragma unroll
-            for (int y = 1; y < 4; ++y) {
-              if (y == ya) xa = v[u][y];
-              if (y == yb) xb = v[u][y];
-            }
-            T Sa, Sb;
-            lane_sum2<T, R>(xa, xb, Sa, Sb, lane);
-#pragma unroll
-            for (int y = 0; y < 4; ++y) {
-              const int q = y * 5;
-              const T ca = CplxOf<R>::a(rd, q);
-              const T x = v[u][y];
-              T o = mk<T>(ca.x * x.x - ca.y * x.y, ca.x * x.y + ca.y * x.x);
-              if (y == ya || y == yb) {
-                const T cb = CplxOf<R>::b(rd, q);
-                const T S = (y == ya) ? Sa : Sb;
-                if (cb.x == (R)0) {  // purely imaginary (the QSVT projector phase)
-                  o.x -= cb.y * S.y;
-                  o.y += cb.y * S.x;
-                } else {
-                  o.x += cb.x * S.x - cb.y * S.y;
-                  o.y += cb.x * S.y + cb.y * S.x;
-                }
-              }
-              v[u][y] = o;
-            }
-          }
-          continue;
-        }
-        if (lmask == 31u && nzB == 0x8421u) {  // every lane and every y: one joint reduction
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            T S[4];
-            lane_sum4<T, R>(v[u], S, lane);
-#pragma unroll
-            for (int y = 0; y < 4; ++y) {
-              const int q = y * 5;
-              const T ca = CplxOf<R>::a(rd, q), cb = CplxOf<R>::b(rd, q);
-              const T x = v[u][y];
-              v[u][y] = mk<T>(ca.x * x.x - ca.y * x.y + cb.x * S[y].x - cb.y * S[y].y,
-                              ca.x * x.y + ca.y * x.x + cb.x * S[y].y + cb.y * S[y].x);
-            }
-          }
-          continue;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-#pragma unroll
-          for (int y = 0; y < 4; ++y) {
-            const int q = y * 5;
-            T S = v[u][y];
-            if ((nzB >> q) & 1u) {
-#pragma unroll
-              for (int b = 0; b < 5; ++b) {
-                if (!((lmask >> b) & 1u)) continue;
-                const T w = shfl_xor_c(S, 1 << b);
-                S.x += w.x;
-                S.y += w.y;
-              }
-            }
-            const T ca = CplxOf<R>::a(rd, q), cb = CplxOf<R>::b(rd, q);
-            const T x = v[u][y];
-            T o = mk<T>(ca.x * x.x - ca.y * x.y, ca.x * x.y + ca.y * x.x);
-            if ((nzB >> q) & 1u) {
-              o.x += cb.x * S.x - cb.y * S.y;
-              o.y += cb.x * S.y + cb.y * S.x;
-            }
-            v[u][y] = o;
-          }
-        }
-        continue;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        T S[4];
-#pragma unroll
-        for (int y = 0; y < 4; ++y) S[y] = v[u][y];
-#pragma unroll
-        for (int b = 0; b < 5; ++b) {
-          if (!((lmask >> b) & 1u)) continue;
-#pragma unroll
-          for (int y = 0; y < 4; ++y) {
-            const T w = shfl_xor_c(S[y], 1 << b);
-            S[y].x += w.x;
-            S[y].y += w.y;
-          }
-        }
-        T o4[4];
-#pragma unroll
-        for (int y = 0; y < 4; ++y) {
-          o4[y] = mk<T>((R)0, (R)0);
-#pragma unroll
-          for (int yp = 0; yp < 4; ++yp) {
-            const int q = y * 4 + yp;
-            if ((nzA >> q) & 1u) {
-              const T c = CplxOf<R>::a(rd, q);
-              o4[y].x += c.x * v[u][yp].x - c.y * v[u][yp].y;
-              o4[y].y += c.x * v[u][yp].y + c.y * v[u][yp].x;
-            }
-            if ((nzB >> q) & 1u) {
-              const T c = CplxOf<R>::b(rd, q);
-              o4[y].x += c.x * S[yp].x - c.y * S[yp].y;
-              o4[y].y += c.x * S[yp].y + c.y * S[yp].x;
-            }
-          }
-        }
-#pragma unroll
-        for (int y = 0; y < 4; ++y) v[u][y] = o4[y];
-      }
+      op_refl<R, U>(a.refl[ocm], v, lane);
       continue;
     }
     const R c = Coef<R>::c(o), s = Coef<R>::s(o);
@@ -607,6 +635,26 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
   }
 }
 
+// Sweep shapes with a kernel of their own, so that the descriptors sit at
+// fixed parameter offsets and no op list is interpreted: 1 = one averaging
+// block; 2 = multiplexer, averaging block, inverse multiplexer.  0 = any op
+// list (apply_ops).
+template <typename R, int U, int SHAPE>
+__device__ __forceinline__ void apply_shaped(const SweepParams& a, typename V2<R>::T (&v)[U][4],
+                                             const uint32_t (&ci)[U], uint32_t lane,
+                                             const uint32_t (&wd)[kPrefetchMux][U]) {
+  if constexpr (SHAPE == 1) {
+    op_refl<R, U>(a.refl[0], v, lane);
+  } else if constexpr (SHAPE == 2) {
+    R mc[U], ms[U];
+    op_mux<R, U>(a, a.mux[0], 0u, v, ci, wd, mc, ms);
+    op_refl<R, U>(a.refl[0], v, lane);
+    op_mux_inverse<R, U>(a.ops[2].target, a.ops[2].lm, a.ops[2].lv, v, mc, ms);
+  } else {
+    apply_ops<R, U>(a, v, ci, lane, wd);
+  }
+}
+
 // Map chunk indices through the permutation segments of a sweep.
 template <int U>
 __device__ __forceinline__ void permute(const SweepParams& a, uint32_t (&x)[U]) {
@@ -647,7 +695,7 @@ __device__ __forceinline__ void permute(const SweepParams& a, uint32_t (&x)[U]) 
 // their deposit L[u] is computed once, and the high part H advances by a
 // masked add of hstep (the deposit of stride >> nfe).  nfe = 0 is the natural
 // order.
-template <typename R, int U, int MINB>
+template <typename R, int U, int MINB, int SHAPE>
 __global__ void __launch_bounds__(256, MINB)
     sweep_kernel(const typename V2<R>::T* in, typename V2<R>::T* out, uint32_t ntiles, int nfe,
                  uint32_t fmask, uint32_t hstep, const __grid_constant__ SweepParams a) {
@@ -692,7 +740,7 @@ __global__ void __launch_bounds__(256, MINB)
     H = nfe > 0 ? (((H | fmask) + hstep) & ~fmask) : (H + nwarps * U);
     T v[U][4];
     uint32_t wd[kPrefetchMux][U];
-    prefetch_mux<U>(a, ci, wd);
+    if constexpr (SHAPE != 1) prefetch_mux<U>(a, ci, wd);
     if (!a.scatter) {
       if (pre) {
 #pragma unroll
@@ -710,14 +758,14 @@ __global__ void __launch_bounds__(256, MINB)
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)mv[u] << 2), v[u]);
-      apply_ops<R, U>(a, v, ci, lane, wd);
+      apply_shaped<R, U, SHAPE>(a, v, ci, lane, wd);
 #pragma unroll
       for (int u = 0; u < U; ++u)
         store_chunk(out + ((size_t)(a.inplace ? mv[u] : ci[u]) << 2), v[u]);
     } else {
 #pragma unroll
       for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)ci[u] << 2), v[u]);
-      apply_ops<R, U>(a, v, ci, lane, wd);
+      apply_shaped<R, U, SHAPE>(a, v, ci, lane, wd);
       if (a.src) {
 #pragma unroll
         for (int u = 0; u < U; ++u) mv[u] = __ldcs(a.src + ci[u]);
@@ -985,13 +1033,13 @@ int sweep_resident() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R, U, MINB>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R, U, MINB, 0>, 256, 0);
     resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
   }
   return resident;
 }
 
-template <typename R, int U, int MINB>
+template <typename R, int U, int MINB, int SHAPE = 0>
 void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepParams& a, cudaStream_t st) {
   using T = typename V2<R>::T;
   const int blk = 256;
@@ -1013,8 +1061,36 @@ void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepParam
     hstep |= (hv & 1u) << b;
     hv >>= 1;
   }
-  sweep_kernel<R, U, MINB><<<(int)grd, blk, 0, st>>>((const T*)in, (T*)out, ntiles, nfe, fmask,
-                                                      hstep, a);
+  sweep_kernel<R, U, MINB, SHAPE><<<(int)grd, blk, 0, st>>>((const T*)in, (T*)out, ntiles, nfe,
+                                                             fmask, hstep, a);
+}
+
+// The sweep shape of a parameter block (see apply_shaped).
+int sweep_shape(const SweepParams& a) {
+  if (a.nops == 1 && a.ops[0].op == 5 && a.ops[0].cm == 0) return 1;
+  if (a.nops == 3 && a.ops[0].op == 4 && a.ops[0].cm == 0 && a.ops[1].op == 5 &&
+      a.ops[1].cm == 0 && a.ops[2].op == 7)
+    return 2;
+  return 0;
+}
+
+// Shaped kernels exist for the default variants only (complex64 <2, 4>,
+// complex128 <1, 2>); CSIM_SWEEP_SHAPES=0 keeps every sweep generic.
+bool shapes_enabled() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_SWEEP_SHAPES");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+
+template <typename R, int U, int MINB>
+void launch_shaped(const void* in, void* out, uint32_t ntiles, const SweepParams& a,
+                   cudaStream_t st) {
+  const int shape = shapes_enabled() ? sweep_shape(a) : 0;
+  if (shape == 1) return launch_sweep_t<R, U, MINB, 1>(in, out, ntiles, a, st);
+  if (shape == 2) return launch_sweep_t<R, U, MINB, 2>(in, out, ntiles, a, st);
+  return launch_sweep_t<R, U, MINB, 0>(in, out, ntiles, a, st);
 }
 
 template <typename R>
@@ -1022,12 +1098,16 @@ void launch_sweep_r(const void* in, void* out, uint32_t ntiles, int u, int minb,
                     cudaStream_t st) {
   while ((uint32_t)u > ntiles) u >>= 1;
   if (minb == 4) {
-    if (u == 2) return launch_sweep_t<R, 2, 4>(in, out, ntiles, a, st);
+    if (u == 2) {
+      if constexpr (sizeof(R) == 4) return launch_shaped<R, 2, 4>(in, out, ntiles, a, st);
+      return launch_sweep_t<R, 2, 4>(in, out, ntiles, a, st);
+    }
     return launch_sweep_t<R, 1, 4>(in, out, ntiles, a, st);
   }
   if (minb == 2) {
     if (u == 4) return launch_sweep_t<R, 4, 2>(in, out, ntiles, a, st);
     if (u == 2) return launch_sweep_t<R, 2, 2>(in, out, ntiles, a, st);
+    if constexpr (sizeof(R) == 8) return launch_shaped<R, 1, 2>(in, out, ntiles, a, st);
     return launch_sweep_t<R, 1, 2>(in, out, ntiles, a, st);
   }
   if (u == 4) return launch_sweep_t<R, 4, 1>(in, out, ntiles, a, st);
@@ -1090,6 +1170,13 @@ cudaError_t warm_r() {
   chk(cudaFuncGetAttributes(&fa, gate_kernel<R>));
   chk(cudaFuncGetAttributes(&fa, norm_kernel<R>));
   chk(cudaFuncGetAttributes(&fa, compact_kernel<R>));
+  if constexpr (sizeof(R) == 4) {
+    chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 2, 4, 1>));
+    chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 2, 4, 2>));
+  } else {
+    chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 1, 2, 1>));
+    chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 1, 2, 2>));
+  }
   sweep_resident<R, 1, 1>();
   sweep_resident<R, 2, 1>();
   sweep_resident<R, 4, 1>();

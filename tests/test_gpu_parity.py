@@ -355,18 +355,20 @@ def test_source_index_tables_equal_lookup_chain(tmp_path):
     same index, the same arithmetic), with the indices loaded one iteration
     ahead or not, and in the scatter form (destination indices); the table
     path is the one in use by default (one table: the U_L^dag chain, which the
-    conjugated sweeps and the last gather share)."""
+    conjugated sweeps and the last gather share).  The kernels specialised on
+    the sweep shape agree with the generic op interpreter within rounding."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     res = {}
-    modes = {"chain": ("0", "1", "gather"), "src-nopre": ("1", "0", "gather"),
-             "default": ("1", "1", "gather"), "chain-scatter": ("0", "1", "scatter"),
-             "scatter": ("1", "1", "scatter")}
-    for name, (flag, pre, form) in modes.items():
+    modes = {"chain": ("0", "1", "gather", "1"), "src-nopre": ("1", "0", "gather", "1"),
+             "default": ("1", "1", "gather", "1"), "chain-scatter": ("0", "1", "scatter", "1"),
+             "scatter": ("1", "1", "scatter", "1"), "generic": ("1", "1", "gather", "0")}
+    for name, (flag, pre, form, shapes) in modes.items():
         path = str(tmp_path / f"{name}.npz")
-        env = dict(os.environ, CSIM_SRC_INDEX=flag, CSIM_SRC_PREFETCH=pre, CSIM_SWEEP_FORM=form)
+        env = dict(os.environ, CSIM_SRC_INDEX=flag, CSIM_SRC_PREFETCH=pre, CSIM_SWEEP_FORM=form,
+                   CSIM_SWEEP_SHAPES=shapes)
         r = subprocess.run([sys.executable, "-c", SRC_SCRIPT, root, path], env=env,
                            capture_output=True, text=True, timeout=600)
         assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
@@ -376,3 +378,8 @@ def test_source_index_tables_equal_lookup_chain(tmp_path):
         assert np.array_equal(res["chain"][prec], res["default"][prec]), prec
         assert np.array_equal(res["src-nopre"][prec], res["default"][prec]), prec
         assert np.array_equal(res["chain-scatter"][prec], res["scatter"][prec]), prec
+        # shaped kernels against the generic op interpreter: the same operations,
+        # compiled in other instantiations (contraction may differ)
+        a, b = res["default"][prec], res["generic"][prec]
+        tol = 1e-14 if prec == "c128" else 1e-6
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < tol, prec
