@@ -17,6 +17,8 @@
 //   compact_kernel       -- gather the postselected block
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -527,12 +529,100 @@ __device__ __forceinline__ void prefetch_mux(const SweepParams& a, const uint32_
   }
 }
 
+// A gate of op code 0-3 (X, H, RY, ZPHASE) on an in-thread bit (target 0-1)
+// or a lane bit (target 2-6), op 6 (ZPHASE above the tile) or op 8 (lane
+// Walsh-Hadamard), with the descriptor o.  The op code is a parameter so that
+// the shaped sweeps, which pass a constant, compile one path.
+template <typename R, int U>
+__device__ __forceinline__ void op_tile_gate(uint32_t op, const LocalOp& o,
+                                             typename V2<R>::T (&v)[U][4], const uint32_t (&ci)[U],
+                                             uint32_t lane) {
+  using T = typename V2<R>::T;
+  const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv, tg = o.target;
+  if (op == 8) {  // H on each lane bit of the mask: butterflies, then one scale
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      if (!((ocm >> b) & 1u)) continue;
+      const R sg = ((lane >> b) & 1u) ? (R)-1 : (R)1;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const T w = shfl_xor_c(v[u][j], 1 << b);
+          v[u][j] = mk<T>(fma(v[u][j].x, sg, w.x), fma(v[u][j].y, sg, w.y));
+        }
+    }
+    const R sc = Coef<R>::c(o);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[u][j] = mk<T>(v[u][j].x * sc, v[u][j].y * sc);
+    return;
+  }
+  const R c = Coef<R>::c(o), s = Coef<R>::s(o);
+  if (op == 6) {  // e^{i phi Z} on chunk-index bit tg (a qubit above the tile)
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if ((ci[u] & ocm) != ocv) continue;
+      const R sg = ((ci[u] >> tg) & 1u) ? -s : s;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (((uint32_t)j & lm) == lv)
+          v[u][j] = mk<T>(v[u][j].x * c - v[u][j].y * sg, v[u][j].x * sg + v[u][j].y * c);
+    }
+    return;
+  }
+  if (tg < 2) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if ((ci[u] & ocm) != ocv) continue;
+      if (tg == 0) {
+        if ((0u & lm) == lv) apply_pair<R>(v[u][0], v[u][1], op, c, s);
+        if ((2u & lm) == lv) apply_pair<R>(v[u][2], v[u][3], op, c, s);
+      } else {
+        if ((0u & lm) == lv) apply_pair<R>(v[u][0], v[u][2], op, c, s);
+        if ((1u & lm) == lv) apply_pair<R>(v[u][1], v[u][3], op, c, s);
+      }
+    }
+    return;
+  }
+  const int lmask = 1 << (tg - 2);
+  const bool hi = (lane & (uint32_t)lmask) != 0;
+  const R h = (R)0.70710678118654752440;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const bool cok = (ci[u] & ocm) == ocv;
+    if (op == 3) {  // diagonal: no partner needed
+      if (!cok) continue;
+      const R sg = hi ? -s : s;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (((uint32_t)j & lm) == lv)
+          v[u][j] = mk<T>(v[u][j].x * c - v[u][j].y * sg, v[u][j].x * sg + v[u][j].y * c);
+      continue;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T w = shfl_xor_c(v[u][j], lmask);
+      if (!cok || (((uint32_t)j & lm) != lv)) continue;
+      if (op == 0) {
+        v[u][j] = w;
+      } else if (op == 1) {
+        v[u][j] = hi ? mk<T>((w.x - v[u][j].x) * h, (w.y - v[u][j].y) * h)
+                     : mk<T>((v[u][j].x + w.x) * h, (v[u][j].y + w.y) * h);
+      } else {
+        v[u][j] = hi ? mk<T>(s * w.x + c * v[u][j].x, s * w.y + c * v[u][j].y)
+                     : mk<T>(c * v[u][j].x - s * w.x, c * v[u][j].y - s * w.y);
+      }
+    }
+  }
+}
+
 // Apply the tile-local ops of one sweep to U tiles held by the warp.
 template <typename R, int U>
 __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::T (&v)[U][4],
                                           const uint32_t (&ci)[U], uint32_t lane,
                                           const uint32_t (&wd)[kPrefetchMux][U]) {
-  using T = typename V2<R>::T;
   // rotation (cos, sin of half the summed angle) of the latest multiplexer, per tile
   R mc[U], ms[U];
 #pragma unroll
@@ -542,7 +632,7 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
   }
   for (int k = 0; k < a.nops; ++k) {
     const LocalOp& o = a.ops[k];
-    const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv, op = o.op, tg = o.target;
+    const uint32_t ocm = o.cm, lm = o.lm, lv = o.lv, op = o.op, tg = o.target;
     if (op == 4) {  // multiplexed RY on bit tg (0 or 1)
       op_mux<R, U>(a, a.mux[ocm], ocm, v, ci, wd, mc, ms);
       continue;
@@ -551,105 +641,88 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
       op_mux_inverse<R, U>(tg, lm, lv, v, mc, ms);
       continue;
     }
-    if (op == 8) {  // H on each lane bit of the mask: butterflies, then one scale
-#pragma unroll
-      for (int b = 0; b < 5; ++b) {
-        if (!((ocm >> b) & 1u)) continue;
-        const R sg = ((lane >> b) & 1u) ? (R)-1 : (R)1;
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const T w = shfl_xor_c(v[u][j], 1 << b);
-            v[u][j] = mk<T>(fma(v[u][j].x, sg, w.x), fma(v[u][j].y, sg, w.y));
-          }
-      }
-      const R sc = Coef<R>::c(o);
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[u][j] = mk<T>(v[u][j].x * sc, v[u][j].y * sc);
-      continue;
-    }
     if (op == 5) {  // I (x) A + J (x) B over the lane bits of lanemask
       op_refl<R, U>(a.refl[ocm], v, lane);
       continue;
     }
-    const R c = Coef<R>::c(o), s = Coef<R>::s(o);
-    if (op == 6) {  // e^{i phi Z} on chunk-index bit tg (a qubit above the tile)
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if ((ci[u] & ocm) != ocv) continue;
-        const R sg = ((ci[u] >> tg) & 1u) ? -s : s;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (((uint32_t)j & lm) == lv)
-            v[u][j] = mk<T>(v[u][j].x * c - v[u][j].y * sg, v[u][j].x * sg + v[u][j].y * c);
-      }
-      continue;
-    }
-    if (tg < 2) {
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if ((ci[u] & ocm) != ocv) continue;
-        if (tg == 0) {
-          if ((0u & lm) == lv) apply_pair<R>(v[u][0], v[u][1], op, c, s);
-          if ((2u & lm) == lv) apply_pair<R>(v[u][2], v[u][3], op, c, s);
-        } else {
-          if ((0u & lm) == lv) apply_pair<R>(v[u][0], v[u][2], op, c, s);
-          if ((1u & lm) == lv) apply_pair<R>(v[u][1], v[u][3], op, c, s);
-        }
-      }
-      continue;
-    }
-    const int lmask = 1 << (tg - 2);
-    const bool hi = (lane & (uint32_t)lmask) != 0;
-    const R h = (R)0.70710678118654752440;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const bool cok = (ci[u] & ocm) == ocv;
-      if (op == 3) {  // diagonal: no partner needed
-        if (!cok) continue;
-        const R sg = hi ? -s : s;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (((uint32_t)j & lm) == lv)
-            v[u][j] = mk<T>(v[u][j].x * c - v[u][j].y * sg, v[u][j].x * sg + v[u][j].y * c);
-        continue;
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const T w = shfl_xor_c(v[u][j], lmask);
-        if (!cok || (((uint32_t)j & lm) != lv)) continue;
-        if (op == 0) {
-          v[u][j] = w;
-        } else if (op == 1) {
-          v[u][j] = hi ? mk<T>((w.x - v[u][j].x) * h, (w.y - v[u][j].y) * h)
-                       : mk<T>((v[u][j].x + w.x) * h, (v[u][j].y + w.y) * h);
-        } else {
-          v[u][j] = hi ? mk<T>(s * w.x + c * v[u][j].x, s * w.y + c * v[u][j].y)
-                       : mk<T>(c * v[u][j].x - s * w.x, c * v[u][j].y - s * w.y);
-        }
-      }
-    }
+    op_tile_gate<R, U>(op, o, v, ci, lane);
   }
 }
 
-// Sweep shapes with a kernel of their own, so that the descriptors sit at
-// fixed parameter offsets and no op list is interpreted: 1 = one averaging
-// block; 2 = multiplexer, averaging block, inverse multiplexer.  0 = any op
-// list (apply_ops).
+// Sweep shapes with a kernel of their own: the op list is fixed at compile
+// time, so the descriptors sit at fixed parameter offsets and no op list is
+// interpreted.  Shape 0 is any op list (apply_ops).  The op codes are those of
+// LocalOp::op; the k-th multiplexer (averaging block) of a list uses mux[k]
+// (refl[k]), as the fuser assigns them.
+struct ShapeAvg {  // 1: one averaging block (the conjugated sweeps)
+  static constexpr int n = 1;
+  static constexpr int op[1] = {5};
+};
+struct ShapeMux {  // 2: multiplexer, averaging block, inverse multiplexer
+  static constexpr int n = 3;
+  static constexpr int op[3] = {4, 5, 7};
+};
+struct ShapeFirst {  // 3: the first QSVT sweep: H, X, ZPHASE, X, X in-thread, W-H, multiplexer
+  static constexpr int n = 7;
+  static constexpr int op[7] = {1, 0, 3, 0, 0, 8, 4};
+};
+struct ShapeLast {  // 4: the last sweep: W-H, X, ZPHASE, X, H
+  static constexpr int n = 5;
+  static constexpr int op[5] = {8, 0, 3, 0, 1};
+};
+
+template <typename S>
+__host__ __device__ constexpr int count_before(int i, int code) {
+  int c = 0;
+  for (int j = 0; j < i; ++j) c += S::op[j] == code ? 1 : 0;
+  return c;
+}
+
+template <typename R, int U, typename S, int I>
+__device__ __forceinline__ void shaped_step(const SweepParams& a, typename V2<R>::T (&v)[U][4],
+                                            const uint32_t (&ci)[U], uint32_t lane,
+                                            const uint32_t (&wd)[kPrefetchMux][U], R (&mc)[U],
+                                            R (&ms)[U]) {
+  constexpr int code = S::op[I];
+  if constexpr (code == 4) {
+    constexpr int m = count_before<S>(I, 4);
+    op_mux<R, U>(a, a.mux[m], (uint32_t)m, v, ci, wd, mc, ms);
+  } else if constexpr (code == 5) {
+    constexpr int r = count_before<S>(I, 5);
+    op_refl<R, U>(a.refl[r], v, lane);
+  } else if constexpr (code == 7) {
+    op_mux_inverse<R, U>(a.ops[I].target, a.ops[I].lm, a.ops[I].lv, v, mc, ms);
+  } else {
+    op_tile_gate<R, U>((uint32_t)code, a.ops[I], v, ci, lane);
+  }
+}
+
+template <typename R, int U, typename S, int... I>
+__device__ __forceinline__ void apply_seq(std::integer_sequence<int, I...>, const SweepParams& a,
+                                          typename V2<R>::T (&v)[U][4], const uint32_t (&ci)[U],
+                                          uint32_t lane, const uint32_t (&wd)[kPrefetchMux][U]) {
+  R mc[U], ms[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    mc[u] = (R)1;
+    ms[u] = (R)0;
+  }
+  (shaped_step<R, U, S, I>(a, v, ci, lane, wd, mc, ms), ...);
+}
+
 template <typename R, int U, int SHAPE>
 __device__ __forceinline__ void apply_shaped(const SweepParams& a, typename V2<R>::T (&v)[U][4],
                                              const uint32_t (&ci)[U], uint32_t lane,
                                              const uint32_t (&wd)[kPrefetchMux][U]) {
   if constexpr (SHAPE == 1) {
-    op_refl<R, U>(a.refl[0], v, lane);
+    apply_seq<R, U, ShapeAvg>(std::make_integer_sequence<int, ShapeAvg::n>{}, a, v, ci, lane, wd);
   } else if constexpr (SHAPE == 2) {
-    R mc[U], ms[U];
-    op_mux<R, U>(a, a.mux[0], 0u, v, ci, wd, mc, ms);
-    op_refl<R, U>(a.refl[0], v, lane);
-    op_mux_inverse<R, U>(a.ops[2].target, a.ops[2].lm, a.ops[2].lv, v, mc, ms);
+    apply_seq<R, U, ShapeMux>(std::make_integer_sequence<int, ShapeMux::n>{}, a, v, ci, lane, wd);
+  } else if constexpr (SHAPE == 3) {
+    apply_seq<R, U, ShapeFirst>(std::make_integer_sequence<int, ShapeFirst::n>{}, a, v, ci, lane,
+                                wd);
+  } else if constexpr (SHAPE == 4) {
+    apply_seq<R, U, ShapeLast>(std::make_integer_sequence<int, ShapeLast::n>{}, a, v, ci, lane, wd);
   } else {
     apply_ops<R, U>(a, v, ci, lane, wd);
   }
@@ -1066,11 +1139,23 @@ void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepParam
 }
 
 // The sweep shape of a parameter block (see apply_shaped).
+template <typename S>
+bool has_ops(const SweepParams& a) {
+  if (a.nops != S::n) return false;
+  int nm = 0, nr = 0;
+  for (int i = 0; i < S::n; ++i) {
+    const LocalOp& o = a.ops[i];
+    if ((int)o.op != S::op[i]) return false;
+    if (o.op == 4 && (int)o.cm != nm++) return false;
+    if (o.op == 5 && (int)o.cm != nr++) return false;
+  }
+  return true;
+}
 int sweep_shape(const SweepParams& a) {
-  if (a.nops == 1 && a.ops[0].op == 5 && a.ops[0].cm == 0) return 1;
-  if (a.nops == 3 && a.ops[0].op == 4 && a.ops[0].cm == 0 && a.ops[1].op == 5 &&
-      a.ops[1].cm == 0 && a.ops[2].op == 7)
-    return 2;
+  if (has_ops<ShapeAvg>(a)) return 1;
+  if (has_ops<ShapeMux>(a)) return 2;
+  if (has_ops<ShapeFirst>(a)) return 3;
+  if (has_ops<ShapeLast>(a)) return 4;
   return 0;
 }
 
@@ -1090,6 +1175,8 @@ void launch_shaped(const void* in, void* out, uint32_t ntiles, const SweepParams
   const int shape = shapes_enabled() ? sweep_shape(a) : 0;
   if (shape == 1) return launch_sweep_t<R, U, MINB, 1>(in, out, ntiles, a, st);
   if (shape == 2) return launch_sweep_t<R, U, MINB, 2>(in, out, ntiles, a, st);
+  if (shape == 3) return launch_sweep_t<R, U, MINB, 3>(in, out, ntiles, a, st);
+  if (shape == 4) return launch_sweep_t<R, U, MINB, 4>(in, out, ntiles, a, st);
   return launch_sweep_t<R, U, MINB, 0>(in, out, ntiles, a, st);
 }
 
@@ -1173,9 +1260,13 @@ cudaError_t warm_r() {
   if constexpr (sizeof(R) == 4) {
     chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 2, 4, 1>));
     chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 2, 4, 2>));
+    chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 2, 4, 3>));
+    chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 2, 4, 4>));
   } else {
     chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 1, 2, 1>));
     chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 1, 2, 2>));
+    chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 1, 2, 3>));
+    chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 1, 2, 4>));
   }
   sweep_resident<R, 1, 1>();
   sweep_resident<R, 2, 1>();
