@@ -81,9 +81,8 @@ MICRO = {
 # keyed by the sha256 of kernels.cu at capture time (profiles/ has the summary).
 # A changed kernel source reports null traffic until it is captured again.
 NCU_TRAFFIC = {
-    # mean of an averaging sweep and a multiplexer sweep (the 4th and 5th launches)
-    ("bd3d5cbed9d01dd3", "precision-nx64-k4-nt16-d13-c64"): 0.5 * ((44.18e9 + 34.37e9) +
-                                                                   (58.99e9 + 34.35e9)),
+    # mean over the 14 sweep launches of one run (single-pass ncu capture)
+    ("1ca175ac005804a1", "precision-nx64-k4-nt16-d13-c64"): 72.99e9,
 }
 
 L2_BYTES = 129 * 1000 * 1000
