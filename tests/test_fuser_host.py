@@ -113,6 +113,33 @@ def test_lane_walsh_hadamard_fused():
     assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-14
 
 
+def test_conjugated_sweep_random_permutation():
+    """A run of multi-controlled X gates, tile-local gates, then the same X gates
+    in reverse: one in-place conjugated sweep, P^-1 . ops . P, then the local
+    gates that follow need no gather.  Every X gate is controlled by lane bit 2,
+    on which the local run has an H, so no X gate commutes across it (as in
+    the QSVT circuit, where U_L's permutation reads the label).  Against the
+    dense simulator."""
+    n = 14
+    rng = np.random.default_rng(21)
+    perm = []
+    for _ in range(40):
+        t = int(rng.integers(7, n))  # above the tile: a permutation gate, never tile-local
+        others = [b for b in range(3, n) if b != t]
+        cs = list(rng.choice(others, int(rng.integers(0, 4)), replace=False)) + [2]
+        cm = sum(1 << int(c) for c in cs)
+        cv = sum(int(rng.integers(2)) << int(c) for c in cs)
+        perm.append((0, t, cm, cv, 0.0, 0))
+    local = [(1, 2, 0, 0, 0.0, 0)] + random_gates(n, 30, 22, ops=(1, 2, 3), maxc=3,
+                                                   targets=list(range(7)))
+    after = random_gates(n, 30, 23, ops=(1, 2, 3), maxc=3, targets=list(range(7)))
+    g = perm + local + perm[::-1] + after
+    psi = I.random_unit_state(n, 9)
+    got, st = N.emulate_fused(g, n, psi)
+    assert st["conjugated"] == 1
+    assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-13
+
+
 def test_averaging_block_detection_general():
     """H layer on lane bits, tile-internal diagonal/controlled gates, H layer: one block."""
     n = 12
