@@ -175,7 +175,7 @@ csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_
 /* Copy the whole state to the host as interleaved doubles (2 * 2^n values). */
 csim_status csim_read_state(csim_circuit* c, double* out, size_t cap_amps);
 
-/* Checkpointed runs, for circuits of large degree (Sec. III.F: d ~ 7e4 calls).
+/* Checkpointed runs, for circuits of large degree (Sec. III.E.2: d ~ 7e4 calls).
  * The QSVT circuit is executed as a fixed sequence of program steps (fused
  * sweeps or single gates; csim_info().n_sweeps_run of them).
  *   csim_run_steps: after csim_init or csim_restore, enqueue the next n_steps
