@@ -10,16 +10,22 @@
 //   init_scatter_kernel  -- zero state + scatter the normalised right-hand side b
 //   gate_kernel          -- one elementary gate over the 2^{n-1-c} matching pairs
 //   sweep_kernel         -- one fused HBM pass: gather through an index
-//                           permutation (a run of multi-controlled X gates),
-//                           then a list of gates acting inside the warp tile
-//                           (in-register for bits 0-1, warp shuffles for 2-6)
+//                           permutation (a run of multi-controlled X gates; its
+//                           precomputed source index, or its lookup-table
+//                           chain), then a list of ops acting inside the warp
+//                           tile (in-register for bits 0-1, warp shuffles for
+//                           2-6), stored contiguously or back to the gathered
+//                           addresses (conjugated, in place).  Specialised on
+//                           the op list (SHAPE) for the QSVT circuit's sweeps.
+//   perm_index_kernel    -- the source-index table of a permutation chain
 //   norm_kernel          -- FP64 sum |a|^2 (total and under a pattern mask)
 //   compact_kernel       -- gather the postselected block
 #include <cuda_runtime.h>
 
-#include <utility>
-
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <utility>
 #include <cstdio>
 #include <cstdlib>
 
