@@ -172,6 +172,19 @@ csim_status csim_sync(csim_circuit* c);
 csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_t* len,
                             double* p_success, double* norm_total);
 
+/* The final-time distribution f(T)[alpha][q] (alpha = 0..Nx-1, q in the order
+ * e = +1, -1, 0), read from the compacted block that csim_postselect returned
+ * (amps: len complex amplitudes, interleaved).  It is the f^(1) part (ord = 0,
+ * second site and velocity 0 at N_C = 2) of the first postselected slot
+ * (m = Nt, k = 0; Sec. II.D.4), rescaled to physical units: the block
+ * approximates poly_scale * lambda_L * L^{-1} b with b = v0 / |v0| and v0 the
+ * Carleman vector of f0 (Sec. II.D.5), so f(T) = Re(block) |v0| /
+ * (poly_scale lambda_L).  f0 is the initial distribution passed to csim_init
+ * (3 Nx doubles); f_out receives 3 Nx doubles.  Host arithmetic only.
+ * CSIM_ERR_ARG for a short block or a zero f0. */
+csim_status csim_final_distribution(const csim_circuit* c, const double* f0, const double* amps,
+                                    size_t len, double* f_out);
+
 /* Copy the whole state to the host as interleaved doubles (2 * 2^n values). */
 csim_status csim_read_state(csim_circuit* c, double* out, size_t cap_amps);
 

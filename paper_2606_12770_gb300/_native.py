@@ -32,6 +32,7 @@ EXPORTED = [
     "csim_sv_load_device", "csim_sv_device", "csim_sv_stats", "csim_pool_create",
     "csim_pool_submit", "csim_pool_poll", "csim_pool_result", "csim_pool_stats", "csim_pool_free",
     "csim_pool_plan", "csim_compile", "csim_run_steps", "csim_checkpoint", "csim_restore",
+    "csim_final_distribution",
 ]
 
 
@@ -94,6 +95,8 @@ def load():
         "csim_set_exec": ([VP, C.c_int], C.c_int),
         "csim_compile": ([VP], C.c_int),
         "csim_run_steps": ([VP, C.c_int64, P(C.c_int64)], C.c_int),
+        "csim_final_distribution": ([VP, P(C.c_double), P(C.c_double), C.c_size_t,
+                                     P(C.c_double)], C.c_int),
         "csim_checkpoint": ([VP, DP, SZ, P(C.c_int64)], C.c_int),
         "csim_restore": ([VP, DP, SZ, C.c_int, C.c_int64, VP], C.c_int),
         "csim_run": ([VP], C.c_int),
@@ -252,6 +255,15 @@ class Circuit:
         pr = C.c_int()
         _check(_lib.csim_state_device(self._h, C.byref(p), C.byref(n), C.byref(pr)))
         return DeviceState(p.value, n.value, pr.value, self)
+
+    def final_distribution(self, f0, amps) -> np.ndarray:
+        """f(T) as an (Nx, 3) array from the compacted block of postselect()
+        (complex amplitudes) and the f0 given to init (csim_final_distribution)."""
+        f = np.ascontiguousarray(np.asarray(f0, dtype=np.float64).reshape(-1))
+        a = np.ascontiguousarray(np.asarray(amps, dtype=np.complex128)).view(np.float64)
+        out = np.zeros(f.shape[0], dtype=np.float64)
+        _check(_lib.csim_final_distribution(self._h, _dp(f), _dp(a), a.shape[0] // 2, _dp(out)))
+        return out.reshape(-1, 3)
 
     def postselect_count(self) -> int:
         """Number of amplitudes in the compacted postselected block."""

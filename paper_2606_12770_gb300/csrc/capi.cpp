@@ -565,6 +565,31 @@ csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_
   return CSIM_OK;
 }
 
+csim_status csim_final_distribution(const csim_circuit* c, const double* f0, const double* amps,
+                                    size_t len, double* f_out) {
+  if (!c || !f0 || !amps || !f_out) return fail(CSIM_ERR_ARG, "null argument");
+  const Layout& L = c->L;
+  const csim::CompactGeom g = csim::compact_geom(c);
+  if (len < g.count) return fail(CSIM_ERR_ARG, "amps is shorter than the postselected block");
+  // |v0|: the norm of the Carleman vector (f0, f0 (x) f0) that csim_init normalised
+  double nrm2 = 0.0, n1 = 0.0;
+  for (int i = 0; i < L.Nx * 3; ++i) n1 += f0[i] * f0[i];
+  nrm2 = n1;
+  if (L.NC == 2) nrm2 += n1 * n1;  // |f0 (x) f0|^2 = |f0|^4
+  if (!(nrm2 > 0) || !std::isfinite(nrm2)) return fail(CSIM_ERR_ARG, "f0 is zero or not finite");
+  const double factor = std::sqrt(nrm2) / (c->scale * c->lambda);
+  const uint64_t fmask = ((uint64_t)1 << g.free_bits) - 1u;
+  for (int a = 0; a < L.Nx; ++a)
+    for (int q = 0; q < 3; ++q) {
+      const uint64_t I = csim::place_bits(L.m, (uint64_t)L.Nt) | csim::place_bits(L.a1, (uint64_t)a) |
+                         csim::place_bits(L.q1, (uint64_t)q);
+      const uint64_t pos = (((I >> g.m_shift) - (uint64_t)L.Nt) << g.free_bits) |
+                           ((I >> g.free_shift) & fmask);
+      f_out[a * 3 + q] = amps[2 * pos] * factor;
+    }
+  return CSIM_OK;
+}
+
 csim_status csim_state_device(const csim_circuit* c, void** d_state, int32_t* n,
                               csim_precision* prec) {
   if (!c || !d_state) return fail(CSIM_ERR_ARG, "null argument");

@@ -120,3 +120,27 @@ def test_amp_update_count():
     g = c.export_gates(1)
     expect = sum(2.0 ** (n - bin(int(x)).count("1")) for x in g["cmask"])
     assert c.info()["amp_updates_run"] == expect
+
+
+def test_final_distribution_matches_oracle():
+    """csim_final_distribution reads f(T) from a postselected block and rescales
+    it to physical units.  The block here is the oracle's own (O5, the exact
+    target polynomial) laid out as csim_postselect compacts it; the densities
+    must equal the oracle's, whose rescaling uses the oracle's own scale and
+    lambda_L (Sec. II.D.5)."""
+    import paper_claims as PC
+    kq, d = 1200.0, 1201
+    c = G.Circuit(*PC.cfg(PC.K3), kappa_qsvt=kq, d=d, bc="bounceback")
+    rho_q, _, y, lay, _, _, _ = PC.oracle_run(PC.K3, kq, d)
+    final = PC.Q.final_slot_mask(lay)
+    sel = lay.physical_indices()[final]
+    fs, ms = 2 + lay.niL, lay.regs["m"][0]
+    pos = ((sel >> ms) - lay.Nt) * (1 << (ms - fs)) + ((sel >> fs) & ((1 << (ms - fs)) - 1))
+    amps = np.zeros(c.postselect_count(), dtype=complex)
+    amps[pos] = y[final]
+    f = c.final_distribution(PC.f0(), amps)
+    assert f.shape == (PC.NX, 3)
+    rho = f.sum(axis=1)
+    assert np.max(np.abs(rho - rho_q)) < 1e-8 * np.max(np.abs(rho_q))
+    with pytest.raises(G.CsimError):
+        c.final_distribution(PC.f0(), amps[:-1])

@@ -40,7 +40,7 @@ def _gpu_run(kdn, kq, d):
     c.run()
     amps, p, tot = c.postselect()
     assert abs(tot - 1.0) < 1e-9
-    return amps, inf
+    return amps, inf, c
 
 
 _cache = {}
@@ -49,7 +49,7 @@ _cache = {}
 def _run(name):
     if name not in _cache:
         kdn, kq, d = RUNS[name]
-        amps, inf = _gpu_run(kdn, kq, d)
+        amps, inf, c = _gpu_run(kdn, kq, d)
         rho_q, rho_x, y, lay, scale, lam, nv = PC.oracle_run(kdn, kq, d)
         got = PC.compacted_rows(amps, lay)
         final = PC.Q.final_slot_mask(lay)
@@ -62,6 +62,9 @@ def _run(name):
         full = np.zeros(y.shape[0], dtype=complex)
         full[final] = got
         rho_g = PC.first_final_density(full, lay) / (scale * lam) * nv
+        # the library's own extraction (csim_final_distribution) agrees
+        rho_lib = c.final_distribution(PC.f0(), amps).sum(axis=1)
+        assert np.max(np.abs(rho_lib - rho_g)) < 1e-8 * np.max(np.abs(rho_g))
         _cache[name] = (err, bound, rho_g, rho_x)
         print(f"{name}: GPU vs O5 rel L2 {err:.3e} (bound {bound:.2e}); L-inf vs Taylor {PC.linf(rho_g, rho_x):.3e}; "
               f"amplitude ratio {PC.amplitude_ratio(rho_g, rho_x):.3f}")
