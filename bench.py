@@ -682,12 +682,13 @@ def main():
     e2e_ms = []
     h2d = 0
     d2h = 0
+    pinned = torch.empty(2 * circ.postselect_count(), dtype=torch.float64, pin_memory=True)
     for s in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         circ.init(f0, precision, stream)
         circ.run()
-        amps, p, tot = circ.postselect(want_amplitudes=True)
+        amps, p, tot = circ.postselect(want_amplitudes=True, out=pinned.numpy())
         torch.cuda.synchronize()
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
         nnz = 3 * Nx + (9 * Nx * Nx if NC == 2 else 0)

@@ -235,18 +235,25 @@ class Circuit:
     def sync(self):
         _check(_lib.csim_sync(self._h))
 
-    def postselect(self, want_amplitudes=True):
-        """Return (amplitudes or None, p_success, norm_total)."""
+    def postselect(self, want_amplitudes=True, out=None):
+        """Return (amplitudes or None, p_success, norm_total).
+
+        out (optional): a caller-owned float64 array of at least
+        2 * postselect_count() values (for example a view of pinned memory),
+        which receives the block; otherwise a new array is allocated."""
         n = C.c_size_t()
         p = C.c_double()
         t = C.c_double()
         if not want_amplitudes:
             _check(_lib.csim_postselect(self._h, None, 0, C.byref(n), C.byref(p), C.byref(t)))
             return None, p.value, t.value
-        _check(_lib.csim_postselect(self._h, None, 0, C.byref(n), C.byref(p), C.byref(t)))
-        out = np.zeros(2 * n.value)
-        _check(_lib.csim_postselect(self._h, _dp(out), n.value, C.byref(n), C.byref(p), C.byref(t)))
-        return out.view(np.complex128), p.value, t.value
+        count = self.postselect_count()
+        if out is None:
+            out = np.zeros(2 * count)
+        elif out.dtype != np.float64 or not out.flags.c_contiguous or out.size < 2 * count:
+            raise ValueError("out must be a contiguous float64 array of 2 * postselect_count() values")
+        _check(_lib.csim_postselect(self._h, _dp(out), count, C.byref(n), C.byref(p), C.byref(t)))
+        return out[:2 * count].view(np.complex128), p.value, t.value
 
     def device_state(self):
         """Borrowed view of the current device state (see DeviceState)."""
