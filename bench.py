@@ -698,7 +698,10 @@ def main():
 
     peaks, peak_kind = measured_peaks()
     sweep_ms = statistics.mean(run_ms) / passes
-    alg_bytes = 2.0 * (1 << n) * esz
+    # every sweep reads and writes the state once, except the first after a
+    # sparse init, which writes it and reads only the tiles of b
+    sparse = bool(info["sparse_init"])
+    alg_bytes = (2.0 * passes - (1.0 if sparse else 0.0)) * (1 << n) * esz / passes
     achieved = alg_bytes / (sweep_ms / 1000.0) / 1e9
     khash = kernel_hash()
     traffic = NCU_TRAFFIC.get((khash, args.workload))
@@ -714,6 +717,8 @@ def main():
                    "gather": (f"source-index tables ({info['n_src_tables']} x {(1 << n) / 1e9:.2f} GB)"
                               if info["n_src_tables"] else "lookup-table chain"),
                    "state_bytes": (1 << n) * esz,
+                   "init": ("tiles of b only; the first sweep reads zeros for the rest" if sparse
+                            else "whole state zero-filled"),
                    "l2": (f"inputs larger than L2 (state {((1 << n) * esz) / 1e6:.0f} MB, two "
                           f"ping-pong buffers {2 * ((1 << n) * esz) / 1e6:.0f} MB; L2 129 MB)"
                           if ((1 << n) * esz) > L2_BYTES
@@ -725,13 +730,13 @@ def main():
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": sweep_ms,
                      "launches_per_step": passes},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (passes + 1 + 2),
+        "gpu_launches": args.steps * (passes + (3 if sparse else 1) + 2),
         "clocks": clk,
         "host_wall_s": t_host,
     }
     if prec == "c128":
         # measured on the 28-qubit complex128 profile workload with ncu
-        line["roofline"]["note"] = ("complex128 sweeps are bound by the FP64 pipe (86-87% of its "
+        line["roofline"]["note"] = ("complex128 sweeps are bound by the FP64 pipe (83-86% of its "
                                     "cycles busy), not by HBM; see the fp64 sweep profile")
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(seconds_target=12.0)

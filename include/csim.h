@@ -101,12 +101,15 @@ typedef struct {
   int64_t n_gates_UL;     /* gates of one U_L */
   int64_t n_gates_total;  /* gates of the whole QSVT circuit */
   int64_t n_sweeps_run;   /* fused sweeps (HBM passes) per csim_run = program steps;
-                             0 until the first csim_run / csim_run_steps fuses
-                             the program (csim_run_steps(c, 0, ...) fuses only) */
+                             0 until csim_init (fused mode), csim_run or
+                             csim_run_steps fuses the program
+                             (csim_run_steps(c, 0, ...) fuses only) */
   double amp_updates_run; /* sum over gates of amplitudes the gate changes */
   uint64_t state_bytes;   /* bytes of the current state (0 before csim_init) */
   int32_t n_src_tables;   /* source-index tables the gather sweeps load (2^n bytes
                              each; 0: the sweeps walk the lookup-table chain) */
+  int32_t sparse_init;    /* 1: the last csim_init wrote the tiles of b only and
+                             left the zeros to the first sweep (csim_init) */
 } csim_info_t;
 
 /* --- building (host only; no GPU needed) -------------------------------- */
@@ -147,8 +150,17 @@ csim_status csim_export_mask(const csim_circuit* c, uint64_t* masks, uint64_t* v
  * CUDA device and load b: f0 is [Nx][3] doubles in the paper's velocity order
  * (e = +1, -1, 0); the Carleman vector (f0, f0 (x) f0) is normalised and
  * placed in slot (m, k) = (0, 0) with all ancillas 0 (Sec. II.D.5).  A second
- * call reuses the allocation when the precision is unchanged.  Errors:
- * CSIM_ERR_OOM (nothing kept), CSIM_ERR_CUDA. */
+ * call reuses the allocation when the precision is unchanged.
+ * In the fused mode at n >= 12, when the program's first step is an in-place
+ * sweep (the circuit's opening Walsh-Hadamard and multiplexer), csim_init
+ * fuses the program, writes only the 128-amplitude tiles that hold b and
+ * marks them in a 2^(n-12)-word bitmap; the first sweep reads zeros for the
+ * unmarked tiles instead of a zero-filled state (csim_info().sparse_init = 1;
+ * CSIM_SPARSE_INIT=0 in the environment always writes the whole state).
+ * Every call that reads the state before that sweep (csim_read_state,
+ * csim_checkpoint, csim_state_device, csim_postselect) writes it whole first,
+ * so the difference is not observable.  Errors: CSIM_ERR_OOM (nothing kept),
+ * CSIM_ERR_CUDA. */
 csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec,
                       void* cuda_stream);
 

@@ -68,7 +68,7 @@ class Info(C.Structure):
                 ("poly_scale", C.c_double), ("n_gates_UL", C.c_int64),
                 ("n_gates_total", C.c_int64), ("n_sweeps_run", C.c_int64),
                 ("amp_updates_run", C.c_double), ("state_bytes", C.c_uint64),
-                ("n_src_tables", C.c_int32)]
+                ("n_src_tables", C.c_int32), ("sparse_init", C.c_int32)]
 
 
 _lib = None

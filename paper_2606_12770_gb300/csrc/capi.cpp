@@ -43,11 +43,75 @@ void record_last_error(const std::string& msg) { g_err = msg; }
 
 namespace {
 
+// Sparse csim_init when the first sweep can read zeros itself
+// (CSIM_SPARSE_INIT=0 always writes the whole state).
+bool sparse_init_enabled() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_SPARSE_INIT");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+
+// Upload b (idx, val) and write the state: the whole state (memset and
+// scatter), or with map the tiles of b only (launch_init_sparse).
+cudaError_t write_initial_state(csim_circuit* c, const std::vector<uint64_t>& idx,
+                                const std::vector<double>& val, uint32_t* map) {
+  uint64_t* d_idx = nullptr;
+  double* d_val = nullptr;
+  cudaError_t e = cudaMallocAsync(&d_idx, idx.size() * sizeof(uint64_t), c->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_val, val.size() * sizeof(double), c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_idx, idx.data(), idx.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_val, val.data(), val.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream);
+  c->cur = 0;
+  if (e == cudaSuccess)
+    e = map ? csim::launch_init_sparse(c->buf[0], c->prec, c->L.n, d_idx, d_val,
+                                       (int64_t)idx.size(), map, c->stream)
+            : csim::launch_init(c->buf[0], c->prec, (uint64_t)1 << c->L.n, d_idx, d_val,
+                                (int64_t)idx.size(), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (d_idx) cudaFreeAsync(d_idx, c->stream);
+  if (d_val) cudaFreeAsync(d_val, c->stream);
+  return e;
+}
+
+// Before the state is read (or handed out) ahead of the first sweep of a
+// sparse init: write it whole.
+cudaError_t materialize(csim_circuit* c) {
+  if (!c->zero_fill) return cudaSuccess;
+  c->zero_fill = false;
+  return write_initial_state(c, c->b_idx, c->b_val, nullptr);
+}
+
+// The zero map for the run's next step: that of a sparse init while the
+// program still starts with a sweep whose kernel reads it.  Otherwise (the
+// execution mode changed since csim_init, say) the state is written whole.
+cudaError_t zero_map_for_run(csim_circuit* c, const uint32_t** zmap) {
+  *zmap = nullptr;
+  if (!c->zero_fill) return cudaSuccess;
+  if (c->next_step == 0 && c->prog.mode == CSIM_EXEC_FUSED && !c->prog.steps.empty()) {
+    const csim::Step& s0 = c->prog.steps[0];
+    if (s0.kind == 0 && !s0.gather &&
+        csim::sweep_takes_zero_map(c->prec, c->L.n, c->prog.params[(size_t)s0.param])) {
+      *zmap = c->d_zmap;
+      return cudaSuccess;
+    }
+  }
+  return materialize(c);
+}
+
 void free_device(csim_circuit* c) {
   for (void*& b : c->buf) {
     if (b) cudaFree(b);
     b = nullptr;
   }
+  if (c->d_zmap) cudaFree(c->d_zmap);
+  c->d_zmap = nullptr;
+  c->zero_fill = false;
   if (c->d_pat) cudaFree(c->d_pat);
   if (c->d_partial) cudaFree(c->d_partial);
   if (c->d_out) cudaFree(c->d_out);
@@ -317,6 +381,7 @@ csim_status csim_info(const csim_circuit* c, csim_info_t* out) {
   out->n_sweeps_run = c->prog_built ? c->prog.passes : 0;
   out->state_bytes = c->bytes;
   out->n_src_tables = (int32_t)c->prog.d_src.size();
+  out->sparse_init = c->sparse_init ? 1 : 0;
   return CSIM_OK;
 }
 
@@ -378,24 +443,33 @@ csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec, vo
     const csim_status st = alloc_state(c, prec);
     if (st != CSIM_OK) return st;
   }
-  uint64_t* d_idx = nullptr;
-  double* d_val = nullptr;
-  cudaError_t e = cudaMallocAsync(&d_idx, idx.size() * sizeof(uint64_t), c->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync(&d_val, val.size() * sizeof(double), c->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_idx, idx.data(), idx.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
-                        c->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_val, val.data(), val.size() * sizeof(double), cudaMemcpyHostToDevice,
-                        c->stream);
-  c->cur = 0;
-  if (e == cudaSuccess)
-    e = csim::launch_init(c->buf[0], prec, (uint64_t)1 << L.n, d_idx, d_val, (int64_t)idx.size(),
-                          c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (d_idx) cudaFreeAsync(d_idx, c->stream);
-  if (d_val) cudaFreeAsync(d_val, c->stream);
+  // sparse when the program's first step is an in-place sweep whose kernel
+  // reads zeros for the tiles that b does not touch
+  bool sparse = false;
+  if (sparse_init_enabled() && c->exec == CSIM_EXEC_FUSED && L.n >= 12) {
+    std::string err;
+    if (csim::ensure_program(c, c->stream, &err) && !c->prog.steps.empty()) {
+      const csim::Step& s0 = c->prog.steps[0];
+      sparse = s0.kind == 0 && !s0.gather &&
+               csim::sweep_takes_zero_map(prec, L.n, c->prog.params[(size_t)s0.param]);
+    }
+    if (sparse && !c->d_zmap) {
+      if (cudaMalloc(&c->d_zmap, ((size_t)1 << (L.n - 12)) * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_zmap = nullptr;
+        sparse = false;
+      }
+    }
+  }
+  c->zero_fill = false;
+  const cudaError_t e = write_initial_state(c, idx, val, sparse ? c->d_zmap : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "csim_init");
+  c->zero_fill = sparse;
+  c->sparse_init = sparse;
+  if (sparse) {
+    c->b_idx = std::move(idx);
+    c->b_val = std::move(val);
+  }
   c->loaded = true;
   c->ran = false;
   c->next_step = 0;
@@ -430,8 +504,12 @@ csim_status csim_run(csim_circuit* c) {
   }
   cudaError_t e = csim::build_src_index(&c->prog, c->stream, kSrcIndexTables);
   if (e != cudaSuccess) return cuda_fail(e, "csim_run: source index");
-  e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream,
-                                          c->next_step, (int64_t)c->prog.steps.size());
+  const uint32_t* zmap = nullptr;
+  e = zero_map_for_run(c, &zmap);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_run: initial state");
+  e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream, c->next_step,
+                              (int64_t)c->prog.steps.size(), nullptr, zmap);
+  c->zero_fill = false;
   if (e != cudaSuccess) return cuda_fail(e, "csim_run");
   c->next_step = (int64_t)c->prog.steps.size();
   c->loaded = false;
@@ -456,8 +534,14 @@ csim_status csim_run_steps(csim_circuit* c, int64_t n_steps, int64_t* next_step)
   const int64_t last = std::min(total, c->next_step + n_steps);
   cudaError_t e = csim::build_src_index(&c->prog, c->stream, kSrcIndexTables);
   if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps: source index");
-  e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream,
-                                          c->next_step, last);
+  const uint32_t* zmap = nullptr;
+  if (last > c->next_step) {
+    e = zero_map_for_run(c, &zmap);
+    if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps: initial state");
+  }
+  e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream, c->next_step, last,
+                              nullptr, zmap);
+  if (last > c->next_step) c->zero_fill = false;
   if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps");
   c->next_step = last;
   if (last == total) {
@@ -490,6 +574,8 @@ csim_status csim_restore(csim_circuit* c, const double* amps, size_t n_amps, csi
     const csim_status st = alloc_state(c, prec);
     if (st != CSIM_OK) return st;
   }
+  c->zero_fill = false;
+  c->sparse_init = false;
   cudaError_t e;
   c->cur = 0;
   if (prec == CSIM_C128) {
@@ -519,6 +605,10 @@ csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_
                             double* p_success, double* norm_total) {
   if (!c) return fail(CSIM_ERR_ARG, "null argument");
   if (!c->buf[c->cur] || c->prec < 0) return fail(CSIM_ERR_STATE, "no state");
+  {
+    const cudaError_t e0 = materialize(c);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "csim_postselect");
+  }
   const Layout& L = c->L;
   const int npat = (int)c->pm.size();
   std::vector<uint64_t> pat(c->pm);
@@ -594,6 +684,10 @@ csim_status csim_state_device(const csim_circuit* c, void** d_state, int32_t* n,
                               csim_precision* prec) {
   if (!c || !d_state) return fail(CSIM_ERR_ARG, "null argument");
   if (!c->buf[c->cur] || c->prec < 0) return fail(CSIM_ERR_STATE, "no state");
+  {  // the handed-out state must be whole (a sparse init writes it now)
+    const cudaError_t e = materialize(const_cast<csim_circuit*>(c));
+    if (e != cudaSuccess) return cuda_fail(e, "csim_state_device");
+  }
   *d_state = c->buf[c->cur];
   if (n) *n = c->L.n;
   if (prec) *prec = (csim_precision)c->prec;
@@ -605,7 +699,8 @@ csim_status csim_read_state(csim_circuit* c, double* out, size_t cap_amps) {
   if (!c->buf[c->cur] || c->prec < 0) return fail(CSIM_ERR_STATE, "no state");
   const size_t N = (size_t)1 << c->L.n;
   if (cap_amps < N) return fail(CSIM_ERR_ARG, "buffer too small");
-  cudaError_t e;
+  cudaError_t e = materialize(c);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_read_state");
   if (c->prec == CSIM_C128) {
     e = cudaMemcpyAsync(out, c->buf[c->cur], N * 16, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -1232,14 +1232,21 @@ cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cuda
 }
 
 cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
-                              int64_t first, int64_t last, const uint32_t* const* src_tables) {
+                              int64_t first, int64_t last, const uint32_t* const* src_tables,
+                              const uint32_t* zero_map) {
   for (int64_t k = first; k < last; ++k) {
     const Step& s = p.steps[(size_t)k];
     cudaError_t e;
     if (s.kind == 1) {
       e = launch_gate(buf[*cur], prec, p.n, s.g, st);
     } else if (!s.gather) {
-      e = launch_sweep(buf[*cur], buf[*cur], prec, p.n, p.params[s.param], st);
+      if (k == 0 && zero_map) {
+        SweepParams a = p.params[(size_t)s.param];
+        a.zero_map = zero_map;
+        e = launch_sweep(buf[*cur], buf[*cur], prec, p.n, a, st);
+      } else {
+        e = launch_sweep(buf[*cur], buf[*cur], prec, p.n, p.params[s.param], st);
+      }
     } else {
       void* out = s.inplace ? buf[*cur] : buf[1 - *cur];
       if (src_tables && (size_t)s.param < p.src_tab.size() && p.src_tab[(size_t)s.param] >= 0) {

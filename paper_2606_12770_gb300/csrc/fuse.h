@@ -101,10 +101,12 @@ cudaError_t launch_src_tables(const Program& p, uint32_t* const* tables, cudaStr
 // their source indices from those tables instead of the program's own.
 cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
                         const uint32_t* const* src_tables = nullptr);
-// Steps [first, last) of the program only (checkpointed runs).
+// Steps [first, last) of the program only (checkpointed runs).  zero_map
+// (launch_init_sparse) goes to step 0, when it is among them.
 cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
                               int64_t first, int64_t last,
-                              const uint32_t* const* src_tables = nullptr);
+                              const uint32_t* const* src_tables = nullptr,
+                              const uint32_t* zero_map = nullptr);
 // Host executor of a fused program (FP64, kernel semantics) for testing.
 void emulate_program(const Program& p, std::vector<double>* amps);
 

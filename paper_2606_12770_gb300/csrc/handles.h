@@ -26,6 +26,14 @@ struct csim_circuit {
   csim_exec exec = CSIM_EXEC_FUSED;
   bool loaded = false, ran = false;
   int64_t next_step = 0;  // next program step of a run in progress (csim_run_steps)
+  // sparse csim_init: only the tiles of b were written (d_zmap marks them);
+  // the run's first sweep reads zeros for the others.  b_idx / b_val keep b
+  // to write the full state when it is read before that sweep.
+  bool zero_fill = false;
+  bool sparse_init = false;  // the last csim_init was sparse (reported by csim_info)
+  uint32_t* d_zmap = nullptr;
+  std::vector<uint64_t> b_idx;
+  std::vector<double> b_val;
   csim::Program prog;
   bool prog_built = false;
   uint64_t* d_pat = nullptr;  // masks then values

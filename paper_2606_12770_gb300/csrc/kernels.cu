@@ -61,6 +61,28 @@ __global__ void init_scatter_kernel(typename V2<R>::T* state, const uint64_t* id
   if (i < count) state[idx[i]] = mk<typename V2<R>::T>((R)val[i], (R)0);
 }
 
+// Sparse init: mark the tile of every entry, then zero the marked tiles (one
+// warp per entry; tiles shared by several entries are zeroed repeatedly).
+__global__ void mark_tiles_kernel(const uint64_t* __restrict__ idx, int64_t count,
+                                  uint32_t* __restrict__ map) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) {
+    const uint64_t tile = idx[i] >> 7;
+    atomicOr(map + (tile >> 5), 1u << (uint32_t)(tile & 31u));
+  }
+}
+template <typename R>
+__global__ void zero_tiles_kernel(typename V2<R>::T* __restrict__ state,
+                                  const uint64_t* __restrict__ idx, int64_t count) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31u;
+  if (w < count) {
+    typename V2<R>::T* t = state + ((idx[w] >> 7) << 7);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[(lane << 2) + j] = mk<typename V2<R>::T>((R)0, (R)0);
+  }
+}
+
 // ------------------------------------------------------- gate-by-gate path
 struct GateParams {
   uint64_t cmask, cval, tbit;
@@ -836,7 +858,19 @@ __global__ void __launch_bounds__(256, MINB)
         permute<U>(a, mv);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)mv[u] << 2), v[u]);
+      for (int u = 0; u < U; ++u) {
+        if constexpr (SHAPE == 3) {  // in place: mv == ci
+          if (a.zero_map) {
+            const uint32_t tile = ci[u] >> 5;
+            if (!((__ldg(a.zero_map + (tile >> 5)) >> (tile & 31u)) & 1u)) {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) v[u][j] = mk<T>((R)0, (R)0);
+              continue;
+            }
+          }
+        }
+        load_chunk(in + ((size_t)mv[u] << 2), v[u]);
+      }
       apply_shaped<R, U, SHAPE>(a, v, ci, lane, wd);
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -1026,6 +1060,26 @@ cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* 
   if (e != cudaSuccess) return e;
   if (count <= 0) return cudaSuccess;
   const int blk = 256;
+  const int grd = (int)((count + blk - 1) / blk);
+  if (prec == CSIM_C64)
+    init_scatter_kernel<float><<<grd, blk, 0, st>>>((float2*)state, d_idx, d_val, count);
+  else
+    init_scatter_kernel<double><<<grd, blk, 0, st>>>((double2*)state, d_idx, d_val, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_sparse(void* state, int prec, int n, const uint64_t* d_idx,
+                               const double* d_val, int64_t count, uint32_t* map, cudaStream_t st) {
+  if (n < 12) return cudaErrorInvalidValue;  // the map has 2^(n-12) words
+  cudaError_t e = cudaMemsetAsync(map, 0, ((size_t)1 << (n - 12)) * sizeof(uint32_t), st);
+  if (e != cudaSuccess || count <= 0) return e;
+  const int blk = 256;
+  mark_tiles_kernel<<<(int)((count + blk - 1) / blk), blk, 0, st>>>(d_idx, count, map);
+  const int zgrd = (int)((count * 32 + blk - 1) / blk);
+  if (prec == CSIM_C64)
+    zero_tiles_kernel<float><<<zgrd, blk, 0, st>>>((float2*)state, d_idx, count);
+  else
+    zero_tiles_kernel<double><<<zgrd, blk, 0, st>>>((double2*)state, d_idx, count);
   const int grd = (int)((count + blk - 1) / blk);
   if (prec == CSIM_C64)
     init_scatter_kernel<float><<<grd, blk, 0, st>>>((float2*)state, d_idx, d_val, count);
@@ -1232,6 +1286,16 @@ cudaError_t launch_perm_index(uint32_t* src, int n, const SweepParams& a, cudaSt
   return cudaGetLastError();
 }
 
+bool sweep_takes_zero_map(int prec, int n, const SweepParams& a) {
+  // the same choice as launch_sweep: the default variant's ShapeFirst kernel
+  if (n < 12 || !shapes_enabled() || a.scatter || a.nseg != 0 || sweep_shape(a) != 3) return false;
+  const SweepCfg c = sweep_cfg();
+  const uint32_t ntiles = 1u << (n - 7);
+  int u = prec == CSIM_C64 ? c.u64 : c.u128;
+  while ((uint32_t)u > ntiles) u >>= 1;
+  return prec == CSIM_C64 ? (u == 2 && c.minb64 == 4) : (u == 1 && c.minb128 == 2);
+}
+
 int norm_partials_needed() { return 2048; }
 
 namespace {
@@ -1260,6 +1324,7 @@ cudaError_t warm_r() {
     if (e == cudaSuccess) e = x;
   };
   chk(cudaFuncGetAttributes(&fa, init_scatter_kernel<R>));
+  chk(cudaFuncGetAttributes(&fa, zero_tiles_kernel<R>));
   chk(cudaFuncGetAttributes(&fa, gate_kernel<R>));
   chk(cudaFuncGetAttributes(&fa, norm_kernel<R>));
   chk(cudaFuncGetAttributes(&fa, compact_kernel<R>));
@@ -1290,6 +1355,7 @@ cudaError_t warm_kernels() {
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, reduce_partials_kernel);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, perm_index_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mark_tiles_kernel);
   if (e == cudaSuccess) e = warm_r<float>();
   if (e == cudaSuccess) e = warm_r<double>();
   sweep_cfg();

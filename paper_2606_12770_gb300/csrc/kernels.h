@@ -109,10 +109,21 @@ struct SweepParams {
   // segments' permutation: a permutation, tile ops, and the inverse
   // permutation in one pass.
   int inplace;
+  // First sweep after a sparse csim_init (shape ShapeFirst only): tiles whose
+  // bit is clear in zero_map (bit t of word t / 32) hold zeros that were never
+  // written; the kernel uses zeros instead of loading them.
+  const uint32_t* zero_map;
 };
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,
                         const double* d_val, int64_t count, cudaStream_t st);
+// Sparse initialisation for a first sweep that takes a zero map: marks the
+// tiles holding the count entries in map (2^(n-7) bits, cleared here), zeroes
+// those tiles and scatters the entries.  The other tiles are left unwritten.
+cudaError_t launch_init_sparse(void* state, int prec, int n, const uint64_t* d_idx,
+                               const double* d_val, int64_t count, uint32_t* map, cudaStream_t st);
+// Whether launch_sweep runs this sweep with the kernel that honours zero_map.
+bool sweep_takes_zero_map(int prec, int n, const SweepParams& a);
 cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaStream_t st);
 cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
                          cudaStream_t st);

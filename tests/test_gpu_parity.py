@@ -383,3 +383,63 @@ def test_source_index_tables_equal_lookup_chain(tmp_path):
         a, b = res["default"][prec], res["generic"][prec]
         tol = 1e-14 if prec == "c128" else 1e-6
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < tol, prec
+
+
+SPARSE_SCRIPT = r"""
+import sys, numpy as np
+sys.path.insert(0, sys.argv[1])
+import lbm_inputs as I, paper_2606_12770_gb300 as G
+ph = np.loadtxt(sys.argv[1] + "/tests/golden/phases_k10_d31.txt")
+f0, _ = I.lbm_instance(4, 0, tau=0.8)
+out = {}
+for name, prec in (("c128", G.CSIM_C128), ("c64", G.CSIM_C64)):
+    c = G.Circuit(4, 0.8, 2, 2, 0.1, 2, phases=ph)
+    c.init(f0, prec)
+    out[name + "_sparse"] = np.array(c.info()["sparse_init"])
+    out[name + "_b"] = c.read_state()           # read before the first sweep
+    c.init(f0, prec)
+    c.run()
+    out[name + "_final"] = c.read_state()
+    c.init(f0, prec)                             # stepped run with a checkpoint
+    c.run_steps(1)
+    out[name + "_ck"] = c.checkpoint()[0]
+    c.run()
+    out[name + "_stepped"] = c.read_state()
+    c.init(f0, prec)                             # postselection before any sweep
+    a, p, t = c.postselect()
+    out[name + "_post0"] = np.array([p, t])
+    c.init(f0, prec)                             # the mode changes after csim_init
+    c.set_exec(G.CSIM_EXEC_GATE)
+    c.run()
+    out[name + "_gate"] = c.read_state()
+np.savez(sys.argv[2], **out)
+print("ok")
+"""
+
+
+def test_sparse_init_is_invisible(tmp_path):
+    """csim_init that writes only the tiles of b (the first in-place sweep
+    reads zeros for the rest) gives, bit for bit, the states of the whole
+    zero-filled init: after a full run, after one step and a checkpoint, when
+    the state is read or postselected before any sweep, and when the
+    execution mode changes between init and run."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for name, flag in (("sparse", "1"), ("whole", "0")):
+        path = str(tmp_path / f"{name}.npz")
+        env = dict(os.environ, CSIM_SPARSE_INIT=flag)
+        r = subprocess.run([sys.executable, "-c", SPARSE_SCRIPT, root, path], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+        res[name] = np.load(path)
+    for prec in ("c128", "c64"):
+        assert int(res["sparse"][prec + "_sparse"]) == 1, prec
+        assert int(res["whole"][prec + "_sparse"]) == 0, prec
+        for key in ("_b", "_final", "_ck", "_stepped", "_post0", "_gate"):
+            assert np.array_equal(res["sparse"][prec + key], res["whole"][prec + key]), prec + key
+        b = res["sparse"][prec + "_b"]
+        assert abs(np.linalg.norm(b) - 1.0) < 1e-6
+        assert 0 < np.count_nonzero(b) < b.size // 64
