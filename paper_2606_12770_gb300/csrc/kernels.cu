@@ -840,6 +840,28 @@ __global__ void __launch_bounds__(256, MINB)
     for (int u = 0; u < U; ++u) mv[u] = ci[u] = ((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane;
     H = nfe > 0 ? (((H | fmask) + hstep) & ~fmask) : (H + nwarps * U);
     T v[U][4];
+    if constexpr (SHAPE == 3) {
+      // first sweep after a sparse init: the sweep maps each tile to itself
+      // linearly, so tiles that b does not touch stay zero; write the zeros
+      // and skip the ops (warp-uniform: a tile belongs to one warp)
+      if (a.zero_map) {
+        bool any = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint32_t tile = ci[u] >> 5;
+          any |= ((__ldg(a.zero_map + (tile >> 5)) >> (tile & 31u)) & 1u) != 0u;
+        }
+        if (!any) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[u][j] = mk<T>((R)0, (R)0);
+            store_chunk(out + ((size_t)ci[u] << 2), v[u]);
+          }
+          continue;
+        }
+      }
+    }
     uint32_t wd[kPrefetchMux][U];
     if constexpr (SHAPE != 1) prefetch_mux<U>(a, ci, wd);
     if (!a.scatter) {

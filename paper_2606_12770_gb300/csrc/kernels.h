@@ -111,7 +111,9 @@ struct SweepParams {
   int inplace;
   // First sweep after a sparse csim_init (shape ShapeFirst only): tiles whose
   // bit is clear in zero_map (bit t of word t / 32) hold zeros that were never
-  // written; the kernel uses zeros instead of loading them.
+  // written.  The sweep maps each tile to itself linearly, so the kernel
+  // writes zeros there without loading them or applying the ops, and uses
+  // zeros for such a tile when it shares a warp iteration with a marked one.
   const uint32_t* zero_map;
 };
 
