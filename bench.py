@@ -47,6 +47,8 @@ WORKLOADS = {
     # 28-qubit member of the precision family (2 GiB in complex64) for ncu captures
     "profile-nx16-k4-nt16-d13-c64": (16, 2, 4, 16, 0.1, None, (0.6, 1.2), 1, 13, 1000.0, "c64"),
     "profile-nx16-k4-nt16-d13-c128": (16, 2, 4, 16, 0.1, None, (0.6, 1.2), 1, 13, 1000.0, "c128"),
+    # 26-qubit member (512 MiB): its gathers keep the natural tile order
+    "profile-nx8-k4-nt16-d13-c64": (8, 2, 4, 16, 0.1, None, (0.6, 1.2), 1, 13, 1000.0, "c64"),
 }
 DEFAULT = "precision-nx64-k4-nt16-d13-c64"
 
@@ -83,7 +85,7 @@ MICRO = {
 NCU_TRAFFIC = {
     # mean over the 14 sweep launches of one run (single-pass ncu capture;
     # the first sweep after the sparse init writes the state and reads 0.05 GB)
-    ("6e13d34f10ec3a62", "precision-nx64-k4-nt16-d13-c64"): 70.49e9,
+    ("ce3b16e7506b79f4", "precision-nx64-k4-nt16-d13-c64"): 69.50e9,
 }
 
 L2_BYTES = 129 * 1000 * 1000

@@ -7,7 +7,11 @@
 // seven bits are the value-encoding target t, the QSVT signal s and the five
 // U_L label qubits, i.e. every qubit that is touched by a non-permutation gate.
 //
-//   init_scatter_kernel  -- zero state + scatter the normalised right-hand side b
+//   init_scatter_kernel  -- scatter the normalised right-hand side b (after a
+//                           memset, or after the sparse init's two kernels)
+//   mark_tiles_kernel    -- sparse init: the tile map of b's 128-amplitude tiles
+//   zero_tiles_kernel    -- sparse init: zero those tiles (the first sweep
+//                           writes the zeros of all others)
 //   gate_kernel          -- one elementary gate over the 2^{n-1-c} matching pairs
 //   sweep_kernel         -- one fused HBM pass: gather through an index
 //                           permutation (a run of multi-controlled X gates; its
@@ -25,9 +29,8 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <utility>
-#include <cstdio>
-#include <cstdlib>
 
 #include "kernels.h"
 
@@ -1251,10 +1254,28 @@ bool shapes_enabled() {
   return v;
 }
 
+// Complex64 averaging sweeps (ShapeAvg, the conjugated gathers) run four
+// tiles per warp iteration at two blocks per SM: a warp then loads and stores
+// the sibling tiles whose chunks share 128-byte lines together.  Not with
+// exactly one fast tile bit: four tiles per warp need two, and would force
+// the natural order.  CSIM_AVG_CFG=2,4 gives them the variant of the other
+// shapes.
+bool avg_four_tiles() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_AVG_CFG");
+    return !(e && std::strcmp(e, "2,4") == 0);
+  }();
+  return v;
+}
+
 template <typename R, int U, int MINB>
 void launch_shaped(const void* in, void* out, uint32_t ntiles, const SweepParams& a,
                    cudaStream_t st) {
   const int shape = shapes_enabled() ? sweep_shape(a) : 0;
+  if constexpr (sizeof(R) == 4) {
+    if (shape == 1 && a.nfast != 1 && ntiles >= 4 && avg_four_tiles())
+      return launch_sweep_t<R, 4, 2, 1>(in, out, ntiles, a, st);
+  }
   if (shape == 1) return launch_sweep_t<R, U, MINB, 1>(in, out, ntiles, a, st);
   if (shape == 2) return launch_sweep_t<R, U, MINB, 2>(in, out, ntiles, a, st);
   if (shape == 3) return launch_sweep_t<R, U, MINB, 3>(in, out, ntiles, a, st);
@@ -1352,6 +1373,7 @@ cudaError_t warm_r() {
   chk(cudaFuncGetAttributes(&fa, compact_kernel<R>));
   if constexpr (sizeof(R) == 4) {
     chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 2, 4, 1>));
+    chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 4, 2, 1>));
     chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 2, 4, 2>));
     chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 2, 4, 3>));
     chk(cudaFuncGetAttributes(&fa, sweep_kernel<R, 2, 4, 4>));

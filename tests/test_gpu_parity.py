@@ -353,7 +353,8 @@ def test_source_index_tables_equal_lookup_chain(tmp_path):
     """The gather sweeps give the same state, bit for bit, whether they load the
     precomputed source index of each chunk or walk the lookup-table chain (the
     same index, the same arithmetic), with the indices loaded one iteration
-    ahead or not, and in the scatter form (destination indices); the table
+    ahead or not, with four or two tiles per warp iteration in the averaging
+    sweeps, and in the scatter form (destination indices); the table
     path is the one in use by default (one table: the U_L^dag chain, which the
     conjugated sweeps and the last gather share).  The kernels specialised on
     the sweep shape agree with the generic op interpreter within rounding."""
@@ -364,11 +365,16 @@ def test_source_index_tables_equal_lookup_chain(tmp_path):
     res = {}
     modes = {"chain": ("0", "1", "gather", "1"), "src-nopre": ("1", "0", "gather", "1"),
              "default": ("1", "1", "gather", "1"), "chain-scatter": ("0", "1", "scatter", "1"),
-             "scatter": ("1", "1", "scatter", "1"), "generic": ("1", "1", "gather", "0")}
+             "scatter": ("1", "1", "scatter", "1"), "generic": ("1", "1", "gather", "0"),
+             "avg-2,4": ("1", "1", "gather", "1")}
     for name, (flag, pre, form, shapes) in modes.items():
         path = str(tmp_path / f"{name}.npz")
         env = dict(os.environ, CSIM_SRC_INDEX=flag, CSIM_SRC_PREFETCH=pre, CSIM_SWEEP_FORM=form,
                    CSIM_SWEEP_SHAPES=shapes)
+        if name == "avg-2,4":
+            env["CSIM_AVG_CFG"] = "2,4"
+        else:
+            env.pop("CSIM_AVG_CFG", None)
         r = subprocess.run([sys.executable, "-c", SRC_SCRIPT, root, path], env=env,
                            capture_output=True, text=True, timeout=600)
         assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
@@ -378,6 +384,9 @@ def test_source_index_tables_equal_lookup_chain(tmp_path):
         assert np.array_equal(res["chain"][prec], res["default"][prec]), prec
         assert np.array_equal(res["src-nopre"][prec], res["default"][prec]), prec
         assert np.array_equal(res["chain-scatter"][prec], res["scatter"][prec]), prec
+        # four tiles per warp iteration in the averaging sweeps (the default)
+        # or two: the same arithmetic per tile
+        assert np.array_equal(res["avg-2,4"][prec], res["default"][prec]), prec
         # shaped kernels against the generic op interpreter: the same operations,
         # compiled in other instantiations (contraction may differ)
         a, b = res["default"][prec], res["generic"][prec]
@@ -443,3 +452,50 @@ def test_sparse_init_is_invisible(tmp_path):
         b = res["sparse"][prec + "_b"]
         assert abs(np.linalg.norm(b) - 1.0) < 1e-6
         assert 0 < np.count_nonzero(b) < b.size // 64
+
+
+AVG_SCRIPT = r"""
+import sys, hashlib, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import lbm_inputs as I, paper_2606_12770_gb300 as G
+Nx = int(sys.argv[2])
+f0, tau = I.lbm_instance(Nx, 1, tau=None, tau_range=(0.6, 1.2))
+c = G.Circuit(Nx, tau, 2, 4, 0.1, 16, kappa_qsvt=1000.0, d=13)
+c.init(f0, G.CSIM_C64, torch.cuda.current_stream())
+c.run()
+_, p, t = c.postselect(want_amplitudes=False)
+x = torch.as_tensor(c.device_state(), device="cuda")
+h = hashlib.sha256()
+for i in range(0, x.shape[0], 1 << 26):
+    h.update(x[i:i + (1 << 26)].cpu().numpy().tobytes())
+np.savez(sys.argv[3], pt=np.array([p, t]), digest=np.frombuffer(h.digest(), dtype=np.uint8))
+print("ok")
+"""
+
+
+@pytest.mark.parametrize("Nx", [8, 32])
+def test_averaging_sweep_launch_shapes_agree(tmp_path, Nx):
+    """The conjugated averaging sweeps of the precision circuit give the same
+    final state, bit for bit (a SHA-256 of the whole complex64 state), with
+    four tiles per warp iteration (the default) and with two
+    (CSIM_AVG_CFG=2,4): at 26 qubits in the natural tile order and at 30
+    qubits with four fast tile bits."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for name, cfg in (("four", None), ("two", "2,4")):
+        path = str(tmp_path / f"{name}.npz")
+        env = dict(os.environ)
+        env.pop("CSIM_AVG_CFG", None)
+        if cfg:
+            env["CSIM_AVG_CFG"] = cfg
+        r = subprocess.run([sys.executable, "-c", AVG_SCRIPT, root, str(Nx), path], env=env,
+                           capture_output=True, text=True, timeout=900)
+        assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+        res[name] = np.load(path)
+    assert np.array_equal(res["four"]["digest"], res["two"]["digest"])
+    assert np.array_equal(res["four"]["pt"], res["two"]["pt"])
+    # unitary circuit: the total norm stays 1 (complex64 rounding)
+    assert abs(res["four"]["pt"][1] - 1.0) < 1e-4
