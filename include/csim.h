@@ -108,8 +108,9 @@ typedef struct {
   uint64_t state_bytes;   /* bytes of the current state (0 before csim_init) */
   int32_t n_src_tables;   /* source-index tables the gather sweeps load (2^n bytes
                              each; 0: the sweeps walk the lookup-table chain) */
-  int32_t sparse_init;    /* 1: the last csim_init wrote the tiles of b only and
-                             left the zeros to the first sweep (csim_init) */
+  int32_t sparse_init;    /* > 0: the last csim_init wrote the tiles of b only and
+                             left the zeros to the first sparse_init sweeps
+                             (csim_init); 0: it wrote the whole state */
 } csim_info_t;
 
 /* --- building (host only; no GPU needed) -------------------------------- */
@@ -154,12 +155,15 @@ csim_status csim_export_mask(const csim_circuit* c, uint64_t* masks, uint64_t* v
  * In the fused mode at n >= 12, when the program's first step is an in-place
  * sweep (the circuit's opening Walsh-Hadamard and multiplexer), csim_init
  * fuses the program, writes only the 128-amplitude tiles that hold b and
- * marks them in a 2^(n-12)-word bitmap; the first sweep reads zeros for the
- * unmarked tiles instead of a zero-filled state (csim_info().sparse_init = 1;
- * CSIM_SPARSE_INIT=0 in the environment always writes the whole state).
- * Every call that reads the state before that sweep (csim_read_state,
- * csim_checkpoint, csim_state_device, csim_postselect) writes it whole first,
- * so the difference is not observable.  Errors: CSIM_ERR_OOM (nothing kept),
+ * marks them in a 2^(n-12)-word bitmap.  The leading sweeps write the zeros
+ * of the unmarked tiles instead of a memset: the first sweep itself
+ * (csim_info().sparse_init = 1), or, when the second is a conjugated gather,
+ * that gather, which reads zeros for chunks in unmarked tiles while the first
+ * sweep touches only the marked ones (sparse_init = 2).  CSIM_SPARSE_INIT=0 in
+ * the environment always writes the whole state.  Every call that reads the
+ * state before those sweeps have run (csim_read_state, csim_checkpoint,
+ * csim_state_device, csim_postselect) zeroes the unmarked tiles first, so the
+ * difference is not observable.  Errors: CSIM_ERR_OOM (nothing kept),
  * CSIM_ERR_CUDA. */
 csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec,
                       void* cuda_stream);

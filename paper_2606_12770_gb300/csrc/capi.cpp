@@ -79,27 +79,50 @@ cudaError_t write_initial_state(csim_circuit* c, const std::vector<uint64_t>& id
   return e;
 }
 
-// Before the state is read (or handed out) ahead of the first sweep of a
-// sparse init: write it whole.
+// Sweeps at the start of the program that complete a sparse init's zero
+// fill: 2 when the first is an in-place tile sweep and the second a gather
+// sweep whose kernels take the zero map (modes 2 and 3), 1 when only the
+// first does (mode 1), else 0.
+int zero_fill_steps(const csim_circuit* c) {
+  const csim::Program& P = c->prog;
+  if (P.mode != CSIM_EXEC_FUSED || P.steps.empty() || c->L.n < 12) return 0;
+  const csim::Step& s0 = P.steps[0];
+  if (s0.kind != 0 || s0.gather ||
+      csim::sweep_zero_kind(c->prec, c->L.n, P.params[(size_t)s0.param]) != 1)
+    return 0;
+  if (P.steps.size() > 1) {
+    const csim::Step& s1 = P.steps[1];
+    if (s1.kind == 0 && s1.gather &&
+        csim::sweep_zero_kind(c->prec, c->L.n, P.params[(size_t)s1.param]) == 3)
+      return 2;
+  }
+  return 1;
+}
+
+// Before the state is read (or handed out) while a sparse init's zero fill is
+// incomplete: zero the unmarked tiles.  The leading sweeps map those tiles to
+// themselves and zero to zero, so this gives the state at any step before
+// the fill completes.
 cudaError_t materialize(csim_circuit* c) {
   if (!c->zero_fill) return cudaSuccess;
   c->zero_fill = false;
-  return write_initial_state(c, c->b_idx, c->b_val, nullptr);
+  cudaError_t e = csim::launch_zero_unmarked(c->buf[c->cur], c->prec, c->L.n, c->d_zmap, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e;
 }
 
-// The zero map for the run's next step: that of a sparse init while the
-// program still starts with a sweep whose kernel reads it.  Otherwise (the
-// execution mode changed since csim_init, say) the state is written whole.
-cudaError_t zero_map_for_run(csim_circuit* c, const uint32_t** zmap) {
+// The zero map for the run from the next step, and how many leading steps
+// take it: those of a sparse init while the program still starts with the
+// same sweeps.  Otherwise (the execution mode changed since csim_init, say)
+// the state is completed first.
+cudaError_t zero_map_for_run(csim_circuit* c, const uint32_t** zmap, int* zsteps) {
   *zmap = nullptr;
+  *zsteps = 0;
   if (!c->zero_fill) return cudaSuccess;
-  if (c->next_step == 0 && c->prog.mode == CSIM_EXEC_FUSED && !c->prog.steps.empty()) {
-    const csim::Step& s0 = c->prog.steps[0];
-    if (s0.kind == 0 && !s0.gather &&
-        csim::sweep_takes_zero_map(c->prec, c->L.n, c->prog.params[(size_t)s0.param])) {
-      *zmap = c->d_zmap;
-      return cudaSuccess;
-    }
+  if (c->next_step < c->zero_steps && zero_fill_steps(c) == c->zero_steps) {
+    *zmap = c->d_zmap;
+    *zsteps = c->zero_steps;
+    return cudaSuccess;
   }
   return materialize(c);
 }
@@ -112,6 +135,7 @@ void free_device(csim_circuit* c) {
   if (c->d_zmap) cudaFree(c->d_zmap);
   c->d_zmap = nullptr;
   c->zero_fill = false;
+  c->zero_steps = 0;
   if (c->d_pat) cudaFree(c->d_pat);
   if (c->d_partial) cudaFree(c->d_partial);
   if (c->d_out) cudaFree(c->d_out);
@@ -381,7 +405,7 @@ csim_status csim_info(const csim_circuit* c, csim_info_t* out) {
   out->n_sweeps_run = c->prog_built ? c->prog.passes : 0;
   out->state_bytes = c->bytes;
   out->n_src_tables = (int32_t)c->prog.d_src.size();
-  out->sparse_init = c->sparse_init ? 1 : 0;
+  out->sparse_init = c->sparse_init;
   return CSIM_OK;
 }
 
@@ -443,33 +467,26 @@ csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec, vo
     const csim_status st = alloc_state(c, prec);
     if (st != CSIM_OK) return st;
   }
-  // sparse when the program's first step is an in-place sweep whose kernel
-  // reads zeros for the tiles that b does not touch
-  bool sparse = false;
+  // sparse when the program's leading sweeps can write the zeros of the
+  // tiles that b does not touch
+  int zsteps = 0;
   if (sparse_init_enabled() && c->exec == CSIM_EXEC_FUSED && L.n >= 12) {
     std::string err;
-    if (csim::ensure_program(c, c->stream, &err) && !c->prog.steps.empty()) {
-      const csim::Step& s0 = c->prog.steps[0];
-      sparse = s0.kind == 0 && !s0.gather &&
-               csim::sweep_takes_zero_map(prec, L.n, c->prog.params[(size_t)s0.param]);
-    }
-    if (sparse && !c->d_zmap) {
+    if (csim::ensure_program(c, c->stream, &err)) zsteps = zero_fill_steps(c);
+    if (zsteps > 0 && !c->d_zmap) {
       if (cudaMalloc(&c->d_zmap, ((size_t)1 << (L.n - 12)) * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         c->d_zmap = nullptr;
-        sparse = false;
+        zsteps = 0;
       }
     }
   }
   c->zero_fill = false;
-  const cudaError_t e = write_initial_state(c, idx, val, sparse ? c->d_zmap : nullptr);
+  const cudaError_t e = write_initial_state(c, idx, val, zsteps > 0 ? c->d_zmap : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "csim_init");
-  c->zero_fill = sparse;
-  c->sparse_init = sparse;
-  if (sparse) {
-    c->b_idx = std::move(idx);
-    c->b_val = std::move(val);
-  }
+  c->zero_fill = zsteps > 0;
+  c->zero_steps = zsteps;
+  c->sparse_init = zsteps;
   c->loaded = true;
   c->ran = false;
   c->next_step = 0;
@@ -505,10 +522,11 @@ csim_status csim_run(csim_circuit* c) {
   cudaError_t e = csim::build_src_index(&c->prog, c->stream, kSrcIndexTables);
   if (e != cudaSuccess) return cuda_fail(e, "csim_run: source index");
   const uint32_t* zmap = nullptr;
-  e = zero_map_for_run(c, &zmap);
+  int zsteps = 0;
+  e = zero_map_for_run(c, &zmap, &zsteps);
   if (e != cudaSuccess) return cuda_fail(e, "csim_run: initial state");
   e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream, c->next_step,
-                              (int64_t)c->prog.steps.size(), nullptr, zmap);
+                              (int64_t)c->prog.steps.size(), nullptr, zmap, zsteps);
   c->zero_fill = false;
   if (e != cudaSuccess) return cuda_fail(e, "csim_run");
   c->next_step = (int64_t)c->prog.steps.size();
@@ -535,13 +553,14 @@ csim_status csim_run_steps(csim_circuit* c, int64_t n_steps, int64_t* next_step)
   cudaError_t e = csim::build_src_index(&c->prog, c->stream, kSrcIndexTables);
   if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps: source index");
   const uint32_t* zmap = nullptr;
+  int zsteps = 0;
   if (last > c->next_step) {
-    e = zero_map_for_run(c, &zmap);
+    e = zero_map_for_run(c, &zmap, &zsteps);
     if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps: initial state");
   }
   e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream, c->next_step, last,
-                              nullptr, zmap);
-  if (last > c->next_step) c->zero_fill = false;
+                              nullptr, zmap, zsteps);
+  if (last >= c->zero_steps) c->zero_fill = false;
   if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps");
   c->next_step = last;
   if (last == total) {
@@ -575,7 +594,7 @@ csim_status csim_restore(csim_circuit* c, const double* amps, size_t n_amps, csi
     if (st != CSIM_OK) return st;
   }
   c->zero_fill = false;
-  c->sparse_init = false;
+  c->sparse_init = 0;
   cudaError_t e;
   c->cur = 0;
   if (prec == CSIM_C128) {

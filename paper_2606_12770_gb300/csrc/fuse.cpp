@@ -1233,30 +1233,33 @@ cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cuda
 
 cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
                               int64_t first, int64_t last, const uint32_t* const* src_tables,
-                              const uint32_t* zero_map) {
+                              const uint32_t* zero_map, int zero_steps) {
   for (int64_t k = first; k < last; ++k) {
     const Step& s = p.steps[(size_t)k];
     cudaError_t e;
     if (s.kind == 1) {
       e = launch_gate(buf[*cur], prec, p.n, s.g, st);
     } else if (!s.gather) {
-      if (k == 0 && zero_map) {
+      if (k == 0 && zero_map && zero_steps >= 1) {
         SweepParams a = p.params[(size_t)s.param];
         a.zero_map = zero_map;
+        a.zero_mode = zero_steps == 2 ? 2 : 1;
         e = launch_sweep(buf[*cur], buf[*cur], prec, p.n, a, st);
       } else {
         e = launch_sweep(buf[*cur], buf[*cur], prec, p.n, p.params[s.param], st);
       }
     } else {
       void* out = s.inplace ? buf[*cur] : buf[1 - *cur];
+      SweepParams a = p.params[(size_t)s.param];
       if (src_tables && (size_t)s.param < p.src_tab.size() && p.src_tab[(size_t)s.param] >= 0) {
-        SweepParams a = p.params[(size_t)s.param];
         a.src = src_tables[p.src_tab[(size_t)s.param]];
         a.src_prefetch = src_prefetch_enabled() ? 1 : 0;
-        e = launch_sweep(buf[*cur], out, prec, p.n, a, st);
-      } else {
-        e = launch_sweep(buf[*cur], out, prec, p.n, p.params[s.param], st);
       }
+      if (k == 1 && zero_map && zero_steps == 2) {
+        a.zero_map = zero_map;
+        a.zero_mode = 3;
+      }
+      e = launch_sweep(buf[*cur], out, prec, p.n, a, st);
       if (!s.inplace) *cur = 1 - *cur;
     }
     if (e != cudaSuccess) return e;

@@ -102,11 +102,13 @@ cudaError_t launch_src_tables(const Program& p, uint32_t* const* tables, cudaStr
 cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
                         const uint32_t* const* src_tables = nullptr);
 // Steps [first, last) of the program only (checkpointed runs).  zero_map
-// (launch_init_sparse) goes to step 0, when it is among them.
+// (launch_init_sparse) goes to the first zero_steps steps, when they are
+// among them: with zero_steps = 1, step 0 in mode 1; with 2, step 0 in mode 2
+// and step 1 in mode 3 (SweepParams::zero_mode).
 cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
                               int64_t first, int64_t last,
                               const uint32_t* const* src_tables = nullptr,
-                              const uint32_t* zero_map = nullptr);
+                              const uint32_t* zero_map = nullptr, int zero_steps = 0);
 // Host executor of a fused program (FP64, kernel semantics) for testing.
 void emulate_program(const Program& p, std::vector<double>* amps);
 

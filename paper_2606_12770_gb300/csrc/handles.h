@@ -27,13 +27,13 @@ struct csim_circuit {
   bool loaded = false, ran = false;
   int64_t next_step = 0;  // next program step of a run in progress (csim_run_steps)
   // sparse csim_init: only the tiles of b were written (d_zmap marks them);
-  // the run's first sweep reads zeros for the others.  b_idx / b_val keep b
-  // to write the full state when it is read before that sweep.
+  // the program's first zero_steps sweeps (1 or 2) write the zeros of the
+  // others.  Until they have run, zero_fill is set, and reading the state
+  // zeroes the unmarked tiles first.
   bool zero_fill = false;
-  bool sparse_init = false;  // the last csim_init was sparse (reported by csim_info)
+  int zero_steps = 0;
+  int sparse_init = 0;  // zero_steps of the last csim_init, 0 if plain (csim_info)
   uint32_t* d_zmap = nullptr;
-  std::vector<uint64_t> b_idx;
-  std::vector<double> b_val;
   csim::Program prog;
   bool prog_built = false;
   uint64_t* d_pat = nullptr;  // masks then values

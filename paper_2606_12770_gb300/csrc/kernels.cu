@@ -10,8 +10,9 @@
 //   init_scatter_kernel  -- scatter the normalised right-hand side b (after a
 //                           memset, or after the sparse init's two kernels)
 //   mark_tiles_kernel    -- sparse init: the tile map of b's 128-amplitude tiles
-//   zero_tiles_kernel    -- sparse init: zero those tiles (the first sweep
-//                           writes the zeros of all others)
+//   zero_tiles_kernel    -- sparse init: zero those tiles (the leading sweeps
+//                           write the zeros of all others)
+//   zero_unmarked_kernel -- write the zeros of a sparse init whole (state read early)
 //   gate_kernel          -- one elementary gate over the 2^{n-1-c} matching pairs
 //   sweep_kernel         -- one fused HBM pass: gather through an index
 //                           permutation (a run of multi-controlled X gates; its
@@ -83,6 +84,20 @@ __global__ void zero_tiles_kernel(typename V2<R>::T* __restrict__ state,
     typename V2<R>::T* t = state + ((idx[w] >> 7) << 7);
 #pragma unroll
     for (int j = 0; j < 4; ++j) t[(lane << 2) + j] = mk<typename V2<R>::T>((R)0, (R)0);
+  }
+}
+
+// Zero every tile whose bit is clear in map (grid-stride, one warp per tile).
+template <typename R>
+__global__ void zero_unmarked_kernel(typename V2<R>::T* __restrict__ state,
+                                     const uint32_t* __restrict__ map, uint32_t ntiles) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ntiles; w += nwarps) {
+    if ((__ldg(map + (w >> 5)) >> (w & 31u)) & 1u) continue;
+    typename V2<R>::T* t = state + ((size_t)w << 7);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[(j << 5) + lane] = mk<typename V2<R>::T>((R)0, (R)0);
   }
 }
 
@@ -829,6 +844,43 @@ __global__ void __launch_bounds__(256, MINB)
 #pragma unroll
     for (int u = 0; u < U; ++u) L[u] = (uint32_t)u;
   }
+  if constexpr (SHAPE == 3) {
+    // zero mode 2 (the next sweep reads zeros for unmarked tiles): visit the
+    // marked tiles only.  Warp w takes map words w, w + nwarps, ... (b's
+    // tiles fill a run of consecutive words, which this spreads over the
+    // warps) and the tiles of each set bit, U aligned tiles at a time; an
+    // unmarked tile of such a group is read as zeros.
+    if (a.zero_map && a.zero_mode == 2) {
+      const uint32_t nwords = ntiles >> 5;
+      for (uint32_t wi = warp; wi < nwords; wi += nwarps) {
+        const uint32_t word = __ldg(a.zero_map + wi);
+        uint32_t bits = word;
+        while (bits != 0u) {
+          const uint32_t b0 = (uint32_t)(__ffs((int)bits) - 1) & ~(uint32_t)(U - 1);
+          bits &= ~(((1u << U) - 1u) << b0);
+          uint32_t ci[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) ci[u] = (((wi << 5) + b0 + (uint32_t)u) << 5) | lane;
+          uint32_t wd[kPrefetchMux][U];
+          prefetch_mux<U>(a, ci, wd);
+          T v[U][4];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if ((word >> (b0 + (uint32_t)u)) & 1u) {
+              load_chunk(in + ((size_t)ci[u] << 2), v[u]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) v[u][q] = mk<T>((R)0, (R)0);
+            }
+          }
+          apply_shaped<R, U, SHAPE>(a, v, ci, lane, wd);
+#pragma unroll
+          for (int u = 0; u < U; ++u) store_chunk(out + ((size_t)ci[u] << 2), v[u]);
+        }
+      }
+      return;
+    }
+  }
   // source indices of the warp's next tiles, loaded one iteration ahead
   const bool pre = a.src != nullptr && a.src_prefetch != 0 && !a.scatter;
   uint32_t nxt[U];
@@ -845,8 +897,9 @@ __global__ void __launch_bounds__(256, MINB)
     T v[U][4];
     if constexpr (SHAPE == 3) {
       // first sweep after a sparse init: the sweep maps each tile to itself
-      // linearly, so tiles that b does not touch stay zero; write the zeros
-      // and skip the ops (warp-uniform: a tile belongs to one warp)
+      // linearly, so tiles that b does not touch stay zero.  Mode 1 writes
+      // the zeros and skips the ops; mode 2 leaves them to the next sweep
+      // (warp-uniform: a tile belongs to one warp).
       if (a.zero_map) {
         bool any = false;
 #pragma unroll
@@ -855,11 +908,13 @@ __global__ void __launch_bounds__(256, MINB)
           any |= ((__ldg(a.zero_map + (tile >> 5)) >> (tile & 31u)) & 1u) != 0u;
         }
         if (!any) {
+          if (a.zero_mode == 1) {
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
+            for (int u = 0; u < U; ++u) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[u][j] = mk<T>((R)0, (R)0);
-            store_chunk(out + ((size_t)ci[u] << 2), v[u]);
+              for (int j = 0; j < 4; ++j) v[u][j] = mk<T>((R)0, (R)0);
+              store_chunk(out + ((size_t)ci[u] << 2), v[u]);
+            }
           }
           continue;
         }
@@ -884,9 +939,9 @@ __global__ void __launch_bounds__(256, MINB)
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if constexpr (SHAPE == 3) {  // in place: mv == ci
+        if constexpr (SHAPE == 1 || SHAPE == 3) {  // chunks of unmarked tiles read as zeros
           if (a.zero_map) {
-            const uint32_t tile = ci[u] >> 5;
+            const uint32_t tile = mv[u] >> 5;
             if (!((__ldg(a.zero_map + (tile >> 5)) >> (tile & 31u)) & 1u)) {
 #pragma unroll
               for (int j = 0; j < 4; ++j) v[u][j] = mk<T>((R)0, (R)0);
@@ -1329,14 +1384,34 @@ cudaError_t launch_perm_index(uint32_t* src, int n, const SweepParams& a, cudaSt
   return cudaGetLastError();
 }
 
-bool sweep_takes_zero_map(int prec, int n, const SweepParams& a) {
-  // the same choice as launch_sweep: the default variant's ShapeFirst kernel
-  if (n < 12 || !shapes_enabled() || a.scatter || a.nseg != 0 || sweep_shape(a) != 3) return false;
+int sweep_zero_kind(int prec, int n, const SweepParams& a) {
+  // the same choice as launch_sweep: a shaped kernel of the default variant
+  // (ShapeFirst in place, or ShapeAvg gathering)
+  if (n < 12 || !shapes_enabled() || a.scatter) return 0;
+  const int shape = sweep_shape(a);
+  int kind = 0;
+  if (shape == 3 && a.nseg == 0) kind = 1;
+  if (shape == 1 && a.nseg > 0) kind = 3;
+  if (kind == 0) return 0;
   const SweepCfg c = sweep_cfg();
   const uint32_t ntiles = 1u << (n - 7);
   int u = prec == CSIM_C64 ? c.u64 : c.u128;
   while ((uint32_t)u > ntiles) u >>= 1;
-  return prec == CSIM_C64 ? (u == 2 && c.minb64 == 4) : (u == 1 && c.minb128 == 2);
+  const bool shaped = prec == CSIM_C64 ? (u == 2 && c.minb64 == 4) : (u == 1 && c.minb128 == 2);
+  return shaped ? kind : 0;
+}
+
+cudaError_t launch_zero_unmarked(void* state, int prec, int n, const uint32_t* map,
+                                 cudaStream_t st) {
+  if (n < 12) return cudaErrorInvalidValue;
+  const uint32_t ntiles = 1u << (n - 7);
+  const int blk = 256;
+  const int grd = grid_for((uint64_t)ntiles * 32, blk);
+  if (prec == CSIM_C64)
+    zero_unmarked_kernel<float><<<grd, blk, 0, st>>>((float2*)state, map, ntiles);
+  else
+    zero_unmarked_kernel<double><<<grd, blk, 0, st>>>((double2*)state, map, ntiles);
+  return cudaGetLastError();
 }
 
 int norm_partials_needed() { return 2048; }
@@ -1368,6 +1443,7 @@ cudaError_t warm_r() {
   };
   chk(cudaFuncGetAttributes(&fa, init_scatter_kernel<R>));
   chk(cudaFuncGetAttributes(&fa, zero_tiles_kernel<R>));
+  chk(cudaFuncGetAttributes(&fa, zero_unmarked_kernel<R>));
   chk(cudaFuncGetAttributes(&fa, gate_kernel<R>));
   chk(cudaFuncGetAttributes(&fa, norm_kernel<R>));
   chk(cudaFuncGetAttributes(&fa, compact_kernel<R>));

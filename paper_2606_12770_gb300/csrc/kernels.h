@@ -109,12 +109,21 @@ struct SweepParams {
   // segments' permutation: a permutation, tile ops, and the inverse
   // permutation in one pass.
   int inplace;
-  // First sweep after a sparse csim_init (shape ShapeFirst only): tiles whose
-  // bit is clear in zero_map (bit t of word t / 32) hold zeros that were never
-  // written.  The sweep maps each tile to itself linearly, so the kernel
-  // writes zeros there without loading them or applying the ops, and uses
-  // zeros for such a tile when it shares a warp iteration with a marked one.
+  // The leading sweeps after a sparse csim_init.  Tiles (128 amplitudes)
+  // whose bit is clear in zero_map (bit t of word t / 32) hold zeros that
+  // were never written.  zero_mode says how the sweep treats them:
+  //   1: in-place tile sweep (ShapeFirst).  The sweep maps each tile to
+  //      itself linearly, so it writes zeros there without loading them or
+  //      applying the ops;
+  //   2: the same sweep, but unmarked tiles are left unwritten (the next
+  //      sweep reads zeros for them);
+  //   3: gather sweep (ShapeAvg): a gathered chunk in an unmarked tile is
+  //      read as zeros.  The sweep writes every chunk, so the state is whole
+  //      afterwards.
+  // In modes 1 and 2 a tile that shares a warp iteration with a marked one
+  // is read as zeros.
   const uint32_t* zero_map;
+  int zero_mode;
 };
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,
@@ -124,8 +133,13 @@ cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* 
 // those tiles and scatters the entries.  The other tiles are left unwritten.
 cudaError_t launch_init_sparse(void* state, int prec, int n, const uint64_t* d_idx,
                                const double* d_val, int64_t count, uint32_t* map, cudaStream_t st);
-// Whether launch_sweep runs this sweep with the kernel that honours zero_map.
-bool sweep_takes_zero_map(int prec, int n, const SweepParams& a);
+// Whether launch_sweep runs this sweep with a kernel that honours zero_map:
+// 1 for an in-place tile sweep (modes 1, 2), 3 for a gather sweep (mode 3),
+// 0 otherwise.
+int sweep_zero_kind(int prec, int n, const SweepParams& a);
+// Zero the tiles whose bit is clear in map (completes a sparse init early).
+cudaError_t launch_zero_unmarked(void* state, int prec, int n, const uint32_t* map,
+                                 cudaStream_t st);
 cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaStream_t st);
 cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
                          cudaStream_t st);

@@ -414,6 +414,12 @@ for name, prec in (("c128", G.CSIM_C128), ("c64", G.CSIM_C64)):
     out[name + "_ck"] = c.checkpoint()[0]
     c.run()
     out[name + "_stepped"] = c.read_state()
+    c.init(f0, prec)                             # the two leading sweeps one by one
+    c.run_steps(1)
+    c.run_steps(1)
+    out[name + "_ck2"] = c.checkpoint()[0]
+    c.run()
+    out[name + "_stepped2"] = c.read_state()
     c.init(f0, prec)                             # postselection before any sweep
     a, p, t = c.postselect()
     out[name + "_post0"] = np.array([p, t])
@@ -428,10 +434,11 @@ print("ok")
 
 def test_sparse_init_is_invisible(tmp_path):
     """csim_init that writes only the tiles of b (the first in-place sweep
-    reads zeros for the rest) gives, bit for bit, the states of the whole
-    zero-filled init: after a full run, after one step and a checkpoint, when
-    the state is read or postselected before any sweep, and when the
-    execution mode changes between init and run."""
+    leaves the other tiles unwritten and the first conjugated gather reads
+    zeros for them) gives, bit for bit, the states of the whole zero-filled
+    init: after a full run, after one or two steps and a checkpoint, when the
+    state is read or postselected before any sweep, and when the execution
+    mode changes between init and run."""
     import os
     import subprocess
     import sys
@@ -445,9 +452,10 @@ def test_sparse_init_is_invisible(tmp_path):
         assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
         res[name] = np.load(path)
     for prec in ("c128", "c64"):
-        assert int(res["sparse"][prec + "_sparse"]) == 1, prec
+        # the first sweep and the first conjugated gather complete the zeros
+        assert int(res["sparse"][prec + "_sparse"]) == 2, prec
         assert int(res["whole"][prec + "_sparse"]) == 0, prec
-        for key in ("_b", "_final", "_ck", "_stepped", "_post0", "_gate"):
+        for key in ("_b", "_final", "_ck", "_stepped", "_ck2", "_stepped2", "_post0", "_gate"):
             assert np.array_equal(res["sparse"][prec + key], res["whole"][prec + key]), prec + key
         b = res["sparse"][prec + "_b"]
         assert abs(np.linalg.norm(b) - 1.0) < 1e-6
