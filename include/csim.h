@@ -312,6 +312,9 @@ typedef struct {
   uint64_t bytes_in_use, peak_bytes, budget;
   int64_t graph_launches; /* admission passes launched as one CUDA graph */
   int64_t src_tables;     /* source-index tables built in the arena for admitted requests */
+  uint64_t sparse_saved_bytes; /* state reads and writes that admitted requests'
+                                  sparse inits left out: one state's bytes per
+                                  request with one leading sweep, three with two */
 } csim_pool_stats_t;
 
 csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out);

@@ -443,7 +443,8 @@ class PoolStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
                 ("rejected", C.c_int64), ("queued", C.c_int64), ("running", C.c_int64),
                 ("bytes_in_use", C.c_uint64), ("peak_bytes", C.c_uint64), ("budget", C.c_uint64),
-                ("graph_launches", C.c_int64), ("src_tables", C.c_int64)]
+                ("graph_launches", C.c_int64), ("src_tables", C.c_int64),
+                ("sparse_saved_bytes", C.c_uint64)]
 
 
 class Pool:

@@ -43,15 +43,6 @@ void record_last_error(const std::string& msg) { g_err = msg; }
 
 namespace {
 
-// Sparse csim_init when the first sweep can read zeros itself
-// (CSIM_SPARSE_INIT=0 always writes the whole state).
-bool sparse_init_enabled() {
-  static const bool v = [] {
-    const char* e = std::getenv("CSIM_SPARSE_INIT");
-    return !(e && e[0] == '0');
-  }();
-  return v;
-}
 
 // Upload b (idx, val) and write the state: the whole state (memset and
 // scatter), or with map the tiles of b only (launch_init_sparse).
@@ -79,26 +70,6 @@ cudaError_t write_initial_state(csim_circuit* c, const std::vector<uint64_t>& id
   return e;
 }
 
-// Sweeps at the start of the program that complete a sparse init's zero
-// fill: 2 when the first is an in-place tile sweep and the second a gather
-// sweep whose kernels take the zero map (modes 2 and 3), 1 when only the
-// first does (mode 1), else 0.
-int zero_fill_steps(const csim_circuit* c) {
-  const csim::Program& P = c->prog;
-  if (P.mode != CSIM_EXEC_FUSED || P.steps.empty() || c->L.n < 12) return 0;
-  const csim::Step& s0 = P.steps[0];
-  if (s0.kind != 0 || s0.gather ||
-      csim::sweep_zero_kind(c->prec, c->L.n, P.params[(size_t)s0.param]) != 1)
-    return 0;
-  if (P.steps.size() > 1) {
-    const csim::Step& s1 = P.steps[1];
-    if (s1.kind == 0 && s1.gather &&
-        csim::sweep_zero_kind(c->prec, c->L.n, P.params[(size_t)s1.param]) == 3)
-      return 2;
-  }
-  return 1;
-}
-
 // Before the state is read (or handed out) while a sparse init's zero fill is
 // incomplete: zero the unmarked tiles.  The leading sweeps map those tiles to
 // themselves and zero to zero, so this gives the state at any step before
@@ -119,7 +90,7 @@ cudaError_t zero_map_for_run(csim_circuit* c, const uint32_t** zmap, int* zsteps
   *zmap = nullptr;
   *zsteps = 0;
   if (!c->zero_fill) return cudaSuccess;
-  if (c->next_step < c->zero_steps && zero_fill_steps(c) == c->zero_steps) {
+  if (c->next_step < c->zero_steps && csim::zero_fill_steps(c, c->prec) == c->zero_steps) {
     *zmap = c->d_zmap;
     *zsteps = c->zero_steps;
     return cudaSuccess;
@@ -210,6 +181,36 @@ void ensure_built(csim_circuit* c) {
   std::vector<Gate> all = csim::build_qsvt(c->L, c->UL, c->phases);
   csim::build_program(all, c->L.n, c->exec, &c->prog);
   c->prog_built = true;
+}
+
+// Sparse initialisation (csim_init and pool requests) unless
+// CSIM_SPARSE_INIT=0.
+bool sparse_init_enabled() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_SPARSE_INIT");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+
+// Sweeps at the start of the program that complete a sparse init's zero
+// fill (launch_init_sparse) for a state of precision prec: 2 when the first
+// is an in-place tile sweep and the second an in-place gather sweep whose
+// kernels take the zero map (modes 2 and 3), 1 when only the first does
+// (mode 1), else 0.  Neither leading sweep writes the second state buffer.
+int zero_fill_steps(const csim_circuit* c, int prec) {
+  const Program& P = c->prog;
+  if (P.mode != CSIM_EXEC_FUSED || P.steps.empty() || c->L.n < 12) return 0;
+  const Step& s0 = P.steps[0];
+  if (s0.kind != 0 || s0.gather || sweep_zero_kind(prec, c->L.n, P.params[(size_t)s0.param]) != 1)
+    return 0;
+  if (P.steps.size() > 1) {
+    const Step& s1 = P.steps[1];
+    if (s1.kind == 0 && s1.gather && s1.inplace &&
+        sweep_zero_kind(prec, c->L.n, P.params[(size_t)s1.param]) == 3)
+      return 2;
+  }
+  return 1;
 }
 
 bool ensure_program(csim_circuit* c, cudaStream_t st, std::string* err) {
@@ -470,9 +471,9 @@ csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec, vo
   // sparse when the program's leading sweeps can write the zeros of the
   // tiles that b does not touch
   int zsteps = 0;
-  if (sparse_init_enabled() && c->exec == CSIM_EXEC_FUSED && L.n >= 12) {
+  if (csim::sparse_init_enabled() && c->exec == CSIM_EXEC_FUSED && L.n >= 12) {
     std::string err;
-    if (csim::ensure_program(c, c->stream, &err)) zsteps = zero_fill_steps(c);
+    if (csim::ensure_program(c, c->stream, &err)) zsteps = csim::zero_fill_steps(c, prec);
     if (zsteps > 0 && !c->d_zmap) {
       if (cudaMalloc(&c->d_zmap, ((size_t)1 << (L.n - 12)) * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();

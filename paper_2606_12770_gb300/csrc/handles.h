@@ -60,6 +60,9 @@ uint64_t place_bits(const std::vector<int>& bits, uint64_t v);
 void ensure_built(csim_circuit* c);
 // ensure_built, then upload the program's tables to the device (once).
 bool ensure_program(csim_circuit* c, cudaStream_t st, std::string* err);
+// Leading sweeps of the fused program that complete a sparse init (0, 1, 2).
+int zero_fill_steps(const csim_circuit* c, int prec);
+bool sparse_init_enabled();
 // Normalised right-hand side b = (f, f (x) f) as (state index, value) pairs
 // (Sec. II.D.5); false with a message for a non-finite or zero f0.
 bool circuit_rhs(const csim_circuit* c, const double* f0, std::vector<uint64_t>* idx,

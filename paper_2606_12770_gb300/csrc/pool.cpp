@@ -289,11 +289,20 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, bool in_graph, co
     *where = "b copy";
     e = cudaMemcpyAsync(d_stage, hs + pat_bytes, nnz * 16, cudaMemcpyHostToDevice, st);
   }
+  // sparse init: write the tiles of b only and leave the zeros to the
+  // program's leading sweeps.  The tile map sits at the start of the second
+  // state buffer, which those (in-place) sweeps do not write.
+  const int zsteps =
+      buf[1] && csim::sparse_init_enabled() ? csim::zero_fill_steps(c, r.prec) : 0;
+  uint32_t* zmap = zsteps > 0 ? static_cast<uint32_t*>(buf[1]) : nullptr;
   if (e == cudaSuccess) *where = "init";
-  if (e == cudaSuccess)
-    e = csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n,
-                          reinterpret_cast<const uint64_t*>(d_stage),
-                          reinterpret_cast<const double*>(d_stage + nnz * 8), (int64_t)nnz, st);
+  if (e == cudaSuccess) {
+    const uint64_t* d_idx = reinterpret_cast<const uint64_t*>(d_stage);
+    const double* d_val = reinterpret_cast<const double*>(d_stage + nnz * 8);
+    e = zmap ? csim::launch_init_sparse(buf[0], r.prec, c->L.n, d_idx, d_val, (int64_t)nnz, zmap, st)
+             : csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n, d_idx, d_val,
+                                 (int64_t)nnz, st);
+  }
   uint32_t* tabs[kMaxPoolTables] = {nullptr, nullptr};
   for (int t = 0; t < r.ntab; ++t) tabs[t] = reinterpret_cast<uint32_t*>(base + r.offs[kTabBlock + t]);
   if (e == cudaSuccess && r.ntab > 0) {
@@ -303,7 +312,8 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, bool in_graph, co
   int cur = 0;
   if (e == cudaSuccess) {
     *where = "program";
-    e = csim::run_program(c->prog, buf, &cur, r.prec, st, r.ntab > 0 ? tabs : nullptr);
+    e = csim::run_program_steps(c->prog, buf, &cur, r.prec, st, 0, (int64_t)c->prog.steps.size(),
+                                r.ntab > 0 ? tabs : nullptr, zmap, zsteps);
   }
   int lowk = 0;
   uint64_t lowv = 0;
@@ -355,6 +365,10 @@ csim_status admit(csim_pool* P) {
     P->queue.pop_front();
     P->stats.admitted++;
     P->stats.src_tables += r.ntab;
+    if (r.offs[1] != ~0ull && csim::sparse_init_enabled()) {
+      const int z = csim::zero_fill_steps(r.c, r.prec);
+      P->stats.sparse_saved_bytes += (uint64_t)(z == 2 ? 3 : z) * r.sizes[0];
+    }
     P->stats.bytes_in_use = P->arena.in_use();
     P->stats.peak_bytes = std::max(P->stats.peak_bytes, P->arena.in_use());
     started.emplace_back(r.id, free_slot);
