@@ -23,7 +23,21 @@
  *     may share a stream.
  *   - Complex amplitudes cross the ABI as interleaved (re, im) doubles.
  *   - Qubit indices are bit positions in the state index (bit 0 least
- *     significant), in the register layout documented in oracle/LAYOUT.md.
+ *     significant).  Registers are little-endian and allocated from bit 0 up:
+ *       t    1 bit   value-encoding target of the RY branches
+ *       s    1 bit   QSVT signal qubit
+ *       iL   n_iL    row label of U_L (n_iL = max(1 + n_iA, 2 + n_k), n_iA = 2
+ *                    for N_C = 1 and 4 for N_C = 2); iL[0..1] is the A11
+ *                    output-velocity label, iL[2..3] the N_C = 2 case label
+ *       q1   2 bits  velocity 0 (e = +1), 1 (e = -1), 2 (e = 0); 3 unused
+ *       a1   n_a     lattice site (n_a = log2 Nx)
+ *       q2, a2, ord  (N_C = 2 only) second velocity, second site, Carleman
+ *                    order (0: f^(1), 1: f^(1) (x) f^(1))
+ *       k    n_k     Taylor index (n_k = bit length of K)
+ *       m    n_m     time step (n_m = bit length of Nt - 1, plus 1)
+ *     A basis state is physical when t, s and iL are 0, every velocity is at
+ *     most 2 and, for N_C = 2 and ord = 0, q2 = a2 = 0.  csim_info reports n;
+ *     csim_export_mask gives the postselected patterns in these bit positions.
  */
 #ifndef CSIM_H
 #define CSIM_H
@@ -368,15 +382,18 @@ csim_status csim_pool_plan(uint64_t budget, uint64_t min_block, int32_t n_stream
  * pm, pv: host arrays of npat masks and values (0 <= npat <= 16); an index i
  * is selected when (i & pm[k]) == pv[k] for some k (csim_export_mask gives the
  * circuit's postselection patterns).
- * d_out: device memory for 2 doubles, receiving sum |a|^2 over the whole state
- * and over the selected indices.
+ * d_out: device memory for 2 doubles, 8-byte aligned, receiving sum |a|^2 over
+ * the whole state and over the selected indices (each |a|^2 formed and summed
+ * in FP64, complex64 amplitudes widened first).
  * The work is enqueued on cuda_stream (NULL = the legacy default stream); the
  * call does not synchronise.  The caller owns d_state, d_out and the host
  * arrays, which only need to stay valid for the call itself.
  *
  * Errors: CSIM_ERR_TOO_LARGE for n > 34 or more than 16 patterns; CSIM_ERR_ARG
- * for null or misaligned pointers, n < 1, or a value outside its mask;
- * CSIM_ERR_CUDA when the launch or the set-up fails.
+ * for null or misaligned pointers (d_state not 16-byte, d_out not 8-byte
+ * aligned), n < 1, a value outside its mask, or a mask with bits at or above
+ * n; CSIM_ERR_CUDA when the launch or the set-up fails (a failed set-up is
+ * retried by the next call).
  *
  * The first call on each device looks up the array's device address with that
  * device current.  That lookup can load the library's module, so make the

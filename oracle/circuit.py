@@ -1,7 +1,9 @@
 """O3 -- the oracle's own gate compiler (U_A inside U_L, QSVT wrapper, mask).
 
-Test infrastructure only.  Follows ``oracle/LAYOUT.md`` literally, in plain
-Python.  The construction realises, with multi-controlled elementary gates
+Test infrastructure only.  Written independently of the product's compiler,
+in plain Python, from the same gate-level construction (registers as in
+``layout.py``; U_A as one permutation of site, velocity and label followed by
+the RY value encodings on t).  The construction realises, with multi-controlled elementary gates
 and no work ancillas, the sparse-oracle block encoding of Eq. UM-structure
 (Sec. II.D.1) for the Carleman matrix of Eq. carleman-system and the Taylor
 matrix L of Fig. L (Sec. II.D.4), wrapped in the QSVT sequence of
@@ -227,7 +229,7 @@ def _wall_fix(lay, base, areg, qreg, vfun, ios, ko, dt, Lmax, t):
 
 # -------------------------------------------------------------------- U_L
 def build_UL(Nx, tau, NC, K, dt, Nt, bc="periodic"):
-    """Gate list of U_L (LAYOUT.md "U_L, in time order"); bc "periodic" or
+    """Gate list of U_L in time order (Fig. L's block structure); bc "periodic" or
     "bounceback" (reading R2)."""
     if bc not in ("periodic", "bounceback"):
         raise ValueError(bc)

@@ -1,7 +1,9 @@
 """Register layout and the embedding of physics indices into the qubit register.
 
-Test infrastructure only.  Implements the "Qubits" and "Physical states"
-sections of ``oracle/LAYOUT.md`` in plain Python.  The register sizes follow
+Test infrastructure only.  Registers, little-endian from bit 0: t, s, iL, q1,
+a1, then (N_C = 2) q2, a2, ord, then k and m.  A basis state is physical when
+t, s and iL are 0, every velocity is at most 2 and, for N_C = 2 and ord = 0,
+q2 = a2 = 0.  The register sizes follow
 the paper: n_alpha = ceil(log2 Nx) (Sec. II.D.2), n_k = ceil(log2(K+1)),
 n_m = ceil(log2(Nt)+1), n_i^L = max(1 + n_i^A, 2 + n_k) (Sec. II.D.4), and the
 I/O qubit count reproduces Table qubit-count (plus one signal qubit).

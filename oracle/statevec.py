@@ -11,7 +11,7 @@ Test infrastructure only.  Three independent ways to apply a gate list:
                       storing only non-zero amplitudes (used for the
                       block-encoding sweep of App. B).
 
-Gate semantics (``oracle/LAYOUT.md``): the 2x2 matrix G acts on the target
+Gate semantics: the 2x2 matrix G acts on the target
 qubit of every basis pair whose index satisfies (index & cmask) == cval.
 """
 from __future__ import annotations

@@ -36,7 +36,10 @@ double v11(int qo, int io, double tau);
 double max_abs_A(double tau, int NC, int bc = CSIM_BC_PERIODIC);
 double lmax_value(double tau, int NC, double dt, int bc = CSIM_BC_PERIODIC);
 
-// Gate lists (the canonical construction of oracle/LAYOUT.md).
+// Gate lists of the ancilla-free construction: U_A as one permutation of
+// (site, velocity, label) followed by RY value encodings on t, U_L as the
+// Taylor / coupling / identity label classes over (k, m), the QSVT wrapper
+// with signal Hadamards and projector phases (Fig. circuit-qsvt).
 std::vector<Gate> build_UL(const Layout& L, double tau, double dt);
 std::vector<Gate> dagger(const std::vector<Gate>& g);
 std::vector<Gate> phase_gates(const Layout& L, double phi);

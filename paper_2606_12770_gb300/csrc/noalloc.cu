@@ -60,8 +60,11 @@ struct Amp<double> {
   using V = double2;
 };
 
+// |a|^2 of the amplitudes in one 16-byte vector, every product in FP64 (the
+// reduction is bandwidth-bound, so widening first costs nothing measurable).
 __device__ __forceinline__ double sq16(const float4 v) {
-  return (double)(v.x * v.x + v.y * v.y) + (double)(v.z * v.z + v.w * v.w);
+  const double x = v.x, y = v.y, z = v.z, w = v.w;
+  return (x * x + y * y) + (z * z + w * w);
 }
 __device__ __forceinline__ double sq16(const double2 v) { return v.x * v.x + v.y * v.y; }
 
@@ -126,23 +129,30 @@ __global__ void norms_final_noalloc(const double* __restrict__ scratch, int nblo
   }
 }
 
-// Device address of g_norm_scratch on the current device, looked up once
-// per device while that device is current. The lookup can load the module
-// on that device, which is not allowed while a stream is being captured.
-// Hence the first call on each device must come before any capture.
+// Device address of g_norm_scratch on the current device, looked up while
+// that device is current.  The lookup can load the module on that device,
+// which is not allowed while a stream is being captured; hence the first
+// call on each device should come before any capture.  Only a successful
+// lookup is cached: after a failure (a capture in progress, say) the next
+// call tries again, and the failure's non-sticky error is cleared so that it
+// does not surface in the caller's next cudaGetLastError.
 void* g_scratch_ptr[kMaxDevices] = {};
-std::once_flag g_scratch_once[kMaxDevices];
-cudaError_t g_scratch_err[kMaxDevices] = {};
+std::mutex g_scratch_mu[kMaxDevices];
 
 cudaError_t scratch_on_current_device(int dev, double** out) {
-  std::call_once(g_scratch_once[dev], [dev] {
+  std::lock_guard<std::mutex> lk(g_scratch_mu[dev]);
+  if (g_scratch_ptr[dev] == nullptr) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_norm_scratch);
-    g_scratch_err[dev] = e;
-    if (e == cudaSuccess) g_scratch_ptr[dev] = p;
-  });
+    if (e != cudaSuccess || p == nullptr) {
+      (void)cudaGetLastError();
+      *out = nullptr;
+      return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    }
+    g_scratch_ptr[dev] = p;
+  }
   *out = static_cast<double*>(g_scratch_ptr[dev]);
-  return g_scratch_err[dev];
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -166,6 +176,8 @@ extern "C" csim_status csim_norms_noalloc(const void* d_state, int32_t n, csim_p
                                            std::to_string(kNoAllocMaxPatterns));
   if ((reinterpret_cast<uintptr_t>(d_state) & 15) != 0)
     return na_fail(CSIM_ERR_ARG, "csim_norms_noalloc: state must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(d_out) & 7) != 0)
+    return na_fail(CSIM_ERR_ARG, "csim_norms_noalloc: d_out must be 8-byte aligned");
   const uint64_t N = 1ull << n;
   Patterns pat{};
   for (int k = 0; k < npat; ++k) {

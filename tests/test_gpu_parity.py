@@ -302,11 +302,28 @@ print("ok")
 '''
 
 
-@pytest.mark.parametrize("conj", ["1", "0"])
-@pytest.mark.parametrize("src", ["1", "0"])
-@pytest.mark.parametrize("waves", ["4", "1"])
-@pytest.mark.parametrize("form", ["gather", "scatter"])
-@pytest.mark.parametrize("cfg", ["1,1", "2,1", "4,1", "1,2", "2,2", "4,2", "1,4", "2,4"])
+def _variant_cases():
+    """The launch variants worth running: every (tiles per iteration, blocks
+    per SM) variant in both forms with four resident waves; single-wave grids
+    on three variants; the lookup-table chain on the default gather variant;
+    separate permutation sweeps (no conjugation) on the two default
+    variants."""
+    cfgs = ["1,1", "2,1", "4,1", "1,2", "2,2", "4,2", "1,4", "2,4"]
+    out = []
+    for form in ("gather", "scatter"):
+        for cfg in cfgs:
+            out.append((cfg, form, "4", "1", "1"))
+        for cfg in ("1,4", "2,4", "4,2"):
+            out.append((cfg, form, "1", "1", "1"))
+    out.append(("2,4", "gather", "4", "0", "1"))
+    out.append(("2,4", "gather", "1", "0", "1"))
+    out.append(("2,4", "gather", "4", "1", "0"))
+    out.append(("1,2", "gather", "4", "1", "0"))
+    out.append(("2,4", "gather", "4", "0", "0"))
+    return out
+
+
+@pytest.mark.parametrize("cfg,form,waves,src,conj", _variant_cases())
 def test_sweep_kernel_variants(cfg, form, waves, src, conj):
     """Every compiled sweep-kernel variant (tiles per iteration, blocks per SM,
     form); one resident wave makes each warp loop over several tiles at 20
@@ -317,12 +334,6 @@ def test_sweep_kernel_variants(cfg, form, waves, src, conj):
     import os
     import subprocess
     import sys
-    if waves == "1" and cfg not in ("1,4", "2,4", "4,2"):
-        pytest.skip("single-wave grids are checked on three variants")
-    if src == "0" and (form != "gather" or cfg != "2,4"):
-        pytest.skip("the lookup-table chain is checked on the default gather variant")
-    if conj == "0" and (form != "gather" or cfg not in ("2,4", "1,2") or waves != "4"):
-        pytest.skip("separate permutation sweeps are checked on the default variants")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, CSIM_SWEEP_CFG=cfg, CSIM_SWEEP_FORM=form, CSIM_SWEEP_WAVES=waves,
                CSIM_SRC_INDEX=src, CSIM_CONJUGATE=conj)

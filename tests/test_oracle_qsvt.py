@@ -92,13 +92,37 @@ def test_inverse_target_minimal_residual(kappa, d):
     assert np.max(np.abs(Pf(-x) + Pf(x))) < 1e-12
 
 
-def test_degree_formula():
-    """Eq. d-star with eps = 1e-3, rounded up to odd."""
-    for kappa in (7.0, 294.31456452027527, 7100.0):
-        d = Q.degree_from_kappa(kappa, 1e-3)
-        raw = kappa * math.log(2 * kappa / 1e-3) / 2
-        assert d % 2 == 1 and raw <= d <= raw + 2
-    assert Q.degree_from_kappa(294.31456452027527, 1e-3) == 1957
+def _golden_kappa(row: int) -> float:
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "kappa.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return float(rows[row][5])
+
+
+def test_degree_matches_paper_ratio():
+    """Eq. d-star is pinned by the paper's own statement next to it (Sec. III.F.2):
+    with eps = 1e-3 the degree comes to d/kappa of about 7 in the setup of
+    Fig. qsvt-d-comparison, whose kappa(L) the paper prints as about 800
+    (golden kappa table, first row).  The natural logarithm gives 7.14; a
+    base-2 or base-10 logarithm (10.3, 3.1), a missing factor 1/2 (14.3) or a
+    missing factor 2 inside the logarithm (6.8) all fall outside the band."""
+    kappa = _golden_kappa(0)
+    assert kappa == 800
+    d = Q.degree_from_kappa(kappa, 1e-3)
+    assert d % 2 == 1
+    assert 6.9 <= d / kappa <= 7.3
+    # "rounded up to the next odd integer": every result is odd, never below
+    # a neighbouring smaller kappa's and growing with 1/eps.
+    prev = 0
+    for k in (7.0, 50.0, 294.31456452027527, 799.4, 800.0, 7100.0):
+        dk = Q.degree_from_kappa(k, 1e-3)
+        assert dk % 2 == 1 and dk >= prev
+        assert Q.degree_from_kappa(k, 1e-4) >= dk
+        prev = dk
+    # one decade of eps adds kappa * ln(10) / 2 to the degree (up to rounding)
+    k = 7100.0
+    gain = (Q.degree_from_kappa(k, 1e-4) - Q.degree_from_kappa(k, 1e-3)) / k
+    assert abs(gain - 1.1513) < 3.0 / k
 
 
 @pytest.mark.parametrize("cfg", [(4, 0.8, 2, 2, 0.1, 2), (8, 0.7, 1, 3, 0.2, 3)])

@@ -6,7 +6,9 @@ complex64 state with a smaller grid, so a stale partial sum left in the shared
 scratch array by the first call would show up in the second.  Tolerances:
 complex128, both paths accumulate in FP64 and differ only in summation order,
 1e-12 relative; complex64, csim_postselect adds eight FP32 products in FP32
-before its FP64 accumulation (relative error below 8 * 2^-24 = 5e-7), 1e-6.
+before its FP64 accumulation (relative error below 8 * 2^-24 = 5e-7), 1e-6,
+while this entry point forms every product in FP64, so against the host sum
+of the same values it is held to 1e-12 as well.
 """
 import numpy as np
 import pytest
@@ -73,7 +75,53 @@ def test_noalloc_norms_match_postselect_twice():
     torch.cuda.synchronize()
     tot2, sel2 = out.cpu().tolist()
     assert _close(tot2, t2, TOL_C64) and _close(sel2, p2), (tot2, t2, sel2, p2)
+    # against the host sum of the same complex64 values, widened: both sides
+    # form every product in FP64, so only the summation order differs
+    hs2, ht2 = _masked_norm_host(psi2.astype(np.complex128), pm2, pv2)
+    assert _close(tot2, ht2) and _close(sel2, hs2), (tot2, ht2, sel2, hs2)
     assert sel2 != sel1
+
+
+@pytest.mark.parametrize("prec", [G.CSIM_C128, G.CSIM_C64])
+def test_noalloc_edge_patterns(prec):
+    """Edge paths of the candidate enumeration on an 8-qubit random state: no
+    pattern (the masked sum is exactly 0), one pattern that fixes every index
+    bit (a single candidate), and two full patterns that share only their low
+    bits; each against the host sum."""
+    torch = pytest.importorskip("torch")
+    n = 8
+    rng = np.random.default_rng(11)
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    if prec == G.CSIM_C64:
+        psi = psi.astype(np.complex64)
+        dev = torch.from_numpy(psi.view(np.float32).copy()).cuda()
+    else:
+        dev = torch.from_numpy(psi.view(np.float64).copy()).cuda()
+    wide = psi.astype(np.complex128)
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    full = (1 << n) - 1
+    cases = [([], []), ([full], [0x5A]), ([full, full], [0x13, 0xF3])]
+    for pm, pv in cases:
+        out.fill_(float("nan"))
+        N.norms_noalloc(dev.data_ptr(), n, prec, np.array(pm, dtype=np.uint64),
+                        np.array(pv, dtype=np.uint64), out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        tot, sel = out.cpu().tolist()
+        hs, ht = _masked_norm_host(wide, pm, pv)
+        assert _close(tot, ht) and _close(sel, hs), (pm, pv, tot, ht, sel, hs)
+        if not pm:
+            assert sel == 0.0
+        if len(pm) == 1:
+            assert sel == pytest.approx(abs(wide[pv[0]]) ** 2, rel=1e-15)
+
+
+def test_noalloc_rejects_misaligned_output():
+    torch = pytest.importorskip("torch")
+    buf = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(G.CsimError) as e:
+        N.norms_noalloc(buf.data_ptr(), 4, G.CSIM_C128, [], [], buf.data_ptr() + 4)
+    assert e.value.status == -1
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits():
