@@ -85,6 +85,26 @@ bool tile_order_enabled() {
   return v;
 }
 
+// Fast tile bits of the in-place conjugated sweeps, replacing the model's
+// choice (CSIM_CONJ_FAST_BITS="b0,b1,..."; tile-index bits, most useful
+// first).  Empty when unset.
+const std::vector<int>& conj_fast_override() {
+  static const std::vector<int> v = [] {
+    std::vector<int> r;
+    const char* e = std::getenv("CSIM_CONJ_FAST_BITS");
+    if (!e) return r;
+    for (const char* q = e; *q;) {
+      char* end = nullptr;
+      const long b = std::strtol(q, &end, 10);
+      if (end == q) break;
+      if (b >= 0 && b < 32 && (int)r.size() < kMaxFast) r.push_back((int)b);
+      q = (*end == ',') ? end + 1 : end;
+    }
+    return r;
+  }();
+  return v;
+}
+
 bool perm_eligible(const csim_gate& g) {
   return g.op == OP_X && g.target >= 2 && (g.cmask & 3ull) == 0;
 }
@@ -888,6 +908,12 @@ bool emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vecto
     }
     sp.nfast = (int)hit->second.size();
     std::memcpy(sp.fast, hit->second.data(), hit->second.size());
+    if (sp.inplace && !conj_fast_override().empty()) {
+      const std::vector<int>& ov = conj_fast_override();
+      sp.nfast = 0;
+      for (int b : ov)
+        if (b < p->n - 7) sp.fast[sp.nfast++] = (uint8_t)b;
+    }
     if (const char* dbg = std::getenv("CSIM_FUSE_STATS")) {
       if (dbg[0] == '2' && p->n >= 24) {
         std::vector<int> fb(sp.fast, sp.fast + sp.nfast), none;
