@@ -30,3 +30,71 @@ def test_counts_grow_with_grid_size():
         assert sum(GC.histogram(g).values()) == len(g)
         tot.append(e["TOFFOLI"])
     assert all(b > a for a, b in zip(tot, tot[1:]))
+
+
+def _small_ul():
+    c = G.Circuit(2, 0.8, 1, 1, 0.1, 1, kappa_qsvt=10.0, d=3)
+    return c.export_gates(0), c.info()["n_qubits"]
+
+
+def test_expansion_and_peephole_preserve_the_operator():
+    """The V-chain expansion of one U_L (N_C = 1, Nx = 2: 10 qubits plus the
+    chain's ancillas), before and after the peephole pass, applied by the
+    oracle's naive simulator to a random register state with the ancillas in
+    0, equals the compiled gate list applied to the register alone, and
+    leaves every ancilla in 0."""
+    import numpy as np
+    from oracle import statevec as S
+    g, n = _small_ul()
+    elem, na = GC.expand(g, n)
+    pe = GC.peephole(elem)
+    assert 0 < len(pe) < len(elem)
+    rng = np.random.default_rng(5)
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    psi /= np.linalg.norm(psi)
+    ref = S.DenseSim(n).run(psi.copy(), [tuple(x) for x in
+                                          ((int(r["op"]), int(r["target"]), int(r["cmask"]),
+                                            int(r["cval"]), float(r["angle"]), 0) for r in g)])
+    for lst in (elem, pe):
+        big = np.zeros(1 << (n + na), dtype=complex)
+        big[: 1 << n] = psi
+        out = S.DenseSim(n + na).run(big, [x + (0,) for x in lst])
+        assert np.linalg.norm(out[1 << n:]) < 1e-13
+        assert np.linalg.norm(out[: 1 << n] - ref) < 1e-12
+
+
+def test_peephole_cancels_only_identical_adjacent_pairs():
+    X = 0
+    tof = (X, 5, 0b11, 0b11, 0.0)
+    # T T -> nothing; X X -> nothing; T (X on another qubit) T -> nothing
+    assert GC.peephole([tof, tof]) == []
+    assert GC.peephole([(X, 2, 0, 0, 0.0), (X, 2, 0, 0, 0.0)]) == []
+    assert GC.peephole([tof, (X, 7, 0, 0, 0.0), tof]) == [(X, 7, 0, 0, 0.0)]
+    # a gate on a shared qubit in between blocks the pair
+    blk = (X, 0, 0, 0, 0.0)
+    assert GC.peephole([tof, blk, tof]) == [tof, blk, tof]
+    # nested pairs: T1 T2 T2 T1 -> nothing
+    tof2 = (X, 6, 0b101, 0b101, 0.0)
+    assert GC.peephole([tof, tof2, tof2, tof]) == []
+    # CNOT pairs and rotations are left alone (the paper's pass removes
+    # Toffoli and X-X pairs only)
+    cn = (X, 3, 0b1, 0b1, 0.0)
+    assert GC.peephole([cn, cn]) == [cn, cn]
+
+
+def test_interpolated_count_matches_direct_count():
+    """Sec. III.F.2: the QSVT gate count is linear in d, so the counts at
+    d = 3 and d = 13 interpolate to any odd degree; checked against a direct
+    count at d = 31, with and without the peephole pass."""
+    def build(d):
+        return G.Circuit(4, 0.8, 1, 2, 0.1, 2, kappa_qsvt=10.0, d=d).export_gates(1)
+    for pp in (False, True):
+        est = GC.interpolated_counts(build, 31, peephole_pass=pp)
+        direct = GC.elementary_counts(build(31), peephole_pass=pp)
+        assert set(est) == set(direct)
+        for k, v in direct.items():
+            assert abs(est[k] - v) < 1e-9, (pp, k, est[k], v)
+    # the peephole pass removes Toffolis in the whole circuit
+    full = GC.elementary_counts(build(13))
+    pp = GC.elementary_counts(build(13), peephole_pass=True)
+    assert pp["TOFFOLI"] < full["TOFFOLI"] and pp["RY"] == full["RY"]
