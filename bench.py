@@ -13,8 +13,13 @@ csim_postselect (FP64 norm and success probability).  The metric is
 amplitude-gate updates per second: the sum over the circuit's elementary
 gates of the amplitudes each gate changes, divided by the step time.
 
-Output: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-(naive gate-by-gate simulator) on a bounded sample instead.
+Output: one JSON line (rank 0).  Outside the timed region the line also
+carries the oracle beside the GPU numbers (cpu_baseline: the classical QSVT
+evaluator on the whole workload, one thread and all cores, and the naive
+simulator's per-update rate) and, for the precision workloads, the plain
+gate-by-gate complex128 GPU path on the same circuit with each result's
+relative L2 error against the oracle.  --impl reference times the oracle's
+classical evaluator on the same workload instead (one thread per step).
 """
 from __future__ import annotations
 
@@ -175,16 +180,23 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def oracle_sample(seconds_target=15.0):
-    """Naive FP64 simulator on a bounded prefix of the plain (20-qubit) circuit."""
+def oracle_sample(workload, seconds_target=15.0):
+    """Naive FP64 gate-by-gate simulator (O2) on a bounded prefix of the
+    workload's circuit family at Nx = 4: the same construction, K, Nt, tau,
+    degree and kappa_QSVT, 24 qubits for the precision workloads (their 32
+    qubits need 64 GB of FP64 state plus the simulator's index tables).  The
+    rate is per amplitude update, which the naive simulator spends at about
+    the same cost at any size."""
     from oracle import circuit as OC
     from oracle import statevec as S
     from oracle.layout import Layout
 
-    cfg = (4, 0.8, 2, 2, 0.1, 2)
-    lay = Layout(4, 2, 2, 2)
-    f0, _ = I.lbm_instance(4, 0, tau=0.8)
-    gates = OC.build_qsvt(*cfg, list(I.random_phases(13, 0)))
+    Nx, NC, K, Nt, dt, tau, tau_range, seed, d, kappa, prec = WORKLOADS.get(workload,
+                                                                             WORKLOADS[DEFAULT])
+    Nx = 4
+    f0, tau = I.lbm_instance(Nx, seed, tau=tau, tau_range=tau_range)
+    lay = Layout(Nx, NC, K, Nt)
+    gates = OC.build_qsvt(Nx, tau, NC, K, dt, Nt, list(I.random_phases(d if d else 13, 0)))
     psi = np.zeros(1 << lay.n, dtype=complex)
     init, _ = OC.initial_state(lay, f0)
     for k, v in init.items():
@@ -200,11 +212,94 @@ def oracle_sample(seconds_target=15.0):
             count += 1
             if time.perf_counter() - t0 > seconds_target:
                 break
-    dt = time.perf_counter() - t0
-    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{count} gates ({len(gates)} per pass) of the 20-qubit plain circuit (Nx=4, "
-                      f"N_C=2, K=2, Nt=2, d=13) through the naive FP64 gate-by-gate simulator, "
-                      f"{dt:.1f} s; the 32-qubit state does not fit the oracle"}
+    dt_s = time.perf_counter() - t0
+    return {"value": upd / dt_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "seconds": dt_s,
+            "sample": f"{count} gates ({len(gates)} per pass) of the {lay.n}-qubit member (Nx=4, "
+                      f"N_C={NC}, K={K}, Nt={Nt}) of this workload's circuit family through the "
+                      f"naive FP64 gate-by-gate simulator (O2), {dt_s:.1f} s, per amplitude "
+                      f"update"}
+
+
+# Classical QSVT evaluation (O5) of a workload, run in a fresh interpreter so
+# that its thread count is fixed before NumPy loads.  Writes the postselected
+# physical block and its state indices when asked.
+O5_SCRIPT = r"""
+import json, sys, time
+import numpy as np
+a = json.loads(sys.argv[1])
+sys.path.insert(0, a["root"])
+from oracle import qsvt as Q
+f0 = np.asarray(a["f0"], dtype=np.float64)
+ph = np.asarray(a["phases"], dtype=np.float64)
+t0 = time.perf_counter()
+y, lay, _, _ = Q.qsvt_postselected(a["Nx"], a["tau"], a["NC"], a["K"], a["dt"], a["Nt"], f0, ph)
+sec = time.perf_counter() - t0
+if a.get("out"):
+    D = lay.carleman_dim()
+    base = np.array([lay.embed_index(0, j) for j in range(D)], dtype=np.int64)
+    off = np.array([lay.place(k=int(s) & ((1 << lay.nk) - 1), m=int(s) >> lay.nk)
+                    for s in range(lay.n_slots())], dtype=np.int64)
+    np.savez(a["out"], y=y, idx=(off[:, None] | base[None, :]).reshape(-1))
+print(json.dumps({"seconds": sec, "entries": int(y.size)}))
+"""
+
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def oracle_classical(cfg, f0, phases, threads=None, out=None):
+    """Seconds of one O5 evaluation (classical QSVT of the same phases on the
+    workload's L) in a fresh interpreter; threads=1 pins every math library
+    to one thread, None leaves them at their defaults (all cores)."""
+    Nx, tau, NC, K, dt, Nt = cfg
+    env = dict(os.environ)
+    for v in THREAD_VARS:
+        if threads is None:
+            env.pop(v, None)
+        else:
+            env[v] = str(threads)
+    arg = json.dumps({"root": ROOT, "Nx": Nx, "tau": tau, "NC": NC, "K": K, "dt": dt, "Nt": Nt,
+                      "f0": np.asarray(f0).tolist(), "phases": np.asarray(phases).tolist(),
+                      "out": out})
+    r = subprocess.run([sys.executable, "-c", O5_SCRIPT, arg], env=env, capture_output=True,
+                       text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("classical oracle failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_amp_updates(cfg, phases):
+    """Amplitude-gate updates of the whole circuit, counted on the oracle's own
+    gate list (O3): sum over gates of 2^(n - controls)."""
+    from oracle import circuit as OC
+    from oracle.layout import Layout
+    Nx, tau, NC, K, dt, Nt = cfg
+    lay = Layout(Nx, NC, K, Nt)
+    gates = OC.build_qsvt(Nx, tau, NC, K, dt, Nt, list(phases))
+    return float(sum(2.0 ** (lay.n - bin(g[2]).count("1")) for g in gates))
+
+
+def cpu_baselines(workload, cfg, f0, phases, updates, out=None):
+    """The oracle beside the GPU numbers: O5 at the whole workload, one thread
+    and all cores (its equivalent rate: the circuit's amplitude updates over
+    the time O5 takes to produce the same postselected block), and the naive
+    gate-by-gate simulator's per-update rate on a bounded sample."""
+    one = oracle_classical(cfg, f0, phases, threads=1, out=out)
+    allc = oracle_classical(cfg, f0, phases, threads=None)
+    naive = oracle_sample(workload, seconds_target=10.0)
+    cores = os.cpu_count()
+    return {"value": updates / one["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "seconds_per_run": one["seconds"],
+            "sample": (f"the whole workload through the oracle's classical QSVT evaluator (O5: "
+                       f"the circuit's polynomial of L applied to b with sparse products, "
+                       f"{one['entries']} physical entries), one thread, {one['seconds']:.2f} s; "
+                       f"value = the circuit's amplitude-gate updates over that time"),
+            "all_cores": {"value": updates / allc["seconds"], "seconds_per_run": allc["seconds"],
+                          "cores": cores,
+                          "note": "math libraries at their default thread count; the sparse "
+                                  "products themselves run on one thread"},
+            "naive_simulator": naive,
+            "host_cores": cores}
 
 
 def oracle_micro_sample(n, seconds_target=12.0):
@@ -224,7 +319,7 @@ def oracle_micro_sample(n, seconds_target=12.0):
         if time.perf_counter() - t0 > seconds_target:
             break
     dt = time.perf_counter() - t0
-    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": dt,
             "sample": f"first {count} gates of the vocabulary stream at {n} qubits through the "
                       f"naive FP64 gate-by-gate simulator, {dt:.1f} s (the benchmark's 2^30/2^33 "
                       f"states do not fit the oracle's FP64 copies in host memory in that time)"}
@@ -572,29 +667,67 @@ def run_serving(args, rank, world, local, torch, G, dist):
     _finish_line(args, line, world, dist)
 
 
+def _reference_inputs(workload):
+    """(cfg, f0, phases) of a workload for the oracle alone: the seeded
+    instance and, since O5's cost depends on the degree and not on the phase
+    values, seeded phases of the workload's degree (Eq. d-star from the
+    oracle's kappa(L) where the workload leaves d to the build)."""
+    from oracle import physics as OP
+    from oracle import qsvt as Q
+    Nx, NC, K, Nt, dt, tau, tau_range, seed, d, kappa, prec = WORKLOADS[workload]
+    f0, tau = I.lbm_instance(Nx, seed, tau=tau, tau_range=tau_range)
+    bc = BOUNDARY.get(workload, "periodic")
+    if d <= 0:
+        kap = kappa if kappa > 0 else OP.kappa_L(Nx, tau, NC, K, dt, Nt, bc=bc)
+        d = Q.degree_from_kappa(kap, 1e-3)
+    return (Nx, tau, NC, K, dt, Nt), f0, I.random_phases(d, 0)
+
+
 def run_reference(args, rank, world):
+    """The oracle on this arm's workload: each step is one classical QSVT
+    evaluation (O5) of the whole workload on one host thread, reported as the
+    circuit's amplitude-gate updates over its time; the microbenchmark
+    workloads, which have no classical evaluator, time the naive simulator."""
     if rank != 0:
         return
     W, K = args.warmup, args.steps
-    times = []
+    secs = []
     vals = []
-    for i in range(W + K):
-        if args.workload in MICRO:
-            r = oracle_micro_sample(22, seconds_target=args.ref_seconds)
-        else:
-            r = oracle_sample(seconds_target=args.ref_seconds)
-        if i >= W:
-            vals.append(r["value"])
-            times.append(args.ref_seconds)
+    extra = {}
+    if args.workload in WORKLOADS and BOUNDARY.get(args.workload, "periodic") == "periodic":
+        cfg, f0, ph = _reference_inputs(args.workload)
+        updates = oracle_amp_updates(cfg, ph)
+        r = None
+        for i in range(W + K):
+            r = oracle_classical(cfg, f0, ph, threads=1)
+            if i >= W:
+                secs.append(r["seconds"])
+                vals.append(updates / r["seconds"])
+        workload = args.workload
+        sample = (f"the whole workload ({args.workload}) per step through the oracle's classical "
+                  f"QSVT evaluator (O5, FP64, {r['entries']} physical entries, degree "
+                  f"{len(ph) - 1}), one thread; value = the circuit's amplitude-gate updates "
+                  f"({updates:.4g}, counted on the oracle's gate list) over its time")
+        extra["naive_simulator"] = oracle_sample(args.workload, seconds_target=8.0)
+    else:
+        n = 22
+        for i in range(W + K):
+            r = oracle_micro_sample(n, seconds_target=args.ref_seconds)
+            if i >= W:
+                secs.append(r["seconds"])
+                vals.append(r["value"])
+        workload = args.workload if args.workload in MICRO else f"microbench-n{n}-c128"
+        sample = r["sample"]
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": K, "warmup": W, "ms_per_step": 1000.0 * args.ref_seconds,
+            "steps": K, "warmup": W, "ms_per_step": 1000.0 * statistics.median(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "complex128 (fp64)", "data": "synthetic",
-            "config": {"workload": args.workload},
+            "config": {"workload": workload, "host_cores": os.cpu_count(), "threads": 1},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": r["sample"]},
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    line.update(extra)
     print(json.dumps(line), flush=True)
 
 
@@ -735,7 +868,7 @@ def main():
                           f"ping-pong buffers {2 * ((1 << n) * esz) / 1e6:.0f} MB; L2 129 MB)"
                           if ((1 << n) * esz) > L2_BYTES
                           else "state resident in L2 (smaller than 129 MB); no flush"),
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "host_cores": os.cpu_count()},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "kernel": "sweep_kernel", "peak_kind": f"{peak_kind} (STREAM-style copy)",
@@ -751,11 +884,74 @@ def main():
         line["roofline"]["note"] = ("complex128 sweeps are bound by the FP64 pipe (83-86% of its "
                                     "cycles busy), not by HBM; see the fp64 sweep profile")
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(seconds_target=12.0)
+        cfg = (Nx, tau, NC, K, dt, Nt)
+        fd, o5_path = tempfile.mkstemp(suffix=".npz")
+        os.close(fd)
+        try:
+            line["cpu_baseline"] = cpu_baselines(args.workload, cfg, f0, circ.export_phases(),
+                                                 updates, out=o5_path)
+            if args.workload.startswith("precision-") and args.exec == "fused":
+                line["precision_comparison"] = precision_comparison(
+                    torch, G, circ, cfg, f0, prec, o5_path, ms_per_step / 1000.0, stream)
+        finally:
+            os.unlink(o5_path)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _rel_l2_at(torch, dev_state, o5):
+    """Relative L2 distance of the device state's entries at the oracle's
+    physical indices from the oracle's block (both FP64 on the host)."""
+    t = torch.as_tensor(dev_state, device="cuda")
+    sel = t[torch.from_numpy(o5["idx"]).cuda()].double().cpu().numpy()
+    got = sel[:, 0] + 1j * sel[:, 1]
+    y = o5["y"]
+    return float(np.linalg.norm(got - y) / np.linalg.norm(y))
+
+
+def precision_comparison(torch, G, circ, cfg, f0, prec, o5_path, fused_s, stream):
+    """The precision configuration's comparison, outside the timed region: the
+    fused run just timed against the plain gate-by-gate complex128 GPU path on
+    the same circuit (one step, CUDA events), each result's relative L2 error
+    against the oracle's classical evaluation on the physical entries (all
+    time slots, t = s = label = 0)."""
+    with np.load(o5_path) as z:
+        o5 = {"y": z["y"], "idx": z["idx"]}
+    err_fused = _rel_l2_at(torch, circ.device_state(), o5)
+    ph = circ.export_phases()
+    Nx, tau, NC, K, dt, Nt = cfg
+    circ.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    plain = G.Circuit(Nx, tau, NC, K, dt, Nt, phases=ph)
+    plain.set_exec(G.CSIM_EXEC_GATE)
+    plain.compile()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    plain.init(f0, G.CSIM_C128, stream)
+    plain.run()
+    plain.postselect(want_amplitudes=False)
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain_s = a.elapsed_time(b) / 1000.0
+    err_plain = _rel_l2_at(torch, plain.device_state(), o5)
+    n_gates = plain.info()["n_gates_total"]
+    plain.close()
+    torch.cuda.empty_cache()
+    return {
+        "fused": {"dtype": "complex64" if prec == "c64" else "complex128", "s_per_run": fused_s,
+                  "runs_per_s": 1.0 / fused_s, "rel_l2_vs_oracle": err_fused,
+                  "tolerance": 1e-4 if prec == "c64" else 1e-12},
+        "plain_c128_gate_by_gate": {"s_per_run": plain_s, "runs_per_s": 1.0 / plain_s,
+                                    "rel_l2_vs_oracle": err_plain, "tolerance": 1e-12,
+                                    "launches": n_gates},
+        "runs_per_s_ratio": plain_s / fused_s,
+        "oracle": (f"classical QSVT evaluation (O5, FP64) of the same phases, compared on the "
+                   f"{o5['y'].size} physical entries"),
+    }
 
 
 if __name__ == "__main__":
