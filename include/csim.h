@@ -290,13 +290,15 @@ csim_status csim_sv_free(csim_sv* sv);
  * sweeps (lookup-table permutations, multiplexed rotations, warp-tile gates)
  * on the host in FP64 with the kernel's semantics.  amps: 2^n interleaved
  * complex values, updated in place (n in [7, 24]), or NULL to compile only and
- * report the statistics (n in [7, 34]).  For testing the fuser without a GPU.  If stats is non-NULL it receives 16 counters: sweeps,
- * single-gate steps, permutation gates, lookup tables, local gates,
- * multiplexers, multiplexed gates, multiplexer entries, largest bucket,
- * table entries, largest table support, HBM passes, averaging blocks,
- * multiplexers run as the inverse of the sweep's previous multiplexer,
- * Walsh-Hadamard ops (H on several lane bits fused), and in-place
- * conjugated sweeps (a permutation, tile ops and the inverse permutation). */
+ * report the statistics (n in [7, 34]).  For testing the fuser without a GPU.
+ * If stats is non-NULL it receives 18 counters: sweeps, single-gate steps,
+ * permutation gates, lookup tables, local gates, multiplexers, multiplexed
+ * gates, multiplexer entries, largest bucket, table entries, largest table
+ * support, HBM passes, averaging blocks, multiplexers run as the inverse of
+ * the sweep's previous multiplexer, Walsh-Hadamard ops (H on several lane
+ * bits fused), in-place conjugated sweeps (a permutation, tile ops and the
+ * inverse permutation), sweeps that stage qubits above the warp tile in
+ * registers, and gates on those staged qubits. */
 csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n, double* amps,
                                int64_t* stats);
 

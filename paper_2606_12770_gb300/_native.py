@@ -391,7 +391,7 @@ class StateVector:
 
 FUSE_STAT_NAMES = ["sweeps", "single", "perm_gates", "segments", "local_gates", "mux",
                    "mux_gates", "mux_entries", "max_bucket", "lut_entries", "max_support", "passes",
-                   "reflect", "mux_inverse", "wht", "conjugated"]
+                   "reflect", "mux_inverse", "wht", "conjugated", "staged_sweeps", "staged_gates"]
 
 
 def emulate_fused(gates, n, amps):
@@ -400,7 +400,7 @@ def emulate_fused(gates, n, amps):
     amps=None compiles only and returns (None, stats)."""
     lib = load()
     g = gates_to_records(gates)
-    st = np.zeros(16, dtype=np.int64)
+    st = np.zeros(len(FUSE_STAT_NAMES), dtype=np.int64)
     a = None if amps is None else np.ascontiguousarray(amps, dtype=np.complex128).copy()
     _check(lib.csim_emulate_fused(g.ctypes.data_as(C.c_void_p), g.shape[0], int(n),
                                   None if a is None else _dp(a.view(np.float64)),

@@ -912,10 +912,10 @@ csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n
   }
   if (stats) {
     const csim::FuseStats& f = p.stats;
-    const int64_t v[16] = {f.sweeps,      f.single,      f.perm_gates,  f.segments, f.local_gates,
+    const int64_t v[18] = {f.sweeps,      f.single,      f.perm_gates,  f.segments, f.local_gates,
                            f.mux,         f.mux_gates,   f.mux_entries, f.max_bucket,
                            f.lut_entries, f.max_support, p.passes,      f.reflect,  f.mux_inverse,
-                           f.wht,         f.conjugated};
+                           f.wht,         f.conjugated,  f.staged_sweeps, f.staged_gates};
     std::memcpy(stats, v, sizeof(v));
   }
   return CSIM_OK;

@@ -105,6 +105,18 @@ const std::vector<int>& conj_fast_override() {
   return v;
 }
 
+// High qubits a sweep may stage in registers (CSIM_STAGE=0..3; default 3):
+// gates on up to this many qubits above the warp tile join the sweep, which
+// then runs 2^k tiles per warp iteration.
+int stage_limit() {
+  static const int v = [] {
+    const char* e = std::getenv("CSIM_STAGE");
+    const int k = e ? std::atoi(e) : kMaxStage;
+    return (k >= 0 && k <= kMaxStage) ? k : kMaxStage;
+  }();
+  return v;
+}
+
 bool perm_eligible(const csim_gate& g) {
   return g.op == OP_X && g.target >= 2 && (g.cmask & 3ull) == 0;
 }
@@ -866,13 +878,24 @@ void choose_fast_bits(const std::vector<csim_gate>& perm, const Program& p, cons
 // through P^-1, applies the ops and stores back to the gathered addresses
 // (P^-1 . ops . P); returns whether it did.
 bool emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vector<csim_gate>& local,
-                bool conj = false) {
+                bool conj = false, const std::vector<int>& stage = {}) {
   const std::vector<PermSeg> segs = compile_perm(perm, p->scatter, p);
   const size_t first_param = p->params.size();
   std::vector<std::vector<PermSeg>> sc;
   for (size_t k = 0; k < segs.size(); k += kMaxSeg)
     sc.emplace_back(segs.begin() + k, segs.begin() + std::min(segs.size(), k + kMaxSeg));
-  std::vector<std::vector<OpItem>> oc = chunk_ops(compile_local(local, p));
+  std::vector<OpItem> ops = compile_local(local, p);
+  // gates on staged qubits (above the tile, not diagonal): ops 9-11 on the
+  // qubit's index in `stage`
+  for (OpItem& it : ops) {
+    LocalOp& o = it.op;
+    if (o.op > 2 || o.target < 7) continue;
+    const auto f = std::find(stage.begin(), stage.end(), (int)o.target);
+    o.op = (uint8_t)(9 + o.op);
+    o.target = (uint8_t)(f - stage.begin());
+    p->stats.staged_gates++;
+  }
+  std::vector<std::vector<OpItem>> oc = chunk_ops(ops);
   conj = conj && !p->scatter && sc.size() == 1 && oc.size() <= 1;
   if (conj) {
     emit_sweep(p, sc[0], oc.empty() ? std::vector<OpItem>() : oc[0]);
@@ -893,6 +916,17 @@ bool emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vecto
                oc.empty() ? std::vector<OpItem>() : oc.back());
     for (size_t k = 1; k < sc.size(); ++k) emit_sweep(p, sc[k], {});
   }
+  if (!stage.empty()) {
+    // every sweep of the group stages the same qubits: they are its first
+    // fast tile bits, and the gather's own order (below) follows them
+    for (size_t k = first_param; k < p->params.size(); ++k) {
+      SweepParams& sp = p->params[k];
+      sp.nstage = (int)stage.size();
+      sp.nfast = 0;
+      for (int q : stage) sp.fast[sp.nfast++] = (uint8_t)(q - 7);
+      p->stats.staged_sweeps++;
+    }
+  }
   if (p->scatter || !tile_order_enabled()) return conj;
   for (size_t k = first_param; k < p->params.size(); ++k) {
     SweepParams& sp = p->params[k];
@@ -905,6 +939,16 @@ bool emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vecto
       choose_fast_bits(perm, *p, sp, fast, &nfast);
       hit = p->order_cache.emplace(std::move(key), std::string(reinterpret_cast<char*>(fast), nfast))
                 .first;
+    }
+    if (sp.nstage > 0) {
+      // staged qubits first, then the gather's fast bits that are not staged
+      for (char b : hit->second) {
+        if (sp.nfast >= kMaxFast) break;
+        bool dup = false;
+        for (int j = 0; j < sp.nstage; ++j) dup = dup || sp.fast[j] == (uint8_t)b;
+        if (!dup) sp.fast[sp.nfast++] = (uint8_t)b;
+      }
+      continue;
     }
     sp.nfast = (int)hit->second.size();
     std::memcpy(sp.fast, hit->second.data(), hit->second.size());
@@ -951,6 +995,8 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
     return;
   }
   std::vector<csim_gate> perm, local;
+  std::vector<int> stage;  // staged qubits of the open group
+  const int kstage = (n - 7 >= 1) ? std::min(stage_limit(), n - 7) : 0;
   bool open = false;
   const double sweep_cost = std::ldexp(1.0, n);
   // groups and lone gates in circuit order; emitted after the scan so that a
@@ -958,6 +1004,7 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
   struct Item {
     bool group = false;
     std::vector<csim_gate> perm, local;
+    std::vector<int> stage;
     csim_gate g{};
   };
   std::vector<Item> items;
@@ -972,10 +1019,24 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
     it.group = true;
     it.perm = perm;
     it.local = local;
+    it.stage = stage;
     items.push_back(std::move(it));
     perm.clear();
     local.clear();
+    stage.clear();
     open = false;
+  };
+  // a non-diagonal gate above the tile joins the group as a staged-qubit gate
+  // when its target is staged already or a staging slot is free (gather form)
+  auto stageable = [&](const csim_gate& g) {
+    if (p->scatter || g.target < 7 || g.op == OP_ZPHASE) return false;
+    return std::find(stage.begin(), stage.end(), (int)g.target) != stage.end() ||
+           (int)stage.size() < kstage;
+  };
+  auto add_staged = [&](const csim_gate& g) {
+    if (std::find(stage.begin(), stage.end(), (int)g.target) == stage.end())
+      stage.push_back((int)g.target);
+    local.push_back(g);
   };
   auto commutes_all = [&](const csim_gate& g) {
     for (const csim_gate& l : local)
@@ -991,6 +1052,10 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
       }
       if (open && le) {
         local.push_back(g);
+        continue;
+      }
+      if (open && stageable(g)) {
+        add_staged(g);
         continue;
       }
     } else {  // scatter form: [local][perm]
@@ -1010,6 +1075,9 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
         (pe ? perm : local).push_back(g);
       else
         (le ? local : perm).push_back(g);
+    } else if (stageable(g)) {
+      open = true;
+      add_staged(g);
     } else {
       single(g);
     }
@@ -1048,7 +1116,7 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
     const bool conj = conjugation_enabled() && !p->scatter && !it.perm.empty() &&
                       k + 1 < items.size() && items[k + 1].group &&
                       reversed_equal(it.perm, items[k + 1].perm);
-    if (emit_group(p, it.perm, it.local, conj) && conj) items[k + 1].perm.clear();
+    if (emit_group(p, it.perm, it.local, conj, it.stage) && conj) items[k + 1].perm.clear();
   }
   p->passes = (int64_t)p->steps.size();
   for (const Step& s : p->steps)
@@ -1325,12 +1393,10 @@ uint32_t emu_permute(const Program& p, const SweepParams& sp, uint32_t x) {
   return x;
 }
 
-void emu_ops(const Program& p, const SweepParams& sp, uint32_t tile, double (&v)[32][4][2]) {
-  double mc[32], ms[32];  // the latest multiplexer's rotation per lane (op 7 inverts it)
-  for (int l = 0; l < 32; ++l) {
-    mc[l] = 1.0;
-    ms[l] = 0.0;
-  }
+// Ops [k0, k1) of a sweep on one tile.  mc / ms: the latest multiplexer's
+// rotation per lane (op 7 inverts it), carried across calls.
+void emu_ops(const Program& p, const SweepParams& sp, uint32_t tile, double (&v)[32][4][2],
+             int k0, int k1, double (&mc)[32], double (&ms)[32]) {
   auto rot_all = [&](uint32_t lane, int target, uint32_t lm, uint32_t lv, double c, double s) {
     for (int j0 = 0; j0 < 4; ++j0) {
       if (j0 & (1 << target)) continue;
@@ -1338,7 +1404,7 @@ void emu_ops(const Program& p, const SweepParams& sp, uint32_t tile, double (&v)
       pair_op(v[lane][j0], v[lane][j0 | (1 << target)], 2, c, s);
     }
   };
-  for (int k = 0; k < sp.nops; ++k) {
+  for (int k = k0; k < k1; ++k) {
     const LocalOp& o = sp.ops[k];
     if (o.op == 4) {
       const MuxDesc& md = sp.mux[o.cm];
@@ -1488,24 +1554,66 @@ void emulate_program(const Program& p, std::vector<double>* amps) {
     const SweepParams& sp = p.params[st.param];
     std::vector<double>& dst = (st.gather && !st.inplace) ? *nxt : *cur;
     const uint32_t ntiles = (uint32_t)(N >> 7);
-    for (uint32_t tile = 0; tile < ntiles; ++tile) {
-      double v[32][4][2];
-      uint32_t where[32];
-      for (uint32_t lane = 0; lane < 32; ++lane) {
-        const uint32_t ci = (tile << 5) | lane;
-        const uint32_t src = sp.scatter ? ci : emu_permute(p, sp, ci);
-        where[lane] = sp.scatter ? emu_permute(p, sp, ci) : (st.inplace ? src : ci);
-        for (int j = 0; j < 4; ++j) {
-          v[lane][j][0] = (*cur)[2 * (((size_t)src << 2) + j)];
-          v[lane][j][1] = (*cur)[2 * (((size_t)src << 2) + j) + 1];
+    // the 2^nstage tiles that differ in the staged qubits go together (one
+    // group of one tile without staging)
+    const int U = 1 << sp.nstage;
+    uint32_t smask = 0;
+    for (int j = 0; j < sp.nstage; ++j) smask |= 1u << sp.fast[j];
+    std::vector<std::array<std::array<std::array<double, 2>, 4>, 32>> vg((size_t)U);
+    std::vector<std::array<uint32_t, 32>> where((size_t)U);
+    std::vector<uint32_t> tiles((size_t)U);
+    std::vector<std::array<double, 32>> mcs((size_t)U), mss((size_t)U);
+    for (uint32_t base = 0; base < ntiles; ++base) {
+      if (base & smask) continue;
+      for (int u = 0; u < U; ++u) {
+        uint32_t t = base;
+        for (int j = 0; j < sp.nstage; ++j)
+          if ((u >> j) & 1) t |= 1u << sp.fast[j];
+        tiles[(size_t)u] = t;
+        for (uint32_t lane = 0; lane < 32; ++lane) {
+          const uint32_t ci = (t << 5) | lane;
+          const uint32_t src = sp.scatter ? ci : emu_permute(p, sp, ci);
+          where[(size_t)u][lane] = sp.scatter ? emu_permute(p, sp, ci) : (st.inplace ? src : ci);
+          for (int j = 0; j < 4; ++j) {
+            vg[(size_t)u][lane][j][0] = (*cur)[2 * (((size_t)src << 2) + j)];
+            vg[(size_t)u][lane][j][1] = (*cur)[2 * (((size_t)src << 2) + j) + 1];
+          }
         }
+        mcs[(size_t)u].fill(1.0);
+        mss[(size_t)u].fill(0.0);
       }
-      emu_ops(p, sp, tile, v);
-      for (uint32_t lane = 0; lane < 32; ++lane)
-        for (int j = 0; j < 4; ++j) {
-          dst[2 * (((size_t)where[lane] << 2) + j)] = v[lane][j][0];
-          dst[2 * (((size_t)where[lane] << 2) + j) + 1] = v[lane][j][1];
+      auto tile_v = [&](int u) -> double(&)[32][4][2] {
+        return *reinterpret_cast<double(*)[32][4][2]>(vg[(size_t)u].data());
+      };
+      auto tile_m = [&](std::vector<std::array<double, 32>>& m, int u) -> double(&)[32] {
+        return *reinterpret_cast<double(*)[32]>(m[(size_t)u].data());
+      };
+      for (int k = 0; k < sp.nops; ++k) {
+        const LocalOp& o = sp.ops[k];
+        if (o.op >= 9) {  // a gate on staged qubit o.target: pairs tiles u, u | bit
+          const int bit = 1 << o.target;
+          for (int u = 0; u < U; ++u) {
+            if (u & bit) continue;
+            for (uint32_t lane = 0; lane < 32; ++lane) {
+              const uint32_t ci = (tiles[(size_t)u] << 5) | lane;
+              if ((ci & o.cm) != o.cv) continue;
+              for (int j = 0; j < 4; ++j)
+                if (((uint32_t)j & o.lm) == o.lv)
+                  pair_op(vg[(size_t)u][lane][j].data(), vg[(size_t)(u | bit)][lane][j].data(),
+                          o.op - 9, o.cd, o.sd);
+            }
+          }
+          continue;
         }
+        for (int u = 0; u < U; ++u)
+          emu_ops(p, sp, tiles[(size_t)u], tile_v(u), k, k + 1, tile_m(mcs, u), tile_m(mss, u));
+      }
+      for (int u = 0; u < U; ++u)
+        for (uint32_t lane = 0; lane < 32; ++lane)
+          for (int j = 0; j < 4; ++j) {
+            dst[2 * (((size_t)where[(size_t)u][lane] << 2) + j)] = vg[(size_t)u][lane][j][0];
+            dst[2 * (((size_t)where[(size_t)u][lane] << 2) + j) + 1] = vg[(size_t)u][lane][j][1];
+          }
     }
     if (st.gather && !st.inplace) std::swap(cur, nxt);
   }

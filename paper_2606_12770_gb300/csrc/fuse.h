@@ -27,6 +27,8 @@ struct FuseStats {
   int64_t mux_inverse = 0;  // multiplexers run as the inverse of the sweep's previous one
   int64_t wht = 0;          // Walsh-Hadamard ops (H on several lane bits)
   int64_t conjugated = 0;   // in-place P^-1 . ops . P sweeps
+  int64_t staged_sweeps = 0;  // sweeps that stage qubits above the tile
+  int64_t staged_gates = 0;   // gates on staged qubits
 };
 
 struct Program {

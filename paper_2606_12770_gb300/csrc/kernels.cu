@@ -579,13 +579,13 @@ __device__ __forceinline__ void prefetch_mux(const SweepParams& a, const uint32_
 // or a lane bit (target 2-6), op 6 (ZPHASE above the tile) or op 8 (lane
 // Walsh-Hadamard), with the descriptor o.  The op code is a parameter so that
 // the shaped sweeps, which pass a constant, compile one path.
-template <typename R, int U>
+template <typename R, int U, bool WHT = true>
 __device__ __forceinline__ void op_tile_gate(uint32_t op, const LocalOp& o,
                                              typename V2<R>::T (&v)[U][4], const uint32_t (&ci)[U],
                                              uint32_t lane) {
   using T = typename V2<R>::T;
   const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv, tg = o.target;
-  if (op == 8) {  // H on each lane bit of the mask: butterflies, then one scale
+  if (WHT && op == 8) {  // H on each lane bit of the mask: butterflies, then one scale
 #pragma unroll
     for (int b = 0; b < 5; ++b) {
       if (!((ocm >> b) & 1u)) continue;
@@ -664,7 +664,58 @@ __device__ __forceinline__ void op_tile_gate(uint32_t op, const LocalOp& o,
   }
 }
 
+// X / H / RY (kind 0 / 1 / 2) on staged qubit J: the warp's tiles u and
+// u | (1 << J) hold the amplitudes with that qubit 0 and 1 at the same lane
+// and in-thread position, so the gate pairs their registers.  Controls come
+// from the chunk index of the tile with the qubit clear (a control never
+// includes the target) and from the in-thread bits.
+template <typename R, int U, int J>
+__device__ __forceinline__ void stage_pairs(uint32_t kind, const LocalOp& o,
+                                            typename V2<R>::T (&v)[U][4],
+                                            const uint32_t (&ci)[U]) {
+  const R c = Coef<R>::c(o), s = Coef<R>::s(o);
+  const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (u & (1 << J)) continue;
+    if ((ci[u] & ocm) != ocv) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (((uint32_t)j & lm) == lv) apply_pair<R>(v[u][j], v[u | (1 << J)][j], (int)kind, c, s);
+  }
+}
+
+template <typename R, int U>
+__device__ __forceinline__ void op_stage_gate(uint32_t kind, const LocalOp& o,
+                                              typename V2<R>::T (&v)[U][4],
+                                              const uint32_t (&ci)[U]) {
+  const uint32_t j = o.target;
+  if constexpr (U >= 2)
+    if (j == 0) return stage_pairs<R, U, 0>(kind, o, v, ci);
+  if constexpr (U >= 4)
+    if (j == 1) return stage_pairs<R, U, 1>(kind, o, v, ci);
+  if constexpr (U >= 8)
+    if (j == 2) return stage_pairs<R, U, 2>(kind, o, v, ci);
+}
+
 // Apply the tile-local ops of one sweep to U tiles held by the warp.
+// Gates only (ops 0-3, 6 and the staged-qubit ops 9-11): the interpreter of
+// gate streams, without the multiplexer, averaging-block and Walsh-Hadamard
+// code and its registers (the kernels that stage 2^k tiles per warp).
+template <typename R, int U>
+__device__ __forceinline__ void apply_gates(const SweepParams& a, typename V2<R>::T (&v)[U][4],
+                                            const uint32_t (&ci)[U], uint32_t lane) {
+  for (int k = 0; k < a.nops; ++k) {
+    const LocalOp& o = a.ops[k];
+    const uint32_t op = o.op;
+    if (op >= 9) {
+      op_stage_gate<R, U>(op - 9, o, v, ci);
+      continue;
+    }
+    op_tile_gate<R, U, false>(op, o, v, ci, lane);
+  }
+}
+
 template <typename R, int U>
 __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::T (&v)[U][4],
                                           const uint32_t (&ci)[U], uint32_t lane,
@@ -689,6 +740,10 @@ __device__ __forceinline__ void apply_ops(const SweepParams& a, typename V2<R>::
     }
     if (op == 5) {  // I (x) A + J (x) B over the lane bits of lanemask
       op_refl<R, U>(a.refl[ocm], v, lane);
+      continue;
+    }
+    if (op >= 9) {  // a gate on a staged qubit
+      op_stage_gate<R, U>(op - 9, o, v, ci);
       continue;
     }
     op_tile_gate<R, U>(op, o, v, ci, lane);
@@ -769,6 +824,8 @@ __device__ __forceinline__ void apply_shaped(const SweepParams& a, typename V2<R
                                 wd);
   } else if constexpr (SHAPE == 4) {
     apply_seq<R, U, ShapeLast>(std::make_integer_sequence<int, ShapeLast::n>{}, a, v, ci, lane, wd);
+  } else if constexpr (SHAPE == 5) {
+    apply_gates<R, U>(a, v, ci, lane);
   } else {
     apply_ops<R, U>(a, v, ci, lane, wd);
   }
@@ -921,7 +978,7 @@ __global__ void __launch_bounds__(256, MINB)
       }
     }
     uint32_t wd[kPrefetchMux][U];
-    if constexpr (SHAPE != 1) prefetch_mux<U>(a, ci, wd);
+    if constexpr (SHAPE != 1 && SHAPE != 5) prefetch_mux<U>(a, ci, wd);
     if (!a.scatter) {
       if (pre) {
 #pragma unroll
@@ -1360,6 +1417,42 @@ void launch_sweep_r(const void* in, void* out, uint32_t ntiles, int u, int minb,
   return launch_sweep_t<R, 1, 1>(in, out, ntiles, a, st);
 }
 
+// A sweep with staged qubits runs 2^nstage tiles per warp iteration (the
+// lean gate interpreter when it holds gates only); the resident blocks per SM
+// fall as the registers hold 2^nstage x 4 amplitudes a thread.
+// A sweep of gates only (no multiplexer, averaging block or Walsh-Hadamard
+// op) runs the lean interpreter (SHAPE 5).
+bool gates_only(const SweepParams& a) {
+  for (int k = 0; k < a.nops; ++k) {
+    const int op = a.ops[k].op;
+    if (op == 4 || op == 5 || op == 7 || op == 8) return false;
+  }
+  return true;
+}
+
+template <typename R, int U, int MINB>
+void launch_staged_u(const void* in, void* out, uint32_t ntiles, const SweepParams& a,
+                     cudaStream_t st) {
+  if (gates_only(a)) return launch_sweep_t<R, U, MINB, 5>(in, out, ntiles, a, st);
+  return launch_sweep_t<R, U, MINB, 0>(in, out, ntiles, a, st);
+}
+
+template <typename R>
+void launch_staged(const void* in, void* out, uint32_t ntiles, const SweepParams& a,
+                   cudaStream_t st) {
+  if (a.nstage == 1) {
+    if constexpr (sizeof(R) == 4) return launch_staged_u<R, 2, 4>(in, out, ntiles, a, st);
+    return launch_staged_u<R, 2, 2>(in, out, ntiles, a, st);
+  }
+  if (a.nstage == 2) {
+    if constexpr (sizeof(R) == 4) return launch_staged_u<R, 4, 2>(in, out, ntiles, a, st);
+    return launch_staged_u<R, 4, 1>(in, out, ntiles, a, st);
+  }
+  // eight tiles (32 complex64 or complex128 amplitudes a thread): one block
+  // per SM, the register file is the limit either way
+  return launch_staged_u<R, 8, 1>(in, out, ntiles, a, st);
+}
+
 }  // namespace
 
 cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
@@ -1368,6 +1461,18 @@ cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const Sweep
   if (((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 31u) != 0)
     return cudaErrorInvalidValue;
   const uint32_t ntiles = 1u << (n - 7);
+  if (a.nstage > 0) {
+    // the staged qubits are the first fast bits, all below the tile count
+    if (a.nstage > kMaxStage || a.nfast < a.nstage || a.scatter || (ntiles >> a.nstage) == 0)
+      return cudaErrorInvalidValue;
+    for (int j = 0; j < a.nstage; ++j)
+      if ((1u << a.fast[j]) >= ntiles) return cudaErrorInvalidValue;
+    if (prec == CSIM_C64)
+      launch_staged<float>(in, out, ntiles, a, st);
+    else
+      launch_staged<double>(in, out, ntiles, a, st);
+    return cudaGetLastError();
+  }
   const SweepCfg c = sweep_cfg();
   if (prec == CSIM_C64)
     launch_sweep_r<float>(in, out, ntiles, c.u64, c.minb64, a, st);
@@ -1467,6 +1572,7 @@ cudaError_t warm_r() {
   sweep_resident<R, 4, 2>();
   sweep_resident<R, 1, 4>();
   sweep_resident<R, 2, 4>();
+  sweep_resident<R, 8, 1>();
   return e;
 }
 }  // namespace

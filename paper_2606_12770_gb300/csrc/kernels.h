@@ -35,7 +35,10 @@ struct PermSeg {
 // the tile (target = its chunk-index bit, state bit - 2), 7 the inverse of the
 // sweep's latest multiplexed RY (the same rotation with the sine negated; its
 // target and bit 0-1 controls in target, lm, lv), 8 H on every lane bit of the
-// mask cm (no controls), followed by one scale 2^(-k/2) in cf / cd.
+// mask cm (no controls), followed by one scale 2^(-k/2) in cf / cd,
+// 9 / 10 / 11 X / H / RY on the staged qubit `target` (an index into the
+// sweep's staged qubits, see SweepParams::nstage): a 2 x 2 map between the
+// warp's tiles u and u ^ (1 << target), held in registers.
 struct LocalOp {
   uint32_t cm, cv;
   uint8_t lm, lv, op, target;
@@ -124,7 +127,14 @@ struct SweepParams {
   // is read as zeros.
   const uint32_t* zero_map;
   int zero_mode;
+  // Staged high qubits (gather or in-place sweeps; 0 = none, at most 3).  The
+  // sweep runs 2^nstage tiles per warp iteration, and its first nstage fast
+  // tile bits (fast[0..nstage-1], always honoured) are these qubits' tile
+  // bits (state bit - 7): the warp's tile u has bit j of u in fast[j].  Gates
+  // on those qubits (ops 9-11) then pair registers of two tiles of the warp.
+  int nstage;
 };
+constexpr int kMaxStage = 3;
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,
                         const double* d_val, int64_t count, cudaStream_t st);
