@@ -1027,9 +1027,14 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
     open = false;
   };
   // a non-diagonal gate above the tile joins the group as a staged-qubit gate
-  // when its target is staged already or a staging slot is free (gather form)
+  // when its target is staged already or a staging slot is free (gather
+  // form).  A permutation gate that cannot join the gather starts the next
+  // group's gather instead unless the group stages qubits already: that keeps
+  // the permutation runs of the QSVT circuit whole, so that a run and its
+  // inverse still meet in one conjugated sweep.
   auto stageable = [&](const csim_gate& g) {
     if (p->scatter || g.target < 7 || g.op == OP_ZPHASE) return false;
+    if (perm_eligible(g) && stage.empty()) return false;
     return std::find(stage.begin(), stage.end(), (int)g.target) != stage.end() ||
            (int)stage.size() < kstage;
   };

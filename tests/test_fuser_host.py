@@ -153,3 +153,23 @@ def test_averaging_block_detection_general():
     got, st = N.emulate_fused(g, n, psi)
     assert st["reflect"] == 1
     assert rel(got, S.DenseSim(n).run(psi.copy(), g)) < 1e-13
+
+
+def test_staged_sweeps_match_oracle_on_host():
+    """Gates on qubits above the warp tile join sweeps that hold 2^k tiles per
+    warp (k <= 3 staged qubits): the host executor of the fused program
+    against the dense oracle on seeded vocabulary streams, and the 30-qubit
+    stream needs far fewer passes than its 1505 gates."""
+    import numpy as np
+    import lbm_inputs as I
+    from oracle import statevec as S
+    from paper_2606_12770_gb300 import _native as N
+    for n, count, seed in ((12, 200, 1), (14, 300, 2)):
+        gates = I.microbench_gates(n, count, seed)
+        psi = I.random_unit_state(n, seed)
+        ref = S.DenseSim(n).run(psi.copy(), gates)
+        got, st = N.emulate_fused(gates, n, psi)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-13
+        assert st["staged_sweeps"] > 0 and st["staged_gates"] > 0
+    _, st = N.emulate_fused(I.microbench_gates(30, 1000, 0), 30, None)
+    assert st["passes"] <= 200
