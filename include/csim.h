@@ -331,6 +331,9 @@ typedef struct {
   uint64_t sparse_saved_bytes; /* state reads and writes that admitted requests'
                                   sparse inits left out: one state's bytes per
                                   request with one leading sweep, three with two */
+  int64_t failed;         /* requests that failed on the host before their device
+                             work (a refused pinned or arena allocation) */
+  int64_t cancelled;      /* csim_pool_cancel calls that took effect */
 } csim_pool_stats_t;
 
 csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out);
@@ -351,10 +354,33 @@ csim_status csim_pool_submit(csim_pool* p, csim_circuit* c, const double* f0,
 csim_status csim_pool_poll(csim_pool* p, int32_t wait_ms, int64_t* done, size_t cap,
                            size_t* n_done);
 /* Results of a finished request, as csim_postselect; times (may be NULL)
- * receives 3 doubles in seconds: queueing (submit to admission), submit to
- * retirement, device time of the request.  Releases the request record. */
+ * receives 5 doubles in seconds: queueing (submit to admission), submit to
+ * retirement, device time of the request, and its device start and end on
+ * the pool's clock (after an event recorded when the pool was created; -1
+ * for requests run inside a graph, whose events do not time).  Releases the
+ * request record.  A request that failed before its device work (see
+ * failures below) returns that error here, with its message, and is released
+ * too. */
 csim_status csim_pool_result(csim_pool* p, int64_t id, double* p_success, double* norm_total,
                              double* out_amps, size_t cap, size_t* len, double* times);
+/* Cancel a request.  A queued request leaves the queue at once; a running one
+ * cannot be stopped on the device, so its work finishes and its blocks are
+ * freed at retirement with the result dropped; a finished one is released.
+ * Either way the id is no longer reported or accepted, and whatever memory or
+ * slot this frees goes to the next queued requests.  CSIM_ERR_ARG for an
+ * unknown id.
+ *
+ * Failures of single requests: when a request's pinned staging (or, through
+ * csim_pool_inject, its arena blocks) cannot be allocated at admission, that
+ * request alone fails: it leaves the queue holding no memory, poll reports it,
+ * csim_pool_result returns CSIM_ERR_OOM, and the other requests proceed. */
+csim_status csim_pool_cancel(csim_pool* p, int64_t id);
+/* Host-side fault injection for tests: make an allocation of request `id`
+ * fail at its admission as if the host or the arena refused it
+ * (CSIM_INJECT_PINNED: the pinned staging; CSIM_INJECT_ARENA: the arena
+ * blocks; CSIM_INJECT_NONE clears).  Nothing is faulted on the device. */
+enum { CSIM_INJECT_NONE = 0, CSIM_INJECT_PINNED = 1, CSIM_INJECT_ARENA = 2 };
+csim_status csim_pool_inject(csim_pool* p, int32_t what, int64_t id);
 csim_status csim_pool_stats(const csim_pool* p, csim_pool_stats_t* out);
 /* Waits for running work, then frees everything (pending results are lost). */
 csim_status csim_pool_free(csim_pool* p);

@@ -19,6 +19,7 @@ CSIM_OK, CSIM_ERR_ARG, CSIM_ERR_TOO_LARGE, CSIM_ERR_OOM = 0, -1, -2, -3
 CSIM_ERR_CUDA, CSIM_ERR_STATE, CSIM_ERR_TIMEOUT, CSIM_ERR_NUMERIC = -4, -5, -6, -7
 CSIM_C64, CSIM_C128 = 0, 1
 CSIM_EXEC_FUSED, CSIM_EXEC_GATE = 0, 1
+CSIM_INJECT_NONE, CSIM_INJECT_PINNED, CSIM_INJECT_ARENA = 0, 1, 2
 _NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_TOO_LARGE", -3: "ERR_OOM", -4: "ERR_CUDA",
           -5: "ERR_STATE", -6: "ERR_TIMEOUT", -7: "ERR_NUMERIC"}
 
@@ -32,7 +33,7 @@ EXPORTED = [
     "csim_sv_load_device", "csim_sv_device", "csim_sv_stats", "csim_pool_create",
     "csim_pool_submit", "csim_pool_poll", "csim_pool_result", "csim_pool_stats", "csim_pool_free",
     "csim_pool_plan", "csim_compile", "csim_run_steps", "csim_checkpoint", "csim_restore",
-    "csim_final_distribution",
+    "csim_final_distribution", "csim_pool_cancel", "csim_pool_inject",
 ]
 
 
@@ -123,6 +124,8 @@ def load():
         "csim_pool_result": ([VP, C.c_int64, DP, DP, DP, SZ, SZP, DP], C.c_int),
         "csim_pool_stats": ([VP, VP], C.c_int),
         "csim_pool_free": ([VP], C.c_int),
+        "csim_pool_cancel": ([VP, C.c_int64], C.c_int),
+        "csim_pool_inject": ([VP, C.c_int32, C.c_int64], C.c_int),
         "csim_pool_plan": ([C.c_uint64, C.c_uint64, C.c_int32, SZ, P(C.c_uint64), DP, DP, DP, DP,
                             P(C.c_uint64)], C.c_int),
         "csim_norms_noalloc": ([VP, C.c_int32, C.c_int, P(C.c_uint64), P(C.c_uint64), C.c_int32,
@@ -444,7 +447,8 @@ class PoolStats(C.Structure):
                 ("rejected", C.c_int64), ("queued", C.c_int64), ("running", C.c_int64),
                 ("bytes_in_use", C.c_uint64), ("peak_bytes", C.c_uint64), ("budget", C.c_uint64),
                 ("graph_launches", C.c_int64), ("src_tables", C.c_int64),
-                ("sparse_saved_bytes", C.c_uint64)]
+                ("sparse_saved_bytes", C.c_uint64), ("failed", C.c_int64),
+                ("cancelled", C.c_int64)]
 
 
 class Pool:
@@ -493,7 +497,7 @@ class Pool:
         p = C.c_double()
         t = C.c_double()
         n = C.c_size_t()
-        times = np.zeros(3)
+        times = np.zeros(5)
         out = None
         if want_amplitudes:
             # the count is known from the circuit's geometry: ask with cap 0 first is not
@@ -508,7 +512,18 @@ class Pool:
                                          C.byref(n), _dp(times)))
         self._keep.pop(rid, None)
         return out, p.value, t.value, {"queue_s": times[0], "latency_s": times[1],
-                                       "device_s": times[2]}
+                                       "device_s": times[2], "device_start_s": times[3],
+                                       "device_end_s": times[4]}
+
+    def cancel(self, rid):
+        """csim_pool_cancel: drop a queued, running or finished request."""
+        _check(_lib.csim_pool_cancel(self._h, int(rid)))
+        self._keep.pop(rid, None)
+
+    def inject(self, what, rid):
+        """csim_pool_inject: host-side allocation failure of request rid at its
+        admission (CSIM_INJECT_PINNED or CSIM_INJECT_ARENA; NONE clears)."""
+        _check(_lib.csim_pool_inject(self._h, int(what), int(rid)))
 
     def stats(self):
         st = PoolStats()

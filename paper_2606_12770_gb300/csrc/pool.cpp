@@ -179,7 +179,11 @@ struct Request {
   int wave = -1;       // index into csim_pool::waves when launched in a graph
   double t_submit = 0, t_start = 0, t_done = 0;
   double p = 0, tot = 0, dev_ms = 0;
+  double dev_t0 = -1, dev_t1 = -1;  // device start / end after the pool's epoch (stream mode)
   std::vector<double> amps;
+  csim_status err = CSIM_OK;  // a request that failed on the host before its device work
+  std::string err_msg;
+  bool cancelled = false;     // discarded at retirement
 };
 
 struct Slot {
@@ -221,6 +225,9 @@ struct csim_pool {
   std::vector<Wave> waves;
   int64_t next_id = 1;
   csim_pool_stats_t stats{};
+  cudaEvent_t epoch = nullptr;  // recorded on the origin stream at creation
+  // host-side fault injection (csim_pool_inject): request id -> what fails
+  std::unordered_map<int64_t, int> inject;
 };
 
 namespace {
@@ -339,6 +346,20 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, bool in_graph, co
   return e;
 }
 
+// A request that fails before any of its device work is enqueued: it leaves
+// the queue with its error, holds no memory, and is reported by the next
+// poll like a finished one; the pool keeps serving the others.
+void fail_request(csim_pool* P, Request& r, csim_status err, const std::string& msg) {
+  release_all(&P->arena, r.offs, kAllocs);
+  for (uint64_t& o : r.offs) o = ~0ull;
+  r.err = err;
+  r.err_msg = msg;
+  r.st = RState::Done;
+  r.t_start = r.t_done = now_s();
+  P->stats.failed++;
+  if (!r.cancelled) P->done_unreported.push_back(r.id);
+}
+
 // Admit queued requests (FIFO) into free slots while their blocks fit.
 csim_status admit(csim_pool* P) {
   std::vector<std::pair<int64_t, int>> started;
@@ -351,12 +372,25 @@ csim_status admit(csim_pool* P) {
       }
     if (free_slot < 0) break;
     Request& r = P->reqs[P->queue.front()];
+    const auto inj = P->inject.find(r.id);
+    const int fault = inj == P->inject.end() ? 0 : inj->second;
+    if (fault == CSIM_INJECT_ARENA) {  // as if the arena refused the request's blocks
+      P->queue.pop_front();
+      fail_request(P, r, CSIM_ERR_OOM, "csim_pool: arena allocation refused (injected)");
+      continue;
+    }
     if (!alloc_all(&P->arena, r.sizes, r.offs, kAllocs)) break;
     Slot& s = P->slots[free_slot];
-    cudaError_t e = grow_pinned(&s, 16 * kMaxPatterns + r.idx.size() * 16, r.count * 16 + 16);
+    cudaError_t e = fault == CSIM_INJECT_PINNED
+                        ? cudaErrorMemoryAllocation
+                        : grow_pinned(&s, 16 * kMaxPatterns + r.idx.size() * 16, r.count * 16 + 16);
     if (e != cudaSuccess) {
-      release_all(&P->arena, r.offs, kAllocs);
-      return pcuda(e, "csim_pool: pinned staging");
+      cudaGetLastError();
+      P->queue.pop_front();
+      fail_request(P, r, CSIM_ERR_OOM,
+                   std::string("csim_pool: pinned staging: ") + cudaGetErrorString(e) +
+                       (fault == CSIM_INJECT_PINNED ? " (injected)" : ""));
+      continue;
     }
     s.req = r.id;
     r.slot = free_slot;
@@ -491,13 +525,27 @@ csim_status retire(csim_pool* P, int* n_retired) {
       r.dev_ms = ms;
     else
       cudaGetLastError();  // a failed timing query must not linger as the last error
+    if (r.wave < 0 && P->epoch) {  // the request's device interval on the pool's clock
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, P->epoch, s.ev0) == cudaSuccess &&
+          cudaEventElapsedTime(&b, P->epoch, s.ev1) == cudaSuccess) {
+        r.dev_t0 = a * 1e-3;
+        r.dev_t1 = b * 1e-3;
+      } else {
+        cudaGetLastError();
+      }
+    }
     r.t_done = now_s();
     r.st = RState::Done;
     release_all(&P->arena, r.offs, kAllocs);
     s.req = -1;
-    P->done_unreported.push_back(r.id);
     P->stats.completed++;
     ++*n_retired;
+    if (r.cancelled) {  // cancelled while running: its result is dropped
+      P->reqs.erase(r.id);
+      continue;
+    }
+    P->done_unreported.push_back(r.id);
   }
   P->stats.bytes_in_use = P->arena.in_use();
   bool busy = false;
@@ -534,6 +582,7 @@ void destroy_pool(csim_pool* P) {
     if (s.h_amps) cudaFreeHost(s.h_amps);
     if (s.st) cudaStreamDestroy(s.st);
   }
+  if (P->epoch) cudaEventDestroy(P->epoch);
   if (P->origin) cudaStreamDestroy(P->origin);
   if (P->d_arena) cudaFree(P->d_arena);
   delete P;
@@ -588,6 +637,8 @@ csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out) {
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_out, 2 * sizeof(double));
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&P->epoch);
+  if (e == cudaSuccess) e = cudaEventRecord(P->epoch, P->origin);
   // load every kernel and fill the launch-configuration caches now: a lazy
   // module load must not happen inside a graph capture
   if (e == cudaSuccess) e = csim::warm_kernels();
@@ -676,6 +727,12 @@ csim_status csim_pool_result(csim_pool* P, int64_t id, double* p_success, double
   if (it == P->reqs.end()) return pfail(CSIM_ERR_ARG, "unknown request id");
   Request& r = it->second;
   if (r.st != RState::Done) return pfail(CSIM_ERR_STATE, "request not finished");
+  if (r.err != CSIM_OK) {  // failed before its device work: report and release
+    const csim_status err = r.err;
+    const std::string msg = r.err_msg;
+    P->reqs.erase(it);
+    return pfail(err, msg);
+  }
   if (len) *len = r.count;
   if (out_amps) {
     if (cap < r.count) return pfail(CSIM_ERR_ARG, "out_amps too small");
@@ -687,8 +744,45 @@ csim_status csim_pool_result(csim_pool* P, int64_t id, double* p_success, double
     times[0] = r.t_start - r.t_submit;  // queueing
     times[1] = r.t_done - r.t_submit;   // submit to retirement
     times[2] = r.dev_ms * 1e-3;         // device time of the request's stream work
+    times[3] = r.dev_t0;                // device start and end after the pool's epoch,
+    times[4] = r.dev_t1;                // -1 for requests run inside a graph
   }
   P->reqs.erase(it);
+  return CSIM_OK;
+}
+
+csim_status csim_pool_cancel(csim_pool* P, int64_t id) {
+  if (!P) return pfail(CSIM_ERR_ARG, "null argument");
+  auto it = P->reqs.find(id);
+  if (it == P->reqs.end() || it->second.cancelled) return pfail(CSIM_ERR_ARG, "unknown request id");
+  Request& r = it->second;
+  P->stats.cancelled++;
+  if (r.st == RState::Queued) {
+    P->queue.erase(std::find(P->queue.begin(), P->queue.end(), id));
+    P->stats.queued = (int64_t)P->queue.size();
+    P->reqs.erase(it);
+  } else if (r.st == RState::Running) {
+    r.cancelled = true;  // its device work finishes; retirement frees it and drops the result
+  } else {
+    P->done_unreported.erase(std::remove(P->done_unreported.begin(), P->done_unreported.end(), id),
+                             P->done_unreported.end());
+    P->reqs.erase(it);
+  }
+  // memory or a slot may have been freed: admit what now fits
+  int n = 0;
+  csim_status s = retire(P, &n);
+  if (s == CSIM_OK) s = admit(P);
+  return s;
+}
+
+csim_status csim_pool_inject(csim_pool* P, int32_t what, int64_t id) {
+  if (!P) return pfail(CSIM_ERR_ARG, "null argument");
+  if (what != CSIM_INJECT_NONE && what != CSIM_INJECT_PINNED && what != CSIM_INJECT_ARENA)
+    return pfail(CSIM_ERR_ARG, "unknown fault kind");
+  if (what == CSIM_INJECT_NONE)
+    P->inject.erase(id);
+  else
+    P->inject[id] = what;
   return CSIM_OK;
 }
 

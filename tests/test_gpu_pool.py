@@ -91,3 +91,80 @@ def test_pool_rejects_requests_larger_than_the_budget():
         pool.submit(c, f0, G.CSIM_C128)
     assert e.value.status == -2
     pool.close()
+
+
+def _drain(pool, n, polls=20000):
+    done = []
+    for _ in range(polls):
+        done += pool.poll(wait_ms=20)
+        if len(done) >= n:
+            break
+    return done
+
+
+def test_pool_requests_overlap_on_device():
+    """Continuous batching runs requests side by side: in stream mode each
+    request's device interval (its first and last event on its stream, on the
+    pool's clock) is reported, and at least two admitted requests' intervals
+    intersect.  The requests are 24-26-qubit runs of d = 21, long enough that
+    one still runs when the next is admitted."""
+    specs = [((8, 0.7, 2, 2, 0.1, 2), 21), ((8, 0.9, 2, 3, 0.1, 3), 21),
+             ((4, 1.1, 2, 4, 0.1, 8), 21), ((8, 0.6, 2, 2, 0.1, 4), 21)]
+    inst = []
+    for k, (cfg, d) in enumerate(specs):
+        f0, _ = I.lbm_instance(cfg[0], 40 + k, tau=cfg[1])
+        inst.append((G.Circuit(*cfg, kappa_qsvt=10.0, d=d), f0))
+    pool = G.Pool(n_streams=4, max_qubits=30)
+    ids = [pool.submit(c, f0, G.CSIM_C64) for c, f0 in inst]
+    assert len(_drain(pool, len(ids))) == len(ids)
+    iv = []
+    for rid in ids:
+        _, _, _, times = pool.result(rid, want_amplitudes=False)
+        assert 0.0 <= times["device_start_s"] < times["device_end_s"]
+        iv.append((times["device_start_s"], times["device_end_s"]))
+    overlaps = sum(1 for i in range(len(iv)) for j in range(i + 1, len(iv))
+                   if iv[i][0] < iv[j][1] and iv[j][0] < iv[i][1])
+    print("device intervals (s):", [(round(a, 4), round(b, 4)) for a, b in iv],
+          "overlapping pairs:", overlaps)
+    assert overlaps >= 1
+    pool.close()
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_pool_failures_and_cancellation_leave_the_rest_intact(graphs):
+    """Host-side failures and cancellation inside a busy pool: request 3's
+    pinned staging and request 5's arena blocks are refused at admission
+    (injected on the host; nothing faults on the device), request 7 is
+    cancelled while queued and request 2 while it may be running.  The
+    failed requests report CSIM_ERR_OOM and hold no memory, the cancelled ones
+    are never reported, every other request equals its run alone bit for bit,
+    and the arena is empty at the end."""
+    alone = _alone(_instances())
+    inst = _instances()
+    pool = G.Pool(n_streams=2, hbm_budget=160 << 20, max_qubits=30, use_graphs=graphs)
+    # ids are assigned in submission order from 1: inject before submitting
+    pool.inject(G._native.CSIM_INJECT_PINNED, 3)
+    pool.inject(G._native.CSIM_INJECT_ARENA, 5)
+    ids = [pool.submit(c, f0, prec) for c, f0, prec in inst]
+    assert ids == list(range(1, len(inst) + 1))
+    pool.cancel(7)  # two slots: request 7 is still queued
+    pool.cancel(2)
+    with pytest.raises(G.CsimError):
+        pool.cancel(7)
+    expect = [i for i in ids if i not in (2, 7)]
+    done = _drain(pool, len(expect))
+    assert sorted(done) == expect
+    st = pool.stats()
+    assert st["failed"] == 2 and st["cancelled"] == 2
+    for rid in expect:
+        if rid in (3, 5):
+            with pytest.raises(G.CsimError) as e:
+                pool.result(rid)
+            assert e.value.status == -3
+            continue
+        amps0, p0, t0 = alone[rid - 1]
+        amps, p, t, _ = pool.result(rid)
+        assert np.array_equal(amps, amps0) and p == p0 and t == t0
+    pool.poll(wait_ms=100)
+    assert pool.stats()["bytes_in_use"] == 0
+    pool.close()
