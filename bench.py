@@ -80,6 +80,8 @@ SERVING = {"serving-poisson-200": 200}
 # Gate-vocabulary microbenchmark: (qubits, gates, seed); complex64, seeded
 # random normalised initial state generated on the device.
 MICRO = {
+    # 28 qubits (2 GiB): the same stream's fusion at a size for ncu captures
+    "microbench-n28-c64": (28, 1000, 0),
     "microbench-n30-c64": (30, 1000, 0),
     "microbench-n33-c64": (33, 1000, 0),
 }
