@@ -18,8 +18,9 @@ carries the oracle beside the GPU numbers (cpu_baseline: the classical QSVT
 evaluator on the whole workload, one thread and all cores, and the naive
 simulator's per-update rate) and, for the precision workloads, the plain
 gate-by-gate complex128 GPU path on the same circuit with each result's
-relative L2 error against the oracle.  --impl reference times the oracle's
-classical evaluator on the same workload instead (one thread per step).
+relative L2 error against the oracle.  --impl reference times the oracle
+instead: the naive simulator per amplitude update, one thread per step, with
+the classical evaluator's time on the whole workload beside it.
 """
 from __future__ import annotations
 
@@ -182,13 +183,13 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def oracle_sample(workload, seconds_target=15.0):
-    """Naive FP64 gate-by-gate simulator (O2) on a bounded prefix of the
-    workload's circuit family at Nx = 4: the same construction, K, Nt, tau,
-    degree and kappa_QSVT, 24 qubits for the precision workloads (their 32
-    qubits need 64 GB of FP64 state plus the simulator's index tables).  The
-    rate is per amplitude update, which the naive simulator spends at about
-    the same cost at any size."""
+def oracle_sample(workload, threads=1):
+    """The oracle's naive gate-by-gate simulator (O2, its tensor-axis form) on
+    one U_L call -- the unit the QSVT circuit repeats d times -- of the
+    workload's circuit family at Nx = 4: the same construction, K, Nt and
+    tau, 24 qubits for the precision workloads (their 32 qubits hold 64 GB of
+    FP64 state).  The rate is per amplitude update, which the naive simulator
+    spends at about the same cost at any size."""
     from oracle import circuit as OC
     from oracle import statevec as S
     from oracle.layout import Layout
@@ -198,29 +199,23 @@ def oracle_sample(workload, seconds_target=15.0):
     Nx = 4
     f0, tau = I.lbm_instance(Nx, seed, tau=tau, tau_range=tau_range)
     lay = Layout(Nx, NC, K, Nt)
-    gates = OC.build_qsvt(Nx, tau, NC, K, dt, Nt, list(I.random_phases(d if d else 13, 0)))
+    gates = OC.build_UL(Nx, tau, NC, K, dt, Nt, bc=BOUNDARY.get(workload, "periodic"))
     psi = np.zeros(1 << lay.n, dtype=complex)
     init, _ = OC.initial_state(lay, f0)
     for k, v in init.items():
         psi[k] = v
-    sim = S.DenseSim(lay.n)
-    upd = 0.0
-    count = 0
+    sim = S.AxisSim(lay.n, threads=threads)
+    upd = sum(2.0 ** (lay.n - bin(g[2]).count("1")) for g in gates)
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds_target:  # repeat the circuit up to the time target
-        for g in gates:
-            sim.apply(psi, g)
-            upd += 2.0 ** (lay.n - bin(g[2]).count("1"))
-            count += 1
-            if time.perf_counter() - t0 > seconds_target:
-                break
+    sim.run(psi, gates)
     dt_s = time.perf_counter() - t0
-    return {"value": upd / dt_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": upd / dt_s, "unit": UNIT, "cores": threads, "kind": "oracle",
             "seconds": dt_s,
-            "sample": f"{count} gates ({len(gates)} per pass) of the {lay.n}-qubit member (Nx=4, "
-                      f"N_C={NC}, K={K}, Nt={Nt}) of this workload's circuit family through the "
-                      f"naive FP64 gate-by-gate simulator (O2), {dt_s:.1f} s, per amplitude "
-                      f"update"}
+            "sample": f"one U_L call ({len(gates)} gates, {upd:.4g} amplitude updates) of the "
+                      f"{lay.n}-qubit member (Nx=4, N_C={NC}, K={K}, Nt={Nt}) of this workload's "
+                      f"circuit family through the oracle's naive FP64 gate-by-gate simulator "
+                      f"(O2, tensor-axis form, {threads} thread), {dt_s:.1f} s; per amplitude "
+                      f"update, which it spends at about the same cost at any size"}
 
 
 # Classical QSVT evaluation (O5) of a workload, run in a fresh interpreter so
@@ -282,26 +277,29 @@ def oracle_amp_updates(cfg, phases):
 
 
 def cpu_baselines(workload, cfg, f0, phases, updates, out=None):
-    """The oracle beside the GPU numbers: O5 at the whole workload, one thread
-    and all cores (its equivalent rate: the circuit's amplitude updates over
-    the time O5 takes to produce the same postselected block), and the naive
-    gate-by-gate simulator's per-update rate on a bounded sample."""
+    """The oracle beside the GPU numbers: the naive gate-by-gate simulator's
+    rate per amplitude update on a bounded sample (the metric's own unit),
+    and the classical QSVT evaluator (O5) on the whole workload, one thread
+    and all cores: the time it takes to produce the same postselected block,
+    with the circuit's amplitude updates over that time as an equivalent
+    rate."""
+    naive = oracle_sample(workload, threads=1)
     one = oracle_classical(cfg, f0, phases, threads=1, out=out)
     allc = oracle_classical(cfg, f0, phases, threads=None)
-    naive = oracle_sample(workload, seconds_target=10.0)
     cores = os.cpu_count()
-    return {"value": updates / one["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "seconds_per_run": one["seconds"],
-            "sample": (f"the whole workload through the oracle's classical QSVT evaluator (O5: "
-                       f"the circuit's polynomial of L applied to b with sparse products, "
-                       f"{one['entries']} physical entries), one thread, {one['seconds']:.2f} s; "
-                       f"value = the circuit's amplitude-gate updates over that time"),
-            "all_cores": {"value": updates / allc["seconds"], "seconds_per_run": allc["seconds"],
-                          "cores": cores,
-                          "note": "math libraries at their default thread count; the sparse "
-                                  "products themselves run on one thread"},
-            "naive_simulator": naive,
-            "host_cores": cores}
+    naive["host_cores"] = cores
+    naive["classical_o5"] = {
+        "what": (f"the whole workload through the oracle's classical QSVT evaluator (O5: the "
+                 f"circuit's polynomial of L applied to b with sparse products, "
+                 f"{one['entries']} physical entries); equivalent_value = the circuit's "
+                 f"amplitude-gate updates over its time"),
+        "one_thread": {"seconds_per_run": one["seconds"], "equivalent_value": updates / one["seconds"],
+                       "cores": 1},
+        "all_cores": {"seconds_per_run": allc["seconds"],
+                      "equivalent_value": updates / allc["seconds"], "cores": cores,
+                      "note": "math libraries at their default thread count; the sparse products "
+                              "themselves run on one thread"}}
+    return naive
 
 
 def oracle_micro_sample(n, seconds_target=12.0):
@@ -686,48 +684,49 @@ def _reference_inputs(workload):
 
 
 def run_reference(args, rank, world):
-    """The oracle on this arm's workload: each step is one classical QSVT
-    evaluation (O5) of the whole workload on one host thread, reported as the
-    circuit's amplitude-gate updates over its time; the microbenchmark
-    workloads, which have no classical evaluator, time the naive simulator."""
+    """The oracle on this arm's workload, in the metric's own unit: each step
+    is a bounded sample of the naive gate-by-gate simulator (O2): one U_L
+    call of the workload's circuit family at 24 qubits (a time-bounded
+    prefix of the vocabulary stream at 22 qubits for the microbenchmark
+    workloads), one thread, per amplitude update.  The line also carries the classical QSVT
+    evaluator (O5) on the whole workload, one thread, for the circuit
+    workloads."""
     if rank != 0:
         return
     W, K = args.warmup, args.steps
     secs = []
     vals = []
     extra = {}
-    if args.workload in WORKLOADS and BOUNDARY.get(args.workload, "periodic") == "periodic":
+    circuit = args.workload in WORKLOADS
+    r = None
+    for i in range(W + K):
+        if circuit:
+            r = oracle_sample(args.workload, threads=1)
+        else:
+            r = oracle_micro_sample(22, seconds_target=args.ref_seconds)
+        if i >= W:
+            secs.append(r["seconds"])
+            vals.append(r["value"])
+    workload = args.workload if (circuit or args.workload in MICRO) else "microbench-n22-c128"
+    if circuit and BOUNDARY.get(args.workload, "periodic") == "periodic":
         cfg, f0, ph = _reference_inputs(args.workload)
         updates = oracle_amp_updates(cfg, ph)
-        r = None
-        for i in range(W + K):
-            r = oracle_classical(cfg, f0, ph, threads=1)
-            if i >= W:
-                secs.append(r["seconds"])
-                vals.append(updates / r["seconds"])
-        workload = args.workload
-        sample = (f"the whole workload ({args.workload}) per step through the oracle's classical "
-                  f"QSVT evaluator (O5, FP64, {r['entries']} physical entries, degree "
-                  f"{len(ph) - 1}), one thread; value = the circuit's amplitude-gate updates "
-                  f"({updates:.4g}, counted on the oracle's gate list) over its time")
-        extra["naive_simulator"] = oracle_sample(args.workload, seconds_target=8.0)
-    else:
-        n = 22
-        for i in range(W + K):
-            r = oracle_micro_sample(n, seconds_target=args.ref_seconds)
-            if i >= W:
-                secs.append(r["seconds"])
-                vals.append(r["value"])
-        workload = args.workload if args.workload in MICRO else f"microbench-n{n}-c128"
-        sample = r["sample"]
+        o5 = oracle_classical(cfg, f0, ph, threads=1)
+        extra["classical_o5"] = {
+            "what": (f"the whole workload through the oracle's classical QSVT evaluator (O5, "
+                     f"FP64, {o5['entries']} physical entries, degree {len(ph) - 1}), one thread; "
+                     f"equivalent_value = the circuit's amplitude-gate updates ({updates:.4g}, "
+                     f"counted on the oracle's gate list) over its time"),
+            "seconds_per_run": o5["seconds"], "equivalent_value": updates / o5["seconds"]}
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": 1000.0 * statistics.median(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "complex128 (fp64)", "data": "synthetic",
-            "config": {"workload": workload, "host_cores": os.cpu_count(), "threads": 1},
+            "config": {"workload": workload, "host_cores": os.cpu_count(), "threads": 1,
+                       "sample_per_step": r["sample"]},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": r["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     line.update(extra)
     print(json.dumps(line), flush=True)

@@ -871,8 +871,8 @@ __device__ __forceinline__ void permute(const SweepParams& a, uint32_t (&x)[U]) 
 // their deposit L[u] is computed once, and the high part H advances by a
 // masked add of hstep (the deposit of stride >> nfe).  nfe = 0 is the natural
 // order.
-template <typename R, int U, int MINB, int SHAPE>
-__global__ void __launch_bounds__(256, MINB)
+template <typename R, int U, int MINB, int SHAPE, int BLK = 256>
+__global__ void __launch_bounds__(BLK, MINB)
     sweep_kernel(const typename V2<R>::T* in, typename V2<R>::T* out, uint32_t ntiles, int nfe,
                  uint32_t fmask, uint32_t hstep, const __grid_constant__ SweepParams a) {
   using T = typename V2<R>::T;
@@ -1296,24 +1296,28 @@ int sweep_waves() {
 }
 
 // Co-resident blocks of one sweep-kernel instantiation on the device (cached).
-template <typename R, int U, int MINB>
+template <typename R, int U, int MINB, int SHAPE = 0, int BLK = 256>
 int sweep_resident() {
   static int resident = 0;
   if (!resident) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R, U, MINB, 0>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R, U, MINB, SHAPE, BLK>,
+                                                  BLK, 0);
     resident = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
   }
   return resident;
 }
 
-template <typename R, int U, int MINB, int SHAPE = 0>
+template <typename R, int U, int MINB, int SHAPE = 0, int BLK = 256>
 void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepParams& a, cudaStream_t st) {
   using T = typename V2<R>::T;
-  const int blk = 256;
-  uint64_t grd = (uint64_t)sweep_resident<R, U, MINB>() * sweep_waves();
+  const int blk = BLK;
+  // the default-block variants share one occupancy figure per (U, MINB)
+  uint64_t grd = (uint64_t)(BLK == 256 ? sweep_resident<R, U, MINB>()
+                                       : sweep_resident<R, U, MINB, SHAPE, BLK>()) *
+                 sweep_waves();
   const uint64_t need = ((uint64_t)ntiles / U * 32 + blk - 1) / blk;
   if (grd > need) grd = need;
   if (grd < 1) grd = 1;
@@ -1331,8 +1335,8 @@ void launch_sweep_t(const void* in, void* out, uint32_t ntiles, const SweepParam
     hstep |= (hv & 1u) << b;
     hv >>= 1;
   }
-  sweep_kernel<R, U, MINB, SHAPE><<<(int)grd, blk, 0, st>>>((const T*)in, (T*)out, ntiles, nfe,
-                                                             fmask, hstep, a);
+  sweep_kernel<R, U, MINB, SHAPE, BLK><<<(int)grd, blk, 0, st>>>((const T*)in, (T*)out, ntiles,
+                                                                  nfe, fmask, hstep, a);
 }
 
 // The sweep shape of a parameter block (see apply_shaped).
@@ -1430,27 +1434,31 @@ bool gates_only(const SweepParams& a) {
   return true;
 }
 
-template <typename R, int U, int MINB>
+// MINB / BLK: the lean kernel's launch shape; the generic interpreter keeps
+// 256-thread blocks at MINB0.
+template <typename R, int U, int MINB, int BLK, int MINB0>
 void launch_staged_u(const void* in, void* out, uint32_t ntiles, const SweepParams& a,
                      cudaStream_t st) {
-  if (gates_only(a)) return launch_sweep_t<R, U, MINB, 5>(in, out, ntiles, a, st);
-  return launch_sweep_t<R, U, MINB, 0>(in, out, ntiles, a, st);
+  if (gates_only(a)) return launch_sweep_t<R, U, MINB, 5, BLK>(in, out, ntiles, a, st);
+  return launch_sweep_t<R, U, MINB0, 0>(in, out, ntiles, a, st);
 }
 
 template <typename R>
 void launch_staged(const void* in, void* out, uint32_t ntiles, const SweepParams& a,
                    cudaStream_t st) {
   if (a.nstage == 1) {
-    if constexpr (sizeof(R) == 4) return launch_staged_u<R, 2, 4>(in, out, ntiles, a, st);
-    return launch_staged_u<R, 2, 2>(in, out, ntiles, a, st);
+    if constexpr (sizeof(R) == 4) return launch_staged_u<R, 2, 4, 256, 4>(in, out, ntiles, a, st);
+    return launch_staged_u<R, 2, 2, 256, 2>(in, out, ntiles, a, st);
   }
+  // 128-thread blocks: the register file, not the block size, sets how many
+  // warps a 4- or 8-tile sweep keeps resident
   if (a.nstage == 2) {
-    if constexpr (sizeof(R) == 4) return launch_staged_u<R, 4, 2>(in, out, ntiles, a, st);
-    return launch_staged_u<R, 4, 1>(in, out, ntiles, a, st);
+    if constexpr (sizeof(R) == 4) return launch_staged_u<R, 4, 5, 128, 2>(in, out, ntiles, a, st);
+    return launch_staged_u<R, 4, 2, 128, 1>(in, out, ntiles, a, st);
   }
-  // eight tiles (32 complex64 or complex128 amplitudes a thread): one block
-  // per SM, the register file is the limit either way
-  return launch_staged_u<R, 8, 1>(in, out, ntiles, a, st);
+  // eight tiles (32 complex64 or complex128 amplitudes a thread)
+  if constexpr (sizeof(R) == 4) return launch_staged_u<R, 8, 3, 128, 1>(in, out, ntiles, a, st);
+  return launch_staged_u<R, 8, 2, 128, 1>(in, out, ntiles, a, st);
 }
 
 }  // namespace
@@ -1572,7 +1580,13 @@ cudaError_t warm_r() {
   sweep_resident<R, 4, 2>();
   sweep_resident<R, 1, 4>();
   sweep_resident<R, 2, 4>();
-  sweep_resident<R, 8, 1>();
+  if constexpr (sizeof(R) == 4) {
+    sweep_resident<R, 4, 5, 5, 128>();
+    sweep_resident<R, 8, 3, 5, 128>();
+  } else {
+    sweep_resident<R, 4, 2, 5, 128>();
+    sweep_resident<R, 8, 2, 5, 128>();
+  }
   return e;
 }
 }  // namespace
