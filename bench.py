@@ -86,6 +86,13 @@ MICRO = {
     "microbench-n30-c64": (30, 1000, 0),
     "microbench-n33-c64": (33, 1000, 0),
 }
+# Dense-block stream: (qubits, blocks, seed); complex64, each block 16 gates
+# on 5 random qubits (lbm_inputs.dense_block_gates), fused into one dense
+# 5-qubit block on the tensor cores per run.
+DENSE = {
+    "dense5-n28-c64": (28, 64, 0),
+    "dense5-n30-c64": (30, 64, 0),
+}
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one sweep_kernel launch,
 # keyed by the sha256 of kernels.cu at capture time (profiles/ has the summary).
@@ -327,8 +334,12 @@ def oracle_micro_sample(n, seconds_target=12.0):
 
 def run_micro(args, rank, world, local, torch, G, dist):
     """One step = the whole 1000-gate vocabulary stream over the resident state."""
-    n, count, seed = MICRO[args.workload]
-    gates = I.microbench_gates(n, count, seed)
+    if args.workload in DENSE:
+        n, count, seed = DENSE[args.workload]
+        gates = I.dense_block_gates(n, count, seed)
+    else:
+        n, count, seed = MICRO[args.workload]
+        gates = I.microbench_gates(n, count, seed)
     records = G.gates_to_records(gates)
     stream = torch.cuda.current_stream()
     gen = torch.Generator(device="cuda")
@@ -399,6 +410,19 @@ def run_micro(args, rank, world, local, torch, G, dist):
         "gpu_launches": args.steps * st["passes"],
         "clocks": clk,
     }
+    line["config"]["dense_blocks"] = st["dense_blocks"]
+    line["config"]["staged_sweeps"] = st["staged_sweeps"]
+    if st["dense_blocks"] and st["dense_blocks"] == st["passes"]:
+        # every pass is a dense block: the tensor work the split products
+        # execute (3 x 2 x 64 x 64 FLOP per group of 32 amplitudes) against
+        # the bf16 peak, beside the HBM roofline above
+        flops = 3.0 * 2 * 64 * 64 * (1 << (n - 5)) * st["dense_blocks"]
+        line["tensor"] = {"kernel": "dense5_tc_kernel", "achieved": flops / (ms / 1000.0) / 1e12,
+                          "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                          "frac": flops / (ms / 1000.0) / 1e12 / peaks["bf16_tflops"],
+                          "note": "split BF16x3: three BF16 products per complex64 block; "
+                                  "the pass is HBM-bound at this intensity (48 FLOP/B)",
+                          "engine": os.environ.get("CSIM_DENSE_ENGINE", "tc")}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_micro_sample(22)
     if rank == 0:
@@ -707,7 +731,8 @@ def run_reference(args, rank, world):
         if i >= W:
             secs.append(r["seconds"])
             vals.append(r["value"])
-    workload = args.workload if (circuit or args.workload in MICRO) else "microbench-n22-c128"
+    workload = (args.workload if (circuit or args.workload in MICRO or args.workload in DENSE)
+                else "microbench-n22-c128")
     if circuit and BOUNDARY.get(args.workload, "periodic") == "periodic":
         cfg, f0, ph = _reference_inputs(args.workload)
         updates = oracle_amp_updates(cfg, ph)
@@ -738,7 +763,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(MICRO) + sorted(BATCH) + sorted(SERVING))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(MICRO) + sorted(DENSE) + sorted(BATCH) +
+                    sorted(SERVING))
     ap.add_argument("--exec", default="fused", choices=["fused", "gate"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
@@ -760,7 +786,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    if args.workload in MICRO:
+    if args.workload in MICRO or args.workload in DENSE:
         return run_micro(args, rank, world, local, torch, G, dist)
     if args.workload in BATCH:
         return run_batch(args, rank, world, local, torch, G, dist)

@@ -281,9 +281,27 @@ typedef struct {
   double amp_updates;   /* sum over gates of the amplitudes each gate changes */
   double pass_amps;
   uint64_t state_bytes;
+  int64_t dense_blocks;  /* of the passes, dense 5-qubit blocks */
+  int64_t staged_sweeps; /* of the fused sweeps, those that stage qubits above the tile */
 } csim_sv_stats_t;
 csim_status csim_sv_stats(const csim_sv* sv, csim_sv_stats_t* out);
 csim_status csim_sv_free(csim_sv* sv);
+
+/* A dense 5-qubit block: apply the 32 x 32 complex matrix u (row-major,
+ * interleaved re/im doubles; element bit j of its row and column index is
+ * qubit qubits[j]) to the complex64 state, for every group of 32 amplitudes
+ * that differ only in those five distinct qubits.  Enqueued on the state's
+ * stream; the fuser emits the same operation for long runs of gates on at
+ * most five qubits.  engine 0: the tensor cores (tcgen05 MMA into TMEM, split
+ * BF16x3 with FP32 accumulation: each factor is a sum of two BF16 values,
+ * three of the four cross products are kept, relative error about 2^-17 per
+ * product; n >= 12); engine 1: the CUDA cores in FP32 (n >= 5).  The
+ * tensor-core kernel waits for its products with an iteration limit; when it
+ * runs out the kernel gives up on the state and the next csim_sv_read
+ * returns CSIM_ERR_TIMEOUT.  CSIM_ERR_ARG for a complex128 state, repeated or
+ * out-of-range qubits, too few qubits or an unknown engine. */
+csim_status csim_sv_apply_dense(csim_sv* sv, const int32_t* qubits, const double* u,
+                                int32_t engine);
 
 /* Host-only reference executor of the fused-program format: compiles the gate
  * list with the same fuser as CSIM_EXEC_FUSED and executes the resulting
@@ -291,14 +309,15 @@ csim_status csim_sv_free(csim_sv* sv);
  * on the host in FP64 with the kernel's semantics.  amps: 2^n interleaved
  * complex values, updated in place (n in [7, 24]), or NULL to compile only and
  * report the statistics (n in [7, 34]).  For testing the fuser without a GPU.
- * If stats is non-NULL it receives 18 counters: sweeps, single-gate steps,
+ * If stats is non-NULL it receives 20 counters: sweeps, single-gate steps,
  * permutation gates, lookup tables, local gates, multiplexers, multiplexed
  * gates, multiplexer entries, largest bucket, table entries, largest table
  * support, HBM passes, averaging blocks, multiplexers run as the inverse of
  * the sweep's previous multiplexer, Walsh-Hadamard ops (H on several lane
  * bits fused), in-place conjugated sweeps (a permutation, tile ops and the
  * inverse permutation), sweeps that stage qubits above the warp tile in
- * registers, and gates on those staged qubits. */
+ * registers, gates on those staged qubits, dense 5-qubit blocks, and the
+ * gates those blocks hold. */
 csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n, double* amps,
                                int64_t* stats);
 

@@ -108,6 +108,27 @@ def microbench_gates(n: int, count: int, seed: int):
     return out
 
 
+def dense_block_gates(n: int, blocks: int, seed: int):
+    """Gate stream of dense 5-qubit blocks (canonical records, tag 0): each
+    block picks 5 distinct random qubits and applies RY on each (angles
+    U[0, 2pi)), a CNOT chain along them, RY on each again and H on two of
+    them: 16 gates whose targets and controls stay inside the block."""
+    rng = np.random.default_rng(seed)
+    X, H, RY = 0, 1, 2
+    out = []
+    for _ in range(blocks):
+        q = [int(v) for v in rng.choice(n, 5, replace=False)]
+        for t in q:
+            out.append((RY, t, 0, 0, float(rng.uniform(0.0, 2.0 * math.pi)), 0))
+        for a, b in zip(q, q[1:]):
+            out.append((X, b, 1 << a, 1 << a, 0.0, 0))
+        for t in q:
+            out.append((RY, t, 0, 0, float(rng.uniform(0.0, 2.0 * math.pi)), 0))
+        for t in rng.choice(q, 2, replace=False):
+            out.append((H, int(t), 0, 0, 0.0, 0))
+    return out
+
+
 def batch_instance(i: int):
     """Instance i of the 256-instance batching workload (seed i).
 

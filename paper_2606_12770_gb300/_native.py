@@ -33,7 +33,7 @@ EXPORTED = [
     "csim_sv_load_device", "csim_sv_device", "csim_sv_stats", "csim_pool_create",
     "csim_pool_submit", "csim_pool_poll", "csim_pool_result", "csim_pool_stats", "csim_pool_free",
     "csim_pool_plan", "csim_compile", "csim_run_steps", "csim_checkpoint", "csim_restore",
-    "csim_final_distribution", "csim_pool_cancel", "csim_pool_inject",
+    "csim_final_distribution", "csim_pool_cancel", "csim_pool_inject", "csim_sv_apply_dense",
 ]
 
 
@@ -125,6 +125,7 @@ def load():
         "csim_pool_stats": ([VP, VP], C.c_int),
         "csim_pool_free": ([VP], C.c_int),
         "csim_pool_cancel": ([VP, C.c_int64], C.c_int),
+        "csim_sv_apply_dense": ([VP, P(C.c_int32), DP, C.c_int32], C.c_int),
         "csim_pool_inject": ([VP, C.c_int32, C.c_int64], C.c_int),
         "csim_pool_plan": ([C.c_uint64, C.c_uint64, C.c_int32, SZ, P(C.c_uint64), DP, DP, DP, DP,
                             P(C.c_uint64)], C.c_int),
@@ -313,7 +314,8 @@ class Circuit:
 
 class SvStats(C.Structure):
     _fields_ = [("passes", C.c_int64), ("sweeps", C.c_int64), ("single", C.c_int64),
-                ("amp_updates", C.c_double), ("pass_amps", C.c_double), ("state_bytes", C.c_uint64)]
+                ("amp_updates", C.c_double), ("pass_amps", C.c_double), ("state_bytes", C.c_uint64),
+                ("dense_blocks", C.c_int64), ("staged_sweeps", C.c_int64)]
 
 
 class DeviceState:
@@ -386,6 +388,18 @@ class StateVector:
         _check(_lib.csim_sv_info(self._h, C.byref(ns), C.byref(au), C.byref(sb)))
         return {"n_sweeps": ns.value, "amp_updates": au.value, "state_bytes": sb.value}
 
+    def apply_dense(self, qubits, u, engine=0):
+        """csim_sv_apply_dense: the 32 x 32 matrix u (element bit j = qubits[j])
+        on five qubits; engine 0 tensor cores (split BF16x3), 1 CUDA cores FP32."""
+        q = np.ascontiguousarray(qubits, dtype=np.int32)
+        if q.shape != (5,):
+            raise ValueError("five qubits")
+        m = np.ascontiguousarray(u, dtype=np.complex128)
+        if m.shape != (32, 32):
+            raise ValueError("u must be 32 x 32")
+        _check(_lib.csim_sv_apply_dense(self._h, q.ctypes.data_as(C.POINTER(C.c_int32)),
+                                        _dp(m.view(np.float64)), int(engine)))
+
     def stats(self):
         st = SvStats()
         _check(_lib.csim_sv_stats(self._h, C.cast(C.byref(st), C.c_void_p)))
@@ -394,7 +408,8 @@ class StateVector:
 
 FUSE_STAT_NAMES = ["sweeps", "single", "perm_gates", "segments", "local_gates", "mux",
                    "mux_gates", "mux_entries", "max_bucket", "lut_entries", "max_support", "passes",
-                   "reflect", "mux_inverse", "wht", "conjugated", "staged_sweeps", "staged_gates"]
+                   "reflect", "mux_inverse", "wht", "conjugated", "staged_sweeps", "staged_gates",
+                   "dense_blocks", "dense_gates"]
 
 
 def emulate_fused(gates, n, amps):

@@ -763,6 +763,7 @@ csim_status csim_sv_create(int32_t n, csim_precision prec, void* stream, csim_sv
     delete s;
     return fail(CSIM_ERR_OOM, std::string("state allocation: ") + cudaGetErrorString(e));
   }
+  if (csim::dense_timeouts(&s->timeouts_seen) != cudaSuccess) cudaGetLastError();
   *out = s;
   return CSIM_OK;
 }
@@ -796,7 +797,7 @@ csim_status csim_sv_compile(csim_sv* s, const csim_gate* gates, size_t n_gates, 
   }
   csim::free_program(&s->prog);
   std::vector<Gate> gl(gates, gates + n_gates);
-  csim::build_program(gl, s->n, mode, &s->prog);
+  csim::build_program(gl, s->n, mode, &s->prog, s->prec == CSIM_C64);
   cudaError_t e = csim::upload_program(&s->prog, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "csim_sv_compile");
   if (s->prog.pingpong && !s->buf[1]) {
@@ -838,6 +839,54 @@ csim_status csim_sv_read(csim_sv* s, double* out, size_t n_amps) {
     for (size_t i = 0; i < 2 * N; ++i) out[i] = tmp[i];
   }
   if (e != cudaSuccess) return cuda_fail(e, "csim_sv_read");
+  unsigned int to = 0;
+  if (csim::dense_timeouts(&to) == cudaSuccess && to != s->timeouts_seen) {
+    s->timeouts_seen = to;
+    return fail(CSIM_ERR_TIMEOUT, "csim_sv_read: a dense block's wait for its tensor-core "
+                                  "products ran out; the state is not valid");
+  }
+  return CSIM_OK;
+}
+
+csim_status csim_sv_apply_dense(csim_sv* s, const int32_t* qubits, const double* u,
+                                int32_t engine) {
+  if (!s || !qubits || !u) return fail(CSIM_ERR_ARG, "null argument");
+  if (s->prec != CSIM_C64) return fail(CSIM_ERR_ARG, "dense blocks need a complex64 state");
+  if (engine != csim::DENSE_TC && engine != csim::DENSE_FP32)
+    return fail(CSIM_ERR_ARG, "unknown engine");
+  if (s->n < (engine == csim::DENSE_TC ? 12 : 5))
+    return fail(CSIM_ERR_ARG, "too few qubits for this engine");
+  int order[5];
+  for (int j = 0; j < 5; ++j) {
+    if (qubits[j] < 0 || qubits[j] >= s->n) return fail(CSIM_ERR_ARG, "qubit out of range");
+    for (int k = 0; k < j; ++k)
+      if (qubits[k] == qubits[j]) return fail(CSIM_ERR_ARG, "repeated qubit");
+    order[j] = j;
+  }
+  std::sort(order, order + 5, [&](int a, int b) { return qubits[a] < qubits[b]; });
+  // element bit j of the caller's U is qubits[j]; the kernels take the
+  // qubits ascending, so U's rows and columns are relabelled to that order
+  auto relabel = [&](int x) {
+    int y = 0;
+    for (int j = 0; j < 5; ++j)
+      if ((x >> order[j]) & 1) y |= 1 << j;
+    return y;
+  };
+  csim::DenseBlock& b = s->dense;
+  for (int j = 0; j < 5; ++j) b.q[j] = (uint8_t)qubits[order[j]];
+  b.u.assign(2 * 1024, 0.0);
+  for (int r = 0; r < 32; ++r)
+    for (int c = 0; c < 32; ++c) {
+      const int r2 = relabel(r), c2 = relabel(c);
+      b.u[2 * (32 * r2 + c2)] = u[2 * (32 * r + c)];
+      b.u[2 * (32 * r2 + c2) + 1] = u[2 * (32 * r + c) + 1];
+    }
+  csim::make_dense_block(&b);
+  // the previous block's device copy may still be read by queued work
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess) e = csim::upload_dense(&b, s->stream);
+  if (e == cudaSuccess) e = csim::launch_dense(s->buf[s->cur], s->n, b, engine, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_sv_apply_dense");
   return CSIM_OK;
 }
 
@@ -860,6 +909,8 @@ csim_status csim_sv_stats(const csim_sv* s, csim_sv_stats_t* out) {
   out->single = s->prog.stats.single;
   out->amp_updates = s->prog.amp_updates;
   out->pass_amps = s->prog.pass_amps;
+  out->dense_blocks = s->prog.stats.dense_blocks;
+  out->staged_sweeps = s->prog.stats.staged_sweeps;
   return CSIM_OK;
 }
 
@@ -887,6 +938,7 @@ csim_status csim_sv_free(csim_sv* s) {
     b = nullptr;
   }
   csim::free_program(&s->prog);
+  csim::free_dense(&s->dense);
   delete s;
   return CSIM_OK;
 }
@@ -903,7 +955,7 @@ csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n
   }
   Program p;
   std::vector<Gate> gl(gates, gates + n_gates);
-  csim::build_program(gl, n, CSIM_EXEC_FUSED, &p);
+  csim::build_program(gl, n, CSIM_EXEC_FUSED, &p, true);
   if (amps) {
     const size_t N = (size_t)1 << n;
     std::vector<double> st(amps, amps + 2 * N);
@@ -912,10 +964,11 @@ csim_status csim_emulate_fused(const csim_gate* gates, size_t n_gates, int32_t n
   }
   if (stats) {
     const csim::FuseStats& f = p.stats;
-    const int64_t v[18] = {f.sweeps,      f.single,      f.perm_gates,  f.segments, f.local_gates,
+    const int64_t v[20] = {f.sweeps,      f.single,      f.perm_gates,  f.segments, f.local_gates,
                            f.mux,         f.mux_gates,   f.mux_entries, f.max_bucket,
                            f.lut_entries, f.max_support, p.passes,      f.reflect,  f.mux_inverse,
-                           f.wht,         f.conjugated,  f.staged_sweeps, f.staged_gates};
+                           f.wht,         f.conjugated,  f.staged_sweeps, f.staged_gates,
+                           f.dense_blocks, f.dense_gates};
     std::memcpy(stats, v, sizeof(v));
   }
   return CSIM_OK;

@@ -1,0 +1,522 @@
+// Fused dense 5-qubit blocks on the tensor cores (sm_103a: tcgen05 + TMEM).
+//
+// A run of gates that touch at most five qubits Q = {q0 < ... < q4} (targets
+// and controls) composes to one 32 x 32 complex unitary U.  Applying it to a
+// complex64 state is a dense contraction: for every group of 32 amplitudes
+// that differ only in the bits of Q,
+//     y = U x,
+// 2^(n-5) independent columns.  Written over the reals with (re, im)
+// interleaved, x is a 64-vector and U the 64 x 64 real matrix
+//     W[2i][2j] = Re U_ij, W[2i][2j+1] = -Im U_ij,
+//     W[2i+1][2j] = Im U_ij, W[2i+1][2j+1] = Re U_ij,
+// so a tile of 128 groups is the GEMM  D (128 x 64) = X (128 x 64) W^T.
+//
+// dense5_tc_kernel runs it on the 5th-generation tensor cores in split
+// BF16x3 with FP32 accumulation: X = Xhi + Xlo and W = Whi + Wlo with every
+// part a BF16 (hi = bf16(v), lo = bf16(v - hi), together 16 significant
+// bits), and D = Xhi Whi^T + Xhi Wlo^T + Xlo Whi^T.  One CTA of four warps
+// per tile of 128 groups:
+//   1. the threads load the tile's 4096 amplitudes in address order
+//      (coalesced), split them and write both BF16 planes of X into shared
+//      memory in the no-swizzle K-major core-matrix layout (8 rows x 16 B
+//      per core matrix);
+//   2. one thread issues the 12 tcgen05.mma (M = 128, N = 64, K = 16; three
+//      products x four K steps) into a 64-column FP32 accumulator in TMEM
+//      and commits them to an mbarrier;
+//   3. every warp reads its 32 TMEM lanes (one group per thread, 64 FP32
+//      columns) with tcgen05.ld and stores the 32 output amplitudes.
+// The BF16 planes of W^T come from the host once per block, already in the
+// shared-memory image the MMA reads.  The mbarrier wait has an iteration
+// limit: when it runs out the kernel counts a timeout, waits (with a limit
+// again) for its MMAs to finish, frees its TMEM and returns.
+//
+// dense5_fp32_kernel is the same operation on the CUDA cores in FP32 (one
+// thread per group), the comparison the tensor-core path is measured
+// against and its check.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+
+#include "dense.h"
+
+namespace csim {
+namespace {
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor of tcgen05.mma: start address, leading
+// (K-direction) and stride (M/N-direction) byte offsets, all >> 4; bits
+// 46-48 hold the fixed value 0b001; no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// One try of the phase-parity wait; true once the phase with parity `par`
+// has completed.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t par) {
+  uint32_t ok = 0;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(par)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+// Generic-proxy writes to shared memory made visible to the tensor core.
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// D (TMEM) = A (smem) . B (smem) [+ D]; BF16 inputs, FP32 accumulator.
+__device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Arrive on the mbarrier once every MMA issued so far by this thread is done.
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+// TMEM: a warp allocates `ncols` columns (a power of two >= 32) and writes
+// their base address to shared memory; the same warp frees them.
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (32x32b shape: warp
+// w reads lanes 32 w .. 32 w + 31, one per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&d)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) d[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Round to the nearest BF16 (ties to even) and return its 16 bits; the
+// inputs are finite.
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+__device__ __forceinline__ float bf16_value(uint32_t b) { return __uint_as_float(b << 16); }
+
+// Byte offset of element (row, k) in a no-swizzle K-major operand of 64 BF16
+// columns: core matrices of 8 rows x 8 elements (128 B), the 8 along K
+// adjacent (LBO = 128 B), the 8-row groups 1024 B apart (SBO).
+__device__ __forceinline__ uint32_t core_off(uint32_t row, uint32_t k) {
+  return (((row >> 3) * 8u + (k >> 3)) << 7) + ((row & 7u) << 4) + ((k & 7u) << 1);
+}
+
+constexpr uint32_t kDenseSmem = 16384 * 2 + 8192 * 2 + 64;
+constexpr uint32_t kTmemCols = 64;
+
+// kind::f16 instruction descriptor: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kIdescBf16M128N64 =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__global__ void __launch_bounds__(128) dense5_tc_kernel(float2* __restrict__ st,
+                                                         const __grid_constant__ DenseParams P) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint8_t* Ahi = sm;
+  uint8_t* Alo = sm + 16384;
+  uint8_t* Bhi = sm + 32768;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 49152);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 49160);
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+
+  // W^T in both BF16 planes, already in the operand layout (16 KB)
+  for (uint32_t i = tid; i < 1024u; i += 128u)
+    reinterpret_cast<uint4*>(Bhi)[i] = __ldg(P.bimg + i);
+  if (warp == 0) tmem_alloc(smem_u32(tslot), kTmemCols);
+  if (tid == 0) {
+    mbar_init(smem_u32(bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t sbar = smem_u32(bar);
+
+  // local bits of the tile: the low 7 of the thread's local index lambda
+  // come from tid, the high 5 from the load step i; pos[m] is the state bit
+  // and tag[m] the role (0-6 group-in-tile bit, 8-12 element bit) of bit m
+  uint64_t a_lo = 0;
+  uint32_t g_lo = 0, e_lo = 0;
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+    const uint32_t b = (tid >> m) & 1u;
+    a_lo |= (uint64_t)b << P.pos[m];
+    if (P.tag[m] < 8) g_lo |= b << P.tag[m];
+    else e_lo |= b << (P.tag[m] - 8);
+  }
+  uint64_t a_hi[5];
+  uint32_t g_hi[5], e_hi[5];
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    a_hi[b] = 1ull << P.pos[7 + b];
+    g_hi[b] = P.tag[7 + b] < 8 ? 1u << P.tag[7 + b] : 0u;
+    e_hi[b] = P.tag[7 + b] < 8 ? 0u : 1u << (P.tag[7 + b] - 8);
+  }
+  // the epilogue's group (TMEM lane) and its element addresses
+  const uint32_t row = (warp << 5) | lane;
+  uint64_t a_row = 0;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) a_row |= (uint64_t)((row >> j) & 1u) << P.nonq[j];
+  uint64_t a_el[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) a_el[j] = 1ull << P.q[j];
+
+  uint32_t phase = 0;
+  for (uint32_t t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
+    uint64_t base = 0;
+    for (int j = 0; j < P.n - 12; ++j) base |= (uint64_t)((t >> j) & 1u) << P.nonq[7 + j];
+    // 1. load 32 amplitudes per thread in address order, split into BF16 planes
+    float2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      uint64_t a = base | a_lo;
+#pragma unroll
+      for (int b = 0; b < 5; ++b)
+        if ((i >> b) & 1) a |= a_hi[b];
+      v[i] = __ldcs(st + a);
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      uint32_t g = g_lo, e = e_lo;
+#pragma unroll
+      for (int b = 0; b < 5; ++b)
+        if ((i >> b) & 1) {
+          g |= g_hi[b];
+          e |= e_hi[b];
+        }
+      const uint32_t hr = bf16_bits(v[i].x), hi_ = bf16_bits(v[i].y);
+      const uint32_t lr = bf16_bits(v[i].x - bf16_value(hr));
+      const uint32_t li = bf16_bits(v[i].y - bf16_value(hi_));
+      const uint32_t off = core_off(g, 2u * e);  // (re, im) share one 32-bit word
+      *reinterpret_cast<uint32_t*>(Ahi + off) = hr | (hi_ << 16);
+      *reinterpret_cast<uint32_t*>(Alo + off) = lr | (li << 16);
+    }
+    fence_async_smem();
+    __syncthreads();
+    // 2. one thread issues the split products into the TMEM accumulator
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi),
+                     bl = smem_u32(Bhi + 8192);
+#pragma unroll
+      for (uint32_t j = 0; j < 4; ++j) {  // K = 64 in steps of 16 (two core columns)
+        const uint64_t dah = smem_desc(ah + 256u * j, 128u, 1024u);
+        const uint64_t dal = smem_desc(al + 256u * j, 128u, 1024u);
+        const uint64_t dbh = smem_desc(bh + 256u * j, 128u, 1024u);
+        const uint64_t dbl = smem_desc(bl + 256u * j, 128u, 1024u);
+        tc_mma_bf16(tmem, dah, dbh, kIdescBf16M128N64, j > 0 ? 1u : 0u);
+        tc_mma_bf16(tmem, dah, dbl, kIdescBf16M128N64, 1u);
+        tc_mma_bf16(tmem, dal, dbh, kIdescBf16M128N64, 1u);
+      }
+      tc_commit(sbar);
+    }
+    // bounded wait for the products; spin = 0 gives up at once (tests)
+    bool ok = false;
+    if (P.spin > 0) {
+      uint32_t it = 0;
+      while (!(ok = mbar_try(sbar, phase)) && ++it < P.spin) {
+      }
+    }
+    const int timed_out = __syncthreads_or(!ok);
+    if (timed_out) {
+      // record it, let the issued MMAs finish (bounded again) before the
+      // TMEM is freed, and stop
+      if (tid == 0) atomicAdd(P.timeouts, 1u);
+      uint32_t it = 0;
+      while (!mbar_try(sbar, phase) && ++it < (1u << 26)) {
+      }
+      break;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    // 3. every thread stores its group's 32 outputs
+    float d[64];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float part[16];
+      tmem_ld16(tmem + ((warp * 32u) << 16) + 16u * (uint32_t)c, part);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) d[16 * c + i] = part[i];
+    }
+    tmem_ld_wait();
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      uint64_t a = base | a_row;
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+        if ((e >> j) & 1) a |= a_el[j];
+      __stcs(st + a, make_float2(d[2 * e], d[2 * e + 1]));
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, kTmemCols);
+}
+
+}  // namespace
+}  // namespace csim
+
+namespace csim {
+namespace {
+
+// The same block on the CUDA cores in FP32: one thread per group of 32
+// amplitudes, U from shared memory (broadcast reads).
+__global__ void __launch_bounds__(256) dense5_fp32_kernel(float2* __restrict__ st,
+                                                           const __grid_constant__ DenseParams P) {
+  __shared__ float2 U[1024];
+  for (uint32_t i = threadIdx.x; i < 1024u; i += blockDim.x) U[i] = P.uf[i];
+  __syncthreads();
+  const uint64_t ngroups = 1ull << (P.n - 5);
+  uint64_t a_el[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) a_el[j] = 1ull << P.q[j];
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t base = 0;
+    for (int j = 0; j < P.n - 5; ++j) base |= ((g >> j) & 1ull) << P.nonq[j];
+    float2 x[32];
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      uint64_t a = base;
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+        if ((e >> j) & 1) a |= a_el[j];
+      x[e] = st[a];
+    }
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float2 u = U[i * 32 + j];
+        re = fmaf(u.x, x[j].x, fmaf(-u.y, x[j].y, re));
+        im = fmaf(u.x, x[j].y, fmaf(u.y, x[j].x, im));
+      }
+      uint64_t a = base;
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+        if ((i >> j) & 1) a |= a_el[j];
+      st[a] = make_float2(re, im);
+    }
+  }
+}
+
+__device__ unsigned int g_dense_timeouts;
+
+// BF16 bits of a double, rounded to float first and then to the nearest
+// BF16 (ties to even).
+uint16_t bf16_host(double v) {
+  const float f = (float)v;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+double bf16_host_value(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+uint32_t dense_spin() {
+  static const uint32_t v = [] {
+    const char* e = std::getenv("CSIM_DENSE_SPIN");
+    return e ? (uint32_t)std::strtoul(e, nullptr, 10) : (1u << 20);
+  }();
+  return v;
+}
+
+}  // namespace
+
+void make_dense_block(DenseBlock* b) {
+  // W (64 x 64 real, interleaved re/im) from U; the MMA's B operand is W^T
+  // viewed N x K (row n = W's row n), K-major: core matrices of 8 rows x 8
+  // BF16, the 8 along K adjacent (128 B), the 8-row groups 1024 B apart.
+  b->bimg.assign(2 * 4096, 0);
+  b->uf.assign(2 * 1024, 0.f);
+  for (int i = 0; i < 32; ++i)
+    for (int j = 0; j < 32; ++j) {
+      const double re = b->u[2 * (32 * i + j)], im = b->u[2 * (32 * i + j) + 1];
+      b->uf[2 * (32 * i + j)] = (float)re;
+      b->uf[2 * (32 * i + j) + 1] = (float)im;
+      const double w[2][2] = {{re, -im}, {im, re}};
+      for (int a = 0; a < 2; ++a)
+        for (int c = 0; c < 2; ++c) {
+          const int n = 2 * i + a, k = 2 * j + c;
+          const int off = ((((n >> 3) * 8 + (k >> 3)) << 7) + ((n & 7) << 4) + ((k & 7) << 1)) / 2;
+          const uint16_t hi = bf16_host(w[a][c]);
+          const uint16_t lo = bf16_host(w[a][c] - bf16_host_value(hi));
+          b->bimg[off] = hi;
+          b->bimg[4096 + off] = lo;
+        }
+    }
+}
+
+cudaError_t upload_dense(DenseBlock* b, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (!b->d_bimg) e = cudaMalloc(&b->d_bimg, b->bimg.size() * 2);
+  if (e == cudaSuccess && !b->d_uf) e = cudaMalloc(&b->d_uf, b->uf.size() * 4);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_bimg, b->bimg.data(), b->bimg.size() * 2, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_uf, b->uf.data(), b->uf.size() * 4, cudaMemcpyHostToDevice, st);
+  return e;
+}
+
+void free_dense(DenseBlock* b) {
+  if (b->d_bimg) cudaFree(b->d_bimg);
+  if (b->d_uf) cudaFree(b->d_uf);
+  b->d_bimg = nullptr;
+  b->d_uf = nullptr;
+}
+
+namespace {
+unsigned int* timeout_counter() {
+  static unsigned int* p = [] {
+    void* a = nullptr;
+    if (cudaGetSymbolAddress(&a, g_dense_timeouts) != cudaSuccess) {
+      cudaGetLastError();
+      return (unsigned int*)nullptr;
+    }
+    return static_cast<unsigned int*>(a);
+  }();
+  return p;
+}
+
+int dense_tc_grid(uint32_t ntiles) {
+  static int resident = 0;
+  if (!resident) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(dense5_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kDenseSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense5_tc_kernel, 128, kDenseSmem);
+    resident = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  return (int)(ntiles < (uint32_t)resident ? ntiles : (uint32_t)resident);
+}
+}  // namespace
+
+cudaError_t launch_dense(void* state, int n, const DenseBlock& b, int engine, cudaStream_t st) {
+  if (n < 5 || n > 34 || (engine == DENSE_TC && n < 12)) return cudaErrorInvalidValue;
+  DenseParams P{};
+  P.n = n;
+  uint32_t qm = 0;
+  for (int j = 0; j < 5; ++j) {
+    if (b.q[j] >= n || (j > 0 && b.q[j] <= b.q[j - 1])) return cudaErrorInvalidValue;
+    P.q[j] = b.q[j];
+    qm |= 1u << b.q[j];
+  }
+  int k = 0;
+  for (int bit = 0; bit < n; ++bit)
+    if (!((qm >> bit) & 1u)) P.nonq[k++] = (uint8_t)bit;
+  P.bimg = b.d_bimg;
+  P.uf = b.d_uf;
+  P.spin = dense_spin();
+  if (engine == DENSE_FP32) {
+    const uint64_t groups = 1ull << (n - 5);
+    uint64_t grd = (groups + 255) / 256;
+    if (grd > 152ull * 16) grd = 152ull * 16;
+    dense5_fp32_kernel<<<(int)grd, 256, 0, st>>>(static_cast<float2*>(state), P);
+    return cudaGetLastError();
+  }
+  // the tile's 12 local bits in ascending order of their state bit
+  int lp[12], lt[12], m = 0;
+  int gi = 0, qi = 0;
+  for (int bit = 0; bit < n && m < 12; ++bit) {
+    if ((qm >> bit) & 1u) {
+      lp[m] = bit;
+      lt[m++] = 8 + qi++;
+    } else if (gi < 7) {
+      lp[m] = bit;
+      lt[m++] = gi++;
+    }
+  }
+  for (int j = 0; j < 12; ++j) {
+    P.pos[j] = (uint8_t)lp[j];
+    P.tag[j] = (uint8_t)lt[j];
+  }
+  P.ntiles = 1u << (n - 12);
+  P.timeouts = timeout_counter();
+  if (!P.timeouts) return cudaErrorInvalidSymbol;
+  const int grd = dense_tc_grid(P.ntiles);
+  dense5_tc_kernel<<<grd, 128, kDenseSmem, st>>>(static_cast<float2*>(state), P);
+  return cudaGetLastError();
+}
+
+cudaError_t dense_timeouts(unsigned int* out) {
+  return cudaMemcpyFromSymbol(out, g_dense_timeouts, sizeof(unsigned int));
+}
+
+cudaError_t warm_dense() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, dense5_tc_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, dense5_fp32_kernel);
+  if (e == cudaSuccess) dense_tc_grid(1);
+  if (e == cudaSuccess && !timeout_counter()) e = cudaErrorInvalidSymbol;
+  return e;
+}
+
+}  // namespace csim

@@ -975,25 +975,11 @@ bool emit_group(Program* p, const std::vector<csim_gate>& perm, const std::vecto
 
 }  // namespace
 
-void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p) {
-  *p = Program();
-  p->n = n;
-  p->mode = mode;
-  const char* form = std::getenv("CSIM_SWEEP_FORM");
-  p->scatter = form && std::strcmp(form, "scatter") == 0;
-  for (const csim_gate& g : gates) p->amp_updates += gate_amp_updates(g, n);
-  if (mode == CSIM_EXEC_GATE || n < 7 || n > 34) {
-    for (const csim_gate& g : gates) {
-      Step s;
-      s.kind = 1;
-      s.g = g;
-      p->steps.push_back(s);
-    }
-    p->passes = (int64_t)p->steps.size();
-    p->stats.single = p->passes;
-    p->pass_amps = p->amp_updates;
-    return;
-  }
+void pair_op(double* a, double* b, int op, double c, double s);  // host executor (below)
+
+// Fused steps of one run of gates, appended to the program.
+void build_segment(const std::vector<csim_gate>& gates, Program* p) {
+  const int n = p->n;
   std::vector<csim_gate> perm, local;
   std::vector<int> stage;  // staged qubits of the open group
   const int kstage = (n - 7 >= 1) ? std::min(stage_limit(), n - 7) : 0;
@@ -1123,9 +1109,138 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
                       reversed_equal(it.perm, items[k + 1].perm);
     if (emit_group(p, it.perm, it.local, conj, it.stage) && conj) items[k + 1].perm.clear();
   }
+}
+
+// Dense blocks (CSIM_DENSE=0 disables them; CSIM_DENSE_MIN sets the least
+// number of gates a block must hold, default 10).
+bool dense_enabled() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_DENSE");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+int dense_min_gates() {
+  static const int v = [] {
+    const char* e = std::getenv("CSIM_DENSE_MIN");
+    const int k = e ? std::atoi(e) : 10;
+    return k >= 2 ? k : 10;
+  }();
+  return v;
+}
+int dense_engine_default() {
+  const char* e = std::getenv("CSIM_DENSE_ENGINE");
+  return (e && std::strcmp(e, "fp32") == 0) ? DENSE_FP32 : DENSE_TC;
+}
+
+uint64_t gate_support(const csim_gate& g) { return g.cmask | (1ull << g.target); }
+
+// The 32 x 32 unitary of a run of gates on the qubits q[0..4] (ascending;
+// the run touches no other qubit), applied column by column in FP64.
+void compose_block(const std::vector<csim_gate>& run, const uint8_t (&q)[5], std::vector<double>* u) {
+  auto local = [&](uint64_t mask) {
+    uint32_t m = 0;
+    for (int j = 0; j < 5; ++j)
+      if ((mask >> q[j]) & 1ull) m |= 1u << j;
+    return m;
+  };
+  std::vector<double> M(2 * 1024, 0.0);  // M[r][c], column c = the image of basis state c
+  for (int c = 0; c < 32; ++c) M[2 * (32 * c + c)] = 1.0;
+  for (const csim_gate& g : run) {
+    int t = 0;
+    while (q[t] != g.target) ++t;
+    const uint32_t cm = local(g.cmask), cv = local(g.cval), tb = 1u << t;
+    double c = 0.0, sn = 0.0;
+    if (g.op == OP_RY) {
+      c = std::cos(g.angle / 2.0);
+      sn = std::sin(g.angle / 2.0);
+    } else if (g.op == OP_ZPHASE) {
+      c = std::cos(g.angle);
+      sn = std::sin(g.angle);
+    }
+    for (int col = 0; col < 32; ++col)
+      for (uint32_t r = 0; r < 32; ++r) {
+        if ((r & tb) || (r & cm) != cv) continue;
+        pair_op(&M[2 * (32 * r + col)], &M[2 * (32 * (r | tb) + col)], g.op, c, sn);
+      }
+  }
+  *u = std::move(M);
+}
+
+void emit_dense(const std::vector<csim_gate>& run, uint64_t support, Program* p) {
+  DenseBlock b;
+  int j = 0;
+  for (int bit = 0; bit < p->n && j < 5; ++bit)
+    if ((support >> bit) & 1ull) b.q[j++] = (uint8_t)bit;
+  for (int bit = 0; j < 5; ++bit)  // fewer than five qubits: pad with others
+    if (!((support >> bit) & 1ull)) {
+      b.q[j++] = (uint8_t)bit;
+      support |= 1ull << bit;
+    }
+  std::sort(b.q, b.q + 5);
+  compose_block(run, b.q, &b.u);
+  make_dense_block(&b);
+  Step st;
+  st.kind = 2;
+  st.param = (int)p->dense.size();
+  p->dense.push_back(std::move(b));
+  p->steps.push_back(st);
+  p->stats.dense_blocks++;
+  p->stats.dense_gates += (int64_t)run.size();
+}
+
+void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p,
+                   bool allow_dense) {
+  *p = Program();
+  p->n = n;
+  p->mode = mode;
+  const char* form = std::getenv("CSIM_SWEEP_FORM");
+  p->scatter = form && std::strcmp(form, "scatter") == 0;
+  p->dense_engine = dense_engine_default();
+  for (const csim_gate& g : gates) p->amp_updates += gate_amp_updates(g, n);
+  if (mode == CSIM_EXEC_GATE || n < 7 || n > 34) {
+    for (const csim_gate& g : gates) {
+      Step s;
+      s.kind = 1;
+      s.g = g;
+      p->steps.push_back(s);
+    }
+    p->passes = (int64_t)p->steps.size();
+    p->stats.single = p->passes;
+    p->pass_amps = p->amp_updates;
+    return;
+  }
+  if (allow_dense && dense_enabled() && n >= 12 && !p->scatter) {
+    // runs of consecutive gates on at most five qubits (targets and
+    // controls); the long ones become dense blocks, the rest go to the sweep
+    // fuser in order
+    std::vector<csim_gate> pending, run;
+    uint64_t sup = 0;
+    auto close_run = [&]() {
+      if ((int)run.size() >= dense_min_gates()) {
+        if (!pending.empty()) build_segment(pending, p);
+        pending.clear();
+        emit_dense(run, sup, p);
+      } else {
+        pending.insert(pending.end(), run.begin(), run.end());
+      }
+      run.clear();
+      sup = 0;
+    };
+    for (const csim_gate& g : gates) {
+      const uint64_t s2 = sup | gate_support(g);
+      if (__builtin_popcountll(s2) > 5) close_run();
+      sup |= gate_support(g);
+      run.push_back(g);
+    }
+    close_run();
+    if (!pending.empty()) build_segment(pending, p);
+  } else {
+    build_segment(gates, p);
+  }
   p->passes = (int64_t)p->steps.size();
   for (const Step& s : p->steps)
-    p->pass_amps += s.kind == 0 ? std::ldexp(1.0, n) : gate_amp_updates(s.g, n);
+    p->pass_amps += s.kind != 1 ? std::ldexp(1.0, n) : gate_amp_updates(s.g, n);
   for (const Step& s : p->steps)
     if (s.kind == 0 && s.gather && !s.inplace) p->pingpong = true;
   p->stats.lut_entries = (int64_t)p->lut.size();
@@ -1144,6 +1259,12 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
       // one line per fused sweep: segments by kind, then the local ops
       for (size_t k = 0; k < p->steps.size(); ++k) {
         const Step& st = p->steps[k];
+        if (st.kind == 2) {
+          const DenseBlock& b = p->dense[(size_t)st.param];
+          std::fprintf(stderr, "[csim fuse] step %zu: dense block on qubits %d %d %d %d %d\n", k,
+                       b.q[0], b.q[1], b.q[2], b.q[3], b.q[4]);
+          continue;
+        }
         if (st.kind != 0) {
           std::fprintf(stderr, "[csim fuse] step %zu: single gate op %d target %d\n", k,
                        (int)st.g.op, (int)st.g.target);
@@ -1197,6 +1318,8 @@ cudaError_t upload_program(Program* p, cudaStream_t st) {
   if (e == cudaSuccess) e = up(&p->d_mentd, p->mentd, st);
   if (e == cudaSuccess) e = up(&p->d_angf, p->angf, st);
   if (e == cudaSuccess) e = up(&p->d_angd, p->angd, st);
+  for (DenseBlock& b : p->dense)
+    if (e == cudaSuccess) e = upload_dense(&b, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     free_program(p);
@@ -1311,6 +1434,7 @@ void free_program(Program* p) {
   for (uint32_t* q : p->d_src)
     if (q) cudaFree(q);
   p->d_src.clear();
+  for (DenseBlock& b : p->dense) free_dense(&b);
   p->src_tried = false;
   for (SweepParams& sp : p->params) {
     sp.src = nullptr;
@@ -1338,6 +1462,9 @@ cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec
     cudaError_t e;
     if (s.kind == 1) {
       e = launch_gate(buf[*cur], prec, p.n, s.g, st);
+    } else if (s.kind == 2) {
+      e = prec == CSIM_C64 ? launch_dense(buf[*cur], p.n, p.dense[(size_t)s.param], p.dense_engine, st)
+                           : cudaErrorInvalidValue;
     } else if (!s.gather) {
       if (k == 0 && zero_map && zero_steps >= 1) {
         SweepParams a = p.params[(size_t)s.param];
@@ -1367,8 +1494,6 @@ cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec
 }
 
 // ------------------------------------------------------------ host executor
-namespace {
-
 void pair_op(double* a, double* b, int op, double c, double s) {
   const double h = 0.70710678118654752440;
   const double ar = a[0], ai = a[1], br = b[0], bi = b[1];
@@ -1379,6 +1504,8 @@ void pair_op(double* a, double* b, int op, double c, double s) {
     default: a[0] = ar * c - ai * s; a[1] = ar * s + ai * c; b[0] = br * c + bi * s; b[1] = -br * s + bi * c; break;
   }
 }
+
+namespace {
 
 uint32_t emu_permute(const Program& p, const SweepParams& sp, uint32_t x) {
   for (int k = 0; k < sp.nseg; ++k) {
@@ -1539,6 +1666,40 @@ void emulate_program(const Program& p, std::vector<double>* amps) {
   std::vector<double>* cur = amps;
   std::vector<double>* nxt = &other;
   for (const Step& st : p.steps) {
+    if (st.kind == 2) {  // y = U x on every group of the block's qubits, FP64
+      const DenseBlock& b = p.dense[(size_t)st.param];
+      uint64_t qm = 0;
+      for (int j = 0; j < 5; ++j) qm |= 1ull << b.q[j];
+      std::vector<double> x(64), y(64);
+      for (uint64_t i = 0; i < N; ++i) {
+        if (i & qm) continue;
+        auto at = [&](int e) {
+          uint64_t a = i;
+          for (int j = 0; j < 5; ++j)
+            if ((e >> j) & 1) a |= 1ull << b.q[j];
+          return a;
+        };
+        for (int e = 0; e < 32; ++e) {
+          x[2 * e] = (*cur)[2 * at(e)];
+          x[2 * e + 1] = (*cur)[2 * at(e) + 1];
+        }
+        for (int r = 0; r < 32; ++r) {
+          double re = 0.0, im = 0.0;
+          for (int c = 0; c < 32; ++c) {
+            const double ur = b.u[2 * (32 * r + c)], ui = b.u[2 * (32 * r + c) + 1];
+            re += ur * x[2 * c] - ui * x[2 * c + 1];
+            im += ur * x[2 * c + 1] + ui * x[2 * c];
+          }
+          y[2 * r] = re;
+          y[2 * r + 1] = im;
+        }
+        for (int e = 0; e < 32; ++e) {
+          (*cur)[2 * at(e)] = y[2 * e];
+          (*cur)[2 * at(e) + 1] = y[2 * e + 1];
+        }
+      }
+      continue;
+    }
     if (st.kind == 1) {
       const csim_gate& g = st.g;
       double c = 0, s = 0;

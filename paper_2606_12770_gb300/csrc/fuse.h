@@ -7,14 +7,15 @@
 #include <unordered_map>
 #include <vector>
 
+#include "dense.h"
 #include "internal.h"
 #include "kernels.h"
 
 namespace csim {
 
 struct Step {
-  int kind = 0;    // 0 = fused sweep, 1 = single gate
-  int param = -1;  // index into Program::params (sweeps)
+  int kind = 0;    // 0 = fused sweep, 1 = single gate, 2 = dense 5-qubit block
+  int param = -1;  // index into Program::params (sweeps) or Program::dense (blocks)
   bool gather = false;  // the sweep has segments (moves data)
   bool inplace = false;  // ... and stores back to the gathered addresses (in == out)
   csim_gate g{};
@@ -29,6 +30,8 @@ struct FuseStats {
   int64_t conjugated = 0;   // in-place P^-1 . ops . P sweeps
   int64_t staged_sweeps = 0;  // sweeps that stage qubits above the tile
   int64_t staged_gates = 0;   // gates on staged qubits
+  int64_t dense_blocks = 0;   // runs of gates on at most 5 qubits applied as one dense block
+  int64_t dense_gates = 0;    // gates in those runs
 };
 
 struct Program {
@@ -75,13 +78,22 @@ struct Program {
   // none) and the first sweep of each table
   std::vector<int> src_tab, src_first;
   bool src_planned = false;
+  // dense 5-qubit blocks (complex64 programs only; Step kind 2) and the
+  // engine that applies them (DENSE_TC or DENSE_FP32)
+  std::vector<DenseBlock> dense;
+  int dense_engine = DENSE_TC;
 };
 
 // Build the program for `gates` on an n-qubit state.  FUSED mode needs
 // 7 <= n <= 34 (the warp tile and 32-bit chunk indices); other sizes fall
 // back to one launch per gate.  The sweep form is gather unless
 // CSIM_SWEEP_FORM=scatter.
-void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p);
+// With allow_dense (complex64 states of at least 12 qubits), a run of at
+// least CSIM_DENSE_MIN (default 10) consecutive gates that touch at most five
+// qubits becomes one dense block on the tensor cores (CSIM_DENSE=0 turns
+// this off; CSIM_DENSE_ENGINE=fp32 applies the blocks on the CUDA cores).
+void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p,
+                   bool allow_dense = false);
 cudaError_t upload_program(Program* p, cudaStream_t st);
 void free_program(Program* p);
 // After upload_program: precompute the source-index table of each distinct

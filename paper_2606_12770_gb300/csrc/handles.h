@@ -51,6 +51,8 @@ struct csim_sv {
   size_t bytes = 0;
   csim::Program prog;
   bool compiled = false;
+  csim::DenseBlock dense;            // the block of the latest csim_sv_apply_dense
+  unsigned int timeouts_seen = 0;    // the tensor-core wait timeouts already reported
 };
 
 namespace csim {

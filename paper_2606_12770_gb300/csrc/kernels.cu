@@ -669,9 +669,8 @@ __device__ __forceinline__ void op_tile_gate(uint32_t op, const LocalOp& o,
 // and in-thread position, so the gate pairs their registers.  Controls come
 // from the chunk index of the tile with the qubit clear (a control never
 // includes the target) and from the in-thread bits.
-template <typename R, int U, int J>
-__device__ __forceinline__ void stage_pairs(uint32_t kind, const LocalOp& o,
-                                            typename V2<R>::T (&v)[U][4],
+template <typename R, int U, int J, int KIND>
+__device__ __forceinline__ void stage_pairs(const LocalOp& o, typename V2<R>::T (&v)[U][4],
                                             const uint32_t (&ci)[U]) {
   const R c = Coef<R>::c(o), s = Coef<R>::s(o);
   const uint32_t ocm = o.cm, ocv = o.cv, lm = o.lm, lv = o.lv;
@@ -681,8 +680,17 @@ __device__ __forceinline__ void stage_pairs(uint32_t kind, const LocalOp& o,
     if ((ci[u] & ocm) != ocv) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (((uint32_t)j & lm) == lv) apply_pair<R>(v[u][j], v[u | (1 << J)][j], (int)kind, c, s);
+      if (((uint32_t)j & lm) == lv) apply_pair<R>(v[u][j], v[u | (1 << J)][j], KIND, c, s);
   }
+}
+
+// The gate kind is dispatched once per op, outside the tile loops.
+template <typename R, int U, int J>
+__device__ __forceinline__ void stage_kind(uint32_t kind, const LocalOp& o,
+                                           typename V2<R>::T (&v)[U][4], const uint32_t (&ci)[U]) {
+  if (kind == 2) return stage_pairs<R, U, J, 2>(o, v, ci);
+  if (kind == 1) return stage_pairs<R, U, J, 1>(o, v, ci);
+  stage_pairs<R, U, J, 0>(o, v, ci);
 }
 
 template <typename R, int U>
@@ -691,11 +699,11 @@ __device__ __forceinline__ void op_stage_gate(uint32_t kind, const LocalOp& o,
                                               const uint32_t (&ci)[U]) {
   const uint32_t j = o.target;
   if constexpr (U >= 2)
-    if (j == 0) return stage_pairs<R, U, 0>(kind, o, v, ci);
+    if (j == 0) return stage_kind<R, U, 0>(kind, o, v, ci);
   if constexpr (U >= 4)
-    if (j == 1) return stage_pairs<R, U, 1>(kind, o, v, ci);
+    if (j == 1) return stage_kind<R, U, 1>(kind, o, v, ci);
   if constexpr (U >= 8)
-    if (j == 2) return stage_pairs<R, U, 2>(kind, o, v, ci);
+    if (j == 2) return stage_kind<R, U, 2>(kind, o, v, ci);
 }
 
 // Apply the tile-local ops of one sweep to U tiles held by the warp.
@@ -707,12 +715,15 @@ __device__ __forceinline__ void apply_gates(const SweepParams& a, typename V2<R>
                                             const uint32_t (&ci)[U], uint32_t lane) {
   for (int k = 0; k < a.nops; ++k) {
     const LocalOp& o = a.ops[k];
-    const uint32_t op = o.op;
-    if (op >= 9) {
-      op_stage_gate<R, U>(op - 9, o, v, ci);
-      continue;
+    // one specialised body per op code (the code is a constant inside each case)
+    switch (o.op) {
+      case 0: op_tile_gate<R, U, false>(0, o, v, ci, lane); break;
+      case 1: op_tile_gate<R, U, false>(1, o, v, ci, lane); break;
+      case 2: op_tile_gate<R, U, false>(2, o, v, ci, lane); break;
+      case 3: op_tile_gate<R, U, false>(3, o, v, ci, lane); break;
+      case 6: op_tile_gate<R, U, false>(6, o, v, ci, lane); break;
+      default: op_stage_gate<R, U>((uint32_t)o.op - 9u, o, v, ci); break;
     }
-    op_tile_gate<R, U, false>(op, o, v, ci, lane);
   }
 }
 
@@ -1453,8 +1464,8 @@ void launch_staged(const void* in, void* out, uint32_t ntiles, const SweepParams
   // 128-thread blocks: the register file, not the block size, sets how many
   // warps a 4- or 8-tile sweep keeps resident
   if (a.nstage == 2) {
-    if constexpr (sizeof(R) == 4) return launch_staged_u<R, 4, 5, 128, 2>(in, out, ntiles, a, st);
-    return launch_staged_u<R, 4, 2, 128, 1>(in, out, ntiles, a, st);
+    if constexpr (sizeof(R) == 4) return launch_staged_u<R, 4, 6, 128, 2>(in, out, ntiles, a, st);
+    return launch_staged_u<R, 4, 4, 128, 1>(in, out, ntiles, a, st);
   }
   // eight tiles (32 complex64 or complex128 amplitudes a thread)
   if constexpr (sizeof(R) == 4) return launch_staged_u<R, 8, 3, 128, 1>(in, out, ntiles, a, st);
@@ -1581,10 +1592,10 @@ cudaError_t warm_r() {
   sweep_resident<R, 1, 4>();
   sweep_resident<R, 2, 4>();
   if constexpr (sizeof(R) == 4) {
-    sweep_resident<R, 4, 5, 5, 128>();
+    sweep_resident<R, 4, 6, 5, 128>();
     sweep_resident<R, 8, 3, 5, 128>();
   } else {
-    sweep_resident<R, 4, 2, 5, 128>();
+    sweep_resident<R, 4, 4, 5, 128>();
     sweep_resident<R, 8, 2, 5, 128>();
   }
   return e;

@@ -173,3 +173,25 @@ def test_staged_sweeps_match_oracle_on_host():
         assert st["staged_sweeps"] > 0 and st["staged_gates"] > 0
     _, st = N.emulate_fused(I.microbench_gates(30, 1000, 0), 30, None)
     assert st["passes"] <= 200
+
+
+def test_dense_blocks_match_oracle_on_host():
+    """Runs of at least ten gates on at most five qubits become dense blocks
+    (the host executor applies their composed 32 x 32 matrices in FP64): the
+    fused program against the dense oracle on a seeded stream of 5-qubit
+    blocks, one block per run; the vocabulary stream, whose gates spread over
+    all qubits, forms none."""
+    import numpy as np
+    import lbm_inputs as I
+    from oracle import statevec as S
+    from paper_2606_12770_gb300 import _native as N
+    n = 14
+    gates = I.dense_block_gates(n, 12, 3)
+    psi = I.random_unit_state(n, 3)
+    ref = S.DenseSim(n).run(psi.copy(), gates)
+    got, st = N.emulate_fused(gates, n, psi)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-13
+    assert st["dense_blocks"] == 12 and st["dense_gates"] == 12 * 16
+    assert st["passes"] == 12
+    _, st = N.emulate_fused(I.microbench_gates(30, 1000, 0), 30, None)
+    assert st["dense_blocks"] == 0
