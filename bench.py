@@ -351,7 +351,13 @@ def run_micro(args, rank, world, local, torch, G, dist):
     del x
     torch.cuda.empty_cache()
     mode = G.CSIM_EXEC_FUSED if args.exec == "fused" else G.CSIM_EXEC_GATE
-    sv.compile(records, mode)
+    tune = None
+    if mode == G.CSIM_EXEC_FUSED and not args.no_autotune:
+        # fusion width (staged qubits, dense blocks) picked by timed trials on
+        # this state, before the timed region; the state is restored
+        tune = sv.autotune(records, reps=1)
+    else:
+        sv.compile(records, mode)
     st = sv.stats()
     for _ in range(max(args.warmup, 0)):
         sv.run()
@@ -410,6 +416,7 @@ def run_micro(args, rank, world, local, torch, G, dist):
         "gpu_launches": args.steps * st["passes"],
         "clocks": clk,
     }
+    line["config"]["autotune"] = tune
     line["config"]["dense_blocks"] = st["dense_blocks"]
     line["config"]["staged_sweeps"] = st["staged_sweeps"]
     if st["dense_blocks"] and st["dense_blocks"] == st["passes"]:
@@ -767,6 +774,8 @@ def main():
                     sorted(SERVING))
     ap.add_argument("--exec", default="fused", choices=["fused", "gate"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="gate streams: keep the default fusion width instead of timing trials")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     args = ap.parse_args()
 

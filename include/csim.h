@@ -287,6 +287,29 @@ typedef struct {
 csim_status csim_sv_stats(const csim_sv* sv, csim_sv_stats_t* out);
 csim_status csim_sv_free(csim_sv* sv);
 
+/* Autotuner of a gate stream's fusion width.  Compiles the gate list (fused)
+ * with every staging width k = 0..3 (how many qubits above the warp tile a
+ * sweep may hold in registers) and, for complex64 states of at least 12
+ * qubits whose stream has runs on at most five qubits, with and without
+ * dense blocks; times `reps` runs of each on this state after one untimed run
+ * (CUDA events on the state's stream), and leaves the fastest program
+ * compiled, as csim_sv_compile would.  The state is restored afterwards: the
+ * call takes a device copy of it for the duration (CSIM_ERR_OOM when that
+ * copy cannot be allocated).  out receives the choice, its time per run and
+ * up to 8 trials.  Later csim_sv_compile calls on this state use the chosen
+ * width and dense-block setting. */
+typedef struct {
+  int32_t stage;        /* chosen staging width */
+  int32_t dense;        /* 1: dense blocks chosen */
+  double ms;            /* time per run of the chosen program */
+  int32_t n_trials;
+  int32_t trial_stage[8];
+  int32_t trial_dense[8];
+  double trial_ms[8];
+} csim_tune_t;
+csim_status csim_sv_autotune(csim_sv* sv, const csim_gate* gates, size_t n_gates, int32_t reps,
+                             csim_tune_t* out);
+
 /* A dense 5-qubit block: apply the 32 x 32 complex matrix u (row-major,
  * interleaved re/im doubles; element bit j of its row and column index is
  * qubit qubits[j]) to the complex64 state, for every group of 32 amplitudes

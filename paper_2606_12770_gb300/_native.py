@@ -34,6 +34,7 @@ EXPORTED = [
     "csim_pool_submit", "csim_pool_poll", "csim_pool_result", "csim_pool_stats", "csim_pool_free",
     "csim_pool_plan", "csim_compile", "csim_run_steps", "csim_checkpoint", "csim_restore",
     "csim_final_distribution", "csim_pool_cancel", "csim_pool_inject", "csim_sv_apply_dense",
+    "csim_sv_autotune",
 ]
 
 
@@ -126,6 +127,7 @@ def load():
         "csim_pool_free": ([VP], C.c_int),
         "csim_pool_cancel": ([VP, C.c_int64], C.c_int),
         "csim_sv_apply_dense": ([VP, P(C.c_int32), DP, C.c_int32], C.c_int),
+        "csim_sv_autotune": ([VP, VP, SZ, C.c_int32, VP], C.c_int),
         "csim_pool_inject": ([VP, C.c_int32, C.c_int64], C.c_int),
         "csim_pool_plan": ([C.c_uint64, C.c_uint64, C.c_int32, SZ, P(C.c_uint64), DP, DP, DP, DP,
                             P(C.c_uint64)], C.c_int),
@@ -318,6 +320,12 @@ class SvStats(C.Structure):
                 ("dense_blocks", C.c_int64), ("staged_sweeps", C.c_int64)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("stage", C.c_int32), ("dense", C.c_int32), ("ms", C.c_double),
+                ("n_trials", C.c_int32), ("trial_stage", C.c_int32 * 8),
+                ("trial_dense", C.c_int32 * 8), ("trial_ms", C.c_double * 8)]
+
+
 class DeviceState:
     """A borrowed device state exposed through ``__cuda_array_interface__`` as
     a (2^n, 2) array of float32 (complex64 state) or float64 (complex128 state)
@@ -387,6 +395,18 @@ class StateVector:
         sb = C.c_uint64()
         _check(_lib.csim_sv_info(self._h, C.byref(ns), C.byref(au), C.byref(sb)))
         return {"n_sweeps": ns.value, "amp_updates": au.value, "state_bytes": sb.value}
+
+    def autotune(self, gates, reps=1):
+        """csim_sv_autotune: time every staging width (and dense blocks where
+        they apply), keep the fastest compiled; returns the choice and trials."""
+        g = gates if isinstance(gates, np.ndarray) else gates_to_records(gates)
+        g = np.ascontiguousarray(g)
+        r = TuneResult()
+        _check(_lib.csim_sv_autotune(self._h, g.ctypes.data_as(C.c_void_p), g.shape[0], int(reps),
+                                     C.cast(C.byref(r), C.c_void_p)))
+        trials = [{"stage": r.trial_stage[i], "dense": r.trial_dense[i], "ms": r.trial_ms[i]}
+                  for i in range(r.n_trials)]
+        return {"stage": r.stage, "dense": r.dense, "ms": r.ms, "trials": trials}
 
     def apply_dense(self, qubits, u, engine=0):
         """csim_sv_apply_dense: the 32 x 32 matrix u (element bit j = qubits[j])

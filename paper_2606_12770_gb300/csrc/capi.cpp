@@ -743,6 +743,11 @@ csim_status csim_free(csim_circuit* c) {
 }
 
 // ------------------------------------------------------------ raw states
+namespace {
+csim_status sv_compile(csim_sv* s, const std::vector<Gate>& gl, csim_exec mode, bool allow_dense,
+                       int stage_k);
+}
+
 csim_status csim_sv_create(int32_t n, csim_precision prec, void* stream, csim_sv** out) {
   if (!out) return fail(CSIM_ERR_ARG, "null argument");
   *out = nullptr;
@@ -795,9 +800,16 @@ csim_status csim_sv_compile(csim_sv* s, const csim_gate* gates, size_t n_gates, 
         (s->n < 64 && (g.cmask >> s->n)))
       return fail(CSIM_ERR_ARG, "invalid gate record " + std::to_string(i));
   }
-  csim::free_program(&s->prog);
   std::vector<Gate> gl(gates, gates + n_gates);
-  csim::build_program(gl, s->n, mode, &s->prog, s->prec == CSIM_C64);
+  return sv_compile(s, gl, mode, s->prec == CSIM_C64 && s->tune_dense != 0, s->tune_stage);
+}
+
+namespace {
+csim_status sv_compile(csim_sv* s, const std::vector<Gate>& gl, csim_exec mode, bool allow_dense,
+                       int stage_k) {
+  s->compiled = false;
+  csim::free_program(&s->prog);
+  csim::build_program(gl, s->n, mode, &s->prog, allow_dense, stage_k);
   cudaError_t e = csim::upload_program(&s->prog, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "csim_sv_compile");
   if (s->prog.pingpong && !s->buf[1]) {
@@ -811,6 +823,81 @@ csim_status csim_sv_compile(csim_sv* s, const csim_gate* gates, size_t n_gates, 
   e = csim::build_src_index(&s->prog, s->stream, kSrcIndexTables);
   if (e != cudaSuccess) return cuda_fail(e, "csim_sv_compile: source index");
   s->compiled = true;
+  return CSIM_OK;
+}
+}  // namespace
+
+csim_status csim_sv_autotune(csim_sv* s, const csim_gate* gates, size_t n_gates, int32_t reps,
+                             csim_tune_t* out) {
+  if (!s || !out || (!gates && n_gates)) return fail(CSIM_ERR_ARG, "null argument");
+  if (reps < 1) return fail(CSIM_ERR_ARG, "reps must be at least 1");
+  *out = csim_tune_t{};
+  // validate through the plain compile first (and keep its program if the
+  // trials fail)
+  s->tune_stage = s->tune_dense = -1;
+  csim_status st = csim_sv_compile(s, gates, n_gates, CSIM_EXEC_FUSED);
+  if (st != CSIM_OK) return st;
+  std::vector<Gate> gl(gates, gates + n_gates);
+  void* saved = nullptr;
+  cudaError_t e = cudaMalloc(&saved, s->bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CSIM_ERR_OOM, "csim_sv_autotune: copy of the state");
+  }
+  e = cudaMemcpyAsync(saved, s->buf[s->cur], s->bytes, cudaMemcpyDeviceToDevice, s->stream);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  double best = 1e300;
+  int best_k = 0, best_d = 0;
+  const bool dense_ok = s->prec == CSIM_C64 && s->n >= 12;
+  for (int d = 0; d <= (dense_ok ? 1 : 0) && e == cudaSuccess; ++d) {
+    for (int k = 0; k <= csim::kMaxStage && e == cudaSuccess; ++k) {
+      st = sv_compile(s, gl, CSIM_EXEC_FUSED, d == 1, k);
+      if (st != CSIM_OK) break;
+      if (d == 1 && !s->prog.dense_on) break;
+      if (d == 1 && s->prog.stats.dense_blocks == 0) break;  // the same programs as without
+      e = csim::run_program(s->prog, s->buf, &s->cur, s->prec, s->stream);  // untimed
+      if (e == cudaSuccess) e = cudaEventRecord(a, s->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        e = csim::run_program(s->prog, s->buf, &s->cur, s->prec, s->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(b, s->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e != cudaSuccess) break;
+      const double per = (double)ms / reps;
+      if (out->n_trials < 8) {
+        out->trial_stage[out->n_trials] = k;
+        out->trial_dense[out->n_trials] = d;
+        out->trial_ms[out->n_trials] = per;
+        out->n_trials++;
+      }
+      if (per < best) {
+        best = per;
+        best_k = k;
+        best_d = d;
+      }
+    }
+  }
+  // the state the caller loaded, then the fastest program
+  if (e == cudaSuccess) {
+    s->cur = 0;
+    e = cudaMemcpyAsync(s->buf[0], saved, s->bytes, cudaMemcpyDeviceToDevice, s->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(saved);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_sv_autotune");
+  if (st != CSIM_OK) return st;
+  st = sv_compile(s, gl, CSIM_EXEC_FUSED, best_d == 1, best_k);
+  if (st != CSIM_OK) return st;
+  s->tune_stage = best_k;
+  s->tune_dense = best_d;
+  out->stage = best_k;
+  out->dense = best_d;
+  out->ms = best;
   return CSIM_OK;
 }
 

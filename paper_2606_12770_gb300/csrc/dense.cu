@@ -17,9 +17,10 @@
 // bits), and D = Xhi Whi^T + Xhi Wlo^T + Xlo Whi^T.  One CTA of four warps
 // per tile of 128 groups:
 //   1. the threads load the tile's 4096 amplitudes in address order
-//      (coalesced), split them and write both BF16 planes of X into shared
-//      memory in the no-swizzle K-major core-matrix layout (8 rows x 16 B
-//      per core matrix);
+//      (coalesced; issued while the previous tile's products and stores are
+//      still running), split them and write both BF16 planes of X into
+//      shared memory in the no-swizzle K-major core-matrix layout (8 rows x
+//      16 B per core matrix);
 //   2. one thread issues the 12 tcgen05.mma (M = 128, N = 64, K = 16; three
 //      products x four K steps) into a 64-column FP32 accumulator in TMEM
 //      and commits them to an mbarrier;
@@ -168,7 +169,7 @@ constexpr uint32_t kTmemCols = 64;
 constexpr uint32_t kIdescBf16M128N64 =
     (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
-__global__ void __launch_bounds__(128) dense5_tc_kernel(float2* __restrict__ st,
+__global__ void __launch_bounds__(128, 3) dense5_tc_kernel(float2* __restrict__ st,
                                                          const __grid_constant__ DenseParams P) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t* Ahi = sm;
@@ -221,12 +222,13 @@ __global__ void __launch_bounds__(128) dense5_tc_kernel(float2* __restrict__ st,
 #pragma unroll
   for (int j = 0; j < 5; ++j) a_el[j] = 1ull << P.q[j];
 
-  uint32_t phase = 0;
-  for (uint32_t t = blockIdx.x; t < P.ntiles; t += gridDim.x) {
-    uint64_t base = 0;
-    for (int j = 0; j < P.n - 12; ++j) base |= (uint64_t)((t >> j) & 1u) << P.nonq[7 + j];
-    // 1. load 32 amplitudes per thread in address order, split into BF16 planes
-    float2 v[32];
+  auto tile_base = [&](uint32_t t) {
+    uint64_t b = 0;
+    for (int j = 0; j < P.n - 12; ++j) b |= (uint64_t)((t >> j) & 1u) << P.nonq[7 + j];
+    return b;
+  };
+  // 32 amplitudes per thread in address order (coalesced across the warp)
+  auto load_tile = [&](uint64_t base, float2 (&v)[32]) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       uint64_t a = base | a_lo;
@@ -235,6 +237,15 @@ __global__ void __launch_bounds__(128) dense5_tc_kernel(float2* __restrict__ st,
         if ((i >> b) & 1) a |= a_hi[b];
       v[i] = __ldcs(st + a);
     }
+  };
+
+  uint32_t phase = 0;
+  float2 v[32];
+  uint32_t t = blockIdx.x;
+  uint64_t base = t < P.ntiles ? tile_base(t) : 0;
+  if (t < P.ntiles) load_tile(base, v);
+  for (; t < P.ntiles; t += gridDim.x) {
+    // 1. split the tile's amplitudes into the two BF16 planes of X
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       uint32_t g = g_lo, e = e_lo;
@@ -270,6 +281,10 @@ __global__ void __launch_bounds__(128) dense5_tc_kernel(float2* __restrict__ st,
       }
       tc_commit(sbar);
     }
+    // the next tile's loads go out while the products and this epilogue run
+    const uint32_t tn = t + gridDim.x;
+    const uint64_t base_next = tn < P.ntiles ? tile_base(tn) : 0;
+    if (tn < P.ntiles) load_tile(base_next, v);
     // bounded wait for the products; spin = 0 gives up at once (tests)
     bool ok = false;
     if (P.spin > 0) {
@@ -289,24 +304,23 @@ __global__ void __launch_bounds__(128) dense5_tc_kernel(float2* __restrict__ st,
     }
     phase ^= 1u;
     tc_fence_after();
-    // 3. every thread stores its group's 32 outputs
-    float d[64];
+    // 3. every thread stores its group's 32 outputs, 8 at a time
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      float part[16];
-      tmem_ld16(tmem + ((warp * 32u) << 16) + 16u * (uint32_t)c, part);
+      float d[16];
+      tmem_ld16(tmem + ((warp * 32u) << 16) + 16u * (uint32_t)c, d);
+      tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) d[16 * c + i] = part[i];
+      for (int k = 0; k < 8; ++k) {
+        const int e = 8 * c + k;
+        uint64_t a = base | a_row;
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+          if ((e >> j) & 1) a |= a_el[j];
+        __stcs(st + a, make_float2(d[2 * k], d[2 * k + 1]));
+      }
     }
-    tmem_ld_wait();
-#pragma unroll
-    for (int e = 0; e < 32; ++e) {
-      uint64_t a = base | a_row;
-#pragma unroll
-      for (int j = 0; j < 5; ++j)
-        if ((e >> j) & 1) a |= a_el[j];
-      __stcs(st + a, make_float2(d[2 * e], d[2 * e + 1]));
-    }
+    base = base_next;
     tc_fence_before();
     __syncthreads();
   }

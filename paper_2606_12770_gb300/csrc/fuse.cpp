@@ -982,7 +982,7 @@ void build_segment(const std::vector<csim_gate>& gates, Program* p) {
   const int n = p->n;
   std::vector<csim_gate> perm, local;
   std::vector<int> stage;  // staged qubits of the open group
-  const int kstage = (n - 7 >= 1) ? std::min(stage_limit(), n - 7) : 0;
+  const int kstage = (n - 7 >= 1) ? std::min(p->stage_k, n - 7) : 0;
   bool open = false;
   const double sweep_cost = std::ldexp(1.0, n);
   // groups and lone gates in circuit order; emitted after the scan so that a
@@ -1190,10 +1190,11 @@ void emit_dense(const std::vector<csim_gate>& run, uint64_t support, Program* p)
 }
 
 void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p,
-                   bool allow_dense) {
+                   bool allow_dense, int stage_k) {
   *p = Program();
   p->n = n;
   p->mode = mode;
+  p->stage_k = (stage_k >= 0 && stage_k <= kMaxStage) ? stage_k : stage_limit();
   const char* form = std::getenv("CSIM_SWEEP_FORM");
   p->scatter = form && std::strcmp(form, "scatter") == 0;
   p->dense_engine = dense_engine_default();
@@ -1210,7 +1211,8 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
     p->pass_amps = p->amp_updates;
     return;
   }
-  if (allow_dense && dense_enabled() && n >= 12 && !p->scatter) {
+  p->dense_on = allow_dense && dense_enabled() && n >= 12 && !p->scatter;
+  if (p->dense_on) {
     // runs of consecutive gates on at most five qubits (targets and
     // controls); the long ones become dense blocks, the rest go to the sweep
     // fuser in order

@@ -82,6 +82,8 @@ struct Program {
   // engine that applies them (DENSE_TC or DENSE_FP32)
   std::vector<DenseBlock> dense;
   int dense_engine = DENSE_TC;
+  int stage_k = kMaxStage;  // most qubits a sweep stages above the tile
+  bool dense_on = false;    // runs on <= 5 qubits were eligible for dense blocks
 };
 
 // Build the program for `gates` on an n-qubit state.  FUSED mode needs
@@ -92,8 +94,9 @@ struct Program {
 // least CSIM_DENSE_MIN (default 10) consecutive gates that touch at most five
 // qubits becomes one dense block on the tensor cores (CSIM_DENSE=0 turns
 // this off; CSIM_DENSE_ENGINE=fp32 applies the blocks on the CUDA cores).
+// stage_k (0..3) overrides the staging width (CSIM_STAGE, default 3).
 void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p,
-                   bool allow_dense = false);
+                   bool allow_dense = false, int stage_k = -1);
 cudaError_t upload_program(Program* p, cudaStream_t st);
 void free_program(Program* p);
 // After upload_program: precompute the source-index table of each distinct

@@ -53,6 +53,7 @@ struct csim_sv {
   bool compiled = false;
   csim::DenseBlock dense;            // the block of the latest csim_sv_apply_dense
   unsigned int timeouts_seen = 0;    // the tensor-core wait timeouts already reported
+  int tune_stage = -1, tune_dense = -1;  // csim_sv_autotune's choice (-1: defaults)
 };
 
 namespace csim {

@@ -84,3 +84,22 @@ def test_every_staging_width(k):
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
     staged = int(r.stdout.split("staged")[1].split()[0])
     assert (staged == 0) == (k == "0")
+
+
+def test_autotune_picks_a_trial_and_keeps_the_state():
+    """csim_sv_autotune times the stream at every staging width (and with
+    dense blocks) on the loaded state, restores that state, and leaves the
+    fastest program compiled: its result equals the oracle's."""
+    n = 20
+    gates = I.microbench_gates(n, 300, 8) + I.dense_block_gates(n, 4, 8)
+    psi0 = I.random_unit_state(n, 8)
+    ref = S.DenseSim(n).run(psi0.copy(), gates)
+    sv = G.StateVector(n, G.CSIM_C64)
+    sv.load(psi0)
+    tune = sv.autotune(gates, reps=2)
+    assert len(tune["trials"]) >= 5
+    assert (tune["stage"], tune["dense"]) in [(t["stage"], t["dense"]) for t in tune["trials"]]
+    assert tune["ms"] == min(t["ms"] for t in tune["trials"])
+    assert np.array_equal(sv.read(), psi0.astype(np.complex64).astype(np.complex128))
+    sv.run(1)
+    assert rel_l2(sv.read(), ref) < 1e-4
