@@ -464,9 +464,30 @@ int dense_tc_grid(uint32_t ntiles) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // 48 KB of operands per CTA: opt in above the default dynamic limit and
+    // ask for the largest shared-memory carveout, so that three CTAs (the
+    // register limit) share an SM
     cudaFuncSetAttribute(dense5_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kDenseSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense5_tc_kernel, 128, kDenseSmem);
+    cudaFuncSetAttribute(dense5_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dense5_tc_kernel, 128, kDenseSmem) !=
+        cudaSuccess)
+      per = 0;
+    cudaGetLastError();
+    // the same bound from the kernel's registers and the SM's shared memory,
+    // in case the runtime's figure assumes a smaller carveout
+    cudaFuncAttributes fa{};
+    int smem_sm = 0;
+    if (cudaFuncGetAttributes(&fa, dense5_tc_kernel) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) ==
+            cudaSuccess &&
+        fa.numRegs > 0) {
+      const int by_regs = 65536 / (128 * fa.numRegs);
+      const int by_smem = smem_sm / ((int)kDenseSmem + 1024);
+      const int calc = by_regs < by_smem ? by_regs : by_smem;
+      if (calc > per) per = calc;
+    }
+    cudaGetLastError();
     resident = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
   return (int)(ntiles < (uint32_t)resident ? ntiles : (uint32_t)resident);
