@@ -107,6 +107,42 @@ NCU_TRAFFIC = {
 L2_BYTES = 129 * 1000 * 1000
 
 
+def measure_l2_copy(torch, nbytes):
+    """Read + write GB/s of a device copy between two buffers of nbytes each
+    (both fit the 129 MB L2 together for the states this is used on): best
+    of 20 after warm-up, CUDA events."""
+    a = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda").fill_(1.0)
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    best = 1e30
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * nbytes / (best / 1000.0) / 1e9
+
+
+def measure_fp64_peak(torch, m=4096):
+    """FP64 TFLOP/s of a square DGEMM (2 m^3 FLOP), best of 5: the rate the
+    complex128 sweeps' FP64 work is set against."""
+    a = torch.randn(m, m, dtype=torch.float64, device="cuda")
+    b = torch.randn(m, m, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * m ** 3 / (best / 1000.0) / 1e12
+
+
 def max_over_ranks(x, dist, device="cuda"):
     """The largest value of x over all ranks: the job takes as long as its
     slowest replica.  dist None (one process) returns x."""
@@ -919,6 +955,15 @@ def main():
         # measured on the 28-qubit complex128 profile workload with ncu
         line["roofline"]["note"] = ("complex128 sweeps are bound by the FP64 pipe (83-86% of its "
                                     "cycles busy), not by HBM; see the fp64 sweep profile")
+        line["fp64_peak_tflops_measured"] = measure_fp64_peak(torch)
+    if (1 << n) * esz <= L2_BYTES:
+        # an L2-resident state: its sweeps against the L2 copy bandwidth
+        # measured here (the HBM figure above does not bound them)
+        l2 = measure_l2_copy(torch, (1 << n) * esz)
+        line["roofline_l2"] = {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s",
+                               "frac": achieved / l2,
+                               "peak_kind": "measured here: device copy of a buffer of the state's "
+                                            "size, best of 20, CUDA events"}
     if rank == 0 and not args.no_cpu_baseline:
         cfg = (Nx, tau, NC, K, dt, Nt)
         fd, o5_path = tempfile.mkstemp(suffix=".npz")

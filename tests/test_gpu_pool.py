@@ -106,14 +106,17 @@ def test_pool_requests_overlap_on_device():
     """Continuous batching runs requests side by side: in stream mode each
     request's device interval (its first and last event on its stream, on the
     pool's clock) is reported, and at least two admitted requests' intervals
-    intersect.  The requests are 24-26-qubit runs of d = 21, long enough that
+    intersect.  The requests are 26-27-qubit runs of d = 21 (several ms of
+    device work each), fused on the host before they are submitted, so that
     one still runs when the next is admitted."""
-    specs = [((8, 0.7, 2, 2, 0.1, 2), 21), ((8, 0.9, 2, 3, 0.1, 3), 21),
-             ((4, 1.1, 2, 4, 0.1, 8), 21), ((8, 0.6, 2, 2, 0.1, 4), 21)]
+    specs = [((16, 0.7, 2, 4, 0.1, 8), 21), ((16, 0.9, 2, 3, 0.1, 8), 21),
+             ((16, 1.1, 2, 4, 0.1, 4), 21), ((8, 0.6, 2, 4, 0.1, 16), 21)]
     inst = []
     for k, (cfg, d) in enumerate(specs):
         f0, _ = I.lbm_instance(cfg[0], 40 + k, tau=cfg[1])
-        inst.append((G.Circuit(*cfg, kappa_qsvt=10.0, d=d), f0))
+        c = G.Circuit(*cfg, kappa_qsvt=10.0, d=d)
+        c.compile()
+        inst.append((c, f0))
     pool = G.Pool(n_streams=4, max_qubits=30)
     ids = [pool.submit(c, f0, G.CSIM_C64) for c, f0 in inst]
     assert len(_drain(pool, len(ids))) == len(ids)
