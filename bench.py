@@ -992,6 +992,81 @@ def _rel_l2_at(torch, dev_state, o5):
     return float(np.linalg.norm(got - y) / np.linalg.norm(y))
 
 
+def label_layer(records):
+    """The QSVT circuit's label layer between the first U_L^dag and the next
+    U_L: the unprepare Hadamards, the projector-phase gates and the prepare
+    Hadamards (tags 4, 6, 1), the second such run of the gate list (the first
+    sits before the first call)."""
+    tags = records["tag"]
+    runs, k = [], 0
+    while k < len(records):
+        if tags[k] in (1, 4, 6):
+            j = k
+            while j < len(records) and tags[j] in (1, 4, 6):
+                j += 1
+            if (tags[k:j] == 6).any():
+                runs.append(records[k:j])
+            k = j
+        else:
+            k += 1
+    return runs[1] if len(runs) > 1 else runs[0]
+
+
+def label_layer_alternative(torch, G, n, layer, stream, reps=3):
+    """The label layer of the precision circuit applied alone to a seeded
+    random complex64 state of the circuit's size, three ways, each timed over
+    `reps` runs with CUDA events: the warp reduction the sweeps use (one
+    streaming sweep), a dense block on the tensor cores (split BF16x3; the
+    layer touches the five label qubits and the signal qubit, whose value
+    selects the block's matrix), and the same block on the CUDA cores in
+    FP32; the dense results against the warp reduction's, relative L2."""
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    x = torch.randn((1 << n, 2), generator=gen, device="cuda", dtype=torch.float32)
+    x /= torch.linalg.vector_norm(x)
+    sv = G.StateVector(n, G.CSIM_C64, stream)
+
+    def one(dense, engine):
+        old = os.environ.get("CSIM_DENSE_ENGINE")
+        os.environ["CSIM_DENSE_ENGINE"] = engine
+        try:
+            sv.compile(layer, stage=0, dense=dense)
+        finally:
+            if old is None:
+                os.environ.pop("CSIM_DENSE_ENGINE", None)
+            else:
+                os.environ["CSIM_DENSE_ENGINE"] = old
+        st = sv.stats()
+        sv.load_device(x.data_ptr())
+        sv.run(1)
+        torch.cuda.synchronize()
+        out = torch.as_tensor(sv.device_state(), device="cuda").clone()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sv.run(reps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return out, a.elapsed_time(b) / reps, st
+
+    ref, ms_warp, st0 = one(0, "tc")
+    tc, ms_tc, st1 = one(2, "tc")
+    err_tc = float(torch.linalg.vector_norm(tc - ref) / torch.linalg.vector_norm(ref))
+    del tc
+    f32, ms_f32, _ = one(2, "fp32")
+    err_f32 = float(torch.linalg.vector_norm(f32 - ref) / torch.linalg.vector_norm(ref))
+    del f32, ref, x
+    sv.close()
+    torch.cuda.empty_cache()
+    return {"gates": int(len(layer)), "qubits": n,
+            "warp_reduction": {"ms_per_pass": ms_warp, "passes": st0["passes"]},
+            "tensor_cores_bf16x3": {"ms_per_pass": ms_tc, "passes": st1["passes"],
+                                    "dense_blocks": st1["dense_blocks"],
+                                    "rel_l2_vs_warp_reduction": err_tc},
+            "cuda_cores_fp32": {"ms_per_pass": ms_f32, "rel_l2_vs_warp_reduction": err_f32},
+            "kept": "warp reduction: in the circuit it rides in the conjugated and multiplexer "
+                    "sweeps with the gather and the multiplexers, at no pass of its own"}
+
+
 def precision_comparison(torch, G, circ, cfg, f0, prec, o5_path, fused_s, stream):
     """The precision configuration's comparison, outside the timed region: the
     fused run just timed against the plain gate-by-gate complex128 GPU path on
@@ -1003,9 +1078,12 @@ def precision_comparison(torch, G, circ, cfg, f0, prec, o5_path, fused_s, stream
     err_fused = _rel_l2_at(torch, circ.device_state(), o5)
     ph = circ.export_phases()
     Nx, tau, NC, K, dt, Nt = cfg
+    layer = label_layer(circ.export_gates(1))
+    n = circ.info()["n_qubits"]
     circ.close()
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    alt = label_layer_alternative(torch, G, n, layer, stream) if prec == "c64" else None
     plain = G.Circuit(Nx, tau, NC, K, dt, Nt, phases=ph)
     plain.set_exec(G.CSIM_EXEC_GATE)
     plain.compile()
@@ -1030,6 +1108,7 @@ def precision_comparison(torch, G, circ, cfg, f0, prec, o5_path, fused_s, stream
                                     "rel_l2_vs_oracle": err_plain, "tolerance": 1e-12,
                                     "launches": n_gates},
         "runs_per_s_ratio": plain_s / fused_s,
+        "label_layer_alternative": alt,
         "oracle": (f"classical QSVT evaluation (O5, FP64) of the same phases, compared on the "
                    f"{o5['y'].size} physical entries"),
     }

@@ -287,6 +287,15 @@ typedef struct {
 csim_status csim_sv_stats(const csim_sv* sv, csim_sv_stats_t* out);
 csim_status csim_sv_free(csim_sv* sv);
 
+/* csim_sv_compile with the fuser's choices fixed: stage = how many qubits
+ * above the warp tile a sweep may stage (0-3; -1 the default), dense = 0 no
+ * dense blocks, 1 dense blocks for runs on at most five qubits (plus up to
+ * two selector qubits) that mix amplitudes across the warp tile, 2 for every
+ * such run of at least the minimum length, inside the tile too (-1 the
+ * default).  Dense blocks need a complex64 state of at least 12 qubits. */
+csim_status csim_sv_compile_opts(csim_sv* sv, const csim_gate* gates, size_t n_gates,
+                                 csim_exec mode, int32_t stage, int32_t dense);
+
 /* Autotuner of a gate stream's fusion width.  Compiles the gate list (fused)
  * with every staging width k = 0..3 (how many qubits above the warp tile a
  * sweep may hold in registers) and, for complex64 states of at least 12

@@ -34,7 +34,7 @@ EXPORTED = [
     "csim_pool_submit", "csim_pool_poll", "csim_pool_result", "csim_pool_stats", "csim_pool_free",
     "csim_pool_plan", "csim_compile", "csim_run_steps", "csim_checkpoint", "csim_restore",
     "csim_final_distribution", "csim_pool_cancel", "csim_pool_inject", "csim_sv_apply_dense",
-    "csim_sv_autotune",
+    "csim_sv_autotune", "csim_sv_compile_opts",
 ]
 
 
@@ -128,6 +128,7 @@ def load():
         "csim_pool_cancel": ([VP, C.c_int64], C.c_int),
         "csim_sv_apply_dense": ([VP, P(C.c_int32), DP, C.c_int32], C.c_int),
         "csim_sv_autotune": ([VP, VP, SZ, C.c_int32, VP], C.c_int),
+        "csim_sv_compile_opts": ([VP, VP, SZ, C.c_int, C.c_int32, C.c_int32], C.c_int),
         "csim_pool_inject": ([VP, C.c_int32, C.c_int64], C.c_int),
         "csim_pool_plan": ([C.c_uint64, C.c_uint64, C.c_int32, SZ, P(C.c_uint64), DP, DP, DP, DP,
                             P(C.c_uint64)], C.c_int),
@@ -376,9 +377,17 @@ class StateVector:
         _check(_lib.csim_sv_device(self._h, C.byref(p)))
         return DeviceState(p.value, self.n, self.precision, self)
 
-    def compile(self, gates, mode=CSIM_EXEC_FUSED):
+    def compile(self, gates, mode=CSIM_EXEC_FUSED, stage=None, dense=None):
+        """csim_sv_compile, or csim_sv_compile_opts when stage (0-3) or dense
+        (0 off, 1 runs mixing across the warp tile, 2 every long run) is given."""
         g = gates_to_records(gates)
-        _check(_lib.csim_sv_compile(self._h, g.ctypes.data_as(C.c_void_p), g.shape[0], int(mode)))
+        if stage is None and dense is None:
+            _check(_lib.csim_sv_compile(self._h, g.ctypes.data_as(C.c_void_p), g.shape[0],
+                                        int(mode)))
+        else:
+            _check(_lib.csim_sv_compile_opts(self._h, g.ctypes.data_as(C.c_void_p), g.shape[0],
+                                             int(mode), -1 if stage is None else int(stage),
+                                             -1 if dense is None else int(dense)))
 
     def run(self, reps=1):
         _check(_lib.csim_sv_run(self._h, int(reps)))

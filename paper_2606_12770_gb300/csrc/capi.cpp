@@ -745,7 +745,7 @@ csim_status csim_free(csim_circuit* c) {
 // ------------------------------------------------------------ raw states
 namespace {
 csim_status sv_compile(csim_sv* s, const std::vector<Gate>& gl, csim_exec mode, bool allow_dense,
-                       int stage_k);
+                       int stage_k, int dense_mode = -1);
 }
 
 csim_status csim_sv_create(int32_t n, csim_precision prec, void* stream, csim_sv** out) {
@@ -806,10 +806,10 @@ csim_status csim_sv_compile(csim_sv* s, const csim_gate* gates, size_t n_gates, 
 
 namespace {
 csim_status sv_compile(csim_sv* s, const std::vector<Gate>& gl, csim_exec mode, bool allow_dense,
-                       int stage_k) {
+                       int stage_k, int dense_mode) {
   s->compiled = false;
   csim::free_program(&s->prog);
-  csim::build_program(gl, s->n, mode, &s->prog, allow_dense, stage_k);
+  csim::build_program(gl, s->n, mode, &s->prog, allow_dense, stage_k, dense_mode);
   cudaError_t e = csim::upload_program(&s->prog, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "csim_sv_compile");
   if (s->prog.pingpong && !s->buf[1]) {
@@ -826,6 +826,21 @@ csim_status sv_compile(csim_sv* s, const std::vector<Gate>& gl, csim_exec mode, 
   return CSIM_OK;
 }
 }  // namespace
+
+csim_status csim_sv_compile_opts(csim_sv* s, const csim_gate* gates, size_t n_gates,
+                                 csim_exec mode, int32_t stage, int32_t dense) {
+  if (!s || (!gates && n_gates)) return fail(CSIM_ERR_ARG, "null argument");
+  if (stage < -1 || stage > csim::kMaxStage || dense < -1 || dense > 2)
+    return fail(CSIM_ERR_ARG, "stage must be in [-1, 3] and dense in [-1, 2]");
+  for (size_t i = 0; i < n_gates; ++i) {
+    const csim_gate& g = gates[i];
+    if (g.op > 3 || g.target >= s->n || ((g.cmask >> g.target) & 1ull) || (g.cval & ~g.cmask) ||
+        (s->n < 64 && (g.cmask >> s->n)))
+      return fail(CSIM_ERR_ARG, "invalid gate record " + std::to_string(i));
+  }
+  std::vector<Gate> gl(gates, gates + n_gates);
+  return sv_compile(s, gl, mode, s->prec == CSIM_C64 && dense != 0, stage, dense);
+}
 
 csim_status csim_sv_autotune(csim_sv* s, const csim_gate* gates, size_t n_gates, int32_t reps,
                              csim_tune_t* out) {
@@ -960,6 +975,7 @@ csim_status csim_sv_apply_dense(csim_sv* s, const int32_t* qubits, const double*
     return y;
   };
   csim::DenseBlock& b = s->dense;
+  b.nsel = 0;
   for (int j = 0; j < 5; ++j) b.q[j] = (uint8_t)qubits[order[j]];
   b.u.assign(2 * 1024, 0.0);
   for (int r = 0; r < 32; ++r)

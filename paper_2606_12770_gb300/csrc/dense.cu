@@ -179,9 +179,14 @@ __global__ void __launch_bounds__(128, 3) dense5_tc_kernel(float2* __restrict__ 
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 49160);
   const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
 
-  // W^T in both BF16 planes, already in the operand layout (16 KB)
+  // W^T of this CTA's selector value in both BF16 planes, already in the
+  // operand layout (16 KB); the grid is a multiple of 2^nsel and the
+  // selector bits are the lowest tile bits, so every tile of the CTA has it
+  const uint32_t y = blockIdx.x & ((1u << P.nsel) - 1u);
+  uint64_t ybits = 0;
+  for (int j = 0; j < P.nsel; ++j) ybits |= (uint64_t)((y >> j) & 1u) << P.sel[j];
   for (uint32_t i = tid; i < 1024u; i += 128u)
-    reinterpret_cast<uint4*>(Bhi)[i] = __ldg(P.bimg + i);
+    reinterpret_cast<uint4*>(Bhi)[i] = __ldg(P.bimg + 1024u * y + i);
   if (warp == 0) tmem_alloc(smem_u32(tslot), kTmemCols);
   if (tid == 0) {
     mbar_init(smem_u32(bar), 1);
@@ -223,8 +228,9 @@ __global__ void __launch_bounds__(128, 3) dense5_tc_kernel(float2* __restrict__ 
   for (int j = 0; j < 5; ++j) a_el[j] = 1ull << P.q[j];
 
   auto tile_base = [&](uint32_t t) {
-    uint64_t b = 0;
-    for (int j = 0; j < P.n - 12; ++j) b |= (uint64_t)((t >> j) & 1u) << P.nonq[7 + j];
+    uint64_t b = ybits;
+    const uint32_t th = t >> P.nsel;
+    for (int j = 0; j < P.n - 12 - P.nsel; ++j) b |= (uint64_t)((th >> j) & 1u) << P.nonq[7 + j];
     return b;
   };
   // 32 amplitudes per thread in address order (coalesced across the warp)
@@ -338,8 +344,8 @@ namespace {
 // amplitudes, U from shared memory (broadcast reads).
 __global__ void __launch_bounds__(256) dense5_fp32_kernel(float2* __restrict__ st,
                                                            const __grid_constant__ DenseParams P) {
-  __shared__ float2 U[1024];
-  for (uint32_t i = threadIdx.x; i < 1024u; i += blockDim.x) U[i] = P.uf[i];
+  __shared__ float2 Us[4 * 1024];
+  for (uint32_t i = threadIdx.x; i < (1024u << P.nsel); i += blockDim.x) Us[i] = P.uf[i];
   __syncthreads();
   const uint64_t ngroups = 1ull << (P.n - 5);
   uint64_t a_el[5];
@@ -347,8 +353,13 @@ __global__ void __launch_bounds__(256) dense5_fp32_kernel(float2* __restrict__ s
   for (int j = 0; j < 5; ++j) a_el[j] = 1ull << P.q[j];
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
        g += (uint64_t)gridDim.x * blockDim.x) {
+    // the low nsel bits of g select the matrix, the others place the group
+    const uint32_t y = (uint32_t)(g & ((1u << P.nsel) - 1u));
+    const float2* U = Us + 1024u * y;
     uint64_t base = 0;
-    for (int j = 0; j < P.n - 5; ++j) base |= ((g >> j) & 1ull) << P.nonq[j];
+    for (int j = 0; j < P.nsel; ++j) base |= (uint64_t)((y >> j) & 1u) << P.sel[j];
+    const uint64_t gh = g >> P.nsel;
+    for (int j = 0; j < P.n - 5 - P.nsel; ++j) base |= ((gh >> j) & 1ull) << P.nonq[j];
     float2 x[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
@@ -404,33 +415,52 @@ uint32_t dense_spin() {
 }  // namespace
 
 void make_dense_block(DenseBlock* b) {
-  // W (64 x 64 real, interleaved re/im) from U; the MMA's B operand is W^T
-  // viewed N x K (row n = W's row n), K-major: core matrices of 8 rows x 8
-  // BF16, the 8 along K adjacent (128 B), the 8-row groups 1024 B apart.
-  b->bimg.assign(2 * 4096, 0);
-  b->uf.assign(2 * 1024, 0.f);
-  for (int i = 0; i < 32; ++i)
-    for (int j = 0; j < 32; ++j) {
-      const double re = b->u[2 * (32 * i + j)], im = b->u[2 * (32 * i + j) + 1];
-      b->uf[2 * (32 * i + j)] = (float)re;
-      b->uf[2 * (32 * i + j) + 1] = (float)im;
-      const double w[2][2] = {{re, -im}, {im, re}};
-      for (int a = 0; a < 2; ++a)
-        for (int c = 0; c < 2; ++c) {
-          const int n = 2 * i + a, k = 2 * j + c;
-          const int off = ((((n >> 3) * 8 + (k >> 3)) << 7) + ((n & 7) << 4) + ((k & 7) << 1)) / 2;
-          const uint16_t hi = bf16_host(w[a][c]);
-          const uint16_t lo = bf16_host(w[a][c] - bf16_host_value(hi));
-          b->bimg[off] = hi;
-          b->bimg[4096 + off] = lo;
-        }
-    }
+  // W (64 x 64 real, interleaved re/im) from each U_y; the MMA's B operand
+  // is W^T viewed N x K (row n = W's row n), K-major: core matrices of 8 rows
+  // x 8 BF16, the 8 along K adjacent (128 B), the 8-row groups 1024 B apart.
+  const int ny = 1 << b->nsel;
+  b->bimg.assign((size_t)ny * 2 * 4096, 0);
+  b->uf.assign((size_t)ny * 2 * 1024, 0.f);
+  for (int y = 0; y < ny; ++y) {
+    const double* u = b->u.data() + (size_t)y * 2048;
+    float* uf = b->uf.data() + (size_t)y * 2048;
+    uint16_t* img = b->bimg.data() + (size_t)y * 8192;
+    for (int i = 0; i < 32; ++i)
+      for (int j = 0; j < 32; ++j) {
+        const double re = u[2 * (32 * i + j)], im = u[2 * (32 * i + j) + 1];
+        uf[2 * (32 * i + j)] = (float)re;
+        uf[2 * (32 * i + j) + 1] = (float)im;
+        const double w[2][2] = {{re, -im}, {im, re}};
+        for (int a = 0; a < 2; ++a)
+          for (int c = 0; c < 2; ++c) {
+            const int n = 2 * i + a, k = 2 * j + c;
+            const int off =
+                ((((n >> 3) * 8 + (k >> 3)) << 7) + ((n & 7) << 4) + ((k & 7) << 1)) / 2;
+            const uint16_t hi = bf16_host(w[a][c]);
+            const uint16_t lo = bf16_host(w[a][c] - bf16_host_value(hi));
+            img[off] = hi;
+            img[4096 + off] = lo;
+          }
+      }
+  }
 }
 
 cudaError_t upload_dense(DenseBlock* b, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
-  if (!b->d_bimg) e = cudaMalloc(&b->d_bimg, b->bimg.size() * 2);
-  if (e == cudaSuccess && !b->d_uf) e = cudaMalloc(&b->d_uf, b->uf.size() * 4);
+  if (b->d_bimg_bytes < b->bimg.size() * 2) {  // (re)allocate when the block grew
+    if (b->d_bimg) cudaFree(b->d_bimg);
+    b->d_bimg = nullptr;
+    b->d_bimg_bytes = 0;
+    e = cudaMalloc(&b->d_bimg, b->bimg.size() * 2);
+    if (e == cudaSuccess) b->d_bimg_bytes = b->bimg.size() * 2;
+  }
+  if (e == cudaSuccess && b->d_uf_bytes < b->uf.size() * 4) {
+    if (b->d_uf) cudaFree(b->d_uf);
+    b->d_uf = nullptr;
+    b->d_uf_bytes = 0;
+    e = cudaMalloc(&b->d_uf, b->uf.size() * 4);
+    if (e == cudaSuccess) b->d_uf_bytes = b->uf.size() * 4;
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_bimg, b->bimg.data(), b->bimg.size() * 2, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -443,6 +473,7 @@ void free_dense(DenseBlock* b) {
   if (b->d_uf) cudaFree(b->d_uf);
   b->d_bimg = nullptr;
   b->d_uf = nullptr;
+  b->d_bimg_bytes = b->d_uf_bytes = 0;
 }
 
 namespace {
@@ -495,18 +526,25 @@ int dense_tc_grid(uint32_t ntiles) {
 }  // namespace
 
 cudaError_t launch_dense(void* state, int n, const DenseBlock& b, int engine, cudaStream_t st) {
-  if (n < 5 || n > 34 || (engine == DENSE_TC && n < 12)) return cudaErrorInvalidValue;
+  if (b.nsel > 2 || n < 5 + b.nsel || n > 34 || (engine == DENSE_TC && n < 12 + b.nsel))
+    return cudaErrorInvalidValue;
   DenseParams P{};
   P.n = n;
-  uint32_t qm = 0;
+  uint64_t qm = 0, sm = 0;
   for (int j = 0; j < 5; ++j) {
     if (b.q[j] >= n || (j > 0 && b.q[j] <= b.q[j - 1])) return cudaErrorInvalidValue;
     P.q[j] = b.q[j];
-    qm |= 1u << b.q[j];
+    qm |= 1ull << b.q[j];
+  }
+  P.nsel = b.nsel;
+  for (int j = 0; j < b.nsel; ++j) {
+    if (b.sel[j] >= n || ((qm | sm) >> b.sel[j]) & 1ull) return cudaErrorInvalidValue;
+    P.sel[j] = b.sel[j];
+    sm |= 1ull << b.sel[j];
   }
   int k = 0;
   for (int bit = 0; bit < n; ++bit)
-    if (!((qm >> bit) & 1u)) P.nonq[k++] = (uint8_t)bit;
+    if (!(((qm | sm) >> bit) & 1ull)) P.nonq[k++] = (uint8_t)bit;
   P.bimg = b.d_bimg;
   P.uf = b.d_uf;
   P.spin = dense_spin();
@@ -517,11 +555,13 @@ cudaError_t launch_dense(void* state, int n, const DenseBlock& b, int engine, cu
     dense5_fp32_kernel<<<(int)grd, 256, 0, st>>>(static_cast<float2*>(state), P);
     return cudaGetLastError();
   }
-  // the tile's 12 local bits in ascending order of their state bit
+  // the tile's 12 local bits in ascending order of their state bit (the
+  // selector bits belong to the tile index)
   int lp[12], lt[12], m = 0;
   int gi = 0, qi = 0;
   for (int bit = 0; bit < n && m < 12; ++bit) {
-    if ((qm >> bit) & 1u) {
+    if ((sm >> bit) & 1ull) continue;
+    if ((qm >> bit) & 1ull) {
       lp[m] = bit;
       lt[m++] = 8 + qi++;
     } else if (gi < 7) {
@@ -536,7 +576,10 @@ cudaError_t launch_dense(void* state, int n, const DenseBlock& b, int engine, cu
   P.ntiles = 1u << (n - 12);
   P.timeouts = timeout_counter();
   if (!P.timeouts) return cudaErrorInvalidSymbol;
-  const int grd = dense_tc_grid(P.ntiles);
+  // a multiple of 2^nsel CTAs, so that a CTA's tiles share their selector value
+  int grd = dense_tc_grid(P.ntiles);
+  grd &= ~((1 << b.nsel) - 1);
+  if (grd < (1 << b.nsel)) grd = 1 << b.nsel;
   dense5_tc_kernel<<<grd, 128, kDenseSmem, st>>>(static_cast<float2*>(state), P);
   return cudaGetLastError();
 }

@@ -1120,6 +1120,25 @@ bool dense_enabled() {
   }();
   return v;
 }
+// CSIM_DENSE=2 also turns runs that stay inside the warp tile into dense
+// blocks (for measurements: the sweep fuser applies those without a pass
+// of their own).
+bool dense_inside_tile() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_DENSE");
+    return e && e[0] == '2';
+  }();
+  return v;
+}
+// A run earns a pass of its own only when it mixes amplitudes across the
+// warp tile: an H or RY on a qubit above it.  Tile gates, phases and
+// multi-controlled X (the gather's permutations) the sweeps apply for free.
+bool run_leaves_tile(const std::vector<csim_gate>& run, bool force) {
+  if (force) return true;
+  for (const csim_gate& g : run)
+    if (g.target >= 7 && (g.op == OP_H || g.op == OP_RY)) return true;
+  return false;
+}
 int dense_min_gates() {
   static const int v = [] {
     const char* e = std::getenv("CSIM_DENSE_MIN");
@@ -1135,17 +1154,20 @@ int dense_engine_default() {
 
 uint64_t gate_support(const csim_gate& g) { return g.cmask | (1ull << g.target); }
 
-// The 32 x 32 unitary of a run of gates on the qubits q[0..4] (ascending;
-// the run touches no other qubit), applied column by column in FP64.
-void compose_block(const std::vector<csim_gate>& run, const uint8_t (&q)[5], std::vector<double>* u) {
+// The 2^k x 2^k unitary of a run of gates on the qubits q[0..k-1] (the run
+// touches no other qubit; local bit j is qubit q[j]), composed column by
+// column in FP64.  M[r][c] is at 2 * (dim * r + c).
+std::vector<double> compose_run(const std::vector<csim_gate>& run, const std::vector<int>& q) {
+  const int k = (int)q.size();
+  const uint32_t dim = 1u << k;
   auto local = [&](uint64_t mask) {
     uint32_t m = 0;
-    for (int j = 0; j < 5; ++j)
+    for (int j = 0; j < k; ++j)
       if ((mask >> q[j]) & 1ull) m |= 1u << j;
     return m;
   };
-  std::vector<double> M(2 * 1024, 0.0);  // M[r][c], column c = the image of basis state c
-  for (int c = 0; c < 32; ++c) M[2 * (32 * c + c)] = 1.0;
+  std::vector<double> M(2 * (size_t)dim * dim, 0.0);
+  for (uint32_t c = 0; c < dim; ++c) M[2 * (dim * c + c)] = 1.0;
   for (const csim_gate& g : run) {
     int t = 0;
     while (q[t] != g.target) ++t;
@@ -1158,15 +1180,35 @@ void compose_block(const std::vector<csim_gate>& run, const uint8_t (&q)[5], std
       c = std::cos(g.angle);
       sn = std::sin(g.angle);
     }
-    for (int col = 0; col < 32; ++col)
-      for (uint32_t r = 0; r < 32; ++r) {
+    for (uint32_t col = 0; col < dim; ++col)
+      for (uint32_t r = 0; r < dim; ++r) {
         if ((r & tb) || (r & cm) != cv) continue;
-        pair_op(&M[2 * (32 * r + col)], &M[2 * (32 * (r | tb) + col)], g.op, c, sn);
+        pair_op(&M[2 * (dim * r + col)], &M[2 * (dim * (r | tb) + col)], g.op, c, sn);
       }
   }
-  *u = std::move(M);
+  return M;
 }
 
+std::vector<int> bits_of(uint64_t m) {
+  std::vector<int> v;
+  for (int b = 0; b < 64; ++b)
+    if ((m >> b) & 1ull) v.push_back(b);
+  return v;
+}
+
+void push_dense(DenseBlock&& b, size_t ngates, Program* p) {
+  make_dense_block(&b);
+  Step st;
+  st.kind = 2;
+  st.param = (int)p->dense.size();
+  p->dense.push_back(std::move(b));
+  p->steps.push_back(st);
+  p->stats.dense_blocks++;
+  p->stats.dense_gates += (int64_t)ngates;
+}
+
+// A run on at most five qubits: one 32 x 32 block (padded with other qubits
+// when it touches fewer).
 void emit_dense(const std::vector<csim_gate>& run, uint64_t support, Program* p) {
   DenseBlock b;
   int j = 0;
@@ -1178,19 +1220,64 @@ void emit_dense(const std::vector<csim_gate>& run, uint64_t support, Program* p)
       support |= 1ull << bit;
     }
   std::sort(b.q, b.q + 5);
-  compose_block(run, b.q, &b.u);
-  make_dense_block(&b);
-  Step st;
-  st.kind = 2;
-  st.param = (int)p->dense.size();
-  p->dense.push_back(std::move(b));
-  p->steps.push_back(st);
-  p->stats.dense_blocks++;
-  p->stats.dense_gates += (int64_t)run.size();
+  b.u = compose_run(run, std::vector<int>(b.q, b.q + 5));
+  push_dense(std::move(b), run.size(), p);
+}
+
+// A run on six or seven qubits whose matrix never mixes the values of one or
+// two of them (the selectors): one 32 x 32 block per selector value on the
+// other five.  Returns false when no such pair or single qubit exists.
+bool emit_dense_selected(const std::vector<csim_gate>& run, uint64_t support, Program* p) {
+  const std::vector<int> q = bits_of(support);
+  const int k = (int)q.size(), nsel = k - 5;
+  if (nsel < 1 || nsel > 2) return false;
+  const std::vector<double> M = compose_run(run, q);
+  const uint32_t dim = 1u << k;
+  for (int a = 0; a < k; ++a)
+    for (int b2 = (nsel == 2 ? a + 1 : a); b2 < (nsel == 2 ? k : a + 1); ++b2) {
+      const uint32_t smask = (1u << a) | (1u << b2);
+      bool diag = true;  // no entry between different selector values
+      for (uint32_t r = 0; r < dim && diag; ++r)
+        for (uint32_t c = 0; c < dim; ++c) {
+          if (((r ^ c) & smask) == 0) continue;
+          if (std::abs(M[2 * (dim * r + c)]) + std::abs(M[2 * (dim * r + c) + 1]) > 1e-13) {
+            diag = false;
+            break;
+          }
+        }
+      if (!diag) continue;
+      DenseBlock blk;
+      std::vector<int> rest;  // local indices of the five block qubits
+      for (int j = 0; j < k; ++j)
+        if (!((smask >> j) & 1u)) rest.push_back(j);
+      for (int j = 0; j < 5; ++j) blk.q[j] = (uint8_t)q[rest[j]];
+      blk.nsel = (uint8_t)nsel;
+      blk.sel[0] = (uint8_t)q[a];
+      if (nsel == 2) blk.sel[1] = (uint8_t)q[b2];
+      blk.u.assign((size_t)(2 << nsel) * 1024, 0.0);
+      for (int y = 0; y < (1 << nsel); ++y) {
+        uint32_t ybits = (y & 1) ? (1u << a) : 0u;
+        if (nsel == 2 && (y & 2)) ybits |= 1u << b2;
+        for (uint32_t r = 0; r < 32; ++r)
+          for (uint32_t c = 0; c < 32; ++c) {
+            uint32_t R = ybits, Cc = ybits;
+            for (int j = 0; j < 5; ++j) {
+              R |= ((r >> j) & 1u) << rest[j];
+              Cc |= ((c >> j) & 1u) << rest[j];
+            }
+            double* dst = blk.u.data() + (size_t)y * 2048 + 2 * (32 * r + c);
+            dst[0] = M[2 * (dim * R + Cc)];
+            dst[1] = M[2 * (dim * R + Cc) + 1];
+          }
+      }
+      push_dense(std::move(blk), run.size(), p);
+      return true;
+    }
+  return false;
 }
 
 void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p,
-                   bool allow_dense, int stage_k) {
+                   bool allow_dense, int stage_k, int dense_mode) {
   *p = Program();
   p->n = n;
   p->mode = mode;
@@ -1211,31 +1298,65 @@ void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, P
     p->pass_amps = p->amp_updates;
     return;
   }
-  p->dense_on = allow_dense && dense_enabled() && n >= 12 && !p->scatter;
+  // dense_mode: -1 the switches (CSIM_DENSE), 0 off, 1 runs that leave the
+  // tile, 2 runs inside the tile too
+  const bool dense_wanted = dense_mode < 0 ? dense_enabled() : dense_mode > 0;
+  const bool force_tile = dense_mode < 0 ? dense_inside_tile() : dense_mode == 2;
+  p->dense_on = allow_dense && dense_wanted && n >= 12 && !p->scatter;
   if (p->dense_on) {
     // runs of consecutive gates on at most five qubits (targets and
-    // controls); the long ones become dense blocks, the rest go to the sweep
+    // controls), or on six or seven of which one or two only select the
+    // matrix; the long ones become dense blocks, the rest go to the sweep
     // fuser in order
-    std::vector<csim_gate> pending, run;
-    uint64_t sup = 0;
-    auto close_run = [&]() {
-      if ((int)run.size() >= dense_min_gates()) {
+    std::vector<csim_gate> pending;
+    size_t i = 0;
+    const size_t N = gates.size();
+    while (i < N) {
+      uint64_t sup = 0, sup5 = 0;
+      size_t j = i, p5 = i;  // the run is gates[i, j); gates[i, p5) stay on <= 5 qubits
+      while (j < N && __builtin_popcountll(sup | gate_support(gates[j])) <= 7) {
+        sup |= gate_support(gates[j]);
+        ++j;
+        if (__builtin_popcountll(sup) <= 5) {
+          p5 = j;
+          sup5 = sup;
+        }
+      }
+      const std::vector<csim_gate> run(gates.begin() + i, gates.begin() + j);
+      const int minimum = dense_min_gates();
+      auto flush = [&]() {
         if (!pending.empty()) build_segment(pending, p);
         pending.clear();
+      };
+      const bool leaves = run_leaves_tile(run, force_tile);
+      if ((int)run.size() >= minimum && leaves && __builtin_popcountll(sup) <= 5) {
+        flush();
         emit_dense(run, sup, p);
-      } else {
-        pending.insert(pending.end(), run.begin(), run.end());
+        i = j;
+        continue;
       }
-      run.clear();
-      sup = 0;
-    };
-    for (const csim_gate& g : gates) {
-      const uint64_t s2 = sup | gate_support(g);
-      if (__builtin_popcountll(s2) > 5) close_run();
-      sup |= gate_support(g);
-      run.push_back(g);
+      if ((int)run.size() >= minimum && leaves) {
+        // try the selector form without disturbing the program when it fails
+        Program trial;
+        trial.n = p->n;
+        if (emit_dense_selected(run, sup, &trial)) {
+          flush();
+          emit_dense_selected(run, sup, p);
+          i = j;
+          continue;
+        }
+      }
+      if ((int)(p5 - i) >= minimum &&
+          run_leaves_tile(std::vector<csim_gate>(gates.begin() + i, gates.begin() + p5),
+                          force_tile)) {
+        flush();
+        emit_dense(std::vector<csim_gate>(gates.begin() + i, gates.begin() + p5), sup5, p);
+        i = p5;  // the rest of the run is scanned again
+        continue;
+      }
+      pending.push_back(gates[i]);
+      ++i;
     }
-    close_run();
     if (!pending.empty()) build_segment(pending, p);
   } else {
     build_segment(gates, p);
@@ -1675,6 +1796,9 @@ void emulate_program(const Program& p, std::vector<double>* amps) {
       std::vector<double> x(64), y(64);
       for (uint64_t i = 0; i < N; ++i) {
         if (i & qm) continue;
+        int ysel = 0;  // the matrix the selector bits of this group pick
+        for (int j = 0; j < b.nsel; ++j) ysel |= (int)((i >> b.sel[j]) & 1ull) << j;
+        const double* um = b.u.data() + (size_t)ysel * 2048;
         auto at = [&](int e) {
           uint64_t a = i;
           for (int j = 0; j < 5; ++j)
@@ -1688,7 +1812,7 @@ void emulate_program(const Program& p, std::vector<double>* amps) {
         for (int r = 0; r < 32; ++r) {
           double re = 0.0, im = 0.0;
           for (int c = 0; c < 32; ++c) {
-            const double ur = b.u[2 * (32 * r + c)], ui = b.u[2 * (32 * r + c) + 1];
+            const double ur = um[2 * (32 * r + c)], ui = um[2 * (32 * r + c) + 1];
             re += ur * x[2 * c] - ui * x[2 * c + 1];
             im += ur * x[2 * c + 1] + ui * x[2 * c];
           }

@@ -94,9 +94,11 @@ struct Program {
 // least CSIM_DENSE_MIN (default 10) consecutive gates that touch at most five
 // qubits becomes one dense block on the tensor cores (CSIM_DENSE=0 turns
 // this off; CSIM_DENSE_ENGINE=fp32 applies the blocks on the CUDA cores).
-// stage_k (0..3) overrides the staging width (CSIM_STAGE, default 3).
+// stage_k (0..3) overrides the staging width (CSIM_STAGE, default 3);
+// dense_mode overrides CSIM_DENSE (0 off, 1 runs that mix across the warp
+// tile, 2 every long run, -1 the switch).
 void build_program(const std::vector<csim_gate>& gates, int n, csim_exec mode, Program* p,
-                   bool allow_dense = false, int stage_k = -1);
+                   bool allow_dense = false, int stage_k = -1, int dense_mode = -1);
 cudaError_t upload_program(Program* p, cudaStream_t st);
 void free_program(Program* p);
 // After upload_program: precompute the source-index table of each distinct

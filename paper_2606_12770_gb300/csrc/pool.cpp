@@ -226,6 +226,7 @@ struct csim_pool {
   int64_t next_id = 1;
   csim_pool_stats_t stats{};
   cudaEvent_t epoch = nullptr;  // recorded on the origin stream at creation
+  cudaStream_t upload = nullptr;  // program uploads of submitted circuits
   // host-side fault injection (csim_pool_inject): request id -> what fails
   std::unordered_map<int64_t, int> inject;
 };
@@ -583,6 +584,10 @@ void destroy_pool(csim_pool* P) {
     if (s.st) cudaStreamDestroy(s.st);
   }
   if (P->epoch) cudaEventDestroy(P->epoch);
+  if (P->upload) {
+    cudaStreamSynchronize(P->upload);
+    cudaStreamDestroy(P->upload);
+  }
   if (P->origin) cudaStreamDestroy(P->origin);
   if (P->d_arena) cudaFree(P->d_arena);
   delete P;
@@ -637,6 +642,11 @@ csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out) {
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_out, 2 * sizeof(double));
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->upload, cudaStreamNonBlocking);
+  // pinned staging for typical requests now: growing it later (a pinned
+  // allocation) would stall the device work of the requests in flight
+  for (Slot& s : P->slots)
+    if (e == cudaSuccess) e = grow_pinned(&s, 256u << 10, 2u << 20);
   if (e == cudaSuccess) e = cudaEventCreate(&P->epoch);
   if (e == cudaSuccess) e = cudaEventRecord(P->epoch, P->origin);
   // load every kernel and fill the launch-configuration caches now: a lazy
@@ -665,7 +675,9 @@ csim_status csim_pool_submit(csim_pool* P, csim_circuit* c, const double* f0, cs
   }
   if ((int)c->pm.size() > kMaxPatterns) return pfail(CSIM_ERR_ARG, "too many mask patterns");
   std::string err;
-  if (!csim::ensure_program(c, P->slots[0].st, &err)) return pfail(CSIM_ERR_CUDA, err);
+  // a stream of its own for program uploads: the upload waits for itself,
+  // not for the requests already running on the slots
+  if (!csim::ensure_program(c, P->upload, &err)) return pfail(CSIM_ERR_CUDA, err);
   Request r;
   if (!csim::circuit_rhs(c, f0, &r.idx, &r.val, &err)) return pfail(CSIM_ERR_ARG, err);
   r.c = c;

@@ -132,3 +132,69 @@ def test_tensor_core_wait_times_out_cleanly():
                        text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "timeout reported" in r.stdout and r.stdout.strip().endswith("ok"), r.stdout
+
+
+def _label_layer(n_x=4):
+    """The label layer of the precision circuit's family member (between the
+    first U_L^dag and the next U_L): 13 gates on the five label qubits, the
+    signal and the value-encoding target; the latter two only select the
+    matrix (it is diagonal in them)."""
+    import bench
+    f0, tau = I.lbm_instance(n_x, 1, tau_range=(0.6, 1.2))
+    c = G.Circuit(n_x, tau, 2, 4, 0.1, 16, kappa_qsvt=1000.0, d=13)
+    return bench.label_layer(c.export_gates(1)), c.info()["n_qubits"]
+
+
+@pytest.mark.parametrize("engine,tol", [("tc", 3e-5), ("fp32", 1e-6)])
+def test_label_layer_as_selector_block(engine, tol, monkeypatch):
+    """The QSVT label layer as one dense block with two selector qubits (a
+    32 x 32 matrix per value of t and s) against the warp reduction the sweeps
+    use and against the oracle's naive simulator, at 24 qubits."""
+    layer, n = _label_layer()
+    gates = [(int(g["op"]), int(g["target"]), int(g["cmask"]), int(g["cval"]),
+              float(g["angle"]), 0) for g in layer]
+    psi0 = I.random_unit_state(n, 3)
+    ref = S.AxisSim(n).run(psi0.copy(), gates)
+    monkeypatch.setenv("CSIM_DENSE_ENGINE", engine)
+    sv = G.StateVector(n, G.CSIM_C64)
+    sv.load(psi0)
+    sv.compile(layer, stage=0, dense=2)
+    st = sv.stats()
+    assert st["dense_blocks"] == 1 and st["passes"] == 1
+    sv.run(1)
+    dense = sv.read()
+    sv.load(psi0)
+    sv.compile(layer, stage=0, dense=0)
+    assert sv.stats()["dense_blocks"] == 0
+    sv.run(1)
+    warp = sv.read()
+    e1, e2 = rel_l2(dense, ref), rel_l2(dense, warp)
+    print(f"label layer as a selector block, {engine}: vs oracle {e1:.3e}, vs warp reduction {e2:.3e}")
+    assert e1 < tol and e2 < tol and rel_l2(warp, ref) < 1e-6
+
+
+@pytest.mark.parametrize("engine,tol", [("tc", 3e-5), ("fp32", 1e-6)])
+def test_selector_block_above_the_tile(engine, tol, monkeypatch):
+    """A run on five qubits above the tile and one selector qubit (a phase on
+    it controlled by two of the five, between layers of RY and H) as one dense
+    block, at 20 qubits, against the oracle."""
+    n = 20
+    rng = np.random.default_rng(12)
+    q = [8, 11, 13, 16, 19]
+    sel = 9
+    gates = [(2, t, 0, 0, float(rng.uniform(0, 6.28)), 0) for t in q]
+    gates += [(0, q[1], 1 << q[0], 1 << q[0], 0.0, 0)]
+    m = (1 << q[2]) | (1 << q[4])
+    gates += [(0, sel, m, m, 0.0, 0), (3, sel, 0, 0, 0.37, 0), (0, sel, m, m, 0.0, 0)]
+    gates += [(1, t, 0, 0, 0.0, 0) for t in q]
+    psi0 = I.random_unit_state(n, 12)
+    ref = S.DenseSim(n).run(psi0.copy(), gates)
+    monkeypatch.setenv("CSIM_DENSE_ENGINE", engine)
+    sv = G.StateVector(n, G.CSIM_C64)
+    sv.load(psi0)
+    sv.compile(gates)
+    assert sv.stats()["dense_blocks"] == 1
+    sv.run(1)
+    err = rel_l2(sv.read(), ref)
+    print(f"selector block above the tile, {engine}: rel L2 {err:.3e}")
+    assert err < tol
