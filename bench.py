@@ -102,6 +102,10 @@ NCU_TRAFFIC = {
     # after the sparse init the first sweep touches only the tiles of b and
     # the first conjugated gather reads only its index table)
     ("85ac97949cbcb0a7", "precision-nx64-k4-nt16-d13-c64"): 64.48e9,
+    # the same shaped kernels after the staged-qubit and block-size changes:
+    # the 28-qubit family member's 14 launches (dram__bytes_read + write,
+    # one pass), mean per launch scaled by the 16x larger state
+    ("bc1adbfeda1ad1d4", "precision-nx64-k4-nt16-d13-c64"): 64.81e9,
 }
 
 L2_BYTES = 129 * 1000 * 1000
