@@ -536,8 +536,10 @@ def run_batch(args, rank, world, local, torch, G, dist):
     results = {}
     clk = None
     graph_error = None
-    for graphs in (False, True):
-        pool = G.Pool(n_streams=8, hbm_budget=budget, max_qubits=32, use_graphs=graphs)
+    for mode in ("streams", "graphs", "persistent"):
+        graphs = mode == "graphs"
+        pool = G.Pool(n_streams=8, hbm_budget=budget, max_qubits=32, use_graphs=graphs,
+                      persistent=mode == "persistent")
         try:
             for _ in range(max(args.warmup, 1)):
                 pool_step(pool)
@@ -546,7 +548,7 @@ def run_batch(args, rank, world, local, torch, G, dist):
                 raise
             graph_error = str(e)
             pool.close()
-            break
+            continue
         torch.cuda.synchronize()
         clocks = ClockSampler(local)
         clocks.start()
@@ -559,7 +561,7 @@ def run_batch(args, rank, world, local, torch, G, dist):
         st = pool.stats()
         st["saved_per_step"] = (st["sparse_saved_bytes"] - saved0) / args.steps
         pool.close()
-        results["graphs" if graphs else "streams"] = (statistics.median(ts), st)
+        results[mode] = (statistics.median(ts), st)
     # the per-instance loop: one instance at a time through csim_init/run/postselect
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -587,6 +589,8 @@ def run_batch(args, rank, world, local, torch, G, dist):
                    "runs_per_s": count * world / step_s,
                    "streams_step_s": results["streams"][0],
                    "graphs_step_s": results["graphs"][0] if "graphs" in results else graph_error,
+                   "persistent_step_s": (results["persistent"][0] if "persistent" in results
+                                         else None),
                    "per_instance_loop_s": loop_s,
                    "pool_budget_bytes": st["budget"], "pool_peak_bytes": st["peak_bytes"],
                    "timing": "host wall clock per step (work spread over the pool's streams)",

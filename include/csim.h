@@ -373,6 +373,8 @@ typedef struct {
   uint64_t hbm_budget;  /* arena bytes; 0: 90% of the free device memory */
   int32_t use_graphs;   /* 1: one CUDA graph launch per admission pass */
   uint32_t min_block;   /* smallest arena block in bytes, a multiple of 256; 0: 1 MiB */
+  int32_t persistent;   /* 1: the sweeps of all requests admitted in one pass run in one
+                           persistent launch (complex64 passes; see below) */
 } csim_pool_opts;
 typedef struct {
   int64_t submitted, admitted, completed, rejected, queued, running;
@@ -382,9 +384,10 @@ typedef struct {
   uint64_t sparse_saved_bytes; /* state reads and writes that admitted requests'
                                   sparse inits left out: one state's bytes per
                                   request with one leading sweep, three with two */
-  int64_t failed;         /* requests that failed on the host before their device
-                             work (a refused pinned or arena allocation) */
+  int64_t failed;         /* requests that failed: refused pinned or arena allocations,
+                             and every request of a persistent pass whose wait ran out */
   int64_t cancelled;      /* csim_pool_cancel calls that took effect */
+  int64_t batch_launches; /* admission passes run as one persistent launch */
 } csim_pool_stats_t;
 
 csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out);
@@ -429,8 +432,24 @@ csim_status csim_pool_cancel(csim_pool* p, int64_t id);
 /* Host-side fault injection for tests: make an allocation of request `id`
  * fail at its admission as if the host or the arena refused it
  * (CSIM_INJECT_PINNED: the pinned staging; CSIM_INJECT_ARENA: the arena
- * blocks; CSIM_INJECT_NONE clears).  Nothing is faulted on the device. */
-enum { CSIM_INJECT_NONE = 0, CSIM_INJECT_PINNED = 1, CSIM_INJECT_ARENA = 2 };
+ * blocks; CSIM_INJECT_NONE clears), or, in persistent mode, keep one work
+ * item of the request's second sweep from signalling its completion
+ * (CSIM_INJECT_BATCH_SIGNAL): the items that depend on it wait out their
+ * time limit and the whole pass reports CSIM_ERR_TIMEOUT.  Nothing is faulted
+ * on the device.
+ *
+ * Persistent mode (csim_pool_opts.persistent): an admission pass of complex64
+ * requests runs as the requests' uploads and inits, one launch of a
+ * persistent kernel over the sweeps of all of them, then their norms and
+ * compactions, all on one stream (one CUDA graph with use_graphs is not
+ * combined with it).  The kernel's co-resident CTAs take work items (a tile
+ * range of one sweep of one request) from a queue in device memory, level by
+ * level, and wait, with a 2 s limit per wait, for the previous sweep of the
+ * same request.  Passes with complex128 requests, and programs with steps
+ * other than sweeps, take the stream path.  The results agree with the run
+ * alone within rounding (the kernel uses the general op interpreter). */
+enum { CSIM_INJECT_NONE = 0, CSIM_INJECT_PINNED = 1, CSIM_INJECT_ARENA = 2,
+       CSIM_INJECT_BATCH_SIGNAL = 3 };
 csim_status csim_pool_inject(csim_pool* p, int32_t what, int64_t id);
 csim_status csim_pool_stats(const csim_pool* p, csim_pool_stats_t* out);
 /* Waits for running work, then frees everything (pending results are lost). */

@@ -19,7 +19,7 @@ CSIM_OK, CSIM_ERR_ARG, CSIM_ERR_TOO_LARGE, CSIM_ERR_OOM = 0, -1, -2, -3
 CSIM_ERR_CUDA, CSIM_ERR_STATE, CSIM_ERR_TIMEOUT, CSIM_ERR_NUMERIC = -4, -5, -6, -7
 CSIM_C64, CSIM_C128 = 0, 1
 CSIM_EXEC_FUSED, CSIM_EXEC_GATE = 0, 1
-CSIM_INJECT_NONE, CSIM_INJECT_PINNED, CSIM_INJECT_ARENA = 0, 1, 2
+CSIM_INJECT_NONE, CSIM_INJECT_PINNED, CSIM_INJECT_ARENA, CSIM_INJECT_BATCH_SIGNAL = 0, 1, 2, 3
 _NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_TOO_LARGE", -3: "ERR_OOM", -4: "ERR_CUDA",
           -5: "ERR_STATE", -6: "ERR_TIMEOUT", -7: "ERR_NUMERIC"}
 
@@ -483,7 +483,7 @@ def norms_noalloc(state_ptr, n, prec, pm, pv, out_ptr, stream=None):
 
 class PoolOpts(C.Structure):
     _fields_ = [("n_streams", C.c_int32), ("max_qubits", C.c_int32), ("hbm_budget", C.c_uint64),
-                ("use_graphs", C.c_int32), ("min_block", C.c_uint32)]
+                ("use_graphs", C.c_int32), ("min_block", C.c_uint32), ("persistent", C.c_int32)]
 
 
 class PoolStats(C.Structure):
@@ -492,18 +492,20 @@ class PoolStats(C.Structure):
                 ("bytes_in_use", C.c_uint64), ("peak_bytes", C.c_uint64), ("budget", C.c_uint64),
                 ("graph_launches", C.c_int64), ("src_tables", C.c_int64),
                 ("sparse_saved_bytes", C.c_uint64), ("failed", C.c_int64),
-                ("cancelled", C.c_int64)]
+                ("cancelled", C.c_int64), ("batch_launches", C.c_int64)]
 
 
 class Pool:
     """Handle of ``csim_pool``: admission under an HBM budget, concurrent streams,
     optional CUDA-graph admission waves (batching and serving)."""
 
-    def __init__(self, n_streams=4, hbm_budget=0, max_qubits=32, use_graphs=False, min_block=0):
+    def __init__(self, n_streams=4, hbm_budget=0, max_qubits=32, use_graphs=False, min_block=0,
+                 persistent=False):
         lib = load()
         o = PoolOpts()
         o.n_streams, o.hbm_budget, o.max_qubits = int(n_streams), int(hbm_budget), int(max_qubits)
         o.use_graphs, o.min_block = int(bool(use_graphs)), int(min_block)
+        o.persistent = int(bool(persistent))
         h = C.c_void_p()
         _check(lib.csim_pool_create(C.cast(C.byref(o), C.c_void_p), C.byref(h)))
         self._h = h

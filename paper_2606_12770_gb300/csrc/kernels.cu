@@ -1656,3 +1656,185 @@ cudaError_t launch_compact(const void* state, int prec, double* d_out, uint64_t 
 }
 
 }  // namespace csim
+
+// ------------------------------------------------------ persistent batches
+namespace csim {
+namespace {
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchU = 2;
+constexpr uint64_t kBatchWaitNs = 2000000000ull;  // a dependency wait gives up after 2 s
+
+// One persistent launch over the sweeps of many programs.  Every CTA takes
+// the next item (a range of tile counters of one step) from a queue in
+// global memory; an item waits, with a time limit, until every item of the
+// step it depends on (the same program's previous step) has signalled; then
+// its warps apply the step to their tiles with the general op interpreter
+// and the CTA signals.  Items are queued level by level (step k of every
+// program before step k + 1 of any), so a waiting CTA only waits on items
+// that CTAs already hold: the grid is co-resident, nothing waits for work
+// that cannot start.  When a wait runs out the kernel records the error and
+// every CTA stops at its next wait.
+template <typename R>
+__global__ void __launch_bounds__(kBatchThreads, 2)
+    batch_kernel(const BatchStep* __restrict__ steps, const BatchItem* __restrict__ items,
+                 uint32_t nitems, uint32_t* done, BatchCtl* ctl) {
+  using T = typename V2<R>::T;
+  constexpr int U = kBatchU;
+  __shared__ uint32_t s_item;
+  __shared__ int s_ok;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctl->next, 1u);
+    __syncthreads();
+    const uint32_t k = s_item;
+    if (k >= nitems) break;
+    const BatchItem it = items[k];
+    const BatchStep& bs = steps[it.step];
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      if (bs.dep >= 0) {
+        const uint32_t need = steps[bs.dep].nitems;
+        const uint64_t t0 = global_ns();
+        while (*reinterpret_cast<volatile uint32_t*>(done + bs.dep) < need) {
+          if (*reinterpret_cast<volatile uint32_t*>(&ctl->error) != 0u) {
+            ok = 0;
+            break;
+          }
+          if (global_ns() - t0 > kBatchWaitNs) {
+            atomicOr(&ctl->error, 1u);
+            ok = 0;
+            break;
+          }
+          __nanosleep(200);
+        }
+      }
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const SweepParams& a = *bs.sp;
+    const T* in = static_cast<const T*>(bs.in);
+    T* out = static_cast<T*>(bs.out);
+    const int nfe = (int)bs.nfe;
+    const uint32_t fmask = bs.fmask;
+    // this warp's counters: c = c0 + wib U + u + j kBatchThreads/32 U; the low
+    // nfe counter bits are fixed per warp (c0 is a multiple of the stride)
+    uint32_t L[U];
+    const uint32_t cw = it.c0 + wib * U;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      uint32_t d = 0;
+      for (int j = 0; j < nfe; ++j) d |= (((cw + (uint32_t)u) >> j) & 1u) << a.fast[j];
+      L[u] = nfe > 0 ? d : (uint32_t)u;
+    }
+    uint32_t H = 0;
+    if (nfe > 0) {
+      uint32_t hv = cw >> nfe;
+      for (int b = 0; hv != 0u && b < 32; ++b) {
+        if ((fmask >> b) & 1u) continue;
+        H |= (hv & 1u) << b;
+        hv >>= 1;
+      }
+    } else {
+      H = cw;
+    }
+    const uint32_t stride = (kBatchThreads / 32) * U;
+    for (uint32_t c = cw; c < it.c1; c += stride) {
+      uint32_t ci[U], mv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) mv[u] = ci[u] = ((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane;
+      H = nfe > 0 ? (((H | fmask) + bs.hstep) & ~fmask) : (H + stride);
+      uint32_t wd[kPrefetchMux][U];
+      prefetch_mux<U>(a, ci, wd);
+      T v[U][4];
+      if (!a.scatter) {
+        if (a.src) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) mv[u] = __ldcs(a.src + ci[u]);
+        } else {
+          permute<U>(a, mv);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)mv[u] << 2), v[u]);
+        apply_ops<R, U>(a, v, ci, lane, wd);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          store_chunk(out + ((size_t)(a.inplace ? mv[u] : ci[u]) << 2), v[u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)ci[u] << 2), v[u]);
+        apply_ops<R, U>(a, v, ci, lane, wd);
+        if (a.src) {
+#pragma unroll
+          for (int u = 0; u < U; ++u) mv[u] = __ldcs(a.src + ci[u]);
+        } else {
+          permute<U>(a, mv);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) store_chunk(out + ((size_t)mv[u] << 2), v[u]);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (k != ctl->drop_item) atomicAdd(done + it.step, 1u);
+    }
+  }
+}
+
+}  // namespace
+
+uint32_t batch_stride() { return (kBatchThreads / 32) * kBatchU; }
+
+void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t* fmask,
+                 uint32_t* hstep) {
+  // tile order of the persistent kernel: the fast bits that fit its stride
+  const uint32_t stride = batch_stride();
+  int f = a.nstage > 0 ? 0 : a.nfast;
+  while (f > 0 && (stride & ((1u << f) - 1u)) != 0u) --f;
+  if (f > 0 && (1u << f) < (uint32_t)kBatchU) f = 0;
+  uint32_t fm = 0, hs = 0;
+  for (int j = 0; j < f; ++j) fm |= 1u << a.fast[j];
+  uint32_t hv = stride >> f;
+  for (int b = 0; hv != 0u && b < 32; ++b) {
+    if ((fm >> b) & 1u) continue;
+    hs |= (hv & 1u) << b;
+    hv >>= 1;
+  }
+  (void)ntiles;
+  *nfe = (uint32_t)f;
+  *fmask = fm;
+  *hstep = hs;
+}
+
+int batch_grid() {
+  static int resident = 0;
+  if (!resident) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<float>, kBatchThreads, 0);
+    resident = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  return resident;
+}
+
+cudaError_t launch_batch(const BatchStep* d_steps, const BatchItem* d_items, uint32_t nitems,
+                         uint32_t* d_done, BatchCtl* d_ctl, cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  // co-resident CTAs only: a waiting CTA must never hold up the CTA whose
+  // item it waits for
+  batch_kernel<float><<<batch_grid(), kBatchThreads, 0, st>>>(d_steps, d_items, nitems, d_done,
+                                                              d_ctl);
+  return cudaGetLastError();
+}
+
+}  // namespace csim

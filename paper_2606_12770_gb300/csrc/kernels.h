@@ -165,6 +165,34 @@ cudaError_t warm_kernels();
 cudaError_t launch_norms(const void* state, int prec, int n, const uint64_t* d_pm,
                          const uint64_t* d_pv, int npat, int lowk, uint64_t lowv, double* d_partial,
                          double* d_out, cudaStream_t st);
+// Persistent batch execution of many fused programs (complex64): one step of
+// one program, cut into items of tile-counter ranges.
+struct BatchStep {
+  const SweepParams* sp;  // device copy of the step's parameters (source tables filled)
+  const void* in;
+  void* out;
+  uint32_t nitems;        // items the step was cut into
+  int32_t dep;            // step that must finish first (the program's previous step), or -1
+  uint32_t nfe, fmask, hstep;  // tile order for the kernel's stride (batch_order)
+};
+struct BatchItem {
+  uint32_t step;    // index into the step array
+  uint32_t c0, c1;  // tile counters [c0, c1), c0 a multiple of batch_stride()
+};
+struct BatchCtl {
+  uint32_t next;       // queue head, 0 at launch
+  uint32_t error;      // set when a dependency wait ran out
+  uint32_t drop_item;  // an item that does not signal (tests of the timeout); ~0u: none
+  uint32_t pad;
+};
+uint32_t batch_stride();
+void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t* fmask,
+                 uint32_t* hstep);
+int batch_grid();
+// One launch of co-resident CTAs over all items; done[] (one counter per step)
+// and ctl must be zeroed (drop_item set) before it.
+cudaError_t launch_batch(const BatchStep* d_steps, const BatchItem* d_items, uint32_t nitems,
+                         uint32_t* d_done, BatchCtl* d_ctl, cudaStream_t st);
 cudaError_t launch_compact(const void* state, int prec, double* d_out, uint64_t count,
                            int free_shift, int free_bits, uint64_t m_first, int m_shift,
                            cudaStream_t st);

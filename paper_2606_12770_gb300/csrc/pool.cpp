@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -184,6 +185,7 @@ struct Request {
   csim_status err = CSIM_OK;  // a request that failed on the host before its device work
   std::string err_msg;
   bool cancelled = false;     // discarded at retirement
+  bool batched = false;       // ran in a persistent launch (its slot's flag holds the error)
 };
 
 struct Slot {
@@ -197,6 +199,7 @@ struct Slot {
   double* h_out = nullptr;  // pinned: 2 doubles
   double* h_amps = nullptr;  // pinned: compacted block
   size_t h_amps_cap = 0;
+  uint32_t* h_flag = nullptr;  // pinned: the persistent launch's error word
   int64_t req = -1;
 };
 
@@ -347,6 +350,197 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, bool in_graph, co
   return e;
 }
 
+// Whether an admission pass can run as one persistent launch: complex64
+// requests whose programs are fused sweeps only.
+bool batch_eligible(csim_pool* P, const std::vector<std::pair<int64_t, int>>& started) {
+  for (auto& [id, k] : started) {
+    const Request& r = P->reqs[id];
+    if (r.prec != CSIM_C64 || r.c->L.n < 12) return false;
+    for (const csim::Step& st : r.c->prog.steps)
+      if (st.kind != 0 || r.c->prog.params[(size_t)st.param].nstage != 0) return false;
+  }
+  return true;
+}
+
+// The persistent path of an admission pass (see csim.h): uploads and plain
+// inits, the source-index tables, one launch over every request's sweeps
+// (items queued level by level), then norms, compactions and result copies,
+// all on the origin stream.
+cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int>>& started,
+                          const char** where) {
+  cudaStream_t st = P->origin;
+  char* base = static_cast<char*>(P->d_arena);
+  std::vector<csim::SweepParams> sps;
+  std::vector<csim::BatchStep> steps;
+  std::vector<std::vector<int>> prog_steps(started.size());  // global step indices per request
+  std::vector<int> final_cur(started.size(), 0);
+  const uint32_t stride = csim::batch_stride();
+  const uint32_t item_tiles = stride * 64;  // 1024 tiles (1 MiB of complex64) per item
+  uint32_t drop = ~0u;
+  cudaError_t e = cudaSuccess;
+  csim_pool::Wave w;
+  *where = "wave events";
+  e = cudaEventCreate(&w.start);
+  if (e == cudaSuccess) e = cudaEventCreate(&w.done);
+  if (e == cudaSuccess) e = cudaEventRecord(w.start, st);
+  for (size_t q = 0; q < started.size() && e == cudaSuccess; ++q) {
+    Request& r = P->reqs[started[q].first];
+    Slot& sl = P->slots[started[q].second];
+    csim_circuit* c = r.c;
+    void* buf[2] = {base + r.offs[0], r.offs[1] != ~0ull ? base + r.offs[1] : nullptr};
+    char* d_stage = base + r.offs[3];
+    const size_t nnz = r.idx.size();
+    const int npat = (int)c->pm.size();
+    char* hs = static_cast<char*>(sl.h_stage);
+    std::memcpy(hs, c->pm.data(), npat * 8);
+    std::memcpy(hs + npat * 8, c->pv.data(), npat * 8);
+    const size_t pat_bytes = 16 * (size_t)npat;
+    std::memcpy(hs + pat_bytes, r.idx.data(), nnz * 8);
+    std::memcpy(hs + pat_bytes + nnz * 8, r.val.data(), nnz * 8);
+    *where = "uploads";
+    e = cudaMemcpyAsync(sl.d_pat, hs, pat_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_stage, hs + pat_bytes, nnz * 16, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      *where = "init";
+      const uint64_t* d_idx = reinterpret_cast<const uint64_t*>(d_stage);
+      const double* d_val = reinterpret_cast<const double*>(d_stage + nnz * 8);
+      e = csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n, d_idx, d_val, (int64_t)nnz, st);
+    }
+    uint32_t* tabs[kMaxPoolTables] = {nullptr, nullptr};
+    for (int t = 0; t < r.ntab; ++t) tabs[t] = reinterpret_cast<uint32_t*>(base + r.offs[kTabBlock + t]);
+    if (e == cudaSuccess && r.ntab > 0) {
+      *where = "source-index tables";
+      e = csim::launch_src_tables(c->prog, tabs, st);
+    }
+    // the request's sweeps as batch steps, with the buffers each one reads
+    // and writes
+    const uint32_t ntiles = 1u << (c->L.n - 7);
+    int cur = 0, prev = -1;
+    for (size_t j = 0; j < c->prog.steps.size(); ++j) {
+      const csim::Step& stp = c->prog.steps[j];
+      csim::SweepParams a = c->prog.params[(size_t)stp.param];
+      if (r.ntab > 0 && (size_t)stp.param < c->prog.src_tab.size() &&
+          c->prog.src_tab[(size_t)stp.param] >= 0)
+        a.src = tabs[c->prog.src_tab[(size_t)stp.param]];
+      a.src_prefetch = 0;
+      a.zero_map = nullptr;
+      a.zero_mode = 0;
+      csim::BatchStep bs{};
+      bs.in = buf[cur];
+      const bool moves = stp.gather && !stp.inplace;
+      bs.out = moves ? buf[1 - cur] : buf[cur];
+      if (moves) cur = 1 - cur;
+      bs.nitems = (ntiles + item_tiles - 1) / item_tiles;
+      bs.dep = prev;
+      csim::batch_order(a, ntiles, &bs.nfe, &bs.fmask, &bs.hstep);
+      prev = (int)steps.size();
+      prog_steps[q].push_back(prev);
+      sps.push_back(a);
+      steps.push_back(bs);
+    }
+    final_cur[q] = cur;
+    const auto inj = P->inject.find(r.id);
+    if (inj != P->inject.end() && inj->second == CSIM_INJECT_BATCH_SIGNAL &&
+        prog_steps[q].size() > 2)
+      drop = (uint32_t)prog_steps[q][1];  // resolved to an item index below
+    r.batched = true;
+  }
+  // items level by level: step k of every request before step k + 1 of any
+  std::vector<csim::BatchItem> items;
+  size_t levels = 0;
+  for (const auto& v : prog_steps) levels = std::max(levels, v.size());
+  uint32_t drop_item = ~0u;
+  for (size_t lv = 0; lv < levels; ++lv)
+    for (size_t q = 0; q < prog_steps.size(); ++q) {
+      if (lv >= prog_steps[q].size()) continue;
+      const int gs = prog_steps[q][lv];
+      const Request& r = P->reqs[started[q].first];
+      const uint32_t ntiles = 1u << (r.c->L.n - 7);
+      for (uint32_t c0 = 0; c0 < ntiles; c0 += item_tiles) {
+        if ((uint32_t)gs == drop && drop_item == ~0u) drop_item = (uint32_t)items.size();
+        items.push_back(csim::BatchItem{(uint32_t)gs, c0, std::min(ntiles, c0 + item_tiles)});
+      }
+    }
+  // the tables in one stream-ordered allocation, freed after the launch
+  const size_t o_steps = 0;
+  const size_t o_sps = (o_steps + steps.size() * sizeof(csim::BatchStep) + 255) & ~(size_t)255;
+  const size_t o_items = (o_sps + sps.size() * sizeof(csim::SweepParams) + 255) & ~(size_t)255;
+  const size_t o_done = (o_items + items.size() * sizeof(csim::BatchItem) + 255) & ~(size_t)255;
+  const size_t o_ctl = (o_done + steps.size() * 4 + 255) & ~(size_t)255;
+  const size_t total = o_ctl + sizeof(csim::BatchCtl);
+  char* d = nullptr;
+  if (e == cudaSuccess) {
+    *where = "table allocation";
+    e = cudaMallocAsync(reinterpret_cast<void**>(&d), total, st);
+  }
+  if (e == cudaSuccess) {
+    for (size_t i = 0; i < steps.size(); ++i)
+      steps[i].sp = reinterpret_cast<const csim::SweepParams*>(d + o_sps) + i;
+    const csim::BatchCtl ctl{0u, 0u, drop_item, 0u};
+    *where = "table upload";
+    e = cudaMemcpyAsync(d + o_steps, steps.data(), steps.size() * sizeof(csim::BatchStep),
+                        cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d + o_sps, sps.data(), sps.size() * sizeof(csim::SweepParams),
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d + o_items, items.data(), items.size() * sizeof(csim::BatchItem),
+                          cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d + o_done, 0, steps.size() * 4, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d + o_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) {
+    *where = "persistent launch";
+    e = csim::launch_batch(reinterpret_cast<const csim::BatchStep*>(d + o_steps),
+                           reinterpret_cast<const csim::BatchItem*>(d + o_items),
+                           (uint32_t)items.size(), reinterpret_cast<uint32_t*>(d + o_done),
+                           reinterpret_cast<csim::BatchCtl*>(d + o_ctl), st);
+  }
+  // norms, compactions and result copies of every request
+  for (size_t q = 0; q < started.size() && e == cudaSuccess; ++q) {
+    Request& r = P->reqs[started[q].first];
+    Slot& sl = P->slots[started[q].second];
+    csim_circuit* c = r.c;
+    void* fin = base + r.offs[final_cur[q] == 0 ? 0 : 1];
+    double* d_compact = reinterpret_cast<double*>(base + r.offs[2]);
+    const int npat = (int)c->pm.size();
+    int lowk = 0;
+    uint64_t lowv = 0;
+    csim::mask_low_bits(c, &lowk, &lowv);
+    *where = "norms";
+    e = csim::launch_norms(fin, r.prec, c->L.n, sl.d_pat, sl.d_pat + npat, npat, lowk, lowv,
+                           sl.d_partial, sl.d_out, st);
+    const csim::CompactGeom g = csim::compact_geom(c);
+    if (e == cudaSuccess && g.count) {
+      *where = "compaction";
+      e = csim::launch_compact(fin, r.prec, d_compact, g.count, g.free_shift, g.free_bits,
+                               (uint64_t)c->L.Nt, g.m_shift, st);
+    }
+    if (e == cudaSuccess) {
+      *where = "result copy";
+      e = cudaMemcpyAsync(sl.h_out, sl.d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess && g.count)
+      e = cudaMemcpyAsync(sl.h_amps, d_compact, g.count * 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && d)
+      e = cudaMemcpyAsync(sl.h_flag, d + o_ctl + offsetof(csim::BatchCtl, error), 4,
+                          cudaMemcpyDeviceToHost, st);
+  }
+  if (d) {
+    const cudaError_t fe = cudaFreeAsync(d, st);
+    if (e == cudaSuccess) e = fe;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(w.done, st);
+  w.pending = (int)started.size();
+  const int wi = (int)P->waves.size();
+  P->waves.push_back(w);
+  for (auto& [id, k] : started) P->reqs[id].wave = wi;
+  if (e == cudaSuccess) P->stats.batch_launches++;
+  return e;
+}
+
 // A request that fails before any of its device work is enqueued: it leaves
 // the queue with its error, holds no memory, and is reported by the next
 // poll like a finished one; the pool keeps serving the others.
@@ -410,6 +604,16 @@ csim_status admit(csim_pool* P) {
   }
   if (started.empty()) return CSIM_OK;
   cudaError_t e = cudaSuccess;
+  if (P->o.persistent && batch_eligible(P, started)) {
+    const char* where = "";
+    e = enqueue_batch(P, started, &where);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return pfail(CSIM_ERR_CUDA, std::string("csim_pool: persistent pass, ") + where + ": " +
+                                      cudaGetErrorString(e));
+    }
+    return CSIM_OK;
+  }
   if (!P->o.use_graphs) {
     for (auto& [id, k] : started) {
       const char* step = "";
@@ -538,6 +742,12 @@ csim_status retire(csim_pool* P, int* n_retired) {
     }
     r.t_done = now_s();
     r.st = RState::Done;
+    if (r.batched && *s.h_flag != 0u) {  // a dependency wait of the launch ran out
+      r.err = CSIM_ERR_TIMEOUT;
+      r.err_msg = "csim_pool: the persistent launch's dependency wait ran out; results invalid";
+      P->stats.failed++;
+      *s.h_flag = 0u;
+    }
     release_all(&P->arena, r.offs, kAllocs);
     s.req = -1;
     P->stats.completed++;
@@ -581,6 +791,7 @@ void destroy_pool(csim_pool* P) {
     if (s.h_stage) cudaFreeHost(s.h_stage);
     if (s.h_out) cudaFreeHost(s.h_out);
     if (s.h_amps) cudaFreeHost(s.h_amps);
+    if (s.h_flag) cudaFreeHost(s.h_flag);
     if (s.st) cudaStreamDestroy(s.st);
   }
   if (P->epoch) cudaEventDestroy(P->epoch);
@@ -640,6 +851,8 @@ csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out) {
       e = cudaMalloc(&s.d_partial, 2 * csim::norm_partials_needed() * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s.d_out, 2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_out, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_flag, sizeof(uint32_t));
+    if (e == cudaSuccess) *s.h_flag = 0;
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->origin, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->upload, cudaStreamNonBlocking);
@@ -789,7 +1002,8 @@ csim_status csim_pool_cancel(csim_pool* P, int64_t id) {
 
 csim_status csim_pool_inject(csim_pool* P, int32_t what, int64_t id) {
   if (!P) return pfail(CSIM_ERR_ARG, "null argument");
-  if (what != CSIM_INJECT_NONE && what != CSIM_INJECT_PINNED && what != CSIM_INJECT_ARENA)
+  if (what != CSIM_INJECT_NONE && what != CSIM_INJECT_PINNED && what != CSIM_INJECT_ARENA &&
+      what != CSIM_INJECT_BATCH_SIGNAL)
     return pfail(CSIM_ERR_ARG, "unknown fault kind");
   if (what == CSIM_INJECT_NONE)
     P->inject.erase(id);

@@ -171,3 +171,61 @@ def test_pool_failures_and_cancellation_leave_the_rest_intact(graphs):
     pool.poll(wait_ms=100)
     assert pool.stats()["bytes_in_use"] == 0
     pool.close()
+
+
+MIX64 = [(cfg, d, G.CSIM_C64) for cfg, d, _ in MIX]
+
+
+def _instances64():
+    out = []
+    for k, (cfg, d, prec) in enumerate(MIX64):
+        f0, _ = I.lbm_instance(cfg[0], 10 + k, tau=cfg[1])
+        out.append((G.Circuit(*cfg, kappa_qsvt=10.0, d=d), f0, prec))
+    return out
+
+
+def test_persistent_pass_equals_alone():
+    """Persistent mode: every admission pass runs the sweeps of all its
+    requests in one launch of co-resident CTAs that take work items from a
+    device queue and wait (with a time limit) for each request's previous
+    sweep.  Each result equals the circuit run alone within complex64
+    rounding (the launch uses the general op interpreter, the run alone the
+    shaped kernels): 1e-5 relative on the block, 1e-6 on the norms."""
+    alone = _alone(_instances64())
+    inst = _instances64()
+    pool = G.Pool(n_streams=4, hbm_budget=160 << 20, max_qubits=30, persistent=True)
+    ids = [pool.submit(c, f0, prec) for c, f0, prec in inst]
+    assert len(_drain(pool, len(ids))) == len(ids)
+    st = pool.stats()
+    assert st["batch_launches"] >= 2 and st["completed"] == len(ids) and st["failed"] == 0
+    for rid, (amps0, p0, t0) in zip(ids, alone):
+        amps, p, t, _ = pool.result(rid)
+        err = float(np.linalg.norm(amps - amps0) / max(np.linalg.norm(amps0), 1e-300))
+        assert err < 1e-5, (rid, err)
+        assert abs(t - t0) < 1e-6 and abs(p - p0) <= 1e-5 * max(p0, 1e-30) + 1e-12
+    pool.close()
+
+
+def test_persistent_wait_times_out_and_pool_recovers():
+    """A work item that never signals (injected on the host: the first item of
+    one request's second sweep keeps its completion count back) makes the
+    items that depend on it wait out their 2 s limit; the launch stops, every
+    request of that pass reports CSIM_ERR_TIMEOUT, and the next pass runs
+    normally.  Nothing faults or hangs on the device."""
+    inst = _instances64()[:2]
+    pool = G.Pool(n_streams=2, max_qubits=30, persistent=True)
+    pool.inject(G._native.CSIM_INJECT_BATCH_SIGNAL, 1)
+    ids = [pool.submit(c, f0, prec) for c, f0, prec in inst]
+    assert sorted(_drain(pool, 2)) == ids
+    for rid in ids:
+        with pytest.raises(G.CsimError) as e:
+            pool.result(rid)
+        assert e.value.status == -6
+    assert pool.stats()["failed"] == 2
+    alone = _alone(_instances64()[:2])
+    ids2 = [pool.submit(c, f0, prec) for c, f0, prec in _instances64()[:2]]
+    assert sorted(_drain(pool, 2)) == ids2
+    for rid, (amps0, p0, t0) in zip(ids2, alone):
+        amps, p, t, _ = pool.result(rid)
+        assert float(np.linalg.norm(amps - amps0) / max(np.linalg.norm(amps0), 1e-300)) < 1e-5
+    pool.close()
