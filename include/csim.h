@@ -388,6 +388,7 @@ typedef struct {
                              and every request of a persistent pass whose wait ran out */
   int64_t cancelled;      /* csim_pool_cancel calls that took effect */
   int64_t batch_launches; /* admission passes run as one persistent launch */
+  int64_t batch_dropped_signals; /* persistent passes launched with an injected missing signal */
 } csim_pool_stats_t;
 
 csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out);

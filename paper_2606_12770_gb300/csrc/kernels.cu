@@ -1764,7 +1764,16 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)mv[u] << 2), v[u]);
-        apply_ops<R, U>(a, v, ci, lane, wd);
+        // the same op bodies as the sweep kernels (shaped where the step has
+        // one of their op lists), so a request's result does not depend on
+        // which path ran it
+        switch (bs.shape) {
+          case 1: apply_shaped<R, U, 1>(a, v, ci, lane, wd); break;
+          case 2: apply_shaped<R, U, 2>(a, v, ci, lane, wd); break;
+          case 3: apply_shaped<R, U, 3>(a, v, ci, lane, wd); break;
+          case 4: apply_shaped<R, U, 4>(a, v, ci, lane, wd); break;
+          default: apply_ops<R, U>(a, v, ci, lane, wd); break;
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u)
           store_chunk(out + ((size_t)(a.inplace ? mv[u] : ci[u]) << 2), v[u]);
@@ -1793,6 +1802,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
 }  // namespace
 
 uint32_t batch_stride() { return (kBatchThreads / 32) * kBatchU; }
+
+int batch_shape(const SweepParams& a) { return shapes_enabled() ? sweep_shape(a) : 0; }
 
 void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t* fmask,
                  uint32_t* hstep) {

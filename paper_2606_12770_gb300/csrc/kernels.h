@@ -174,6 +174,7 @@ struct BatchStep {
   uint32_t nitems;        // items the step was cut into
   int32_t dep;            // step that must finish first (the program's previous step), or -1
   uint32_t nfe, fmask, hstep;  // tile order for the kernel's stride (batch_order)
+  int32_t shape;          // op list of a shaped sweep kernel (batch_shape), 0 for any other
 };
 struct BatchItem {
   uint32_t step;    // index into the step array
@@ -186,6 +187,7 @@ struct BatchCtl {
   uint32_t pad;
 };
 uint32_t batch_stride();
+int batch_shape(const SweepParams& a);
 void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t* fmask,
                  uint32_t* hstep);
 int batch_grid();

@@ -434,6 +434,7 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
       bs.nitems = (ntiles + item_tiles - 1) / item_tiles;
       bs.dep = prev;
       csim::batch_order(a, ntiles, &bs.nfe, &bs.fmask, &bs.hstep);
+      bs.shape = csim::batch_shape(a);
       prev = (int)steps.size();
       prog_steps[q].push_back(prev);
       sps.push_back(a);
@@ -478,6 +479,7 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
     for (size_t i = 0; i < steps.size(); ++i)
       steps[i].sp = reinterpret_cast<const csim::SweepParams*>(d + o_sps) + i;
     const csim::BatchCtl ctl{0u, 0u, drop_item, 0u};
+    if (drop_item != ~0u) P->stats.batch_dropped_signals++;
     *where = "table upload";
     e = cudaMemcpyAsync(d + o_steps, steps.data(), steps.size() * sizeof(csim::BatchStep),
                         cudaMemcpyHostToDevice, st);
