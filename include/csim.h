@@ -373,8 +373,8 @@ typedef struct {
   uint64_t hbm_budget;  /* arena bytes; 0: 90% of the free device memory */
   int32_t use_graphs;   /* 1: one CUDA graph launch per admission pass */
   uint32_t min_block;   /* smallest arena block in bytes, a multiple of 256; 0: 1 MiB */
-  int32_t persistent;   /* 1: the sweeps of all requests admitted in one pass run in one
-                           persistent launch (complex64 passes; see below) */
+  int32_t persistent;   /* 1: the sweeps of the complex64 requests admitted in one pass
+                           run in one persistent launch (see below) */
 } csim_pool_opts;
 typedef struct {
   int64_t submitted, admitted, completed, rejected, queued, running;
@@ -393,7 +393,8 @@ typedef struct {
 
 csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out);
 /* Queue one run of circuit c (QSVT circuit on b from f0, as csim_init +
- * csim_run + csim_postselect) and try to admit.  f0 is copied.  *id receives
+ * csim_run + csim_postselect) and try to admit (in persistent mode, admission
+ * waits for the next csim_pool_poll).  f0 is copied.  *id receives
  * the request id.  Besides its state buffers, a request takes the source-index
  * tables of its sweeps from the arena (2^n bytes per distinct permutation
  * chain, one for a QSVT circuit; built on the request's stream before its
@@ -439,16 +440,21 @@ csim_status csim_pool_cancel(csim_pool* p, int64_t id);
  * time limit and the whole pass reports CSIM_ERR_TIMEOUT.  Nothing is faulted
  * on the device.
  *
- * Persistent mode (csim_pool_opts.persistent): an admission pass of complex64
- * requests runs as the requests' uploads and inits, one launch of a
- * persistent kernel over the sweeps of all of them, then their norms and
- * compactions, all on one stream (one CUDA graph with use_graphs is not
- * combined with it).  The kernel's co-resident CTAs take work items (a tile
- * range of one sweep of one request) from a queue in device memory, level by
- * level, and wait, with a 2 s limit per wait, for the previous sweep of the
- * same request.  Passes with complex128 requests, and programs with steps
- * other than sweeps, take the stream path.  The results agree with the run
- * alone within rounding (the kernel uses the general op interpreter). */
+ * Persistent mode (csim_pool_opts.persistent): submissions only queue, and
+ * the next csim_pool_poll admits them, so a burst of submissions forms
+ * admission passes of at most half of n_streams requests each (the next pass
+ * is admitted while one runs).  A pass's complex64 requests whose programs are fused
+ * sweeps (at least 12 qubits, no staged high qubits) run as their uploads and
+ * inits, one launch of a persistent kernel over the sweeps of all of them,
+ * then their norms and compactions, all on the stream of the pass's first
+ * slot; its other requests run on their own streams as in stream mode
+ * (use_graphs is not combined with it).  The kernel's CTAs take work items (a
+ * range of 1024 tile counters of one sweep of one request) from a queue in
+ * device memory, level by level with the largest requests first, and wait,
+ * with a 2 s limit per wait, for the previous sweep of the same request;
+ * consecutive passes use different streams and may overlap.  The kernel runs
+ * the sweep kernels' op bodies, so results agree with the run alone within
+ * rounding. */
 enum { CSIM_INJECT_NONE = 0, CSIM_INJECT_PINNED = 1, CSIM_INJECT_ARENA = 2,
        CSIM_INJECT_BATCH_SIGNAL = 3 };
 csim_status csim_pool_inject(csim_pool* p, int32_t what, int64_t id);

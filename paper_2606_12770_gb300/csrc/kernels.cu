@@ -1675,14 +1675,16 @@ constexpr uint64_t kBatchWaitNs = 2000000000ull;  // a dependency wait gives up 
 // the next item (a range of tile counters of one step) from a queue in
 // global memory; an item waits, with a time limit, until every item of the
 // step it depends on (the same program's previous step) has signalled; then
-// its warps apply the step to their tiles with the general op interpreter
+// its warps apply the step to their tiles (the sweep kernels' op bodies)
 // and the CTA signals.  Items are queued level by level (step k of every
-// program before step k + 1 of any), so a waiting CTA only waits on items
-// that CTAs already hold: the grid is co-resident, nothing waits for work
-// that cannot start.  When a wait runs out the kernel records the error and
-// every CTA stops at its next wait.
-template <typename R>
-__global__ void __launch_bounds__(kBatchThreads, 2)
+// program before step k + 1 of any), and an item only waits on items earlier
+// in the queue, which running CTAs have already taken: the earliest
+// unfinished item never waits, so the launch progresses whether or not all
+// its CTAs are resident at once (another launch may share the SMs).  When a
+// wait runs out the kernel records the error and every CTA stops at its next
+// wait.
+template <typename R, int MINB>
+__global__ void __launch_bounds__(kBatchThreads, MINB)
     batch_kernel(const BatchStep* __restrict__ steps, const BatchItem* __restrict__ items,
                  uint32_t nitems, uint32_t* done, BatchCtl* ctl) {
   using T = typename V2<R>::T;
@@ -1826,25 +1828,45 @@ void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t*
   *hstep = hs;
 }
 
+// CTAs per SM of the persistent kernel: 2 (no spills) by default; 3 trades
+// spills of the op interpreter's registers for more loads in flight
+// (CSIM_BATCH_MINB=3).
+int batch_minb() {
+  static const int v = [] {
+    const char* e = std::getenv("CSIM_BATCH_MINB");
+    return e && std::strcmp(e, "3") == 0 ? 3 : 2;
+  }();
+  return v;
+}
+
 int batch_grid() {
-  static int resident = 0;
-  if (!resident) {
+  static int resident[4] = {0, 0, 0, 0};
+  const int m = batch_minb();
+  if (!resident[m]) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<float>, kBatchThreads, 0);
-    resident = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    if (m == 3)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<float, 3>, kBatchThreads, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<float, 2>, kBatchThreads, 0);
+    resident[m] = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
-  return resident;
+  return resident[m];
 }
 
 cudaError_t launch_batch(const BatchStep* d_steps, const BatchItem* d_items, uint32_t nitems,
                          uint32_t* d_done, BatchCtl* d_ctl, cudaStream_t st) {
   if (nitems == 0) return cudaSuccess;
-  // co-resident CTAs only: a waiting CTA must never hold up the CTA whose
-  // item it waits for
-  batch_kernel<float><<<batch_grid(), kBatchThreads, 0, st>>>(d_steps, d_items, nitems, d_done,
-                                                              d_ctl);
+  // the grid is the resident CTA count: more CTAs would only queue behind
+  // the persistent ones.  (Progress does not depend on it: an item waits only
+  // for items earlier in the queue, which running CTAs hold.)
+  if (batch_minb() == 3)
+    batch_kernel<float, 3><<<batch_grid(), kBatchThreads, 0, st>>>(d_steps, d_items, nitems,
+                                                                   d_done, d_ctl);
+  else
+    batch_kernel<float, 2><<<batch_grid(), kBatchThreads, 0, st>>>(d_steps, d_items, nitems,
+                                                                   d_done, d_ctl);
   return cudaGetLastError();
 }
 

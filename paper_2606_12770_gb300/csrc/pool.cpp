@@ -350,25 +350,24 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, bool in_graph, co
   return e;
 }
 
-// Whether an admission pass can run as one persistent launch: complex64
-// requests whose programs are fused sweeps only.
-bool batch_eligible(csim_pool* P, const std::vector<std::pair<int64_t, int>>& started) {
-  for (auto& [id, k] : started) {
-    const Request& r = P->reqs[id];
-    if (r.prec != CSIM_C64 || r.c->L.n < 12) return false;
-    for (const csim::Step& st : r.c->prog.steps)
-      if (st.kind != 0 || r.c->prog.params[(size_t)st.param].nstage != 0) return false;
-  }
+// Whether a request can run in a persistent launch: complex64, at least 12
+// qubits, and a program of fused sweeps only (no staged high qubits).
+bool batch_eligible(const Request& r) {
+  if (r.prec != CSIM_C64 || r.c->L.n < 12) return false;
+  for (const csim::Step& st : r.c->prog.steps)
+    if (st.kind != 0 || r.c->prog.params[(size_t)st.param].nstage != 0) return false;
   return true;
 }
 
 // The persistent path of an admission pass (see csim.h): uploads and plain
 // inits, the source-index tables, one launch over every request's sweeps
 // (items queued level by level), then norms, compactions and result copies,
-// all on the origin stream.
+// all on the stream of the pass's first slot.  The slots of a pass are free
+// when it is admitted, so consecutive passes run on different streams and
+// the next one fills the GPU while the last levels of the previous one drain.
 cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int>>& started,
                           const char** where) {
-  cudaStream_t st = P->origin;
+  cudaStream_t st = P->slots[started.front().second].st;
   char* base = static_cast<char*>(P->d_arena);
   std::vector<csim::SweepParams> sps;
   std::vector<csim::BatchStep> steps;
@@ -447,13 +446,21 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
       drop = (uint32_t)prog_steps[q][1];  // resolved to an item index below
     r.batched = true;
   }
-  // items level by level: step k of every request before step k + 1 of any
+  // items level by level: step k of every request before step k + 1 of any,
+  // the largest requests first within a level, so that the other requests'
+  // items of the level separate the tail of a large request's step from its
+  // next step
   std::vector<csim::BatchItem> items;
   size_t levels = 0;
   for (const auto& v : prog_steps) levels = std::max(levels, v.size());
+  std::vector<size_t> order(prog_steps.size());
+  for (size_t q = 0; q < order.size(); ++q) order[q] = q;
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+    return P->reqs[started[x].first].c->L.n > P->reqs[started[y].first].c->L.n;
+  });
   uint32_t drop_item = ~0u;
   for (size_t lv = 0; lv < levels; ++lv)
-    for (size_t q = 0; q < prog_steps.size(); ++q) {
+    for (size_t q : order) {
       if (lv >= prog_steps[q].size()) continue;
       const int gs = prog_steps[q][lv];
       const Request& r = P->reqs[started[q].first];
@@ -557,10 +564,13 @@ void fail_request(csim_pool* P, Request& r, csim_status err, const std::string& 
   if (!r.cancelled) P->done_unreported.push_back(r.id);
 }
 
-// Admit queued requests (FIFO) into free slots while their blocks fit.
-csim_status admit(csim_pool* P) {
+// Admit queued requests (FIFO) into free slots while their blocks fit, at
+// most `cap` of them, as one admission pass; *n_started receives how many
+// were admitted.
+csim_status admit_pass(csim_pool* P, size_t cap, size_t* n_started) {
   std::vector<std::pair<int64_t, int>> started;
-  while (!P->queue.empty()) {
+  *n_started = 0;
+  while (!P->queue.empty() && started.size() < cap) {
     int free_slot = -1;
     for (int k = 0; k < (int)P->slots.size(); ++k)
       if (P->slots[k].req < 0) {
@@ -604,19 +614,27 @@ csim_status admit(csim_pool* P) {
     P->stats.peak_bytes = std::max(P->stats.peak_bytes, P->arena.in_use());
     started.emplace_back(r.id, free_slot);
   }
+  *n_started = started.size();
   if (started.empty()) return CSIM_OK;
   cudaError_t e = cudaSuccess;
-  if (P->o.persistent && batch_eligible(P, started)) {
-    const char* where = "";
-    e = enqueue_batch(P, started, &where);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return pfail(CSIM_ERR_CUDA, std::string("csim_pool: persistent pass, ") + where + ": " +
-                                      cudaGetErrorString(e));
+  if (P->o.persistent) {
+    // the eligible requests of the pass in one persistent launch, the others
+    // on their own streams
+    std::vector<std::pair<int64_t, int>> batch, rest;
+    for (auto& pr : started) (batch_eligible(P->reqs[pr.first]) ? batch : rest).push_back(pr);
+    if (!batch.empty()) {
+      const char* where = "";
+      e = enqueue_batch(P, batch, &where);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return pfail(CSIM_ERR_CUDA, std::string("csim_pool: persistent pass, ") + where + ": " +
+                                        cudaGetErrorString(e));
+      }
     }
-    return CSIM_OK;
+    started.swap(rest);
+    if (started.empty()) return CSIM_OK;
   }
-  if (!P->o.use_graphs) {
+  if (!P->o.use_graphs || P->o.persistent) {
     for (auto& [id, k] : started) {
       const char* step = "";
       e = enqueue_request(P, P->reqs[id], P->slots[k], false, &step);
@@ -709,6 +727,22 @@ csim_status admit(csim_pool* P) {
   }
   P->stats.graph_launches++;
   return CSIM_OK;
+}
+
+// Admission.  In persistent mode a pass takes at most half of the slots, so
+// that the next pass is admitted while it runs and fills the GPU as its last
+// levels drain; passes are formed until nothing more fits.
+csim_status admit(csim_pool* P) {
+  if (!P->o.persistent) {
+    size_t n = 0;
+    return admit_pass(P, P->slots.size(), &n);
+  }
+  const size_t cap = std::max<size_t>(1, P->slots.size() / 2);
+  for (;;) {
+    size_t n = 0;
+    const csim_status s = admit_pass(P, cap, &n);
+    if (s != CSIM_OK || n == 0) return s;
+  }
 }
 
 // Retire every running request whose completion event has fired.
@@ -917,7 +951,9 @@ csim_status csim_pool_submit(csim_pool* P, csim_circuit* c, const double* f0, cs
   P->reqs.emplace(r.id, std::move(r));
   int n = 0;
   csim_status s = retire(P, &n);
-  if (s == CSIM_OK) s = admit(P);
+  // persistent mode admits at the next poll, so that a burst of submissions
+  // forms one pass
+  if (s == CSIM_OK && !P->o.persistent) s = admit(P);
   P->stats.queued = (int64_t)P->queue.size();
   return s;
 }

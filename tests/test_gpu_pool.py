@@ -186,11 +186,11 @@ def _instances64():
 
 def test_persistent_pass_equals_alone():
     """Persistent mode: every admission pass runs the sweeps of all its
-    requests in one launch of co-resident CTAs that take work items from a
-    device queue and wait (with a time limit) for each request's previous
-    sweep.  Each result equals the circuit run alone within complex64
-    rounding (the launch uses the general op interpreter, the run alone the
-    shaped kernels): 1e-5 relative on the block, 1e-6 on the norms."""
+    requests in one launch whose CTAs take work items from a device queue and
+    wait (with a time limit) for each request's previous sweep.  Each result
+    equals the circuit run alone within complex64 rounding (the launch runs
+    the sweep kernels' op bodies, with another number of tiles per warp):
+    1e-5 relative on the block, 1e-6 on the norms."""
     alone = _alone(_instances64())
     inst = _instances64()
     pool = G.Pool(n_streams=4, hbm_budget=160 << 20, max_qubits=30, persistent=True)
@@ -236,4 +236,28 @@ def test_persistent_wait_times_out_and_pool_recovers():
     for rid, (amps0, p0, t0) in zip(ids2, alone):
         amps, p, t, _ = pool.result(rid)
         assert float(np.linalg.norm(amps - amps0) / max(np.linalg.norm(amps0), 1e-300)) < 1e-5
+    pool.close()
+
+
+def test_persistent_mixed_precisions():
+    """A persistent pool given complex64 and complex128 requests together:
+    the complex64 ones of a pass share one persistent launch, the complex128
+    ones run on their own streams in the same pass; every result equals the
+    circuit run alone (bit for bit in complex128, within complex64 rounding
+    otherwise)."""
+    inst = [(c, f0, G.CSIM_C128 if k % 2 else prec) for k, (c, f0, prec) in enumerate(_instances64())]
+    alone = _alone(inst)
+    inst = [(c, f0, G.CSIM_C128 if k % 2 else prec) for k, (c, f0, prec) in enumerate(_instances64())]
+    pool = G.Pool(n_streams=8, max_qubits=30, persistent=True)
+    ids = [pool.submit(c, f0, prec) for c, f0, prec in inst]
+    assert sorted(_drain(pool, len(ids))) == ids
+    st = pool.stats()
+    assert st["batch_launches"] >= 1 and st["failed"] == 0
+    for rid, (amps0, p0, t0), (_, _, prec) in zip(ids, alone, inst):
+        amps, p, t, _ = pool.result(rid)
+        if prec == G.CSIM_C128:
+            assert np.array_equal(amps, amps0) and p == p0 and t == t0
+        else:
+            err = float(np.linalg.norm(amps - amps0) / max(np.linalg.norm(amps0), 1e-300))
+            assert err < 1e-5, (rid, err)
     pool.close()
