@@ -1668,7 +1668,6 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 constexpr int kBatchThreads = 256;
-constexpr int kBatchU = 2;
 constexpr uint64_t kBatchWaitNs = 2000000000ull;  // a dependency wait gives up after 2 s
 
 // One persistent launch over the sweeps of many programs.  Every CTA takes
@@ -1683,14 +1682,16 @@ constexpr uint64_t kBatchWaitNs = 2000000000ull;  // a dependency wait gives up 
 // its CTAs are resident at once (another launch may share the SMs).  When a
 // wait runs out the kernel records the error and every CTA stops at its next
 // wait.
-template <typename R, int MINB>
+template <typename R, int U, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
     batch_kernel(const BatchStep* __restrict__ steps, const BatchItem* __restrict__ items,
                  uint32_t nitems, uint32_t* done, BatchCtl* ctl) {
   using T = typename V2<R>::T;
-  constexpr int U = kBatchU;
   __shared__ uint32_t s_item;
   __shared__ int s_ok;
+  // the item's sweep parameters, copied once per item: the op bodies read
+  // them from shared memory instead of holding global loads in registers
+  __shared__ __align__(16) SweepParams s_a;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(&ctl->next, 1u);
@@ -1722,7 +1723,13 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
     }
     __syncthreads();
     if (!s_ok) break;
-    const SweepParams& a = *bs.sp;
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(bs.sp);
+      uint4* dst = reinterpret_cast<uint4*>(&s_a);
+      for (uint32_t i = threadIdx.x; i < sizeof(SweepParams) / 16; i += kBatchThreads) dst[i] = src[i];
+    }
+    __syncthreads();
+    const SweepParams& a = s_a;
     const T* in = static_cast<const T*>(bs.in);
     T* out = static_cast<T*>(bs.out);
     const int nfe = (int)bs.nfe;
@@ -1749,18 +1756,31 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
       H = cw;
     }
     const uint32_t stride = (kBatchThreads / 32) * U;
+    // source indices of the warp's next tiles, loaded one iteration ahead
+    const bool pre = a.src != nullptr && !a.scatter;
+    uint32_t nxt[U];
+    if (pre && cw < it.c1) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        nxt[u] = __ldcs(a.src + (((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane));
+    }
     for (uint32_t c = cw; c < it.c1; c += stride) {
       uint32_t ci[U], mv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) mv[u] = ci[u] = ((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane;
       H = nfe > 0 ? (((H | fmask) + bs.hstep) & ~fmask) : (H + stride);
       uint32_t wd[kPrefetchMux][U];
-      prefetch_mux<U>(a, ci, wd);
+      if (bs.shape != 1) prefetch_mux<U>(a, ci, wd);
       T v[U][4];
       if (!a.scatter) {
-        if (a.src) {
+        if (pre) {
 #pragma unroll
-          for (int u = 0; u < U; ++u) mv[u] = __ldcs(a.src + ci[u]);
+          for (int u = 0; u < U; ++u) mv[u] = nxt[u];
+          if (c + stride < it.c1) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              nxt[u] = __ldcs(a.src + (((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane));
+          }
         } else {
           permute<U>(a, mv);
         }
@@ -1803,7 +1823,29 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
 
 }  // namespace
 
-uint32_t batch_stride() { return (kBatchThreads / 32) * kBatchU; }
+// Tiles per warp iteration and CTAs per SM of the persistent kernel
+// (CSIM_BATCH_CFG="U,MINB": 2,2 without spills; 2,3 and 2,4 spill some of
+// the op bodies' registers for more loads in flight; 4,2 holds four tiles a
+// warp at 128 registers).
+struct BatchCfg {
+  int u, minb;
+};
+
+BatchCfg batch_cfg() {
+  static const BatchCfg c = [] {
+    BatchCfg v{2, 3};
+    if (const char* e = std::getenv("CSIM_BATCH_CFG")) {
+      int u = 0, m = 0;
+      if (std::sscanf(e, "%d,%d", &u, &m) == 2 &&
+          ((u == 2 && (m == 2 || m == 3 || m == 4)) || (u == 4 && m == 2)))
+        v = BatchCfg{u, m};
+    }
+    return v;
+  }();
+  return c;
+}
+
+uint32_t batch_stride() { return (kBatchThreads / 32) * (uint32_t)batch_cfg().u; }
 
 int batch_shape(const SweepParams& a) { return shapes_enabled() ? sweep_shape(a) : 0; }
 
@@ -1813,7 +1855,7 @@ void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t*
   const uint32_t stride = batch_stride();
   int f = a.nstage > 0 ? 0 : a.nfast;
   while (f > 0 && (stride & ((1u << f) - 1u)) != 0u) --f;
-  if (f > 0 && (1u << f) < (uint32_t)kBatchU) f = 0;
+  if (f > 0 && (1u << f) < (uint32_t)batch_cfg().u) f = 0;
   uint32_t fm = 0, hs = 0;
   for (int j = 0; j < f; ++j) fm |= 1u << a.fast[j];
   uint32_t hv = stride >> f;
@@ -1828,45 +1870,55 @@ void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t*
   *hstep = hs;
 }
 
-// CTAs per SM of the persistent kernel: 2 (no spills) by default; 3 trades
-// spills of the op interpreter's registers for more loads in flight
-// (CSIM_BATCH_MINB=3).
-int batch_minb() {
-  static const int v = [] {
-    const char* e = std::getenv("CSIM_BATCH_MINB");
-    return e && std::strcmp(e, "3") == 0 ? 3 : 2;
-  }();
-  return v;
-}
+namespace {
 
-int batch_grid() {
-  static int resident[4] = {0, 0, 0, 0};
-  const int m = batch_minb();
-  if (!resident[m]) {
+template <int U, int MINB>
+int batch_resident() {
+  static int resident = 0;
+  if (!resident) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (m == 3)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<float, 3>, kBatchThreads, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<float, 2>, kBatchThreads, 0);
-    resident[m] = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<float, U, MINB>,
+                                                  kBatchThreads, 0);
+    resident = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
-  return resident[m];
+  return resident;
+}
+
+template <int U, int MINB>
+void launch_batch_t(const BatchStep* d_steps, const BatchItem* d_items, uint32_t nitems,
+                    uint32_t* d_done, BatchCtl* d_ctl, cudaStream_t st) {
+  // the grid is the resident CTA count: more CTAs would only queue behind
+  // the persistent ones.  (Progress does not depend on it: an item waits only
+  // for items earlier in the queue, which running CTAs hold.)
+  batch_kernel<float, U, MINB><<<batch_resident<U, MINB>(), kBatchThreads, 0, st>>>(
+      d_steps, d_items, nitems, d_done, d_ctl);
+}
+
+}  // namespace
+
+cudaError_t warm_batch() {
+  const BatchCfg c = batch_cfg();
+  if (c.u == 4) batch_resident<4, 2>();
+  if (c.u == 2 && c.minb == 2) batch_resident<2, 2>();
+  if (c.u == 2 && c.minb == 3) batch_resident<2, 3>();
+  if (c.u == 2 && c.minb == 4) batch_resident<2, 4>();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const BatchStep* d_steps, const BatchItem* d_items, uint32_t nitems,
                          uint32_t* d_done, BatchCtl* d_ctl, cudaStream_t st) {
   if (nitems == 0) return cudaSuccess;
-  // the grid is the resident CTA count: more CTAs would only queue behind
-  // the persistent ones.  (Progress does not depend on it: an item waits only
-  // for items earlier in the queue, which running CTAs hold.)
-  if (batch_minb() == 3)
-    batch_kernel<float, 3><<<batch_grid(), kBatchThreads, 0, st>>>(d_steps, d_items, nitems,
-                                                                   d_done, d_ctl);
+  const BatchCfg c = batch_cfg();
+  if (c.u == 4)
+    launch_batch_t<4, 2>(d_steps, d_items, nitems, d_done, d_ctl, st);
+  else if (c.minb == 2)
+    launch_batch_t<2, 2>(d_steps, d_items, nitems, d_done, d_ctl, st);
+  else if (c.minb == 4)
+    launch_batch_t<2, 4>(d_steps, d_items, nitems, d_done, d_ctl, st);
   else
-    batch_kernel<float, 2><<<batch_grid(), kBatchThreads, 0, st>>>(d_steps, d_items, nitems,
-                                                                   d_done, d_ctl);
+    launch_batch_t<2, 3>(d_steps, d_items, nitems, d_done, d_ctl, st);
   return cudaGetLastError();
 }
 

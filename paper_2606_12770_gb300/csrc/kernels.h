@@ -190,7 +190,8 @@ uint32_t batch_stride();
 int batch_shape(const SweepParams& a);
 void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t* fmask,
                  uint32_t* hstep);
-int batch_grid();
+// Kernel load and occupancy cache of the persistent kernel (before capture).
+cudaError_t warm_batch();
 // One launch of co-resident CTAs over all items; done[] (one counter per step)
 // and ctl must be zeroed (drop_item set) before it.
 cudaError_t launch_batch(const BatchStep* d_steps, const BatchItem* d_items, uint32_t nitems,

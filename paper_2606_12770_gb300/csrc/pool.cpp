@@ -901,6 +901,7 @@ csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out) {
   // load every kernel and fill the launch-configuration caches now: a lazy
   // module load must not happen inside a graph capture
   if (e == cudaSuccess) e = csim::warm_kernels();
+  if (e == cudaSuccess && P->o.persistent) e = csim::warm_batch();
   if (e != cudaSuccess) {
     cudaGetLastError();
     destroy_pool(P);

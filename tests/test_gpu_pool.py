@@ -198,11 +198,15 @@ def test_persistent_pass_equals_alone():
     assert len(_drain(pool, len(ids))) == len(ids)
     st = pool.stats()
     assert st["batch_launches"] >= 2 and st["completed"] == len(ids) and st["failed"] == 0
+    errs = []
     for rid, (amps0, p0, t0) in zip(ids, alone):
         amps, p, t, _ = pool.result(rid)
         err = float(np.linalg.norm(amps - amps0) / max(np.linalg.norm(amps0), 1e-300))
+        errs.append(err)
         assert err < 1e-5, (rid, err)
         assert abs(t - t0) < 1e-6 and abs(p - p0) <= 1e-5 * max(p0, 1e-30) + 1e-12
+    print(f"persistent pass vs alone: max rel L2 {max(errs):.3e}, "
+          f"{sum(e == 0.0 for e in errs)} of {len(errs)} bit-identical")
     pool.close()
 
 
