@@ -819,7 +819,8 @@ def main():
     ap.add_argument("--exec", default="fused", choices=["fused", "gate"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="gate streams: keep the default fusion width instead of timing trials")
+                    help="keep the default fusion width (gate streams) and sweep launch shape "
+                         "(circuits) instead of timing trials")
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     args = ap.parse_args()
 
@@ -856,6 +857,17 @@ def main():
     info = circ.info()
     n = info["n_qubits"]
     esz = 8 if prec == "c64" else 16
+
+    # launch shape of this (precision, size) class from short timed trials on a
+    # scratch state, before the warm-up (the circuit's own state is untouched)
+    tune = None
+    if args.exec == "fused" and not args.no_autotune:
+        t = circ.tune_launch(precision, max_steps=16, reps=2)
+        tune = {k: t[k] for k in ("u", "minb", "waves", "ms", "ms_default", "steps")}
+        tune["n_trials"] = len(t["trials"])
+        tune["what"] = ("sweep launch shape per (precision, qubits): tiles per warp iteration u, "
+                        "blocks per SM minb, grid in resident waves; ms = the first `steps` "
+                        "program steps")
 
     def step(want_amps=False, out=None):
         circ.init(f0, precision, stream)
@@ -948,7 +960,8 @@ def main():
                           f"ping-pong buffers {2 * ((1 << n) * esz) / 1e6:.0f} MB; L2 129 MB)"
                           if ((1 << n) * esz) > L2_BYTES
                           else "state resident in L2 (smaller than 129 MB); no flush"),
-                   "parallelism": f"replicas x{world}", "host_cores": os.cpu_count()},
+                   "parallelism": f"replicas x{world}", "host_cores": os.cpu_count(),
+                   "autotune": tune},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "kernel": "sweep_kernel", "peak_kind": f"{peak_kind} (STREAM-style copy)",

@@ -184,6 +184,38 @@ csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec,
 
 csim_status csim_set_exec(csim_circuit* c, csim_exec mode);
 
+/* Launch-shape autotuner of the fused sweeps, per (precision, qubit count)
+ * class.  Times the circuit's first max_steps program steps on a scratch
+ * state of its size (two buffers when the program moves data; filled with
+ * finite values; CSIM_ERR_OOM when they cannot be allocated) for each
+ * candidate launch shape: the default kernel variant (tiles per warp
+ * iteration u, minimum resident blocks per SM minb) at grids of 1, 2, 4 and
+ * 8 resident waves, and every other variant at the default grid.  Each
+ * candidate runs once untimed, then `reps` times between CUDA events.  The
+ * fastest becomes the process-wide shape of the class: every later sweep of a
+ * fused program on a state of this precision and size uses it, except the
+ * sweeps that complete a sparse csim_init (their zero handling exists in the
+ * default variant only).  The circuit's own state is not touched.  Results do
+ * not depend on the shape beyond rounding: variants other than the default
+ * run the general op interpreter instead of the shaped op lists.  Needs the
+ * fused exec mode. */
+typedef struct {
+  int32_t u, minb, waves;  /* chosen shape */
+  double ms;               /* time of the steps with it */
+  double ms_default;       /* time of the steps with the default shape */
+  int32_t steps;           /* program steps timed */
+  int32_t n_trials;
+  int32_t trial_u[32], trial_minb[32], trial_waves[32];
+  double trial_ms[32];
+} csim_launch_tune_t;
+csim_status csim_tune_launch(csim_circuit* c, csim_precision prec, int32_t max_steps,
+                             int32_t reps, csim_launch_tune_t* out);
+/* Set the launch shape of a class directly (u = 0 clears it; the default
+ * shape is then used).  u in {1, 2, 4}, minb in {1, 2, 4} (not 4 with 4),
+ * waves in 1..64; CSIM_ERR_ARG otherwise. */
+csim_status csim_set_launch_shape(csim_precision prec, int32_t n_qubits, int32_t u, int32_t minb,
+                                  int32_t waves);
+
 /* Compile the circuit's program for the current exec mode on the host (the
  * fusing that the first csim_run or pool submission would otherwise do); no
  * GPU work.  Calls on different handles may run in parallel threads. */

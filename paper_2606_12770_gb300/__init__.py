@@ -7,8 +7,9 @@ binding.  Importing this package does not load the library; the first call
 that needs it does, and raises if it cannot.
 """
 from ._native import (CSIM_C64, CSIM_C128, CSIM_EXEC_FUSED, CSIM_EXEC_GATE, Circuit,  # noqa: F401
-                      CsimError, Pool, StateVector, gates_to_records, load, pool_plan)
+                      CsimError, Pool, StateVector, gates_to_records, load, pool_plan,
+                      set_launch_shape)
 
 __all__ = ["Circuit", "StateVector", "Pool", "pool_plan", "CsimError", "load", "gates_to_records",
-           "CSIM_C64",
+           "set_launch_shape", "CSIM_C64",
            "CSIM_C128", "CSIM_EXEC_FUSED", "CSIM_EXEC_GATE"]

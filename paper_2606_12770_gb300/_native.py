@@ -34,7 +34,7 @@ EXPORTED = [
     "csim_pool_submit", "csim_pool_poll", "csim_pool_result", "csim_pool_stats", "csim_pool_free",
     "csim_pool_plan", "csim_compile", "csim_run_steps", "csim_checkpoint", "csim_restore",
     "csim_final_distribution", "csim_pool_cancel", "csim_pool_inject", "csim_sv_apply_dense",
-    "csim_sv_autotune", "csim_sv_compile_opts",
+    "csim_sv_autotune", "csim_sv_compile_opts", "csim_tune_launch", "csim_set_launch_shape",
 ]
 
 
@@ -129,6 +129,8 @@ def load():
         "csim_sv_apply_dense": ([VP, P(C.c_int32), DP, C.c_int32], C.c_int),
         "csim_sv_autotune": ([VP, VP, SZ, C.c_int32, VP], C.c_int),
         "csim_sv_compile_opts": ([VP, VP, SZ, C.c_int, C.c_int32, C.c_int32], C.c_int),
+        "csim_tune_launch": ([VP, C.c_int, C.c_int32, C.c_int32, VP], C.c_int),
+        "csim_set_launch_shape": ([C.c_int, C.c_int32, C.c_int32, C.c_int32, C.c_int32], C.c_int),
         "csim_pool_inject": ([VP, C.c_int32, C.c_int64], C.c_int),
         "csim_pool_plan": ([C.c_uint64, C.c_uint64, C.c_int32, SZ, P(C.c_uint64), DP, DP, DP, DP,
                             P(C.c_uint64)], C.c_int),
@@ -236,6 +238,18 @@ class Circuit:
     def set_exec(self, mode):
         _check(_lib.csim_set_exec(self._h, int(mode)))
 
+    def tune_launch(self, precision, max_steps=32, reps=2):
+        """csim_tune_launch: time the first max_steps program steps on a scratch
+        state under each candidate launch shape and keep the fastest for this
+        (precision, qubit count) class; returns the choice and the trials."""
+        r = LaunchTuneResult()
+        _check(_lib.csim_tune_launch(self._h, int(precision), int(max_steps), int(reps),
+                                     C.cast(C.byref(r), C.c_void_p)))
+        trials = [{"u": r.trial_u[i], "minb": r.trial_minb[i], "waves": r.trial_waves[i],
+                   "ms": r.trial_ms[i]} for i in range(r.n_trials)]
+        return {"u": r.u, "minb": r.minb, "waves": r.waves, "ms": r.ms,
+                "ms_default": r.ms_default, "steps": r.steps, "trials": trials}
+
     def run(self):
         _check(_lib.csim_run(self._h))
 
@@ -319,6 +333,18 @@ class SvStats(C.Structure):
     _fields_ = [("passes", C.c_int64), ("sweeps", C.c_int64), ("single", C.c_int64),
                 ("amp_updates", C.c_double), ("pass_amps", C.c_double), ("state_bytes", C.c_uint64),
                 ("dense_blocks", C.c_int64), ("staged_sweeps", C.c_int64)]
+
+
+class LaunchTuneResult(C.Structure):
+    _fields_ = [("u", C.c_int32), ("minb", C.c_int32), ("waves", C.c_int32), ("ms", C.c_double),
+                ("ms_default", C.c_double), ("steps", C.c_int32), ("n_trials", C.c_int32),
+                ("trial_u", C.c_int32 * 32), ("trial_minb", C.c_int32 * 32),
+                ("trial_waves", C.c_int32 * 32), ("trial_ms", C.c_double * 32)]
+
+
+def set_launch_shape(precision, n_qubits, u=0, minb=0, waves=0):
+    """csim_set_launch_shape: fix (u, minb, waves) for a class; u = 0 clears."""
+    _check(_lib.csim_set_launch_shape(int(precision), int(n_qubits), int(u), int(minb), int(waves)))
 
 
 class TuneResult(C.Structure):

@@ -500,6 +500,121 @@ csim_status csim_compile(csim_circuit* c) {
   return CSIM_OK;
 }
 
+csim_status csim_set_launch_shape(csim_precision prec, int32_t n_qubits, int32_t u, int32_t minb,
+                                  int32_t waves) {
+  if (prec != CSIM_C64 && prec != CSIM_C128) return fail(CSIM_ERR_ARG, "bad precision");
+  if (n_qubits < 7 || n_qubits >= 64) return fail(CSIM_ERR_ARG, "qubit count out of range");
+  if (u == 0) {
+    csim::set_launch_shape(prec, n_qubits, nullptr);
+    return CSIM_OK;
+  }
+  const csim::LaunchShape sh{u, minb, waves};
+  if (!csim::valid_launch_shape(prec, sh)) return fail(CSIM_ERR_ARG, "unsupported launch shape");
+  csim::set_launch_shape(prec, n_qubits, &sh);
+  return CSIM_OK;
+}
+
+csim_status csim_tune_launch(csim_circuit* c, csim_precision prec, int32_t max_steps,
+                             int32_t reps, csim_launch_tune_t* out) {
+  if (!c || !out) return fail(CSIM_ERR_ARG, "null argument");
+  if (prec != CSIM_C64 && prec != CSIM_C128) return fail(CSIM_ERR_ARG, "bad precision");
+  if (max_steps < 1 || reps < 1) return fail(CSIM_ERR_ARG, "max_steps and reps must be positive");
+  if (c->exec != CSIM_EXEC_FUSED) return fail(CSIM_ERR_ARG, "the launch tuner needs fused mode");
+  *out = csim_launch_tune_t{};
+  const int n = c->L.n;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "csim_tune_launch: stream");
+  std::string err;
+  if (!csim::ensure_program(c, st, &err)) {
+    cudaStreamDestroy(st);
+    return fail(CSIM_ERR_CUDA, err);
+  }
+  e = csim::build_src_index(&c->prog, st, kSrcIndexTables);
+  const size_t bytes = ((size_t)1 << n) * (prec == CSIM_C64 ? 8 : 16);
+  void* buf[2] = {nullptr, nullptr};
+  if (e == cudaSuccess) e = cudaMalloc(&buf[0], bytes);
+  if (e == cudaSuccess && c->prog.pingpong) e = cudaMalloc(&buf[1], bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    if (buf[0]) cudaFree(buf[0]);
+    cudaStreamDestroy(st);
+    return fail(CSIM_ERR_OOM, "csim_tune_launch: scratch state");
+  }
+  // finite amplitudes of about 0.01: every trial does real arithmetic
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf[0], 0x3c, bytes, st);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  const int64_t last = std::min<int64_t>((int64_t)c->prog.steps.size(), max_steps);
+  // candidates: the default first, then the other kernel variants and grids
+  const csim::LaunchShape def = csim::default_launch_shape(prec);
+  std::vector<csim::LaunchShape> cand{def};
+  const int uvals[] = {1, 2, 4}, mvals[] = {1, 2, 4}, wvals[] = {1, 2, 4, 8};
+  for (int u : uvals)
+    for (int m : mvals) {
+      if (u == 4 && m == 4) continue;  // no such kernel (launch_sweep runs it as 1, 4)
+      for (int w : wvals) {
+        const csim::LaunchShape x{u, m, w};
+        if (x.u == def.u && x.minb == def.minb && x.waves == def.waves) continue;
+        // the default kernel at other grids, and other kernels at the default grid
+        if (!(x.u == def.u && x.minb == def.minb) && x.waves != def.waves) continue;
+        cand.push_back(x);
+      }
+    }
+  csim::LaunchShape saved;
+  const bool had = csim::launch_shape_for(prec, n, &saved);
+  double best = 1e300;
+  csim::LaunchShape pick = def;
+  for (const csim::LaunchShape& x : cand) {
+    if (e != cudaSuccess) break;
+    csim::set_launch_shape(prec, n, &x);
+    int cur = 0;
+    e = csim::run_program_steps(c->prog, buf, &cur, prec, st, 0, last);  // untimed
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+      e = csim::run_program_steps(c->prog, buf, &cur, prec, st, 0, last);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) break;
+    const double per = (double)ms / reps;
+    if (out->n_trials < 32) {
+      const int k = out->n_trials++;
+      out->trial_u[k] = x.u;
+      out->trial_minb[k] = x.minb;
+      out->trial_waves[k] = x.waves;
+      out->trial_ms[k] = per;
+    }
+    if (&x == &cand.front()) out->ms_default = per;
+    if (per < best) {
+      best = per;
+      pick = x;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  for (void* q : buf)
+    if (q) cudaFree(q);
+  cudaStreamDestroy(st);
+  if (e != cudaSuccess) {
+    if (had)
+      csim::set_launch_shape(prec, n, &saved);
+    else
+      csim::set_launch_shape(prec, n, nullptr);
+    return cuda_fail(e, "csim_tune_launch");
+  }
+  csim::set_launch_shape(prec, n, &pick);
+  out->u = pick.u;
+  out->minb = pick.minb;
+  out->waves = pick.waves;
+  out->ms = best;
+  out->steps = (int32_t)last;
+  return CSIM_OK;
+}
+
 csim_status csim_set_exec(csim_circuit* c, csim_exec mode) {
   if (!c) return fail(CSIM_ERR_ARG, "null argument");
   if (mode != CSIM_EXEC_FUSED && mode != CSIM_EXEC_GATE) return fail(CSIM_ERR_ARG, "bad mode");

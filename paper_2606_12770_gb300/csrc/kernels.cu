@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -1297,14 +1298,27 @@ SweepCfg sweep_cfg() {
 // blocks per SM x waves (CSIM_SWEEP_WAVES overrides; default 4).  Measured on
 // the 32-qubit QSVT circuit: 4 waves is 3% faster than one persistent wave,
 // which also reads more from DRAM.
+// A tuned launch shape (launch_sweep) sets the waves of the launches it makes
+// on this thread.
+thread_local int t_waves = 0;
+
 int sweep_waves() {
   static const int w = [] {
     const char* e = std::getenv("CSIM_SWEEP_WAVES");
     const int v = e ? std::atoi(e) : 4;
     return (v >= 1 && v <= 64) ? v : 4;
   }();
-  return w;
+  return t_waves > 0 ? t_waves : w;
 }
+
+// Tuned launch shapes per (precision, qubit count): u | minb << 4 | waves << 8,
+// 0 for none.
+std::atomic<uint32_t> g_shapes[2][64];
+
+struct WavesScope {
+  explicit WavesScope(int w) { t_waves = w; }
+  ~WavesScope() { t_waves = 0; }
+};
 
 // Co-resident blocks of one sweep-kernel instantiation on the device (cached).
 template <typename R, int U, int MINB, int SHAPE = 0, int BLK = 256>
@@ -1493,11 +1507,57 @@ cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const Sweep
     return cudaGetLastError();
   }
   const SweepCfg c = sweep_cfg();
+  int u = prec == CSIM_C64 ? c.u64 : c.u128, minb = prec == CSIM_C64 ? c.minb64 : c.minb128;
+  // a tuned shape for this class, except on the sweeps that complete a sparse
+  // init (their zero handling exists in the default variant only)
+  LaunchShape t;
+  const bool tuned = a.zero_map == nullptr && launch_shape_for(prec, n, &t);
+  if (tuned) {
+    u = t.u;
+    minb = t.minb;
+  }
+  WavesScope ws(tuned ? t.waves : 0);
   if (prec == CSIM_C64)
-    launch_sweep_r<float>(in, out, ntiles, c.u64, c.minb64, a, st);
+    launch_sweep_r<float>(in, out, ntiles, u, minb, a, st);
   else
-    launch_sweep_r<double>(in, out, ntiles, c.u128, c.minb128, a, st);
+    launch_sweep_r<double>(in, out, ntiles, u, minb, a, st);
   return cudaGetLastError();
+}
+
+bool valid_launch_shape(int prec, const LaunchShape& s) {
+  if (s.waves < 1 || s.waves > 64) return false;
+  if (!(s.u == 1 || s.u == 2 || s.u == 4) || !(s.minb == 1 || s.minb == 2 || s.minb == 4))
+    return false;
+  if (s.u == 4 && s.minb == 4) return false;  // not a kernel variant
+  (void)prec;
+  return true;
+}
+
+void set_launch_shape(int prec, int n, const LaunchShape* s) {
+  if (n < 0 || n >= 64) return;
+  const int p = prec == CSIM_C64 ? 0 : 1;
+  const uint32_t v = s ? (uint32_t)s->u | ((uint32_t)s->minb << 4) | ((uint32_t)s->waves << 8) : 0u;
+  g_shapes[p][n].store(v, std::memory_order_relaxed);
+}
+
+bool launch_shape_for(int prec, int n, LaunchShape* s) {
+  if (n < 0 || n >= 64) return false;
+  const uint32_t v = g_shapes[prec == CSIM_C64 ? 0 : 1][n].load(std::memory_order_relaxed);
+  if (v == 0u) return false;
+  s->u = (int)(v & 15u);
+  s->minb = (int)((v >> 4) & 15u);
+  s->waves = (int)(v >> 8);
+  return true;
+}
+
+LaunchShape default_launch_shape(int prec) {
+  const SweepCfg c = sweep_cfg();
+  const int save = t_waves;
+  t_waves = 0;
+  LaunchShape s{prec == CSIM_C64 ? c.u64 : c.u128, prec == CSIM_C64 ? c.minb64 : c.minb128,
+                sweep_waves()};
+  t_waves = save;
+  return s;
 }
 
 cudaError_t launch_perm_index(uint32_t* src, int n, const SweepParams& a, cudaStream_t st) {

@@ -151,6 +151,17 @@ int sweep_zero_kind(int prec, int n, const SweepParams& a);
 cudaError_t launch_zero_unmarked(void* state, int prec, int n, const uint32_t* map,
                                  cudaStream_t st);
 cudaError_t launch_gate(void* state, int prec, int n, const csim_gate& g, cudaStream_t st);
+// Launch shape of the sweeps of one (precision, qubit count) class: tiles per
+// warp iteration, minimum resident blocks per SM, grid in resident waves.
+// set_launch_shape (nullptr clears) makes launch_sweep use it for that class
+// in this process; the sweeps that complete a sparse init keep the default.
+struct LaunchShape {
+  int u, minb, waves;
+};
+bool valid_launch_shape(int prec, const LaunchShape& s);
+void set_launch_shape(int prec, int n, const LaunchShape* s);
+bool launch_shape_for(int prec, int n, LaunchShape* s);
+LaunchShape default_launch_shape(int prec);
 cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
                          cudaStream_t st);
 // src[x] = the segments of `a` applied to chunk index x, for every chunk of an

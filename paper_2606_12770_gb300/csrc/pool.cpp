@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cstddef>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -359,6 +360,14 @@ bool batch_eligible(const Request& r) {
   return true;
 }
 
+bool batch_by_level() {
+  static const bool v = [] {
+    const char* e = std::getenv("CSIM_BATCH_ORDER");
+    return e && std::strcmp(e, "level") == 0;
+  }();
+  return v;
+}
+
 // The persistent path of an admission pass (see csim.h): uploads and plain
 // inits, the source-index tables, one launch over every request's sweeps
 // (items queued level by level), then norms, compactions and result copies,
@@ -446,30 +455,40 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
       drop = (uint32_t)prog_steps[q][1];  // resolved to an item index below
     r.batched = true;
   }
-  // items level by level: step k of every request before step k + 1 of any,
-  // the largest requests first within a level, so that the other requests'
-  // items of the level separate the tail of a large request's step from its
-  // next step
-  std::vector<csim::BatchItem> items;
-  size_t levels = 0;
-  for (const auto& v : prog_steps) levels = std::max(levels, v.size());
-  std::vector<size_t> order(prog_steps.size());
-  for (size_t q = 0; q < order.size(); ++q) order[q] = q;
-  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
-    return P->reqs[started[x].first].c->L.n > P->reqs[started[y].first].c->L.n;
+  // The queue order of the steps.  Every step comes after the previous step
+  // of its request, which is all the kernel's progress needs.  By progress
+  // (default): step k of a request with L steps at key (k + 1) / L, so that
+  // every request advances at the same relative pace and finishes near the
+  // end of the pass; a request's consecutive steps are then separated by the
+  // other requests' items, and the pass does not end on one small request's
+  // last steps run alone.  By level (CSIM_BATCH_ORDER=level): step k of every
+  // request before step k + 1 of any.  Ties: the larger request first.
+  struct Entry {
+    double key;
+    int n;
+    size_t q, k;
+  };
+  std::vector<Entry> order;
+  for (size_t q = 0; q < prog_steps.size(); ++q) {
+    const size_t L = prog_steps[q].size();
+    for (size_t k = 0; k < L; ++k)
+      order.push_back(Entry{batch_by_level() ? (double)k : (double)(k + 1) / (double)L,
+                            P->reqs[started[q].first].c->L.n, q, k});
+  }
+  std::stable_sort(order.begin(), order.end(), [](const Entry& x, const Entry& y) {
+    if (x.key != y.key) return x.key < y.key;
+    return x.n > y.n;
   });
+  std::vector<csim::BatchItem> items;
   uint32_t drop_item = ~0u;
-  for (size_t lv = 0; lv < levels; ++lv)
-    for (size_t q : order) {
-      if (lv >= prog_steps[q].size()) continue;
-      const int gs = prog_steps[q][lv];
-      const Request& r = P->reqs[started[q].first];
-      const uint32_t ntiles = 1u << (r.c->L.n - 7);
-      for (uint32_t c0 = 0; c0 < ntiles; c0 += item_tiles) {
-        if ((uint32_t)gs == drop && drop_item == ~0u) drop_item = (uint32_t)items.size();
-        items.push_back(csim::BatchItem{(uint32_t)gs, c0, std::min(ntiles, c0 + item_tiles)});
-      }
+  for (const Entry& en : order) {
+    const int gs = prog_steps[en.q][en.k];
+    const uint32_t ntiles = 1u << (en.n - 7);
+    for (uint32_t c0 = 0; c0 < ntiles; c0 += item_tiles) {
+      if ((uint32_t)gs == drop && drop_item == ~0u) drop_item = (uint32_t)items.size();
+      items.push_back(csim::BatchItem{(uint32_t)gs, c0, std::min(ntiles, c0 + item_tiles)});
     }
+  }
   // the tables in one stream-ordered allocation, freed after the launch
   const size_t o_steps = 0;
   const size_t o_sps = (o_steps + steps.size() * sizeof(csim::BatchStep) + 255) & ~(size_t)255;
