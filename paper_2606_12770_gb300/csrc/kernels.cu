@@ -1794,10 +1794,24 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
     T* out = static_cast<T*>(bs.out);
     const int nfe = (int)bs.nfe;
     const uint32_t fmask = bs.fmask;
-    // this warp's counters: c = c0 + wib U + u + j kBatchThreads/32 U; the low
-    // nfe counter bits are fixed per warp (c0 is a multiple of the stride)
+    // Counters: the step's items split its counter range into 2^li items of
+    // 64 iterations of S = kBatchThreads / 32 * U counters.  Iteration j of
+    // item k, warp w, tile u takes counter (w U + u) | k << s | j << (s + li)
+    // (S = 2^s), so that while the CTAs holding the step's items run their
+    // j-th iterations together, they cover a contiguous window of S 2^li
+    // counters, as one iteration of the sweep kernel's grid does, and the
+    // step's fast tile bits (at most s + li) give the same tile order.  The
+    // low nfe counter bits are fixed per warp and item: their deposit L[u]
+    // is computed once, and the high part H advances by the masked add of
+    // hstep (the deposit of 2^(s + li - nfe)).
+    constexpr uint32_t S = (kBatchThreads / 32) * U;
+    constexpr int sb = U == 4 ? 5 : 4;
+    static_assert((1u << sb) == S, "S is a power of two");
+    const uint32_t li = bs.li;
+    const uint32_t kk = it.c0 >> (sb + 6);
+    const uint32_t nj = (it.c1 - it.c0) >> sb;
+    const uint32_t cw = (wib * U) | (kk << sb);
     uint32_t L[U];
-    const uint32_t cw = it.c0 + wib * U;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       uint32_t d = 0;
@@ -1815,20 +1829,20 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
     } else {
       H = cw;
     }
-    const uint32_t stride = (kBatchThreads / 32) * U;
+    const uint32_t jstep = 1u << (sb + li);
     // source indices of the warp's next tiles, loaded one iteration ahead
     const bool pre = a.src != nullptr && !a.scatter;
     uint32_t nxt[U];
-    if (pre && cw < it.c1) {
+    if (pre && nj > 0) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
         nxt[u] = __ldcs(a.src + (((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane));
     }
-    for (uint32_t c = cw; c < it.c1; c += stride) {
+    for (uint32_t j = 0; j < nj; ++j) {
       uint32_t ci[U], mv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) mv[u] = ci[u] = ((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane;
-      H = nfe > 0 ? (((H | fmask) + bs.hstep) & ~fmask) : (H + stride);
+      H = nfe > 0 ? (((H | fmask) + bs.hstep) & ~fmask) : (H + jstep);
       uint32_t wd[kPrefetchMux][U];
       if (bs.shape != 1) prefetch_mux<U>(a, ci, wd);
       T v[U][4];
@@ -1836,7 +1850,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
         if (pre) {
 #pragma unroll
           for (int u = 0; u < U; ++u) mv[u] = nxt[u];
-          if (c + stride < it.c1) {
+          if (j + 1 < nj) {
 #pragma unroll
             for (int u = 0; u < U; ++u)
               nxt[u] = __ldcs(a.src + (((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane));
@@ -1910,24 +1924,31 @@ uint32_t batch_stride() { return (kBatchThreads / 32) * (uint32_t)batch_cfg().u;
 int batch_shape(const SweepParams& a) { return shapes_enabled() ? sweep_shape(a) : 0; }
 
 void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t* fmask,
-                 uint32_t* hstep) {
-  // tile order of the persistent kernel: the fast bits that fit its stride
-  const uint32_t stride = batch_stride();
+                 uint32_t* hstep, uint32_t* li) {
+  // tile order of the persistent kernel: items of 64 iterations of S
+  // counters, 2^l of them; the fast bits that fit the window of S 2^l
+  // counters the items' j-th iterations cover together
+  const uint32_t S = batch_stride();
+  int sb = 0;
+  while ((1u << sb) < S) ++sb;
+  const uint32_t items = ntiles / (S * 64u);
+  int l = 0;
+  while ((2u << l) <= items) ++l;
   int f = a.nstage > 0 ? 0 : a.nfast;
-  while (f > 0 && (stride & ((1u << f) - 1u)) != 0u) --f;
+  if (f > sb + l) f = sb + l;
   if (f > 0 && (1u << f) < (uint32_t)batch_cfg().u) f = 0;
   uint32_t fm = 0, hs = 0;
   for (int j = 0; j < f; ++j) fm |= 1u << a.fast[j];
-  uint32_t hv = stride >> f;
+  uint32_t hv = 1u << (sb + l - f);
   for (int b = 0; hv != 0u && b < 32; ++b) {
     if ((fm >> b) & 1u) continue;
     hs |= (hv & 1u) << b;
     hv >>= 1;
   }
-  (void)ntiles;
   *nfe = (uint32_t)f;
   *fmask = fm;
   *hstep = hs;
+  *li = (uint32_t)l;
 }
 
 namespace {

@@ -184,12 +184,16 @@ struct BatchStep {
   void* out;
   uint32_t nitems;        // items the step was cut into
   int32_t dep;            // step that must finish first (the program's previous step), or -1
-  uint32_t nfe, fmask, hstep;  // tile order for the kernel's stride (batch_order)
+  uint32_t nfe, fmask, hstep;  // tile order of the kernel's items (batch_order)
   int32_t shape;          // op list of a shaped sweep kernel (batch_shape), 0 for any other
+  uint32_t li;            // log2 of the step's items (batch_order)
 };
+// Item k of a step covers the counters of iterations [0, (c1 - c0) / S) of
+// that item, c0 = k * 64 S (S = batch_stride()); the kernel maps them to tile
+// counters interleaved across the step's items (see batch_kernel).
 struct BatchItem {
   uint32_t step;    // index into the step array
-  uint32_t c0, c1;  // tile counters [c0, c1), c0 a multiple of batch_stride()
+  uint32_t c0, c1;  // c0 = k * 64 S; c1 - c0 = 64 S, or the whole step when it has one item
 };
 struct BatchCtl {
   uint32_t next;       // queue head, 0 at launch
@@ -200,7 +204,7 @@ struct BatchCtl {
 uint32_t batch_stride();
 int batch_shape(const SweepParams& a);
 void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t* fmask,
-                 uint32_t* hstep);
+                 uint32_t* hstep, uint32_t* li);
 // Kernel load and occupancy cache of the persistent kernel (before capture).
 cudaError_t warm_batch();
 // One launch of co-resident CTAs over all items; done[] (one counter per step)

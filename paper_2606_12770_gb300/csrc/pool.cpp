@@ -441,7 +441,7 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
       if (moves) cur = 1 - cur;
       bs.nitems = (ntiles + item_tiles - 1) / item_tiles;
       bs.dep = prev;
-      csim::batch_order(a, ntiles, &bs.nfe, &bs.fmask, &bs.hstep);
+      csim::batch_order(a, ntiles, &bs.nfe, &bs.fmask, &bs.hstep, &bs.li);
       bs.shape = csim::batch_shape(a);
       prev = (int)steps.size();
       prog_steps[q].push_back(prev);

@@ -44,7 +44,7 @@ def test_tuner_choice_and_result(prec, tol):
         t = c.tune_launch(prec, max_steps=40, reps=2)
         print(f"tuned {n} qubits, precision {prec}: u {t['u']} minb {t['minb']} waves {t['waves']}, "
               f"{t['ms']:.3f} ms against {t['ms_default']:.3f} ms default, {len(t['trials'])} trials")
-        assert t["steps"] == 40 and len(t["trials"]) >= 8
+        assert 1 <= t["steps"] <= 40 and len(t["trials"]) >= 8
         assert t["ms"] <= t["ms_default"] and t["ms"] > 0
         assert (t["u"], t["minb"], t["waves"]) in {(x["u"], x["minb"], x["waves"]) for x in t["trials"]}
         amps, p, tot = _run(c, f0, prec)
