@@ -467,7 +467,8 @@ csim_status csim_pool_cancel(csim_pool* p, int64_t id);
  * fail at its admission as if the host or the arena refused it
  * (CSIM_INJECT_PINNED: the pinned staging; CSIM_INJECT_ARENA: the arena
  * blocks; CSIM_INJECT_NONE clears), or, in persistent mode, keep one work
- * item of the request's second sweep from signalling its completion
+ * item of the second sweep the launch runs for the request from signalling
+ * its completion
  * (CSIM_INJECT_BATCH_SIGNAL): the items that depend on it wait out their
  * time limit and the whole pass reports CSIM_ERR_TIMEOUT.  Nothing is faulted
  * on the device.
@@ -480,7 +481,10 @@ csim_status csim_pool_cancel(csim_pool* p, int64_t id);
  * inits, one launch of a persistent kernel over the sweeps of all of them,
  * then their norms and compactions, all on the stream of the pass's first
  * slot; its other requests run on their own streams as in stream mode
- * (use_graphs is not combined with it).  The kernel's CTAs take work items (a
+ * (use_graphs is not combined with it).  The launch takes the sweeps with the
+ * four op lists of the QSVT circuits' sweeps, gathers from source-index
+ * tables; a request with any other step runs on its stream.  The sweeps that
+ * complete a sparse init run before the launch, with the sweep kernels.  The kernel's CTAs take work items (a
  * range of 1024 tile counters of one sweep of one request) from a queue in
  * device memory, level by level with the largest requests first, and wait,
  * with a 2 s limit per wait, for the previous sweep of the same request;

@@ -1734,8 +1734,10 @@ constexpr uint64_t kBatchWaitNs = 2000000000ull;  // a dependency wait gives up 
 // the next item (a range of tile counters of one step) from a queue in
 // global memory; an item waits, with a time limit, until every item of the
 // step it depends on (the same program's previous step) has signalled; then
-// its warps apply the step to their tiles (the sweep kernels' op bodies)
-// and the CTA signals.  Items are queued level by level (step k of every
+// its warps apply the step to their tiles (the sweep kernels' op bodies for
+// the four sweep op lists; the pool sends only such steps, gathers with
+// source-index tables, and runs the sweeps that complete a sparse init
+// before the launch) and the CTA signals.  Items are queued level by level (step k of every
 // program before step k + 1 of any), and an item only waits on items earlier
 // in the queue, which running CTAs have already taken: the earliest
 // unfinished item never waits, so the launch progresses whether or not all
@@ -1831,7 +1833,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
     }
     const uint32_t jstep = 1u << (sb + li);
     // source indices of the warp's next tiles, loaded one iteration ahead
-    const bool pre = a.src != nullptr && !a.scatter;
+    const bool pre = a.src != nullptr;
     uint32_t nxt[U];
     if (pre && nj > 0) {
 #pragma unroll
@@ -1846,46 +1848,30 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
       uint32_t wd[kPrefetchMux][U];
       if (bs.shape != 1) prefetch_mux<U>(a, ci, wd);
       T v[U][4];
-      if (!a.scatter) {
-        if (pre) {
+      // gathers load their source indices (one iteration ahead); the other
+      // sweeps do not move data (mv = ci)
+      if (pre) {
 #pragma unroll
-          for (int u = 0; u < U; ++u) mv[u] = nxt[u];
-          if (j + 1 < nj) {
+        for (int u = 0; u < U; ++u) mv[u] = nxt[u];
+        if (j + 1 < nj) {
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-              nxt[u] = __ldcs(a.src + (((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane));
-          }
-        } else {
-          permute<U>(a, mv);
+          for (int u = 0; u < U; ++u)
+            nxt[u] = __ldcs(a.src + (((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane));
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)mv[u] << 2), v[u]);
-        // the same op bodies as the sweep kernels (shaped where the step has
-        // one of their op lists), so a request's result does not depend on
-        // which path ran it
-        switch (bs.shape) {
-          case 1: apply_shaped<R, U, 1>(a, v, ci, lane, wd); break;
-          case 2: apply_shaped<R, U, 2>(a, v, ci, lane, wd); break;
-          case 3: apply_shaped<R, U, 3>(a, v, ci, lane, wd); break;
-          case 4: apply_shaped<R, U, 4>(a, v, ci, lane, wd); break;
-          default: apply_ops<R, U>(a, v, ci, lane, wd); break;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          store_chunk(out + ((size_t)(a.inplace ? mv[u] : ci[u]) << 2), v[u]);
-      } else {
-#pragma unroll
-        for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)ci[u] << 2), v[u]);
-        apply_ops<R, U>(a, v, ci, lane, wd);
-        if (a.src) {
-#pragma unroll
-          for (int u = 0; u < U; ++u) mv[u] = __ldcs(a.src + ci[u]);
-        } else {
-          permute<U>(a, mv);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) store_chunk(out + ((size_t)mv[u] << 2), v[u]);
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) load_chunk(in + ((size_t)mv[u] << 2), v[u]);
+      // the sweep kernels' op bodies, so a request's result does not depend
+      // on which path ran it
+      switch (bs.shape) {
+        case 1: apply_shaped<R, U, 1>(a, v, ci, lane, wd); break;
+        case 2: apply_shaped<R, U, 2>(a, v, ci, lane, wd); break;
+        case 3: apply_shaped<R, U, 3>(a, v, ci, lane, wd); break;
+        default: apply_shaped<R, U, 4>(a, v, ci, lane, wd); break;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        store_chunk(out + ((size_t)(a.inplace ? mv[u] : ci[u]) << 2), v[u]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1898,16 +1884,16 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
 }  // namespace
 
 // Tiles per warp iteration and CTAs per SM of the persistent kernel
-// (CSIM_BATCH_CFG="U,MINB": 2,2 without spills; 2,3 and 2,4 spill some of
-// the op bodies' registers for more loads in flight; 4,2 holds four tiles a
-// warp at 128 registers).
+// (CSIM_BATCH_CFG="U,MINB"): 2,4 by default, as the sweep kernel's complex64
+// variant, with a few of the op bodies' registers spilled; 2,2 keeps all of
+// them at half the warps; 2,3 between; 4,2 holds four tiles a warp.
 struct BatchCfg {
   int u, minb;
 };
 
 BatchCfg batch_cfg() {
   static const BatchCfg c = [] {
-    BatchCfg v{2, 3};
+    BatchCfg v{2, 4};
     if (const char* e = std::getenv("CSIM_BATCH_CFG")) {
       int u = 0, m = 0;
       if (std::sscanf(e, "%d,%d", &u, &m) == 2 &&

@@ -355,8 +355,19 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, bool in_graph, co
 // qubits, and a program of fused sweeps only (no staged high qubits).
 bool batch_eligible(const Request& r) {
   if (r.prec != CSIM_C64 || r.c->L.n < 12) return false;
-  for (const csim::Step& st : r.c->prog.steps)
-    if (st.kind != 0 || r.c->prog.params[(size_t)st.param].nstage != 0) return false;
+  const csim::Program& p = r.c->prog;
+  for (const csim::Step& st : p.steps) {
+    const csim::SweepParams& a = p.params[(size_t)st.param];
+    if (st.kind != 0 || a.nstage != 0 || a.scatter) return false;
+    // one of the four sweep op lists the kernel carries
+    const int shape = csim::batch_shape(a);
+    if (shape < 1 || shape > 4) return false;
+    // a gather from its source-index table (built in the arena)
+    if (st.gather && (r.ntab == 0 || (size_t)st.param >= p.src_tab.size() ||
+                      p.src_tab[(size_t)st.param] < 0))
+      return false;
+    if (!st.gather && a.nseg != 0) return false;
+  }
   return true;
 }
 
@@ -409,11 +420,20 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
     e = cudaMemcpyAsync(sl.d_pat, hs, pat_bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_stage, hs + pat_bytes, nnz * 16, cudaMemcpyHostToDevice, st);
+    // sparse init, as on the stream path: the tiles of b only, the zeros
+    // left to the program's leading sweeps (the tile map at the start of the
+    // second buffer)
+    const int zsteps =
+        buf[1] && csim::sparse_init_enabled() ? csim::zero_fill_steps(c, r.prec) : 0;
+    uint32_t* zmap = zsteps > 0 ? static_cast<uint32_t*>(buf[1]) : nullptr;
     if (e == cudaSuccess) {
       *where = "init";
       const uint64_t* d_idx = reinterpret_cast<const uint64_t*>(d_stage);
       const double* d_val = reinterpret_cast<const double*>(d_stage + nnz * 8);
-      e = csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n, d_idx, d_val, (int64_t)nnz, st);
+      e = zmap ? csim::launch_init_sparse(buf[0], r.prec, c->L.n, d_idx, d_val, (int64_t)nnz, zmap,
+                                          st)
+               : csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n, d_idx, d_val,
+                                   (int64_t)nnz, st);
     }
     uint32_t* tabs[kMaxPoolTables] = {nullptr, nullptr};
     for (int t = 0; t < r.ntab; ++t) tabs[t] = reinterpret_cast<uint32_t*>(base + r.offs[kTabBlock + t]);
@@ -421,11 +441,18 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
       *where = "source-index tables";
       e = csim::launch_src_tables(c->prog, tabs, st);
     }
-    // the request's sweeps as batch steps, with the buffers each one reads
-    // and writes
-    const uint32_t ntiles = 1u << (c->L.n - 7);
+    // the sweeps that complete the sparse init run here, with the sweep
+    // kernels (their zero handling), before the launch on the same stream
     int cur = 0, prev = -1;
-    for (size_t j = 0; j < c->prog.steps.size(); ++j) {
+    if (e == cudaSuccess && zsteps > 0) {
+      *where = "leading sweeps";
+      e = csim::run_program_steps(c->prog, buf, &cur, r.prec, st, 0, zsteps,
+                                  r.ntab > 0 ? tabs : nullptr, zmap, zsteps);
+    }
+    // the request's other sweeps as batch steps, with the buffers each one
+    // reads and writes
+    const uint32_t ntiles = 1u << (c->L.n - 7);
+    for (size_t j = (size_t)zsteps; j < c->prog.steps.size(); ++j) {
       const csim::Step& stp = c->prog.steps[j];
       csim::SweepParams a = c->prog.params[(size_t)stp.param];
       if (r.ntab > 0 && (size_t)stp.param < c->prog.src_tab.size() &&
