@@ -538,8 +538,10 @@ def run_batch(args, rank, world, local, torch, G, dist):
     graph_error = None
     for mode in ("streams", "graphs", "persistent"):
         graphs = mode == "graphs"
-        pool = G.Pool(n_streams=8, hbm_budget=budget, max_qubits=32, use_graphs=graphs,
-                      persistent=mode == "persistent")
+        # persistent passes take half the slots each: 16 slots give passes of
+        # eight requests, two in flight
+        pool = G.Pool(n_streams=16 if mode == "persistent" else 8, hbm_budget=budget,
+                      max_qubits=32, use_graphs=graphs, persistent=mode == "persistent")
         try:
             for _ in range(max(args.warmup, 1)):
                 pool_step(pool)

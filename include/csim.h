@@ -421,6 +421,7 @@ typedef struct {
   int64_t cancelled;      /* csim_pool_cancel calls that took effect */
   int64_t batch_launches; /* admission passes run as one persistent launch */
   int64_t batch_dropped_signals; /* persistent passes launched with an injected missing signal */
+  int64_t batch_requests; /* requests whose sweeps ran in a persistent launch */
 } csim_pool_stats_t;
 
 csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out);

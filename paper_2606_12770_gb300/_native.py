@@ -519,7 +519,7 @@ class PoolStats(C.Structure):
                 ("graph_launches", C.c_int64), ("src_tables", C.c_int64),
                 ("sparse_saved_bytes", C.c_uint64), ("failed", C.c_int64),
                 ("cancelled", C.c_int64), ("batch_launches", C.c_int64),
-                ("batch_dropped_signals", C.c_int64)]
+                ("batch_dropped_signals", C.c_int64), ("batch_requests", C.c_int64)]
 
 
 class Pool:

@@ -1731,19 +1731,17 @@ constexpr int kBatchThreads = 256;
 constexpr uint64_t kBatchWaitNs = 2000000000ull;  // a dependency wait gives up after 2 s
 
 // One persistent launch over the sweeps of many programs.  Every CTA takes
-// the next item (a range of tile counters of one step) from a queue in
-// global memory; an item waits, with a time limit, until every item of the
-// step it depends on (the same program's previous step) has signalled; then
-// its warps apply the step to their tiles (the sweep kernels' op bodies for
-// the four sweep op lists; the pool sends only such steps, gathers with
-// source-index tables, and runs the sweeps that complete a sparse init
-// before the launch) and the CTA signals.  Items are queued level by level (step k of every
-// program before step k + 1 of any), and an item only waits on items earlier
-// in the queue, which running CTAs have already taken: the earliest
-// unfinished item never waits, so the launch progresses whether or not all
-// its CTAs are resident at once (another launch may share the SMs).  When a
-// wait runs out the kernel records the error and every CTA stops at its next
-// wait.
+// the head of a queue of work items in global memory (a range of tile
+// counters of one step) once every item of the step it depends on (the same
+// program's previous step) has signalled; its warps apply the step to their
+// tiles (the sweep kernels' op bodies for the four sweep op lists; the pool
+// sends only such steps, gathers with source-index tables, and runs the
+// sweeps that complete a sparse init before the launch) and the CTA
+// signals.  A claimed item never waits, and the head depends only on items
+// claimed before it, so the launch progresses whether or not all its CTAs
+// are resident at once (another launch may share the SMs).  While the head
+// waits, CTAs beyond its step's item count leave.  A wait that runs out (2 s)
+// records the error and every CTA stops.
 template <typename R, int U, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
     batch_kernel(const BatchStep* __restrict__ steps, const BatchItem* __restrict__ items,
@@ -1756,35 +1754,50 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
   __shared__ __align__(16) SweepParams s_a;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&ctl->next, 1u);
-    __syncthreads();
-    const uint32_t k = s_item;
-    if (k >= nitems) break;
-    const BatchItem it = items[k];
-    const BatchStep& bs = steps[it.step];
+    // thread 0 claims the queue's head item once the step it depends on has
+    // finished, so that no CTA holds an item it cannot start; while the head
+    // waits, CTAs beyond the head step's item count leave the launch, making
+    // room on the SMs for other launches (the next pass)
     if (threadIdx.x == 0) {
+      uint32_t got = ~0u;
       int ok = 1;
-      if (bs.dep >= 0) {
-        const uint32_t need = steps[bs.dep].nitems;
-        const uint64_t t0 = global_ns();
-        while (*reinterpret_cast<volatile uint32_t*>(done + bs.dep) < need) {
-          if (*reinterpret_cast<volatile uint32_t*>(&ctl->error) != 0u) {
-            ok = 0;
-            break;
-          }
-          if (global_ns() - t0 > kBatchWaitNs) {
-            atomicOr(&ctl->error, 1u);
-            ok = 0;
-            break;
-          }
-          __nanosleep(200);
+      const uint64_t t0 = global_ns();
+      for (;;) {
+        const uint32_t h = *reinterpret_cast<volatile uint32_t*>(&ctl->next);
+        if (h >= nitems) break;
+        if (*reinterpret_cast<volatile uint32_t*>(&ctl->error) != 0u) {
+          ok = 0;
+          break;
         }
+        const BatchStep& hs = steps[items[h].step];
+        const bool ready =
+            hs.dep < 0 || *reinterpret_cast<volatile uint32_t*>(done + hs.dep) >= steps[hs.dep].nitems;
+        if (ready) {
+          if (atomicCAS(&ctl->next, h, h + 1u) == h) {
+            got = h;
+            break;
+          }
+          continue;
+        }
+        const uint32_t gone = atomicAdd(&ctl->exited, 1u);
+        if (gridDim.x - gone > hs.nitems) break;  // surplus: leave
+        atomicSub(&ctl->exited, 1u);
+        if (global_ns() - t0 > kBatchWaitNs) {
+          atomicOr(&ctl->error, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(256);
       }
       __threadfence();
+      s_item = got;
       s_ok = ok;
     }
     __syncthreads();
-    if (!s_ok) break;
+    const uint32_t k = s_item;
+    if (!s_ok || k == ~0u) break;
+    const BatchItem it = items[k];
+    const BatchStep& bs = steps[it.step];
     {
       const uint4* src = reinterpret_cast<const uint4*>(bs.sp);
       uint4* dst = reinterpret_cast<uint4*>(&s_a);

@@ -199,7 +199,7 @@ struct BatchCtl {
   uint32_t next;       // queue head, 0 at launch
   uint32_t error;      // set when a dependency wait ran out
   uint32_t drop_item;  // an item that does not signal (tests of the timeout); ~0u: none
-  uint32_t pad;
+  uint32_t exited;     // CTAs that left the launch early, 0 at launch
 };
 uint32_t batch_stride();
 int batch_shape(const SweepParams& a);

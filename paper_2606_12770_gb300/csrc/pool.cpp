@@ -592,7 +592,10 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
   const int wi = (int)P->waves.size();
   P->waves.push_back(w);
   for (auto& [id, k] : started) P->reqs[id].wave = wi;
-  if (e == cudaSuccess) P->stats.batch_launches++;
+  if (e == cudaSuccess) {
+    P->stats.batch_launches++;
+    P->stats.batch_requests += (int64_t)started.size();
+  }
   return e;
 }
 

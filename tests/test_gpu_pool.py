@@ -198,6 +198,9 @@ def test_persistent_pass_equals_alone():
     assert len(_drain(pool, len(ids))) == len(ids)
     st = pool.stats()
     assert st["batch_launches"] >= 2 and st["completed"] == len(ids) and st["failed"] == 0
+    print(f"persistent pass: {st['batch_requests']} of {len(ids)} requests in "
+          f"{st['batch_launches']} launches")
+    assert st["batch_requests"] >= len(ids) // 2
     errs = []
     for rid, (amps0, p0, t0) in zip(ids, alone):
         amps, p, t, _ = pool.result(rid)
