@@ -1731,21 +1731,22 @@ constexpr int kBatchThreads = 256;
 constexpr uint64_t kBatchWaitNs = 2000000000ull;  // a dependency wait gives up after 2 s
 
 // One persistent launch over the sweeps of many programs.  Every CTA takes
-// the head of a queue of work items in global memory (a range of tile
-// counters of one step) once every item of the step it depends on (the same
-// program's previous step) has signalled; its warps apply the step to their
-// tiles (the sweep kernels' op bodies for the four sweep op lists; the pool
-// sends only such steps, gathers with source-index tables, and runs the
-// sweeps that complete a sparse init before the launch) and the CTA
-// signals.  A claimed item never waits, and the head depends only on items
-// claimed before it, so the launch progresses whether or not all its CTAs
-// are resident at once (another launch may share the SMs).  While the head
-// waits, CTAs beyond its step's item count leave.  A wait that runs out (2 s)
-// records the error and every CTA stops.
+// the next item of a queue in global memory (a range of tile counters of one
+// step) and waits, with a time limit, until every item of the step it
+// depends on (the same program's previous step) has signalled; its warps
+// apply the step to their tiles (the sweep kernels' op bodies for the four
+// sweep op lists; the pool sends only such steps, gathers with source-index
+// tables, and runs the sweeps that complete a sparse init before the launch)
+// and the CTA signals.  An item waits only for items earlier in the queue,
+// which running CTAs have taken, so the earliest unfinished item never waits
+// and the launch progresses whether or not all its CTAs are resident at once
+// (another launch may share the SMs).  While the queue's head waits, CTAs
+// beyond its step's item count leave.  A wait that runs out (2 s) records
+// the error and every CTA stops at its next wait.
 template <typename R, int U, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
     batch_kernel(const BatchStep* __restrict__ steps, const BatchItem* __restrict__ items,
-                 uint32_t nitems, uint32_t* done, BatchCtl* ctl) {
+                 uint32_t nitems, uint32_t* done, BatchCtl* ctl, int may_leave) {
   using T = typename V2<R>::T;
   __shared__ uint32_t s_item;
   __shared__ int s_ok;
@@ -1754,40 +1755,47 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
   __shared__ __align__(16) SweepParams s_a;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   for (;;) {
-    // thread 0 claims the queue's head item once the step it depends on has
-    // finished, so that no CTA holds an item it cannot start; while the head
-    // waits, CTAs beyond the head step's item count leave the launch, making
-    // room on the SMs for other launches (the next pass)
+    // thread 0 takes the next ticket of the queue (one atomic add) and waits
+    // until every item of the step the ticket's item depends on has
+    // signalled.  Before that, while the queue's head item cannot start yet,
+    // CTAs beyond the head step's item count leave the launch: they would
+    // only wait, and their SMs go to other launches (the next pass).
     if (threadIdx.x == 0) {
       uint32_t got = ~0u;
       int ok = 1;
-      const uint64_t t0 = global_ns();
-      for (;;) {
-        const uint32_t h = *reinterpret_cast<volatile uint32_t*>(&ctl->next);
-        if (h >= nitems) break;
-        if (*reinterpret_cast<volatile uint32_t*>(&ctl->error) != 0u) {
-          ok = 0;
-          break;
-        }
+      const uint32_t h = *reinterpret_cast<volatile uint32_t*>(&ctl->next);
+      bool leave = h >= nitems;
+      if (!leave && may_leave) {
         const BatchStep& hs = steps[items[h].step];
-        const bool ready =
-            hs.dep < 0 || *reinterpret_cast<volatile uint32_t*>(done + hs.dep) >= steps[hs.dep].nitems;
-        if (ready) {
-          if (atomicCAS(&ctl->next, h, h + 1u) == h) {
-            got = h;
-            break;
+        if (hs.dep >= 0 &&
+            *reinterpret_cast<volatile uint32_t*>(done + hs.dep) < steps[hs.dep].nitems) {
+          const uint32_t gone = atomicAdd(&ctl->exited, 1u);
+          leave = gridDim.x - gone > hs.nitems;
+          if (!leave) atomicSub(&ctl->exited, 1u);
+        }
+      }
+      if (!leave) {
+        const uint32_t t = atomicAdd(&ctl->next, 1u);
+        if (t < nitems) {
+          got = t;
+          const BatchStep& ts = steps[items[t].step];
+          if (ts.dep >= 0) {
+            const uint32_t need = steps[ts.dep].nitems;
+            const uint64_t t0 = global_ns();
+            while (*reinterpret_cast<volatile uint32_t*>(done + ts.dep) < need) {
+              if (*reinterpret_cast<volatile uint32_t*>(&ctl->error) != 0u) {
+                ok = 0;
+                break;
+              }
+              if (global_ns() - t0 > kBatchWaitNs) {
+                atomicOr(&ctl->error, 1u);
+                ok = 0;
+                break;
+              }
+              __nanosleep(200);
+            }
           }
-          continue;
         }
-        const uint32_t gone = atomicAdd(&ctl->exited, 1u);
-        if (gridDim.x - gone > hs.nitems) break;  // surplus: leave
-        atomicSub(&ctl->exited, 1u);
-        if (global_ns() - t0 > kBatchWaitNs) {
-          atomicOr(&ctl->error, 1u);
-          ok = 0;
-          break;
-        }
-        __nanosleep(256);
       }
       __threadfence();
       s_item = got;
@@ -1972,8 +1980,12 @@ void launch_batch_t(const BatchStep* d_steps, const BatchItem* d_items, uint32_t
   // the grid is the resident CTA count: more CTAs would only queue behind
   // the persistent ones.  (Progress does not depend on it: an item waits only
   // for items earlier in the queue, which running CTAs hold.)
+  static const int leave = [] {
+    const char* e = std::getenv("CSIM_BATCH_LEAVE");
+    return e && e[0] == '0' ? 0 : 1;
+  }();
   batch_kernel<float, U, MINB><<<batch_resident<U, MINB>(), kBatchThreads, 0, st>>>(
-      d_steps, d_items, nitems, d_done, d_ctl);
+      d_steps, d_items, nitems, d_done, d_ctl, leave);
 }
 
 }  // namespace
