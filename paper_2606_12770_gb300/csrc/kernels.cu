@@ -1960,17 +1960,6 @@ void batch_order(const SweepParams& a, uint32_t ntiles, uint32_t* nfe, uint32_t*
 
 namespace {
 
-// CTAs per SM the persistent kernel leaves to other work, such as the next
-// pass's preparation (CSIM_BATCH_RESERVE, default 0).
-int batch_reserve() {
-  static const int v = [] {
-    const char* e = std::getenv("CSIM_BATCH_RESERVE");
-    const int r = e ? std::atoi(e) : 0;
-    return r >= 0 && r <= 3 ? r : 0;
-  }();
-  return v;
-}
-
 template <int U, int MINB>
 int batch_resident() {
   static int resident = 0;
@@ -1980,7 +1969,6 @@ int batch_resident() {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_kernel<float, U, MINB>,
                                                   kBatchThreads, 0);
-    if (per > batch_reserve()) per -= batch_reserve();
     resident = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
   return resident;

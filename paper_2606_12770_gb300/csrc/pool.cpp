@@ -416,13 +416,10 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
     const size_t pat_bytes = 16 * (size_t)npat;
     std::memcpy(hs + pat_bytes, r.idx.data(), nnz * 8);
     std::memcpy(hs + pat_bytes + nnz * 8, r.val.data(), nnz * 8);
-    // the request's preparation on its own slot's stream, so that the
-    // requests of the pass prepare concurrently; the launch waits for all
-    const cudaStream_t rs = sl.st;
     *where = "uploads";
-    e = cudaMemcpyAsync(sl.d_pat, hs, pat_bytes, cudaMemcpyHostToDevice, rs);
+    e = cudaMemcpyAsync(sl.d_pat, hs, pat_bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(d_stage, hs + pat_bytes, nnz * 16, cudaMemcpyHostToDevice, rs);
+      e = cudaMemcpyAsync(d_stage, hs + pat_bytes, nnz * 16, cudaMemcpyHostToDevice, st);
     // sparse init, as on the stream path: the tiles of b only, the zeros
     // left to the program's leading sweeps (the tile map at the start of the
     // second buffer)
@@ -434,28 +431,23 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
       const uint64_t* d_idx = reinterpret_cast<const uint64_t*>(d_stage);
       const double* d_val = reinterpret_cast<const double*>(d_stage + nnz * 8);
       e = zmap ? csim::launch_init_sparse(buf[0], r.prec, c->L.n, d_idx, d_val, (int64_t)nnz, zmap,
-                                          rs)
+                                          st)
                : csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n, d_idx, d_val,
-                                   (int64_t)nnz, rs);
+                                   (int64_t)nnz, st);
     }
     uint32_t* tabs[kMaxPoolTables] = {nullptr, nullptr};
     for (int t = 0; t < r.ntab; ++t) tabs[t] = reinterpret_cast<uint32_t*>(base + r.offs[kTabBlock + t]);
     if (e == cudaSuccess && r.ntab > 0) {
       *where = "source-index tables";
-      e = csim::launch_src_tables(c->prog, tabs, rs);
+      e = csim::launch_src_tables(c->prog, tabs, st);
     }
     // the sweeps that complete the sparse init run here, with the sweep
     // kernels (their zero handling), before the launch on the same stream
     int cur = 0, prev = -1;
     if (e == cudaSuccess && zsteps > 0) {
       *where = "leading sweeps";
-      e = csim::run_program_steps(c->prog, buf, &cur, r.prec, rs, 0, zsteps,
+      e = csim::run_program_steps(c->prog, buf, &cur, r.prec, st, 0, zsteps,
                                   r.ntab > 0 ? tabs : nullptr, zmap, zsteps);
-    }
-    if (e == cudaSuccess && rs != st) {
-      *where = "preparation join";
-      e = cudaEventRecord(sl.ev0, rs);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, sl.ev0, 0);
     }
     // the request's other sweeps as batch steps, with the buffers each one
     // reads and writes
