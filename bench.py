@@ -106,6 +106,10 @@ NCU_TRAFFIC = {
     # the 28-qubit family member's 14 launches (dram__bytes_read + write,
     # one pass), mean per launch scaled by the 16x larger state
     ("bc1adbfeda1ad1d4", "precision-nx64-k4-nt16-d13-c64"): 64.81e9,
+    # the same sweep kernels with the persistent pool kernel and the launch
+    # tuner's table in the source; captured at the default grid (the tuner may
+    # pick another number of waves for the same kernels)
+    ("0f3b1fc150ae926c", "precision-nx64-k4-nt16-d13-c64"): 64.83e9,
 }
 
 L2_BYTES = 129 * 1000 * 1000
@@ -593,6 +597,10 @@ def run_batch(args, rank, world, local, torch, G, dist):
                    "graphs_step_s": results["graphs"][0] if "graphs" in results else graph_error,
                    "persistent_step_s": (results["persistent"][0] if "persistent" in results
                                          else None),
+                   "persistent": ({"slots": 16, "passes_per_step":
+                                   results["persistent"][1]["batch_launches"] / (args.steps + max(args.warmup, 1)),
+                                   "requests_batched": results["persistent"][1]["batch_requests"]}
+                                  if "persistent" in results else None),
                    "per_instance_loop_s": loop_s,
                    "pool_budget_bytes": st["budget"], "pool_peak_bytes": st["peak_bytes"],
                    "timing": "host wall clock per step (work spread over the pool's streams)",
