@@ -639,10 +639,12 @@ def run_batch(args, rank, world, local, torch, G, dist):
 
 
 def run_serving(args, rank, world, local, torch, G, dist):
-    """Poisson arrivals at 0.8 of the measured capacity.  Each request is
-    built and compiled on the host after it arrives (8 builder threads), then
-    submitted to the pool; latency = arrival to result.  Requests above 32
-    qubits (Nx = 256 and 1024, and the largest Nx = 64 ones) are rejected."""
+    """Poisson arrivals at 0.8 of the measured capacity (the line), after a
+    sweep of loads 0.5, 1.0 and 1.25 on the first 100 requests (its
+    config).  Each request is built and compiled on the host after it arrives
+    (8 builder threads), then submitted to the pool; latency = arrival to
+    result.  Requests above 32 qubits (Nx = 256 and 1024, and the largest
+    Nx = 64 ones) are rejected."""
     from concurrent.futures import ThreadPoolExecutor
 
     count = SERVING[args.workload]
@@ -703,42 +705,61 @@ def run_serving(args, rank, world, local, torch, G, dist):
     # algorithmic bytes of the whole request stream
     bytes_per_s = sum(est_bytes(r) for r in calib) / t_cal
     mean_bytes = sum(est_bytes(r) for r in reqs) / len(reqs)
-    rate = 0.8 * bytes_per_s / max(mean_bytes, 1.0)
-    arrivals = np.cumsum([r["gap"] for r in reqs]) / rate
-    lat = []
-    rejected = 0
-    amp_upd = 0.0
     ex = ThreadPoolExecutor(8)
+
+    def session(load, n):
+        """Poisson arrivals of the first n requests at `load` times the
+        measured byte throughput: (latencies s, rejected, amp updates, wall s,
+        arrival rate)."""
+        rate = load * bytes_per_s / max(mean_bytes, 1.0)
+        arrivals = np.cumsum([r["gap"] for r in reqs[:n]]) / rate
+        lat = []
+        rejected = 0
+        amp_upd = 0.0
+        t0 = time.perf_counter()
+        nxt = 0
+        building = {}
+        live = {}
+        while nxt < n or building or live:
+            now = time.perf_counter() - t0
+            while nxt < n and arrivals[nxt] <= now:
+                building[ex.submit(build, reqs[nxt])] = nxt
+                nxt += 1
+            for fut in [f for f in building if f.done()]:
+                i = building.pop(fut)
+                c = fut.result()
+                if c is None:
+                    rejected += 1
+                    continue
+                try:
+                    rid = pool.submit(c, I.serving_f0(reqs[i]), precs[reqs[i]["prec"]])
+                    live[rid] = (i, c)
+                except G.CsimError:
+                    rejected += 1
+            for rid in pool.poll(wait_ms=1 if live else 0):
+                i, c = live.pop(rid)
+                pool.result(rid, want_amplitudes=True)
+                lat.append(time.perf_counter() - t0 - arrivals[i])
+                amp_upd += c.info()["amp_updates_run"]
+            if not live and not building and nxt < n:
+                time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
+        return lat, rejected, amp_upd, time.perf_counter() - t0, rate
+
+    def pctl(lat, q):
+        ms = sorted(1000.0 * x for x in lat)
+        return ms[min(len(ms) - 1, int(q * len(ms)))] if ms else None
+
+    # the rate sweep (shorter prefixes), then the reported session at 0.8
+    sweep = []
+    n_sweep = min(count, 100)
+    for load in (0.5, 1.0, 1.25):
+        l2, rj, au, w2, rt = session(load, n_sweep)
+        sweep.append({"load": load, "requests": n_sweep, "arrival_rate_req_per_s": rt,
+                      "completed": len(l2), "runs_per_s": len(l2) / w2,
+                      "latency_ms_p50": pctl(l2, 0.5), "latency_ms_p99": pctl(l2, 0.99)})
     clocks = ClockSampler(local)
     clocks.start()
-    t0 = time.perf_counter()
-    nxt = 0
-    building = {}
-    live = {}
-    while nxt < count or building or live:
-        now = time.perf_counter() - t0
-        while nxt < count and arrivals[nxt] <= now:
-            building[ex.submit(build, reqs[nxt])] = nxt
-            nxt += 1
-        for fut in [f for f in building if f.done()]:
-            i = building.pop(fut)
-            c = fut.result()
-            if c is None:
-                rejected += 1
-                continue
-            try:
-                rid = pool.submit(c, I.serving_f0(reqs[i]), precs[reqs[i]["prec"]])
-                live[rid] = (i, c)
-            except G.CsimError:
-                rejected += 1
-        for rid in pool.poll(wait_ms=1 if live else 0):
-            i, c = live.pop(rid)
-            pool.result(rid, want_amplitudes=True)
-            lat.append(time.perf_counter() - t0 - arrivals[i])
-            amp_upd += c.info()["amp_updates_run"]
-        if not live and not building and nxt < count:
-            time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
-    wall = time.perf_counter() - t0
+    lat, rejected, amp_upd, wall, rate = session(0.8, count)
     clk = clocks.stop()
     ex.shutdown()
     st = pool.stats()
@@ -757,6 +778,7 @@ def run_serving(args, rank, world, local, torch, G, dist):
                    "calibration_bytes_per_s": bytes_per_s,
                    "arrival_rate_req_per_s": rate, "runs_per_s": len(lat) / wall,
                    "latency_ms_p50": pct(0.5), "latency_ms_p99": pct(0.99),
+                   "load": 0.8, "rate_sweep": sweep,
                    "pool_budget_bytes": st["budget"], "pool_peak_bytes": st["peak_bytes"],
                    "timing": "host wall clock over the serving session",
                    "parallelism": f"replicas x{world}"},
