@@ -1741,7 +1741,7 @@ constexpr uint64_t kBatchWaitNs = 2000000000ull;  // a dependency wait gives up 
 // which running CTAs have taken, so the earliest unfinished item never waits
 // and the launch progresses whether or not all its CTAs are resident at once
 // (another launch may share the SMs).  While the queue's head waits, CTAs
-// beyond its step's item count leave.  A wait that runs out (2 s) records
+// beyond the number of items left leave.  A wait that runs out (2 s) records
 // the error and every CTA stops at its next wait.
 template <typename R, int U, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
@@ -1758,8 +1758,9 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
     // thread 0 takes the next ticket of the queue (one atomic add) and waits
     // until every item of the step the ticket's item depends on has
     // signalled.  Before that, while the queue's head item cannot start yet,
-    // CTAs beyond the head step's item count leave the launch: they would
-    // only wait, and their SMs go to other launches (the next pass).
+    // CTAs beyond the number of items left in the queue leave the launch:
+    // they would only wait, and their SMs go to other launches (the next
+    // pass).
     if (threadIdx.x == 0) {
       uint32_t got = ~0u;
       int ok = 1;
@@ -1770,7 +1771,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
         if (hs.dep >= 0 &&
             *reinterpret_cast<volatile uint32_t*>(done + hs.dep) < steps[hs.dep].nitems) {
           const uint32_t gone = atomicAdd(&ctl->exited, 1u);
-          leave = gridDim.x - gone > hs.nitems;
+          leave = gridDim.x - gone > nitems - h;
           if (!leave) atomicSub(&ctl->exited, 1u);
         }
       }
