@@ -106,6 +106,27 @@ def test_argument_errors():
     assert e.value.status == N.CSIM_ERR_ARG
 
 
+def test_launch_shape_arguments():
+    """csim_set_launch_shape (host only): the kernel variants that exist are
+    accepted and cleared again; the others, waves outside 1..64 and qubit
+    counts outside 7..63 are argument errors.  csim_tune_launch refuses a
+    circuit in gate-by-gate mode before touching the device."""
+    for u, m, w in [(1, 1, 1), (2, 4, 4), (4, 2, 64), (1, 4, 8)]:
+        G.set_launch_shape(G.CSIM_C64, 30, u, m, w)
+        G.set_launch_shape(G.CSIM_C64, 30, 0)
+    for args in [(G.CSIM_C64, 30, 4, 4, 4), (G.CSIM_C64, 30, 3, 2, 4), (G.CSIM_C64, 30, 2, 3, 4),
+                 (G.CSIM_C64, 30, 2, 4, 0), (G.CSIM_C64, 30, 2, 4, 65), (G.CSIM_C128, 6, 1, 2, 4),
+                 (G.CSIM_C128, 64, 1, 2, 4), (7, 30, 1, 2, 4)]:
+        with pytest.raises(N.CsimError) as e:
+            G.set_launch_shape(*args)
+        assert e.value.status == N.CSIM_ERR_ARG
+    c = G.Circuit(4, 0.8, 2, 2, 0.1, 2, kappa_qsvt=10, d=3)
+    c.set_exec(G.CSIM_EXEC_GATE)
+    with pytest.raises(N.CsimError) as e:
+        c.tune_launch(G.CSIM_C64)
+    assert e.value.status == N.CSIM_ERR_ARG
+
+
 def test_run_before_init_is_state_error():
     c = G.Circuit(4, 0.8, 2, 2, 0.1, 2, kappa_qsvt=10, d=3)
     with pytest.raises(N.CsimError) as e:
