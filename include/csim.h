@@ -477,21 +477,20 @@ csim_status csim_pool_cancel(csim_pool* p, int64_t id);
  * Persistent mode (csim_pool_opts.persistent): submissions only queue, and
  * the next csim_pool_poll admits them, so a burst of submissions forms
  * admission passes of at most half of n_streams requests each (the next pass
- * is admitted while one runs).  A pass's complex64 requests whose programs are fused
- * sweeps (at least 12 qubits, no staged high qubits) run as their uploads and
- * inits, one launch of a persistent kernel over the sweeps of all of them,
- * then their norms and compactions, all on the stream of the pass's first
- * slot; its other requests run on their own streams as in stream mode
- * (use_graphs is not combined with it).  The launch takes the sweeps with the
- * four op lists of the QSVT circuits' sweeps, gathers from source-index
- * tables; a request with any other step runs on its stream.  The sweeps that
- * complete a sparse init run before the launch, with the sweep kernels.  The kernel's CTAs take work items (a
- * range of 1024 tile counters of one sweep of one request) from a queue in
- * device memory, level by level with the largest requests first, and wait,
- * with a 2 s limit per wait, for the previous sweep of the same request;
- * consecutive passes use different streams and may overlap.  The kernel runs
- * the sweep kernels' op bodies, so results agree with the run alone within
- * rounding. */
+ * is admitted while one runs).  A pass's complex64 requests of at least 12
+ * qubits whose steps are all sweeps with one of the four op lists of the QSVT
+ * circuits' sweeps (gathers from source-index tables) run as: their uploads,
+ * inits, tables and the sweeps that complete a sparse init (with the sweep
+ * kernels); one launch of a persistent kernel over all their other sweeps;
+ * their norms, compactions and result copies; all on the stream of the
+ * pass's first slot.  The pass's other requests run on their own streams as
+ * in stream mode (use_graphs is not combined with it).  The kernel's CTAs
+ * take work items (64 warp iterations of one sweep of one request) from a
+ * queue in device memory, ordered by each request's relative progress, and
+ * wait, with a 2 s limit per wait, for the previous sweep of the same
+ * request; at the end of the queue, CTAs beyond the items left leave, so
+ * consecutive passes (on different streams) overlap.  The kernel runs the
+ * sweep kernels' op bodies: results equal the run alone. */
 enum { CSIM_INJECT_NONE = 0, CSIM_INJECT_PINNED = 1, CSIM_INJECT_ARENA = 2,
        CSIM_INJECT_BATCH_SIGNAL = 3 };
 csim_status csim_pool_inject(csim_pool* p, int32_t what, int64_t id);
