@@ -402,55 +402,26 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
   e = cudaEventCreate(&w.start);
   if (e == cudaSuccess) e = cudaEventCreate(&w.done);
   if (e == cudaSuccess) e = cudaEventRecord(w.start, st);
-  for (size_t q = 0; q < started.size() && e == cudaSuccess; ++q) {
+  // First, on the host only: each request's leading sweeps (those that
+  // complete its sparse init) and its other sweeps as batch steps, with the
+  // buffers each one reads and writes.  The tables are uploaded before any of
+  // the pass's device work is queued: an upload from pageable memory waits
+  // for the stream's earlier work.
+  std::vector<int> lead(started.size(), 0);
+  for (size_t q = 0; q < started.size(); ++q) {
     Request& r = P->reqs[started[q].first];
-    Slot& sl = P->slots[started[q].second];
     csim_circuit* c = r.c;
     void* buf[2] = {base + r.offs[0], r.offs[1] != ~0ull ? base + r.offs[1] : nullptr};
-    char* d_stage = base + r.offs[3];
-    const size_t nnz = r.idx.size();
-    const int npat = (int)c->pm.size();
-    char* hs = static_cast<char*>(sl.h_stage);
-    std::memcpy(hs, c->pm.data(), npat * 8);
-    std::memcpy(hs + npat * 8, c->pv.data(), npat * 8);
-    const size_t pat_bytes = 16 * (size_t)npat;
-    std::memcpy(hs + pat_bytes, r.idx.data(), nnz * 8);
-    std::memcpy(hs + pat_bytes + nnz * 8, r.val.data(), nnz * 8);
-    *where = "uploads";
-    e = cudaMemcpyAsync(sl.d_pat, hs, pat_bytes, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(d_stage, hs + pat_bytes, nnz * 16, cudaMemcpyHostToDevice, st);
-    // sparse init, as on the stream path: the tiles of b only, the zeros
-    // left to the program's leading sweeps (the tile map at the start of the
-    // second buffer)
     const int zsteps =
         buf[1] && csim::sparse_init_enabled() ? csim::zero_fill_steps(c, r.prec) : 0;
-    uint32_t* zmap = zsteps > 0 ? static_cast<uint32_t*>(buf[1]) : nullptr;
-    if (e == cudaSuccess) {
-      *where = "init";
-      const uint64_t* d_idx = reinterpret_cast<const uint64_t*>(d_stage);
-      const double* d_val = reinterpret_cast<const double*>(d_stage + nnz * 8);
-      e = zmap ? csim::launch_init_sparse(buf[0], r.prec, c->L.n, d_idx, d_val, (int64_t)nnz, zmap,
-                                          st)
-               : csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n, d_idx, d_val,
-                                   (int64_t)nnz, st);
-    }
+    lead[q] = zsteps;
     uint32_t* tabs[kMaxPoolTables] = {nullptr, nullptr};
     for (int t = 0; t < r.ntab; ++t) tabs[t] = reinterpret_cast<uint32_t*>(base + r.offs[kTabBlock + t]);
-    if (e == cudaSuccess && r.ntab > 0) {
-      *where = "source-index tables";
-      e = csim::launch_src_tables(c->prog, tabs, st);
-    }
-    // the sweeps that complete the sparse init run here, with the sweep
-    // kernels (their zero handling), before the launch on the same stream
     int cur = 0, prev = -1;
-    if (e == cudaSuccess && zsteps > 0) {
-      *where = "leading sweeps";
-      e = csim::run_program_steps(c->prog, buf, &cur, r.prec, st, 0, zsteps,
-                                  r.ntab > 0 ? tabs : nullptr, zmap, zsteps);
+    for (int j = 0; j < zsteps; ++j) {  // as run_program_steps moves the state
+      const csim::Step& stp = c->prog.steps[(size_t)j];
+      if (stp.kind == 0 && stp.gather && !stp.inplace) cur = 1 - cur;
     }
-    // the request's other sweeps as batch steps, with the buffers each one
-    // reads and writes
     const uint32_t ntiles = 1u << (c->L.n - 7);
     for (size_t j = (size_t)zsteps; j < c->prog.steps.size(); ++j) {
       const csim::Step& stp = c->prog.steps[j];
@@ -545,6 +516,54 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
     if (e == cudaSuccess) e = cudaMemsetAsync(d + o_done, 0, steps.size() * 4, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d + o_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, st);
+  }
+  // each request's uploads, init, source-index tables and leading sweeps
+  for (size_t q = 0; q < started.size() && e == cudaSuccess; ++q) {
+    Request& r = P->reqs[started[q].first];
+    Slot& sl = P->slots[started[q].second];
+    csim_circuit* c = r.c;
+    void* buf[2] = {base + r.offs[0], r.offs[1] != ~0ull ? base + r.offs[1] : nullptr};
+    char* d_stage = base + r.offs[3];
+    const size_t nnz = r.idx.size();
+    const int npat = (int)c->pm.size();
+    char* hs = static_cast<char*>(sl.h_stage);
+    std::memcpy(hs, c->pm.data(), npat * 8);
+    std::memcpy(hs + npat * 8, c->pv.data(), npat * 8);
+    const size_t pat_bytes = 16 * (size_t)npat;
+    std::memcpy(hs + pat_bytes, r.idx.data(), nnz * 8);
+    std::memcpy(hs + pat_bytes + nnz * 8, r.val.data(), nnz * 8);
+    *where = "uploads";
+    e = cudaMemcpyAsync(sl.d_pat, hs, pat_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_stage, hs + pat_bytes, nnz * 16, cudaMemcpyHostToDevice, st);
+    // sparse init, as on the stream path: the tiles of b only, the zeros
+    // left to the program's leading sweeps (the tile map at the start of the
+    // second buffer)
+    const int zsteps = lead[q];
+    uint32_t* zmap = zsteps > 0 ? static_cast<uint32_t*>(buf[1]) : nullptr;
+    if (e == cudaSuccess) {
+      *where = "init";
+      const uint64_t* d_idx = reinterpret_cast<const uint64_t*>(d_stage);
+      const double* d_val = reinterpret_cast<const double*>(d_stage + nnz * 8);
+      e = zmap ? csim::launch_init_sparse(buf[0], r.prec, c->L.n, d_idx, d_val, (int64_t)nnz, zmap,
+                                          st)
+               : csim::launch_init(buf[0], r.prec, (uint64_t)1 << c->L.n, d_idx, d_val,
+                                   (int64_t)nnz, st);
+    }
+    uint32_t* tabs[kMaxPoolTables] = {nullptr, nullptr};
+    for (int t = 0; t < r.ntab; ++t) tabs[t] = reinterpret_cast<uint32_t*>(base + r.offs[kTabBlock + t]);
+    if (e == cudaSuccess && r.ntab > 0) {
+      *where = "source-index tables";
+      e = csim::launch_src_tables(c->prog, tabs, st);
+    }
+    // the sweeps that complete the sparse init, with the sweep kernels (their
+    // zero handling)
+    if (e == cudaSuccess && zsteps > 0) {
+      *where = "leading sweeps";
+      int cur = 0;
+      e = csim::run_program_steps(c->prog, buf, &cur, r.prec, st, 0, zsteps,
+                                  r.ntab > 0 ? tabs : nullptr, zmap, zsteps);
+    }
   }
   if (e == cudaSuccess) {
     *where = "persistent launch";
