@@ -222,7 +222,12 @@ csim_status csim_set_launch_shape(csim_precision prec, int32_t n_qubits, int32_t
 csim_status csim_compile(csim_circuit* c);
 
 /* Enqueue the whole QSVT circuit on the stream.  CSIM_ERR_STATE unless a
- * csim_init has loaded the state since the last run. */
+ * csim_init has loaded the state since the last run.  When the program's
+ * last sweep is the shaped last-sweep kernel of the default variant, it also
+ * sums |a|^2 of the state it writes (FP64 per-block partials; complex64
+ * amplitudes squared and added in FP32 four at a time), which the next
+ * csim_postselect takes as the total instead of reading the state again
+ * (csim_run_steps does the same when it runs the last sweep). */
 csim_status csim_run(csim_circuit* c);
 csim_status csim_sync(csim_circuit* c);
 

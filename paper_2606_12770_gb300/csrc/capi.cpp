@@ -111,6 +111,9 @@ void free_device(csim_circuit* c) {
   if (c->d_partial) cudaFree(c->d_partial);
   if (c->d_out) cudaFree(c->d_out);
   if (c->d_compact) cudaFree(c->d_compact);
+  if (c->d_npart) cudaFree(c->d_npart);
+  c->d_npart = nullptr;
+  c->norm_fused = false;
   c->d_pat = nullptr;
   c->d_partial = nullptr;
   c->d_out = nullptr;
@@ -491,6 +494,7 @@ csim_status csim_init(csim_circuit* c, const double* f0, csim_precision prec, vo
   c->loaded = true;
   c->ran = false;
   c->next_step = 0;
+  c->norm_fused = false;
   return CSIM_OK;
 }
 
@@ -622,6 +626,18 @@ csim_status csim_set_exec(csim_circuit* c, csim_exec mode) {
   return CSIM_OK;
 }
 
+// The fused-norm buffer of a run that reaches the program's last sweep, when
+// that sweep can sum |a|^2 (nullptr otherwise, or when it cannot be
+// allocated: the norms are then read separately).
+double* fused_norm_buffer(csim_circuit* c) {
+  if (!csim::program_fuses_norm(c->prog, c->prec)) return nullptr;
+  if (!c->d_npart && cudaMalloc(&c->d_npart, csim::kNormPartCap * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_npart = nullptr;
+  }
+  return c->d_npart;
+}
+
 csim_status csim_run(csim_circuit* c) {
   if (!c) return fail(CSIM_ERR_ARG, "null argument");
   if (!c->loaded) return fail(CSIM_ERR_STATE, "csim_run needs a fresh csim_init");
@@ -641,10 +657,13 @@ csim_status csim_run(csim_circuit* c) {
   int zsteps = 0;
   e = zero_map_for_run(c, &zmap, &zsteps);
   if (e != cudaSuccess) return cuda_fail(e, "csim_run: initial state");
+  double* npart = fused_norm_buffer(c);
+  c->norm_fused = false;
   e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream, c->next_step,
-                              (int64_t)c->prog.steps.size(), nullptr, zmap, zsteps);
+                              (int64_t)c->prog.steps.size(), nullptr, zmap, zsteps, npart);
   c->zero_fill = false;
   if (e != cudaSuccess) return cuda_fail(e, "csim_run");
+  c->norm_fused = npart != nullptr && !c->prog.steps.empty();
   c->next_step = (int64_t)c->prog.steps.size();
   c->loaded = false;
   c->ran = true;
@@ -674,10 +693,13 @@ csim_status csim_run_steps(csim_circuit* c, int64_t n_steps, int64_t* next_step)
     e = zero_map_for_run(c, &zmap, &zsteps);
     if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps: initial state");
   }
+  double* npart = last == total && last > c->next_step ? fused_norm_buffer(c) : nullptr;
+  if (last > c->next_step) c->norm_fused = false;
   e = csim::run_program_steps(c->prog, c->buf, &c->cur, c->prec, c->stream, c->next_step, last,
-                              nullptr, zmap, zsteps);
+                              nullptr, zmap, zsteps, npart);
   if (last >= c->zero_steps) c->zero_fill = false;
   if (e != cudaSuccess) return cuda_fail(e, "csim_run_steps");
+  if (npart) c->norm_fused = true;
   c->next_step = last;
   if (last == total) {
     c->loaded = false;
@@ -711,6 +733,7 @@ csim_status csim_restore(csim_circuit* c, const double* amps, size_t n_amps, csi
   }
   c->zero_fill = false;
   c->sparse_init = 0;
+  c->norm_fused = false;
   cudaError_t e;
   c->cur = 0;
   if (prec == CSIM_C128) {
@@ -755,8 +778,12 @@ csim_status csim_postselect(csim_circuit* c, double* out_amps, size_t cap, size_
   uint64_t lowv = 0;
   csim::mask_low_bits(c, &lowk, &lowv);
   if (e == cudaSuccess)
-    e = csim::launch_norms(c->buf[c->cur], c->prec, L.n, c->d_pat, c->d_pat + npat, npat, lowk,
-                           lowv, c->d_partial, c->d_out, c->stream);
+    e = c->norm_fused
+            ? csim::launch_norms_fused(c->buf[c->cur], c->prec, L.n, c->d_pat, c->d_pat + npat,
+                                       npat, lowk, lowv, c->d_npart, c->d_partial, c->d_out,
+                                       c->stream)
+            : csim::launch_norms(c->buf[c->cur], c->prec, L.n, c->d_pat, c->d_pat + npat, npat,
+                                 lowk, lowv, c->d_partial, c->d_out, c->stream);
   double h[2] = {0, 0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h, c->d_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream);

@@ -1577,12 +1577,34 @@ cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cuda
   return run_program_steps(p, buf, cur, prec, st, 0, (int64_t)p.steps.size(), src_tables);
 }
 
+bool program_fuses_norm(const Program& p, int prec) {
+  if (p.steps.empty()) return false;
+  const Step& s = p.steps.back();
+  return s.kind == 0 && sweep_fuses_norm(prec, p.n, p.params[(size_t)s.param]);
+}
+
 cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
                               int64_t first, int64_t last, const uint32_t* const* src_tables,
-                              const uint32_t* zero_map, int zero_steps) {
+                              const uint32_t* zero_map, int zero_steps, double* norm_part) {
+  const int64_t final_step = (int64_t)p.steps.size() - 1;
   for (int64_t k = first; k < last; ++k) {
     const Step& s = p.steps[(size_t)k];
     cudaError_t e;
+    if (k == final_step && norm_part && program_fuses_norm(p, prec)) {
+      // the last sweep, summing |a|^2 of the state it writes
+      SweepParams a = p.params[(size_t)s.param];
+      if (s.gather && src_tables && (size_t)s.param < p.src_tab.size() &&
+          p.src_tab[(size_t)s.param] >= 0) {
+        a.src = src_tables[p.src_tab[(size_t)s.param]];
+        a.src_prefetch = src_prefetch_enabled() ? 1 : 0;
+      }
+      a.norm_part = norm_part;
+      void* out = s.gather && !s.inplace ? buf[1 - *cur] : buf[*cur];
+      e = launch_sweep(buf[*cur], out, prec, p.n, a, st);
+      if (s.gather && !s.inplace) *cur = 1 - *cur;
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     if (s.kind == 1) {
       e = launch_gate(buf[*cur], prec, p.n, s.g, st);
     } else if (s.kind == 2) {

@@ -124,10 +124,17 @@ cudaError_t run_program(const Program& p, void* buf[2], int* cur, int prec, cuda
 // (launch_init_sparse) goes to the first zero_steps steps, when they are
 // among them: with zero_steps = 1, step 0 in mode 1; with 2, step 0 in mode 2
 // and step 1 in mode 3 (SweepParams::zero_mode).
+// With norm_part (kNormPartCap doubles) and program_fuses_norm, the
+// program's last sweep also sums |a|^2 of the final state into it, when it
+// is among the steps run (launch_norms_fused then takes the total from it).
 cudaError_t run_program_steps(const Program& p, void* buf[2], int* cur, int prec, cudaStream_t st,
                               int64_t first, int64_t last,
                               const uint32_t* const* src_tables = nullptr,
-                              const uint32_t* zero_map = nullptr, int zero_steps = 0);
+                              const uint32_t* zero_map = nullptr, int zero_steps = 0,
+                              double* norm_part = nullptr);
+// Whether the program's last step is a sweep that can sum the final state's
+// |a|^2 (sweep_fuses_norm).
+bool program_fuses_norm(const Program& p, int prec);
 // Host executor of a fused program (FP64, kernel semantics) for testing.
 void emulate_program(const Program& p, std::vector<double>* amps);
 

@@ -41,6 +41,11 @@ struct csim_circuit {
   double* d_out = nullptr;
   double* d_compact = nullptr;
   size_t compact_cap = 0;
+  // the last sweep's |a|^2 partials (kNormPartCap doubles), and whether they
+  // hold the total of the current state (set by a run that ended with a
+  // fused last sweep, cleared by anything else that writes the state)
+  double* d_npart = nullptr;
+  bool norm_fused = false;
 };
 
 struct csim_sv {

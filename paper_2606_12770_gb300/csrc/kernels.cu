@@ -883,6 +883,35 @@ __device__ __forceinline__ void permute(const SweepParams& a, uint32_t (&x)[U]) 
 // their deposit L[u] is computed once, and the high part H advances by a
 // masked add of hstep (the deposit of stride >> nfe).  nfe = 0 is the natural
 // order.
+// |a|^2 of one chunk (four amplitudes) for a fused norm: complex64 products
+// added in FP32 (as the norm kernel does) and widened once; complex128 in FP64.
+__device__ __forceinline__ double chunk_norm2(const float2 (&c)[4]) {
+  const float s = ((c[0].x * c[0].x + c[0].y * c[0].y) + (c[1].x * c[1].x + c[1].y * c[1].y)) +
+                  ((c[2].x * c[2].x + c[2].y * c[2].y) + (c[3].x * c[3].x + c[3].y * c[3].y));
+  return (double)s;
+}
+__device__ __forceinline__ double chunk_norm2(const double2 (&c)[4]) {
+  return ((c[0].x * c[0].x + c[0].y * c[0].y) + (c[1].x * c[1].x + c[1].y * c[1].y)) +
+         ((c[2].x * c[2].x + c[2].y * c[2].y) + (c[3].x * c[3].x + c[3].y * c[3].y));
+}
+
+// A block's fused-norm partial: warp sums, then the warps in order.
+template <int BLK>
+__device__ __forceinline__ void store_norm_partial(double acc, double* part) {
+  __shared__ double sh[BLK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31u) == 0u) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < BLK / 32; ++k) t += sh[k];
+    if (blockIdx.x + 1u < kNormPartCap) part[1 + blockIdx.x] = t;
+    if (blockIdx.x == 0) part[0] = (double)gridDim.x;
+  }
+}
+
 template <typename R, int U, int MINB, int SHAPE, int BLK = 256>
 __global__ void __launch_bounds__(BLK, MINB)
     sweep_kernel(const typename V2<R>::T* in, typename V2<R>::T* out, uint32_t ntiles, int nfe,
@@ -958,6 +987,7 @@ __global__ void __launch_bounds__(BLK, MINB)
     for (int u = 0; u < U; ++u)
       nxt[u] = __ldcs(a.src + (((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane));
   }
+  double nacc = 0.0;  // fused norm of the last sweep (SHAPE 4)
   for (uint32_t t0 = c0; t0 < ntiles; t0 += nwarps * U) {
     uint32_t ci[U], mv[U];
 #pragma unroll
@@ -1037,6 +1067,15 @@ __global__ void __launch_bounds__(BLK, MINB)
 #pragma unroll
       for (int u = 0; u < U; ++u) store_chunk(out + ((size_t)mv[u] << 2), v[u]);
     }
+    if constexpr (SHAPE == 4) {
+      if (a.norm_part) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) nacc += chunk_norm2(v[u]);
+      }
+    }
+  }
+  if constexpr (SHAPE == 4) {
+    if (a.norm_part) store_norm_partial<BLK>(nacc, a.norm_part);
   }
 }
 
@@ -1103,7 +1142,8 @@ struct Vec16<double> {
 // FP64 sums: the total over the state (streamed as 16-byte vectors) and the
 // sum over the pattern mask.  When every pattern fixes the `lowk` lowest index
 // bits to `lowv`, only the indices lowv + j 2^lowk are candidates.
-template <typename R>
+// TOTAL = false: the masked sum only (the total comes from a fused sweep).
+template <typename R, bool TOTAL = true>
 __global__ void norm_kernel(const typename V2<R>::T* __restrict__ st, uint64_t N,
                             const uint64_t* __restrict__ pm, const uint64_t* __restrict__ pv,
                             int npat, int lowk, uint64_t lowv, double* __restrict__ partial) {
@@ -1111,16 +1151,18 @@ __global__ void norm_kernel(const typename V2<R>::T* __restrict__ st, uint64_t N
   double tot = 0.0, sel = 0.0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const VT* vp = reinterpret_cast<const VT*>(st);
-  const uint64_t nv = N * sizeof(typename V2<R>::T) / sizeof(VT);
-  uint64_t i = tid;
-  // four independent 16-byte loads in flight per thread
-  for (; i + 3 * stride < nv; i += 4 * stride) {
-    const VT v0 = __ldcs(vp + i), v1 = __ldcs(vp + i + stride), v2 = __ldcs(vp + i + 2 * stride),
-             v3 = __ldcs(vp + i + 3 * stride);
-    tot += vec_norm2_4(v0, v1, v2, v3);
+  if constexpr (TOTAL) {
+    const VT* vp = reinterpret_cast<const VT*>(st);
+    const uint64_t nv = N * sizeof(typename V2<R>::T) / sizeof(VT);
+    uint64_t i = tid;
+    // four independent 16-byte loads in flight per thread
+    for (; i + 3 * stride < nv; i += 4 * stride) {
+      const VT v0 = __ldcs(vp + i), v1 = __ldcs(vp + i + stride),
+               v2 = __ldcs(vp + i + 2 * stride), v3 = __ldcs(vp + i + 3 * stride);
+      tot += vec_norm2_4(v0, v1, v2, v3);
+    }
+    for (; i < nv; i += stride) tot += vec_norm2(__ldcs(vp + i));
   }
-  for (; i < nv; i += stride) tot += vec_norm2(__ldcs(vp + i));
   const uint64_t ncand = N >> lowk;
   for (uint64_t j = tid; j < ncand; j += stride) {
     const uint64_t i = lowv | (j << lowk);
@@ -1161,6 +1203,22 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
       a += partial[2 * k];
       b += partial[2 * k + 1];
     }
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+// The total from a fused sweep's partials (norm_part[0] = their count), the
+// masked sum from the norm kernel's partials; the same order as the plain
+// reduction within each.
+__global__ void reduce_fused_kernel(const double* __restrict__ norm_part,
+                                    const double* __restrict__ partial, int nblocks,
+                                    double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int m = (int)norm_part[0];
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < m; ++k) a += norm_part[1 + k];
+    for (int k = 0; k < nblocks; ++k) b += partial[2 * k + 1];
     out[0] = a;
     out[1] = b;
   }
@@ -1675,6 +1733,45 @@ cudaError_t warm_kernels() {
   norm_resident(CSIM_C64);
   norm_resident(CSIM_C128);
   return e;
+}
+
+cudaError_t launch_norms_fused(const void* state, int prec, int n, const uint64_t* d_pm,
+                               const uint64_t* d_pv, int npat, int lowk, uint64_t lowv,
+                               const double* d_norm_part, double* d_partial, double* d_out,
+                               cudaStream_t st) {
+  const uint64_t N = 1ull << n;
+  const int blk = 256;
+  const int res = norm_resident(prec);
+  int grd = grid_for(N >> lowk, blk);
+  if (grd > res) grd = res;
+  if (grd > norm_partials_needed()) grd = norm_partials_needed();
+  if (grd < 1) grd = 1;
+  if (prec == CSIM_C64)
+    norm_kernel<float, false><<<grd, blk, 0, st>>>((const float2*)state, N, d_pm, d_pv, npat,
+                                                   lowk, lowv, d_partial);
+  else
+    norm_kernel<double, false><<<grd, blk, 0, st>>>((const double2*)state, N, d_pm, d_pv, npat,
+                                                    lowk, lowv, d_partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reduce_fused_kernel<<<1, 32, 0, st>>>(d_norm_part, d_partial, grd, d_out);
+  return cudaGetLastError();
+}
+
+bool sweep_fuses_norm(int prec, int n, const SweepParams& a) {
+  // the choice launch_sweep makes: the shaped last-sweep kernel of the
+  // default variant (complex64 <2, 4>, complex128 <1, 2>)
+  if (n < 12 || a.nstage > 0 || !shapes_enabled() || sweep_shape(a) != 4) return false;
+  const SweepCfg c = sweep_cfg();
+  int u = prec == CSIM_C64 ? c.u64 : c.u128, minb = prec == CSIM_C64 ? c.minb64 : c.minb128;
+  LaunchShape t;
+  if (a.zero_map == nullptr && launch_shape_for(prec, n, &t)) {
+    u = t.u;
+    minb = t.minb;
+  }
+  const uint32_t ntiles = 1u << (n - 7);
+  while ((uint32_t)u > ntiles) u >>= 1;
+  return prec == CSIM_C64 ? (u == 2 && minb == 4) : (u == 1 && minb == 2);
 }
 
 cudaError_t launch_norms(const void* state, int prec, int n, const uint64_t* d_pm,

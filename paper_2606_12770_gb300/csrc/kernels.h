@@ -133,8 +133,19 @@ struct SweepParams {
   // bits (state bit - 7): the warp's tile u has bit j of u in fast[j].  Gates
   // on those qubits (ops 9-11) then pair registers of two tiles of the warp.
   int nstage;
+  // The last sweep of a program (ShapeLast, the shaped kernel) may also sum
+  // |a|^2 of the state it writes: each block adds the FP64 sum of its
+  // chunks (four complex64 amplitudes squared and added in FP32, or complex128
+  // in FP64) into norm_part[1 + block], block 0 writes the block count into
+  // norm_part[0].  nullptr: no sum.  (sweep_fuses_norm says when it applies.)
+  double* norm_part;
+  uint64_t norm_pad;  // keeps the size a multiple of 16 bytes
 };
+static_assert(sizeof(SweepParams) % 16 == 0, "SweepParams is copied as 16-byte words");
 constexpr int kMaxStage = 3;
+// Doubles of a norm_part buffer: the count and one partial per block of the
+// largest sweep grid (8 blocks per SM, 64 resident waves, 152 SMs).
+constexpr size_t kNormPartCap = size_t(1) << 17;
 
 cudaError_t launch_init(void* state, int prec, uint64_t n_amps, const uint64_t* d_idx,
                         const double* d_val, int64_t count, cudaStream_t st);
@@ -162,6 +173,16 @@ bool valid_launch_shape(int prec, const LaunchShape& s);
 void set_launch_shape(int prec, int n, const LaunchShape* s);
 bool launch_shape_for(int prec, int n, LaunchShape* s);
 LaunchShape default_launch_shape(int prec);
+// Whether launch_sweep runs this sweep with the kernel that sums |a|^2 into
+// norm_part (the shaped last sweep of the default kernel variant).
+bool sweep_fuses_norm(int prec, int n, const SweepParams& a);
+// launch_norms with the total taken from a fused sweep's norm_part (the
+// masked sum is computed here); the same output (d_out[0] total, d_out[1]
+// masked).
+cudaError_t launch_norms_fused(const void* state, int prec, int n, const uint64_t* d_pm,
+                               const uint64_t* d_pv, int npat, int lowk, uint64_t lowv,
+                               const double* d_norm_part, double* d_partial, double* d_out,
+                               cudaStream_t st);
 cudaError_t launch_sweep(const void* in, void* out, int prec, int n, const SweepParams& a,
                          cudaStream_t st);
 // src[x] = the segments of `a` applied to chunk index x, for every chunk of an

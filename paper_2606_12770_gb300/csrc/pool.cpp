@@ -195,6 +195,7 @@ struct Slot {
   uint64_t* d_pat = nullptr;
   double* d_partial = nullptr;
   double* d_out = nullptr;
+  double* d_npart = nullptr;  // the last sweep's |a|^2 partials (kNormPartCap doubles)
   void* h_stage = nullptr;  // pinned: patterns, then idx, then val
   size_t h_stage_cap = 0;
   double* h_out = nullptr;  // pinned: 2 doubles
@@ -322,18 +323,24 @@ cudaError_t enqueue_request(csim_pool* P, Request& r, Slot& s, bool in_graph, co
     e = csim::launch_src_tables(c->prog, tabs, st);
   }
   int cur = 0;
+  // the last sweep sums |a|^2 as csim_run's does, so the norms equal the run
+  // alone bit for bit
+  const bool fused = csim::program_fuses_norm(c->prog, r.prec);
   if (e == cudaSuccess) {
     *where = "program";
     e = csim::run_program_steps(c->prog, buf, &cur, r.prec, st, 0, (int64_t)c->prog.steps.size(),
-                                r.ntab > 0 ? tabs : nullptr, zmap, zsteps);
+                                r.ntab > 0 ? tabs : nullptr, zmap, zsteps,
+                                fused ? s.d_npart : nullptr);
   }
   int lowk = 0;
   uint64_t lowv = 0;
   csim::mask_low_bits(c, &lowk, &lowv);
   if (e == cudaSuccess) *where = "norms";
   if (e == cudaSuccess)
-    e = csim::launch_norms(buf[cur], r.prec, c->L.n, s.d_pat, s.d_pat + npat, npat, lowk, lowv,
-                           s.d_partial, s.d_out, st);
+    e = fused ? csim::launch_norms_fused(buf[cur], r.prec, c->L.n, s.d_pat, s.d_pat + npat, npat,
+                                         lowk, lowv, s.d_npart, s.d_partial, s.d_out, st)
+              : csim::launch_norms(buf[cur], r.prec, c->L.n, s.d_pat, s.d_pat + npat, npat, lowk,
+                                   lowv, s.d_partial, s.d_out, st);
   const csim::CompactGeom g = csim::compact_geom(c);
   if (e == cudaSuccess) *where = "compaction";
   if (e == cudaSuccess && g.count)
@@ -892,6 +899,7 @@ void destroy_pool(csim_pool* P) {
     if (s.d_pat) cudaFree(s.d_pat);
     if (s.d_partial) cudaFree(s.d_partial);
     if (s.d_out) cudaFree(s.d_out);
+    if (s.d_npart) cudaFree(s.d_npart);
     if (s.h_stage) cudaFreeHost(s.h_stage);
     if (s.h_out) cudaFreeHost(s.h_out);
     if (s.h_amps) cudaFreeHost(s.h_amps);
@@ -954,6 +962,7 @@ csim_status csim_pool_create(const csim_pool_opts* opts, csim_pool** out) {
     if (e == cudaSuccess)
       e = cudaMalloc(&s.d_partial, 2 * csim::norm_partials_needed() * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s.d_out, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_npart, csim::kNormPartCap * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_out, 2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_flag, sizeof(uint32_t));
     if (e == cudaSuccess) *s.h_flag = 0;
