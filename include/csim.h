@@ -495,7 +495,9 @@ csim_status csim_pool_cancel(csim_pool* p, int64_t id);
  * wait, with a 2 s limit per wait, for the previous sweep of the same
  * request; at the end of the queue, CTAs beyond the items left leave, so
  * consecutive passes (on different streams) overlap.  The kernel runs the
- * sweep kernels' op bodies: results equal the run alone. */
+ * sweep kernels' op bodies: the amplitudes equal the run alone; each
+ * request's last sweep also sums |a|^2 per work item for its norms, which
+ * agree with the run alone up to the order of the FP64 summation. */
 enum { CSIM_INJECT_NONE = 0, CSIM_INJECT_PINNED = 1, CSIM_INJECT_ARENA = 2,
        CSIM_INJECT_BATCH_SIGNAL = 3 };
 csim_status csim_pool_inject(csim_pool* p, int32_t what, int64_t id);

@@ -1959,6 +1959,8 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
       for (int u = 0; u < U; ++u)
         nxt[u] = __ldcs(a.src + (((nfe > 0 ? (H | L[u]) : (H + L[u])) << 5) | lane));
     }
+    double* const npart = bs.shape == 4 ? bs.norm_part : nullptr;
+    double nacc = 0.0;
     for (uint32_t j = 0; j < nj; ++j) {
       uint32_t ci[U], mv[U];
 #pragma unroll
@@ -1991,6 +1993,24 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
 #pragma unroll
       for (int u = 0; u < U; ++u)
         store_chunk(out + ((size_t)(a.inplace ? mv[u] : ci[u]) << 2), v[u]);
+      if (npart) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) nacc += chunk_norm2(v[u]);
+      }
+    }
+    if (npart) {  // the item's |a|^2, in a fixed order (CTA-uniform branch)
+      __shared__ double s_norm[kBatchThreads / 32];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
+      if (lane == 0) s_norm[wib] = nacc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kBatchThreads / 32; ++w) t += s_norm[w];
+        if (kk + 1u < kNormPartCap) npart[1 + kk] = t;
+        if (kk == 0) npart[0] = (double)bs.nitems;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -208,6 +208,11 @@ struct BatchStep {
   uint32_t nfe, fmask, hstep;  // tile order of the kernel's items (batch_order)
   int32_t shape;          // op list of a shaped sweep kernel (batch_shape), 0 for any other
   uint32_t li;            // log2 of the step's items (batch_order)
+  // the request's last sweep (shape 4) may sum |a|^2 of what it writes:
+  // item k adds its FP64 sum into norm_part[1 + k], item 0 writes the item
+  // count into norm_part[0] (the layout of SweepParams::norm_part); nullptr:
+  // no sum
+  double* norm_part;
 };
 // Item k of a step covers the counters of iterations [0, (c1 - c0) / S) of
 // that item, c0 = k * 64 S (S = batch_stride()); the kernel maps them to tile

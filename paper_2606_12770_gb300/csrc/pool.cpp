@@ -453,6 +453,10 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
       sps.push_back(a);
       steps.push_back(bs);
     }
+    // the request's last sweep sums |a|^2 of the final state for its norms
+    if (!prog_steps[q].empty() && (size_t)prog_steps[q].back() + 1 == steps.size() &&
+        steps.back().shape == 4)
+      steps.back().norm_part = P->slots[started[q].second].d_npart;
     final_cur[q] = cur;
     const auto inj = P->inject.find(r.id);
     if (inj != P->inject.end() && inj->second == CSIM_INJECT_BATCH_SIGNAL &&
@@ -591,8 +595,11 @@ cudaError_t enqueue_batch(csim_pool* P, const std::vector<std::pair<int64_t, int
     uint64_t lowv = 0;
     csim::mask_low_bits(c, &lowk, &lowv);
     *where = "norms";
-    e = csim::launch_norms(fin, r.prec, c->L.n, sl.d_pat, sl.d_pat + npat, npat, lowk, lowv,
-                           sl.d_partial, sl.d_out, st);
+    const bool fused = !prog_steps[q].empty() && steps[(size_t)prog_steps[q].back()].norm_part;
+    e = fused ? csim::launch_norms_fused(fin, r.prec, c->L.n, sl.d_pat, sl.d_pat + npat, npat,
+                                         lowk, lowv, sl.d_npart, sl.d_partial, sl.d_out, st)
+              : csim::launch_norms(fin, r.prec, c->L.n, sl.d_pat, sl.d_pat + npat, npat, lowk,
+                                   lowv, sl.d_partial, sl.d_out, st);
     const csim::CompactGeom g = csim::compact_geom(c);
     if (e == cudaSuccess && g.count) {
       *where = "compaction";
