@@ -320,11 +320,18 @@ __device__ __forceinline__ void load_chunk(const double2* base, double2 (&v)[4])
                  : "=d"(v[2 * h].x), "=d"(v[2 * h].y), "=d"(v[2 * h + 1].x), "=d"(v[2 * h + 1].y)
                  : "l"(base + 2 * h));
 }
+// Complex64 chunk stores carry an L2 evict-first policy: a sweep's output is
+// read again only by the next sweep, after the whole state has streamed
+// through L2.  Measured on the 32-qubit precision circuit: 166.6 against
+// 171.4 ms per step (evict-last gave the same 166.2 ms).
 __device__ __forceinline__ void store_chunk(float2* base, const float2 (&v)[4]) {
-  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(base), "f"(v[0].x),
-               "f"(v[0].y), "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y), "f"(v[3].x),
-               "f"(v[3].y)
-               : "memory");
+  asm volatile(
+      "{\n\t.reg .b64 pol;\n\t"
+      "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+      "st.global.L2::cache_hint.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8}, pol;\n\t}" ::"l"(base),
+      "f"(v[0].x), "f"(v[0].y), "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y), "f"(v[3].x),
+      "f"(v[3].y)
+      : "memory");
 }
 __device__ __forceinline__ void store_chunk(double2* base, const double2 (&v)[4]) {
 #pragma unroll
